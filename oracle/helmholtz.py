@@ -1,0 +1,402 @@
+"""FP64 CPU oracle: Helmholtz operator, shifted-Laplacian V-cycle, GMRES, FGMRES.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+statement of what the GPU path computes.  Only tests/, the smoke check and the
+benchmark's CPU-baseline/reference legs may import it; the product path never
+does, and it shares no code with the CUDA library.
+
+All arithmetic is complex128 / float64.  Arrays are (..., ny, nx), row-major,
+unknown (iy, ix) at node index (iy, ix); values outside the grid are zero
+(zero padding of size 1 = Dirichlet, Sec. 2.4).
+
+Readings of points the paper leaves open (each also listed in the design doc):
+  * A = L - w^2 k^2 (1 - g i) with L the 5-point negative Laplacian (Eq. 2.1,
+    2.2); the shifted Laplacian is M = L - w^2 k^2 (1 - (g + beta) i)
+    (Eq. 2.4 with alpha = 1, the shift added to the attenuation).
+  * Absorbing layer: g(d) = g_max (1 - d/W)^2 for d < W cells from the nearest
+    edge (d = 0 on the outermost unknown), 0 inside; on level l the width is
+    W >> l.
+  * Coarse operators: rediscretisation on H = 2h with k^2 restricted by full
+    weighting, renormalised by the in-domain weight sum.
+  * Coarsest solve: GMRES(m) with x0 = 0, right-preconditioned by the
+    diagonal (Jacobi) of the coarsest operator, exactly m Arnoldi steps (fewer
+    only on breakdown), no relaxation on that level.
+  * Prolongation: the transposed stride-2 convolution with output size n
+    (Eq. 2.9), so that R = P^T / 4 exactly.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Eq. 2.9: full-weighting (restriction) and bilinear (prolongation) kernels.
+K_RESTRICT = np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]], dtype=np.float64) / 16.0
+K_PROLONG = np.array([[1, 2, 1], [2, 4, 2], [1, 2, 1]], dtype=np.float64) / 4.0
+
+
+# ----------------------------------------------------------------------------
+# Medium, absorbing layer, levels
+# ----------------------------------------------------------------------------
+def abc_gamma(ny: int, nx: int, width: int, gamma_max: float = 1.0) -> np.ndarray:
+    """Absorbing-layer attenuation g(x) (Eq. 2.1; the layer of Sec. 4)."""
+    iy = np.arange(ny)[:, None]
+    ix = np.arange(nx)[None, :]
+    d = np.minimum(np.minimum(iy, ny - 1 - iy), np.minimum(ix, nx - 1 - ix)).astype(np.float64)
+    g = np.zeros((ny, nx))
+    if width > 0:
+        inside = d < width
+        g[inside] = gamma_max * (1.0 - d[inside] / width) ** 2
+    return g
+
+
+@dataclass
+class Level:
+    """One grid of the hierarchy: the data that define A or M on it."""
+    ny: int
+    nx: int
+    h: float
+    omega: float
+    kappa2: np.ndarray          # (ny, nx) float64
+    gamma: np.ndarray           # (ny, nx) float64
+    beta: float = 0.0           # shift of the operator (0 -> A, 0.5 -> M)
+
+    def with_shift(self, beta: float) -> "Level":
+        return Level(self.ny, self.nx, self.h, self.omega, self.kappa2, self.gamma, beta)
+
+
+@dataclass
+class Problem:
+    """Fine-grid problem description (Sec. 2.1, 4): grid, frequency, medium, layer."""
+    kappa2: np.ndarray
+    omega: float
+    h: float
+    abc_width: int = 16
+    gamma_max: float = 1.0
+    beta: float = 0.5
+    levels: int = 3
+    nu1: int = 1
+    nu2: int = 1
+    jacobi_w: float = 0.8
+    coarse_its: int = 10
+    hierarchy: list = field(default_factory=list)
+
+    def __post_init__(self):
+        self.kappa2 = np.asarray(self.kappa2, dtype=np.float64)
+        ny, nx = self.kappa2.shape
+        k2 = self.kappa2
+        for l in range(self.levels):
+            if l > 0:
+                k2 = coarsen_kappa2(k2)
+            lny, lnx = ny >> l, nx >> l
+            g = abc_gamma(lny, lnx, self.abc_width >> l, self.gamma_max)
+            self.hierarchy.append(Level(lny, lnx, self.h * (1 << l), self.omega, k2, g, self.beta))
+
+    @property
+    def A(self) -> Level:
+        """The Helmholtz operator on the fine grid (no shift)."""
+        return self.hierarchy[0].with_shift(0.0)
+
+    @property
+    def M(self) -> Level:
+        """The shifted-Laplacian operator on the fine grid."""
+        return self.hierarchy[0]
+
+
+# ----------------------------------------------------------------------------
+# Operators (Eq. 2.2, 2.4), Jacobi
+# ----------------------------------------------------------------------------
+def diagonal(lv: Level) -> np.ndarray:
+    """Diagonal of the operator: 4/h^2 - w^2 k^2 (1 - (g + beta) i)."""
+    return 4.0 / lv.h ** 2 - lv.omega ** 2 * lv.kappa2 * (1.0 - (lv.gamma + lv.beta) * 1j)
+
+
+def apply_op(lv: Level, u: np.ndarray) -> np.ndarray:
+    """y = K u for the 5-point stencil of Eq. 2.2 (with shift beta), zero outside."""
+    up = np.zeros_like(u)
+    up[..., 1:, :] += u[..., :-1, :]
+    up[..., :-1, :] += u[..., 1:, :]
+    up[..., :, 1:] += u[..., :, :-1]
+    up[..., :, :-1] += u[..., :, 1:]
+    return diagonal(lv) * u - up / lv.h ** 2
+
+
+def residual(lv: Level, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    return f - apply_op(lv, u)
+
+
+def jacobi(lv: Level, u: np.ndarray, f: np.ndarray, w: float) -> np.ndarray:
+    """One damped Jacobi sweep: u + w D^-1 (f - K u)."""
+    return u + w * (f - apply_op(lv, u)) / diagonal(lv)
+
+
+def assemble_dense(lv: Level) -> np.ndarray:
+    """Dense matrix of the operator, assembled node by node from the stencil (Eq. 2.2)."""
+    ny, nx = lv.ny, lv.nx
+    n = ny * nx
+    K = np.zeros((n, n), dtype=np.complex128)
+    d = diagonal(lv)
+    off = -1.0 / lv.h ** 2
+    for iy in range(ny):
+        for ix in range(nx):
+            p = iy * nx + ix
+            K[p, p] = d[iy, ix]
+            for dy, dx in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                jy, jx = iy + dy, ix + dx
+                if 0 <= jy < ny and 0 <= jx < nx:
+                    K[p, jy * nx + jx] = off
+    return K
+
+
+# ----------------------------------------------------------------------------
+# Transfer operators (Eq. 2.9): stride-2 convolution, zero padding 1
+# ----------------------------------------------------------------------------
+def restrict_fw(r: np.ndarray) -> np.ndarray:
+    """Full weighting: r_H(I,J) = sum_{a,b} K_R[a,b] r_h(2I+a, 2J+b), a,b in {-1,0,1}."""
+    ny, nx = r.shape[-2:]
+    pad = np.zeros(r.shape[:-2] + (ny + 2, nx + 2), dtype=r.dtype)
+    pad[..., 1:-1, 1:-1] = r
+    out = np.zeros(r.shape[:-2] + (ny // 2, nx // 2), dtype=r.dtype)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            out += K_RESTRICT[a + 1, b + 1] * pad[..., 1 + a:1 + a + ny - 1:2, 1 + b:1 + b + nx - 1:2]
+    return out
+
+
+def prolong_bilinear(e: np.ndarray, ny: int, nx: int) -> np.ndarray:
+    """Bilinear prolongation as the transposed stride-2 convolution (output ny x nx):
+    out(2I+a, 2J+b) += K_P[a,b] e(I,J), contributions landing outside dropped."""
+    nY, nX = e.shape[-2:]
+    pad = np.zeros(e.shape[:-2] + (ny + 2, nx + 2), dtype=e.dtype)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            pad[..., 1 + a:1 + a + 2 * nY:2, 1 + b:1 + b + 2 * nX:2] += K_PROLONG[a + 1, b + 1] * e
+    return pad[..., 1:ny + 1, 1:nx + 1]
+
+
+def coarsen_kappa2(k2: np.ndarray) -> np.ndarray:
+    """Coarse-grid medium: full weighting of k^2 divided by the in-domain weight sum."""
+    return restrict_fw(k2) / restrict_fw(np.ones_like(k2))
+
+
+# ----------------------------------------------------------------------------
+# Givens rotations and small least squares (used by GMRES and FGMRES)
+# ----------------------------------------------------------------------------
+def givens(a: complex, b: complex):
+    """Rotation (c real, s complex) with [c s; -conj(s) c] [a; b] = [r; 0]."""
+    if b == 0:
+        return 1.0, 0.0j, a
+    if a == 0:
+        return 0.0, 1.0 + 0.0j, b
+    t = np.hypot(abs(a), abs(b))
+    c = abs(a) / t
+    phase = a / abs(a)
+    s = phase * np.conj(b) / t
+    return c, s, phase * t
+
+
+def back_substitute(R: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Solve the k x k upper triangular system R y = g."""
+    k = R.shape[0]
+    y = np.zeros(k, dtype=np.complex128)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - R[i, i + 1:k] @ y[i + 1:k]) / R[i, i]
+    return y
+
+
+class ArnoldiLS:
+    """Hessenberg least-squares state updated column by column with Givens rotations."""
+
+    def __init__(self, m: int, beta: float):
+        self.H = np.zeros((m + 1, m), dtype=np.complex128)    # rotated (upper triangular part)
+        self.Hraw = np.zeros((m + 1, m), dtype=np.complex128)  # the Arnoldi Hessenberg itself
+        self.cs = np.zeros(m)
+        self.sn = np.zeros(m, dtype=np.complex128)
+        self.g = np.zeros(m + 1, dtype=np.complex128)
+        self.g[0] = beta
+        self.k = 0
+
+    def add_column(self, h: np.ndarray) -> float:
+        """Append Hessenberg column j (length j+2); return the residual estimate |g_{j+1}|."""
+        j = self.k
+        self.Hraw[:j + 2, j] = h
+        col = h.astype(np.complex128).copy()
+        for i in range(j):
+            c, s = self.cs[i], self.sn[i]
+            t = c * col[i] + s * col[i + 1]
+            col[i + 1] = -np.conj(s) * col[i] + c * col[i + 1]
+            col[i] = t
+        c, s, r = givens(col[j], col[j + 1])
+        self.cs[j], self.sn[j] = c, s
+        col[j], col[j + 1] = r, 0.0
+        self.H[:j + 2, j] = col
+        self.g[j + 1] = -np.conj(s) * self.g[j]
+        self.g[j] = c * self.g[j]
+        self.k = j + 1
+        return abs(self.g[j + 1])
+
+    def solve(self) -> np.ndarray:
+        k = self.k
+        return back_substitute(self.H[:k, :k], self.g[:k])
+
+
+def _dot(u: np.ndarray, v: np.ndarray) -> complex:
+    """<u, v> = u^H v."""
+    return complex(np.vdot(u.ravel(), v.ravel()))
+
+
+def _norm(u: np.ndarray) -> float:
+    return float(np.sqrt(np.vdot(u.ravel(), u.ravel()).real))
+
+
+# ----------------------------------------------------------------------------
+# Coarsest-grid GMRES(m) with diagonal right preconditioning (Sec. 2.4, 4)
+# ----------------------------------------------------------------------------
+def gmres_jacobi(lv: Level, f: np.ndarray, m: int = 10, breakdown: float = 0.0) -> np.ndarray:
+    """m steps of GMRES on K D^-1 y = f from y0 = 0, x = D^-1 y (single right-hand side)."""
+    dinv = 1.0 / diagonal(lv)
+    beta = _norm(f)
+    if beta == 0.0:
+        return np.zeros_like(f)
+    V = [f / beta]
+    ls = ArnoldiLS(m, beta)
+    for j in range(m):
+        w = apply_op(lv, dinv * V[j])
+        h = np.zeros(j + 2, dtype=np.complex128)
+        for i in range(j + 1):                 # modified Gram-Schmidt
+            h[i] = _dot(V[i], w)
+            w = w - h[i] * V[i]
+        h[j + 1] = _norm(w)
+        ls.add_column(h)
+        if h[j + 1].real <= breakdown * beta:  # happy breakdown: the space is invariant
+            break
+        V.append(w / h[j + 1].real)
+    y = ls.solve()
+    u = np.zeros_like(f)
+    for i in range(ls.k):
+        u = u + y[i] * V[i]
+    return dinv * u
+
+
+def coarse_direct(lv: Level, f: np.ndarray) -> np.ndarray:
+    """Exact coarsest solve by the oracle's own dense LU (test mode of Alg. 1)."""
+    K = assemble_dense(lv)
+    return lu_solve(K, f.ravel()).reshape(f.shape)
+
+
+# ----------------------------------------------------------------------------
+# V-cycle (Alg. 1) on the shifted Laplacian hierarchy
+# ----------------------------------------------------------------------------
+def vcycle(prob: Problem, f: np.ndarray, v: np.ndarray | None = None, level: int = 0,
+           coarse: str = "gmres") -> np.ndarray:
+    """v <- V-cycle(v, f) for one right-hand side (ny, nx), Alg. 1 with nu1/nu2 damped
+    Jacobi sweeps, full weighting, bilinear prolongation, recursion to the coarsest level."""
+    lv = prob.hierarchy[level]
+    if v is None:
+        v = np.zeros_like(f)
+    if level == len(prob.hierarchy) - 1:
+        if coarse == "direct":
+            return coarse_direct(lv, f)
+        return gmres_jacobi(lv, f, prob.coarse_its)
+    for _ in range(prob.nu1):
+        v = jacobi(lv, v, f, prob.jacobi_w)
+    fc = restrict_fw(residual(lv, f, v))
+    vc = vcycle(prob, fc, None, level + 1, coarse)
+    v = v + prolong_bilinear(vc, lv.ny, lv.nx)
+    for _ in range(prob.nu2):
+        v = jacobi(lv, v, f, prob.jacobi_w)
+    return v
+
+
+def precond_v(prob: Problem):
+    """M_V: one SL V-cycle from a zero guess (Sec. 4)."""
+    return lambda r: vcycle(prob, r)
+
+
+# ----------------------------------------------------------------------------
+# Restarted flexible GMRES(m), right preconditioned (Eq. 2.5; Saad 1993)
+# ----------------------------------------------------------------------------
+@dataclass
+class FgmresResult:
+    x: np.ndarray
+    iters: int
+    relres: float               # final true relative residual ||b - A x|| / ||b||
+    converged: bool
+    history: list               # (iteration, relative residual estimate) per step
+    true_history: list          # true relative residual at each restart
+
+
+def fgmres(A: Level, precond, b: np.ndarray, x0: np.ndarray | None = None, m: int = 10,
+           tol: float = 1e-7, maxit: int = 2000) -> FgmresResult:
+    """Solve A x = b (one right-hand side) with restarted FGMRES(m).
+
+    Each cycle starts from the true residual r = b - A x; Arnoldi uses modified
+    Gram-Schmidt on w = A z_j with z_j = precond(v_j); the cycle ends after m
+    steps or when the Givens residual estimate drops to tol*||b||; then
+    x += Z y.  Converged when the true relative residual is <= tol."""
+    x = np.zeros_like(b) if x0 is None else x0.astype(np.complex128).copy()
+    bnorm = _norm(b)
+    if bnorm == 0.0:
+        return FgmresResult(np.zeros_like(b), 0, 0.0, True, [], [0.0])
+    iters = 0
+    history, true_history = [], []
+    while True:
+        r = b - apply_op(A, x)
+        beta = _norm(r)
+        true_history.append(beta / bnorm)
+        if beta / bnorm <= tol:
+            return FgmresResult(x, iters, beta / bnorm, True, history, true_history)
+        if iters >= maxit:
+            return FgmresResult(x, iters, beta / bnorm, False, history, true_history)
+        V = [r / beta]
+        Z = []
+        ls = ArnoldiLS(m, beta)
+        for j in range(m):
+            z = precond(V[j])
+            Z.append(z)
+            w = apply_op(A, z)
+            h = np.zeros(j + 2, dtype=np.complex128)
+            for i in range(j + 1):
+                h[i] = _dot(V[i], w)
+                w = w - h[i] * V[i]
+            h[j + 1] = _norm(w)
+            est = ls.add_column(h)
+            iters += 1
+            history.append((iters, est / bnorm))
+            if est / bnorm <= tol or h[j + 1].real == 0.0 or iters >= maxit:
+                break
+            V.append(w / h[j + 1].real)
+        y = ls.solve()
+        for i in range(ls.k):
+            x = x + y[i] * Z[i]
+
+
+def convergence_factor(history_true0: float, final: float, iters: int) -> float:
+    """Eq. 4.1: rho = (||r_T|| / ||r_0||)^(1/T)."""
+    if iters <= 0:
+        return 0.0
+    return (final / history_true0) ** (1.0 / iters)
+
+
+# ----------------------------------------------------------------------------
+# Dense LU with partial pivoting (test-mode coarse solve and the 16x16 pin)
+# ----------------------------------------------------------------------------
+def lu_solve(K: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Gaussian elimination with row partial pivoting, then two triangular solves."""
+    a = np.array(K, dtype=np.complex128)
+    n = a.shape[0]
+    piv = np.arange(n)
+    for k in range(n - 1):
+        p = k + int(np.argmax(np.abs(a[k:, k])))
+        if p != k:
+            a[[k, p]] = a[[p, k]]
+            piv[[k, p]] = piv[[p, k]]
+        a[k + 1:, k] /= a[k, k]
+        a[k + 1:, k + 1:] -= np.outer(a[k + 1:, k], a[k, k + 1:])
+    y = np.array(f, dtype=np.complex128)[piv]
+    for i in range(n):                       # L y = P f (unit lower)
+        y[i] -= a[i, :i] @ y[:i]
+    x = np.zeros(n, dtype=np.complex128)
+    for i in range(n - 1, -1, -1):           # U x = y
+        x[i] = (y[i] - a[i, i + 1:] @ x[i + 1:]) / a[i, i]
+    return x

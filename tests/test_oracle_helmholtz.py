@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle (operator, transfers, V-cycle, GMRES, FGMRES) against
+what the paper and the mathematics fix, independently of the oracle itself."""
+import numpy as np
+import pytest
+
+from conftest import load_golden_kernels
+from oracle import helmholtz as H
+from paper_2203_11025_gb300 import synth
+
+
+def _level(ny, nx, seed=0, omega=20.0, beta=0.3, width=3):
+    rng = np.random.default_rng(seed)
+    k2 = rng.uniform(0.1, 1.0, (ny, nx))
+    g = H.abc_gamma(ny, nx, width, 1.0)
+    return H.Level(ny, nx, 1.0 / nx, omega, k2, g, beta)
+
+
+def _crandn(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------- operator
+def test_stencil_matches_printed_kernel():
+    """Eq. 2.2: h^2 (A u) at an interior node of a delta reproduces the printed
+    off-centre stencil; the centre is 4 - w^2 k^2 h^2 (1 - g i)."""
+    gold = load_golden_kernels()["stencil_offdiag"]
+    lv = _level(9, 11, beta=0.0)
+    u = np.zeros((9, 11), complex)
+    u[4, 5] = 1.0
+    y = H.apply_op(lv, u) * lv.h ** 2
+    off = y[3:6, 4:7].copy()
+    centre = off[1, 1]
+    off[1, 1] = 0
+    assert np.allclose(off, gold, atol=1e-14)
+    k2, g = lv.kappa2[4, 5], lv.gamma[4, 5]
+    assert np.isclose(centre, 4 - lv.omega ** 2 * k2 * lv.h ** 2 * (1 - g * 1j), rtol=1e-14)
+
+
+def test_apply_matches_nodewise_assembly():
+    """Array-shift formulation == explicit node-by-node assembly (non-square grid)."""
+    lv = _level(7, 10, seed=1)
+    u = _crandn(np.random.default_rng(2), (7, 10))
+    K = H.assemble_dense(lv)
+    assert np.allclose(H.apply_op(lv, u).ravel(), K @ u.ravel(), rtol=1e-14, atol=1e-12)
+
+
+@pytest.mark.parametrize("ny,nx", [(12, 12), (10, 14)])
+def test_discrete_laplacian_eigenpairs(ny, nx):
+    """Constant medium, no attenuation: sin modes are eigenvectors with the closed-form
+    eigenvalue (4/h^2)[sin^2(j pi/(2(nx+1))) + sin^2(k pi/(2(ny+1)))] - w^2 k^2."""
+    h, omega, k2 = 1.0 / nx, 17.0, 0.7
+    lv = H.Level(ny, nx, h, omega, np.full((ny, nx), k2), np.zeros((ny, nx)), 0.0)
+    p = np.arange(ny)[:, None]
+    q = np.arange(nx)[None, :]
+    for j, k in [(1, 1), (2, 5), (ny, nx), (3, 1)]:
+        v = np.sin(j * np.pi * (p + 1) / (ny + 1)) * np.sin(k * np.pi * (q + 1) / (nx + 1)) + 0j
+        lam = (4 / h ** 2) * (np.sin(j * np.pi / (2 * (ny + 1))) ** 2
+                              + np.sin(k * np.pi / (2 * (nx + 1))) ** 2) - omega ** 2 * k2
+        assert np.allclose(H.apply_op(lv, v), lam * v, rtol=1e-12, atol=1e-9 * abs(lam))
+
+
+def test_complex_symmetric_and_absorbing():
+    """A^T = A (complex symmetric), and Im(x^H A x) = w^2 sum k^2 (g+beta) |x|^2 >= 0."""
+    lv = _level(6, 8, seed=3, beta=0.5)
+    K = H.assemble_dense(lv)
+    assert np.allclose(K, K.T, atol=0)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        x = _crandn(rng, (6, 8))
+        q = np.vdot(x, H.apply_op(lv, x))
+        expect = lv.omega ** 2 * np.sum(lv.kappa2 * (lv.gamma + lv.beta) * np.abs(x) ** 2)
+        assert q.imag >= 0 and np.isclose(q.imag, expect, rtol=1e-12)
+
+
+def test_abc_profile():
+    """Quadratic layer: 1 on the outermost unknowns, (1 - d/W)^2 inside, 0 in the interior."""
+    g = H.abc_gamma(40, 40, 16, 1.0)
+    assert g[0, 20] == 1.0 and g[20, 0] == 1.0 and g[39, 20] == 1.0
+    assert np.isclose(g[20, 3], (1 - 3 / 16) ** 2)
+    assert g[20, 16] == 0.0 and g[20, 20] == 0.0
+    assert np.isclose(g[5, 7], (1 - 5 / 16) ** 2)   # nearest edge decides
+
+
+# ---------------------------------------------------------------- transfers
+def test_transfer_kernels_match_paper():
+    """Eq. 2.9: P of a coarse delta is the printed bilinear kernel centred on the fine
+    node 2I; R^T of a coarse delta is the printed full-weighting kernel."""
+    gold = load_golden_kernels()
+    n = 12
+    e = np.zeros((6, 6))
+    e[2, 3] = 1.0
+    Pe = H.prolong_bilinear(e, n, n)
+    assert np.allclose(Pe[3:6, 5:8], gold["prolong"], atol=0)
+    assert np.isclose(Pe.sum(), gold["prolong"].sum())
+    # R^T e: column of R for a coarse delta, via R applied to fine deltas
+    Rt = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            d = np.zeros((n, n))
+            d[i, j] = 1.0
+            Rt[i, j] = H.restrict_fw(d)[2, 3]
+    assert np.allclose(Rt[3:6, 5:8], gold["restrict"], atol=0)
+    assert np.isclose(Rt.sum(), 1.0)
+
+
+def test_restriction_is_quarter_prolongation_transpose():
+    ny, nx = 8, 10
+    N, Nc = ny * nx, (ny // 2) * (nx // 2)
+    P = np.zeros((N, Nc))
+    R = np.zeros((Nc, N))
+    for k in range(Nc):
+        e = np.zeros(Nc)
+        e[k] = 1
+        P[:, k] = H.prolong_bilinear(e.reshape(ny // 2, nx // 2), ny, nx).ravel()
+    for k in range(N):
+        e = np.zeros(N)
+        e[k] = 1
+        R[:, k] = H.restrict_fw(e.reshape(ny, nx)).ravel()
+    assert np.array_equal(R, P.T / 4)
+
+
+def test_transfers_reproduce_constants_and_bilinears():
+    n = 16
+    c = np.full((n, n), 3.5)
+    Rc = H.restrict_fw(c)
+    assert np.allclose(Rc[1:, 1:], 3.5)            # interior coarse nodes (not touching node -1)
+    I = np.arange(n // 2)[:, None]
+    J = np.arange(n // 2)[None, :]
+    lin = 1.0 + 0.3 * (2 * I) - 0.7 * (2 * J) + 0.05 * (2 * I) * (2 * J)
+    Pl = H.prolong_bilinear(lin, n, n)
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    exact = 1.0 + 0.3 * i - 0.7 * j + 0.05 * i * j
+    assert np.allclose(Pl[:n - 1, :n - 1], exact[:n - 1, :n - 1], atol=1e-13)
+
+
+def test_coarse_operator_consistent_with_galerkin():
+    """Rediscretisation on H = 2h agrees with R A_h P on smooth interior functions to
+    O(H^2): the error drops ~4x per refinement (pins the coarse spacing and medium)."""
+    errs = []
+    for n in (32, 64, 128):
+        yy, xx = np.meshgrid(np.arange(n) / n, np.arange(n) / n, indexing="ij")
+        k2 = 0.5 + 0.3 * np.sin(2 * np.pi * xx) * np.cos(np.pi * yy)
+        prob = H.Problem(k2, omega=30.0, h=1.0 / n, abc_width=0, beta=0.5, levels=2)
+        f0, f1 = prob.hierarchy
+        Y, X = np.meshgrid(np.arange(n // 2) * 2 / n, np.arange(n // 2) * 2 / n, indexing="ij")
+        phi = np.sin(3 * X + 1) * np.cos(2 * Y) + 0j
+        gal = H.restrict_fw(H.apply_op(f0, H.prolong_bilinear(phi, n, n)))
+        red = H.apply_op(f1, phi)
+        s = slice(2, n // 2 - 2)
+        errs.append(np.abs(gal - red)[s, s].max() / np.abs(red[s, s]).max())
+    assert errs[0] < 0.02
+    assert 3.2 < errs[0] / errs[1] < 4.8 and 3.2 < errs[1] / errs[2] < 4.8
+
+
+def test_coarse_medium_is_weighted_average():
+    k2 = np.random.default_rng(5).uniform(0.0625, 1.0, (16, 16))
+    c = H.coarsen_kappa2(k2)
+    assert c.min() >= k2.min() - 1e-15 and c.max() <= k2.max() + 1e-15
+    assert np.isclose(c[3, 4], np.sum(load_golden_kernels()["restrict"] * k2[5:8, 7:10]))
+    # corner (0,0): weights 4,2,2,1 over the in-domain 2x2 block, renormalised by 9
+    assert np.isclose(c[0, 0], (4 * k2[0, 0] + 2 * k2[0, 1] + 2 * k2[1, 0] + k2[1, 1]) / 9)
+
+
+# ---------------------------------------------------------------- smoothing / V-cycle
+def test_jacobi_on_eigenmodes_closed_form():
+    """Damped Jacobi on a Dirichlet sin mode of the constant-coefficient operator multiplies
+    the error by 1 - w lambda / D exactly; the Poisson high-frequency factor is <= 0.6."""
+    n, h = 14, 1.0 / 14
+    lv = H.Level(n, n, h, 0.0, np.ones((n, n)), np.zeros((n, n)), 0.0)
+    p = np.arange(n)[:, None]
+    worst = 0.0
+    for j in range(1, n + 1):
+        for k in range(1, n + 1):
+            v = np.sin(j * np.pi * (p + 1) / (n + 1)) * np.sin(k * np.pi * (p.T + 1) / (n + 1)) + 0j
+            lam = (4 / h ** 2) * (np.sin(j * np.pi / (2 * (n + 1))) ** 2 + np.sin(k * np.pi / (2 * (n + 1))) ** 2)
+            e1 = H.jacobi(lv, v, np.zeros_like(v), 0.8)   # error propagation with f = 0
+            fac = 1 - 0.8 * lam / (4 / h ** 2)
+            assert np.allclose(e1, fac * v, atol=1e-12)
+            if max(j, k) > (n + 1) / 2:
+                worst = max(worst, abs(fac))
+    assert worst <= 0.6 + 1e-12
+
+
+def test_two_grid_equals_error_propagation_matrix():
+    """Alg. 1 with two levels and an exact coarse solve is the linear map whose error
+    propagation is S (I - P M_H^-1 R M) S, S = I - w D^-1 M (16x16 SL problem)."""
+    n = 16
+    k2 = synth.grf_kappa2(n, n, 7, sigma=2.0).astype(np.float64)
+    prob = H.Problem(k2, omega=synth.omega_for(n), h=1.0 / n, abc_width=4, levels=2)
+    M = H.assemble_dense(prob.hierarchy[0])
+    MH = H.assemble_dense(prob.hierarchy[1])
+    N, Nc = n * n, (n // 2) ** 2
+    P = np.zeros((N, Nc))
+    for k in range(Nc):
+        e = np.zeros(Nc)
+        e[k] = 1
+        P[:, k] = H.prolong_bilinear(e.reshape(n // 2, n // 2), n, n).ravel()
+    R = P.T / 4
+    S = np.eye(N) - 0.8 * M / np.diag(M)[:, None]
+    E = S @ (np.eye(N) - P @ np.linalg.solve(MH, R @ M)) @ S
+    B = np.zeros((N, N), complex)
+    for k in range(N):
+        e = np.zeros(N, complex)
+        e[k] = 1
+        B[:, k] = H.vcycle(prob, e.reshape(n, n), coarse="direct").ravel()
+    assert np.abs((np.eye(N) - B @ M) - E).max() < 1e-12
+
+
+def test_two_grid_poisson_contracts():
+    """Two-grid Poisson cycle with exact coarse solve contracts (rho < 0.5 at n = 16).
+    (With the stride-2 / pad-1 grid alignment the low-side boundaries of fine and
+    coarse grids differ by h, so deeper Poisson hierarchies do not reach the LFA value.)"""
+    n = 16
+    prob = H.Problem(np.ones((n, n)), omega=0.0, h=1.0 / n, abc_width=0, beta=0.0, levels=2)
+    A = H.assemble_dense(prob.hierarchy[0])
+    N = n * n
+    B = np.zeros((N, N), complex)
+    for k in range(N):
+        e = np.zeros(N, complex)
+        e[k] = 1
+        B[:, k] = H.vcycle(prob, e.reshape(n, n), coarse="direct").ravel()
+    rho = np.abs(np.linalg.eigvals(np.eye(N) - B @ A)).max()
+    assert 0.3 < rho < 0.5
+
+
+# ---------------------------------------------------------------- GMRES / Givens
+def test_givens_least_squares_matches_lstsq():
+    rng = np.random.default_rng(8)
+    m = 7
+    Hh = np.triu(_crandn(rng, (m + 1, m)), -1)
+    Hh[np.arange(1, m + 1), np.arange(m)] = np.abs(Hh[np.arange(1, m + 1), np.arange(m)])
+    ls = H.ArnoldiLS(m, 2.5)
+    for j in range(m):
+        est = ls.add_column(Hh[:j + 2, j])
+        rhs = np.zeros(j + 2, complex)
+        rhs[0] = 2.5
+        y_ref, *_ = np.linalg.lstsq(Hh[:j + 2, :j + 1], rhs, rcond=None)
+        assert np.isclose(est, np.linalg.norm(rhs - Hh[:j + 2, :j + 1] @ y_ref), rtol=1e-10)
+    assert np.allclose(ls.solve(), y_ref, rtol=1e-10)
+
+
+def test_gmres_minimises_over_explicit_krylov_space():
+    """GMRES(m) from 0 returns D^-1 y, y = argmin_{y in K_m(K D^-1, f)} ||f - K D^-1 y||,
+    checked against a least-squares solve over an explicitly built Krylov basis."""
+    n, m = 8, 6
+    lv = _level(n, n, seed=9, omega=9.0, beta=0.5, width=2)
+    f = _crandn(np.random.default_rng(10), (n, n))
+    x = H.gmres_jacobi(lv, f, m)
+    K = H.assemble_dense(lv)
+    dinv = 1.0 / np.diag(K)
+    B = K * dinv[None, :]
+    cols = [f.ravel() / np.linalg.norm(f)]
+    for _ in range(m - 1):
+        w = B @ cols[-1]
+        cols.append(w / np.linalg.norm(w))
+    Q, _ = np.linalg.qr(np.stack(cols, 1))
+    c, *_ = np.linalg.lstsq(B @ Q, f.ravel(), rcond=None)
+    x_ref = dinv * (Q @ c)
+    assert np.linalg.norm(x.ravel() - x_ref) / np.linalg.norm(x_ref) < 1e-8
+
+
+def test_gmres_exact_in_n_steps():
+    lv = _level(3, 4, seed=11, omega=5.0)
+    f = _crandn(np.random.default_rng(12), (3, 4))
+    x = H.gmres_jacobi(lv, f, 12)
+    assert np.linalg.norm(H.apply_op(lv, x) - f) / np.linalg.norm(f) < 1e-10
+
+
+def test_lu_solve_matches_numpy():
+    rng = np.random.default_rng(13)
+    K = _crandn(rng, (30, 30))
+    f = _crandn(rng, 30)
+    assert np.allclose(H.lu_solve(K, f), np.linalg.solve(K, f), rtol=1e-11)
+
+
+# ---------------------------------------------------------------- FGMRES
+def _small_problem(n=16, seed=14):
+    k2 = synth.grf_kappa2(n, n, seed, sigma=2.0).astype(np.float64)
+    return H.Problem(k2, omega=synth.omega_for(n), h=1.0 / n, abc_width=4, levels=3)
+
+
+def test_fgmres_vcycle_matches_dense_direct_16():
+    """FGMRES(10) + M_V on a 16x16 heterogeneous problem reproduces the dense LU solve."""
+    prob = _small_problem()
+    b = synth.point_sources(16, 16, [(8, 8)], prob.h)[0] + _crandn(np.random.default_rng(15), (16, 16))
+    res = H.fgmres(prob.A, H.precond_v(prob), b, tol=1e-13, maxit=400)
+    x_ref = H.lu_solve(H.assemble_dense(prob.A), b.ravel()).reshape(16, 16)
+    assert res.converged
+    assert np.linalg.norm(res.x - x_ref) / np.linalg.norm(x_ref) < 1e-10
+
+
+def test_fgmres_exact_preconditioner_one_step():
+    prob = _small_problem(8, 16)
+    Ainv = np.linalg.inv(H.assemble_dense(prob.A))
+    b = _crandn(np.random.default_rng(17), (8, 8))
+    res = H.fgmres(prob.A, lambda r: (Ainv @ r.ravel()).reshape(r.shape), b, tol=1e-12)
+    assert res.converged and res.iters == 1
+
+
+def test_fgmres_estimates_monotone_and_match_true_residual():
+    """Within a cycle the Givens estimate never grows; at each restart it equals the
+    true residual recomputed from x (to FP64 rounding)."""
+    prob = _small_problem()
+    b = _crandn(np.random.default_rng(18), (16, 16))
+    res = H.fgmres(prob.A, H.precond_v(prob), b, m=5, tol=1e-10, maxit=200)
+    ests = [e for _, e in res.history]
+    for c in range(0, len(ests), 5):
+        cyc = ests[c:c + 5]
+        assert all(cyc[i + 1] <= cyc[i] * (1 + 1e-12) for i in range(len(cyc) - 1))
+    for c, true in enumerate(res.true_history[1:]):
+        assert np.isclose(ests[5 * c + 4] if 5 * c + 4 < len(ests) else ests[-1], true, rtol=1e-6)
+
+
+def test_fgmres_identity_preconditioner_is_gmres():
+    """With M = I and one cycle, FGMRES gives the GMRES minimiser over K_m(A, b)."""
+    prob = _small_problem(8, 19)
+    b = _crandn(np.random.default_rng(20), (8, 8))
+    m = 6
+    res = H.fgmres(prob.A, lambda r: r, b, m=m, tol=0.0, maxit=m)
+    K = H.assemble_dense(prob.A)
+    cols = [b.ravel() / np.linalg.norm(b)]
+    for _ in range(m - 1):
+        w = K @ cols[-1]
+        cols.append(w / np.linalg.norm(w))
+    Q, _ = np.linalg.qr(np.stack(cols, 1))
+    c, *_ = np.linalg.lstsq(K @ Q, b.ravel(), rcond=None)
+    assert np.linalg.norm(res.x.ravel() - Q @ c) / np.linalg.norm(Q @ c) < 1e-8
+
+
+def test_manufactured_continuum_second_order():
+    """u = sin(pi x) sin(pi y) in a constant medium with no layer, nodes at (i+1)h,
+    h = 1/(n+1): the discrete solution error is O(h^2) (ratio ~4 on refinement)."""
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / (n + 1)
+        x = (np.arange(n) + 1) * h
+        U = np.sin(np.pi * x)[:, None] * np.sin(np.pi * x)[None, :]
+        omega, k2 = 6.0, 1.0
+        prob = H.Problem(np.full((n, n), k2), omega=omega, h=h, abc_width=0, levels=3)
+        f = (2 * np.pi ** 2 - omega ** 2 * k2) * U + 0j
+        res = H.fgmres(prob.A, H.precond_v(prob), f, tol=1e-12, maxit=300)
+        errs.append(np.abs(res.x - U).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+def test_manufactured_discrete_solution():
+    prob = _small_problem(32, 21)
+    u_star = _crandn(np.random.default_rng(22), (32, 32))
+    f = H.apply_op(prob.A, u_star)
+    res = H.fgmres(prob.A, H.precond_v(prob), f, tol=1e-11, maxit=1000)
+    assert res.converged
+    assert np.linalg.norm(res.x - u_star) / np.linalg.norm(u_star) < 1e-7
+
+
+@pytest.mark.slow
+def test_sl_iterations_in_paper_regime():
+    """Paper setting (Sec. 4): 128^2, omega = 20 pi, kappa^2 in [0.25, 1], M_V with
+    shift 0.5, 3 levels, V(1,1), w_J = 0.8, coarse GMRES(10): the paper reports
+    rho_V ~ 0.9 and > 130 iterations for a 10^6 reduction (block FGMRES, 10 RHS).
+    Our independent-RHS FGMRES must land in the same regime: T within +-40% of 137,
+    i.e. rho = 10^(-6/T) between 0.84 and 0.95."""
+    n = 128
+    kappa = np.sqrt(synth.grf_kappa2(n, n, 31, kappa_min=0.5).astype(np.float64))
+    prob = H.Problem(kappa ** 2, omega=20 * np.pi, h=1.0 / n, abc_width=10, levels=3)
+    b = synth.gaussian_rhs(n, n, 1, 32)[0]
+    res = H.fgmres(prob.A, H.precond_v(prob), b, tol=1e-6, maxit=400)
+    rho = H.convergence_factor(1.0, res.relres, res.iters)
+    assert res.converged
+    assert 80 <= res.iters <= 200, res.iters
+    assert 0.84 <= rho <= 0.95, rho
