@@ -1,0 +1,158 @@
+/*
+ * libhelm — preconditioned Krylov solver for the 2D heterogeneous Helmholtz
+ * equation on one GB300 GPU (sm_103a), after Azulay & Treister,
+ * "Multigrid-augmented deep learning preconditioners for the Helmholtz
+ * equation" (arXiv 2203.11025).
+ *
+ *   -Lap u - w^2 k(x)^2 (1 - g(x) i) u = f    on [0,1]^2        (Eq. 2.1)
+ *
+ * discretised by the 5-point stencil of Eq. 2.2 on an nx-by-ny grid of
+ * unknowns with spacing h and zero (Dirichlet) values outside the grid; g is
+ * an absorbing layer (quadratic profile, width abc_width cells, peak
+ * abc_gamma_max).  The shifted Laplacian M replaces (1 - g i) by
+ * (1 - (g + beta) i) (Eq. 2.4, alpha = 1).
+ *
+ * Conventions for every entry point
+ *   - Vectors are complex, interleaved (re, im), row-major [rhs][y][x];
+ *     dtype HELM_C32 = float2 elements, HELM_C64 = double2 elements.
+ *   - Pointers are DEVICE pointers owned by the caller unless a flag says
+ *     otherwise; the library never frees them.  kappa2 is float32 [y][x].
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; calls return without synchronising except where noted.
+ *   - Return value: 0 (HELM_OK) on success, > 0 a non-fatal outcome, < 0 an
+ *     error; helm_last_error() gives a message (thread-local).  No exception
+ *     crosses this boundary.  On error nothing is guaranteed about outputs.
+ *   - Grid sizes: nx and ny divisible by 2^(levels-1).
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx* helm_t;
+typedef void* helm_stream_t;
+
+enum {
+  HELM_OK = 0,
+  HELM_MAXIT = 1,          /* FGMRES stopped at maxit before reaching tol      */
+  HELM_EINVAL = -1,        /* bad argument                                     */
+  HELM_ECUDA = -2,         /* a CUDA call failed (message has the CUDA error)  */
+  HELM_ENAN = -3,          /* a non-finite residual was met                    */
+  HELM_ENOMEM = -5,        /* device allocation failed                         */
+  HELM_EUNSUPPORTED = -6   /* feature not built for this configuration         */
+};
+enum { HELM_OP_A = 0, HELM_OP_M = 1 };       /* Helmholtz A (Eq. 2.2) / shifted M (Eq. 2.4) */
+enum { HELM_C32 = 0, HELM_C64 = 1 };
+enum { HELM_PREC_NONE = 0, HELM_PREC_V = 1, HELM_PREC_JU = 2, HELM_PREC_VU = 3 };
+
+/* Problem and multigrid description (Sec. 2.1, 2.2, 4). */
+typedef struct {
+  int nx, ny;              /* unknowns per row / per column                    */
+  double h;                /* mesh width                                       */
+  double omega;            /* angular frequency                                */
+  double beta;             /* SL shift (Sec. 4: 0.5)                           */
+  int abc_width;           /* absorbing layer width in fine cells (>= 0)       */
+  double abc_gamma_max;    /* layer attenuation on the outermost unknowns      */
+  int levels;              /* V-cycle levels incl. the coarsest (Sec. 4: 3)    */
+  int nu1, nu2;            /* pre/post damped-Jacobi sweeps (Sec. 4: 1, 1)     */
+  double jacobi_w;         /* Jacobi damping (Sec. 4: 0.8)                     */
+  int coarse_its;          /* GMRES steps on the coarsest grid (Sec. 4: 10)   */
+} helm_desc;
+
+/* Fill `d` with the paper's defaults (Sec. 4) for an n-by-n grid, h = 1/n,
+ * omega from max(omega k h) = 2 pi / 10 with max k = 1 (Sec. 2.1), a 16-cell
+ * quadratic layer with peak 1.  Returns HELM_EINVAL if d is NULL. */
+int helm_desc_default(helm_desc* d, int nx, int ny);
+
+/* Build the level hierarchy: copies kappa2 (device, float32 [ny][nx]) and
+ * derives coarse media by full weighting renormalised at the edges
+ * (rediscretisation on H = 2h, Sec. 2.2).  Synchronises `stream` before
+ * returning.  The handle owns all workspace; free it with helm_destroy. */
+int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream, helm_t* out);
+void helm_destroy(helm_t h);
+const char* helm_last_error(void);
+
+/* Level sizes (level 0 = fine grid). */
+int helm_level_shape(helm_t h, int level, int* nx, int* ny);
+/* Copy the level's kappa^2 (float64, [ny][nx]) into a device buffer. */
+int helm_level_kappa2(helm_t h, int level, double* out);
+
+/* y = K x on `level`, K = A (op HELM_OP_A) or M (HELM_OP_M), Eq. 2.2 / 2.4. */
+int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream);
+/* r = b - K x. */
+int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,
+                  helm_stream_t stream);
+/* One damped Jacobi sweep x_out = x_in + w D^-1 (b - K x_in) (Sec. 4, w = desc.jacobi_w);
+ * x_in NULL means a zero guess.  x_out must not alias x_in. */
+int helm_jacobi(helm_t h, int op, int level, const void* b, const void* x_in, void* x_out, int nrhs, int dtype,
+                helm_stream_t stream);
+/* Full-weighting restriction (Eq. 2.9) from `level` to level+1. */
+int helm_restrict(helm_t h, int level, const void* fine, void* coarse, int nrhs, int dtype, helm_stream_t stream);
+/* fine += P coarse: bilinear prolongation (Eq. 2.9, transposed stride-2 conv) from level+1 to `level`. */
+int helm_prolong_add(helm_t h, int level, const void* coarse, void* fine, int nrhs, int dtype,
+                     helm_stream_t stream);
+/* Coarsest-grid solve: desc.coarse_its GMRES steps with diagonal (Jacobi)
+ * right preconditioning from x = 0 on M of the coarsest level (Sec. 2.4, 4). */
+int helm_coarse_solve(helm_t h, const void* f, void* x, int nrhs, int dtype, helm_stream_t stream);
+
+/* One shifted-Laplacian V-cycle on M (Alg. 1): x <- V-cycle(x, f) with nu1/nu2
+ * damped-Jacobi sweeps, full weighting, bilinear prolongation and the coarsest
+ * GMRES solve.  x_is_zero != 0 ignores the content of x (zero guess, as in M_V).
+ * f and x must not alias. */
+int sl_vcycle(helm_t h, const void* f, void* x, int nrhs, int dtype, int x_is_zero, helm_stream_t stream);
+
+/* Restarted flexible GMRES (Sec. 2.2 and 4: FGMRES(m), right preconditioned,
+ * Eq. 2.5), one independent Krylov process per right-hand side. */
+enum {
+  HELM_FLAG_X0_ZERO = 1,   /* start from x = 0 (x content ignored)              */
+  HELM_FLAG_HOST_IO = 2,   /* b and x are HOST pointers (copied in and out)      */
+  HELM_FLAG_NO_GRAPH = 4,  /* launch kernels directly instead of a CUDA graph    */
+  HELM_FLAG_FP64 = 8       /* FP64 Krylov vectors and preconditioner (checking)  */
+};
+typedef struct {
+  int restart;             /* m (Sec. 4: 10), 1..32                             */
+  double tol;              /* stop when ||b - A x|| / ||b|| <= tol in FP64       */
+  int maxit;               /* cap on inner iterations per right-hand side        */
+  int flags;               /* HELM_FLAG_*                                        */
+} fgmres_opts;
+typedef struct {
+  int iters_max;           /* iterations of the slowest right-hand side          */
+  int cycles;              /* restart cycles run                                 */
+  double relres_max;       /* max over right-hand sides of the FP64 true relres  */
+  int status;              /* HELM_OK, HELM_MAXIT or HELM_ENAN                   */
+  int* iters;              /* optional host array [nrhs], may be NULL            */
+  double* relres;          /* optional host array [nrhs], may be NULL            */
+  long long launches;      /* kernels this library launched for the solve (-1 if
+                              not counted: HELM_FLAG_NO_GRAPH)                  */
+} fgmres_result;
+
+/* Solve A x = b for nrhs right-hand sides.  b, x: complex FP64 ([rhs][y][x]),
+ * device pointers unless HELM_FLAG_HOST_IO.  x holds x0 on entry (unless
+ * HELM_FLAG_X0_ZERO) and the solution on return.  precond: HELM_PREC_V
+ * (one SL V-cycle, M_V), HELM_PREC_NONE, or a U-Net preconditioner (needs
+ * `net`, see unet.h).  Blocks the calling thread until the solve ends
+ * (the host reads a convergence flag once per restart). */
+int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
+                 fgmres_result* result, helm_stream_t stream);
+
+/* Measurement hook (no counterpart in the paper): launch one of the solver's
+ * internal kernels `reps` times back to back on `stream` over the FP32
+ * workspace of nrhs right-hand sides (fine grid) and return the mean device
+ * time per launch in *ms (CUDA events on `stream`) and the kernel's
+ * algorithmic bytes per launch in *bytes.  Workspace contents are overwritten.
+ *   kernel 0: operator apply y = A x            (20 B per point)
+ *   kernel 1: fused residual + full weighting   (8+4 B read per fine point + 8 B per coarse point)
+ *   kernel 2: fused prolongation + Jacobi       (8+4+8 B per fine point + 8 B per coarse point)
+ *   kernel 3: MGS pass, dot + axpy              (32 B per point)
+ *   kernel 4: one whole V-cycle (M_V)            (bytes: sum of its kernels)  */
+int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

@@ -1,0 +1,186 @@
+// Internal declarations of libhelm: device helpers shared by the kernel files
+// and the host-side launchers the solver driver calls.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace helm {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { typedef float2 type; };
+template <> struct vec2<double> { typedef double2 type; };
+
+// ---------------------------------------------------------------------------
+// Operator description passed by value to every stencil kernel.
+// K = (1/h^2)(5-point negative Laplacian) - w^2 k^2 (1 - (g + beta) i),
+// g the quadratic absorbing-layer profile of width abc_w on this level
+// (Eq. 2.1, 2.2; Eq. 2.4 with alpha = 1 for the shifted operator).
+// ---------------------------------------------------------------------------
+template <typename T> struct Op {
+  int nx, ny, abc_w;
+  T inv_h2, omega2, gmax, beta;
+  const T* k2;  // kappa^2 on this level, [ny][nx]
+};
+
+// Per-level storage owned by the handle.
+struct Level {
+  int nx, ny, abc_w;
+  double h;
+  float* k2f;   // kappa^2 (float32)
+  double* k2d;  // kappa^2 (float64)
+};
+
+template <typename T>
+inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
+  Op<T> op;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.inv_h2 = (T)(1.0 / (L.h * L.h));
+  op.omega2 = (T)(omega * omega);
+  op.gmax = (T)gmax;
+  op.beta = (T)beta;
+  op.k2 = nullptr;
+  return op;
+}
+template <> inline Op<float> make_op<float>(const Level& L, double omega, double gmax, double beta) {
+  Op<float> op;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.inv_h2 = (float)(1.0 / (L.h * L.h));
+  op.omega2 = (float)(omega * omega);
+  op.gmax = (float)gmax; op.beta = (float)beta; op.k2 = L.k2f;
+  return op;
+}
+template <> inline Op<double> make_op<double>(const Level& L, double omega, double gmax, double beta) {
+  Op<double> op;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.inv_h2 = 1.0 / (L.h * L.h);
+  op.omega2 = omega * omega;
+  op.gmax = gmax; op.beta = beta; op.k2 = L.k2d;
+  return op;
+}
+
+#ifdef __CUDACC__
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T2, typename T> __device__ __forceinline__ T2 cscale(T2 a, T s) { T2 r; r.x = a.x * s; r.y = a.y * s; return r; }
+template <typename T2> __device__ __forceinline__ T2 czero() { T2 r; r.x = 0; r.y = 0; return r; }
+template <typename T2> __device__ __forceinline__ T2 cinv(T2 a) {
+  auto d = a.x * a.x + a.y * a.y;
+  T2 r; r.x = a.x / d; r.y = -a.y / d; return r;
+}
+
+// Absorbing-layer attenuation g at node (x, y): g_max (1 - d/W)^2 for d < W,
+// d the distance in cells to the nearest edge (0 on the outermost unknowns).
+template <typename T> __device__ __forceinline__ T gamma_at(const Op<T>& op, int x, int y) {
+  int d = min(min(x, op.nx - 1 - x), min(y, op.ny - 1 - y));
+  if (d >= op.abc_w) return T(0);
+  T t = T(1) - T(d) / T(op.abc_w);
+  return t * t * op.gmax;
+}
+
+// Diagonal of K at (x, y): 4/h^2 - w^2 k^2 + i w^2 k^2 (g + beta).
+template <typename T>
+__device__ __forceinline__ typename vec2<T>::type diag_at(const Op<T>& op, int x, int y) {
+  T wk = op.omega2 * op.k2[(size_t)y * op.nx + x];
+  typename vec2<T>::type d;
+  d.x = T(4) * op.inv_h2 - wk;
+  d.y = wk * (gamma_at(op, x, y) + op.beta);
+  return d;
+}
+#endif
+
+// Block sizes shared by launchers.
+constexpr int kVecThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Launchers (stencil.cu).  All vectors are complex, interleaved, [rhs][y][x];
+// `active` (nullable) holds one int per right-hand side: 0 = skip it.
+// ---------------------------------------------------------------------------
+template <typename T> void launch_apply(const Op<T>& op, const void* x, const void* b, void* y, int nrhs,
+                                        const int* active, cudaStream_t s);
+template <typename T> void launch_jacobi(const Op<T>& op, T w, const void* f, const void* x_in, void* x_out,
+                                         int nrhs, const int* active, cudaStream_t s);
+template <typename T> void launch_restrict(int nx, int ny, const void* rf, void* rc, int nrhs,
+                                           const int* active, cudaStream_t s);
+template <typename T> void launch_prolong_add(int nxc, int nyc, int nx, int ny, const void* ec, void* xf,
+                                              int nrhs, const int* active, cudaStream_t s);
+template <typename T> void launch_resid_restrict(const Op<T>& fine, T w, const void* f, const void* v,
+                                                 void* fc, int nrhs, const int* active, cudaStream_t s);
+template <typename T> void launch_prolong_jacobi(const Op<T>& fine, T w, const void* f, const void* v,
+                                                 bool implicit_v, const void* ec, int nxc, int nyc, void* out,
+                                                 int nrhs, const int* active, cudaStream_t s);
+void launch_coarsen_kappa2(const double* k2d_fine, int nx, int ny, double* k2d_coarse, float* k2f_coarse,
+                           cudaStream_t s);
+void launch_widen_kappa2(const float* k2f, double* k2d, size_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Krylov machinery (krylov.cu).  One Arnoldi process per right-hand side,
+// batched; reductions accumulate per thread in T, per block and across blocks
+// in FP64; the last block to finish a reduction writes the result (and, for
+// the norm, performs the Givens update) so no extra launch is needed.
+// ---------------------------------------------------------------------------
+struct ArnoldiState {      // device arrays, per right-hand side
+  double2* H;              // [nrhs][m+1][m] Hessenberg (raw), complex FP64
+  double2* R;              // [nrhs][m+1][m] rotated Hessenberg
+  double* cs;              // [nrhs][m]
+  double2* sn;             // [nrhs][m]
+  double2* g;              // [nrhs][m+1]
+  double2* y;              // [nrhs][m]
+  double* beta;            // [nrhs]   initial residual norm of the cycle
+  int* active;             // [nrhs]   1 while Arnoldi runs in this cycle
+  int* k;                  // [nrhs]   steps taken in this cycle
+  int* kmax;               // [nrhs]   steps allowed in this cycle
+  double* est;             // [nrhs]   latest residual estimate |g_k|
+  double* tol_abs;         // [nrhs]   stop when |g_k| <= tol_abs (0: run m steps)
+  double2* part;           // [nrhs][nbmax] block partials
+  int* counter;            // [nrhs]   arrival tickets of the last-block reduction
+  int nbmax;
+  int m;
+};
+
+struct SolveState {         // FGMRES, per right-hand side, device
+  double* bnorm;
+  double* relres;
+  int* done;                // converged (or failed) for good
+  int* iters;
+  int* status;              // 0 running/converged, 1 max iterations, -3 non-finite
+};
+
+int vec_blocks(size_t N, int nrhs, int nsm);
+
+// Start of a cycle from f: beta = ||f||, g_0 = beta, active = gate && beta > 0,
+// then v_0 = f / beta (two launches).
+template <typename T> void launch_start(const void* f, void* v0, size_t N, int nrhs, ArnoldiState& st, int nb,
+                                        const int* gate, cudaStream_t s);
+// w = K z (or K D^-1 z) and h_{0j} = <v_0, w>.
+template <typename T> void launch_apply_dot(const Op<T>& op, bool diag_precond, const void* z, void* w,
+                                            const void* v0, int nrhs, ArnoldiState& st, int j, int nb,
+                                            cudaStream_t s);
+// MGS pass i (1 <= i <= j+1): w -= h_{i-1,j} v_{i-1}; then h_{ij} = <v_i, w> (i <= j)
+// or h_{j+1,j} = ||w|| followed by the Givens update and the stopping test (i = j+1).
+template <typename T> void launch_mgs(const void* V, size_t vstride, void* w, size_t N, int nrhs, int j, int i,
+                                      ArnoldiState& st, int nb, cudaStream_t s);
+template <typename T> void launch_normalize(void* w, size_t N, int nrhs, int j, ArnoldiState& st, int nb,
+                                            cudaStream_t s);
+// y = R^-1 g per right-hand side; iters (nullable) += steps taken.
+void launch_backsolve(ArnoldiState& st, int nrhs, int* iters, cudaStream_t s);
+// out = (D^-1) sum_i y_i V_i over the k steps of each right-hand side (0 if k = 0);
+// right-hand sides with gate == 0 are skipped.
+template <typename T> void launch_combine(const void* V, size_t vstride, size_t N, int nrhs, ArnoldiState& st,
+                                          const Op<T>* dinv_op, void* out, const int* gate, int nb,
+                                          cudaStream_t s);
+
+// FGMRES (outer solver)
+void launch_bnorm(const double2* b, size_t N, int nrhs, SolveState& ss, ArnoldiState& st, int nb, double tol,
+                  cudaStream_t s);
+template <typename T> void launch_true_residual(const Op<double>& A, const double2* b, const double2* x, void* r0,
+                                                int nrhs, SolveState& ss, ArnoldiState& st, int nb, int maxit,
+                                                cudaStream_t s);
+template <typename T> void launch_scale_v0(void* v0, size_t N, int nrhs, ArnoldiState& st, int nb, cudaStream_t s);
+template <typename T> void launch_update_x(const void* Z, size_t vstride, size_t N, int nrhs, ArnoldiState& st,
+                                           double2* x, int nb, cudaStream_t s);
+
+}  // namespace helm

@@ -1,0 +1,716 @@
+// libhelm driver: handle, workspace, V-cycle orchestration, coarsest GMRES,
+// restarted FGMRES with one CUDA graph per restart cycle, and the C ABI
+// declared in include/helm.h.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "helm_internal.cuh"
+#include "unet_api.h"
+
+namespace {
+thread_local std::string g_err;
+}  // namespace
+
+namespace helm {
+void set_error(const std::string& s) { g_err = s; }
+}  // namespace helm
+
+#define HCHECK(call)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      g_err = std::string(#call) + ": " + cudaGetErrorString(e_);                             \
+      return HELM_ECUDA;                                                                      \
+    }                                                                                         \
+  } while (0)
+#define HLAUNCH()                                                                             \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess) {                                                                  \
+      g_err = std::string("kernel launch: ") + cudaGetErrorString(e_);                        \
+      return HELM_ECUDA;                                                                      \
+    }                                                                                         \
+  } while (0)
+#define HTRY(call)               \
+  do {                           \
+    int r_ = (call);             \
+    if (r_ < 0) return r_;       \
+  } while (0)
+
+using namespace helm;
+
+namespace {
+
+// A device arena: one cudaMalloc carved into 256-byte aligned pieces.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  void* take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > size) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+// Workspace for one real type T (float: solver; double: FP64 checking runs).
+struct Work {
+  int cap = 0;               // right-hand sides the buffers hold
+  int m = 0;                 // FGMRES restart length the buffers hold
+  Arena arena;
+  std::vector<void*> F, E, T1, T2;   // per level: restricted rhs, coarse correction, two scratch vectors
+  void* CV = nullptr;                // coarsest GMRES basis [(mc+1)][rhs][Nc]
+  ArnoldiState cst{};                // coarsest GMRES state
+  void* V = nullptr;                 // FGMRES basis [(m+1)][rhs][N]
+  void* Z = nullptr;                 // FGMRES preconditioned vectors [m][rhs][N]
+  ArnoldiState fst{};
+  SolveState ss{};
+  double2* bx = nullptr;             // staging for HOST_IO: b and x (FP64) [rhs][N] each
+  double2* xx = nullptr;
+};
+
+struct GraphKey {
+  int dtype, precond, nrhs, m, maxit;
+  const void* b;
+  const void* x;
+  const void* net;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(dtype, precond, nrhs, m, maxit, b, x, net) <
+           std::tie(o.dtype, o.precond, o.nrhs, o.m, o.maxit, o.b, o.x, o.net);
+  }
+};
+
+}  // namespace
+
+struct helm_ctx {
+  helm_desc d{};
+  int device = 0, nsm = 148;
+  std::vector<Level> L;
+  void* level_mem = nullptr;
+  Work w32, w64;
+  cudaStream_t own = nullptr;        // stream that graphs are captured on and launched from
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int* h_done = nullptr;             // pinned host mirror of done flags
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, long long> graph_kernels;  // kernel nodes per captured cycle
+};
+
+namespace {
+
+size_t level_points(const helm_ctx* c, int l) { return (size_t)c->L[l].nx * c->L[l].ny; }
+
+void free_work(Work& W) {
+  if (W.arena.base) cudaFree(W.arena.base);
+  W = Work();
+}
+
+void drop_graphs(helm_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  c->graph_kernels.clear();
+}
+
+template <typename T> Work& work_of(helm_ctx* c);
+template <> Work& work_of<float>(helm_ctx* c) { return c->w32; }
+template <> Work& work_of<double>(helm_ctx* c) { return c->w64; }
+
+// (Re)allocate the workspace of type T for `nrhs` right-hand sides and restart m.
+template <typename T>
+int ensure_work(helm_ctx* c, int nrhs, int m) {
+  Work& W = work_of<T>(c);
+  if (W.cap >= nrhs && W.m >= m) return HELM_OK;
+  nrhs = std::max(nrhs, W.cap);
+  m = std::max(m, std::max(W.m, c->d.coarse_its));
+  drop_graphs(c);
+  free_work(W);
+  const int L = c->d.levels;
+  const size_t es = sizeof(typename vec2<T>::type);
+  const size_t N0 = level_points(c, 0), Nc = level_points(c, L - 1);
+  const int mc = c->d.coarse_its;
+  const int nbmax = 4096;
+  auto st_bytes = [&](int mm) {
+    return (size_t)nrhs * ((size_t)(mm + 1) * mm * 16 * 2 + mm * 8 + mm * 16 + (mm + 1) * 16 + mm * 16 + 8 * 3 +
+                           4 * 4 + (size_t)nbmax * 16) + 256 * 16;
+  };
+  size_t total = 0;
+  for (int l = 0; l < L; ++l) total += 4 * (nrhs * level_points(c, l) * es + 256);
+  total += (size_t)(mc + 1) * nrhs * Nc * es + 256;
+  total += (size_t)(2 * m + 1) * nrhs * N0 * es + 512;
+  total += 2 * (size_t)nrhs * N0 * 16 + 512;
+  total += st_bytes(mc) + st_bytes(m) + (size_t)nrhs * 64 + 4096;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    g_err = "workspace allocation of " + std::to_string(total) + " bytes failed";
+    return HELM_ENOMEM;
+  }
+  W.arena.base = (char*)mem;
+  W.arena.size = total;
+  W.cap = nrhs;
+  W.m = m;
+  W.F.assign(L, nullptr); W.E.assign(L, nullptr); W.T1.assign(L, nullptr); W.T2.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    size_t b = nrhs * level_points(c, l) * es;
+    W.F[l] = W.arena.take(b); W.E[l] = W.arena.take(b); W.T1[l] = W.arena.take(b); W.T2[l] = W.arena.take(b);
+  }
+  W.CV = W.arena.take((size_t)(mc + 1) * nrhs * Nc * es);
+  W.V = W.arena.take((size_t)(m + 1) * nrhs * N0 * es);
+  W.Z = W.arena.take((size_t)m * nrhs * N0 * es);
+  W.bx = (double2*)W.arena.take((size_t)nrhs * N0 * 16);
+  W.xx = (double2*)W.arena.take((size_t)nrhs * N0 * 16);
+  auto make_st = [&](ArnoldiState& st, int mm) {
+    st.m = mm;
+    st.nbmax = nbmax;
+    st.H = (double2*)W.arena.take((size_t)nrhs * (mm + 1) * mm * 16);
+    st.R = (double2*)W.arena.take((size_t)nrhs * (mm + 1) * mm * 16);
+    st.cs = (double*)W.arena.take((size_t)nrhs * mm * 8);
+    st.sn = (double2*)W.arena.take((size_t)nrhs * mm * 16);
+    st.g = (double2*)W.arena.take((size_t)nrhs * (mm + 1) * 16);
+    st.y = (double2*)W.arena.take((size_t)nrhs * mm * 16);
+    st.beta = (double*)W.arena.take((size_t)nrhs * 8);
+    st.est = (double*)W.arena.take((size_t)nrhs * 8);
+    st.tol_abs = (double*)W.arena.take((size_t)nrhs * 8);
+    st.active = (int*)W.arena.take((size_t)nrhs * 4);
+    st.k = (int*)W.arena.take((size_t)nrhs * 4);
+    st.kmax = (int*)W.arena.take((size_t)nrhs * 4);
+    st.counter = (int*)W.arena.take((size_t)nrhs * 4);
+    st.part = (double2*)W.arena.take((size_t)nrhs * nbmax * 16);
+  };
+  make_st(W.cst, mc);
+  make_st(W.fst, m);
+  W.ss.bnorm = (double*)W.arena.take((size_t)nrhs * 8);
+  W.ss.relres = (double*)W.arena.take((size_t)nrhs * 8);
+  W.ss.done = (int*)W.arena.take((size_t)nrhs * 4);
+  W.ss.iters = (int*)W.arena.take((size_t)nrhs * 4);
+  W.ss.status = (int*)W.arena.take((size_t)nrhs * 4);
+  if (!W.ss.status || !W.fst.part) {
+    g_err = "workspace layout overflow";
+    free_work(W);
+    return HELM_ENOMEM;
+  }
+  // zero everything: counters must start at 0, coarse tol_abs = 0 (run all steps)
+  HCHECK(cudaMemset(W.arena.base, 0, W.arena.size));
+  if (c->h_done) cudaFreeHost(c->h_done);
+  HCHECK(cudaMallocHost(&c->h_done, (size_t)nrhs * sizeof(int)));
+  return HELM_OK;
+}
+
+template <typename T> Op<T> op_on(helm_ctx* c, int level, double beta) {
+  return make_op<T>(c->L[level], c->d.omega, c->d.abc_gamma_max, beta);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest grid: GMRES(mc) on M D^-1 y = f from 0, x = D^-1 y (Sec. 2.4, 4).
+template <typename T>
+int coarse_gmres(helm_ctx* c, const void* f, void* out, int nrhs, const int* gate, cudaStream_t s) {
+  Work& W = work_of<T>(c);
+  const int lc = c->d.levels - 1, mc = c->d.coarse_its;
+  const size_t Nc = level_points(c, lc);
+  const size_t es = sizeof(typename vec2<T>::type);
+  const size_t vstride = (size_t)nrhs * Nc;
+  char* CV = (char*)W.CV;
+  Op<T> op = op_on<T>(c, lc, c->d.beta);
+  ArnoldiState& st = W.cst;
+  const int nb = vec_blocks(Nc, nrhs, c->nsm);
+  launch_start<T>(f, CV, Nc, nrhs, st, nb, gate, s);
+  for (int j = 0; j < mc; ++j) {
+    void* w = CV + (size_t)(j + 1) * vstride * es;
+    launch_apply_dot<T>(op, true, CV + (size_t)j * vstride * es, w, CV, nrhs, st, j, nb, s);
+    for (int i = 1; i <= j + 1; ++i) launch_mgs<T>(CV, vstride, w, Nc, nrhs, j, i, st, nb, s);
+    if (j + 1 < mc) launch_normalize<T>(w, Nc, nrhs, j, st, nb, s);
+  }
+  launch_backsolve(st, nrhs, nullptr, s);
+  launch_combine<T>(CV, vstride, Nc, nrhs, st, &op, out, gate, nb, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+// out = V-cycle(v_in, f) on `level` of M (Alg. 1).  v_in == nullptr: zero guess.
+// out must not alias f or v_in.
+template <typename T>
+int vcycle(helm_ctx* c, int level, const void* f, const void* v_in, void* out, int nrhs, const int* gate,
+           cudaStream_t s) {
+  Work& W = work_of<T>(c);
+  const helm_desc& d = c->d;
+  if (level == d.levels - 1) return coarse_gmres<T>(c, f, out, nrhs, gate, s);
+  const Level& Lv = c->L[level];
+  const Op<T> op = op_on<T>(c, level, d.beta);
+  const T w = (T)d.jacobi_w;
+  const size_t bytes = (size_t)nrhs * level_points(c, level) * sizeof(typename vec2<T>::type);
+  void* sa = W.T1[level];
+  void* sb = W.T2[level];
+  // pre-smoothing: the first sweep from a zero guess stays implicit (fused)
+  const void* cur = v_in;
+  bool implicit = false;
+  int nu1 = d.nu1;
+  if (!cur && nu1 >= 1) { implicit = true; --nu1; }
+  if (implicit && nu1 > 0) {
+    launch_jacobi<T>(op, w, f, nullptr, sa, nrhs, gate, s);
+    cur = sa; implicit = false;
+    std::swap(sa, sb);
+  }
+  for (; nu1 > 0; --nu1) {
+    launch_jacobi<T>(op, w, f, cur, sa, nrhs, gate, s);
+    cur = sa;
+    std::swap(sa, sb);
+  }
+  if (cur == out) {  // only when nu1 == 0 and v_in aliases out
+    HCHECK(cudaMemcpyAsync(sa, cur, bytes, cudaMemcpyDeviceToDevice, s));
+    cur = sa;
+    std::swap(sa, sb);
+  }
+  // residual, restriction, coarse correction
+  void* fc = W.F[level + 1];
+  if (implicit || cur) launch_resid_restrict<T>(op, w, f, implicit ? nullptr : cur, fc, nrhs, gate, s);
+  else launch_restrict<T>(Lv.nx, Lv.ny, f, fc, nrhs, gate, s);
+  void* ec = W.E[level + 1];
+  HTRY(vcycle<T>(c, level + 1, fc, nullptr, ec, nrhs, gate, s));
+  const int nxc = c->L[level + 1].nx, nyc = c->L[level + 1].ny;
+  // correction and post-smoothing
+  if (d.nu2 == 0) {
+    if (implicit) launch_jacobi<T>(op, w, f, nullptr, out, nrhs, gate, s);
+    else if (cur) HCHECK(cudaMemcpyAsync(out, cur, bytes, cudaMemcpyDeviceToDevice, s));
+    else HCHECK(cudaMemsetAsync(out, 0, bytes, s));
+    launch_prolong_add<T>(nxc, nyc, Lv.nx, Lv.ny, ec, out, nrhs, gate, s);
+  } else {
+    int nu2 = d.nu2;
+    void* dst = (nu2 == 1) ? out : (sa != cur ? sa : sb);
+    launch_prolong_jacobi<T>(op, w, f, implicit ? nullptr : cur, implicit, ec, nxc, nyc, dst, nrhs, gate, s);
+    const void* x = dst;
+    for (--nu2; nu2 > 0; --nu2) {
+      void* nxt = (nu2 == 1) ? out : (x == sa ? sb : sa);
+      launch_jacobi<T>(op, w, f, x, nxt, nrhs, gate, s);
+      x = nxt;
+    }
+  }
+  HLAUNCH();
+  return HELM_OK;
+}
+
+// z = M^-1 v for the chosen preconditioner.
+template <typename T>
+int precond_apply(helm_ctx* c, int precond, void* net, const void* v, void* z, int nrhs, const int* gate,
+                  cudaStream_t s) {
+  const size_t bytes = (size_t)nrhs * level_points(c, 0) * sizeof(typename vec2<T>::type);
+  switch (precond) {
+    case HELM_PREC_NONE:
+      HCHECK(cudaMemcpyAsync(z, v, bytes, cudaMemcpyDeviceToDevice, s));
+      return HELM_OK;
+    case HELM_PREC_V:
+      return vcycle<T>(c, 0, v, nullptr, z, nrhs, gate, s);
+    case HELM_PREC_JU:
+    case HELM_PREC_VU:
+      return unet_precond_impl(c, net, precond, v, z, nrhs, (int)sizeof(T), gate, s);
+    default:
+      g_err = "unknown preconditioner";
+      return HELM_EINVAL;
+  }
+}
+
+// One restart cycle's Arnoldi steps and the update x += Z y (graph-capturable).
+template <typename T>
+int fgmres_cycle(helm_ctx* c, int precond, void* net, double2* x, int nrhs, int m, cudaStream_t s) {
+  Work& W = work_of<T>(c);
+  const size_t N = level_points(c, 0);
+  const size_t es = sizeof(typename vec2<T>::type);
+  const size_t vstride = (size_t)nrhs * N;
+  char* V = (char*)W.V;
+  char* Z = (char*)W.Z;
+  ArnoldiState& st = W.fst;
+  const Op<T> A = op_on<T>(c, 0, 0.0);
+  const int nb = vec_blocks(N, nrhs, c->nsm);
+  launch_scale_v0<T>(V, N, nrhs, st, nb, s);
+  for (int j = 0; j < m; ++j) {
+    void* vj = V + (size_t)j * vstride * es;
+    void* zj = Z + (size_t)j * vstride * es;
+    void* w = V + (size_t)(j + 1) * vstride * es;
+    HTRY(precond_apply<T>(c, precond, net, vj, zj, nrhs, st.active, s));
+    launch_apply_dot<T>(A, false, zj, w, V, nrhs, st, j, nb, s);
+    for (int i = 1; i <= j + 1; ++i) launch_mgs<T>(V, vstride, w, N, nrhs, j, i, st, nb, s);
+    if (j + 1 < m) launch_normalize<T>(w, N, nrhs, j, st, nb, s);
+  }
+  launch_backsolve(st, nrhs, W.ss.iters, s);
+  launch_update_x<T>(Z, vstride, N, nrhs, st, x, nb, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+template <typename T>
+int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int nrhs, const fgmres_opts& o,
+               fgmres_result* res, cudaStream_t caller) {
+  HTRY(ensure_work<T>(c, nrhs, o.restart));
+  Work& W = work_of<T>(c);
+  const size_t N = level_points(c, 0);
+  const int nb = vec_blocks(N, nrhs, c->nsm);
+  const int m = o.restart;
+  cudaStream_t s = c->own;
+  HCHECK(cudaEventRecord(c->ev_in, caller));
+  HCHECK(cudaStreamWaitEvent(s, c->ev_in, 0));
+  if (o.flags & HELM_FLAG_X0_ZERO) HCHECK(cudaMemsetAsync(x, 0, (size_t)nrhs * N * 16, s));
+  const Op<double> A64 = op_on<double>(c, 0, 0.0);
+  launch_bnorm(b, N, nrhs, W.ss, W.fst, nb, o.tol, s);
+  HLAUNCH();
+  cudaGraphExec_t exec = nullptr;
+  long long per_cycle = -1;
+  const bool use_graph = !(o.flags & HELM_FLAG_NO_GRAPH);
+  if (use_graph) {
+    GraphKey key{(int)sizeof(T), precond, nrhs, m, o.maxit, b, x, net};
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+      exec = it->second;
+      per_cycle = c->graph_kernels[key];
+    } else {
+      cudaGraph_t g;
+      HCHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int r = fgmres_cycle<T>(c, precond, net, x, nrhs, m, s);
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (r < 0) return r;
+      if (ce != cudaSuccess) { g_err = std::string("graph capture: ") + cudaGetErrorString(ce); return HELM_ECUDA; }
+      size_t nn = 0;
+      HCHECK(cudaGraphGetNodes(g, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      HCHECK(cudaGraphGetNodes(g, nodes.data(), &nn));
+      per_cycle = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        HCHECK(cudaGraphNodeGetType(nd, &ty));
+        if (ty == cudaGraphNodeTypeKernel) ++per_cycle;
+      }
+      HCHECK(cudaGraphInstantiate(&exec, g, 0));
+      cudaGraphDestroy(g);
+      c->graphs[key] = exec;
+      c->graph_kernels[key] = per_cycle;
+    }
+  }
+  const int max_cycles = o.maxit / std::max(1, m) + 3 + o.maxit;
+  int cycles = 0;
+  for (;;) {
+    launch_true_residual<T>(A64, b, x, W.V, nrhs, W.ss, W.fst, nb, o.maxit, s);
+    HLAUNCH();
+    HCHECK(cudaMemcpyAsync(c->h_done, W.ss.done, (size_t)nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    HCHECK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all = all && c->h_done[r];
+    if (all) break;
+    if (++cycles > max_cycles) { g_err = "FGMRES cycle guard tripped"; return HELM_ECUDA; }
+    if (exec) HCHECK(cudaGraphLaunch(exec, s));
+    else HTRY(fgmres_cycle<T>(c, precond, net, x, nrhs, m, s));
+  }
+  std::vector<int> iters(nrhs), status(nrhs);
+  std::vector<double> relres(nrhs);
+  HCHECK(cudaMemcpyAsync(iters.data(), W.ss.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  HCHECK(cudaMemcpyAsync(status.data(), W.ss.status, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  HCHECK(cudaMemcpyAsync(relres.data(), W.ss.relres, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HCHECK(cudaStreamSynchronize(s));
+  HCHECK(cudaEventRecord(c->ev_out, s));
+  HCHECK(cudaStreamWaitEvent(caller, c->ev_out, 0));
+  int st = HELM_OK;
+  if (res) {
+    res->iters_max = 0;
+    res->relres_max = 0;
+    res->cycles = cycles;
+    // bnorm + one true-residual kernel per check + the cycle graphs
+    res->launches = per_cycle < 0 ? -1 : 1 + (long long)(cycles + 1) + (long long)cycles * per_cycle;
+    for (int r = 0; r < nrhs; ++r) {
+      res->iters_max = std::max(res->iters_max, iters[r]);
+      res->relres_max = std::max(res->relres_max, relres[r]);
+      if (res->iters) res->iters[r] = iters[r];
+      if (res->relres) res->relres[r] = relres[r];
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    if (status[r] == -3) st = HELM_ENAN;
+    else if (status[r] == 1 && st == HELM_OK) st = HELM_MAXIT;
+  }
+  if (res) res->status = st;
+  if (st == HELM_ENAN) g_err = "non-finite residual in FGMRES";
+  return st;
+}
+
+int check_common(helm_t h, int nrhs, int dtype) {
+  if (!h) { g_err = "null handle"; return HELM_EINVAL; }
+  if (nrhs <= 0 || nrhs > 65535) { g_err = "nrhs out of range"; return HELM_EINVAL; }
+  if (dtype != HELM_C32 && dtype != HELM_C64) { g_err = "dtype must be HELM_C32 or HELM_C64"; return HELM_EINVAL; }
+  return HELM_OK;
+}
+int check_level(helm_t h, int level, int need_coarser) {
+  if (level < 0 || level + need_coarser >= h->d.levels) { g_err = "level out of range"; return HELM_EINVAL; }
+  return HELM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* helm_last_error(void) { return g_err.c_str(); }
+
+int helm_desc_default(helm_desc* d, int nx, int ny) {
+  if (!d) { g_err = "null desc"; return HELM_EINVAL; }
+  std::memset(d, 0, sizeof(*d));
+  d->nx = nx; d->ny = ny;
+  d->h = 1.0 / (double)nx;
+  d->omega = 2.0 * 3.14159265358979323846 / 10.0 / d->h;
+  d->beta = 0.5;
+  d->abc_width = 16;
+  d->abc_gamma_max = 1.0;
+  d->levels = 3;
+  d->nu1 = 1; d->nu2 = 1;
+  d->jacobi_w = 0.8;
+  d->coarse_its = 10;
+  return HELM_OK;
+}
+
+int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream, helm_t* out) {
+  if (!desc || !kappa2 || !out) { g_err = "null argument"; return HELM_EINVAL; }
+  const helm_desc& d = *desc;
+  if (d.levels < 1 || d.levels > 12) { g_err = "levels must be in 1..12"; return HELM_EINVAL; }
+  const int div = 1 << (d.levels - 1);
+  if (d.nx <= 0 || d.ny <= 0 || d.nx % div || d.ny % div) {
+    g_err = "nx, ny must be positive multiples of 2^(levels-1)";
+    return HELM_EINVAL;
+  }
+  if (d.coarse_its < 1 || d.coarse_its > 32) { g_err = "coarse_its must be in 1..32"; return HELM_EINVAL; }
+  if (d.nu1 < 0 || d.nu2 < 0 || d.h <= 0 || d.abc_width < 0) { g_err = "bad smoothing/mesh/layer parameter"; return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  helm_ctx* c = new helm_ctx();
+  c->d = d;
+  HCHECK(cudaGetDevice(&c->device));
+  HCHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  size_t total = 0;
+  for (int l = 0; l < d.levels; ++l) total += (size_t)(d.nx >> l) * (d.ny >> l) * 12 + 512;
+  if (cudaMalloc(&c->level_mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    g_err = "level allocation failed";
+    return HELM_ENOMEM;
+  }
+  Arena a{(char*)c->level_mem, total, 0};
+  for (int l = 0; l < d.levels; ++l) {
+    Level L;
+    L.nx = d.nx >> l; L.ny = d.ny >> l;
+    L.h = d.h * (double)(1 << l);
+    L.abc_w = d.abc_width >> l;
+    size_t n = (size_t)L.nx * L.ny;
+    L.k2f = (float*)a.take(n * 4);
+    L.k2d = (double*)a.take(n * 8);
+    c->L.push_back(L);
+  }
+  const size_t n0 = (size_t)d.nx * d.ny;
+  HCHECK(cudaMemcpyAsync(c->L[0].k2f, kappa2, n0 * 4, cudaMemcpyDeviceToDevice, s));
+  launch_widen_kappa2(c->L[0].k2f, c->L[0].k2d, n0, s);
+  for (int l = 1; l < d.levels; ++l)
+    launch_coarsen_kappa2(c->L[l - 1].k2d, c->L[l - 1].nx, c->L[l - 1].ny, c->L[l].k2d, c->L[l].k2f, s);
+  HLAUNCH();
+  HCHECK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+  HCHECK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  HCHECK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  HCHECK(cudaStreamSynchronize(s));
+  *out = c;
+  return HELM_OK;
+}
+
+void helm_destroy(helm_t h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  drop_graphs(h);
+  unet_release_ctx(h);
+  free_work(h->w32);
+  free_work(h->w64);
+  if (h->level_mem) cudaFree(h->level_mem);
+  if (h->h_done) cudaFreeHost(h->h_done);
+  if (h->own) cudaStreamDestroy(h->own);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  delete h;
+}
+
+int helm_level_shape(helm_t h, int level, int* nx, int* ny) {
+  if (!h) { g_err = "null handle"; return HELM_EINVAL; }
+  HTRY(check_level(h, level, 0));
+  if (nx) *nx = h->L[level].nx;
+  if (ny) *ny = h->L[level].ny;
+  return HELM_OK;
+}
+
+int helm_level_kappa2(helm_t h, int level, double* out) {
+  if (!h || !out) { g_err = "null argument"; return HELM_EINVAL; }
+  HTRY(check_level(h, level, 0));
+  HCHECK(cudaMemcpy(out, h->L[level].k2d, level_points(h, level) * 8, cudaMemcpyDeviceToDevice));
+  return HELM_OK;
+}
+
+int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream) {
+  return helm_residual(h, op, level, nullptr, x, y, nrhs, dtype, stream);
+}
+
+int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,
+                  helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  HTRY(check_level(h, level, 0));
+  if (!x || !r) { g_err = "null vector"; return HELM_EINVAL; }
+  const double beta = (op == HELM_OP_M) ? h->d.beta : 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == HELM_C32) launch_apply<float>(op_on<float>(h, level, beta), x, b, r, nrhs, nullptr, s);
+  else launch_apply<double>(op_on<double>(h, level, beta), x, b, r, nrhs, nullptr, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+int helm_jacobi(helm_t h, int op, int level, const void* b, const void* x_in, void* x_out, int nrhs, int dtype,
+                helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  HTRY(check_level(h, level, 0));
+  if (!b || !x_out || x_in == x_out) { g_err = "bad vectors (x_out must not alias x_in)"; return HELM_EINVAL; }
+  const double beta = (op == HELM_OP_M) ? h->d.beta : 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == HELM_C32)
+    launch_jacobi<float>(op_on<float>(h, level, beta), (float)h->d.jacobi_w, b, x_in, x_out, nrhs, nullptr, s);
+  else
+    launch_jacobi<double>(op_on<double>(h, level, beta), h->d.jacobi_w, b, x_in, x_out, nrhs, nullptr, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+int helm_restrict(helm_t h, int level, const void* fine, void* coarse, int nrhs, int dtype, helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  HTRY(check_level(h, level, 1));
+  if (!fine || !coarse) { g_err = "null vector"; return HELM_EINVAL; }
+  const Level& L = h->L[level];
+  if (dtype == HELM_C32) launch_restrict<float>(L.nx, L.ny, fine, coarse, nrhs, nullptr, (cudaStream_t)stream);
+  else launch_restrict<double>(L.nx, L.ny, fine, coarse, nrhs, nullptr, (cudaStream_t)stream);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+int helm_prolong_add(helm_t h, int level, const void* coarse, void* fine, int nrhs, int dtype,
+                     helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  HTRY(check_level(h, level, 1));
+  if (!fine || !coarse) { g_err = "null vector"; return HELM_EINVAL; }
+  const Level& L = h->L[level];
+  const Level& C = h->L[level + 1];
+  if (dtype == HELM_C32) launch_prolong_add<float>(C.nx, C.ny, L.nx, L.ny, coarse, fine, nrhs, nullptr, (cudaStream_t)stream);
+  else launch_prolong_add<double>(C.nx, C.ny, L.nx, L.ny, coarse, fine, nrhs, nullptr, (cudaStream_t)stream);
+  HLAUNCH();
+  return HELM_OK;
+}
+
+int helm_coarse_solve(helm_t h, const void* f, void* x, int nrhs, int dtype, helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  if (!f || !x || f == x) { g_err = "bad vectors"; return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == HELM_C32) {
+    HTRY(ensure_work<float>(h, nrhs, h->d.coarse_its));
+    return coarse_gmres<float>(h, f, x, nrhs, nullptr, s);
+  }
+  HTRY(ensure_work<double>(h, nrhs, h->d.coarse_its));
+  return coarse_gmres<double>(h, f, x, nrhs, nullptr, s);
+}
+
+int sl_vcycle(helm_t h, const void* f, void* x, int nrhs, int dtype, int x_is_zero, helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, dtype));
+  if (!f || !x || f == x) { g_err = "bad vectors (f and x must differ)"; return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == HELM_C32) {
+    HTRY(ensure_work<float>(h, nrhs, h->d.coarse_its));
+    return vcycle<float>(h, 0, f, x_is_zero ? nullptr : x, x, nrhs, nullptr, s);
+  }
+  HTRY(ensure_work<double>(h, nrhs, h->d.coarse_its));
+  return vcycle<double>(h, 0, f, x_is_zero ? nullptr : x, x, nrhs, nullptr, s);
+}
+
+int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
+                 fgmres_result* result, helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, HELM_C32));
+  if (!b || !x || !opts) { g_err = "null argument"; return HELM_EINVAL; }
+  fgmres_opts o = *opts;
+  if (o.restart < 1 || o.restart > 32) { g_err = "restart must be in 1..32"; return HELM_EINVAL; }
+  if (!(o.tol >= 0) || o.maxit < 0) { g_err = "bad tol/maxit"; return HELM_EINVAL; }
+  if ((precond == HELM_PREC_JU || precond == HELM_PREC_VU) && !net) { g_err = "U-Net preconditioner needs net"; return HELM_EINVAL; }
+  cudaStream_t caller = (cudaStream_t)stream;
+  const size_t bytes = (size_t)nrhs * h->d.nx * h->d.ny * 16;
+  const bool fp64 = (o.flags & HELM_FLAG_FP64) != 0;
+  const void* bd = b;
+  void* xd = x;
+  if (o.flags & HELM_FLAG_HOST_IO) {
+    if (fp64) HTRY(ensure_work<double>(h, nrhs, o.restart));
+    else HTRY(ensure_work<float>(h, nrhs, o.restart));
+    Work& W = fp64 ? h->w64 : h->w32;
+    HCHECK(cudaMemcpyAsync(W.bx, b, bytes, cudaMemcpyHostToDevice, caller));
+    if (!(o.flags & HELM_FLAG_X0_ZERO)) HCHECK(cudaMemcpyAsync(W.xx, x, bytes, cudaMemcpyHostToDevice, caller));
+    bd = W.bx;
+    xd = W.xx;
+  }
+  int r = fp64 ? fgmres_run<double>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller)
+               : fgmres_run<float>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller);
+  if (r < 0 && r != HELM_ENAN) return r;
+  if (o.flags & HELM_FLAG_HOST_IO) {
+    HCHECK(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, caller));
+    HCHECK(cudaStreamSynchronize(caller));
+  }
+  return r;
+}
+
+int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes) {
+  HTRY(check_common(h, nrhs, HELM_C32));
+  if (reps < 1 || !ms || !bytes) { g_err = "bad reps/outputs"; return HELM_EINVAL; }
+  HTRY(ensure_work<float>(h, nrhs, 10));
+  Work& W = h->w32;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = level_points(h, 0), Nc1 = level_points(h, std::min(1, h->d.levels - 1));
+  const size_t es = 8, vstride = (size_t)nrhs * N;
+  char* V = (char*)W.V;
+  const Op<float> A = op_on<float>(h, 0, 0.0), M = op_on<float>(h, 0, h->d.beta);
+  const int nb = vec_blocks(N, nrhs, h->nsm);
+  // active flags on, finite Hessenberg entries
+  HCHECK(cudaMemsetAsync(W.fst.H, 0, (size_t)nrhs * (W.fst.m + 1) * W.fst.m * 16, s));
+  std::vector<int> ones(nrhs, 1);
+  HCHECK(cudaMemcpyAsync(W.fst.active, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  HCHECK(cudaMemcpyAsync(W.fst.kmax, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  HCHECK(cudaStreamSynchronize(s));
+  auto run = [&](void) -> int {
+    switch (kernel) {
+      case 0: launch_apply<float>(A, V, nullptr, V + vstride * es, nrhs, nullptr, s); break;
+      case 1: launch_resid_restrict<float>(M, 0.8f, V, nullptr, W.F[1], nrhs, nullptr, s); break;
+      case 2: launch_prolong_jacobi<float>(M, 0.8f, V, nullptr, true, W.E[1], h->L[1].nx, h->L[1].ny,
+                                           V + vstride * es, nrhs, nullptr, s); break;
+      case 3: launch_mgs<float>(V, vstride, V + 5 * vstride * es, N, nrhs, 4, 2, W.fst, nb, s); break;
+      case 4: return vcycle<float>(h, 0, V, nullptr, V + vstride * es, nrhs, nullptr, s);
+      default: g_err = "unknown kernel id"; return HELM_EINVAL;
+    }
+    return HELM_OK;
+  };
+  const double n = (double)N * nrhs, nc = (double)Nc1 * nrhs;
+  switch (kernel) {
+    case 0: *bytes = 20.0 * n; break;
+    case 1: *bytes = 12.0 * n + 8.0 * nc; break;
+    case 2: *bytes = 20.0 * n + 8.0 * nc; break;
+    case 3: *bytes = 32.0 * n; break;
+    default: *bytes = 0.0; break;
+  }
+  HTRY(run());  // warm-up
+  cudaEvent_t e0, e1;
+  HCHECK(cudaEventCreate(&e0));
+  HCHECK(cudaEventCreate(&e1));
+  HCHECK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) HTRY(run());
+  HCHECK(cudaEventRecord(e1, s));
+  HCHECK(cudaEventSynchronize(e1));
+  float t = 0;
+  HCHECK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  HLAUNCH();
+  return HELM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,12 @@
+// Internal bridge between the solver driver and the U-Net preconditioners.
+#pragma once
+#include <cuda_runtime.h>
+
+struct helm_ctx;
+
+// z = U-Net-based preconditioner applied to v (Alg. 2 for HELM_PREC_JU,
+// Eq. 3.4 for HELM_PREC_VU); real_bytes = sizeof(real type) of v and z.
+int unet_precond_impl(helm_ctx* c, void* net, int kind, const void* v, void* z, int nrhs, int real_bytes,
+                      const int* gate, cudaStream_t s);
+// Release U-Net workspace attached to a solver handle.
+void unet_release_ctx(helm_ctx* c);

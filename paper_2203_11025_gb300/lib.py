@@ -1,0 +1,276 @@
+"""Thin Python binding of libhelm's C ABI (include/helm.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Functions keep the C names; `Helmholtz` bundles a handle for convenience.
+Vectors are torch tensors on the GPU (complex64 -> HELM_C32, complex128 ->
+HELM_C64), contiguous, shaped (nrhs, ny, nx) or (ny, nx).  Loading fails
+loudly if the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhelm.so")
+
+HELM_OK, HELM_MAXIT = 0, 1
+HELM_EINVAL, HELM_ECUDA, HELM_ENAN, HELM_ENOMEM, HELM_EUNSUPPORTED = -1, -2, -3, -5, -6
+HELM_OP_A, HELM_OP_M = 0, 1
+HELM_C32, HELM_C64 = 0, 1
+HELM_PREC_NONE, HELM_PREC_V, HELM_PREC_JU, HELM_PREC_VU = 0, 1, 2, 3
+HELM_FLAG_X0_ZERO, HELM_FLAG_HOST_IO, HELM_FLAG_NO_GRAPH, HELM_FLAG_FP64 = 1, 2, 4, 8
+
+# Every symbol include/helm.h declares (checked by the CPU test suite).
+ABI_SYMBOLS = [
+    "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
+    "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
+    "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "helm_time_kernel",
+]
+
+
+class helm_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("h", ctypes.c_double), ("omega", ctypes.c_double),
+                ("beta", ctypes.c_double), ("abc_width", ctypes.c_int), ("abc_gamma_max", ctypes.c_double),
+                ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("jacobi_w", ctypes.c_double), ("coarse_its", ctypes.c_int)]
+
+
+class fgmres_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class fgmres_result(ctypes.Structure):
+    _fields_ = [("iters_max", ctypes.c_int), ("cycles", ctypes.c_int), ("relres_max", ctypes.c_double),
+                ("status", ctypes.c_int), ("iters", ctypes.POINTER(ctypes.c_int)),
+                ("relres", ctypes.POINTER(ctypes.c_double)), ("launches", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load():
+    """Open libhelm.so (once).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhelm.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "helm_desc_default": (I, [ctypes.POINTER(helm_desc), I, I]),
+        "helm_setup": (I, [ctypes.POINTER(helm_desc), P, P, ctypes.POINTER(P)]),
+        "helm_destroy": (None, [P]),
+        "helm_last_error": (ctypes.c_char_p, []),
+        "helm_level_shape": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "helm_level_kappa2": (I, [P, I, P]),
+        "helm_apply": (I, [P, I, I, P, P, I, I, P]),
+        "helm_residual": (I, [P, I, I, P, P, P, I, I, P]),
+        "helm_jacobi": (I, [P, I, I, P, P, P, I, I, P]),
+        "helm_restrict": (I, [P, I, P, P, I, I, P]),
+        "helm_prolong_add": (I, [P, I, P, P, I, I, P]),
+        "helm_coarse_solve": (I, [P, P, P, I, I, P]),
+        "sl_vcycle": (I, [P, P, P, I, I, I, P]),
+        "fgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
+        "helm_time_kernel": (I, [P, I, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HelmError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().helm_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _check(code, where, ok=(HELM_OK,)):
+    if code not in ok:
+        raise HelmError(code, where)
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _dtype(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return HELM_C32
+    if t.dtype == torch.complex128:
+        return HELM_C64
+    raise TypeError(f"vectors must be complex64 or complex128, got {t.dtype}")
+
+
+def _nrhs(t, ny, nx):
+    if t.dim() == 2:
+        return 1
+    if t.dim() == 3 and tuple(t.shape[1:]) == (ny, nx):
+        return t.shape[0]
+    raise ValueError(f"vector shape {tuple(t.shape)} does not match grid ({ny}, {nx})")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+# ---------------------------------------------------------------- thin C-named calls
+def helm_desc_default(nx, ny=None):
+    d = helm_desc()
+    _check(load().helm_desc_default(ctypes.byref(d), nx, ny or nx), "helm_desc_default")
+    return d
+
+
+def helm_setup(desc, kappa2, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().helm_setup(ctypes.byref(desc), _ptr(kappa2), _stream(stream), ctypes.byref(h)), "helm_setup")
+    return h
+
+
+def helm_destroy(h):
+    load().helm_destroy(h)
+
+
+class Helmholtz:
+    """A solver handle: medium kappa^2 (float32 CUDA tensor [ny, nx]) plus desc."""
+
+    def __init__(self, kappa2, desc=None, **overrides):
+        import torch
+        if kappa2.dtype != torch.float32 or not kappa2.is_cuda:
+            raise TypeError("kappa2 must be a float32 CUDA tensor")
+        ny, nx = kappa2.shape
+        self.desc = desc if desc is not None else helm_desc_default(nx, ny)
+        for k, v in overrides.items():
+            setattr(self.desc, k, v)
+        self.kappa2 = kappa2.contiguous()
+        self.h = helm_setup(self.desc, self.kappa2)
+        self.lib = load()
+
+    def close(self):
+        if self.h:
+            helm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_shape(self, level):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.helm_level_shape(self.h, level, ctypes.byref(nx), ctypes.byref(ny)), "helm_level_shape")
+        return ny.value, nx.value
+
+    def level_kappa2(self, level):
+        import torch
+        ny, nx = self.level_shape(level)
+        out = torch.empty(ny, nx, dtype=torch.float64, device="cuda")
+        _check(self.lib.helm_level_kappa2(self.h, level, _ptr(out)), "helm_level_kappa2")
+        torch.cuda.synchronize()
+        return out
+
+    def _vec(self, t, level=0):
+        ny, nx = self.level_shape(level)
+        if not t.is_contiguous():
+            raise ValueError("vectors must be contiguous")
+        return _nrhs(t, ny, nx), _dtype(t)
+
+    def apply(self, x, op=HELM_OP_A, level=0, out=None, stream=None):
+        import torch
+        n, dt = self._vec(x, level)
+        y = torch.empty_like(x) if out is None else out
+        _check(self.lib.helm_apply(self.h, op, level, _ptr(x), _ptr(y), n, dt, _stream(stream)), "helm_apply")
+        return y
+
+    def residual(self, b, x, op=HELM_OP_A, level=0, out=None, stream=None):
+        import torch
+        n, dt = self._vec(x, level)
+        r = torch.empty_like(x) if out is None else out
+        _check(self.lib.helm_residual(self.h, op, level, _ptr(b), _ptr(x), _ptr(r), n, dt, _stream(stream)),
+               "helm_residual")
+        return r
+
+    def jacobi(self, b, x_in=None, op=HELM_OP_M, level=0, out=None, stream=None):
+        import torch
+        n, dt = self._vec(b, level)
+        y = torch.empty_like(b) if out is None else out
+        _check(self.lib.helm_jacobi(self.h, op, level, _ptr(b), _ptr(x_in), _ptr(y), n, dt, _stream(stream)),
+               "helm_jacobi")
+        return y
+
+    def restrict(self, fine, level=0, out=None, stream=None):
+        import torch
+        n, dt = self._vec(fine, level)
+        ny, nx = self.level_shape(level + 1)
+        c = torch.empty((fine.shape[0], ny, nx) if fine.dim() == 3 else (ny, nx), dtype=fine.dtype,
+                        device=fine.device) if out is None else out
+        _check(self.lib.helm_restrict(self.h, level, _ptr(fine), _ptr(c), n, dt, _stream(stream)), "helm_restrict")
+        return c
+
+    def prolong_add(self, coarse, fine, level=0, stream=None):
+        n, dt = self._vec(fine, level)
+        _check(self.lib.helm_prolong_add(self.h, level, _ptr(coarse), _ptr(fine), n, dt, _stream(stream)),
+               "helm_prolong_add")
+        return fine
+
+    def coarse_solve(self, f, out=None, stream=None):
+        import torch
+        n, dt = self._vec(f, self.desc.levels - 1)
+        x = torch.empty_like(f) if out is None else out
+        _check(self.lib.helm_coarse_solve(self.h, _ptr(f), _ptr(x), n, dt, _stream(stream)), "helm_coarse_solve")
+        return x
+
+    def vcycle(self, f, x=None, stream=None):
+        import torch
+        n, dt = self._vec(f, 0)
+        zero = x is None
+        if zero:
+            x = torch.empty_like(f)
+        _check(self.lib.sl_vcycle(self.h, _ptr(f), _ptr(x), n, dt, 1 if zero else 0, _stream(stream)), "sl_vcycle")
+        return x
+
+    def time_kernel(self, kernel, nrhs, reps=20, stream=None):
+        """Mean device ms per launch and algorithmic bytes per launch of an internal kernel."""
+        ms, nbytes = ctypes.c_float(), ctypes.c_double()
+        _check(self.lib.helm_time_kernel(self.h, kernel, nrhs, reps, _stream(stream), ctypes.byref(ms),
+                                         ctypes.byref(nbytes)), "helm_time_kernel")
+        return ms.value, nbytes.value
+
+    def fgmres(self, b, x=None, precond=HELM_PREC_V, net=None, restart=10, tol=1e-7, maxit=5000, flags=0,
+               stream=None):
+        """Solve A x = b (complex128 tensors, CUDA or pinned host with HELM_FLAG_HOST_IO).
+        Returns (x, info dict)."""
+        import torch
+        ny, nx = self.level_shape(0)
+        n = _nrhs(b, ny, nx)
+        if b.dtype != torch.complex128:
+            raise TypeError("b must be complex128")
+        if x is None:
+            x = torch.zeros_like(b)
+            flags |= HELM_FLAG_X0_ZERO
+        opts = fgmres_opts(restart, tol, maxit, flags)
+        iters = (ctypes.c_int * n)()
+        relres = (ctypes.c_double * n)()
+        res = fgmres_result(0, 0, 0.0, 0, iters, relres, 0)
+        netp = net.handle if net is not None and hasattr(net, "handle") else net
+        code = self.lib.fgmres_solve(self.h, precond, netp, _ptr(b), _ptr(x), n, ctypes.byref(opts),
+                                     ctypes.byref(res), _stream(stream))
+        _check(code, "fgmres_solve", ok=(HELM_OK, HELM_MAXIT))
+        return x, {"status": code, "iters": list(iters), "relres": list(relres), "iters_max": res.iters_max,
+                   "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches}
