@@ -62,7 +62,12 @@ typedef struct {
   int nu1, nu2;            /* pre/post damped-Jacobi sweeps (Sec. 4: 1, 1)     */
   double jacobi_w;         /* Jacobi damping (Sec. 4: 0.8)                     */
   int coarse_its;          /* GMRES steps on the coarsest grid (Sec. 4: 10)   */
+  int flags;               /* HELM_DESC_* implementation switches (0 = default) */
 } helm_desc;
+/* Run the coarsest GMRES as one kernel launch per Arnoldi pass instead of the
+ * single fused kernel (the fused kernel is used when the coarsest grid fits
+ * in shared memory); same arithmetic, for cross-checking. */
+enum { HELM_DESC_MULTIKERNEL_COARSE = 1 };
 
 /* Fill `d` with the paper's defaults (Sec. 4) for an n-by-n grid, h = 1/n,
  * omega from max(omega k h) = 2 pi / 10 with max k = 1 (Sec. 2.1), a 16-cell

@@ -1,0 +1,212 @@
+// Coarsest-grid solve of the SL V-cycle in ONE launch: m steps of GMRES with
+// diagonal (Jacobi) right preconditioning from x = 0 on M of the coarsest
+// level (Sec. 2.4 and 4; the "solve directly" line of Alg. 1 is replaced by
+// GMRES(10) as the paper's experiments do).
+//
+// One 1024-thread CTA per right-hand side.  Each thread owns a fixed set of
+// grid points (p = tid + 1024 q), keeps its part of the Arnoldi vector w in
+// shared memory, and reads the basis vectors (stored in global memory, L2
+// resident at these sizes) for the stencil neighbours and the Gram-Schmidt
+// passes.  Modified Gram-Schmidt and the Givens least-squares solve follow the
+// multi-kernel path exactly; inner products are accumulated per thread in T
+// and across the block in FP64, in a fixed order (deterministic).  Only block
+// barriers are used: no inter-CTA waiting.
+#include "helm_internal.cuh"
+
+namespace helm {
+
+namespace {
+
+constexpr int CT = 1024;
+constexpr int CMAX = 32;
+
+__device__ __forceinline__ double2 z2(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return z2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+// Sum over the block, returned to every thread (fixed summation order).
+__device__ __forceinline__ double2 block_allsum(double2 v, double2* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double2 t = z2(0, 0);
+#pragma unroll 8
+  for (int i = 0; i < CT / 32; ++i) { t.x += red[i].x; t.y += red[i].y; }
+  __syncthreads();
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ typename vec2<T>::type scaled_by_dinv(const Op<T>& op, const typename vec2<T>::type* v,
+                                                                 int x, int y) {
+  return cmul(v[(size_t)y * op.nx + x], cinv(diag_at(op, x, y)));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename vec2<T>::type* __restrict__ f,
+                                                     typename vec2<T>::type* __restrict__ out,
+                                                     typename vec2<T>::type* __restrict__ Vg, size_t vstride, int m,
+                                                     const int* gate) {
+  typedef typename vec2<T>::type T2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* w = reinterpret_cast<T2*>(smem_raw);
+  __shared__ double2 red[CT / 32];
+  __shared__ double2 Hs[(CMAX + 1) * CMAX];
+  __shared__ double2 ys[CMAX];
+  __shared__ double2 g[CMAX + 1];
+  __shared__ double2 sn[CMAX];
+  __shared__ double cs[CMAX];
+  __shared__ int s_k;
+  const int rhs = blockIdx.x;
+  if (gate && !gate[rhs]) return;
+  const int nx = op.nx, ny = op.ny, N = nx * ny, tid = threadIdx.x;
+  const size_t off = (size_t)rhs * N;
+  const T2* fr = f + off;
+  T2* outr = out + off;
+
+  // beta = ||f||, v_0 = f / beta
+  double2 acc = z2(0, 0);
+  for (int p = tid; p < N; p += CT) { T2 v = fr[p]; acc.x += (double)v.x * v.x + (double)v.y * v.y; }
+  const double beta = sqrt(block_allsum(acc, red).x);
+  if (!(beta > 0.0)) {                                 // zero (or non-finite) right-hand side
+    T2 zv = czero<T2>();
+    if (beta != beta) { zv.x = beta; zv.y = beta; }    // propagate NaN
+    for (int p = tid; p < N; p += CT) outr[p] = zv;
+    return;
+  }
+  {
+    const T inv = (T)(1.0 / beta);
+    T2* v0 = Vg + off;
+    for (int p = tid; p < N; p += CT) v0[p] = cscale(fr[p], inv);
+  }
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    __syncthreads();                                   // v_j complete
+    const T2* vj = Vg + (size_t)j * vstride + off;
+    // w = M D^-1 v_j
+    for (int p = tid; p < N; p += CT) {
+      const int y = p / nx, x = p - y * nx;
+      T2 c = scaled_by_dinv(op, vj, x, y);
+      T2 s = czero<T2>();
+      if (x > 0) s = cadd(s, scaled_by_dinv(op, vj, x - 1, y));
+      if (x < nx - 1) s = cadd(s, scaled_by_dinv(op, vj, x + 1, y));
+      if (y > 0) s = cadd(s, scaled_by_dinv(op, vj, x, y - 1));
+      if (y < ny - 1) s = cadd(s, scaled_by_dinv(op, vj, x, y + 1));
+      T2 r = cmul(diag_at(op, x, y), c);
+      r.x -= s.x * op.inv_h2;
+      r.y -= s.y * op.inv_h2;
+      w[p] = r;
+    }
+    // modified Gram-Schmidt: each thread touches only its own points of w
+    for (int i = 0; i <= j; ++i) {
+      const T2* vi = Vg + (size_t)i * vstride + off;
+      T ax = 0, ay = 0;
+      for (int p = tid; p < N; p += CT) {
+        T2 a = vi[p], b = w[p];
+        ax += a.x * b.x + a.y * b.y;
+        ay += a.x * b.y - a.y * b.x;
+      }
+      const double2 h = block_allsum(z2((double)ax, (double)ay), red);
+      if (tid == 0) Hs[i * m + j] = h;
+      const T hx = (T)h.x, hy = (T)h.y;
+      for (int p = tid; p < N; p += CT) {
+        T2 a = vi[p], b = w[p];
+        b.x -= hx * a.x - hy * a.y;
+        b.y -= hx * a.y + hy * a.x;
+        w[p] = b;
+      }
+    }
+    T nn = 0;
+    for (int p = tid; p < N; p += CT) { T2 b = w[p]; nn += b.x * b.x + b.y * b.y; }
+    const double nrm = sqrt(block_allsum(z2((double)nn, 0.0), red).x);
+    if (tid == 0) Hs[(j + 1) * m + j] = z2(nrm, 0.0);
+    k = j + 1;
+    if (nrm == 0.0) break;                             // happy breakdown (uniform across the block)
+    if (j + 1 < m) {
+      const T inv = (T)(1.0 / nrm);
+      T2* vn = Vg + (size_t)(j + 1) * vstride + off;
+      for (int p = tid; p < N; p += CT) vn[p] = cscale(w[p], inv);
+    }
+  }
+  __syncthreads();
+  // least squares min ||beta e1 - H y|| by Givens rotations, in place in Hs (one thread)
+  if (tid == 0) {
+    g[0] = z2(beta, 0.0);
+    for (int j = 0; j < k; ++j) {
+      for (int i = 0; i < j; ++i) {
+        double2 a = Hs[i * m + j], b = Hs[(i + 1) * m + j];
+        double2 t = z2(cs[i] * a.x + (sn[i].x * b.x - sn[i].y * b.y), cs[i] * a.y + (sn[i].x * b.y + sn[i].y * b.x));
+        double2 cj = zmul(z2(sn[i].x, -sn[i].y), a);
+        Hs[(i + 1) * m + j] = z2(-cj.x + cs[i] * b.x, -cj.y + cs[i] * b.y);
+        Hs[i * m + j] = t;
+      }
+      double2 a = Hs[j * m + j], b = Hs[(j + 1) * m + j];
+      double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y), c;
+      double2 sv, r;
+      if (bb == 0.0) { c = 1.0; sv = z2(0, 0); r = a; }
+      else if (aa == 0.0) { c = 0.0; sv = z2(1, 0); r = b; }
+      else {
+        double t = hypot(aa, bb);
+        c = aa / t;
+        double2 ph = z2(a.x / aa, a.y / aa);
+        sv = zmul(ph, z2(b.x / t, -b.y / t));
+        r = z2(ph.x * t, ph.y * t);
+      }
+      cs[j] = c; sn[j] = sv;
+      Hs[j * m + j] = r;
+      Hs[(j + 1) * m + j] = z2(0, 0);
+      double2 gj = g[j], sg = zmul(z2(sv.x, -sv.y), gj);
+      g[j + 1] = z2(-sg.x, -sg.y);
+      g[j] = z2(c * gj.x, c * gj.y);
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double2 a = g[i];
+      for (int l = i + 1; l < k; ++l) { double2 t = zmul(Hs[i * m + l], ys[l]); a.x -= t.x; a.y -= t.y; }
+      double2 d = Hs[i * m + i];
+      double dd = d.x * d.x + d.y * d.y;
+      ys[i] = z2((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
+    }
+    s_k = k;
+  }
+  __syncthreads();
+  // x = D^-1 sum_i y_i v_i
+  const int kk = s_k;
+  for (int p = tid; p < N; p += CT) {
+    T2 a = czero<T2>();
+    for (int i = 0; i < kk; ++i) {
+      T2 yi;
+      yi.x = (T)ys[i].x; yi.y = (T)ys[i].y;
+      a = cadd(a, cmul(yi, Vg[(size_t)i * vstride + off + p]));
+    }
+    const int y = p / nx, x = p - y * nx;
+    outr[p] = cmul(a, cinv(diag_at(op, x, y)));
+  }
+}
+
+}  // namespace
+
+template <typename T>
+bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* V, size_t vstride, int nrhs, int m,
+                               const int* gate, cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  const size_t smem = (size_t)op.nx * op.ny * sizeof(T2);
+  if (m > CMAX || smem > 160 * 1024) return false;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_coarse_gmres<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    configured = true;
+  }
+  k_coarse_gmres<T><<<nrhs, CT, smem, s>>>(op, (const T2*)f, (T2*)out, (T2*)V, vstride, m, gate);
+  return true;
+}
+
+template bool launch_coarse_gmres_fused<float>(const Op<float>&, const void*, void*, void*, size_t, int, int,
+                                               const int*, cudaStream_t);
+template bool launch_coarse_gmres_fused<double>(const Op<double>&, const void*, void*, void*, size_t, int, int,
+                                                const int*, cudaStream_t);
+
+}  // namespace helm

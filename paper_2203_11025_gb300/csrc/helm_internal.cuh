@@ -173,6 +173,11 @@ template <typename T> void launch_combine(const void* V, size_t vstride, size_t 
                                           const Op<T>* dinv_op, void* out, const int* gate, int nb,
                                           cudaStream_t s);
 
+// Coarsest GMRES(m) in one launch (coarse.cu); false if the grid does not fit.
+template <typename T> bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* V,
+                                                     size_t vstride, int nrhs, int m, const int* gate,
+                                                     cudaStream_t s);
+
 // FGMRES (outer solver)
 void launch_bnorm(const double2* b, size_t N, int nrhs, SolveState& ss, ArnoldiState& st, int nb, double tol,
                   cudaStream_t s);

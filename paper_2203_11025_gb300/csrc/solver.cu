@@ -98,6 +98,7 @@ struct helm_ctx {
   int* h_done = nullptr;             // pinned host mirror of done flags
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, long long> graph_kernels;  // kernel nodes per captured cycle
+  bool fused_coarse = true;          // one-launch coarsest GMRES when the grid fits in shared memory
 };
 
 namespace {
@@ -215,6 +216,10 @@ int coarse_gmres(helm_ctx* c, const void* f, void* out, int nrhs, const int* gat
   const size_t vstride = (size_t)nrhs * Nc;
   char* CV = (char*)W.CV;
   Op<T> op = op_on<T>(c, lc, c->d.beta);
+  if (c->fused_coarse && launch_coarse_gmres_fused<T>(op, f, out, CV, vstride, nrhs, mc, gate, s)) {
+    HLAUNCH();
+    return HELM_OK;
+  }
   ArnoldiState& st = W.cst;
   const int nb = vec_blocks(Nc, nrhs, c->nsm);
   launch_start<T>(f, CV, Nc, nrhs, st, nb, gate, s);
@@ -482,6 +487,7 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   cudaStream_t s = (cudaStream_t)stream;
   helm_ctx* c = new helm_ctx();
   c->d = d;
+  c->fused_coarse = !(d.flags & HELM_DESC_MULTIKERNEL_COARSE);
   HCHECK(cudaGetDevice(&c->device));
   HCHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
   size_t total = 0;

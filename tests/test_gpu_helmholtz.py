@@ -92,9 +92,10 @@ def test_transfer_parity(lib, dtype, tol):
     assert relerr(out, xf + H.prolong_bilinear(e, 48, 80)) < tol
 
 
+@pytest.mark.parametrize("multikernel", [0, 1])
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-11), (torch.complex64, 2e-5)])
-def test_coarse_gmres_parity(lib, dtype, tol):
-    hz, prob = make(lib, 128, 96, abc=16)
+def test_coarse_gmres_parity(lib, dtype, tol, multikernel):
+    hz, prob = make(lib, 128, 96, abc=16, flags=multikernel * lib.HELM_DESC_MULTIKERNEL_COARSE)
     lc = prob.hierarchy[-1]
     f = crandn(10, (4, lc.ny, lc.nx))
     f[2] = 0.0  # a zero right-hand side returns zero
@@ -107,10 +108,10 @@ def test_coarse_gmres_parity(lib, dtype, tol):
             assert relerr(x[k], ref) < tol
 
 
-@pytest.mark.parametrize("ny,nx", [(64, 64), (96, 160)])
+@pytest.mark.parametrize("ny,nx,multikernel", [(64, 64, 0), (96, 160, 0), (96, 160, 1)])
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-11), (torch.complex64, 1e-4)])
-def test_vcycle_parity_zero_guess(lib, ny, nx, dtype, tol):
-    hz, prob = make(lib, ny, nx, abc=16)
+def test_vcycle_parity_zero_guess(lib, ny, nx, multikernel, dtype, tol):
+    hz, prob = make(lib, ny, nx, abc=16, flags=multikernel * lib.HELM_DESC_MULTIKERNEL_COARSE)
     f = crandn(11, (3, ny, nx))
     z = hz.vcycle(dev(f, dtype)).cpu().numpy()
     for k in range(3):
@@ -199,6 +200,17 @@ def test_fgmres_host_io_matches_device(lib):
     _, ih = hz.fgmres(bh, xh, flags=lib.HELM_FLAG_HOST_IO | lib.HELM_FLAG_X0_ZERO)
     assert ih["iters"] == idv["iters"]
     assert torch.equal(xh, xd.cpu())
+
+
+def test_coarse_gmres_large_grid_uses_multikernel_path(lib):
+    """A coarsest grid too large for the one-launch kernel (144x144 complex64 > 160 KB)
+    takes the multi-kernel path automatically; parity holds there too."""
+    hz, prob = make(lib, 576, 576, abc=16)
+    lc = prob.hierarchy[-1]
+    f = crandn(19, (2, lc.ny, lc.nx))
+    x = hz.coarse_solve(dev(f, torch.complex64)).cpu().numpy()
+    for k in range(2):
+        assert relerr(x[k], H.gmres_jacobi(lc, f[k], prob.coarse_its)) < 2e-5
 
 
 def test_fgmres_full_size_bench_config(lib):

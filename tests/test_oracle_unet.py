@@ -1,0 +1,186 @@
+"""Pins of the U-Net oracle: layer identities from the paper's multigrid analogy
+(Eq. 2.9 kernels inside Eq. 3.1/3.3 convolutions), adjointness, finite-difference
+gradients, BatchNorm/eLU/Adam closed forms."""
+import numpy as np
+import pytest
+
+from conftest import load_golden_kernels
+from oracle import helmholtz as H
+from oracle import unet as U
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def test_strided_conv_with_full_weighting_kernel_is_restriction():
+    """A 5x5 stride-2 convolution (pad 2) whose centre 3x3 holds K_{I_h^H} equals R (Eq. 2.9)."""
+    gold = load_golden_kernels()["restrict"]
+    x = _rng(1).standard_normal((2, 12, 16, 1))
+    W = np.zeros((5, 5, 1, 1))
+    W[1:4, 1:4, 0, 0] = gold
+    out = U.conv2d(x, W, 2, 2)[..., 0]
+    assert np.allclose(out, H.restrict_fw(x[..., 0]), atol=1e-14)
+
+
+def test_transposed_conv_with_bilinear_kernel_is_prolongation():
+    gold = load_golden_kernels()["prolong"]
+    e = _rng(2).standard_normal((2, 6, 8, 1))
+    W = np.zeros((5, 5, 1, 1))
+    W[1:4, 1:4, 0, 0] = gold
+    out = U.conv2d_transposed(e, W, 2, 2, 12, 16)[..., 0]
+    assert np.allclose(out, H.prolong_bilinear(e[..., 0], 12, 16), atol=1e-14)
+
+
+@pytest.mark.parametrize("k,s,p", [(5, 2, 2), (3, 1, 1)])
+def test_transposed_conv_is_adjoint_of_conv(k, s, p):
+    rng = _rng(3)
+    x = rng.standard_normal((2, 10, 12, 3))
+    W = rng.standard_normal((k, k, 3, 5))
+    y = U.conv2d(x, W, s, p)
+    z = rng.standard_normal(y.shape)
+    xt = U.conv2d_transposed(z, W.transpose(0, 1, 3, 2), s, p, 10, 12)
+    assert np.isclose(np.sum(y * z), np.sum(x * xt), rtol=1e-12)
+
+
+def test_conv_matches_direct_sum():
+    rng = _rng(4)
+    x = rng.standard_normal((1, 7, 9, 2))
+    W = rng.standard_normal((5, 5, 2, 3))
+    out = U.conv2d(x, W, 2, 2)
+    o, q, d = 2, 3, 1
+    acc = 0.0
+    for ky in range(5):
+        for kx in range(5):
+            iy, ix = 2 * o + ky - 2, 2 * q + kx - 2
+            if 0 <= iy < 7 and 0 <= ix < 9:
+                acc += x[0, iy, ix] @ W[ky, kx, :, d]
+    assert np.isclose(out[0, o, q, d], acc, rtol=1e-13)
+
+
+def test_bn_eval_identity_and_train_statistics():
+    x = _rng(5).standard_normal((3, 4, 5, 6)) * 2 + 1
+    y = U.bn_eval(x, np.ones(6), np.zeros(6), np.zeros(6), np.ones(6))
+    assert np.allclose(y, x / np.sqrt(1 + U.BN_EPS), rtol=1e-15)
+    yt, _ = U.bn_train(x, np.full(6, 2.0), np.full(6, 0.5))
+    assert np.allclose(yt.mean(axis=(0, 1, 2)), 0.5, atol=1e-12)
+    assert np.allclose(yt.var(axis=(0, 1, 2)), 4.0 * x.var(axis=(0, 1, 2)) / (x.var(axis=(0, 1, 2)) + U.BN_EPS))
+
+
+def test_elu_values():
+    x = np.array([-50.0, -1.0, 0.0, 0.5])
+    assert np.allclose(U.elu(x), [np.expm1(-50.0), np.expm1(-1.0), 0.0, 0.5], rtol=0, atol=0)
+    g = U.elu_backward(np.ones(4), x)
+    assert np.allclose(g, [np.exp(-50.0), np.exp(-1.0), 1.0, 1.0])
+
+
+def test_adam_first_step_closed_form():
+    P = {"w": np.array([1.0, -2.0, 3.0])}
+    G = {"w": np.array([0.5, -4.0, 1e-3])}
+    M = {"w": np.zeros(3)}
+    V = {"w": np.zeros(3)}
+    U.adam_step(P, G, M, V, 1, 1e-4)
+    expect = np.array([1.0, -2.0, 3.0]) - 1e-4 * G["w"] / (np.abs(G["w"]) + 1e-8)
+    assert np.allclose(P["w"], expect, rtol=1e-14)
+
+
+def test_architecture_shapes_and_channels():
+    cfg = U.UNetConfig()
+    convs, bns = U.layer_specs(cfg)
+    names = [c[0] for c in convs]
+    assert names[:3] == ["down1", "res1.0.k1", "res1.0.k2"]
+    assert sum(1 for n in names if n.startswith("res4")) == 6       # 3 ResNets at the coarsest level
+    d = {c[0]: c for c in convs}
+    assert d["down1"][3:] == (4, 32) and d["down4"][3:] == (128, 256)
+    assert d["up4"][3:] == (256, 128) and d["up3"][3:] == (256, 64) and d["up2"][3:] == (128, 32)
+    assert d["up1"][3:] == (64, 2)
+    P = U.init_params(cfg, 0)
+    S = U.init_bn_stats(cfg)
+    x = _rng(6).standard_normal((1, 32, 32, 4))
+    out, _, _, feats = U.forward(cfg, P, S, x)
+    assert out.shape == (1, 32, 32, 2)
+    assert [f.shape[1:] for f in feats] == [(32, 32, 2), (16, 16, 32), (8, 8, 64), (4, 4, 128), (2, 2, 256)]
+
+
+def _tiny(context=None):
+    return U.UNetConfig(in_ch=4, out_ch=2, widths=(4, 8), coarse_resnets=2, context=context)
+
+
+def _fd_check(f, params, grads, keys, rng, n=4, eps=1e-5):
+    worst = 0.0
+    for k in keys:
+        for _ in range(n):
+            idx = tuple(rng.integers(0, s) for s in params[k].shape)
+            old = params[k][idx]
+            params[k][idx] = old + eps
+            fp = f()
+            params[k][idx] = old - eps
+            fm = f()
+            params[k][idx] = old
+            fd = (fp - fm) / (2 * eps)
+            worst = max(worst, abs(fd - grads[k][idx]) / max(abs(fd), 1e-3))
+    return worst
+
+
+def test_backward_matches_finite_differences():
+    """Every parameter group and the input: analytic gradient of the train-mode MSE loss
+    equals central finite differences (FP64, tiny net, 8x8 grid, batch 2)."""
+    cfg = _tiny()
+    rng = _rng(7)
+    P = U.init_params(cfg, 3)
+    for k in P:
+        if k.endswith(".beta") or k.endswith(".gamma") or k.endswith("bias"):
+            P[k] = P[k] + 0.1 * rng.standard_normal(P[k].shape)
+    S = U.init_bn_stats(cfg)
+    x = rng.standard_normal((2, 8, 8, 4))
+    tgt = rng.standard_normal((2, 8, 8, 2))
+    out, cache, _, _ = U.forward(cfg, P, S, x, train=True)
+    loss, gout = U.mse_loss(out, tgt)
+    G, gx, _ = U.backward(cfg, P, cache, gout)
+
+    def f():
+        return U.mse_loss(U.forward(cfg, P, S, x, train=True)[0], tgt)[0]
+
+    assert _fd_check(f, P, G, list(P.keys()), rng, n=2) < 1e-6
+    # input gradient
+    worst = 0.0
+    for _ in range(6):
+        idx = tuple(rng.integers(0, s) for s in x.shape)
+        old = x[idx]
+        x[idx] = old + 1e-5
+        fp = f()
+        x[idx] = old - 1e-5
+        fm = f()
+        x[idx] = old
+        fd = (fp - fm) / 2e-5
+        worst = max(worst, abs(fd - gx[idx]) / max(abs(fd), 1e-3))
+    assert worst < 1e-6
+
+
+def test_encoder_solver_backward_matches_finite_differences():
+    """Solver with encoder context (Eq. 3.5): gradients w.r.t. solver parameters and the
+    context features (through which the encoder is trained) match finite differences."""
+    enc_cfg = U.UNetConfig(in_ch=2, out_ch=4, widths=(4, 8), coarse_resnets=1)
+    ctx = U.context_channels(enc_cfg)
+    cfg = _tiny(context=ctx)
+    rng = _rng(8)
+    Pe = U.init_params(enc_cfg, 4)
+    Pe.update({k: v + 0.1 * rng.standard_normal(v.shape) for k, v in Pe.items() if k.endswith("beta")})
+    P = U.init_params(cfg, 5)
+    Se, S = U.init_bn_stats(enc_cfg), U.init_bn_stats(cfg)
+    med = rng.standard_normal((2, 8, 8, 2))
+    x = rng.standard_normal((2, 8, 8, 4))
+    tgt = rng.standard_normal((2, 8, 8, 2))
+
+    def total():
+        _, _, _, fe = U.forward(enc_cfg, Pe, Se, med, train=True)
+        out = U.forward(cfg, P, S, x, train=True, feats=fe)[0]
+        return U.mse_loss(out, tgt)[0]
+
+    _, ce, _, fe = U.forward(enc_cfg, Pe, Se, med, train=True)
+    out, cache, _, _ = U.forward(cfg, P, S, x, train=True, feats=fe)
+    _, gout = U.mse_loss(out, tgt)
+    G, _, gfe = U.backward(cfg, P, cache, gout)
+    assert _fd_check(total, P, G, ["down1", "down2", "up2", "up1", "res2.0.k1"], rng, n=3) < 1e-6
+    Ge = U.backward_features(enc_cfg, Pe, ce, gfe)
+    assert _fd_check(total, Pe, Ge, ["down1", "res2.0.k2", "up2", "up1", "up2.bn.gamma"], rng, n=3) < 1e-6
