@@ -154,7 +154,8 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
  *   kernel 1: fused residual + full weighting   (8+4 B read per fine point + 8 B per coarse point)
  *   kernel 2: fused prolongation + Jacobi       (8+4+8 B per fine point + 8 B per coarse point)
  *   kernel 3: MGS pass, dot + axpy              (32 B per point)
- *   kernel 4: one whole V-cycle (M_V)            (bytes: sum of its kernels)  */
+ *   kernel 4: one whole V-cycle (M_V)            (bytes: not reported, 0)
+ *   kernel 5: the coarsest-grid GMRES solve      (bytes: not reported, 0)      */
 int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes);
 
 #ifdef __cplusplus

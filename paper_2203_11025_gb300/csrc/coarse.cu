@@ -23,21 +23,30 @@ constexpr int CMAX = 32;
 __device__ __forceinline__ double2 z2(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return z2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
-// Sum over the block, returned to every thread (fixed summation order).
-__device__ __forceinline__ double2 block_allsum(double2 v, double2* red) {
+// Sum over the block, returned to every thread (fixed summation order).  The
+// per-thread and per-warp sums stay in T (FP64 throughput is scarce on this
+// part); the 32 warp totals are added in FP64 by one warp and broadcast.
+template <typename T>
+__device__ __forceinline__ double2 block_allsum(T ax, T ay, double2* red, double2* bcast) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = v;
+  if (lane == 0) red[warp] = z2((double)ax, (double)ay);
   __syncthreads();
-  double2 t = z2(0, 0);
-#pragma unroll 8
-  for (int i = 0; i < CT / 32; ++i) { t.x += red[i].x; t.y += red[i].y; }
+  if (warp == 0) {
+    double2 v = red[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if (lane == 0) *bcast = v;
+  }
   __syncthreads();
-  return t;
+  return *bcast;
 }
 
 template <typename T>
@@ -55,6 +64,7 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* w = reinterpret_cast<T2*>(smem_raw);
   __shared__ double2 red[CT / 32];
+  __shared__ double2 bcast;
   __shared__ double2 Hs[(CMAX + 1) * CMAX];
   __shared__ double2 ys[CMAX];
   __shared__ double2 g[CMAX + 1];
@@ -69,9 +79,9 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
   T2* outr = out + off;
 
   // beta = ||f||, v_0 = f / beta
-  double2 acc = z2(0, 0);
-  for (int p = tid; p < N; p += CT) { T2 v = fr[p]; acc.x += (double)v.x * v.x + (double)v.y * v.y; }
-  const double beta = sqrt(block_allsum(acc, red).x);
+  T nb = 0;
+  for (int p = tid; p < N; p += CT) { T2 v = fr[p]; nb += v.x * v.x + v.y * v.y; }
+  const double beta = sqrt(block_allsum(nb, T(0), red, &bcast).x);
   if (!(beta > 0.0)) {                                 // zero (or non-finite) right-hand side
     T2 zv = czero<T2>();
     if (beta != beta) { zv.x = beta; zv.y = beta; }    // propagate NaN
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
         ax += a.x * b.x + a.y * b.y;
         ay += a.x * b.y - a.y * b.x;
       }
-      const double2 h = block_allsum(z2((double)ax, (double)ay), red);
+      const double2 h = block_allsum(ax, ay, red, &bcast);
       if (tid == 0) Hs[i * m + j] = h;
       const T hx = (T)h.x, hy = (T)h.y;
       for (int p = tid; p < N; p += CT) {
@@ -122,7 +132,7 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
     }
     T nn = 0;
     for (int p = tid; p < N; p += CT) { T2 b = w[p]; nn += b.x * b.x + b.y * b.y; }
-    const double nrm = sqrt(block_allsum(z2((double)nn, 0.0), red).x);
+    const double nrm = sqrt(block_allsum(nn, T(0), red, &bcast).x);
     if (tid == 0) Hs[(j + 1) * m + j] = z2(nrm, 0.0);
     k = j + 1;
     if (nrm == 0.0) break;                             // happy breakdown (uniform across the block)

@@ -31,26 +31,24 @@ __device__ __forceinline__ double2 dconj(double2 a) { return d2(a.x, -a.y); }
 __device__ __forceinline__ double dabs(double2 a) { return hypot(a.x, a.y); }
 __device__ __forceinline__ double2 dscale(double2 a, double s) { return d2(a.x * s, a.y * s); }
 
-// Sum over a 256-thread block; the total is valid in thread 0.
-__device__ double2 block_sum(double2 v) {
+// Sum over a 256-thread block; the total is valid in thread 0.  Threads and
+// warps add in T (FP64 throughput is scarce on this part); the 8 warp totals
+// are added in FP64.
+template <typename T>
+__device__ double2 block_sum(T ax, T ay) {
   __shared__ double2 sm[NT / 32];
   __syncthreads();  // protects sm against a previous use
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    ax += __shfl_down_sync(0xffffffffu, ax, o);
+    ay += __shfl_down_sync(0xffffffffu, ay, o);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sm[warp] = v;
+  if (lane == 0) sm[warp] = d2((double)ax, (double)ay);
   __syncthreads();
-  if (warp == 0) {
-    v = lane < NT / 32 ? sm[lane] : d2(0, 0);
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-      v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-      v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-    }
-  }
+  double2 v = d2(0, 0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) { v.x += sm[i].x; v.y += sm[i].y; }
   return v;
 }
 
@@ -67,9 +65,9 @@ __device__ bool finish_reduction(double2 block_total, double2* part, int* counte
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double2 acc = d2(0, 0);
-  for (int i = threadIdx.x; i < nb; i += NT) acc = dadd(acc, __ldcg(part + i));
-  total = block_sum(acc);
+  double ax = 0, ay = 0;
+  for (int i = threadIdx.x; i < nb; i += NT) { double2 p = __ldcg(part + i); ax += p.x; ay += p.y; }
+  total = block_sum<double>(ax, ay);
   if (threadIdx.x == 0) *counter = 0;
   return true;
 }
@@ -134,12 +132,12 @@ __global__ void __launch_bounds__(NT) k_norm_start(const typename vec2<T>::type*
     return;
   }
   const typename vec2<T>::type* fr = f + (size_t)rhs * N;
-  double2 acc = d2(0, 0);
+  T acc = 0;
   for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < N; e += (size_t)nb * NT) {
     auto v = fr[e];
-    acc.x += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    acc += v.x * v.x + v.y * v.y;
   }
-  double2 bt = block_sum(acc), tot;
+  double2 bt = block_sum<T>(acc, T(0)), tot;
   if (finish_reduction(bt, st.part + (size_t)rhs * st.nbmax, st.counter + rhs, nb, tot) && threadIdx.x == 0) {
     double beta = sqrt(tot.x);
     st.beta[rhs] = beta;
@@ -176,8 +174,6 @@ __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, co
   const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
   const T2* zr = z + off;
   T ax = 0, ay = 0;
-  double2 acc = d2(0, 0);
-  int cnt = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
     T2 c, s = czero<T2>();
@@ -199,10 +195,8 @@ __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, co
     r.y -= s.y * op.inv_h2;
     w[off + p] = r;
     cdot_acc(ax, ay, v0[off + p], r);
-    if (++cnt == 4) { acc.x += ax; acc.y += ay; ax = ay = 0; cnt = 0; }
   }
-  acc.x += ax; acc.y += ay;
-  double2 bt = block_sum(acc), tot;
+  double2 bt = block_sum<T>(ax, ay), tot;
   if (finish_reduction(bt, st.part + (size_t)rhs * st.nbmax, st.counter + rhs, nb, tot) && threadIdx.x == 0)
     st.H[(size_t)rhs * (st.m + 1) * st.m + j] = tot;  // row 0, column j
 }
@@ -224,8 +218,6 @@ __global__ void __launch_bounds__(NT) k_mgs(const typename vec2<T>::type* __rest
   const T2* vn = (i <= j) ? V + (size_t)i * vstride + off : nullptr;
   T2* wr = w + off;
   T ax = 0, ay = 0;
-  double2 acc = d2(0, 0);
-  int cnt = 0;
   for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < N; e += (size_t)nb * NT) {
     T2 a = vp[e], wv = wr[e];
     wv.x -= hx * a.x - hy * a.y;
@@ -233,10 +225,8 @@ __global__ void __launch_bounds__(NT) k_mgs(const typename vec2<T>::type* __rest
     wr[e] = wv;
     if (vn) cdot_acc(ax, ay, vn[e], wv);
     else ax += wv.x * wv.x + wv.y * wv.y;
-    if (++cnt == 4) { acc.x += ax; acc.y += ay; ax = ay = 0; cnt = 0; }
   }
-  acc.x += ax; acc.y += ay;
-  double2 bt = block_sum(acc), tot;
+  double2 bt = block_sum<T>(ax, ay), tot;
   if (finish_reduction(bt, st.part + (size_t)rhs * st.nbmax, st.counter + rhs, nb, tot) && threadIdx.x == 0) {
     double2* Hr = st.H + (size_t)rhs * (m + 1) * m;
     if (vn) {
@@ -314,12 +304,12 @@ __global__ void __launch_bounds__(NT) k_bnorm(const double2* __restrict__ b, siz
                                               ArnoldiState st, int nb, double tol) {
   const int rhs = blockIdx.y;
   const double2* br = b + (size_t)rhs * N;
-  double2 acc = d2(0, 0);
+  double acc = 0;
   for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < N; e += (size_t)nb * NT) {
     double2 v = br[e];
-    acc.x += v.x * v.x + v.y * v.y;
+    acc += v.x * v.x + v.y * v.y;
   }
-  double2 bt = block_sum(acc), tot;
+  double2 bt = block_sum<double>(acc, 0.0), tot;
   if (finish_reduction(bt, st.part + (size_t)rhs * st.nbmax, st.counter + rhs, nb, tot) && threadIdx.x == 0) {
     double bn = sqrt(tot.x);
     ss.bnorm[rhs] = bn;
@@ -344,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
   const int nx = A.nx, ny = A.ny;
   const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
   const double2* xr = x + off;
-  double2 acc = d2(0, 0);
+  double acc = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), xx = (int)(p - (size_t)y * nx);
     double2 s = d2(0, 0);
@@ -358,9 +348,9 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
     typename vec2<T>::type rt;
     rt.x = (T)r.x; rt.y = (T)r.y;
     r0[off + p] = rt;
-    acc.x += r.x * r.x + r.y * r.y;
+    acc += r.x * r.x + r.y * r.y;
   }
-  double2 bt = block_sum(acc), tot;
+  double2 bt = block_sum<double>(acc, 0.0), tot;
   if (finish_reduction(bt, st.part + (size_t)rhs * st.nbmax, st.counter + rhs, nb, tot) && threadIdx.x == 0) {
     double beta = sqrt(tot.x);
     ss.relres[rhs] = beta / ss.bnorm[rhs];

@@ -678,6 +678,10 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
   const int nb = vec_blocks(N, nrhs, h->nsm);
   // active flags on, finite Hessenberg entries
   HCHECK(cudaMemsetAsync(W.fst.H, 0, (size_t)nrhs * (W.fst.m + 1) * W.fst.m * 16, s));
+  {  // a nonzero right-hand side on the coarsest level so its solve does real work
+    const int lc = h->d.levels - 1;
+    HCHECK(cudaMemcpyAsync(W.F[lc], V, (size_t)nrhs * level_points(h, lc) * es, cudaMemcpyDeviceToDevice, s));
+  }
   std::vector<int> ones(nrhs, 1);
   HCHECK(cudaMemcpyAsync(W.fst.active, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
   HCHECK(cudaMemcpyAsync(W.fst.kmax, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -690,6 +694,7 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
                                            V + vstride * es, nrhs, nullptr, s); break;
       case 3: launch_mgs<float>(V, vstride, V + 5 * vstride * es, N, nrhs, 4, 2, W.fst, nb, s); break;
       case 4: return vcycle<float>(h, 0, V, nullptr, V + vstride * es, nrhs, nullptr, s);
+      case 5: return coarse_gmres<float>(h, W.F[h->d.levels - 1], W.E[h->d.levels - 1], nrhs, nullptr, s);
       default: g_err = "unknown kernel id"; return HELM_EINVAL;
     }
     return HELM_OK;
