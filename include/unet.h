@@ -1,0 +1,123 @@
+/*
+ * U-Net preconditioners of libhelm (Azulay & Treister, arXiv 2203.11025,
+ * Sec. 3): the network itself, its training (MSE loss of Eq. 3.7, Adam), the
+ * encoder-solver pair (Sec. 3.3) and the preconditioners M_JU (Alg. 2) and
+ * M_VU (Eq. 3.4).
+ *
+ * Network (Sec. 3.1): down levels x_l = eLU(BN(R_l x_{l-1})) with R_l a 5x5
+ * stride-2 convolution doubling the channels (Eq. 3.1), a ResNet block
+ * eLU(BN(x + K2 eLU(BN(K1 x)))) per level and `coarse_resnets` at the coarsest
+ * (Eq. 3.2); up levels u <- cat(BN(P_l eLU(u)), x_{l-1}) with P_l a 5x5
+ * stride-2 transposed convolution (Eq. 3.3); the last up layer maps to
+ * out_ch channels with a bias.  Channel widths are configurable (the paper's
+ * figure with them is lost; default 32, 64, 128, 256).
+ *
+ * Conventions: activations NHWC float32 at this boundary ([B][ny][nx][ch]),
+ * BF16 inside with FP32 accumulation; parameters travel as one flat float32
+ * HOST array: every convolution weight in layer order as [ky][kx][cin][cout],
+ * then the output bias, then (gamma, beta) of every BatchNorm in layer order.
+ * Layer order: down1, res1.0.k1, res1.0.k2, down2, ..., downL, resL.0.k1, ...,
+ * upL, ..., up2, up1; BatchNorms: down1.bn, res1.0.bn1, res1.0.bn2, ..., upL.bn,
+ * ..., up2.bn.  Return codes and helm_last_error() as in helm.h.
+ */
+#ifndef HELM_UNET_H
+#define HELM_UNET_H
+
+#include "helm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct unet_ctx* unet_t;
+
+typedef struct {
+  int in_ch;               /* 4 for a solver (Re r, Im r, kappa^2, gamma), 2 for an encoder */
+  int out_ch;              /* 2 for a solver (Re e, Im e); encoder: channels of f^(0)       */
+  int levels;              /* down/up levels (default 4)                                    */
+  int coarse_resnets;      /* ResNet blocks at the coarsest level (Sec. 3.1: 3)             */
+  int widths[8];           /* channels per level (default 32, 64, 128, 256)                 */
+  int context[9];          /* solver with encoder: channels of f^(0..levels), else all 0    */
+  int flags;               /* UNET_FLAG_*                                                   */
+} unet_cfg;
+/* Run every convolution on CUDA cores (FP32 FMA) instead of the tcgen05 tensor-core
+ * kernel; same arithmetic up to summation order (cross-checking). */
+enum { UNET_FLAG_SIMT = 1 };
+
+enum { UNET_STANDALONE = 0, UNET_ENCODER = 1, UNET_SOLVER = 2 };
+
+/* Defaults of the given kind; UNET_SOLVER fills `context` for the default encoder. */
+int unet_cfg_default(unet_cfg* cfg, int kind);
+/* Create a network with He-normal weights drawn from `seed` (SplitMix64 +
+ * Box-Muller), BN gamma 1, beta 0, running mean 0, var 1. */
+int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out);
+void unet_destroy(unet_t net);
+/* Sizes of the flat parameter vector and of the BN running-stat vector (means then vars). */
+int unet_sizes(unet_t net, long long* n_params, long long* n_bn);
+int unet_set_params(unet_t net, const float* host, long long n);
+int unet_get_params(unet_t net, float* host, long long n);
+int unet_set_bn_stats(unet_t net, const float* host, long long n);
+int unet_get_bn_stats(unet_t net, float* host, long long n);
+/* Synchronise and report a failure recorded by a tensor-core kernel (a bounded
+ * wait that expired): 0 if none.  Clears the record. */
+int unet_status(unet_t net, int* failed);
+/* Parameter gradients accumulated since the last unet_zero_grad (flat, host). */
+int unet_get_grads(unet_t net, float* host, long long n);
+int unet_zero_grad(unet_t net, helm_stream_t stream);
+
+/* Forward pass on x (device float32 [B][ny][nx][in_ch]) into out (device float32
+ * [B][ny][nx][out_ch]).  train != 0 uses batch statistics, updates the running
+ * statistics and keeps what unet_backward needs.  A solver with context reads
+ * the features of its attached encoder's last forward (unet_attach_encoder).
+ * ny, nx must be multiples of 2^levels. */
+int unet_forward(unet_t net, const float* x, float* out, int B, int ny, int nx, int train, helm_stream_t stream);
+/* Backward of the last train-mode forward for the loss sum(gout * out): adds
+ * parameter gradients; writes d loss / d x into gx if not null (device float32
+ * like x).  A solver with an attached encoder also back-propagates into the
+ * encoder (whose own last forward must be train-mode). */
+int unet_backward(unet_t net, const float* gout, float* gx, helm_stream_t stream);
+/* MSE loss of Eq. 3.7 between out and target (device float32, n elements, B
+ * samples): writes gout = d loss / d out (device) and the loss into *loss_dev. */
+int unet_mse(const float* out, const float* target, long long n, int B, float* gout, float* loss_dev,
+             helm_stream_t stream);
+/* One Adam step (bias-corrected) on every parameter of net (and of its attached encoder). */
+int unet_adam_step(unet_t net, float lr, float beta1, float beta2, float eps, helm_stream_t stream);
+
+/* Attach an encoder to a solver net built with context channels; detach with NULL. */
+int unet_attach_encoder(unet_t solver, unet_t encoder);
+/* Run the attached encoder on the medium of h (kappa^2 and the layer
+ * attenuation of the fine grid, batch 1) and keep its features for the
+ * solver: once per medium at solve time (Sec. 3.3, train = 0), or before each
+ * solver training step when the pair is trained jointly (train = 1). */
+int unet_encode(unet_t solver, helm_t h, int train, helm_stream_t stream);
+
+/* Preconditioner application e = M(r) with the U-Net in inference mode:
+ *   HELM_PREC_JU: Alg. 2 (Jacobi on A from 0, U-Net on the new residual, Jacobi)
+ *   HELM_PREC_VU: Eq. 3.4 (V-cycle on M started from U-Net(r))
+ * The network sees [Re, Im](h^2 r / s), kappa^2, gamma with s = RMS(h^2 r) per
+ * right-hand side and its output is scaled back by s.  r, e: complex [nrhs][ny][nx],
+ * device, dtype HELM_C32 or HELM_C64; r and e must differ. */
+int unet_precond(helm_t h, unet_t net, int kind, const void* r, void* e, int nrhs, int dtype,
+                 helm_stream_t stream);
+
+/* Training batch from generated pairs (Sec. 3.4): sample i mixes the pairs
+ * idx[i][q] (q < nmix) with complex coefficients coef[i][q] = (re, im) (the
+ * paper's augmentation by linear combinations; nmix = 1, coef 1 = no mixing),
+ * r' = sum coef r[idx], e' likewise, then writes the network input
+ * x[i] = [Re, Im](h^2 r' / s), kappa^2, gamma and the target [Re, Im](e' / s),
+ * s = RMS(h^2 r').  r, e: device complex128 [npairs][ny][nx]; idx (int) and
+ * coef (double pairs) are HOST arrays [count][nmix]; x: device float32
+ * [count][ny][nx][4]; target: device float32 [count][ny][nx][2].  Synchronises. */
+int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int count, int nmix, const int* idx,
+                    const double* coef, float* x, float* target, helm_stream_t stream);
+
+/* Training pairs of Eq. 3.8-3.9 on the medium of h: x ~ CN(0,1) per node and
+ * k ~ U{1..kmax} per pair from SplitMix64(seed) (counter layout in synth.py),
+ * b = A x, x~ = k FGMRES(m)+M_V iterations from 0, r = b - A x~, e = x - x~.
+ * r, e: device complex128 [count][ny][nx]. */
+int helm_gen_pairs(helm_t h, int count, unsigned long long seed, int kmax, void* r, void* e, helm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_UNET_H */

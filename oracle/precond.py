@@ -1,0 +1,104 @@
+"""FP64 CPU oracle: U-Net preconditioners and the training-pair generator.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+  M_JU (Alg. 2):  e1 = Jacobi(0, r); e2 = e1 + U-Net(r - A e1); e = Jacobi(e2, r)
+                  (damped Jacobi on the Helmholtz operator A, w = 0.8: a reading,
+                  the algorithm names A^h but not the damping).
+  M_VU (Eq. 3.4): e = V-cycle(e0 = U-Net(r), r) on the shifted Laplacian.
+  U-Net(r) = s * net([Re, Im](h^2 r / s), kappa^2, gamma), s = RMS(h^2 r): the
+  network runs in inference mode (BatchNorm with running statistics).
+  Pairs (Eq. 3.8-3.9): b = A x, x~ = k iterations of FGMRES(10) + M_V from 0,
+  r = b - A x~, e = x - x~.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import helmholtz as H
+from oracle import unet as U
+
+
+def unet_apply(prob: H.Problem, cfg, P, S, r, feats=None):
+    """U-Net(r) for residuals r (B, ny, nx) complex."""
+    lv = prob.hierarchy[0]
+    x, s = U.make_input(r, lv.kappa2, lv.gamma, lv.h)
+    out, _, _, _ = U.forward(cfg, P, S, x, train=False, feats=feats)
+    return s[:, None, None] * (out[..., 0] + 1j * out[..., 1])
+
+
+def precond_ju(prob: H.Problem, cfg, P, S, r, feats=None):
+    A = prob.A
+    w = prob.jacobi_w
+    e1 = H.jacobi(A, np.zeros_like(r), r, w)
+    e2 = e1 + unet_apply(prob, cfg, P, S, H.residual(A, r, e1), feats)
+    return H.jacobi(A, e2, r, w)
+
+
+def precond_vu(prob: H.Problem, cfg, P, S, r, feats=None):
+    e0 = unet_apply(prob, cfg, P, S, r, feats)
+    return np.stack([H.vcycle(prob, r[k], e0[k]) for k in range(r.shape[0])])
+
+
+def encoder_features(prob: H.Problem, enc_cfg, Pe, Se):
+    lv = prob.hierarchy[0]
+    med = np.stack([lv.kappa2, lv.gamma], axis=-1)[None]
+    _, _, _, feats = U.forward(enc_cfg, Pe, Se, med, train=False)
+    return feats
+
+
+def gen_pairs(prob: H.Problem, x, ks, m=10):
+    """Eq. 3.8-3.9 for given draws x (count, ny, nx) and iteration counts ks."""
+    A = prob.A
+    rs, es = [], []
+    for j in range(x.shape[0]):
+        b = H.apply_op(A, x[j])
+        res = H.fgmres(A, H.precond_v(prob), b, m=m, tol=0.0, maxit=int(ks[j]))
+        xt = res.x
+        rs.append(b - H.apply_op(A, xt))
+        es.append(x[j] - xt)
+    return np.stack(rs), np.stack(es)
+
+
+def flatten_params(cfg, P):
+    """Flat float parameter vector in the library's order (include/unet.h)."""
+    convs, bns = U.layer_specs(cfg)
+    parts = [P[name].ravel() for name, *_ in convs]
+    parts.append(P["up1.bias"])
+    for name, _ in bns:
+        parts.append(P[name + ".gamma"])
+        parts.append(P[name + ".beta"])
+    return np.concatenate(parts)
+
+
+def unflatten_params(cfg, flat):
+    convs, bns = U.layer_specs(cfg)
+    P, o = {}, 0
+    for name, kind, k, cin, cout in convs:
+        n = k * k * cin * cout
+        P[name] = flat[o:o + n].reshape(k, k, cin, cout).astype(np.float64)
+        o += n
+    P["up1.bias"] = flat[o:o + cfg.out_ch].astype(np.float64)
+    o += cfg.out_ch
+    for name, c in bns:
+        P[name + ".gamma"] = flat[o:o + c].astype(np.float64)
+        P[name + ".beta"] = flat[o + c:o + 2 * c].astype(np.float64)
+        o += 2 * c
+    return P
+
+
+def flatten_bn(cfg, S):
+    _, bns = U.layer_specs(cfg)
+    return np.concatenate([S[n + ".mean"] for n, _ in bns] + [S[n + ".var"] for n, _ in bns])
+
+
+def unflatten_bn(cfg, flat):
+    _, bns = U.layer_specs(cfg)
+    S, o = {}, 0
+    for n, c in bns:
+        S[n + ".mean"] = flat[o:o + c].astype(np.float64)
+        o += c
+    for n, c in bns:
+        S[n + ".var"] = flat[o:o + c].astype(np.float64)
+        o += c
+    return S

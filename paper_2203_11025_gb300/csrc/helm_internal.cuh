@@ -147,6 +147,7 @@ struct SolveState {         // FGMRES, per right-hand side, device
   int* done;                // converged (or failed) for good
   int* iters;
   int* status;              // 0 running/converged, 1 max iterations, -3 non-finite
+  const int* maxit_rhs;     // per right-hand-side iteration cap, or null (use the global one)
 };
 
 int vec_blocks(size_t N, int nrhs, int nsm);

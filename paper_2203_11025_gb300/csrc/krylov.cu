@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
     double beta = sqrt(tot.x);
     ss.relres[rhs] = beta / ss.bnorm[rhs];
     st.k[rhs] = 0;
+    if (ss.maxit_rhs) maxit = ss.maxit_rhs[rhs];
     if (!isfinite(beta)) {
       ss.done[rhs] = 1; ss.status[rhs] = -3; st.active[rhs] = 0;
     } else if (beta <= st.tol_abs[rhs]) {

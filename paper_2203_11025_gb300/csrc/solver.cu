@@ -11,6 +11,7 @@
 #include "../../include/helm.h"
 #include "helm_internal.cuh"
 #include "unet_api.h"
+#include "unet_internal.cuh"
 
 namespace {
 thread_local std::string g_err;
@@ -72,6 +73,9 @@ struct Work {
   SolveState ss{};
   double2* bx = nullptr;             // staging for HOST_IO: b and x (FP64) [rhs][N] each
   double2* xx = nullptr;
+  void* S0 = nullptr;                // two fine-grid scratch vectors for the U-Net preconditioners
+  void* S1 = nullptr;
+  int* maxit_rhs = nullptr;          // per right-hand-side iteration caps (pair generator)
 };
 
 struct GraphKey {
@@ -98,6 +102,7 @@ struct helm_ctx {
   int* h_done = nullptr;             // pinned host mirror of done flags
   std::map<GraphKey, cudaGraphExec_t> graphs;
   std::map<GraphKey, long long> graph_kernels;  // kernel nodes per captured cycle
+  float* gam0 = nullptr;             // absorbing-layer attenuation on the fine grid (float32)
   bool fused_coarse = true;          // one-launch coarsest GMRES when the grid fits in shared memory
 };
 
@@ -143,6 +148,7 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
   total += (size_t)(mc + 1) * nrhs * Nc * es + 256;
   total += (size_t)(2 * m + 1) * nrhs * N0 * es + 512;
   total += 2 * (size_t)nrhs * N0 * 16 + 512;
+  total += 2 * ((size_t)nrhs * N0 * es + 256) + (size_t)nrhs * 4 + 256;
   total += st_bytes(mc) + st_bytes(m) + (size_t)nrhs * 64 + 4096;
   void* mem = nullptr;
   if (cudaMalloc(&mem, total) != cudaSuccess) {
@@ -164,6 +170,9 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
   W.Z = W.arena.take((size_t)m * nrhs * N0 * es);
   W.bx = (double2*)W.arena.take((size_t)nrhs * N0 * 16);
   W.xx = (double2*)W.arena.take((size_t)nrhs * N0 * 16);
+  W.S0 = W.arena.take((size_t)nrhs * N0 * es);
+  W.S1 = W.arena.take((size_t)nrhs * N0 * es);
+  W.maxit_rhs = (int*)W.arena.take((size_t)nrhs * 4);
   auto make_st = [&](ArnoldiState& st, int mm) {
     st.m = mm;
     st.nbmax = nbmax;
@@ -189,6 +198,7 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
   W.ss.done = (int*)W.arena.take((size_t)nrhs * 4);
   W.ss.iters = (int*)W.arena.take((size_t)nrhs * 4);
   W.ss.status = (int*)W.arena.take((size_t)nrhs * 4);
+  W.ss.maxit_rhs = nullptr;
   if (!W.ss.status || !W.fst.part) {
     g_err = "workspace layout overflow";
     free_work(W);
@@ -347,9 +357,15 @@ int fgmres_cycle(helm_ctx* c, int precond, void* net, double2* x, int nrhs, int 
 
 template <typename T>
 int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int nrhs, const fgmres_opts& o,
-               fgmres_result* res, cudaStream_t caller) {
+               fgmres_result* res, cudaStream_t caller, const int* maxit_rhs_host = nullptr) {
   HTRY(ensure_work<T>(c, nrhs, o.restart));
   Work& W = work_of<T>(c);
+  if (maxit_rhs_host) {
+    HCHECK(cudaMemcpyAsync(W.maxit_rhs, maxit_rhs_host, nrhs * sizeof(int), cudaMemcpyHostToDevice, caller));
+    W.ss.maxit_rhs = W.maxit_rhs;
+  } else {
+    W.ss.maxit_rhs = nullptr;
+  }
   const size_t N = level_points(c, 0);
   const int nb = vec_blocks(N, nrhs, c->nsm);
   const int m = o.restart;
@@ -360,11 +376,13 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   const Op<double> A64 = op_on<double>(c, 0, 0.0);
   launch_bnorm(b, N, nrhs, W.ss, W.fst, nb, o.tol, s);
   HLAUNCH();
+  if (precond == HELM_PREC_JU || precond == HELM_PREC_VU) HTRY(unet_prepare_impl(c, net, nrhs));
   cudaGraphExec_t exec = nullptr;
   long long per_cycle = -1;
   const bool use_graph = !(o.flags & HELM_FLAG_NO_GRAPH);
   if (use_graph) {
     GraphKey key{(int)sizeof(T), precond, nrhs, m, o.maxit, b, x, net};
+    if (maxit_rhs_host) key.maxit = -1 - o.maxit;
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
       exec = it->second;
@@ -451,6 +469,62 @@ int check_level(helm_t h, int level, int need_coarser) {
 }  // namespace
 
 // ===========================================================================
+// bridge used by the U-Net preconditioners (unet.cu)
+// ===========================================================================
+namespace helm {
+int vcycle_public(helm_ctx* c, const void* f, const void* v_in, void* out, int nrhs, int real_bytes, const int* gate,
+                  cudaStream_t s) {
+  if (real_bytes == 8) { HTRY(ensure_work<double>(c, nrhs, c->d.coarse_its)); return vcycle<double>(c, 0, f, v_in, out, nrhs, gate, s); }
+  HTRY(ensure_work<float>(c, nrhs, c->d.coarse_its));
+  return vcycle<float>(c, 0, f, v_in, out, nrhs, gate, s);
+}
+int jacobi_public(helm_ctx* c, int op, const void* f, const void* x_in, void* x_out, int nrhs, int real_bytes,
+                  const int* gate, cudaStream_t s) {
+  const double beta = op == HELM_OP_M ? c->d.beta : 0.0;
+  if (real_bytes == 8) launch_jacobi<double>(op_on<double>(c, 0, beta), c->d.jacobi_w, f, x_in, x_out, nrhs, gate, s);
+  else launch_jacobi<float>(op_on<float>(c, 0, beta), (float)c->d.jacobi_w, f, x_in, x_out, nrhs, gate, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+int residual_public(helm_ctx* c, int op, const void* b, const void* x, void* r, int nrhs, int real_bytes,
+                    const int* gate, cudaStream_t s) {
+  const double beta = op == HELM_OP_M ? c->d.beta : 0.0;
+  if (real_bytes == 8) launch_apply<double>(op_on<double>(c, 0, beta), x, b, r, nrhs, gate, s);
+  else launch_apply<float>(op_on<float>(c, 0, beta), x, b, r, nrhs, gate, s);
+  HLAUNCH();
+  return HELM_OK;
+}
+void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double* gmax, const float** k2f,
+                   const float** gam) {
+  *nx = c->d.nx; *ny = c->d.ny; *h = c->d.h; *abc_w = c->d.abc_width; *gmax = c->d.abc_gamma_max;
+  *k2f = c->L[0].k2f;
+  *gam = c->gam0;
+}
+void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
+  const int r = real_bytes == 8 ? ensure_work<double>(c, nrhs, c->d.coarse_its)
+                                : ensure_work<float>(c, nrhs, c->d.coarse_its);
+  if (r < 0) return nullptr;
+  Work& W = real_bytes == 8 ? c->w64 : c->w32;
+  return which == 0 ? W.S0 : W.S1;
+}
+}  // namespace helm
+
+namespace {
+__global__ void k_sub_inplace(double2* __restrict__ e, const double2* __restrict__ xt, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double2 a = e[i], b = xt[i];
+    e[i] = make_double2(a.x - b.x, a.y - b.y);
+  }
+}
+uint64_t host_splitmix(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
@@ -515,6 +589,9 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   for (int l = 1; l < d.levels; ++l)
     launch_coarsen_kappa2(c->L[l - 1].k2d, c->L[l - 1].nx, c->L[l - 1].ny, c->L[l].k2d, c->L[l].k2f, s);
   HLAUNCH();
+  HCHECK(cudaMalloc(&c->gam0, n0 * 4));
+  gamma_field(d.ny, d.nx, d.abc_width, (float)d.abc_gamma_max, c->gam0, s);
+  HLAUNCH();
   HCHECK(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
   HCHECK(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
   HCHECK(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -531,6 +608,7 @@ void helm_destroy(helm_t h) {
   free_work(h->w32);
   free_work(h->w64);
   if (h->level_mem) cudaFree(h->level_mem);
+  if (h->gam0) cudaFree(h->gam0);
   if (h->h_done) cudaFreeHost(h->h_done);
   if (h->own) cudaStreamDestroy(h->own);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -663,6 +741,37 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
     HCHECK(cudaStreamSynchronize(caller));
   }
   return r;
+}
+
+int helm_gen_pairs(helm_t h, int count, unsigned long long seed, int kmax, void* r, void* e, helm_stream_t stream) {
+  HTRY(check_common(h, count, HELM_C64));
+  if (!r || !e || r == e || kmax < 1 || kmax > 1000) { g_err = "bad arguments"; return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)h->d.nx * h->d.ny;
+  HTRY(ensure_work<float>(h, count, h->d.coarse_its > 10 ? h->d.coarse_its : 10));
+  Work& W = h->w32;
+  // x ~ CN(0,1) into e; b = A x into r (FP64)
+  complex_normal(seed, count, N, (double2*)e, s);
+  launch_apply<double>(op_on<double>(h, 0, 0.0), e, nullptr, r, count, nullptr, s);
+  HLAUNCH();
+  // k_j = 1 + floor(U_j kmax), U_j the j-th uniform of stream `seed`
+  std::vector<int> ks(count);
+  for (int j = 0; j < count; ++j) {
+    double u = ((double)(host_splitmix(seed, (uint64_t)j) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    ks[j] = 1 + (int)std::floor(u * kmax);
+    if (ks[j] > kmax) ks[j] = kmax;
+  }
+  // x~ = k_j FGMRES(M_V) iterations from 0 (Eq. 3.8)
+  fgmres_opts o{std::max(10, kmax), 0.0, kmax, HELM_FLAG_X0_ZERO};
+  if (o.restart > 32) o.restart = 32;
+  fgmres_result res{};
+  int st = fgmres_run<float>(h, HELM_PREC_V, nullptr, (const double2*)r, W.xx, count, o, &res, s, ks.data());
+  if (st < 0) return st;
+  // r = b - A x~ ; e = x - x~ (Eq. 3.9)
+  launch_apply<double>(op_on<double>(h, 0, 0.0), W.xx, r, r, count, nullptr, s);
+  k_sub_inplace<<<1024, 256, 0, s>>>((double2*)e, W.xx, (size_t)count * N);
+  HLAUNCH();
+  return HELM_OK;
 }
 
 int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes) {

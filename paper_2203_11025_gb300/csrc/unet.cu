@@ -1,0 +1,882 @@
+// U-Net executor and C ABI (include/unet.h): network layout in the order of
+// Sec. 3.1 (Eq. 3.1-3.3), encoder-solver context (Sec. 3.3, Eq. 3.5),
+// train/inference forward, full backward, Adam (Sec. 3.4), and the
+// preconditioners M_JU (Alg. 2) and M_VU (Eq. 3.4).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "../../include/unet.h"
+#include "helm_internal.cuh"
+#include "unet_api.h"
+#include "unet_internal.cuh"
+
+namespace helm {
+void set_error(const std::string& s);
+}
+using namespace helm;
+
+#define UCHECK(call)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+      return HELM_ECUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+#define UTRY(call)         \
+  do {                     \
+    int r_ = (call);       \
+    if (r_ < 0) return r_; \
+  } while (0)
+
+namespace {
+
+struct ConvL { std::string name; int kind; int k, cin, cout; size_t woff; };  // kind 0 down, 1 same, 2 up
+struct BnL { std::string name; int c; size_t goff; size_t soff; };
+
+// A device arena of float-aligned pieces.
+struct DevArena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  template <typename T> T* take(size_t n) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + n * sizeof(T);
+    return base ? (T*)(base + off) : nullptr;
+  }
+};
+
+}  // namespace
+
+struct unet_ctx {
+  unet_cfg cfg{};
+  int L = 0;
+  std::vector<ConvL> convs;
+  std::vector<BnL> bns;
+  size_t bias_off = 0, nparams = 0, nbn = 0;
+  float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr, *rstats = nullptr;
+  __nv_bfloat16* Wb = nullptr;
+  __nv_bfloat16* WTb = nullptr;                    // K-major weight copies (tensor-core path)
+  int* d_err = nullptr;                            // failure record of the tensor-core kernel
+  bool use_tc = true;
+  float *bn_scale = nullptr, *bn_shift = nullptr;
+  double *bn_mean = nullptr, *bn_var = nullptr;
+  int adam_t = 0;
+  unet_ctx* encoder = nullptr;
+  bool last_train = false;
+  // activation workspace for (B, ny, nx)
+  int B = 0, ny = 0, nx = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  __nv_bfloat16* x_in = nullptr;
+  std::vector<float*> zdown;                       // [l] raw down conv output
+  std::vector<__nv_bfloat16*> h0;                  // [l] after down BN + eLU
+  std::vector<std::vector<float*>> t1, sres;       // [l][r] raw ResNet convs (s includes the residual)
+  std::vector<std::vector<__nv_bfloat16*>> a1, hres;
+  std::vector<__nv_bfloat16*> cat;                 // [l] (1..L-1): [zn of up l+1 | skip h_l]
+  __nv_bfloat16* hL = nullptr;                     // coarsest output
+  std::vector<float*> zup;                         // [l] (2..L) raw up conv output at level l-1
+  std::vector<__nv_bfloat16*> uact, fact;          // eLU'd up-conv inputs (tensor-core path)
+  float* out = nullptr;                            // final output (FP32)
+  __nv_bfloat16* out_bf = nullptr;                 // BF16 copy (encoder feature f^(0))
+  // backward buffers
+  std::vector<float*> gU, gzup, gD, gzd, gfeat;
+  std::vector<std::vector<float*>> gS, gA1, gT1, gH2;
+  float* part = nullptr;                           // reduction partials
+  double* sums = nullptr;
+  int nblk = 64;
+  // preconditioner scratch
+  float *xin32 = nullptr, *scale = nullptr;
+  void* tmp_e = nullptr;
+  size_t tmp_e_bytes = 0;
+};
+
+namespace {
+
+int level_ch_in(const unet_ctx* n, int l) {  // channels of the down-conv source at level l-1
+  return l == 1 ? n->cfg.in_ch : n->cfg.widths[l - 2];
+}
+
+void build_layout(unet_ctx* n) {
+  const unet_cfg& c = n->cfg;
+  const int L = c.levels;
+  n->L = L;
+  size_t off = 0, soff = 0;
+  auto conv = [&](const std::string& nm, int kind, int k, int ci, int co) {
+    n->convs.push_back({nm, kind, k, ci, co, off});
+    off += (size_t)k * k * ci * co;
+  };
+  std::vector<std::pair<std::string, int>> bnl;
+  int cin = c.in_ch;
+  for (int l = 1; l <= L; ++l) {
+    const int w = c.widths[l - 1];
+    conv("down" + std::to_string(l), 0, 5, cin + c.context[l - 1], w);
+    bnl.push_back({"down" + std::to_string(l) + ".bn", w});
+    const int nres = l == L ? c.coarse_resnets : 1;
+    for (int r = 0; r < nres; ++r) {
+      std::string pre = "res" + std::to_string(l) + "." + std::to_string(r);
+      conv(pre + ".k1", 1, 3, w, w);
+      bnl.push_back({pre + ".bn1", w});
+      conv(pre + ".k2", 1, 3, w, w);
+      bnl.push_back({pre + ".bn2", w});
+    }
+    cin = w;
+  }
+  int ucin = c.widths[L - 1];
+  for (int l = L; l >= 2; --l) {
+    const int co = c.widths[l - 2];
+    conv("up" + std::to_string(l), 2, 5, ucin + c.context[l], co);
+    bnl.push_back({"up" + std::to_string(l) + ".bn", co});
+    ucin = 2 * co;
+  }
+  conv("up1", 2, 5, ucin + c.context[1], c.out_ch);
+  n->bias_off = off;
+  off += c.out_ch;
+  for (auto& b : bnl) {
+    n->bns.push_back({b.first, b.second, off, soff});
+    off += 2 * (size_t)b.second;
+    soff += b.second;
+  }
+  n->nparams = off;
+  n->nbn = soff;
+}
+
+const ConvL& conv_of(const unet_ctx* n, const std::string& nm) {
+  for (auto& c : n->convs)
+    if (c.name == nm) return c;
+  return n->convs[0];
+}
+const BnL& bn_of(const unet_ctx* n, const std::string& nm) {
+  for (auto& b : n->bns)
+    if (b.name == nm) return b;
+  return n->bns[0];
+}
+
+void free_ws(unet_ctx* n) {
+  if (n->ws) cudaFree(n->ws);
+  n->ws = nullptr;
+  n->ws_bytes = 0;
+  n->B = n->ny = n->nx = 0;
+}
+
+// Carve every activation and gradient buffer for (B, ny, nx); base == null measures.
+void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
+  const unet_cfg& c = n->cfg;
+  const int L = n->L;
+  auto M = [&](int l) { return (size_t)B * (ny >> l) * (nx >> l); };
+  const int* w = c.widths;
+  n->x_in = a.take<__nv_bfloat16>(M(0) * c.in_ch);
+  n->zdown.assign(L + 1, nullptr); n->h0.assign(L + 1, nullptr);
+  n->t1.assign(L + 1, {}); n->sres.assign(L + 1, {}); n->a1.assign(L + 1, {}); n->hres.assign(L + 1, {});
+  n->cat.assign(L + 1, nullptr); n->zup.assign(L + 1, nullptr);
+  n->gU.assign(L + 1, nullptr); n->gzup.assign(L + 1, nullptr); n->gD.assign(L + 1, nullptr);
+  n->gzd.assign(L + 1, nullptr); n->gfeat.assign(L + 1, nullptr);
+  n->gS.assign(L + 1, {}); n->gA1.assign(L + 1, {}); n->gT1.assign(L + 1, {}); n->gH2.assign(L + 1, {});
+  for (int l = 1; l <= L; ++l) {
+    const size_t m = M(l);
+    const int nres = l == L ? c.coarse_resnets : 1;
+    n->zdown[l] = a.take<float>(m * w[l - 1]);
+    n->h0[l] = a.take<__nv_bfloat16>(m * w[l - 1]);
+    for (int r = 0; r < nres; ++r) {
+      n->t1[l].push_back(a.take<float>(m * w[l - 1]));
+      n->sres[l].push_back(a.take<float>(m * w[l - 1]));
+      n->a1[l].push_back(a.take<__nv_bfloat16>(m * w[l - 1]));
+      n->hres[l].push_back(a.take<__nv_bfloat16>(m * w[l - 1]));
+      n->gS[l].push_back(a.take<float>(m * w[l - 1]));
+      n->gA1[l].push_back(a.take<float>(m * w[l - 1]));
+      n->gT1[l].push_back(a.take<float>(m * w[l - 1]));
+      n->gH2[l].push_back(a.take<float>(m * w[l - 1]));
+    }
+    if (l < L) n->cat[l] = a.take<__nv_bfloat16>(m * 2 * w[l - 1]);
+    if (l >= 2) {
+      n->zup[l] = a.take<float>(M(l - 1) * w[l - 2]);
+      n->gzup[l] = a.take<float>(M(l - 1) * w[l - 2]);
+    }
+    const int cu = (l == L) ? w[L - 1] : 2 * w[l - 1];
+    n->gU[l] = a.take<float>(m * (cu + c.context[l]));
+    n->gD[l] = a.take<float>(M(l - 1) * (level_ch_in(n, l) + c.context[l - 1]));
+    n->gzd[l] = a.take<float>(m * w[l - 1]);
+  }
+  for (int l = 0; l <= L; ++l)
+    if (c.context[l]) n->gfeat[l] = a.take<float>(M(l) * c.context[l]);
+  n->uact.assign(L + 1, nullptr);
+  n->fact.assign(L + 1, nullptr);
+  for (int l = 2; l <= L; ++l) {
+    const int cu = (l == L) ? w[L - 1] : 2 * w[l - 1];
+    n->uact[l] = a.take<__nv_bfloat16>(M(l) * cu);
+    if (c.context[l]) n->fact[l] = a.take<__nv_bfloat16>(M(l) * c.context[l]);
+  }
+  n->hL = a.take<__nv_bfloat16>(M(L) * w[L - 1]);
+  n->out = a.take<float>(M(0) * c.out_ch);
+  n->out_bf = a.take<__nv_bfloat16>(M(0) * c.out_ch);
+  n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
+  n->sums = a.take<double>(2 * 512);
+  n->xin32 = a.take<float>(M(0) * c.in_ch);
+  n->scale = a.take<float>((size_t)B + 8);
+}
+
+int ensure_ws(unet_ctx* n, int B, int ny, int nx) {
+  if (n->ws && n->B == B && n->ny == ny && n->nx == nx) return HELM_OK;
+  free_ws(n);
+  DevArena m;
+  carve(n, m, B, ny, nx);
+  const size_t bytes = m.used + 1024;
+  if (cudaMalloc(&n->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("U-Net workspace allocation failed (" + std::to_string(bytes) + " bytes)");
+    return HELM_ENOMEM;
+  }
+  n->ws_bytes = bytes;
+  DevArena a{(char*)n->ws, bytes, 0};
+  carve(n, a, B, ny, nx);
+  n->B = B; n->ny = ny; n->nx = nx;
+  UCHECK(cudaMemset(n->ws, 0, bytes));
+  return HELM_OK;
+}
+
+// A source tensor for a convolution input.
+struct Src { const void* p; int c, ld; bool bcast; };
+
+// Context feature f^(l) of the attached encoder (BF16 source), or empty.
+Src feat_of(const unet_ctx* n, int l) {
+  const unet_ctx* e = n->encoder;
+  if (!e || !n->cfg.context[l]) return {nullptr, 0, 0, false};
+  const bool bc = (e->B == 1 && n->B > 1);
+  const int L = e->L;
+  if (l == 0) return {e->out_bf, e->cfg.out_ch, e->cfg.out_ch, bc};
+  if (l == L) return {e->hL, e->cfg.widths[L - 1], e->cfg.widths[L - 1], bc};
+  return {e->cat[l], e->cfg.widths[l - 1], 2 * e->cfg.widths[l - 1], bc};
+}
+
+ConvArgs conv_args(const unet_ctx* n, const ConvL& cl, Src a, Src b, bool act, int Hi, int Wi, float* out, int ldo) {
+  ConvArgs c{};
+  c.in0 = a.p; c.c0 = a.c; c.ld0 = a.ld;
+  c.in1 = b.p; c.c1 = b.p ? b.c : 0; c.ld1 = b.ld; c.bcast1 = b.bcast ? 1 : 0;
+  c.in_f32 = 0; c.in_act = act ? 1 : 0;
+  c.B = n->B; c.Hi = Hi; c.Wi = Wi;
+  c.k = cl.k;
+  if (cl.kind == 0) { c.stride = 2; c.pad = 2; c.transposed = 0; c.Ho = Hi / 2; c.Wo = Wi / 2; }
+  else if (cl.kind == 1) { c.stride = 1; c.pad = 1; c.transposed = 0; c.Ho = Hi; c.Wo = Wi; }
+  else { c.stride = 2; c.pad = 2; c.transposed = 1; c.Ho = 2 * Hi; c.Wo = 2 * Wi; }
+  c.Cout = cl.cout;
+  c.W = n->Wb + cl.woff;
+  c.wst = (long long)cl.cin * cl.cout; c.wsk = cl.cout; c.wsn = 1;
+  c.WT = n->WTb + cl.woff;
+  c.out = out; c.ldo = ldo;
+  return c;
+}
+
+void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (n->use_tc && conv_tc_eligible(a)) conv_forward_tc(a, n->d_err, s);
+  else conv_forward(a, s);
+}
+
+// Data gradient of a convolution: the adjoint geometry with transposed weights.
+ConvArgs dgrad_args(const unet_ctx* n, const ConvL& cl, const float* g, int ldg, int Hg, int Wg, float* out, int ldo) {
+  ConvArgs c{};
+  c.in0 = g; c.c0 = cl.cout; c.ld0 = ldg; c.in1 = nullptr; c.c1 = 0;
+  c.in_f32 = 1; c.in_act = 0;
+  c.B = n->B; c.Hi = Hg; c.Wi = Wg; c.k = cl.k;
+  if (cl.kind == 0) { c.stride = 2; c.pad = 2; c.transposed = 1; c.Ho = 2 * Hg; c.Wo = 2 * Wg; }
+  else if (cl.kind == 1) { c.stride = 1; c.pad = 1; c.transposed = 1; c.Ho = Hg; c.Wo = Wg; }
+  else { c.stride = 2; c.pad = 2; c.transposed = 0; c.Ho = Hg / 2; c.Wo = Wg / 2; }
+  c.Cout = cl.cin;
+  c.W = n->Wb + cl.woff;
+  c.wst = (long long)cl.cin * cl.cout; c.wsk = 1; c.wsn = cl.cout;
+  c.out = out; c.ldo = ldo;
+  return c;
+}
+
+// BatchNorm (train: batch statistics, running update; eval: running statistics),
+// then optional eLU, into a BF16 slice.
+void run_bn(unet_ctx* n, const std::string& nm, const float* z, int ldz, int M, bool act, __nv_bfloat16* y, int ldy,
+            bool train, cudaStream_t s) {
+  const BnL& b = bn_of(n, nm);
+  float* gamma = n->P + b.goff;
+  float* beta = gamma + b.c;
+  float* sc = n->bn_scale + b.soff;
+  float* sh = n->bn_shift + b.soff;
+  float* rm = n->rstats + b.soff;
+  float* rv = n->rstats + n->nbn + b.soff;
+  if (train) {
+    bn_batch_stats(z, ldz, b.c, M, n->bn_mean + b.soff, n->bn_var + b.soff, n->part, n->nblk, s);
+    bn_coeffs(n->bn_mean + b.soff, n->bn_var + b.soff, gamma, beta, b.c, sc, sh, rm, rv, true, M, s);
+  } else {
+    bn_coeffs_eval(rm, rv, gamma, beta, b.c, sc, sh, s);
+  }
+  bn_act(z, ldz, b.c, M, sc, sh, act, y, ldy, s);
+}
+
+void run_bn_bwd(unet_ctx* n, const std::string& nm, const float* g, int ldg, const float* z, int ldz, int M, bool act,
+                float* gz, int ldo, cudaStream_t s) {
+  const BnL& b = bn_of(n, nm);
+  bn_backward(g, ldg, z, ldz, b.c, M, n->bn_mean + b.soff, n->bn_var + b.soff, n->bn_scale + b.soff,
+              n->bn_shift + b.soff, act, n->P + b.goff, n->G + b.goff, n->G + b.goff + b.c, n->part, n->nblk,
+              n->sums, gz, ldo, s);
+}
+
+int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
+  const unet_cfg& c = n->cfg;
+  const int L = n->L;
+  const int* w = c.widths;
+  auto hw = [&](int l, int& H, int& W) { H = n->ny >> l; W = n->nx >> l; };
+  auto M = [&](int l) { return n->B * (n->ny >> l) * (n->nx >> l); };
+  for (int l = 1; l <= L; ++l) {
+    int H, W;
+    hw(l - 1, H, W);
+    Src src = l == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
+    const ConvL& dl = conv_of(n, "down" + std::to_string(l));
+    ConvArgs a = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, n->zdown[l], w[l - 1]);
+    run_conv(n, a, s);
+    run_bn(n, "down" + std::to_string(l) + ".bn", n->zdown[l], w[l - 1], M(l), true, n->h0[l], w[l - 1], train, s);
+    const __nv_bfloat16* h = n->h0[l];
+    int ldh = w[l - 1];
+    const int nres = l == L ? c.coarse_resnets : 1;
+    int Hl, Wl;
+    hw(l, Hl, Wl);
+    for (int r = 0; r < nres; ++r) {
+      const std::string pre = "res" + std::to_string(l) + "." + std::to_string(r);
+      ConvArgs k1 = conv_args(n, conv_of(n, pre + ".k1"), Src{h, w[l - 1], ldh, false}, Src{nullptr, 0, 0, false},
+                              false, Hl, Wl, n->t1[l][r], w[l - 1]);
+      run_conv(n, k1, s);
+      run_bn(n, pre + ".bn1", n->t1[l][r], w[l - 1], M(l), true, n->a1[l][r], w[l - 1], train, s);
+      ConvArgs k2 = conv_args(n, conv_of(n, pre + ".k2"), Src{n->a1[l][r], w[l - 1], w[l - 1], false},
+                              Src{nullptr, 0, 0, false}, false, Hl, Wl, n->sres[l][r], w[l - 1]);
+      k2.res = h; k2.ldr = ldh;
+      run_conv(n, k2, s);
+      __nv_bfloat16* dst;
+      int ldd;
+      if (r == nres - 1 && l < L) { dst = n->cat[l] + w[l - 1]; ldd = 2 * w[l - 1]; }
+      else if (r == nres - 1) { dst = n->hL; ldd = w[L - 1]; }
+      else { dst = n->hres[l][r]; ldd = w[l - 1]; }
+      run_bn(n, pre + ".bn2", n->sres[l][r], w[l - 1], M(l), true, dst, ldd, train, s);
+      h = dst;
+      ldh = ldd;
+    }
+  }
+  Src u{n->hL, w[L - 1], w[L - 1], false};
+  for (int l = L; l >= 2; --l) {
+    int H, W;
+    hw(l, H, W);
+    const ConvL& ul = conv_of(n, "up" + std::to_string(l));
+    Src f = feat_of(n, l);
+    ConvArgs a = conv_args(n, ul, u, f, true, H, W, n->zup[l], w[l - 2]);
+    if (n->use_tc) {
+      // the tensor-core gather copies raw bytes: materialise eLU(u) (and eLU(f)) first
+      ConvArgs t = a;
+      t.in_act = 0;
+      if (conv_tc_eligible(t)) {
+        elu_copy_bf16((const __nv_bfloat16*)u.p, u.ld, u.c, (size_t)M(l), n->uact[l], u.c, s);
+        t.in0 = n->uact[l]; t.ld0 = u.c;
+        if (f.p) {
+          const size_t fm = f.bcast ? (size_t)H * W : (size_t)M(l);
+          elu_copy_bf16((const __nv_bfloat16*)f.p, f.ld, f.c, fm, n->fact[l], f.c, s);
+          t.in1 = n->fact[l]; t.ld1 = f.c;
+        }
+        a = t;
+      }
+    }
+    run_conv(n, a, s);
+    run_bn(n, "up" + std::to_string(l) + ".bn", n->zup[l], w[l - 2], M(l - 1), false, n->cat[l - 1], 2 * w[l - 2],
+           train, s);
+    u = Src{n->cat[l - 1], 2 * w[l - 2], 2 * w[l - 2], false};
+  }
+  {
+    int H, W;
+    hw(1, H, W);
+    ConvArgs a = conv_args(n, conv_of(n, "up1"), u, feat_of(n, 1), true, H, W, n->out, c.out_ch);
+    a.bias = n->P + n->bias_off;
+    conv_forward(a, s);
+    f32_to_bf16(n->out, n->out_bf, (size_t)M(0) * c.out_ch, s);
+  }
+  n->last_train = train;
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
+// Backward of the last train forward.  gout: d/d out (ld out_ch).  g_own: gradients
+// arriving on this net's own features (encoder), else null.  gx: input gradient or null.
+int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx, cudaStream_t s) {
+  const unet_cfg& c = n->cfg;
+  const int L = n->L;
+  const int* w = c.widths;
+  auto hw = [&](int l, int& H, int& W) { H = n->ny >> l; W = n->nx >> l; };
+  auto M = [&](int l) { return n->B * (n->ny >> l) * (n->nx >> l); };
+  for (int l = 0; l <= L; ++l)
+    if (n->gfeat[l]) UCHECK(cudaMemsetAsync(n->gfeat[l], 0, (size_t)M(l) * c.context[l] * 4, s));
+  // final layer
+  chan_sum_add(gout, c.out_ch, c.out_ch, M(0), n->G + n->bias_off, n->part, n->nblk, s);
+  {
+    const ConvL& cl = conv_of(n, "up1");
+    int H, W;
+    hw(1, H, W);
+    Src u = L > 1 ? Src{n->cat[1], 2 * w[0], 2 * w[0], false} : Src{n->hL, w[0], w[0], false};
+    ConvArgs fa = conv_args(n, cl, u, feat_of(n, 1), true, H, W, nullptr, 0);
+    conv_wgrad(fa, gout, c.out_ch, n->G + cl.woff, s);
+    const int cu = u.c, ldU = cu + c.context[1];
+    conv_forward(dgrad_args(n, cl, gout, c.out_ch, n->ny, n->nx, n->gU[1], ldU), s);
+    elu_backward_inplace(n->gU[1], ldU, (const __nv_bfloat16*)u.p, u.ld, cu, M(1), 0, s);
+    if (c.context[1]) {
+      Src f = feat_of(n, 1);
+      elu_backward_inplace(n->gU[1] + cu, ldU, (const __nv_bfloat16*)f.p, f.ld, f.c, M(1),
+                           f.bcast ? (size_t)H * W : 0, s);
+      add_slice(n->gfeat[1], c.context[1], n->gU[1] + cu, ldU, c.context[1], M(1), s);
+    }
+  }
+  // up levels 2..L
+  for (int l = 2; l <= L; ++l) {
+    const int cz = w[l - 2];
+    const int ldin = 2 * cz + c.context[l - 1];   // ld of gU[l-1]
+    float* gzn = n->gU[l - 1];
+    if (g_own && g_own[l - 1]) add_slice(gzn, ldin, g_own[l - 1], cz, cz, M(l - 1), s);
+    run_bn_bwd(n, "up" + std::to_string(l) + ".bn", gzn, ldin, n->zup[l], cz, M(l - 1), false, n->gzup[l], cz, s);
+    const ConvL& cl = conv_of(n, "up" + std::to_string(l));
+    int H, W;
+    hw(l, H, W);
+    Src u = (l == L) ? Src{n->hL, w[L - 1], w[L - 1], false} : Src{n->cat[l], 2 * w[l - 1], 2 * w[l - 1], false};
+    ConvArgs fa = conv_args(n, cl, u, feat_of(n, l), true, H, W, nullptr, 0);
+    conv_wgrad(fa, n->gzup[l], cz, n->G + cl.woff, s);
+    const int ldU = u.c + c.context[l];
+    int Hg, Wg;
+    hw(l - 1, Hg, Wg);
+    conv_forward(dgrad_args(n, cl, n->gzup[l], cz, Hg, Wg, n->gU[l], ldU), s);
+    elu_backward_inplace(n->gU[l], ldU, (const __nv_bfloat16*)u.p, u.ld, u.c, M(l), 0, s);
+    if (c.context[l]) {
+      Src f = feat_of(n, l);
+      elu_backward_inplace(n->gU[l] + u.c, ldU, (const __nv_bfloat16*)f.p, f.ld, f.c, M(l), f.bcast ? (size_t)H * W : 0,
+                           s);
+      add_slice(n->gfeat[l], c.context[l], n->gU[l] + u.c, ldU, c.context[l], M(l), s);
+    }
+  }
+  // down path
+  float* gh = n->gU[L];
+  int ldgh = w[L - 1] + c.context[L];
+  if (g_own && g_own[L]) add_slice(gh, ldgh, g_own[L], w[L - 1], w[L - 1], M(L), s);
+  for (int l = L; l >= 1; --l) {
+    const int cw = w[l - 1];
+    if (l < L) {
+      // gradient on h_l = skip part of gU[l] + first cw channels of the down l+1 data gradient
+      const int ldU = 2 * cw + c.context[l];
+      gh = n->gU[l] + cw;
+      ldgh = ldU;
+      add_slice(gh, ldgh, n->gD[l + 1], cw + c.context[l], cw, M(l), s);
+    }
+    const int nres = l == L ? c.coarse_resnets : 1;
+    int Hl, Wl;
+    hw(l, Hl, Wl);
+    for (int r = nres - 1; r >= 0; --r) {
+      const std::string pre = "res" + std::to_string(l) + "." + std::to_string(r);
+      const __nv_bfloat16* hin = r == 0 ? n->h0[l] : n->hres[l][r - 1];
+      run_bn_bwd(n, pre + ".bn2", gh, ldgh, n->sres[l][r], cw, M(l), true, n->gS[l][r], cw, s);
+      const ConvL& k2 = conv_of(n, pre + ".k2");
+      ConvArgs fa2 = conv_args(n, k2, Src{n->a1[l][r], cw, cw, false}, Src{nullptr, 0, 0, false}, false, Hl, Wl, nullptr, 0);
+      conv_wgrad(fa2, n->gS[l][r], cw, n->G + k2.woff, s);
+      conv_forward(dgrad_args(n, k2, n->gS[l][r], cw, Hl, Wl, n->gA1[l][r], cw), s);
+      run_bn_bwd(n, pre + ".bn1", n->gA1[l][r], cw, n->t1[l][r], cw, M(l), true, n->gT1[l][r], cw, s);
+      const ConvL& k1 = conv_of(n, pre + ".k1");
+      ConvArgs fa1 = conv_args(n, k1, Src{hin, cw, cw, false}, Src{nullptr, 0, 0, false}, false, Hl, Wl, nullptr, 0);
+      conv_wgrad(fa1, n->gT1[l][r], cw, n->G + k1.woff, s);
+      conv_forward(dgrad_args(n, k1, n->gT1[l][r], cw, Hl, Wl, n->gH2[l][r], cw), s);
+      add_slice(n->gH2[l][r], cw, n->gS[l][r], cw, cw, M(l), s);   // identity branch
+      gh = n->gH2[l][r];
+      ldgh = cw;
+    }
+    run_bn_bwd(n, "down" + std::to_string(l) + ".bn", gh, ldgh, n->zdown[l], cw, M(l), true, n->gzd[l], cw, s);
+    const ConvL& dl = conv_of(n, "down" + std::to_string(l));
+    int H, W;
+    hw(l - 1, H, W);
+    Src src = l == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
+    ConvArgs fa = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, nullptr, 0);
+    conv_wgrad(fa, n->gzd[l], cw, n->G + dl.woff, s);
+    const int ldD = src.c + c.context[l - 1];
+    conv_forward(dgrad_args(n, dl, n->gzd[l], cw, Hl, Wl, n->gD[l], ldD), s);
+    if (c.context[l - 1]) add_slice(n->gfeat[l - 1], c.context[l - 1], n->gD[l] + src.c, ldD, c.context[l - 1], M(l - 1), s);
+    if (l == 1 && gx) UCHECK(cudaMemcpy2DAsync(gx, c.in_ch * 4, n->gD[1], ldD * 4, c.in_ch * 4, M(0),
+                                                cudaMemcpyDeviceToDevice, s));
+  }
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
+// The context feature gradients of a solver, reduced to the encoder's batch, then
+// the encoder's backward.
+int backward_encoder(unet_ctx* solver, cudaStream_t s) {
+  unet_ctx* e = solver->encoder;
+  if (!e) return HELM_OK;
+  if (!e->last_train) { set_error("encoder's last forward was not train-mode"); return HELM_EINVAL; }
+  const int L = e->L;
+  std::vector<float*> g_own(L + 1, nullptr);
+  // reuse the encoder's gfeat-free scratch: zdown-sized gradient buffers are not needed; use gU/gD of the
+  // encoder? They are overwritten by its own backward.  Reduce into dedicated buffers instead.
+  static_assert(sizeof(float) == 4, "");
+  std::vector<float*> bufs;
+  for (int l = 0; l <= L; ++l) {
+    const size_t P = (size_t)(e->ny >> l) * (e->nx >> l);
+    const int C = solver->cfg.context[l];
+    float* d = nullptr;
+    UCHECK(cudaMallocAsync(&d, P * e->B * C * 4, s));
+    bufs.push_back(d);
+    if (e->B == solver->B) UCHECK(cudaMemcpyAsync(d, solver->gfeat[l], P * e->B * C * 4, cudaMemcpyDeviceToDevice, s));
+    else batch_sum(solver->gfeat[l], C, solver->B, P, C, d, C, false, s);
+    g_own[l] = d;
+  }
+  // f^(0) is the encoder output: its gradient is the encoder's gout
+  int r = backward_impl(e, g_own[0], g_own.data(), nullptr, s);
+  for (float* d : bufs) cudaFreeAsync(d, s);
+  return r;
+}
+
+void refresh_bf16(unet_ctx* n, cudaStream_t s) {
+  f32_to_bf16(n->P, n->Wb, n->nparams, s);
+  for (auto& cl : n->convs) weights_kmajor(n->P + cl.woff, n->WTb + cl.woff, cl.k * cl.k, cl.cin, cl.cout, s);
+}
+
+}  // namespace
+
+// ===========================================================================
+// helm-side bridge: U-Net preconditioners inside FGMRES
+// ===========================================================================
+namespace helm {
+// defined in solver.cu
+int vcycle_public(helm_ctx* c, const void* f, const void* v_in, void* out, int nrhs, int real_bytes, const int* gate,
+                  cudaStream_t s);
+int jacobi_public(helm_ctx* c, int op, const void* f, const void* x_in, void* x_out, int nrhs, int real_bytes,
+                  const int* gate, cudaStream_t s);
+int residual_public(helm_ctx* c, int op, const void* b, const void* x, void* r, int nrhs, int real_bytes,
+                    const int* gate, cudaStream_t s);
+void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double* gmax, const float** k2f,
+                   const float** gam);
+void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs);
+}  // namespace helm
+
+// e = U-Net(r) (inference), with the network input built on the fly.
+static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool add, int nrhs, int real_bytes,
+                      const int* gate, cudaStream_t s) {
+  int nx, ny, abc_w;
+  double h, gmax;
+  const float *k2f, *gam;
+  helm_geometry(hc, &nx, &ny, &h, &abc_w, &gmax, &k2f, &gam);
+  const int div = 1 << n->L;
+  if (nx % div || ny % div) { set_error("grid not divisible by 2^levels of the U-Net"); return HELM_EINVAL; }
+  if (n->cfg.in_ch != 4 || n->cfg.out_ch != 2) { set_error("preconditioner net needs 4 inputs, 2 outputs"); return HELM_EINVAL; }
+  if (n->ws == nullptr || n->B != nrhs || n->ny != ny || n->nx != nx) {
+    cudaStreamCaptureStatus cs;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs != cudaStreamCaptureStatusNone) { set_error("U-Net workspace not prepared before capture"); return HELM_EINVAL; }
+    UTRY(ensure_ws(n, nrhs, ny, nx));
+  }
+  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, 4, n->scale, gate, s);
+  UTRY(forward_impl(n, false, s));
+  write_output(n->out, real_bytes == 8, nrhs, ny, nx, n->scale, e, add, gate, s);
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
+int unet_precond_impl(helm_ctx* hc, void* netp, int kind, const void* v, void* z, int nrhs, int real_bytes,
+                      const int* gate, cudaStream_t s) {
+  unet_ctx* n = (unet_ctx*)netp;
+  if (!n) { set_error("null net"); return HELM_EINVAL; }
+  if (n->cfg.context[0] && !n->encoder) { set_error("solver net needs an attached, encoded encoder"); return HELM_EINVAL; }
+  if (kind == HELM_PREC_VU) {
+    // Eq. 3.4: e = V-cycle(e0 = U-Net(r), r)
+    void* e0 = helm_scratch(hc, real_bytes, 0, nrhs);
+    if (!e0) return HELM_ENOMEM;
+    UTRY(unet_apply(hc, n, v, e0, false, nrhs, real_bytes, gate, s));
+    return vcycle_public(hc, v, e0, z, nrhs, real_bytes, gate, s);
+  }
+  if (kind == HELM_PREC_JU) {
+    // Alg. 2: e1 = Jacobi(0, r); e2 = e1 + U-Net(r - A e1); e = Jacobi(e2, r)   (Jacobi on A)
+    void* e1 = helm_scratch(hc, real_bytes, 0, nrhs);
+    void* rr = helm_scratch(hc, real_bytes, 1, nrhs);
+    if (!e1 || !rr) return HELM_ENOMEM;
+    UTRY(jacobi_public(hc, HELM_OP_A, v, nullptr, e1, nrhs, real_bytes, gate, s));
+    UTRY(residual_public(hc, HELM_OP_A, v, e1, rr, nrhs, real_bytes, gate, s));
+    UTRY(unet_apply(hc, n, rr, e1, true, nrhs, real_bytes, gate, s));
+    return jacobi_public(hc, HELM_OP_A, v, e1, z, nrhs, real_bytes, gate, s);
+  }
+  set_error("unknown U-Net preconditioner kind");
+  return HELM_EINVAL;
+}
+
+void unet_release_ctx(helm_ctx*) {}
+
+int unet_prepare_impl(helm_ctx* hc, void* netp, int nrhs) {
+  unet_ctx* n = (unet_ctx*)netp;
+  if (!n) { set_error("null net"); return HELM_EINVAL; }
+  int nx, ny, abc_w;
+  double h, gmax;
+  const float *k2f, *gam;
+  helm_geometry(hc, &nx, &ny, &h, &abc_w, &gmax, &k2f, &gam);
+  return ensure_ws(n, nrhs, ny, nx);
+}
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int unet_cfg_default(unet_cfg* cfg, int kind) {
+  if (!cfg) { set_error("null cfg"); return HELM_EINVAL; }
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->levels = 4;
+  cfg->coarse_resnets = 3;
+  const int wd[4] = {32, 64, 128, 256};
+  for (int i = 0; i < 4; ++i) cfg->widths[i] = wd[i];
+  if (kind == UNET_ENCODER) { cfg->in_ch = 2; cfg->out_ch = 4; }
+  else { cfg->in_ch = 4; cfg->out_ch = 2; }
+  if (kind == UNET_SOLVER) {
+    cfg->context[0] = 4;
+    for (int l = 1; l < 4; ++l) cfg->context[l] = wd[l - 1];
+    cfg->context[4] = wd[3];
+  }
+  return HELM_OK;
+}
+
+int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
+  if (!cfg || !out) { set_error("null argument"); return HELM_EINVAL; }
+  if (cfg->levels < 1 || cfg->levels > 8 || cfg->in_ch < 1 || cfg->out_ch < 1 || cfg->coarse_resnets < 1) {
+    set_error("bad U-Net configuration");
+    return HELM_EINVAL;
+  }
+  for (int l = 0; l < cfg->levels; ++l)
+    if (cfg->widths[l] < 1 || cfg->widths[l] > 512) { set_error("bad width"); return HELM_EINVAL; }
+  unet_ctx* n = new unet_ctx();
+  n->cfg = *cfg;
+  build_layout(n);
+  const size_t np = n->nparams, nb = n->nbn;
+  UCHECK(cudaMalloc(&n->P, np * 4));
+  UCHECK(cudaMalloc(&n->G, np * 4));
+  UCHECK(cudaMalloc(&n->M1, np * 4));
+  UCHECK(cudaMalloc(&n->M2, np * 4));
+  UCHECK(cudaMalloc(&n->Wb, np * 2));
+  UCHECK(cudaMalloc(&n->WTb, np * 2));
+  UCHECK(cudaMalloc(&n->d_err, sizeof(int)));
+  UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
+  n->use_tc = !(cfg->flags & UNET_FLAG_SIMT);
+  UCHECK(cudaMalloc(&n->rstats, 2 * nb * 4));
+  UCHECK(cudaMalloc(&n->bn_scale, nb * 4));
+  UCHECK(cudaMalloc(&n->bn_shift, nb * 4));
+  UCHECK(cudaMalloc(&n->bn_mean, nb * 8));
+  UCHECK(cudaMalloc(&n->bn_var, nb * 8));
+  UCHECK(cudaMemset(n->G, 0, np * 4));
+  UCHECK(cudaMemset(n->M1, 0, np * 4));
+  UCHECK(cudaMemset(n->M2, 0, np * 4));
+  // He-normal weights from SplitMix64 + Box-Muller (layer i uses stream seed*1000+i,
+  // as the oracle's init_params), BN gamma 1 / beta 0, running mean 0 / var 1.
+  std::vector<float> hp(np, 0.f);
+  for (size_t i = 0; i < n->convs.size(); ++i) {
+    const ConvL& cl = n->convs[i];
+    const size_t cnt = (size_t)cl.k * cl.k * cl.cin * cl.cout;
+    const double stdv = std::sqrt(2.0 / (cl.k * cl.k * cl.cin));
+    const unsigned long long st = seed * 1000ull + i;
+    auto sm = [&](unsigned long long idx) {
+      unsigned long long z = st + (idx + 1ull) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t q = 0; q < cnt; q += 2) {
+      const double u1 = sm(q), u2 = sm(q + 1);
+      const double rad = std::sqrt(-2.0 * std::log(u1));
+      hp[cl.woff + q] = (float)(rad * std::cos(2.0 * M_PI * u2) * stdv);
+      if (q + 1 < cnt) hp[cl.woff + q + 1] = (float)(rad * std::sin(2.0 * M_PI * u2) * stdv);
+    }
+  }
+  for (auto& b : n->bns)
+    for (int c = 0; c < b.c; ++c) hp[b.goff + c] = 1.f;
+  UCHECK(cudaMemcpy(n->P, hp.data(), np * 4, cudaMemcpyHostToDevice));
+  std::vector<float> rs(2 * nb, 0.f);
+  std::fill(rs.begin() + nb, rs.end(), 1.f);
+  UCHECK(cudaMemcpy(n->rstats, rs.data(), 2 * nb * 4, cudaMemcpyHostToDevice));
+  refresh_bf16(n, 0);
+  UCHECK(cudaDeviceSynchronize());
+  *out = n;
+  return HELM_OK;
+}
+
+void unet_destroy(unet_t n) {
+  if (!n) return;
+  cudaDeviceSynchronize();
+  free_ws(n);
+  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb,
+                  (void*)n->d_err, (void*)n->rstats,
+                  (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, n->tmp_e})
+    if (p) cudaFree(p);
+  delete n;
+}
+
+int unet_sizes(unet_t n, long long* np, long long* nb) {
+  if (!n) { set_error("null net"); return HELM_EINVAL; }
+  if (np) *np = (long long)n->nparams;
+  if (nb) *nb = 2 * (long long)n->nbn;
+  return HELM_OK;
+}
+
+int unet_set_params(unet_t n, const float* host, long long cnt) {
+  if (!n || !host || cnt != (long long)n->nparams) { set_error("bad parameter vector"); return HELM_EINVAL; }
+  UCHECK(cudaMemcpy(n->P, host, cnt * 4, cudaMemcpyHostToDevice));
+  refresh_bf16(n, 0);
+  UCHECK(cudaDeviceSynchronize());
+  return HELM_OK;
+}
+int unet_get_params(unet_t n, float* host, long long cnt) {
+  if (!n || !host || cnt != (long long)n->nparams) { set_error("bad parameter vector"); return HELM_EINVAL; }
+  UCHECK(cudaMemcpy(host, n->P, cnt * 4, cudaMemcpyDeviceToHost));
+  return HELM_OK;
+}
+int unet_set_bn_stats(unet_t n, const float* host, long long cnt) {
+  if (!n || !host || cnt != 2 * (long long)n->nbn) { set_error("bad BN vector"); return HELM_EINVAL; }
+  UCHECK(cudaMemcpy(n->rstats, host, cnt * 4, cudaMemcpyHostToDevice));
+  return HELM_OK;
+}
+int unet_get_bn_stats(unet_t n, float* host, long long cnt) {
+  if (!n || !host || cnt != 2 * (long long)n->nbn) { set_error("bad BN vector"); return HELM_EINVAL; }
+  UCHECK(cudaMemcpy(host, n->rstats, cnt * 4, cudaMemcpyDeviceToHost));
+  return HELM_OK;
+}
+int unet_status(unet_t n, int* failed) {
+  if (!n || !failed) { set_error("bad arguments"); return HELM_EINVAL; }
+  UCHECK(cudaDeviceSynchronize());
+  UCHECK(cudaMemcpy(failed, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
+  return HELM_OK;
+}
+
+int unet_get_grads(unet_t n, float* host, long long cnt) {
+  if (!n || !host || cnt != (long long)n->nparams) { set_error("bad gradient vector"); return HELM_EINVAL; }
+  UCHECK(cudaMemcpy(host, n->G, cnt * 4, cudaMemcpyDeviceToHost));
+  return HELM_OK;
+}
+int unet_zero_grad(unet_t n, helm_stream_t stream) {
+  if (!n) { set_error("null net"); return HELM_EINVAL; }
+  UCHECK(cudaMemsetAsync(n->G, 0, n->nparams * 4, (cudaStream_t)stream));
+  if (n->encoder) UCHECK(cudaMemsetAsync(n->encoder->G, 0, n->encoder->nparams * 4, (cudaStream_t)stream));
+  return HELM_OK;
+}
+
+int unet_forward(unet_t n, const float* x, float* out, int B, int ny, int nx, int train, helm_stream_t stream) {
+  if (!n || !x || B < 1) { set_error("bad arguments"); return HELM_EINVAL; }
+  const int div = 1 << n->L;
+  if (ny % div || nx % div || ny <= 0 || nx <= 0) { set_error("ny, nx must be positive multiples of 2^levels"); return HELM_EINVAL; }
+  if (n->cfg.context[0]) {
+    if (!n->encoder || !n->encoder->ws) { set_error("solver net needs an attached encoder that has run"); return HELM_EINVAL; }
+    if (n->encoder->ny != ny || n->encoder->nx != nx || (n->encoder->B != 1 && n->encoder->B != B)) {
+      set_error("encoder features do not match the solver input");
+      return HELM_EINVAL;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  UTRY(ensure_ws(n, B, ny, nx));
+  to_bf16_slice(x, n->cfg.in_ch, n->x_in, n->cfg.in_ch, n->cfg.in_ch, B * ny * nx, s);
+  UTRY(forward_impl(n, train != 0, s));
+  if (out) UCHECK(cudaMemcpyAsync(out, n->out, (size_t)B * ny * nx * n->cfg.out_ch * 4, cudaMemcpyDeviceToDevice, s));
+  return HELM_OK;
+}
+
+int unet_backward(unet_t n, const float* gout, float* gx, helm_stream_t stream) {
+  if (!n || !gout) { set_error("bad arguments"); return HELM_EINVAL; }
+  if (!n->last_train) { set_error("backward needs a train-mode forward first"); return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  UTRY(backward_impl(n, gout, nullptr, gx, s));
+  if (n->encoder) UTRY(backward_encoder(n, s));
+  return HELM_OK;
+}
+
+int unet_mse(const float* out, const float* target, long long cnt, int B, float* gout, float* loss_dev,
+             helm_stream_t stream) {
+  if (!out || !target || !gout || !loss_dev || cnt <= 0 || B < 1) { set_error("bad arguments"); return HELM_EINVAL; }
+  static float* part = nullptr;
+  if (!part) UCHECK(cudaMalloc(&part, 256 * 4));
+  mse_loss(out, target, (size_t)cnt, B, gout, part, loss_dev, (cudaStream_t)stream);
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
+int unet_adam_step(unet_t n, float lr, float b1, float b2, float eps, helm_stream_t stream) {
+  if (!n) { set_error("null net"); return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (unet_ctx* m : {n, n->encoder}) {
+    if (!m) continue;
+    m->adam_t += 1;
+    adam_update(m->P, m->G, m->M1, m->M2, m->nparams, lr, b1, b2, eps, m->adam_t, s);
+    refresh_bf16(m, s);
+  }
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
+int unet_attach_encoder(unet_t solver, unet_t encoder) {
+  if (!solver) { set_error("null solver"); return HELM_EINVAL; }
+  if (encoder) {
+    for (int l = 0; l <= solver->L; ++l) {
+      int need = solver->cfg.context[l], have;
+      if (l == 0) have = encoder->cfg.out_ch;
+      else if (l == encoder->L) have = encoder->cfg.widths[l - 1];
+      else have = encoder->cfg.widths[l - 1];
+      if (encoder->L != solver->L || need != have) { set_error("encoder features do not match solver context"); return HELM_EINVAL; }
+    }
+  }
+  solver->encoder = encoder;
+  return HELM_OK;
+}
+
+int unet_encode(unet_t solver, helm_t h, int train, helm_stream_t stream) {
+  if (!solver || !solver->encoder || !h) { set_error("solver with an attached encoder and a handle needed"); return HELM_EINVAL; }
+  unet_ctx* e = solver->encoder;
+  int nx, ny, abc_w;
+  double hh, gmax;
+  const float *k2f, *gam;
+  helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  if (e->cfg.in_ch != 2) { set_error("encoder must take 2 inputs (kappa^2, gamma)"); return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  UTRY(ensure_ws(e, 1, ny, nx));
+  float* med = e->xin32;  // [ny*nx][2] float32 staging
+  UCHECK(cudaMemcpy2DAsync(med, 8, k2f, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
+  UCHECK(cudaMemcpy2DAsync(med + 1, 8, gam, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
+  to_bf16_slice(med, 2, e->x_in, 2, 2, nx * ny, s);
+  return forward_impl(e, train != 0, s);
+}
+
+int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int count, int nmix, const int* idx,
+                    const double* coef, float* x, float* target, helm_stream_t stream) {
+  if (!h || !r || !e || !idx || !coef || !x || !target || count < 1 || nmix < 1 || npairs < 1) {
+    set_error("bad arguments");
+    return HELM_EINVAL;
+  }
+  for (long long q = 0; q < (long long)count * nmix; ++q)
+    if (idx[q] < 0 || idx[q] >= npairs) { set_error("pair index out of range"); return HELM_EINVAL; }
+  int nx, ny, abc_w;
+  double hh, gmax;
+  const float *k2f, *gam;
+  helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nq = (size_t)count * nmix;
+  int* d_idx = nullptr;
+  double2* d_coef = nullptr;
+  UCHECK(cudaMallocAsync(&d_idx, nq * sizeof(int), s));
+  UCHECK(cudaMallocAsync(&d_coef, nq * sizeof(double2), s));
+  UCHECK(cudaMemcpyAsync(d_idx, idx, nq * sizeof(int), cudaMemcpyHostToDevice, s));
+  UCHECK(cudaMemcpyAsync(d_coef, coef, nq * sizeof(double2), cudaMemcpyHostToDevice, s));
+  make_batch((const double2*)r, (const double2*)e, (size_t)nx * ny, count, d_idx, d_coef, nmix, hh, k2f, gam, x, target, s);
+  cudaFreeAsync(d_idx, s);
+  cudaFreeAsync(d_coef, s);
+  UCHECK(cudaGetLastError());
+  UCHECK(cudaStreamSynchronize(s));   // the host arrays may be released by the caller
+  return HELM_OK;
+}
+
+int unet_precond(helm_t h, unet_t net, int kind, const void* r, void* e, int nrhs, int dtype, helm_stream_t stream) {
+  if (!h || !net || !r || !e || r == e || nrhs < 1 || (dtype != HELM_C32 && dtype != HELM_C64)) {
+    set_error("bad arguments");
+    return HELM_EINVAL;
+  }
+  return unet_precond_impl(h, net, kind, r, e, nrhs, dtype == HELM_C32 ? 4 : 8, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

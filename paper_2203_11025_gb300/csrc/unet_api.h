@@ -10,3 +10,5 @@ int unet_precond_impl(helm_ctx* c, void* net, int kind, const void* v, void* z, 
                       const int* gate, cudaStream_t s);
 // Release U-Net workspace attached to a solver handle.
 void unet_release_ctx(helm_ctx* c);
+// Allocate the network's workspace for nrhs right-hand sides on c's grid (before graph capture).
+int unet_prepare_impl(helm_ctx* c, void* net, int nrhs);

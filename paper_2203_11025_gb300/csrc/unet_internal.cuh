@@ -1,0 +1,73 @@
+// Internal declarations of the U-Net kernels (unet_kernels.cu) used by the
+// network executor (unet.cu).  Not part of the ABI.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace helm {
+
+constexpr float kBnEps = 1e-5f;
+constexpr float kBnMomentum = 0.1f;
+
+// One convolution as an implicit GEMM: rows = output pixels, columns = output
+// channels, reduction over taps x input channels.  The input is the channel
+// concatenation of two sources (in1 may be null); in_f32 selects FP32 sources
+// (gradients) instead of BF16 (activations); in_act applies eLU on load.
+// Weight element (tap, ci, co) sits at W[tap * wst + ci * wsk + co * wsn].
+struct ConvArgs {
+  const void* in0; int c0, ld0;
+  const void* in1; int c1, ld1;
+  int bcast1;                        // in1 is one image shared by the whole batch
+  int in_f32, in_act;
+  int B, Hi, Wi, Ho, Wo, Cout;
+  int k, stride, pad, transposed;
+  const __nv_bfloat16* W; long long wst, wsk, wsn;
+  const __nv_bfloat16* WT;           // K-major copy [cout][tap * cin + ci] for the tensor-core path, or null
+  float* out; int ldo;
+  const float* bias;                 // per output channel, may be null
+  const __nv_bfloat16* res; int ldr; // residual added to the output, may be null
+};
+
+void conv_forward(const ConvArgs& a, cudaStream_t s);
+// Tensor-core path (conv_tc.cu): eligible when inputs are BF16 without on-load
+// activation, channel counts are multiples of 8, Cout a multiple of 16 (<= 256).
+bool conv_tc_eligible(const ConvArgs& a);
+void conv_forward_tc(const ConvArgs& a, int* err, cudaStream_t s);
+void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int cout, cudaStream_t s);
+void elu_copy_bf16(const __nv_bfloat16* src, int lds, int C, size_t M, __nv_bfloat16* dst, int ldd, cudaStream_t s);
+void conv_wgrad(const ConvArgs& a, const float* G, int ldg, float* gW, cudaStream_t s);
+void bn_batch_stats(const float* z, int ldz, int C, int M, double* mean, double* var, float* part, int nblk,
+                    cudaStream_t s);
+void bn_coeffs(const double* mean, const double* var, const float* gamma, const float* beta, int C, float* scale,
+               float* shift, float* rmean, float* rvar, bool update, int M, cudaStream_t s);
+void bn_coeffs_eval(const float* rmean, const float* rvar, const float* gamma, const float* beta, int C,
+                    float* scale, float* shift, cudaStream_t s);
+void bn_act(const float* z, int ldz, int C, int M, const float* scale, const float* shift, bool act,
+            __nv_bfloat16* y, int ldy, cudaStream_t s);
+void bn_backward(const float* g, int ldg, const float* z, int ldz, int C, int M, const double* mean, const double* var,
+                 const float* scale, const float* shift, bool act, const float* gamma, float* ggamma, float* gbeta,
+                 float* part, int nblk, double* sums, float* gz, int ldo, cudaStream_t s);
+// g *= eLU'(u); plane != 0: u is one image of `plane` pixels shared by the batch.
+void elu_backward_inplace(float* g, int ldg, const __nv_bfloat16* u, int ldu, int C, int M, size_t plane,
+                          cudaStream_t s);
+void add_slice(float* dst, int ldd, const float* src, int lds, int C, int M, cudaStream_t s);
+void to_bf16_slice(const float* src, int lds, __nv_bfloat16* dst, int ldd, int C, int M, cudaStream_t s);
+void mse_loss(const float* out, const float* tgt, size_t n, int B, float* gout, float* part, float* loss,
+              cudaStream_t s);
+void adam_update(float* p, const float* g, float* m1, float* m2, size_t n, float lr, float b1, float b2, float eps,
+                 int t, cudaStream_t s);
+void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);
+void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
+                __nv_bfloat16* x, int ldx, float* sc, const int* gate, cudaStream_t s);
+void write_output(const float* out, bool fp64, int B, int ny, int nx, const float* sc, void* e, bool add,
+                  const int* gate, cudaStream_t s);
+void gamma_field(int ny, int nx, int width, float gmax, float* g, cudaStream_t s);
+void chan_sum_add(const float* g, int ld, int C, int M, float* dst, float* part, int nblk, cudaStream_t s);
+void batch_sum(const float* src, int lds, int B, size_t P, int C, float* dst, int ldd, bool accumulate,
+               cudaStream_t s);
+void complex_normal(unsigned long long seed, int count, size_t N, double2* x, cudaStream_t s);
+void make_batch(const double2* r, const double2* e, size_t N, int count, const int* idx, const double2* coef, int nmix,
+                double h, const float* k2, const float* gam, float* x, float* tgt, cudaStream_t s);
+
+}  // namespace helm

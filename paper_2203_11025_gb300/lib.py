@@ -27,7 +27,14 @@ ABI_SYMBOLS = [
     "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
     "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
     "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "helm_time_kernel",
+    # include/unet.h
+    "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
+    "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
+    "unet_mse", "unet_adam_step", "unet_attach_encoder", "unet_encode", "unet_precond", "helm_gen_pairs",
+    "unet_make_batch", "unet_status",
 ]
+UNET_FLAG_SIMT = 1
+UNET_STANDALONE, UNET_ENCODER, UNET_SOLVER = 0, 1, 2
 
 
 class helm_desc(ctypes.Structure):
@@ -35,6 +42,12 @@ class helm_desc(ctypes.Structure):
                 ("beta", ctypes.c_double), ("abc_width", ctypes.c_int), ("abc_gamma_max", ctypes.c_double),
                 ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("jacobi_w", ctypes.c_double), ("coarse_its", ctypes.c_int), ("flags", ctypes.c_int)]
+
+
+class unet_cfg(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("levels", ctypes.c_int),
+                ("coarse_resnets", ctypes.c_int), ("widths", ctypes.c_int * 8), ("context", ctypes.c_int * 9),
+                ("flags", ctypes.c_int)]
 
 
 class fgmres_opts(ctypes.Structure):
@@ -76,6 +89,26 @@ def load():
         "sl_vcycle": (I, [P, P, P, I, I, I, P]),
         "fgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
         "helm_time_kernel": (I, [P, I, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D)]),
+        "unet_cfg_default": (I, [ctypes.POINTER(unet_cfg), I]),
+        "unet_create": (I, [ctypes.POINTER(unet_cfg), ctypes.c_ulonglong, ctypes.POINTER(P)]),
+        "unet_destroy": (None, [P]),
+        "unet_sizes": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "unet_set_params": (I, [P, P, ctypes.c_longlong]),
+        "unet_get_params": (I, [P, P, ctypes.c_longlong]),
+        "unet_set_bn_stats": (I, [P, P, ctypes.c_longlong]),
+        "unet_get_bn_stats": (I, [P, P, ctypes.c_longlong]),
+        "unet_get_grads": (I, [P, P, ctypes.c_longlong]),
+        "unet_zero_grad": (I, [P, P]),
+        "unet_forward": (I, [P, P, P, I, I, I, I, P]),
+        "unet_backward": (I, [P, P, P, P]),
+        "unet_mse": (I, [P, P, ctypes.c_longlong, I, P, P, P]),
+        "unet_adam_step": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
+        "unet_attach_encoder": (I, [P, P]),
+        "unet_encode": (I, [P, P, I, P]),
+        "unet_precond": (I, [P, P, I, P, P, I, I, P]),
+        "helm_gen_pairs": (I, [P, I, ctypes.c_ulonglong, I, P, P, P]),
+        "unet_make_batch": (I, [P, P, P, I, I, I, P, P, P, P, P]),
+        "unet_status": (I, [P, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +286,39 @@ class Helmholtz:
                                          ctypes.byref(nbytes)), "helm_time_kernel")
         return ms.value, nbytes.value
 
+    def gen_pairs(self, count, seed, kmax=10, stream=None):
+        """Training pairs (r, e) of Eq. 3.8-3.9 (complex128 CUDA tensors [count, ny, nx])."""
+        import torch
+        ny, nx = self.level_shape(0)
+        r = torch.empty(count, ny, nx, dtype=torch.complex128, device="cuda")
+        e = torch.empty_like(r)
+        _check(self.lib.helm_gen_pairs(self.h, count, seed, kmax, _ptr(r), _ptr(e), _stream(stream)),
+               "helm_gen_pairs")
+        return r, e
+
+    def make_batch(self, r, e, idx, coef, stream=None):
+        """Network inputs and targets for samples mixing pairs idx [count, nmix] with complex
+        coefficients coef [count, nmix] (numpy); r, e: complex128 CUDA pairs."""
+        import numpy as np
+        import torch
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        coef = np.ascontiguousarray(coef, dtype=np.complex128)
+        count, nmix = idx.shape
+        ny, nx = self.level_shape(0)
+        x = torch.empty(count, ny, nx, 4, dtype=torch.float32, device="cuda")
+        t = torch.empty(count, ny, nx, 2, dtype=torch.float32, device="cuda")
+        _check(self.lib.unet_make_batch(self.h, _ptr(r), _ptr(e), r.shape[0], count, nmix, idx.ctypes.data,
+                                        coef.ctypes.data, _ptr(x), _ptr(t), _stream(stream)), "unet_make_batch")
+        return x, t
+
+    def unet_precond(self, net, r, kind=HELM_PREC_VU, out=None, stream=None):
+        import torch
+        n, dt = self._vec(r, 0)
+        e = torch.empty_like(r) if out is None else out
+        _check(self.lib.unet_precond(self.h, net.handle, kind, _ptr(r), _ptr(e), n, dt, _stream(stream)),
+               "unet_precond")
+        return e
+
     def fgmres(self, b, x=None, precond=HELM_PREC_V, net=None, restart=10, tol=1e-7, maxit=5000, flags=0,
                stream=None):
         """Solve A x = b (complex128 tensors, CUDA or pinned host with HELM_FLAG_HOST_IO).
@@ -275,3 +341,112 @@ class Helmholtz:
         _check(code, "fgmres_solve", ok=(HELM_OK, HELM_MAXIT))
         return x, {"status": code, "iters": list(iters), "relres": list(relres), "iters_max": res.iters_max,
                    "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches}
+
+
+def unet_cfg_default(kind=UNET_STANDALONE):
+    c = unet_cfg()
+    _check(load().unet_cfg_default(ctypes.byref(c), kind), "unet_cfg_default")
+    return c
+
+
+class UNet:
+    """A U-Net of libhelm (include/unet.h): weights live on the GPU."""
+
+    def __init__(self, cfg=None, seed=0, kind=UNET_STANDALONE):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else unet_cfg_default(kind)
+        h = ctypes.c_void_p()
+        _check(self.lib.unet_create(ctypes.byref(self.cfg), seed, ctypes.byref(h)), "unet_create")
+        self.handle = h
+        npar, nbn = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self.lib.unet_sizes(h, ctypes.byref(npar), ctypes.byref(nbn)), "unet_sizes")
+        self.n_params, self.n_bn = npar.value, nbn.value
+        self.encoder = None
+
+    def close(self):
+        if self.handle:
+            self.lib.unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(self.lib.unet_set_params(self.handle, a.ctypes.data, a.size), "unet_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.n_params, np.float32)
+        _check(self.lib.unet_get_params(self.handle, a.ctypes.data, a.size), "unet_get_params")
+        return a
+
+    def set_bn_stats(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(self.lib.unet_set_bn_stats(self.handle, a.ctypes.data, a.size), "unet_set_bn_stats")
+
+    def get_bn_stats(self):
+        import numpy as np
+        a = np.empty(self.n_bn, np.float32)
+        _check(self.lib.unet_get_bn_stats(self.handle, a.ctypes.data, a.size), "unet_get_bn_stats")
+        return a
+
+    def get_grads(self):
+        import numpy as np
+        import torch
+        torch.cuda.synchronize()
+        a = np.empty(self.n_params, np.float32)
+        _check(self.lib.unet_get_grads(self.handle, a.ctypes.data, a.size), "unet_get_grads")
+        return a
+
+    def status(self):
+        """Synchronise; True if a tensor-core kernel recorded an expired wait (then cleared)."""
+        f = ctypes.c_int()
+        _check(self.lib.unet_status(self.handle, ctypes.byref(f)), "unet_status")
+        return bool(f.value)
+
+    def zero_grad(self, stream=None):
+        _check(self.lib.unet_zero_grad(self.handle, _stream(stream)), "unet_zero_grad")
+
+    def attach_encoder(self, enc):
+        _check(self.lib.unet_attach_encoder(self.handle, enc.handle if enc else None), "unet_attach_encoder")
+        self.encoder = enc
+
+    def encode(self, hz, train=False, stream=None):
+        _check(self.lib.unet_encode(self.handle, hz.h, 1 if train else 0, _stream(stream)), "unet_encode")
+
+    def forward(self, x, train=False, stream=None):
+        """x: float32 CUDA tensor [B, ny, nx, in_ch]; returns float32 [B, ny, nx, out_ch]."""
+        import torch
+        B, ny, nx, _ = x.shape
+        out = torch.empty(B, ny, nx, self.cfg.out_ch, dtype=torch.float32, device=x.device)
+        _check(self.lib.unet_forward(self.handle, _ptr(x.contiguous()), _ptr(out), B, ny, nx, 1 if train else 0,
+                                     _stream(stream)), "unet_forward")
+        return out
+
+    def backward(self, gout, want_gx=False, stream=None):
+        import torch
+        gx = None
+        if want_gx:
+            B, ny, nx, _ = gout.shape
+            gx = torch.empty(B, ny, nx, self.cfg.in_ch, dtype=torch.float32, device=gout.device)
+        _check(self.lib.unet_backward(self.handle, _ptr(gout.contiguous()), _ptr(gx), _stream(stream)),
+               "unet_backward")
+        return gx
+
+    def mse(self, out, target, stream=None):
+        """MSE of Eq. 3.7; returns (loss tensor [1] on device, gout)."""
+        import torch
+        gout = torch.empty_like(out)
+        loss = torch.empty(1, dtype=torch.float32, device=out.device)
+        _check(self.lib.unet_mse(_ptr(out), _ptr(target.contiguous()), out.numel(), out.shape[0], _ptr(gout),
+                                 _ptr(loss), _stream(stream)), "unet_mse")
+        return loss, gout
+
+    def adam_step(self, lr=1e-4, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        _check(self.lib.unet_adam_step(self.handle, lr, b1, b2, eps, _stream(stream)), "unet_adam_step")

@@ -97,6 +97,17 @@ def gaussian_rhs(ny: int, nx: int, count: int, seed: int) -> np.ndarray:
     return complex_normal(seed, (count, ny, nx))
 
 
+def pair_draws(seed: int, count: int, ny: int, nx: int, kmax: int):
+    """Random numbers of the training-pair generator (Eq. 3.8-3.9), in the counter
+    layout both implementations use: pair j's x ~ CN(0,1) is complex_normal of stream
+    seed + 1 + j; its iteration count is k_j = 1 + floor(U_j kmax), U_j the j-th
+    uniform of stream seed."""
+    x = np.stack([complex_normal(seed + 1 + j, (ny, nx)) for j in range(count)])
+    u = uniform01(seed, count)
+    ks = np.minimum(1 + np.floor(u * kmax).astype(np.int64), kmax)
+    return x, ks
+
+
 def medium_seed(problem_id: int) -> int:
     return 1000 + problem_id
 

@@ -1,0 +1,288 @@
+"""GPU parity of the U-Net path against the FP64 oracle: forward (inference and
+training BatchNorm), backward (every parameter group and the input), the
+encoder-solver pair, Adam, the preconditioners M_JU / M_VU, and the
+training-pair generator.
+
+Tolerance: the network runs in BF16 (weights and activations, 8-bit mantissa,
+unit roundoff 2^-9) with FP32 accumulation; over ~20 layers the normwise
+relative error of the output stays near 1e-2, so forward checks use 2e-2
+normwise (3e-2 for the full-width default network) and gradient checks 5e-2
+per parameter group."""
+import numpy as np
+import pytest
+
+from gpu_util import crandn, medium
+from oracle import helmholtz as H
+from oracle import precond as PR
+from oracle import unet as U
+from paper_2203_11025_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2203_11025_gb300 import build
+    from paper_2203_11025_gb300 import lib as L
+    build.build()
+    return L
+
+
+def nrel(a, b):
+    a = np.asarray(a, dtype=np.complex128 if np.iscomplexobj(a) else np.float64)
+    b = np.asarray(b, dtype=a.dtype)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def make_cfgs(lib, widths=(8, 16), resnets=2, in_ch=4, out_ch=2, context=None, simt=False):
+    c = lib.unet_cfg()
+    c.in_ch, c.out_ch, c.levels, c.coarse_resnets = in_ch, out_ch, len(widths), resnets
+    c.flags = lib.UNET_FLAG_SIMT if simt else 0
+    for i, w in enumerate(widths):
+        c.widths[i] = w
+    if context:
+        for i, v in enumerate(context):
+            c.context[i] = v
+    oc = U.UNetConfig(in_ch=in_ch, out_ch=out_ch, widths=tuple(widths), coarse_resnets=resnets,
+                      context=tuple(context) if context else None)
+    return c, oc
+
+
+def randomise(lib, net, oc, seed):
+    """Non-trivial BN parameters and running statistics, identical on both sides."""
+    rng = np.random.default_rng(seed)
+    P = U.init_params(oc, seed)
+    for k in P:
+        if k.endswith(".gamma"):
+            P[k] = 1.0 + 0.2 * rng.standard_normal(P[k].shape)
+        elif k.endswith(".beta") or k.endswith("bias"):
+            P[k] = 0.1 * rng.standard_normal(P[k].shape)
+    P = PR.unflatten_params(oc, PR.flatten_params(oc, P).astype(np.float32))   # the same float32 values
+    S = U.init_bn_stats(oc)
+    for k in S:
+        S[k] = (0.05 * rng.standard_normal(S[k].shape)) if k.endswith(".mean") else rng.uniform(0.5, 2.0, S[k].shape)
+    S = PR.unflatten_bn(oc, PR.flatten_bn(oc, S).astype(np.float32))
+    net.set_params(PR.flatten_params(oc, P))
+    net.set_bn_stats(PR.flatten_bn(oc, S))
+    return P, S
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_init_matches_oracle_init(lib):
+    c, oc = make_cfgs(lib)
+    net = lib.UNet(c, seed=5)
+    ref = PR.flatten_params(oc, U.init_params(oc, 5))
+    got = net.get_params()
+    assert got.size == ref.size
+    assert np.allclose(got, ref, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("ny,nx,B", [(32, 48, 3), (16, 16, 1)])
+def test_forward_inference_parity(lib, ny, nx, B, simt):
+    c, oc = make_cfgs(lib, widths=(16, 32), simt=simt)
+    net = lib.UNet(c, seed=1)
+    P, S = randomise(lib, net, oc, 1)
+    x = np.random.default_rng(2).standard_normal((B, ny, nx, 4))
+    out = net.forward(cuda(x)).cpu().numpy()
+    assert not net.status()
+    ref, _, _, _ = U.forward(oc, P, S, x, train=False)
+    assert nrel(out, ref) < 2e-2
+
+
+@pytest.mark.parametrize("simt", [False, True])
+def test_forward_default_architecture(lib, simt):
+    """Full-width network (32..256 channels): every layer type runs on the tensor-core
+    kernel (down 5x5 stride 2, ResNet 3x3, transposed 5x5 per output phase) except the
+    4-channel input and 2-channel output layers."""
+    c = lib.unet_cfg_default(lib.UNET_STANDALONE)
+    c.flags = lib.UNET_FLAG_SIMT if simt else 0
+    oc = U.UNetConfig()
+    net = lib.UNet(c, seed=3)
+    P, S = randomise(lib, net, oc, 3)
+    x = np.random.default_rng(4).standard_normal((2, 64, 64, 4))
+    out = net.forward(cuda(x)).cpu().numpy()
+    assert not net.status()
+    ref, _, _, _ = U.forward(oc, P, S, x, train=False)
+    assert nrel(out, ref) < 3e-2
+
+
+def test_tensor_core_and_cuda_core_paths_agree(lib):
+    c = lib.unet_cfg_default(lib.UNET_STANDALONE)
+    a = lib.UNet(c, seed=21)
+    c2 = lib.unet_cfg_default(lib.UNET_STANDALONE)
+    c2.flags = lib.UNET_FLAG_SIMT
+    b = lib.UNet(c2, seed=21)
+    x = cuda(np.random.default_rng(22).standard_normal((3, 96, 64, 4)))
+    ya, yb = a.forward(x).cpu().numpy(), b.forward(x).cpu().numpy()
+    assert not a.status()
+    assert nrel(ya, yb) < 1e-2
+
+
+def test_train_forward_backward_parity(lib):
+    c, oc = make_cfgs(lib)
+    net = lib.UNet(c, seed=6)
+    P, S = randomise(lib, net, oc, 6)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((3, 32, 32, 4))
+    tgt = rng.standard_normal((3, 32, 32, 2))
+    net.zero_grad()
+    out = net.forward(cuda(x), train=True)
+    loss, gout = net.mse(out, cuda(tgt))
+    gx = net.backward(gout, want_gx=True)
+    ref, cache, new_stats, _ = U.forward(oc, P, S, x, train=True)
+    rloss, rgout = U.mse_loss(ref, tgt)
+    G, rgx, _ = U.backward(oc, P, cache, rgout)
+    assert nrel(out.cpu().numpy(), ref) < 2e-2
+    assert abs(loss.item() - rloss) / rloss < 2e-2
+    Gg = PR.unflatten_params(oc, net.get_grads())
+    for k in G:
+        assert nrel(Gg[k], G[k]) < 5e-2, k
+    assert nrel(gx.cpu().numpy(), rgx) < 5e-2
+    Sg = PR.unflatten_bn(oc, net.get_bn_stats())
+    for k in new_stats:
+        assert nrel(Sg[k], new_stats[k]) < 1e-2, k
+
+
+@pytest.mark.parametrize("simt", [False, True])
+def test_encoder_solver_parity(lib, simt):
+    ec, eoc = make_cfgs(lib, in_ch=2, out_ch=4, widths=(16, 32), simt=simt)
+    ctx = U.context_channels(eoc)
+    sc, soc = make_cfgs(lib, context=ctx, widths=(16, 32), simt=simt)
+    enc, sol = lib.UNet(ec, seed=8), lib.UNet(sc, seed=9)
+    Pe, Se = randomise(lib, enc, eoc, 8)
+    Ps, Ss = randomise(lib, sol, soc, 9)
+    sol.attach_encoder(enc)
+    rng = np.random.default_rng(10)
+    med = rng.standard_normal((1, 32, 32, 2))
+    x = rng.standard_normal((2, 32, 32, 4))
+    tgt = rng.standard_normal((2, 32, 32, 2))
+    # inference: encoder once, features broadcast to the solver batch
+    enc.forward(cuda(med))
+    out = sol.forward(cuda(x)).cpu().numpy()
+    _, _, _, fe = U.forward(eoc, Pe, Se, med, train=False)
+    ref, _, _, _ = U.forward(soc, Ps, Ss, x, train=False, feats=[np.broadcast_to(f, (2,) + f.shape[1:]) for f in fe])
+    assert nrel(out, ref) < 2e-2
+    # training: gradients reach the encoder through the context features
+    sol.zero_grad()
+    enc.forward(cuda(med), train=True)
+    o = sol.forward(cuda(x), train=True)
+    _, gout = sol.mse(o, cuda(tgt))
+    sol.backward(gout)
+    _, ce, _, fe = U.forward(eoc, Pe, Se, med, train=True)
+    feb = [np.repeat(f, 2, axis=0) for f in fe]
+    ro, cs, _, _ = U.forward(soc, Ps, Ss, x, train=True, feats=feb)
+    _, rg = U.mse_loss(ro, tgt)
+    Gs, _, gf = U.backward(soc, Ps, cs, rg)
+    gf = [g.sum(axis=0, keepdims=True) for g in gf]
+    Ge = U.backward_features(eoc, Pe, ce, gf)
+    Gsg = PR.unflatten_params(soc, sol.get_grads())
+    Geg = PR.unflatten_params(eoc, enc.get_grads())
+    for k in ("down1", "down2", "up2", "up1", "res2.1.k2"):
+        assert nrel(Gsg[k], Gs[k]) < 5e-2, k
+    for k in ("down1", "down2", "up2", "up1", "res1.0.k1"):
+        assert nrel(Geg[k], Ge[k]) < 5e-2, k
+
+
+def test_adam_step_matches_oracle(lib):
+    c, oc = make_cfgs(lib)
+    net = lib.UNet(c, seed=11)
+    P, S = randomise(lib, net, oc, 11)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((2, 16, 16, 4))
+    tgt = rng.standard_normal((2, 16, 16, 2))
+    net.zero_grad()
+    out = net.forward(cuda(x), train=True)
+    _, gout = net.mse(out, cuda(tgt))
+    net.backward(gout)
+    G = PR.unflatten_params(oc, net.get_grads())
+    net.adam_step(lr=1e-3)
+    M = {k: np.zeros_like(v) for k, v in P.items()}
+    V = {k: np.zeros_like(v) for k, v in P.items()}
+    P2 = {k: v.copy() for k, v in P.items()}
+    U.adam_step(P2, G, M, V, 1, 1e-3)
+    got = PR.unflatten_params(oc, net.get_params())
+    for k in P2:
+        assert np.allclose(got[k], P2[k], rtol=1e-5, atol=1e-6), k
+
+
+def _helm(lib, n, seed=1000):
+    k2 = medium(n, n, seed)
+    hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+    d = hz.desc
+    prob = H.Problem(k2.astype(np.float64), omega=d.omega, h=d.h, abc_width=d.abc_width, levels=d.levels)
+    return hz, prob
+
+
+@pytest.mark.parametrize("kind", ["ju", "vu"])
+def test_unet_preconditioner_parity(lib, kind):
+    n = 64
+    hz, prob = _helm(lib, n)
+    c, oc = make_cfgs(lib, widths=(16, 32, 64))
+    net = lib.UNet(c, seed=13)
+    P, S = randomise(lib, net, oc, 13)
+    r = crandn(14, (2, n, n))
+    k = lib.HELM_PREC_JU if kind == "ju" else lib.HELM_PREC_VU
+    e = hz.unet_precond(net, torch.from_numpy(r).cuda(), kind=k).cpu().numpy()
+    ref = (PR.precond_ju if kind == "ju" else PR.precond_vu)(prob, oc, P, S, r)
+    assert nrel(e, ref) < 2e-2
+
+
+def test_encoder_solver_preconditioner(lib):
+    n = 64
+    hz, prob = _helm(lib, n)
+    ec, eoc = make_cfgs(lib, in_ch=2, out_ch=4)
+    sc, soc = make_cfgs(lib, context=U.context_channels(eoc))
+    enc, sol = lib.UNet(ec, seed=15), lib.UNet(sc, seed=16)
+    Pe, Se = randomise(lib, enc, eoc, 15)
+    Ps, Ss = randomise(lib, sol, soc, 16)
+    sol.attach_encoder(enc)
+    sol.encode(hz)
+    r = crandn(17, (3, n, n))
+    e = hz.unet_precond(sol, torch.from_numpy(r).cuda(), kind=lib.HELM_PREC_VU).cpu().numpy()
+    fe = PR.encoder_features(prob, eoc, Pe, Se)
+    ref = PR.precond_vu(prob, soc, Ps, Ss, r, feats=[np.broadcast_to(f, (3,) + f.shape[1:]) for f in fe])
+    assert nrel(e, ref) < 2e-2
+
+
+def test_gen_pairs_parity(lib):
+    n = 32
+    hz, prob = _helm(lib, n)
+    r, e = hz.gen_pairs(4, seed=123, kmax=10)
+    r, e = r.cpu().numpy(), e.cpu().numpy()
+    x, ks = synth.pair_draws(123, 4, n, n, 10)
+    rr, er = PR.gen_pairs(prob, x, ks)
+    for j in range(4):
+        # Eq. 3.9 identity: A e = r (independent of solver precision)
+        assert nrel(H.apply_op(prob.A, e[j]), r[j]) < 1e-10
+        # k FP32 Krylov steps vs FP64: the iterate x~ agrees to ~1e-6 relative, and e = x - x~
+        # loses the digits x and x~ share (|e| ~ 1e-2 |x| after a few steps); r = A e
+        # amplifies the high-frequency part of that difference by up to ||A|| ~ 8/h^2
+        assert nrel(e[j], er[j]) < 5e-4 and nrel(r[j], rr[j]) < 1e-2
+
+
+def test_fgmres_vu_with_silent_network_equals_sl(lib):
+    """With the output layer zeroed, U-Net(r) = 0 and M_VU is exactly one V-cycle from
+    zero: FGMRES(M_VU) must take the same iterations as FGMRES(M_V)."""
+    n = 64
+    hz, prob = _helm(lib, n)
+    c, oc = make_cfgs(lib)
+    net = lib.UNet(c, seed=18)
+    P, S = randomise(lib, net, oc, 18)
+    P["up1"][:] = 0.0
+    P["up1.bias"][:] = 0.0
+    net.set_params(PR.flatten_params(oc, P))
+    pos = synth.source_positions(n, n, 2, 5, 16)
+    b = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n)).cuda()
+    _, iv = hz.fgmres(b, precond=lib.HELM_PREC_V, tol=1e-7, maxit=3000)
+    x, iu = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=3000)
+    assert iu["status"] == 0
+    assert all(abs(a - b) <= 2 for a, b in zip(iu["iters"], iv["iters"]))
+    x = x.cpu().numpy()
+    bb = b.cpu().numpy()
+    for j in range(2):
+        assert np.linalg.norm(H.residual(prob.A, bb[j], x[j])) / np.linalg.norm(bb[j]) <= 1e-7
