@@ -111,6 +111,13 @@ int unet_precond(helm_t h, unet_t net, int kind, const void* r, void* e, int nrh
 int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int count, int nmix, const int* idx,
                     const double* coef, float* x, float* target, helm_stream_t stream);
 
+/* Measurement hook (no counterpart in the paper): time one convolution layer
+ * (index in layer order) of the last forward's geometry `reps` times with CUDA
+ * events on `stream`; *ms = mean device time per launch, *flops = 2 * MACs of
+ * the layer (structural zeros of transposed convolutions excluded), *tc = 1 if
+ * it ran on the tensor-core kernel.  Needs a prior unet_forward of that shape. */
+int unet_time_layer(unet_t net, int layer, int reps, helm_stream_t stream, float* ms, double* flops, int* tc);
+
 /* Training pairs of Eq. 3.8-3.9 on the medium of h: x ~ CN(0,1) per node and
  * k ~ U{1..kmax} per pair from SplitMix64(seed) (counter layout in synth.py),
  * b = A x, x~ = k FGMRES(m)+M_V iterations from 0, r = b - A x~, e = x - x~.

@@ -740,6 +740,65 @@ int unet_get_bn_stats(unet_t n, float* host, long long cnt) {
   UCHECK(cudaMemcpy(host, n->rstats, cnt * 4, cudaMemcpyDeviceToHost));
   return HELM_OK;
 }
+int unet_time_layer(unet_t n, int layer, int reps, helm_stream_t stream, float* ms, double* flops, int* tc) {
+  if (!n || !ms || !flops || !tc || reps < 1 || layer < 0 || layer >= (int)n->convs.size() || !n->ws) {
+    set_error("bad arguments (a forward must run first)");
+    return HELM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const ConvL& cl = n->convs[layer];
+  const unet_cfg& c = n->cfg;
+  const int* w = c.widths;
+  const int L = n->L;
+  // reconstruct the layer's geometry from its name (inputs are whatever the buffers hold)
+  int lvl = 0;
+  if (cl.name.rfind("down", 0) == 0) lvl = std::stoi(cl.name.substr(4));
+  else if (cl.name.rfind("res", 0) == 0) lvl = std::stoi(cl.name.substr(3, cl.name.find('.') - 3));
+  else lvl = std::stoi(cl.name.substr(2));
+  int H = 0, W = 0;
+  ConvArgs a{};
+  if (cl.kind == 0) {
+    H = n->ny >> (lvl - 1); W = n->nx >> (lvl - 1);
+    Src src = lvl == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[lvl - 1] + w[lvl - 2], w[lvl - 2], 2 * w[lvl - 2], false};
+    a = conv_args(n, cl, src, feat_of(n, lvl - 1), false, H, W, n->zdown[lvl], w[lvl - 1]);
+  } else if (cl.kind == 1) {
+    H = n->ny >> lvl; W = n->nx >> lvl;
+    a = conv_args(n, cl, Src{n->h0[lvl], w[lvl - 1], w[lvl - 1], false}, Src{nullptr, 0, 0, false}, false, H, W,
+                  n->t1[lvl][0], w[lvl - 1]);
+  } else {
+    H = n->ny >> lvl; W = n->nx >> lvl;
+    if (lvl >= 2) {
+      const int cu = lvl == L ? w[L - 1] : 2 * w[lvl - 1];
+      Src u{n->uact[lvl], cu, cu, false};
+      Src f = feat_of(n, lvl);
+      if (f.p) f = Src{n->fact[lvl], f.c, f.c, f.bcast};
+      a = conv_args(n, cl, u, f, false, H, W, n->zup[lvl], w[lvl - 2]);
+      if (!(n->use_tc && conv_tc_eligible(a))) a.in_act = 1;
+    } else {
+      Src u = L > 1 ? Src{n->cat[1], 2 * w[0], 2 * w[0], false} : Src{n->hL, w[0], w[0], false};
+      a = conv_args(n, cl, u, feat_of(n, 1), true, H, W, n->out, c.out_ch);
+    }
+  }
+  const double taps_eff = cl.kind == 2 ? (double)cl.k * cl.k / 4.0 : (double)cl.k * cl.k;
+  *flops = 2.0 * (double)n->B * a.Ho * a.Wo * taps_eff * cl.cin * cl.cout;
+  *tc = (n->use_tc && conv_tc_eligible(a)) ? 1 : 0;
+  run_conv(n, a, s);  // warm-up
+  cudaEvent_t e0, e1;
+  UCHECK(cudaEventCreate(&e0));
+  UCHECK(cudaEventCreate(&e1));
+  UCHECK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) run_conv(n, a, s);
+  UCHECK(cudaEventRecord(e1, s));
+  UCHECK(cudaEventSynchronize(e1));
+  float t = 0;
+  UCHECK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  UCHECK(cudaGetLastError());
+  return HELM_OK;
+}
+
 int unet_status(unet_t n, int* failed) {
   if (!n || !failed) { set_error("bad arguments"); return HELM_EINVAL; }
   UCHECK(cudaDeviceSynchronize());

@@ -115,6 +115,56 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvArgs a) {
   }
 }
 
+// Thin convolution (few output channels, or few input channels): one thread per
+// output pixel computes all Cout <= 32 outputs; the weights sit in shared memory
+// as float; transposed stride-2 convolutions visit only the taps of the pixel's
+// output phase.
+template <int CO>
+__global__ void __launch_bounds__(128) k_conv_thin(ConvArgs a) {
+  extern __shared__ float wsm[];   // [taps][Cin][CO]
+  const int Cin = a.c0 + a.c1;
+  const int taps = a.k * a.k;
+  for (int i = threadIdx.x; i < taps * Cin * CO; i += blockDim.x) {
+    const int co = i % CO, r = i / CO;
+    const int ci = r % Cin, tap = r / Cin;
+    wsm[i] = co < a.Cout ? bf(a.W[tap * a.wst + ci * a.wsk + co * a.wsn]) : 0.f;
+  }
+  __syncthreads();
+  const int M = a.B * a.Ho * a.Wo;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int b = m / (a.Ho * a.Wo);
+  const int rr = m - b * a.Ho * a.Wo;
+  const int oy = rr / a.Wo, ox = rr - oy * a.Wo;
+  float acc[CO];
+#pragma unroll
+  for (int j = 0; j < CO; ++j) acc[j] = 0.f;
+  const size_t plane = (size_t)a.Hi * a.Wi;
+  int ky0 = 0, kx0 = 0, dk = 1;
+  if (a.transposed) { ky0 = (oy + a.pad) % a.stride; kx0 = (ox + a.pad) % a.stride; dk = a.stride; }
+  for (int ky = ky0; ky < a.k; ky += dk) {
+    for (int kx = kx0; kx < a.k; kx += dk) {
+      int iy, ix;
+      if (!gather_pos(a, oy, ox, ky, kx, iy, ix)) continue;
+      const size_t sp = ((size_t)b * a.Hi + iy) * a.Wi + ix;
+      const float* wt = wsm + (size_t)(ky * a.k + kx) * Cin * CO;
+      for (int ci = 0; ci < Cin; ++ci) {
+        const float v = load_in(a, sp, plane, ci);
+#pragma unroll
+        for (int j = 0; j < CO; ++j) acc[j] = fmaf(v, wt[ci * CO + j], acc[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CO; ++j) {
+    if (j >= a.Cout) break;
+    float val = acc[j];
+    if (a.bias) val += a.bias[j];
+    if (a.res) val += bf(a.res[(size_t)m * a.ldr + j]);
+    a.out[(size_t)m * a.ldo + j] = val;
+  }
+}
+
 // gW[tap][ci][co] += sum_m in(m, tap, ci) G[m][co] over a chunk of output pixels.
 __global__ void __launch_bounds__(256) k_wgrad_simt(ConvArgs a, const float* __restrict__ G, int ldg,
                                                     float* __restrict__ gW, int chunk) {
@@ -580,7 +630,28 @@ void elu_copy_bf16(const __nv_bfloat16* src, int lds, int C, size_t M, __nv_bflo
   k_elu_copy<<<grid_for(M * C), 256, 0, s>>>(src, lds, C, M, dst, ldd);
 }
 
+bool conv_thin(const ConvArgs& a, cudaStream_t s) {
+  const int Cin = a.c0 + a.c1;
+  const size_t wbytes = (size_t)a.k * a.k * Cin * 4;
+  const int M = a.B * a.Ho * a.Wo;
+  const int grid = (M + 127) / 128;
+  if (a.Cout <= 2 && wbytes * 2 <= 96 * 1024) {
+    static bool cfg2 = false;
+    if (!cfg2) { cudaFuncSetAttribute(k_conv_thin<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); cfg2 = true; }
+    k_conv_thin<2><<<grid, 128, wbytes * 2, s>>>(a);
+    return true;
+  }
+  if (Cin <= 8 && a.Cout <= 32 && wbytes * 32 <= 96 * 1024) {
+    static bool cfg32 = false;
+    if (!cfg32) { cudaFuncSetAttribute(k_conv_thin<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); cfg32 = true; }
+    k_conv_thin<32><<<grid, 128, wbytes * 32, s>>>(a);
+    return true;
+  }
+  return false;
+}
+
 void conv_forward(const ConvArgs& a, cudaStream_t s) {
+  if (conv_thin(a, s)) return;
   const int M = a.B * a.Ho * a.Wo;
   dim3 grid((M + 63) / 64, (a.Cout + 63) / 64);
   k_conv_simt<<<grid, 256, 0, s>>>(a);

@@ -31,7 +31,7 @@ ABI_SYMBOLS = [
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
     "unet_mse", "unet_adam_step", "unet_attach_encoder", "unet_encode", "unet_precond", "helm_gen_pairs",
-    "unet_make_batch", "unet_status",
+    "unet_make_batch", "unet_status", "unet_time_layer",
 ]
 UNET_FLAG_SIMT = 1
 UNET_STANDALONE, UNET_ENCODER, UNET_SOLVER = 0, 1, 2
@@ -109,6 +109,7 @@ def load():
         "helm_gen_pairs": (I, [P, I, ctypes.c_ulonglong, I, P, P, P]),
         "unet_make_batch": (I, [P, P, P, I, I, I, P, P, P, P, P]),
         "unet_status": (I, [P, ctypes.POINTER(I)]),
+        "unet_time_layer": (I, [P, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -409,6 +410,13 @@ class UNet:
         f = ctypes.c_int()
         _check(self.lib.unet_status(self.handle, ctypes.byref(f)), "unet_status")
         return bool(f.value)
+
+    def time_layer(self, layer, reps=20, stream=None):
+        """(ms per launch, flops per launch, ran on tensor cores) of convolution `layer`."""
+        ms, fl, tc = ctypes.c_float(), ctypes.c_double(), ctypes.c_int()
+        _check(self.lib.unet_time_layer(self.handle, layer, reps, _stream(stream), ctypes.byref(ms), ctypes.byref(fl),
+                                        ctypes.byref(tc)), "unet_time_layer")
+        return ms.value, fl.value, bool(tc.value)
 
     def zero_grad(self, stream=None):
         _check(self.lib.unet_zero_grad(self.handle, _stream(stream)), "unet_zero_grad")
