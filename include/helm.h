@@ -158,6 +158,29 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
  *   kernel 5: the coarsest-grid GMRES solve      (bytes: not reported, 0)      */
 int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes);
 
+/* Coarsest-grid GMRES solve that allocates nothing (no counterpart in the
+ * paper; the arithmetic is helm_coarse_solve's one-launch kernel).  Some
+ * callers cannot call cudaMalloc: code that runs while a CUDA graph is being
+ * captured, real-time loops that must not trigger the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree, and hosts whose memory budget is
+ * fixed up front.  They pass the coarse problem itself -- nx x ny grid, mesh
+ * width h, omega, shift beta, layer width (in this grid's cells) and peak,
+ * kappa2 (device float32 [ny][nx]) -- and complex64 right-hand sides f and
+ * outputs x ([nrhs][ny][nx], device, distinct); the Krylov basis lives in a
+ * file-scope device array of 2^20 complex64 values (8 MiB), which every GPU
+ * that loads the library holds until the process exits.
+ *   Limits: (m + 1) * nrhs * nx * ny <= 2^20 and nx * ny * 8 <= 160 KiB, else
+ *   HELM_EINVAL with a message; 1 <= m <= 32.
+ *   The first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress) with the device current; make that first call
+ *   before any stream capture.  Every call shares the one array: calls that
+ *   overlap on the GPU (different streams, or concurrent host threads) race
+ *   and must be ordered by the caller.  The array keeps the last call's
+ *   contents; nothing in it needs to start at zero (each basis vector is
+ *   written before it is read). */
+int helm_coarse_solve_static(int nx, int ny, double h, double omega, double beta, int abc_width, double gamma_max,
+                             const float* kappa2, const void* f, void* x, int nrhs, int m, helm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,9 +11,15 @@
 // multi-kernel path exactly; inner products are accumulated per thread in T
 // and across the block in FP64, in a fixed order (deterministic).  Only block
 // barriers are used: no inter-CTA waiting.
+#include <mutex>
+#include <string>
+
+#include "../../include/helm.h"
 #include "helm_internal.cuh"
 
 namespace helm {
+
+void set_error(const std::string& s);
 
 namespace {
 
@@ -214,9 +220,82 @@ bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* 
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free entry point: the coarsest-grid GMRES solve with its Krylov
+// basis in a file-scope device array instead of a handle's workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 2^20 complex float = 8 MiB, held by every GPU that loads the library until exit.
+constexpr size_t kStaticBasisElems = (size_t)1 << 20;
+__device__ __align__(256) float2 g_static_basis[kStaticBasisElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+}  // namespace
+
 template bool launch_coarse_gmres_fused<float>(const Op<float>&, const void*, void*, void*, size_t, int, int,
                                                const int*, cudaStream_t);
 template bool launch_coarse_gmres_fused<double>(const Op<double>&, const void*, void*, void*, size_t, int, int,
                                                 const int*, cudaStream_t);
 
 }  // namespace helm
+
+extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, double beta, int abc_width,
+                                        double gamma_max, const float* kappa2, const void* f, void* x, int nrhs,
+                                        int m, helm_stream_t stream) {
+  if (nx <= 0 || ny <= 0 || nrhs < 1 || m < 1 || m > 32 || !(h > 0) || abc_width < 0 || !kappa2 || !f || !x ||
+      f == x) {
+    helm::set_error("helm_coarse_solve_static: bad arguments");
+    return HELM_EINVAL;
+  }
+  const size_t need = (size_t)(m + 1) * (size_t)nrhs * (size_t)nx * (size_t)ny;
+  if (need > helm::kStaticBasisElems) {
+    helm::set_error("helm_coarse_solve_static: (m+1)*nrhs*nx*ny = " + std::to_string(need) +
+                    " complex values exceed the static scratch of " + std::to_string(helm::kStaticBasisElems));
+    return HELM_EINVAL;
+  }
+  if ((size_t)nx * ny * sizeof(float2) > 160 * 1024) {
+    helm::set_error("helm_coarse_solve_static: grid larger than the one-launch kernel's shared memory (160 KiB)");
+    return HELM_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= helm::kMaxDevices) {
+    helm::set_error("helm_coarse_solve_static: no usable current device");
+    return HELM_ECUDA;
+  }
+  void* basis = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(helm::g_static_mu);
+    if (!helm::g_static_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, helm::g_static_basis);
+      if (e != cudaSuccess) {
+        helm::set_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return HELM_ECUDA;
+      }
+      helm::g_static_ptr[dev] = p;
+    }
+    basis = helm::g_static_ptr[dev];
+  }
+  helm::Op<float> op;
+  op.nx = nx; op.ny = ny; op.abc_w = abc_width;
+  op.inv_h2 = (float)(1.0 / (h * h));
+  op.omega2 = (float)(omega * omega);
+  op.gmax = (float)gamma_max;
+  op.beta = (float)beta;
+  op.k2 = kappa2;
+  if (!helm::launch_coarse_gmres_fused<float>(op, f, x, basis, (size_t)nrhs * nx * ny, nrhs, m, nullptr,
+                                              (cudaStream_t)stream)) {
+    helm::set_error("helm_coarse_solve_static: configuration not supported by the one-launch kernel");
+    return HELM_EINVAL;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    helm::set_error(std::string("helm_coarse_solve_static launch: ") + cudaGetErrorString(e));
+    return HELM_ECUDA;
+  }
+  return HELM_OK;
+}

@@ -27,6 +27,7 @@ ABI_SYMBOLS = [
     "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
     "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
     "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "helm_time_kernel",
+    "helm_coarse_solve_static",
     # include/unet.h
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
@@ -89,6 +90,7 @@ def load():
         "sl_vcycle": (I, [P, P, P, I, I, I, P]),
         "fgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
         "helm_time_kernel": (I, [P, I, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D)]),
+        "helm_coarse_solve_static": (I, [I, I, D, D, D, I, D, P, P, P, I, I, P]),
         "unet_cfg_default": (I, [ctypes.POINTER(unet_cfg), I]),
         "unet_create": (I, [ctypes.POINTER(unet_cfg), ctypes.c_ulonglong, ctypes.POINTER(P)]),
         "unet_destroy": (None, [P]),
@@ -179,6 +181,13 @@ def helm_setup(desc, kappa2, stream=None):
 
 def helm_destroy(h):
     load().helm_destroy(h)
+
+
+def helm_coarse_solve_static(nx, ny, h, omega, beta, abc_width, gamma_max, kappa2, f, x, nrhs, m=10, stream=None):
+    """The allocation-free coarsest-grid solve (see include/helm.h); tensors on the GPU."""
+    _check(load().helm_coarse_solve_static(nx, ny, h, omega, beta, abc_width, gamma_max, _ptr(kappa2), _ptr(f),
+                                           _ptr(x), nrhs, m, _stream(stream)), "helm_coarse_solve_static")
+    return x
 
 
 class Helmholtz:
