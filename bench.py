@@ -37,6 +37,7 @@ TRAIN_PAIRS = 128        # pairs per training medium (Eq. 3.8-3.9)
 TRAIN_EPOCHS = 4
 RETRAIN_PAIRS = 256      # mini-retraining on the benchmark medium (Sec. 3.5)
 RETRAIN_EPOCHS = 6
+TRAIN_LR = 1e-4         # Sec. 4: initial learning rate 1e-4 (1e-3 diverged at 256^2)
 METRIC = "s to FP64 rel-res 1e-7 & FGMRES iters, U-Net+SL vs plain SL on 1 GB300; HBM %"
 WORKLOAD = (f"{N_GRID}x{N_GRID} grid, h=1/{N_GRID}, omega=0.2*pi*{N_GRID}, GRF medium (sigma 8, kappa in "
             f"[0.25,1]), 16-cell quadratic absorbing layer, {NRHS} random point sources; FGMRES({RESTART}) "
@@ -162,7 +163,7 @@ def train_network(lib, dev, rank):
     loss = []
     for ep in range(TRAIN_EPOCHS):
         for j, (hk, pairs) in enumerate(media):
-            loss += T.train(hk, net, pairs=pairs, epochs=1, batch=16, lr=1e-3, seed=100 * ep + j)
+            loss += T.train(hk, net, pairs=pairs, epochs=1, batch=16, lr=TRAIN_LR, seed=100 * ep + j)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     return net, {"gen_s": round(t_gen, 2), "train_s": round(t_train, 2), "loss_first": round(loss[0], 1),

@@ -64,10 +64,11 @@ typedef struct {
   int coarse_its;          /* GMRES steps on the coarsest grid (Sec. 4: 10)   */
   int flags;               /* HELM_DESC_* implementation switches (0 = default) */
 } helm_desc;
-/* Run the coarsest GMRES as one kernel launch per Arnoldi pass instead of the
- * single fused kernel (the fused kernel is used when the coarsest grid fits
- * in shared memory); same arithmetic, for cross-checking. */
-enum { HELM_DESC_MULTIKERNEL_COARSE = 1 };
+/* Coarsest-GMRES implementation switches (default: a thread-block cluster per
+ * right-hand side with the Krylov basis in distributed shared memory when the
+ * grid fits, else one CTA per right-hand side when the grid fits in one CTA's
+ * shared memory, else one launch per Arnoldi pass); for cross-checking. */
+enum { HELM_DESC_MULTIKERNEL_COARSE = 1, HELM_DESC_SINGLE_CTA_COARSE = 2 };
 
 /* Fill `d` with the paper's defaults (Sec. 4) for an n-by-n grid, h = 1/n,
  * omega from max(omega k h) = 2 pi / 10 with max k = 1 (Sec. 2.1), a 16-cell

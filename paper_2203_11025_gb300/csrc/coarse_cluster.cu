@@ -1,0 +1,377 @@
+// Coarsest-grid GMRES(m) of the SL V-cycle on a thread-block cluster per
+// right-hand side (Sec. 2.4 and 4: diagonal-Jacobi right preconditioning,
+// x0 = 0, m steps).
+//
+// The grid's rows are split over the C CTAs of a cluster (C <= 16); every CTA
+// keeps its rows of the whole Krylov basis in shared memory, so the cluster's
+// distributed shared memory holds the basis and no basis vector touches L2.
+// Stencil halos (one row above and below) and inner-product partials are read
+// from neighbouring CTAs through DSMEM after a hardware cluster barrier.
+//
+// Orthogonalisation is classical Gram-Schmidt applied twice (CGS2): per
+// Arnoldi step one batched reduction for <v_i, w> (i <= j), the update, a
+// second batched reduction for the re-orthogonalisation coefficients together
+// with ||w||^2, and ||w - V h2||^2 = ||w||^2 - ||h2||^2 (V orthonormal).  In
+// exact arithmetic this is the same Arnoldi process as modified Gram-Schmidt;
+// CGS2 needs 2 reductions per step instead of j + 2.
+//
+// The matrix-vector product uses u = D^-1 v_j:  (M D^-1 v)(p) = v(p) - (1/h^2)
+// * sum of u over the neighbours of p.  Reductions accumulate per thread and
+// per warp in T, across warps and CTAs in FP64, in a fixed order, so every CTA
+// of a cluster computes the identical Hessenberg matrix and solves the small
+// least-squares problem redundantly.  Only barriers (block and cluster) are
+// used; no CTA spins on memory written by another.
+#include <cooperative_groups.h>
+
+#include "helm_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace helm {
+
+namespace {
+
+constexpr int KT = 256;        // threads per CTA
+constexpr int KMAX = 32;       // largest restart length
+
+__device__ __forceinline__ double2 zz(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
+__device__ __forceinline__ double2 zmul2(double2 a, double2 b) { return zz(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+struct ClusterRed {
+  double2 wsum[KT / 32][KMAX + 2];   // per-warp partials
+  double2 csum[2][KMAX + 2];         // this CTA's totals, double-buffered across reductions
+};
+
+// Sum K (<= MK) complex values over the cluster.  `vals(k, x, y)` gives this thread's
+// partial of value k; all K partials are formed first and their warp reductions are
+// interleaved (independent shuffle chains).  Result, identical in every CTA, in out[k].
+template <typename T, int MK, typename F>
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed& R, int buf, int K, F vals,
+                                               double2* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T px[MK], py[MK];
+#pragma unroll
+  for (int k = 0; k < MK; ++k) {
+    px[k] = 0; py[k] = 0;
+    if (k < K) vals(k, px[k], py[k]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < MK; ++k) {
+      if (k < K) {
+        px[k] += __shfl_xor_sync(0xffffffffu, px[k], o);
+        py[k] += __shfl_xor_sync(0xffffffffu, py[k], o);
+      }
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < MK; ++k)
+      if (k < K) R.wsum[warp][k] = zz((double)px[k], (double)py[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double2 t = zz(0, 0);
+    for (int w = 0; w < KT / 32; ++w) { t.x += R.wsum[w][threadIdx.x].x; t.y += R.wsum[w][threadIdx.x].y; }
+    R.csum[buf][threadIdx.x] = t;
+  }
+  cl.sync();
+  if (threadIdx.x < K) {
+    const int C = (int)cl.num_blocks();
+    double2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      if (r < C) v[r] = cl.map_shared_rank(&R, r)->csum[buf][threadIdx.x];
+    double2 t = zz(0, 0);
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      if (r < C) { t.x += v[r].x; t.y += v[r].y; }
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+template <typename T, int PPT, int MK>
+__global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename vec2<T>::type* __restrict__ f,
+                                                       typename vec2<T>::type* __restrict__ out, int m, int rows,
+                                                       const int* gate) {
+  typedef typename vec2<T>::type T2;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int rhs = blockIdx.y;
+  if (gate && !gate[rhs]) return;                      // uniform over the cluster
+  const int nx = op.nx, ny = op.ny, N = nx * ny;
+  const int NP = rows * nx;                            // points of this CTA
+  const int p0 = rank * NP;                            // first global point
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* V = reinterpret_cast<T2*>(smem_raw);             // [(m+1)][NP]
+  T2* U = V + (size_t)(m + 1) * NP;                    // u = D^-1 v_j, [NP]
+  T2* DI = U + NP;                                     // D^-1, [NP]
+  __shared__ ClusterRed R;
+  __shared__ double2 H[(KMAX + 1) * KMAX];
+  __shared__ double2 hv[KMAX + 2];
+  __shared__ double2 ys[KMAX];
+  __shared__ double2 gg[KMAX + 1];
+  __shared__ double2 snn[KMAX];
+  __shared__ double css[KMAX];
+  __shared__ int s_k;
+  const int tid = threadIdx.x;
+  const T2* fr = f + (size_t)rhs * N + p0;
+  int buf = 0;
+
+  T2 w[PPT];
+  // D^-1 for own points; beta = ||f||
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int lp = tid + q * KT;
+    if (lp < NP) {
+      const int gp = p0 + lp, y = gp / nx, x = gp - y * nx;
+      DI[lp] = cinv(diag_at(op, x, y));
+      w[q] = fr[lp];
+    } else {
+      w[q] = czero<T2>();
+    }
+  }
+  cluster_reduce<T, MK>(cl, R, buf, 1, [&](int, T& a, T& b) {
+    a = 0; b = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) a += w[q].x * w[q].x + w[q].y * w[q].y;
+  }, hv);
+  buf ^= 1;
+  const double beta = sqrt(hv[0].x);
+  T2* outr = out + (size_t)rhs * N + p0;
+  if (!(beta > 0.0)) {
+    T2 zv = czero<T2>();
+    if (beta != beta) { zv.x = beta; zv.y = beta; }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int lp = tid + q * KT;
+      if (lp < NP) outr[lp] = zv;
+    }
+    cl.sync();   // no CTA leaves while others may still read its shared memory
+    return;
+  }
+  {
+    const T inv = (T)(1.0 / beta);
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int lp = tid + q * KT;
+      if (lp < NP) V[lp] = cscale(w[q], inv);
+    }
+  }
+  const T ih2 = op.inv_h2;
+  int k = 0;
+  for (int j = 0; j < m; ++j) {
+    const T2* vj = V + (size_t)j * NP;
+    // u = D^-1 v_j, then halo exchange
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int lp = tid + q * KT;
+      if (lp < NP) U[lp] = cmul(vj[lp], DI[lp]);
+    }
+    cl.sync();
+    const T2* Uup = rank > 0 ? cl.map_shared_rank(U, rank - 1) : nullptr;       // row above: its last row
+    const T2* Udn = rank < C - 1 ? cl.map_shared_rank(U, rank + 1) : nullptr;   // row below: its first row
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int lp = tid + q * KT;
+      if (lp >= NP) continue;
+      const int ly = lp / nx, x = lp - ly * nx;
+      T2 s = czero<T2>();
+      if (x > 0) s = cadd(s, U[lp - 1]);
+      if (x < nx - 1) s = cadd(s, U[lp + 1]);
+      if (ly > 0) s = cadd(s, U[lp - nx]);
+      else if (Uup) s = cadd(s, Uup[(rows - 1) * nx + x]);
+      if (ly < rows - 1) s = cadd(s, U[lp + nx]);
+      else if (Udn) s = cadd(s, Udn[x]);
+      T2 r = vj[lp];
+      r.x -= s.x * ih2;
+      r.y -= s.y * ih2;
+      w[q] = r;
+    }
+    // CGS pass 1: h1_i = <v_i, w>
+    cluster_reduce<T, MK>(cl, R, buf, j + 1, [&](int i, T& a, T& b) {
+      a = 0; b = 0;
+      const T2* vi = V + (size_t)i * NP;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int lp = tid + q * KT;
+        if (lp < NP) { T2 v = vi[lp]; a += v.x * w[q].x + v.y * w[q].y; b += v.x * w[q].y - v.y * w[q].x; }
+      }
+    }, hv);
+    buf ^= 1;
+    if (tid <= j) H[tid * m + j] = hv[tid];
+    for (int i = 0; i <= j; ++i) {
+      const T hx = (T)hv[i].x, hy = (T)hv[i].y;
+      const T2* vi = V + (size_t)i * NP;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int lp = tid + q * KT;
+        if (lp < NP) { T2 v = vi[lp]; w[q].x -= hx * v.x - hy * v.y; w[q].y -= hx * v.y + hy * v.x; }
+      }
+    }
+    __syncthreads();   // hv is rewritten by the next reduction
+    // CGS pass 2: h2_i = <v_i, w> and ||w||^2 in one reduction (value j+1)
+    cluster_reduce<T, MK>(cl, R, buf, j + 2, [&](int i, T& a, T& b) {
+      a = 0; b = 0;
+      if (i <= j) {
+        const T2* vi = V + (size_t)i * NP;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          const int lp = tid + q * KT;
+          if (lp < NP) { T2 v = vi[lp]; a += v.x * w[q].x + v.y * w[q].y; b += v.x * w[q].y - v.y * w[q].x; }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) a += w[q].x * w[q].x + w[q].y * w[q].y;
+      }
+    }, hv);
+    buf ^= 1;
+    double nn = hv[j + 1].x;
+    for (int i = 0; i <= j; ++i) nn -= hv[i].x * hv[i].x + hv[i].y * hv[i].y;
+    const double nrm = sqrt(nn > 0.0 ? nn : 0.0);
+    if (tid <= j) { double2 a = H[tid * m + j]; H[tid * m + j] = zz(a.x + hv[tid].x, a.y + hv[tid].y); }
+    if (tid == 0) H[(j + 1) * m + j] = zz(nrm, 0.0);
+    for (int i = 0; i <= j; ++i) {
+      const T hx = (T)hv[i].x, hy = (T)hv[i].y;
+      const T2* vi = V + (size_t)i * NP;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int lp = tid + q * KT;
+        if (lp < NP) { T2 v = vi[lp]; w[q].x -= hx * v.x - hy * v.y; w[q].y -= hx * v.y + hy * v.x; }
+      }
+    }
+    k = j + 1;
+    if (nrm == 0.0) break;                             // happy breakdown (identical in every CTA)
+    if (j + 1 < m) {
+      const T inv = (T)(1.0 / nrm);
+      T2* vn = V + (size_t)(j + 1) * NP;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        const int lp = tid + q * KT;
+        if (lp < NP) vn[lp] = cscale(w[q], inv);
+      }
+    }
+    __syncthreads();
+  }
+  // least squares by Givens rotations (thread 0 of every CTA, identical inputs)
+  if (tid == 0) {
+    gg[0] = zz(beta, 0.0);
+    for (int j = 0; j < k; ++j) {
+      for (int i = 0; i < j; ++i) {
+        double2 a = H[i * m + j], b = H[(i + 1) * m + j];
+        double2 t = zz(css[i] * a.x + (snn[i].x * b.x - snn[i].y * b.y), css[i] * a.y + (snn[i].x * b.y + snn[i].y * b.x));
+        double2 cj = zmul2(zz(snn[i].x, -snn[i].y), a);
+        H[(i + 1) * m + j] = zz(-cj.x + css[i] * b.x, -cj.y + css[i] * b.y);
+        H[i * m + j] = t;
+      }
+      double2 a = H[j * m + j], b = H[(j + 1) * m + j];
+      double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y), c;
+      double2 sv, r;
+      if (bb == 0.0) { c = 1.0; sv = zz(0, 0); r = a; }
+      else if (aa == 0.0) { c = 0.0; sv = zz(1, 0); r = b; }
+      else {
+        double t = hypot(aa, bb);
+        c = aa / t;
+        double2 ph = zz(a.x / aa, a.y / aa);
+        sv = zmul2(ph, zz(b.x / t, -b.y / t));
+        r = zz(ph.x * t, ph.y * t);
+      }
+      css[j] = c; snn[j] = sv;
+      H[j * m + j] = r;
+      H[(j + 1) * m + j] = zz(0, 0);
+      double2 gj = gg[j], sg = zmul2(zz(sv.x, -sv.y), gj);
+      gg[j + 1] = zz(-sg.x, -sg.y);
+      gg[j] = zz(c * gj.x, c * gj.y);
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double2 a = gg[i];
+      for (int l = i + 1; l < k; ++l) { double2 t = zmul2(H[i * m + l], ys[l]); a.x -= t.x; a.y -= t.y; }
+      double2 d = H[i * m + i];
+      double dd = d.x * d.x + d.y * d.y;
+      ys[i] = zz((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
+    }
+    s_k = k;
+  }
+  __syncthreads();
+  const int kk = s_k;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int lp = tid + q * KT;
+    if (lp >= NP) continue;
+    T2 a = czero<T2>();
+    for (int i = 0; i < kk; ++i) {
+      T2 yi;
+      yi.x = (T)ys[i].x; yi.y = (T)ys[i].y;
+      a = cadd(a, cmul(yi, V[(size_t)i * NP + lp]));
+    }
+    outr[lp] = cmul(a, DI[lp]);
+  }
+  cl.sync();   // keep shared memory alive until every CTA is done with remote reads
+}
+
+template <typename T, int PPT, int MK>
+bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, const int* gate, int C, int rows,
+                    size_t smem, cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  auto kern = k_coarse_cluster<T, PPT, MK>;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    configured = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, nrhs, 1);
+  cfg.blockDim = dim3(KT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, op, (const T2*)f, (T2*)out, m, rows, gate) == cudaSuccess;
+}
+
+}  // namespace
+
+// Cluster geometry: rows per CTA so that each CTA holds <= 1024 points, C <= 16, and
+// the CTA's basis fits in shared memory.  Returns false if the grid does not fit.
+template <typename T>
+bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, const int* gate,
+                                 cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  const int nx = op.nx, ny = op.ny;
+  if (m > KMAX || nx > 1024) return false;
+  int C = 0, rows = 0;
+  for (int c = 1; c <= 16 && !C; c *= 2) {     // fewest CTAs with <= 4 points per thread
+    if (ny % c) break;
+    if ((long long)(ny / c) * nx <= 4 * KT) { C = c; rows = ny / c; }
+  }
+  if (!C) return false;
+  if (m + 2 > 34) return false;
+  const int NP = rows * nx;
+  const size_t smem = ((size_t)(m + 1) + 2) * NP * sizeof(T2);
+  if (smem > 180 * 1024) return false;
+  const int ppt = (NP + KT - 1) / KT;
+  if (m + 2 <= 12) {
+    if (ppt <= 1) return launch_cluster<T, 1, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+    if (ppt <= 2) return launch_cluster<T, 2, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+    return launch_cluster<T, 4, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+  }
+  if (ppt <= 1) return launch_cluster<T, 1, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+  if (ppt <= 2) return launch_cluster<T, 2, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+  return launch_cluster<T, 4, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+}
+
+template bool launch_coarse_gmres_cluster<float>(const Op<float>&, const void*, void*, int, int, const int*,
+                                                 cudaStream_t);
+template bool launch_coarse_gmres_cluster<double>(const Op<double>&, const void*, void*, int, int, const int*,
+                                                  cudaStream_t);
+
+}  // namespace helm

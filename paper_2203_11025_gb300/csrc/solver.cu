@@ -104,6 +104,7 @@ struct helm_ctx {
   std::map<GraphKey, long long> graph_kernels;  // kernel nodes per captured cycle
   float* gam0 = nullptr;             // absorbing-layer attenuation on the fine grid (float32)
   bool fused_coarse = true;          // one-launch coarsest GMRES when the grid fits in shared memory
+  bool cluster_coarse = true;        // cluster-resident coarsest GMRES when the grid fits
 };
 
 namespace {
@@ -226,6 +227,10 @@ int coarse_gmres(helm_ctx* c, const void* f, void* out, int nrhs, const int* gat
   const size_t vstride = (size_t)nrhs * Nc;
   char* CV = (char*)W.CV;
   Op<T> op = op_on<T>(c, lc, c->d.beta);
+  if (c->cluster_coarse && launch_coarse_gmres_cluster<T>(op, f, out, nrhs, mc, gate, s)) {
+    HLAUNCH();
+    return HELM_OK;
+  }
   if (c->fused_coarse && launch_coarse_gmres_fused<T>(op, f, out, CV, vstride, nrhs, mc, gate, s)) {
     HLAUNCH();
     return HELM_OK;
@@ -510,6 +515,12 @@ void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
 }  // namespace helm
 
 namespace {
+__global__ void k_fill_pattern(float2* __restrict__ v, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long z = (i + 1) * 0x9E3779B97F4A7C15ull;
+    v[i] = make_float2((float)((z >> 40) & 0xFFFF) / 65536.f - 0.5f, (float)((z >> 20) & 0xFFFF) / 65536.f - 0.5f);
+  }
+}
 __global__ void k_sub_inplace(double2* __restrict__ e, const double2* __restrict__ xt, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double2 a = e[i], b = xt[i];
@@ -562,6 +573,7 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   helm_ctx* c = new helm_ctx();
   c->d = d;
   c->fused_coarse = !(d.flags & HELM_DESC_MULTIKERNEL_COARSE);
+  c->cluster_coarse = !(d.flags & (HELM_DESC_MULTIKERNEL_COARSE | HELM_DESC_SINGLE_CTA_COARSE));
   HCHECK(cudaGetDevice(&c->device));
   HCHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
   size_t total = 0;
@@ -787,6 +799,7 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
   const int nb = vec_blocks(N, nrhs, h->nsm);
   // active flags on, finite Hessenberg entries
   HCHECK(cudaMemsetAsync(W.fst.H, 0, (size_t)nrhs * (W.fst.m + 1) * W.fst.m * 16, s));
+  k_fill_pattern<<<1024, 256, 0, s>>>((float2*)V, (size_t)nrhs * N);   // nonzero data in v_0
   {  // a nonzero right-hand side on the coarsest level so its solve does real work
     const int lc = h->d.levels - 1;
     HCHECK(cudaMemcpyAsync(W.F[lc], V, (size_t)nrhs * level_points(h, lc) * es, cudaMemcpyDeviceToDevice, s));

@@ -66,6 +66,8 @@ struct unet_ctx {
   bool use_tc = true;
   float *bn_scale = nullptr, *bn_shift = nullptr;
   double *bn_mean = nullptr, *bn_var = nullptr;
+  float *ev_scale = nullptr, *ev_shift = nullptr;  // inference BN coefficients from running statistics
+  bool ev_dirty = true;
   int adam_t = 0;
   unet_ctx* encoder = nullptr;
   bool last_train = false;
@@ -206,7 +208,7 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
     if (c.context[l]) n->gfeat[l] = a.take<float>(M(l) * c.context[l]);
   n->uact.assign(L + 1, nullptr);
   n->fact.assign(L + 1, nullptr);
-  for (int l = 2; l <= L; ++l) {
+  for (int l = 1; l <= L; ++l) {
     const int cu = (l == L) ? w[L - 1] : 2 * w[l - 1];
     n->uact[l] = a.take<__nv_bfloat16>(M(l) * cu);
     if (c.context[l]) n->fact[l] = a.take<__nv_bfloat16>(M(l) * c.context[l]);
@@ -292,6 +294,8 @@ ConvArgs dgrad_args(const unet_ctx* n, const ConvL& cl, const float* g, int ldg,
   return c;
 }
 
+void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s);
+
 // BatchNorm (train: batch statistics, running update; eval: running statistics),
 // then optional eLU, into a BF16 slice.
 void run_bn(unet_ctx* n, const std::string& nm, const float* z, int ldz, int M, bool act, __nv_bfloat16* y, int ldy,
@@ -307,7 +311,9 @@ void run_bn(unet_ctx* n, const std::string& nm, const float* z, int ldz, int M, 
     bn_batch_stats(z, ldz, b.c, M, n->bn_mean + b.soff, n->bn_var + b.soff, n->part, n->nblk, s);
     bn_coeffs(n->bn_mean + b.soff, n->bn_var + b.soff, gamma, beta, b.c, sc, sh, rm, rv, true, M, s);
   } else {
-    bn_coeffs_eval(rm, rv, gamma, beta, b.c, sc, sh, s);
+    ensure_eval_coeffs(n, s);
+    sc = n->ev_scale + b.soff;
+    sh = n->ev_shift + b.soff;
   }
   bn_act(z, ldz, b.c, M, sc, sh, act, y, ldy, s);
 }
@@ -318,6 +324,51 @@ void run_bn_bwd(unet_ctx* n, const std::string& nm, const float* g, int ldg, con
   bn_backward(g, ldg, z, ldz, b.c, M, n->bn_mean + b.soff, n->bn_var + b.soff, n->bn_scale + b.soff,
               n->bn_shift + b.soff, act, n->P + b.goff, n->G + b.goff, n->G + b.goff + b.c, n->part, n->nblk,
               n->sums, gz, ldo, s);
+}
+
+void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s) {
+  if (!n->ev_dirty) return;
+  for (auto& b : n->bns)
+    bn_coeffs_eval(n->rstats + b.soff, n->rstats + n->nbn + b.soff, n->P + b.goff, n->P + b.goff + b.c, b.c,
+                   n->ev_scale + b.soff, n->ev_shift + b.soff, s);
+  n->ev_dirty = false;
+}
+
+// Convolution followed by BatchNorm (+ eLU) into a BF16 slice.  At inference on the
+// tensor-core path the normalisation is applied in the convolution's epilogue.
+void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bfloat16* y, int ldy, int M, bool train,
+             cudaStream_t s) {
+  if (!train && n->use_tc && conv_tc_eligible(a)) {
+    ensure_eval_coeffs(n, s);
+    const BnL& b = bn_of(n, bn);
+    a.scale = n->ev_scale + b.soff;
+    a.shift = n->ev_shift + b.soff;
+    a.ep_act = act ? 1 : 0;
+    a.ybf = y;
+    a.ldy = ldy;
+    conv_forward_tc(a, n->d_err, s);
+    return;
+  }
+  run_conv(n, a, s);
+  run_bn(n, bn, a.out, a.ldo, M, act, y, ldy, train, s);
+}
+
+// Materialise eLU of an up convolution's inputs for the tensor-core gather.
+ConvArgs act_inputs(unet_ctx* n, ConvArgs a, int l, const Src& u, const Src& f, int H, int W, int M, cudaStream_t s) {
+  if (!n->use_tc) return a;
+  ConvArgs t = a;
+  t.in_act = 0;
+  if (!conv_tc_eligible(t)) return a;
+  elu_copy_bf16((const __nv_bfloat16*)u.p, u.ld, u.c, (size_t)M, n->uact[l], u.c, s);
+  t.in0 = n->uact[l];
+  t.ld0 = u.c;
+  if (f.p) {
+    const size_t fm = f.bcast ? (size_t)H * W : (size_t)M;
+    elu_copy_bf16((const __nv_bfloat16*)f.p, f.ld, f.c, fm, n->fact[l], f.c, s);
+    t.in1 = n->fact[l];
+    t.ld1 = f.c;
+  }
+  return t;
 }
 
 int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
@@ -332,8 +383,7 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
     Src src = l == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
     const ConvL& dl = conv_of(n, "down" + std::to_string(l));
     ConvArgs a = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, n->zdown[l], w[l - 1]);
-    run_conv(n, a, s);
-    run_bn(n, "down" + std::to_string(l) + ".bn", n->zdown[l], w[l - 1], M(l), true, n->h0[l], w[l - 1], train, s);
+    conv_bn(n, a, "down" + std::to_string(l) + ".bn", true, n->h0[l], w[l - 1], M(l), train, s);
     const __nv_bfloat16* h = n->h0[l];
     int ldh = w[l - 1];
     const int nres = l == L ? c.coarse_resnets : 1;
@@ -343,18 +393,16 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
       const std::string pre = "res" + std::to_string(l) + "." + std::to_string(r);
       ConvArgs k1 = conv_args(n, conv_of(n, pre + ".k1"), Src{h, w[l - 1], ldh, false}, Src{nullptr, 0, 0, false},
                               false, Hl, Wl, n->t1[l][r], w[l - 1]);
-      run_conv(n, k1, s);
-      run_bn(n, pre + ".bn1", n->t1[l][r], w[l - 1], M(l), true, n->a1[l][r], w[l - 1], train, s);
+      conv_bn(n, k1, pre + ".bn1", true, n->a1[l][r], w[l - 1], M(l), train, s);
       ConvArgs k2 = conv_args(n, conv_of(n, pre + ".k2"), Src{n->a1[l][r], w[l - 1], w[l - 1], false},
                               Src{nullptr, 0, 0, false}, false, Hl, Wl, n->sres[l][r], w[l - 1]);
       k2.res = h; k2.ldr = ldh;
-      run_conv(n, k2, s);
       __nv_bfloat16* dst;
       int ldd;
       if (r == nres - 1 && l < L) { dst = n->cat[l] + w[l - 1]; ldd = 2 * w[l - 1]; }
       else if (r == nres - 1) { dst = n->hL; ldd = w[L - 1]; }
       else { dst = n->hres[l][r]; ldd = w[l - 1]; }
-      run_bn(n, pre + ".bn2", n->sres[l][r], w[l - 1], M(l), true, dst, ldd, train, s);
+      conv_bn(n, k2, pre + ".bn2", true, dst, ldd, M(l), train, s);
       h = dst;
       ldh = ldd;
     }
@@ -366,35 +414,22 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
     const ConvL& ul = conv_of(n, "up" + std::to_string(l));
     Src f = feat_of(n, l);
     ConvArgs a = conv_args(n, ul, u, f, true, H, W, n->zup[l], w[l - 2]);
-    if (n->use_tc) {
-      // the tensor-core gather copies raw bytes: materialise eLU(u) (and eLU(f)) first
-      ConvArgs t = a;
-      t.in_act = 0;
-      if (conv_tc_eligible(t)) {
-        elu_copy_bf16((const __nv_bfloat16*)u.p, u.ld, u.c, (size_t)M(l), n->uact[l], u.c, s);
-        t.in0 = n->uact[l]; t.ld0 = u.c;
-        if (f.p) {
-          const size_t fm = f.bcast ? (size_t)H * W : (size_t)M(l);
-          elu_copy_bf16((const __nv_bfloat16*)f.p, f.ld, f.c, fm, n->fact[l], f.c, s);
-          t.in1 = n->fact[l]; t.ld1 = f.c;
-        }
-        a = t;
-      }
-    }
-    run_conv(n, a, s);
-    run_bn(n, "up" + std::to_string(l) + ".bn", n->zup[l], w[l - 2], M(l - 1), false, n->cat[l - 1], 2 * w[l - 2],
-           train, s);
+    a = act_inputs(n, a, l, u, f, H, W, M(l), s);   // the tensor-core gather copies raw bytes
+    conv_bn(n, a, "up" + std::to_string(l) + ".bn", false, n->cat[l - 1], 2 * w[l - 2], M(l - 1), train, s);
     u = Src{n->cat[l - 1], 2 * w[l - 2], 2 * w[l - 2], false};
   }
   {
     int H, W;
     hw(1, H, W);
-    ConvArgs a = conv_args(n, conv_of(n, "up1"), u, feat_of(n, 1), true, H, W, n->out, c.out_ch);
+    Src f = feat_of(n, 1);
+    ConvArgs a = conv_args(n, conv_of(n, "up1"), u, f, true, H, W, n->out, c.out_ch);
     a.bias = n->P + n->bias_off;
-    conv_forward(a, s);
+    a = act_inputs(n, a, 1, u, f, H, W, M(1), s);
+    run_conv(n, a, s);
     f32_to_bf16(n->out, n->out_bf, (size_t)M(0) * c.out_ch, s);
   }
   n->last_train = train;
+  if (train) n->ev_dirty = true;   // running statistics moved
   UCHECK(cudaGetLastError());
   return HELM_OK;
 }
@@ -570,7 +605,7 @@ static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool ad
     if (cs != cudaStreamCaptureStatusNone) { set_error("U-Net workspace not prepared before capture"); return HELM_EINVAL; }
     UTRY(ensure_ws(n, nrhs, ny, nx));
   }
-  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, 4, n->scale, gate, s);
+  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, 4, n->scale, n->part, gate, s);
   UTRY(forward_impl(n, false, s));
   write_output(n->out, real_bytes == 8, nrhs, ny, nx, n->scale, e, add, gate, s);
   UCHECK(cudaGetLastError());
@@ -612,7 +647,11 @@ int unet_prepare_impl(helm_ctx* hc, void* netp, int nrhs) {
   double h, gmax;
   const float *k2f, *gam;
   helm_geometry(hc, &nx, &ny, &h, &abc_w, &gmax, &k2f, &gam);
-  return ensure_ws(n, nrhs, ny, nx);
+  UTRY(ensure_ws(n, nrhs, ny, nx));
+  ensure_eval_coeffs(n, 0);
+  if (n->encoder) ensure_eval_coeffs(n->encoder, 0);
+  UCHECK(cudaDeviceSynchronize());
+  return HELM_OK;
 }
 
 // ===========================================================================
@@ -662,6 +701,8 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   UCHECK(cudaMalloc(&n->bn_scale, nb * 4));
   UCHECK(cudaMalloc(&n->bn_shift, nb * 4));
   UCHECK(cudaMalloc(&n->bn_mean, nb * 8));
+  UCHECK(cudaMalloc(&n->ev_scale, nb * 4));
+  UCHECK(cudaMalloc(&n->ev_shift, nb * 4));
   UCHECK(cudaMalloc(&n->bn_var, nb * 8));
   UCHECK(cudaMemset(n->G, 0, np * 4));
   UCHECK(cudaMemset(n->M1, 0, np * 4));
@@ -706,7 +747,8 @@ void unet_destroy(unet_t n) {
   free_ws(n);
   for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb,
                   (void*)n->d_err, (void*)n->rstats,
-                  (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, n->tmp_e})
+                  (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
+                  (void*)n->ev_shift, n->tmp_e})
     if (p) cudaFree(p);
   delete n;
 }
@@ -722,6 +764,7 @@ int unet_set_params(unet_t n, const float* host, long long cnt) {
   if (!n || !host || cnt != (long long)n->nparams) { set_error("bad parameter vector"); return HELM_EINVAL; }
   UCHECK(cudaMemcpy(n->P, host, cnt * 4, cudaMemcpyHostToDevice));
   refresh_bf16(n, 0);
+  n->ev_dirty = true;
   UCHECK(cudaDeviceSynchronize());
   return HELM_OK;
 }
@@ -733,6 +776,7 @@ int unet_get_params(unet_t n, float* host, long long cnt) {
 int unet_set_bn_stats(unet_t n, const float* host, long long cnt) {
   if (!n || !host || cnt != 2 * (long long)n->nbn) { set_error("bad BN vector"); return HELM_EINVAL; }
   UCHECK(cudaMemcpy(n->rstats, host, cnt * 4, cudaMemcpyHostToDevice));
+  n->ev_dirty = true;
   return HELM_OK;
 }
 int unet_get_bn_stats(unet_t n, float* host, long long cnt) {
@@ -767,17 +811,13 @@ int unet_time_layer(unet_t n, int layer, int reps, helm_stream_t stream, float* 
                   n->t1[lvl][0], w[lvl - 1]);
   } else {
     H = n->ny >> lvl; W = n->nx >> lvl;
-    if (lvl >= 2) {
-      const int cu = lvl == L ? w[L - 1] : 2 * w[lvl - 1];
-      Src u{n->uact[lvl], cu, cu, false};
-      Src f = feat_of(n, lvl);
-      if (f.p) f = Src{n->fact[lvl], f.c, f.c, f.bcast};
-      a = conv_args(n, cl, u, f, false, H, W, n->zup[lvl], w[lvl - 2]);
-      if (!(n->use_tc && conv_tc_eligible(a))) a.in_act = 1;
-    } else {
-      Src u = L > 1 ? Src{n->cat[1], 2 * w[0], 2 * w[0], false} : Src{n->hL, w[0], w[0], false};
-      a = conv_args(n, cl, u, feat_of(n, 1), true, H, W, n->out, c.out_ch);
-    }
+    const int cu = lvl == L ? w[L - 1] : 2 * w[lvl - 1];
+    Src u{n->uact[lvl], cu, cu, false};
+    Src f = feat_of(n, lvl);
+    if (f.p) f = Src{n->fact[lvl], f.c, f.c, f.bcast};
+    a = conv_args(n, cl, u, f, false, H, W, lvl >= 2 ? n->zup[lvl] : n->out, lvl >= 2 ? w[lvl - 2] : c.out_ch);
+    if (lvl == 1) a.bias = n->P + n->bias_off;
+    if (!(n->use_tc && conv_tc_eligible(a))) a.in_act = 1;
   }
   const double taps_eff = cl.kind == 2 ? (double)cl.k * cl.k / 4.0 : (double)cl.k * cl.k;
   *flops = 2.0 * (double)n->B * a.Ho * a.Wo * taps_eff * cl.cin * cl.cout;
@@ -865,6 +905,7 @@ int unet_adam_step(unet_t n, float lr, float b1, float b2, float eps, helm_strea
     m->adam_t += 1;
     adam_update(m->P, m->G, m->M1, m->M2, m->nparams, lr, b1, b2, eps, m->adam_t, s);
     refresh_bf16(m, s);
+    m->ev_dirty = true;
   }
   UCHECK(cudaGetLastError());
   return HELM_OK;

@@ -27,6 +27,9 @@ struct ConvArgs {
   float* out; int ldo;
   const float* bias;                 // per output channel, may be null
   const __nv_bfloat16* res; int ldr; // residual added to the output, may be null
+  // fused inference BatchNorm epilogue (tensor-core path only): y = act((conv + res) * scale + shift)
+  const float* scale; const float* shift; int ep_act;
+  __nv_bfloat16* ybf; int ldy;       // BF16 destination; when set, `out` is not written
 };
 
 void conv_forward(const ConvArgs& a, cudaStream_t s);
@@ -59,7 +62,7 @@ void adam_update(float* p, const float* g, float* m1, float* m2, size_t n, float
                  int t, cudaStream_t s);
 void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, const int* gate, cudaStream_t s);
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s);
 void write_output(const float* out, bool fp64, int B, int ny, int nx, const float* sc, void* e, bool add,
                   const int* gate, cudaStream_t s);
 void gamma_field(int ny, int nx, int width, float gmax, float* g, cudaStream_t s);

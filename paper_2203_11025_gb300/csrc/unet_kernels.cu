@@ -439,18 +439,22 @@ __global__ void k_f32_to_bf16(const float* __restrict__ s, __nv_bfloat16* __rest
 }
 
 // Network input from complex residuals (Sec. 3.4): channels (Re, Im) of h^2 r / s with
-// s = RMS(h^2 r) per sample, then kappa^2 and gamma.  `sc` receives s.
+// s = RMS(h^2 r) per sample, then kappa^2 and gamma.  Two passes over many blocks:
+// per-block partial sums of |r|^2, then every block of the writer sums its sample's
+// partials (fixed order) and writes the 8-channel BF16 input (channels 4..7 zero).
+constexpr int kInBlocks = 64;
+
 template <typename T2>
-__global__ void __launch_bounds__(256) k_make_input(const T2* __restrict__ r, int ny, int nx, double h2,
-                                                    const float* __restrict__ k2, const float* __restrict__ gam,
-                                                    __nv_bfloat16* __restrict__ x, int ldx, float* __restrict__ sc,
-                                                    const int* gate) {
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(256) k_input_partial(const T2* __restrict__ r, int N, float* __restrict__ part,
+                                                       const int* gate) {
+  const int b = blockIdx.y;
   if (gate && !gate[b]) return;
-  const int N = nx * ny;
   const T2* rb = r + (size_t)b * N;
   float s = 0.f;
-  for (int p = threadIdx.x; p < N; p += blockDim.x) { T2 v = rb[p]; s += (float)(v.x * v.x + v.y * v.y); }
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
+    T2 v = rb[p];
+    s += (float)(v.x * v.x + v.y * v.y);
+  }
   __shared__ float sm[256];
   sm[threadIdx.x] = s;
   __syncthreads();
@@ -458,17 +462,35 @@ __global__ void __launch_bounds__(256) k_make_input(const T2* __restrict__ r, in
     if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
     __syncthreads();
   }
-  const float rms = sqrtf(sm[0] / N) * (float)h2;
-  const float scale = rms > 0.f ? rms : 1.f;
-  if (threadIdx.x == 0) sc[b] = scale;
-  const float f = (float)h2 / scale;
-  for (int p = threadIdx.x; p < N; p += blockDim.x) {
+  if (threadIdx.x == 0) part[b * kInBlocks + blockIdx.x] = sm[0];
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, int N, double h2,
+                                                     const float* __restrict__ k2, const float* __restrict__ gam,
+                                                     const float* __restrict__ part, __nv_bfloat16* __restrict__ x,
+                                                     int ldx, float* __restrict__ sc, const int* gate) {
+  const int b = blockIdx.y;
+  if (gate && !gate[b]) return;
+  __shared__ float s_scale;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kInBlocks; ++i) t += part[b * kInBlocks + i];
+    const float rms = (float)(sqrt(t / N) * h2);
+    s_scale = rms > 0.f ? rms : 1.f;
+    if (blockIdx.x == 0) sc[b] = s_scale;
+  }
+  __syncthreads();
+  const float f = (float)h2 / s_scale;
+  const T2* rb = r + (size_t)b * N;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     T2 v = rb[p];
     __nv_bfloat16* o = x + ((size_t)b * N + p) * ldx;
     o[0] = __float2bfloat16_rn((float)v.x * f);
     o[1] = __float2bfloat16_rn((float)v.y * f);
     o[2] = __float2bfloat16_rn(k2[p]);
     o[3] = __float2bfloat16_rn(gam[p]);
+    for (int c = 4; c < ldx; ++c) o[c] = __float2bfloat16_rn(0.f);
   }
 }
 
@@ -732,9 +754,16 @@ void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s)
 }
 
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, const int* gate, cudaStream_t s) {
-  if (fp64) k_make_input<double2><<<B, 256, 0, s>>>((const double2*)r, ny, nx, h * h, k2, gam, x, ldx, sc, gate);
-  else k_make_input<float2><<<B, 256, 0, s>>>((const float2*)r, ny, nx, h * h, k2, gam, x, ldx, sc, gate);
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s) {
+  const int N = nx * ny;
+  const dim3 grid(kInBlocks, B);
+  if (fp64) {
+    k_input_partial<double2><<<grid, 256, 0, s>>>((const double2*)r, N, part, gate);
+    k_input_write<double2><<<grid, 256, 0, s>>>((const double2*)r, N, h * h, k2, gam, part, x, ldx, sc, gate);
+  } else {
+    k_input_partial<float2><<<grid, 256, 0, s>>>((const float2*)r, N, part, gate);
+    k_input_write<float2><<<grid, 256, 0, s>>>((const float2*)r, N, h * h, k2, gam, part, x, ldx, sc, gate);
+  }
 }
 
 void write_output(const float* out, bool fp64, int B, int ny, int nx, const float* sc, void* e, bool add,

@@ -20,7 +20,7 @@ HELM_OP_A, HELM_OP_M = 0, 1
 HELM_C32, HELM_C64 = 0, 1
 HELM_PREC_NONE, HELM_PREC_V, HELM_PREC_JU, HELM_PREC_VU = 0, 1, 2, 3
 HELM_FLAG_X0_ZERO, HELM_FLAG_HOST_IO, HELM_FLAG_NO_GRAPH, HELM_FLAG_FP64 = 1, 2, 4, 8
-HELM_DESC_MULTIKERNEL_COARSE = 1
+HELM_DESC_MULTIKERNEL_COARSE, HELM_DESC_SINGLE_CTA_COARSE = 1, 2
 
 # Every symbol include/helm.h declares (checked by the CPU test suite).
 ABI_SYMBOLS = [

@@ -1,0 +1,51 @@
+"""Small, self-contained GPU cases for profiling single kernels (ncu), e.g.
+
+  python -m paper_2203_11025_gb300.profcase unet 256 8     # one U-Net forward, 8 images of 256^2
+  python -m paper_2203_11025_gb300.profcase coarse 256 8   # one coarsest-grid solve (fine grid 256^2, 8 RHS)
+  python -m paper_2203_11025_gb300.profcase layers 256 8   # per-layer times of the U-Net forward
+
+Inputs are seeded and synthetic; nothing here checks results (the tests do).
+"""
+from __future__ import annotations
+
+import sys
+
+
+def main(argv):
+    import numpy as np
+    import torch
+
+    from paper_2203_11025_gb300 import lib, synth
+    what = argv[1] if len(argv) > 1 else "unet"
+    n = int(argv[2]) if len(argv) > 2 else 256
+    b = int(argv[3]) if len(argv) > 3 else 8
+    if what in ("unet", "layers"):
+        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=1)
+        x = torch.from_numpy(np.random.default_rng(0).standard_normal((b, n, n, 4)).astype(np.float32)).cuda()
+        net.forward(x)
+        torch.cuda.synchronize()
+        if what == "layers":
+            names = []
+            w = [net.cfg.widths[i] for i in range(net.cfg.levels)]
+            for l in range(1, len(w) + 1):
+                names.append(f"down{l}")
+                for r in range(net.cfg.coarse_resnets if l == len(w) else 1):
+                    names += [f"res{l}.{r}.k1", f"res{l}.{r}.k2"]
+            names += [f"up{l}" for l in range(len(w), 0, -1)]
+            tot = 0.0
+            for i, nm in enumerate(names):
+                ms, fl, tc = net.time_layer(i, reps=10)
+                tot += ms
+                print(f"{nm:12s} {ms * 1e3:8.1f} us {fl / ms / 1e9:7.1f} TFLOP/s {'tc' if tc else 'cuda-core'}")
+            print(f"total {tot * 1e3:.1f} us")
+    elif what == "coarse":
+        k2 = synth.grf_kappa2(n, n, 1000)
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        ms, _ = hz.time_kernel(5, b, reps=3)
+        print(f"coarse solve {ms * 1e3:.1f} us")
+    else:
+        raise SystemExit(f"unknown case {what}")
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -92,10 +92,14 @@ def test_transfer_parity(lib, dtype, tol):
     assert relerr(out, xf + H.prolong_bilinear(e, 48, 80)) < tol
 
 
-@pytest.mark.parametrize("multikernel", [0, 1])
+COARSE_PATHS = [0, 1, 2]   # cluster (default), multi-kernel, one CTA per right-hand side
+
+
+@pytest.mark.parametrize("path", COARSE_PATHS)
+@pytest.mark.parametrize("shape", [(128, 96), (256, 256), (64, 256)])
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-11), (torch.complex64, 2e-5)])
-def test_coarse_gmres_parity(lib, dtype, tol, multikernel):
-    hz, prob = make(lib, 128, 96, abc=16, flags=multikernel * lib.HELM_DESC_MULTIKERNEL_COARSE)
+def test_coarse_gmres_parity(lib, dtype, tol, path, shape):
+    hz, prob = make(lib, shape[0], shape[1], abc=16, flags=path)
     lc = prob.hierarchy[-1]
     f = crandn(10, (4, lc.ny, lc.nx))
     f[2] = 0.0  # a zero right-hand side returns zero
@@ -108,10 +112,10 @@ def test_coarse_gmres_parity(lib, dtype, tol, multikernel):
             assert relerr(x[k], ref) < tol
 
 
-@pytest.mark.parametrize("ny,nx,multikernel", [(64, 64, 0), (96, 160, 0), (96, 160, 1)])
+@pytest.mark.parametrize("ny,nx,path", [(64, 64, 0), (96, 160, 0), (96, 160, 1), (96, 160, 2), (256, 256, 0)])
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-11), (torch.complex64, 1e-4)])
-def test_vcycle_parity_zero_guess(lib, ny, nx, multikernel, dtype, tol):
-    hz, prob = make(lib, ny, nx, abc=16, flags=multikernel * lib.HELM_DESC_MULTIKERNEL_COARSE)
+def test_vcycle_parity_zero_guess(lib, ny, nx, path, dtype, tol):
+    hz, prob = make(lib, ny, nx, abc=16, flags=path)
     f = crandn(11, (3, ny, nx))
     z = hz.vcycle(dev(f, dtype)).cpu().numpy()
     for k in range(3):
