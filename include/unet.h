@@ -40,9 +40,10 @@ typedef struct {
   int context[9];          /* solver with encoder: channels of f^(0..levels), else all 0    */
   int flags;               /* UNET_FLAG_*                                                   */
 } unet_cfg;
-/* Run every convolution on CUDA cores (FP32 FMA) instead of the tcgen05 tensor-core
- * kernel; same arithmetic up to summation order (cross-checking). */
-enum { UNET_FLAG_SIMT = 1 };
+/* Implementation switches (cross-checking; same arithmetic up to summation order):
+ * UNET_FLAG_SIMT runs every convolution on CUDA cores (FP32 FMA); UNET_FLAG_NO_TMA
+ * keeps the tcgen05 kernel but stages operands with cp.async instead of TMA. */
+enum { UNET_FLAG_SIMT = 1, UNET_FLAG_NO_TMA = 2 };
 
 enum { UNET_STANDALONE = 0, UNET_ENCODER = 1, UNET_SOLVER = 2 };
 

@@ -42,33 +42,22 @@ struct ClusterRed {
   double2 csum[2][KMAX + 2];         // this CTA's totals, double-buffered across reductions
 };
 
-// Sum K (<= MK) complex values over the cluster.  `vals(k, x, y)` gives this thread's
-// partial of value k; all K partials are formed first and their warp reductions are
-// interleaved (independent shuffle chains).  Result, identical in every CTA, in out[k].
+// Sum K complex values over the cluster: `vals(k, x, y)` gives this thread's partial
+// of value k (already summed over its points).  Result, identical in every CTA, in out[k].
+// (An all-values-in-registers variant with interleaved shuffles measured slower.)
 template <typename T, int MK, typename F>
 __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed& R, int buf, int K, F vals,
                                                double2* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T px[MK], py[MK];
+  for (int k = 0; k < K; ++k) {
+    T x, y;
+    vals(k, x, y);
 #pragma unroll
-  for (int k = 0; k < MK; ++k) {
-    px[k] = 0; py[k] = 0;
-    if (k < K) vals(k, px[k], py[k]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int k = 0; k < MK; ++k) {
-      if (k < K) {
-        px[k] += __shfl_xor_sync(0xffffffffu, px[k], o);
-        py[k] += __shfl_xor_sync(0xffffffffu, py[k], o);
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
     }
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < MK; ++k)
-      if (k < K) R.wsum[warp][k] = zz((double)px[k], (double)py[k]);
+    if (lane == 0) R.wsum[warp][k] = zz((double)x, (double)y);
   }
   __syncthreads();
   if (threadIdx.x < K) {
@@ -78,15 +67,13 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed
   }
   cl.sync();
   if (threadIdx.x < K) {
-    const int C = (int)cl.num_blocks();
-    double2 v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r)
-      if (r < C) v[r] = cl.map_shared_rank(&R, r)->csum[buf][threadIdx.x];
     double2 t = zz(0, 0);
-#pragma unroll
-    for (int r = 0; r < 16; ++r)
-      if (r < C) { t.x += v[r].x; t.y += v[r].y; }
+    const int C = (int)cl.num_blocks();
+    for (int r = 0; r < C; ++r) {
+      const ClusterRed* rem = cl.map_shared_rank(&R, r);
+      const double2 v = rem->csum[buf][threadIdx.x];
+      t.x += v.x; t.y += v.y;
+    }
     out[threadIdx.x] = t;
   }
   __syncthreads();
@@ -349,9 +336,12 @@ bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int 
   const int nx = op.nx, ny = op.ny;
   if (m > KMAX || nx > 1024) return false;
   int C = 0, rows = 0;
-  for (int c = 1; c <= 16 && !C; c *= 2) {     // fewest CTAs with <= 4 points per thread
-    if (ny % c) break;
-    if ((long long)(ny / c) * nx <= 4 * KT) { C = c; rows = ny / c; }
+  for (int target : {2 * KT, 4 * KT}) {       // prefer <= 2 points per thread (more SMs per solve)
+    for (int c = 1; c <= 16 && !C; c *= 2) {
+      if (ny % c) break;
+      if ((long long)(ny / c) * nx <= target) { C = c; rows = ny / c; }
+    }
+    if (C) break;
   }
   if (!C) return false;
   if (m + 2 > 34) return false;

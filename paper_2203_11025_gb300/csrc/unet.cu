@@ -37,7 +37,14 @@ using namespace helm;
 
 namespace {
 
-struct ConvL { std::string name; int kind; int k, cin, cout; size_t woff; };  // kind 0 down, 1 same, 2 up
+struct ConvL {
+  std::string name;
+  int kind;                 // 0 down (5x5 stride 2), 1 same (3x3), 2 up (5x5 stride-2 transposed)
+  int k, cin, cout;
+  size_t woff;              // offset in the flat parameter vector
+  int c0, c1;               // input split: main source, encoder context
+  size_t wpoff;             // offset of the padded weight copy (TMA path)
+};
 struct BnL { std::string name; int c; size_t goff; size_t soff; };
 
 // A device arena of float-aligned pieces.
@@ -62,6 +69,9 @@ struct unet_ctx {
   float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr, *rstats = nullptr;
   __nv_bfloat16* Wb = nullptr;
   __nv_bfloat16* WTb = nullptr;                    // K-major weight copies (tensor-core path)
+  __nv_bfloat16* WPb = nullptr;                    // padded K-major weight copies (TMA path)
+  size_t nwp = 0;
+  bool use_tma = true;
   int* d_err = nullptr;                            // failure record of the tensor-core kernel
   bool use_tc = true;
   float *bn_scale = nullptr, *bn_shift = nullptr;
@@ -109,22 +119,24 @@ void build_layout(unet_ctx* n) {
   const int L = c.levels;
   n->L = L;
   size_t off = 0, soff = 0;
-  auto conv = [&](const std::string& nm, int kind, int k, int ci, int co) {
-    n->convs.push_back({nm, kind, k, ci, co, off});
+  size_t wpo = 0;
+  auto conv = [&](const std::string& nm, int kind, int k, int ci, int co, int c1) {
+    n->convs.push_back({nm, kind, k, ci, co, off, ci - c1, c1, wpo});
     off += (size_t)k * k * ci * co;
+    wpo += conv_tma_weight_elems(k, ci - c1, c1, co);
   };
   std::vector<std::pair<std::string, int>> bnl;
   int cin = c.in_ch;
   for (int l = 1; l <= L; ++l) {
     const int w = c.widths[l - 1];
-    conv("down" + std::to_string(l), 0, 5, cin + c.context[l - 1], w);
+    conv("down" + std::to_string(l), 0, 5, cin + c.context[l - 1], w, c.context[l - 1]);
     bnl.push_back({"down" + std::to_string(l) + ".bn", w});
     const int nres = l == L ? c.coarse_resnets : 1;
     for (int r = 0; r < nres; ++r) {
       std::string pre = "res" + std::to_string(l) + "." + std::to_string(r);
-      conv(pre + ".k1", 1, 3, w, w);
+      conv(pre + ".k1", 1, 3, w, w, 0);
       bnl.push_back({pre + ".bn1", w});
-      conv(pre + ".k2", 1, 3, w, w);
+      conv(pre + ".k2", 1, 3, w, w, 0);
       bnl.push_back({pre + ".bn2", w});
     }
     cin = w;
@@ -132,11 +144,12 @@ void build_layout(unet_ctx* n) {
   int ucin = c.widths[L - 1];
   for (int l = L; l >= 2; --l) {
     const int co = c.widths[l - 2];
-    conv("up" + std::to_string(l), 2, 5, ucin + c.context[l], co);
+    conv("up" + std::to_string(l), 2, 5, ucin + c.context[l], co, c.context[l]);
     bnl.push_back({"up" + std::to_string(l) + ".bn", co});
     ucin = 2 * co;
   }
-  conv("up1", 2, 5, ucin + c.context[1], c.out_ch);
+  conv("up1", 2, 5, ucin + c.context[1], c.out_ch, c.context[1]);
+  n->nwp = wpo;
   n->bias_off = off;
   off += c.out_ch;
   for (auto& b : bnl) {
@@ -269,11 +282,14 @@ ConvArgs conv_args(const unet_ctx* n, const ConvL& cl, Src a, Src b, bool act, i
   c.W = n->Wb + cl.woff;
   c.wst = (long long)cl.cin * cl.cout; c.wsk = cl.cout; c.wsn = 1;
   c.WT = n->WTb + cl.woff;
+  // the padded copy matches the layer's fixed (main, context) split
+  c.WP = (a.c == cl.c0 && (b.p ? b.c : 0) == cl.c1) ? n->WPb + cl.wpoff : nullptr;
   c.out = out; c.ldo = ldo;
   return c;
 }
 
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) return;
   if (n->use_tc && conv_tc_eligible(a)) conv_forward_tc(a, n->d_err, s);
   else conv_forward(a, s);
 }
@@ -346,7 +362,7 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     a.ep_act = act ? 1 : 0;
     a.ybf = y;
     a.ldy = ldy;
-    conv_forward_tc(a, n->d_err, s);
+    if (!(n->use_tma && conv_forward_tma(a, n->d_err, s))) conv_forward_tc(a, n->d_err, s);
     return;
   }
   run_conv(n, a, s);
@@ -568,7 +584,10 @@ int backward_encoder(unet_ctx* solver, cudaStream_t s) {
 
 void refresh_bf16(unet_ctx* n, cudaStream_t s) {
   f32_to_bf16(n->P, n->Wb, n->nparams, s);
-  for (auto& cl : n->convs) weights_kmajor(n->P + cl.woff, n->WTb + cl.woff, cl.k * cl.k, cl.cin, cl.cout, s);
+  for (auto& cl : n->convs) {
+    weights_kmajor(n->P + cl.woff, n->WTb + cl.woff, cl.k * cl.k, cl.cin, cl.cout, s);
+    conv_tma_weights(n->P + cl.woff, n->WPb + cl.wpoff, cl.k, cl.c0, cl.c1, cl.cout, s);
+  }
 }
 
 }  // namespace
@@ -694,9 +713,11 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   UCHECK(cudaMalloc(&n->M2, np * 4));
   UCHECK(cudaMalloc(&n->Wb, np * 2));
   UCHECK(cudaMalloc(&n->WTb, np * 2));
+  UCHECK(cudaMalloc(&n->WPb, n->nwp * 2));
   UCHECK(cudaMalloc(&n->d_err, sizeof(int)));
   UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
   n->use_tc = !(cfg->flags & UNET_FLAG_SIMT);
+  n->use_tma = !(cfg->flags & UNET_FLAG_NO_TMA);
   UCHECK(cudaMalloc(&n->rstats, 2 * nb * 4));
   UCHECK(cudaMalloc(&n->bn_scale, nb * 4));
   UCHECK(cudaMalloc(&n->bn_shift, nb * 4));
@@ -745,7 +766,7 @@ void unet_destroy(unet_t n) {
   if (!n) return;
   cudaDeviceSynchronize();
   free_ws(n);
-  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb,
+  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb,
                   (void*)n->d_err, (void*)n->rstats,
                   (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
                   (void*)n->ev_shift, n->tmp_e})

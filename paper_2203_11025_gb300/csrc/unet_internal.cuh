@@ -24,6 +24,7 @@ struct ConvArgs {
   int k, stride, pad, transposed;
   const __nv_bfloat16* W; long long wst, wsk, wsn;
   const __nv_bfloat16* WT;           // K-major copy [cout][tap * cin + ci] for the tensor-core path, or null
+  const __nv_bfloat16* WP;           // padded K-major copy [cout][tap][64-channel chunks] for the TMA path, or null
   float* out; int ldo;
   const float* bias;                 // per output channel, may be null
   const __nv_bfloat16* res; int ldr; // residual added to the output, may be null
@@ -38,6 +39,10 @@ void conv_forward(const ConvArgs& a, cudaStream_t s);
 bool conv_tc_eligible(const ConvArgs& a);
 void conv_forward_tc(const ConvArgs& a, int* err, cudaStream_t s);
 void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int cout, cudaStream_t s);
+// TMA-fed tensor-core path (conv_tma.cu); false if the convolution does not fit it.
+bool conv_forward_tma(const ConvArgs& a, int* err, cudaStream_t s);
+size_t conv_tma_weight_elems(int k, int c0, int c1, int cout);
+void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, int cout, cudaStream_t s);
 void elu_copy_bf16(const __nv_bfloat16* src, int lds, int C, size_t M, __nv_bfloat16* dst, int ldd, cudaStream_t s);
 void conv_wgrad(const ConvArgs& a, const float* G, int ldg, float* gW, cudaStream_t s);
 void bn_batch_stats(const float* z, int ldz, int C, int M, double* mean, double* var, float* part, int nblk,

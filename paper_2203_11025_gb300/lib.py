@@ -34,7 +34,7 @@ ABI_SYMBOLS = [
     "unet_mse", "unet_adam_step", "unet_attach_encoder", "unet_encode", "unet_precond", "helm_gen_pairs",
     "unet_make_batch", "unet_status", "unet_time_layer",
 ]
-UNET_FLAG_SIMT = 1
+UNET_FLAG_SIMT, UNET_FLAG_NO_TMA = 1, 2
 UNET_STANDALONE, UNET_ENCODER, UNET_SOLVER = 0, 1, 2
 
 

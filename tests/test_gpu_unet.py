@@ -36,9 +36,10 @@ def nrel(a, b):
 
 
 def make_cfgs(lib, widths=(8, 16), resnets=2, in_ch=4, out_ch=2, context=None, simt=False):
+    """simt: False (tensor cores fed by TMA), True (CUDA cores) or "cpasync" (tensor cores fed by cp.async)."""
     c = lib.unet_cfg()
     c.in_ch, c.out_ch, c.levels, c.coarse_resnets = in_ch, out_ch, len(widths), resnets
-    c.flags = lib.UNET_FLAG_SIMT if simt else 0
+    c.flags = {False: 0, True: lib.UNET_FLAG_SIMT, "cpasync": lib.UNET_FLAG_NO_TMA}[simt]
     for i, w in enumerate(widths):
         c.widths[i] = w
     if context:
@@ -81,8 +82,8 @@ def test_init_matches_oracle_init(lib):
     assert np.allclose(got, ref, rtol=1e-6, atol=1e-7)
 
 
-@pytest.mark.parametrize("simt", [False, True])
-@pytest.mark.parametrize("ny,nx,B", [(32, 48, 3), (16, 16, 1)])
+@pytest.mark.parametrize("simt", [False, True, "cpasync"])
+@pytest.mark.parametrize("ny,nx,B", [(32, 48, 3), (16, 16, 1), (64, 64, 2)])
 def test_forward_inference_parity(lib, ny, nx, B, simt):
     c, oc = make_cfgs(lib, widths=(16, 32), simt=simt)
     net = lib.UNet(c, seed=1)
@@ -94,13 +95,13 @@ def test_forward_inference_parity(lib, ny, nx, B, simt):
     assert nrel(out, ref) < 2e-2
 
 
-@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("simt", [False, True, "cpasync"])
 def test_forward_default_architecture(lib, simt):
     """Full-width network (32..256 channels): every layer type runs on the tensor-core
     kernel (down 5x5 stride 2, ResNet 3x3, transposed 5x5 per output phase) except the
     4-channel input and 2-channel output layers."""
     c = lib.unet_cfg_default(lib.UNET_STANDALONE)
-    c.flags = lib.UNET_FLAG_SIMT if simt else 0
+    c.flags = {False: 0, True: lib.UNET_FLAG_SIMT, "cpasync": lib.UNET_FLAG_NO_TMA}[simt]
     oc = U.UNetConfig()
     net = lib.UNet(c, seed=3)
     P, S = randomise(lib, net, oc, 3)
@@ -111,16 +112,19 @@ def test_forward_default_architecture(lib, simt):
     assert nrel(out, ref) < 3e-2
 
 
-def test_tensor_core_and_cuda_core_paths_agree(lib):
-    c = lib.unet_cfg_default(lib.UNET_STANDALONE)
-    a = lib.UNet(c, seed=21)
-    c2 = lib.unet_cfg_default(lib.UNET_STANDALONE)
-    c2.flags = lib.UNET_FLAG_SIMT
-    b = lib.UNet(c2, seed=21)
-    x = cuda(np.random.default_rng(22).standard_normal((3, 96, 64, 4)))
-    ya, yb = a.forward(x).cpu().numpy(), b.forward(x).cpu().numpy()
-    assert not a.status()
-    assert nrel(ya, yb) < 1e-2
+@pytest.mark.parametrize("shape", [(3, 96, 64), (2, 256, 256), (5, 32, 32)])
+def test_tensor_core_and_cuda_core_paths_agree(lib, shape):
+    """TMA-fed and cp.async-fed tensor-core paths and the CUDA-core path agree (96x64 has
+    non-power-of-two tiles, so TMA declines and the cp.async path runs there)."""
+    outs = []
+    for flags in (0, lib.UNET_FLAG_NO_TMA, lib.UNET_FLAG_SIMT):
+        c = lib.unet_cfg_default(lib.UNET_STANDALONE)
+        c.flags = flags
+        net = lib.UNet(c, seed=21)
+        x = cuda(np.random.default_rng(22).standard_normal(shape + (4,)))
+        outs.append(net.forward(x).cpu().numpy())
+        assert not net.status()
+    assert nrel(outs[0], outs[2]) < 1e-2 and nrel(outs[1], outs[2]) < 1e-2
 
 
 def test_train_forward_backward_parity(lib):
