@@ -212,11 +212,17 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     P = {"M_VU": (lib.HELM_PREC_VU, net), "M_V": (lib.HELM_PREC_V, None), "M_JU": (lib.HELM_PREC_JU, net)}
 
+    # M_JU (a comparison column) may stall on some right-hand sides: it is capped and
+    # its converged count reported; the headline M_VU and the M_V baseline must converge
+    MAXIT = {"M_VU": 20000, "M_V": 20000, "M_JU": 3000}
+
     def solve(name):
         pc, nt = P[name]
-        _, info = hz.fgmres(bd, x, precond=pc, net=nt, tol=TOL, maxit=20000, restart=RESTART,
+        _, info = hz.fgmres(bd, x, precond=pc, net=nt, tol=TOL, maxit=MAXIT[name], restart=RESTART,
                             flags=lib.HELM_FLAG_X0_ZERO)
         return info
+
+    converged = {}
 
     def timed(name, steps):
         tot, its, launches = 0.0, [], []
@@ -232,7 +238,9 @@ def run_ours(args):
             tot += e0.elapsed_time(e1)
             its.append(info["iters_max"])
             launches.append(info["launches"])
-            assert info["status"] == 0 and info["relres_max"] <= TOL, (name, info)
+            converged[name] = int(sum(r <= TOL for r in info["relres"]))
+            if name != "M_JU":
+                assert info["status"] == 0 and info["relres_max"] <= TOL, (name, info)
         return tot / steps, max(its), int(sum(launches))
 
     for name in P:
@@ -295,6 +303,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "c32+f64 Krylov, bf16 U-Net", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precond": "M_VU", "nrhs": NRHS, "grid": N_GRID,
                        "fgmres_iters": {"M_VU": it_vu, "M_V": it_v, "M_JU": it_ju},
+                       "converged_rhs": converged, "maxit": MAXIT,
                        "solve_s": {"M_VU": ms / 1e3, "M_V": ms_v / 1e3, "M_JU": ms_ju / 1e3},
                        "speedup_vs_plain_sl": ms_v / ms, "training": tinfo,
                        "l2": "flushed between timed steps (256 MB write)",

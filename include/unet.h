@@ -114,9 +114,12 @@ int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int coun
 
 /* Measurement hook (no counterpart in the paper): time one convolution layer
  * (index in layer order) of the last forward's geometry `reps` times with CUDA
- * events on `stream`; *ms = mean device time per launch, *flops = 2 * MACs of
- * the layer (structural zeros of transposed convolutions excluded), *tc = 1 if
- * it ran on the tensor-core kernel.  Needs a prior unet_forward of that shape. */
+ * events on `stream`, in its inference form (BatchNorm and eLU applied as the
+ * forward applies them); *ms = mean device time per repetition (all launches
+ * of the layer), *flops = 2 * MACs of the layer (structural zeros of transposed
+ * convolutions excluded), *tc = the convolution kernel that ran: 2 TMA-fed
+ * tensor core, 1 cp.async-fed tensor core, 0 CUDA cores.  Needs a prior
+ * unet_forward of that shape; overwrites that layer's activation buffer. */
 int unet_time_layer(unet_t net, int layer, int reps, helm_stream_t stream, float* ms, double* flops, int* tc);
 
 /* Training pairs of Eq. 3.8-3.9 on the medium of h: x ~ CN(0,1) per node and

@@ -16,11 +16,14 @@
 // CGS2 needs 2 reductions per step instead of j + 2.
 //
 // The matrix-vector product uses u = D^-1 v_j:  (M D^-1 v)(p) = v(p) - (1/h^2)
-// * sum of u over the neighbours of p.  Reductions accumulate per thread and
-// per warp in T, across warps and CTAs in FP64, in a fixed order, so every CTA
-// of a cluster computes the identical Hessenberg matrix and solves the small
-// least-squares problem redundantly.  Only barriers (block and cluster) are
-// used; no CTA spins on memory written by another.
+// * sum of u over the neighbours of p.  All arithmetic, reductions, the
+// Hessenberg matrix and the Givens least-squares solve included, is in the
+// Krylov type T (FP64 is a small fraction of FP32 throughput on this GPU);
+// reductions run per thread, per warp, across warps and across CTAs in a
+// fixed order, so every CTA of a cluster computes the identical Hessenberg
+// matrix and solves the small least-squares problem redundantly.  Only
+// barriers (block and cluster) are used; no CTA spins on memory written by
+// another.
 #include <cooperative_groups.h>
 
 #include "helm_internal.cuh"
@@ -34,44 +37,66 @@ namespace {
 constexpr int KT = 256;        // threads per CTA
 constexpr int KMAX = 32;       // largest restart length
 
-__device__ __forceinline__ double2 zz(double x, double y) { double2 r; r.x = x; r.y = y; return r; }
-__device__ __forceinline__ double2 zmul2(double2 a, double2 b) { return zz(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename T>
+__device__ __forceinline__ typename vec2<T>::type zz(T x, T y) {
+  typename vec2<T>::type r;
+  r.x = x; r.y = y;
+  return r;
+}
+template <typename T2>
+__device__ __forceinline__ T2 zmul2(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+__device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
+__device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
 
+template <typename T>
 struct ClusterRed {
-  double2 wsum[KT / 32][KMAX + 2];   // per-warp partials
-  double2 csum[2][KMAX + 2];         // this CTA's totals, double-buffered across reductions
+  typedef typename vec2<T>::type T2;
+  T2 wsum[KT / 32][KMAX + 2];   // per-warp partials
+  T2 csum[2][KMAX + 2];         // this CTA's totals, double-buffered across reductions
 };
 
 // Sum K complex values over the cluster: `vals(k, x, y)` gives this thread's partial
 // of value k (already summed over its points).  Result, identical in every CTA, in out[k].
-// (An all-values-in-registers variant with interleaved shuffles measured slower.)
+// Values are reduced two at a time so that the two shuffle chains overlap.
 template <typename T, int MK, typename F>
-__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed& R, int buf, int K, F vals,
-                                               double2* out) {
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed<T>& R, int buf, int K, F vals,
+                                               typename vec2<T>::type* out) {
+  typedef typename vec2<T>::type T2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < K; ++k) {
-    T x, y;
-    vals(k, x, y);
+  for (int k = 0; k < K; k += 2) {
+    T x0, y0, x1 = 0, y1 = 0;
+    vals(k, x0, y0);
+    if (k + 1 < K) vals(k + 1, x1, y1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      x += __shfl_xor_sync(0xffffffffu, x, o);
-      y += __shfl_xor_sync(0xffffffffu, y, o);
+      x0 += __shfl_xor_sync(0xffffffffu, x0, o);
+      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+      x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
     }
-    if (lane == 0) R.wsum[warp][k] = zz((double)x, (double)y);
+    if (lane == 0) {
+      R.wsum[warp][k] = zz<T>(x0, y0);
+      if (k + 1 < K) R.wsum[warp][k + 1] = zz<T>(x1, y1);
+    }
   }
   __syncthreads();
   if (threadIdx.x < K) {
-    double2 t = zz(0, 0);
+    T2 t = zz<T>(0, 0);
     for (int w = 0; w < KT / 32; ++w) { t.x += R.wsum[w][threadIdx.x].x; t.y += R.wsum[w][threadIdx.x].y; }
     R.csum[buf][threadIdx.x] = t;
   }
   cl.sync();
   if (threadIdx.x < K) {
-    double2 t = zz(0, 0);
+    T2 t = zz<T>(0, 0);
     const int C = (int)cl.num_blocks();
     for (int r = 0; r < C; ++r) {
-      const ClusterRed* rem = cl.map_shared_rank(&R, r);
-      const double2 v = rem->csum[buf][threadIdx.x];
+      const ClusterRed<T>* rem = cl.map_shared_rank(&R, r);
+      const T2 v = rem->csum[buf][threadIdx.x];
       t.x += v.x; t.y += v.y;
     }
     out[threadIdx.x] = t;
@@ -96,13 +121,13 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
   T2* V = reinterpret_cast<T2*>(smem_raw);             // [(m+1)][NP]
   T2* U = V + (size_t)(m + 1) * NP;                    // u = D^-1 v_j, [NP]
   T2* DI = U + NP;                                     // D^-1, [NP]
-  __shared__ ClusterRed R;
-  __shared__ double2 H[(KMAX + 1) * KMAX];
-  __shared__ double2 hv[KMAX + 2];
-  __shared__ double2 ys[KMAX];
-  __shared__ double2 gg[KMAX + 1];
-  __shared__ double2 snn[KMAX];
-  __shared__ double css[KMAX];
+  __shared__ ClusterRed<T> R;
+  __shared__ T2 H[(KMAX + 1) * KMAX];
+  __shared__ T2 hv[KMAX + 2];
+  __shared__ T2 ys[KMAX];
+  __shared__ T2 gg[KMAX + 1];
+  __shared__ T2 snn[KMAX];
+  __shared__ T css[KMAX];
   __shared__ int s_k;
   const int tid = threadIdx.x;
   const T2* fr = f + (size_t)rhs * N + p0;
@@ -127,9 +152,9 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     for (int q = 0; q < PPT; ++q) a += w[q].x * w[q].x + w[q].y * w[q].y;
   }, hv);
   buf ^= 1;
-  const double beta = sqrt(hv[0].x);
+  const T beta = sqrt(hv[0].x);
   T2* outr = out + (size_t)rhs * N + p0;
-  if (!(beta > 0.0)) {
+  if (!(beta > (T)0)) {
     T2 zv = czero<T2>();
     if (beta != beta) { zv.x = beta; zv.y = beta; }
 #pragma unroll
@@ -141,7 +166,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     return;
   }
   {
-    const T inv = (T)(1.0 / beta);
+    const T inv = (T)1 / beta;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const int lp = tid + q * KT;
@@ -191,7 +216,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     buf ^= 1;
     if (tid <= j) H[tid * m + j] = hv[tid];
     for (int i = 0; i <= j; ++i) {
-      const T hx = (T)hv[i].x, hy = (T)hv[i].y;
+      const T hx = hv[i].x, hy = hv[i].y;
       const T2* vi = V + (size_t)i * NP;
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
@@ -216,13 +241,13 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
       }
     }, hv);
     buf ^= 1;
-    double nn = hv[j + 1].x;
+    T nn = hv[j + 1].x;
     for (int i = 0; i <= j; ++i) nn -= hv[i].x * hv[i].x + hv[i].y * hv[i].y;
-    const double nrm = sqrt(nn > 0.0 ? nn : 0.0);
-    if (tid <= j) { double2 a = H[tid * m + j]; H[tid * m + j] = zz(a.x + hv[tid].x, a.y + hv[tid].y); }
-    if (tid == 0) H[(j + 1) * m + j] = zz(nrm, 0.0);
+    const T nrm = sqrt(nn > (T)0 ? nn : (T)0);
+    if (tid <= j) { T2 a = H[tid * m + j]; H[tid * m + j] = zz<T>(a.x + hv[tid].x, a.y + hv[tid].y); }
+    if (tid == 0) H[(j + 1) * m + j] = zz<T>(nrm, 0);
     for (int i = 0; i <= j; ++i) {
-      const T hx = (T)hv[i].x, hy = (T)hv[i].y;
+      const T hx = hv[i].x, hy = hv[i].y;
       const T2* vi = V + (size_t)i * NP;
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
@@ -231,9 +256,9 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
       }
     }
     k = j + 1;
-    if (nrm == 0.0) break;                             // happy breakdown (identical in every CTA)
+    if (nrm == (T)0) break;                            // happy breakdown (identical in every CTA)
     if (j + 1 < m) {
-      const T inv = (T)(1.0 / nrm);
+      const T inv = (T)1 / nrm;
       T2* vn = V + (size_t)(j + 1) * NP;
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
@@ -245,40 +270,42 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
   }
   // least squares by Givens rotations (thread 0 of every CTA, identical inputs)
   if (tid == 0) {
-    gg[0] = zz(beta, 0.0);
+    gg[0] = zz<T>(beta, 0);
     for (int j = 0; j < k; ++j) {
       for (int i = 0; i < j; ++i) {
-        double2 a = H[i * m + j], b = H[(i + 1) * m + j];
-        double2 t = zz(css[i] * a.x + (snn[i].x * b.x - snn[i].y * b.y), css[i] * a.y + (snn[i].x * b.y + snn[i].y * b.x));
-        double2 cj = zmul2(zz(snn[i].x, -snn[i].y), a);
-        H[(i + 1) * m + j] = zz(-cj.x + css[i] * b.x, -cj.y + css[i] * b.y);
+        const T2 a = H[i * m + j], b = H[(i + 1) * m + j];
+        const T2 t = zz<T>(css[i] * a.x + (snn[i].x * b.x - snn[i].y * b.y),
+                           css[i] * a.y + (snn[i].x * b.y + snn[i].y * b.x));
+        const T2 cj = zmul2(zz<T>(snn[i].x, -snn[i].y), a);
+        H[(i + 1) * m + j] = zz<T>(-cj.x + css[i] * b.x, -cj.y + css[i] * b.y);
         H[i * m + j] = t;
       }
-      double2 a = H[j * m + j], b = H[(j + 1) * m + j];
-      double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y), c;
-      double2 sv, r;
-      if (bb == 0.0) { c = 1.0; sv = zz(0, 0); r = a; }
-      else if (aa == 0.0) { c = 0.0; sv = zz(1, 0); r = b; }
+      const T2 a = H[j * m + j], b = H[(j + 1) * m + j];
+      const T aa = hyp(a.x, a.y), bb = hyp(b.x, b.y);
+      T c;
+      T2 sv, r;
+      if (bb == (T)0) { c = 1; sv = zz<T>(0, 0); r = a; }
+      else if (aa == (T)0) { c = 0; sv = zz<T>(1, 0); r = b; }
       else {
-        double t = hypot(aa, bb);
+        const T t = hyp(aa, bb);
         c = aa / t;
-        double2 ph = zz(a.x / aa, a.y / aa);
-        sv = zmul2(ph, zz(b.x / t, -b.y / t));
-        r = zz(ph.x * t, ph.y * t);
+        const T2 ph = zz<T>(a.x / aa, a.y / aa);
+        sv = zmul2(ph, zz<T>(b.x / t, -b.y / t));
+        r = zz<T>(ph.x * t, ph.y * t);
       }
       css[j] = c; snn[j] = sv;
       H[j * m + j] = r;
-      H[(j + 1) * m + j] = zz(0, 0);
-      double2 gj = gg[j], sg = zmul2(zz(sv.x, -sv.y), gj);
-      gg[j + 1] = zz(-sg.x, -sg.y);
-      gg[j] = zz(c * gj.x, c * gj.y);
+      H[(j + 1) * m + j] = zz<T>(0, 0);
+      const T2 gj = gg[j], sg = zmul2(zz<T>(sv.x, -sv.y), gj);
+      gg[j + 1] = zz<T>(-sg.x, -sg.y);
+      gg[j] = zz<T>(c * gj.x, c * gj.y);
     }
     for (int i = k - 1; i >= 0; --i) {
-      double2 a = gg[i];
-      for (int l = i + 1; l < k; ++l) { double2 t = zmul2(H[i * m + l], ys[l]); a.x -= t.x; a.y -= t.y; }
-      double2 d = H[i * m + i];
-      double dd = d.x * d.x + d.y * d.y;
-      ys[i] = zz((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
+      T2 a = gg[i];
+      for (int l = i + 1; l < k; ++l) { const T2 t = zmul2(H[i * m + l], ys[l]); a.x -= t.x; a.y -= t.y; }
+      const T2 d = H[i * m + i];
+      const T dd = d.x * d.x + d.y * d.y;
+      ys[i] = zz<T>((a.x * d.x + a.y * d.y) / dd, (a.y * d.x - a.x * d.y) / dd);
     }
     s_k = k;
   }
@@ -289,11 +316,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     const int lp = tid + q * KT;
     if (lp >= NP) continue;
     T2 a = czero<T2>();
-    for (int i = 0; i < kk; ++i) {
-      T2 yi;
-      yi.x = (T)ys[i].x; yi.y = (T)ys[i].y;
-      a = cadd(a, cmul(yi, V[(size_t)i * NP + lp]));
-    }
+    for (int i = 0; i < kk; ++i) a = cadd(a, cmul(ys[i], V[(size_t)i * NP + lp]));
     outr[lp] = cmul(a, DI[lp]);
   }
   cl.sync();   // keep shared memory alive until every CTA is done with remote reads

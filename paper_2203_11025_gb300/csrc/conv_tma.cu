@@ -1,21 +1,28 @@
 // Tensor-core implicit-GEMM convolution fed by TMA (sm_103a).
 //
-// A CTA computes a tile of 128 output pixels (a BX x BY x BB box of one or more
+// Work item: a tile of 128 output pixels (a BX x BY x BB box of one or more
 // images; for transposed stride-2 convolutions a box of one output phase) times
-// Cout (<= 256, rounded up to 16).  The reduction runs over K-blocks = (tap,
-// 64-channel chunk of one input source); for each K-block one TMA load brings
+// Cout (<= 256, rounded up to 16), reduced over one range of K-blocks = (tap,
+// 64-channel chunk of one input source).  For each K-block one TMA load brings
 // the input box at the tap's offset -- element stride 2 for stride-2
-// convolutions, zero fill outside the image (the convolution's padding) -- in
-// the 128-byte-swizzled K-major layout the MMA reads, and one TMA load brings
-// the matching weight tile from a padded K-major copy [cout][tap][chunks*64].
-// Warp 4 issues the TMA loads (mbarrier expect_tx), warp 5 issues
-// tcgen05.mma (M = 128, K = 16 x 4 per block) and commits each stage back to
-// the producer; warps 0-3 read the FP32 accumulator from tensor memory and
-// apply bias / residual / BatchNorm / eLU.  All waits are bounded.
+// convolutions, zero fill outside the image (the convolution's padding) and
+// past the real channels -- in the 128-byte-swizzled K-major layout the MMA
+// reads, and one TMA load brings the matching weight tile from a padded K-major
+// copy [cout][tap][chunks*64].
+//
+// The kernel is persistent (one or two CTAs per SM, items strided by the grid).
+// Warp 4 issues the TMA loads into a ring of 4-8 stages (mbarrier expect_tx)
+// without stopping at item boundaries; warp 5 issues tcgen05.mma (M = 128,
+// K = 16 x 4 per block) into one of two TMEM accumulators and commits each
+// stage back to the producer; warps 0-3 read the finished accumulator and
+// apply bias / residual / BatchNorm / eLU while the next item accumulates in
+// the other buffer.  Convolutions with too few tiles to fill the GPU split K
+// across items and accumulate with FP32 atomics.  All waits are bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -27,7 +34,7 @@ namespace {
 
 constexpr int TM = 128;
 constexpr int TK = 64;
-constexpr int NST = 4;
+constexpr int MAXST = 8;           // stage ring capacity (the host picks nst <= MAXST)
 constexpr int NTHR = 192;          // warps 0-3 epilogue, 4 TMA, 5 MMA
 constexpr long long kWait = 1ll << 24;
 
@@ -84,9 +91,14 @@ struct TmaArgs {
   int B, Ho, Wo, Cout, NT;
   int k, stride, pad, transposed;
   int BX, BY, BB;                 // output tile (pixels of the output or phase grid)
-  int tx, ty;                     // tiles along x and y
+  int tx, ty, tb;                 // tiles along x, y and images
   int nch0, nch1;                 // 64-channel chunks per source
   int bcast1;                     // source 1 is one image shared by the batch
+  int ksplit;                     // K-block ranges per tile; > 1: atomic FP32 accumulation
+  int nitems;                     // tiles x phases x ksplit
+  int nst;                        // pipeline stages (<= MAXST)
+  int colsz;                      // TMEM columns of one accumulator (power of two >= 32)
+  int vec;                        // every row pointer of out / ybf / res is 16-byte aligned
   int kpad;                       // padded K per tap = 64 (nch0 + nch1)
   float* out; int ldo;
   const float* bias;
@@ -96,36 +108,61 @@ struct TmaArgs {
   int* err;
 };
 
+// One work item: an output tile of one phase, reduced over one K range.
+struct Item {
+  int x0, y0, b0, py, px, ky0, kx0, dk, ntx, nchk, kbeg, nkb, lead;
+};
+
+__device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
+  const int ntile = a.tx * a.ty * a.tb;
+  int t = w % ntile;
+  const int r = w / ntile;
+  const int nph = a.transposed ? 4 : 1;
+  const int z = r % nph, ys = r / nph;
+  Item it;
+  it.py = a.transposed ? (z >> 1) : 0;
+  it.px = a.transposed ? (z & 1) : 0;
+  it.ky0 = 0; it.kx0 = 0; it.dk = 1;
+  if (a.transposed) { it.ky0 = (it.py + a.pad) & 1; it.kx0 = (it.px + a.pad) & 1; it.dk = 2; }
+  const int nty = (a.k - it.ky0 + it.dk - 1) / it.dk;
+  it.ntx = (a.k - it.kx0 + it.dk - 1) / it.dk;
+  it.nchk = a.nch0 + a.nch1;
+  const int nkb_all = nty * it.ntx * it.nchk;
+  // balanced K ranges; the host keeps ksplit <= nkb_all, so nkb >= 1
+  it.kbeg = ys * nkb_all / a.ksplit;
+  it.nkb = (ys + 1) * nkb_all / a.ksplit - it.kbeg;
+  it.lead = ys == 0;
+  const int tix = t % a.tx; t /= a.tx;
+  const int tiy = t % a.ty; t /= a.ty;
+  it.x0 = tix * a.BX; it.y0 = tiy * a.BY; it.b0 = t * a.BB;
+  return it;
+}
+
+__device__ __forceinline__ bool failed(const volatile int* f) { return *f != 0; }
+
+// Persistent: CTA c takes items c, c + gridDim.x, ...  Warp 4 streams K-blocks
+// through the stage ring across item boundaries, warp 5 accumulates item i in
+// TMEM buffer i & 1, warps 0-3 drain buffer i & 1 while the MMAs of item i + 1 run.
 __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CUtensorMap mA0,
                                                       const __grid_constant__ CUtensorMap mA1,
                                                       const __grid_constant__ CUtensorMap mB, TmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
+  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int N = a.NT, n0 = blockIdx.y * a.NT;
-  const int py = a.transposed ? (blockIdx.z >> 1) : 0, px = a.transposed ? (blockIdx.z & 1) : 0;
-  int ky0 = 0, kx0 = 0, dk = 1;
-  if (a.transposed) { ky0 = (py + a.pad) & 1; kx0 = (px + a.pad) & 1; dk = 2; }
-  const int nty = (a.k - ky0 + dk - 1) / dk, ntx = (a.k - kx0 + dk - 1) / dk;
-  const int nchk = a.nch0 + a.nch1;
-  const int nkb = nty * ntx * nchk;
-  // tile origin in the output (or phase) grid
-  int t = blockIdx.x;
-  const int tix = t % a.tx; t /= a.tx;
-  const int tiy = t % a.ty; t /= a.ty;
-  const int x0 = tix * a.BX, y0 = tiy * a.BY, b0 = t * a.BB;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.NT, NS = a.nst;
 
   const uint32_t base = (su32(smem) + 1023u) & ~1023u;
   const uint32_t a_bytes = TM * 128, b_bytes = (uint32_t)N * 128, stage = a_bytes + b_bytes;
   if (tid == 0) {
-    for (int s = 0; s < NST; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
-    mb_init(su32(&done), 1);
+    for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
+    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), 4); }
+    mb_init(su32(&drain), 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  const uint32_t ncols = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  const uint32_t ncols = 2u * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
                  "r"(ncols)
@@ -136,70 +173,98 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  volatile int* fail = &s_fail;
 
   if (warp == 4) {
-    if ((tid & 31) == 0) {
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % NST;
-        const uint32_t use = (uint32_t)(kb / NST);
-        if (kb >= NST && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
-        const int tap = kb / nchk, ch = kb - tap * nchk;
-        const int ty = tap / ntx, tx = tap - ty * ntx;
-        const int ky = ky0 + dk * ty, kx = kx0 + dk * tx;
-        int ix, iy;
-        if (!a.transposed) { ix = x0 * a.stride + kx - a.pad; iy = y0 * a.stride + ky - a.pad; }
-        else { ix = x0 + (px + a.pad - kx) / 2; iy = y0 + (py + a.pad - ky) / 2; }
-        const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
-        mb_expect_tx(su32(&full[s]), stage);
-        if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, b0, su32(&full[s]));
-        else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : b0, su32(&full[s]));
-        tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, n0, su32(&full[s]));
+    if (lane == 0) {
+      uint32_t g = 0;   // K-blocks issued by this CTA
+      for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x) {
+        const Item it = decode(a, w);
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+          const int s = (int)(g % (uint32_t)NS);
+          const uint32_t use = g / (uint32_t)NS;
+          if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
+          const int kg = it.kbeg + kb;
+          const int tap = kg / it.nchk, ch = kg - tap * it.nchk;
+          const int ty = tap / it.ntx, tx = tap - ty * it.ntx;
+          const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
+          int ix, iy;
+          if (!a.transposed) { ix = it.x0 * a.stride + kx - a.pad; iy = it.y0 * a.stride + ky - a.pad; }
+          else { ix = it.x0 + (it.px + a.pad - kx) / 2; iy = it.y0 + (it.py + a.pad - ky) / 2; }
+          const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
+          mb_expect_tx(su32(&full[s]), stage);
+          if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, it.b0, su32(&full[s]));
+          else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : it.b0, su32(&full[s]));
+          tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, 0, su32(&full[s]));
+        }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
       }
-      if (!ok) atomicExch(&s_fail, 1);
+      // let the loads still in flight land before the CTA can exit (bounded)
+      for (uint32_t j = g > (uint32_t)NS ? g - (uint32_t)NS : 0u; j < g; ++j)
+        mb_wait(su32(&full[j % (uint32_t)NS]), (j / (uint32_t)NS) & 1u);
     }
   } else if (warp == 5) {
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
       const uint32_t id = idesc(N);
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % NST;
-        if (!mb_wait(su32(&full[s]), (uint32_t)(kb / NST) & 1u)) { ok = false; break; }
+      uint32_t g = 0;
+      int li = 0;
+      for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x, ++li) {
+        const Item it = decode(a, w);
+        const int acc = li & 1;
+        const uint32_t use = (uint32_t)(li >> 1);
+        if (li >= 2 && !mb_wait(su32(&tempty[acc]), (use - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t sA = base + (uint32_t)s * stage;
-        const uint64_t da = desc128(sA), db = desc128(sA + a_bytes);
+        const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+          const int s = (int)(g % (uint32_t)NS);
+          if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sA = base + (uint32_t)s * stage;
+          const uint64_t da = desc128(sA), db = desc128(sA + a_bytes);
 #pragma unroll
-        for (int k4 = 0; k4 < TK / 16; ++k4) {
-          const uint32_t acc = (kb > 0 || k4 > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(da + (uint64_t)(2 * k4)), "l"(db + (uint64_t)(2 * k4)), "r"(id), "r"(acc)
-              : "memory");
+          for (int k4 = 0; k4 < TK / 16; ++k4) {
+            const uint32_t accum = (kb > 0 || k4 > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(da + (uint64_t)(2 * k4)), "l"(db + (uint64_t)(2 * k4)), "r"(id), "r"(accum)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           su32(&empty[s]))
+                       : "memory");
         }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         su32(&empty[s]))
+                         su32(&tfull[acc]))
                      : "memory");
       }
-      if (!ok) atomicExch(&s_fail, 1);
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&done))
+      // every MMA issued above completes before tensor memory is released (bounded)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
                    : "memory");
+      mb_wait(su32(&drain), 0);
     }
   } else {
     // epilogue: warps 0-3, tile row = tid
-    const bool fin = mb_wait(su32(&done), 0);
-    if (!fin) atomicExch(&s_fail, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    int li = 0;
     const int m = tid;
     const int bb = m / (a.BY * a.BX), rr = m - bb * a.BY * a.BX, by = rr / a.BX, bx = rr - by * a.BX;
-    const int b = b0 + bb, qy = y0 + by, qx = x0 + bx;
-    const int oy = a.transposed ? 2 * qy + py : qy, ox = a.transposed ? 2 * qx + px : qx;
-    const bool rv = fin && b < a.B && oy < a.Ho && ox < a.Wo;
-    const size_t pix = ((size_t)b * a.Ho + oy) * a.Wo + ox;
-    if (fin) {
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
+      if (failed(fail)) break;
+      const Item it = decode(a, w);
+      const int acc = li & 1;
+      if (!mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
+      const int oy = a.transposed ? 2 * qy + it.py : qy, ox = a.transposed ? 2 * qx + it.px : qx;
+      const bool rv = it.nkb > 0 && b < a.B && oy < a.Ho && ox < a.Wo;
+      const bool lead = it.lead;   // the first K range adds bias and residual
+      const size_t pix = ((size_t)b * a.Ho + oy) * a.Wo + ox;
       for (int c0 = 0; c0 < N; c0 += 16) {
         uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
@@ -207,29 +272,83 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
         if (rv) {
+          const int cb = c0;
+          float f[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int co = n0 + c0 + j;
-            if (co >= a.Cout) break;
-            float f = __uint_as_float(v[j]);
-            if (a.bias) f += a.bias[co];
-            if (a.res) f += __bfloat162float(a.res[pix * a.ldr + co]);
-            if (a.ybf) {
-              if (a.scale) f = f * a.scale[co] + a.shift[co];
-              if (a.act) f = f > 0.f ? f : expm1f(f);
-              a.ybf[pix * a.ldy + co] = __float2bfloat16_rn(f);
+            const int co = cb + j < a.Cout ? cb + j : a.Cout - 1;
+            f[j] = __uint_as_float(v[j]);
+            if (lead && a.bias) f[j] += a.bias[co];
+          }
+          if (cb + 16 <= a.Cout && a.vec) {
+            // full 16-channel chunk: 16-byte loads and stores along the pixel's channel row
+            if (lead && a.res) {
+              const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + cb);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint4 r4 = rp[h];
+                const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&r4);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const float2 rf = __bfloat1622float2(r2[j]);
+                  f[8 * h + 2 * j] += rf.x;
+                  f[8 * h + 2 * j + 1] += rf.y;
+                }
+              }
+            }
+            if (a.ksplit > 1) {
+              float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) atomicAdd(op + q, make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]));
+            } else if (a.ybf) {
+              uint4 o4[2];
+              __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(o4);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (a.scale) f[j] = f[j] * a.scale[cb + j] + a.shift[cb + j];
+                if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+              uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + cb);
+              yp[0] = o4[0];
+              yp[1] = o4[1];
             } else {
-              a.out[pix * a.ldo + co] = f;
+              float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int co = cb + j;
+              if (co >= a.Cout) break;
+              float g = f[j];
+              if (lead && a.res) g += __bfloat162float(a.res[pix * a.ldr + co]);
+              if (a.ksplit > 1) {
+                atomicAdd(&a.out[pix * a.ldo + co], g);
+              } else if (a.ybf) {
+                if (a.scale) g = g * a.scale[co] + a.shift[co];
+                if (a.act) g = g > 0.f ? g : expm1f(g);
+                a.ybf[pix * a.ldy + co] = __float2bfloat16_rn(g);
+              } else {
+                a.out[pix * a.ldo + co] = g;
+              }
             }
           }
         }
       }
+      // accumulator read: hand buffer acc back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&tempty[acc])) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (tid == 0 && s_fail && a.err) atomicExch(a.err, 1);
   if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
   }
 }
@@ -305,24 +424,53 @@ void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, 
                                                                                      64 * nch0);
 }
 
-// Launch if the convolution fits the TMA path; false otherwise (caller falls back).
-bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
-  if (!c.WP || c.in_f32 || c.in_act || c.Cout > 256) return false;
-  if (c.transposed && c.stride != 2) return false;
-  if (!c.transposed && c.stride != 1 && c.stride != 2) return false;
-  if (c.c0 % 8 || (c.in1 && c.c1 % 8)) return false;
-  if (!get_encoder()) return false;
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+int ctas_per_sm(int nt) { return nt <= 64 ? 2 : 1; }
+
+// K split for convolutions whose pixel tiles leave most SMs idle (1 = none).
+int conv_tma_split(const ConvArgs& c) {
   const int Wq = c.transposed ? c.Wo / 2 : c.Wo, Hq = c.transposed ? c.Ho / 2 : c.Ho;
-  if (!pow2(Wq) || !pow2(Hq) || (c.transposed && (c.Wo % 2 || c.Ho % 2))) return false;
+  if (!pow2(Wq) || !pow2(Hq) || c.ldo != c.Cout || c.ybf) return 1;
   const int BX = Wq < 128 ? Wq : 128;
   const int BY = Hq < 128 / BX ? Hq : 128 / BX;
   const int BB = 128 / (BX * BY);
-  if (c.in1 && c.bcast1 && BB > 1) return false;
+  const int tiles = (Wq / BX) * (Hq / BY) * ((c.B + BB - 1) / BB) * (c.transposed ? 4 : 1);
+  const int taps = c.transposed ? (c.k * c.k + 3) / 4 : c.k * c.k;
+  const int nkb = taps * ((c.c0 + 63) / 64 + (c.in1 ? (c.c1 + 63) / 64 : 0));
+  const int slots = sm_count() * ctas_per_sm(((c.Cout + 15) / 16) * 16);
+  int sp = 1;
+  while (tiles * sp * 2 <= slots && nkb / (sp * 2) >= 4 && sp < 16) sp *= 2;
+  return sp;
+}
+
+const char* g_tma_reject = "";
+const char* conv_tma_last_reject() { return g_tma_reject; }
+
+bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
+#define TMA_REJECT(why) do { g_tma_reject = why; return false; } while (0)
+  if (!c.WP) TMA_REJECT("no padded weights");
+  if (c.in_f32 || c.in_act || c.Cout > 256) TMA_REJECT("fp32 or activated input, or Cout > 256");
+  if (c.transposed && c.stride != 2) TMA_REJECT("transposed stride");
+  if (!c.transposed && c.stride != 1 && c.stride != 2) TMA_REJECT("stride");
+  if (c.ld0 % 8 || (c.in1 && c.ld1 % 8)) TMA_REJECT("row stride");   // TMA zero-fills channels past c0 / c1
+  if (!get_encoder()) TMA_REJECT("no tensor-map encoder");
+  const int Wq = c.transposed ? c.Wo / 2 : c.Wo, Hq = c.transposed ? c.Ho / 2 : c.Ho;
+  if (!pow2(Wq) || !pow2(Hq) || (c.transposed && (c.Wo % 2 || c.Ho % 2))) TMA_REJECT("grid not a power of two");
+  const int BX = Wq < 128 ? Wq : 128;
+  const int BY = Hq < 128 / BX ? Hq : 128 / BX;
+  const int BB = 128 / (BX * BY);
+  if (c.in1 && c.bcast1 && BB > 1) TMA_REJECT("broadcast source with several images per tile");
   const int es = c.transposed ? 1 : c.stride;
   CUtensorMap mA0, mA1, mB;
-  if (!encode_act(&mA0, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY, BB, es)) return false;
+  if (!encode_act(&mA0, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY, BB, es)) TMA_REJECT("source 0 map");
   if (c.in1) {
-    if (!encode_act(&mA1, c.in1, c.c1, c.ld1, c.Wi, c.Hi, c.bcast1 ? 1 : c.B, BX, BY, BB, es)) return false;
+    if (!encode_act(&mA1, c.in1, c.c1, c.ld1, c.Wi, c.Hi, c.bcast1 ? 1 : c.B, BX, BY, BB, es))
+      TMA_REJECT("source 1 map");
   } else {
     mA1 = mA0;
   }
@@ -335,20 +483,48 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.nch0 = (c.c0 + 63) / 64;
   a.nch1 = c.in1 ? (c.c1 + 63) / 64 : 0;
   a.bcast1 = (c.in1 && c.bcast1) ? 1 : 0;
+  a.ksplit = conv_tma_split(c);
   a.kpad = 64 * (a.nch0 + a.nch1);
-  if (!encode_w(&mB, c.WP, c.k * c.k * a.kpad, c.Cout, a.NT)) return false;
+  if (!encode_w(&mB, c.WP, c.k * c.k * a.kpad, c.Cout, a.NT)) TMA_REJECT("weight map");
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
   a.scale = c.scale; a.shift = c.shift; a.act = c.ep_act; a.ybf = c.ybf; a.ldy = c.ldy;
   a.err = err;
-  const size_t smem = (size_t)NST * (TM * 128 + (size_t)a.NT * 128) + 1024;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, NST * (TM * 128 + 256 * 128) + 1024);
-    configured = true;
+  a.vec = ((c.ldo % 4 == 0) && !((uintptr_t)c.out & 15) && (c.ldy % 8 == 0) && !((uintptr_t)c.ybf & 15) &&
+           (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15)))) ? 1 : 0;
+  const int nph = c.transposed ? 4 : 1;
+  a.tb = (c.B + BB - 1) / BB;
+  a.nitems = a.tx * a.ty * a.tb * nph * a.ksplit;
+  a.colsz = a.NT <= 32 ? 32 : (a.NT <= 64 ? 64 : (a.NT <= 128 ? 128 : 256));
+  // stage ring sized to the shared memory left per CTA (228 KB per SM, 1 KB reserved per CTA,
+  // barriers and 1 KB alignment slack): 4-8 stages
+  const int per_sm = ctas_per_sm(a.NT);
+  const size_t stage = (size_t)TM * 128 + (size_t)a.NT * 128;
+  const size_t budget = (size_t)228 * 1024 / per_sm - 1024 - 2048;
+  a.nst = (int)std::min<size_t>(MAXST, budget / stage);
+  if (a.nst < 2) TMA_REJECT("shared memory");
+  const size_t smem = (size_t)a.nst * stage + 1024;
+  // dynamic shared memory opt-in: the per-block limit less the kernel's static barriers
+  static int max_dyn = -1;
+  if (max_dyn < 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_conv_tma) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+      max_dyn = 0;
+    else
+      max_dyn = optin - (int)fa.sharedSizeBytes;
   }
-  const int tb = (c.B + BB - 1) / BB;
-  k_conv_tma<<<dim3(a.tx * a.ty * tb, 1, c.transposed ? 4 : 1), NTHR, smem, s>>>(mA0, mA1, mB, a);
+  if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
+  if (a.ksplit > 1 && cudaMemsetAsync(c.out, 0, (size_t)c.B * c.Ho * c.Wo * c.ldo * 4, s) != cudaSuccess)
+    TMA_REJECT("split-K clear");
+  const int grid = std::min(a.nitems, sm_count() * per_sm);
+  k_conv_tma<<<grid, NTHR, smem, s>>>(mA0, mA1, mB, a);
+  g_tma_reject = "";
   return true;
+#undef TMA_REJECT
 }
 
 }  // namespace helm

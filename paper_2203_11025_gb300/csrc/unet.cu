@@ -80,6 +80,8 @@ struct unet_ctx {
   bool ev_dirty = true;
   int adam_t = 0;
   unet_ctx* encoder = nullptr;
+  bool is_encoder = false;                         // attached to a solver: keep a BF16 copy of the output
+  int last_path = 0;                               // kernel of the last convolution: 2 TMA, 1 cp.async, 0 CUDA cores
   bool last_train = false;
   // activation workspace for (B, ny, nx)
   int B = 0, ny = 0, nx = 0;
@@ -109,6 +111,11 @@ struct unet_ctx {
 };
 
 namespace {
+
+// Row stride of the network input and output copies: padded to 8 channels so that
+// rows are 16-byte aligned (the TMA path zero-fills the channels past the real ones).
+int xin_ld(const unet_ctx* n) { return (n->cfg.in_ch + 7) / 8 * 8; }
+int out_ld(const unet_ctx* n) { return (n->cfg.out_ch + 7) / 8 * 8; }
 
 int level_ch_in(const unet_ctx* n, int l) {  // channels of the down-conv source at level l-1
   return l == 1 ? n->cfg.in_ch : n->cfg.widths[l - 2];
@@ -185,7 +192,7 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
   const int L = n->L;
   auto M = [&](int l) { return (size_t)B * (ny >> l) * (nx >> l); };
   const int* w = c.widths;
-  n->x_in = a.take<__nv_bfloat16>(M(0) * c.in_ch);
+  n->x_in = a.take<__nv_bfloat16>(M(0) * xin_ld(n));
   n->zdown.assign(L + 1, nullptr); n->h0.assign(L + 1, nullptr);
   n->t1.assign(L + 1, {}); n->sres.assign(L + 1, {}); n->a1.assign(L + 1, {}); n->hres.assign(L + 1, {});
   n->cat.assign(L + 1, nullptr); n->zup.assign(L + 1, nullptr);
@@ -228,7 +235,7 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
   }
   n->hL = a.take<__nv_bfloat16>(M(L) * w[L - 1]);
   n->out = a.take<float>(M(0) * c.out_ch);
-  n->out_bf = a.take<__nv_bfloat16>(M(0) * c.out_ch);
+  n->out_bf = a.take<__nv_bfloat16>(M(0) * out_ld(n));
   n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
   n->sums = a.take<double>(2 * 512);
   n->xin32 = a.take<float>(M(0) * c.in_ch);
@@ -263,7 +270,7 @@ Src feat_of(const unet_ctx* n, int l) {
   if (!e || !n->cfg.context[l]) return {nullptr, 0, 0, false};
   const bool bc = (e->B == 1 && n->B > 1);
   const int L = e->L;
-  if (l == 0) return {e->out_bf, e->cfg.out_ch, e->cfg.out_ch, bc};
+  if (l == 0) return {e->out_bf, e->cfg.out_ch, out_ld(e), bc};
   if (l == L) return {e->hL, e->cfg.widths[L - 1], e->cfg.widths[L - 1], bc};
   return {e->cat[l], e->cfg.widths[l - 1], 2 * e->cfg.widths[l - 1], bc};
 }
@@ -289,9 +296,9 @@ ConvArgs conv_args(const unet_ctx* n, const ConvL& cl, Src a, Src b, bool act, i
 }
 
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
-  if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) return;
-  if (n->use_tc && conv_tc_eligible(a)) conv_forward_tc(a, n->d_err, s);
-  else conv_forward(a, s);
+  if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) { n->last_path = 2; return; }
+  if (n->use_tc && conv_tc_eligible(a)) { conv_forward_tc(a, n->d_err, s); n->last_path = 1; }
+  else { conv_forward(a, s); n->last_path = 0; }
 }
 
 // Data gradient of a convolution: the adjoint geometry with transposed weights.
@@ -354,16 +361,23 @@ void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s) {
 // tensor-core path the normalisation is applied in the convolution's epilogue.
 void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bfloat16* y, int ldy, int M, bool train,
              cudaStream_t s) {
-  if (!train && n->use_tc && conv_tc_eligible(a)) {
-    ensure_eval_coeffs(n, s);
+  // inference: BatchNorm and eLU fused into the tensor-core epilogue, unless the
+  // TMA path splits K (partial sums are accumulated in FP32 first)
+  if (!train && n->use_tc && !(n->use_tma && conv_tma_split(a) > 1)) {
+    ConvArgs f = a;
     const BnL& b = bn_of(n, bn);
-    a.scale = n->ev_scale + b.soff;
-    a.shift = n->ev_shift + b.soff;
-    a.ep_act = act ? 1 : 0;
-    a.ybf = y;
-    a.ldy = ldy;
-    if (!(n->use_tma && conv_forward_tma(a, n->d_err, s))) conv_forward_tc(a, n->d_err, s);
-    return;
+    ensure_eval_coeffs(n, s);
+    f.scale = n->ev_scale + b.soff;
+    f.shift = n->ev_shift + b.soff;
+    f.ep_act = act ? 1 : 0;
+    f.ybf = y;
+    f.ldy = ldy;
+    if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; return; }
+    if (conv_tc_eligible(f)) {
+      conv_forward_tc(f, n->d_err, s);
+      n->last_path = 1;
+      return;
+    }
   }
   run_conv(n, a, s);
   run_bn(n, bn, a.out, a.ldo, M, act, y, ldy, train, s);
@@ -396,7 +410,7 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
   for (int l = 1; l <= L; ++l) {
     int H, W;
     hw(l - 1, H, W);
-    Src src = l == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
+    Src src = l == 1 ? Src{n->x_in, c.in_ch, xin_ld(n), false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
     const ConvL& dl = conv_of(n, "down" + std::to_string(l));
     ConvArgs a = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, n->zdown[l], w[l - 1]);
     conv_bn(n, a, "down" + std::to_string(l) + ".bn", true, n->h0[l], w[l - 1], M(l), train, s);
@@ -442,7 +456,7 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
     a.bias = n->P + n->bias_off;
     a = act_inputs(n, a, 1, u, f, H, W, M(1), s);
     run_conv(n, a, s);
-    f32_to_bf16(n->out, n->out_bf, (size_t)M(0) * c.out_ch, s);
+    if (n->is_encoder) to_bf16_slice(n->out, c.out_ch, n->out_bf, out_ld(n), c.out_ch, M(0), s);
   }
   n->last_train = train;
   if (train) n->ev_dirty = true;   // running statistics moved
@@ -541,7 +555,7 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     const ConvL& dl = conv_of(n, "down" + std::to_string(l));
     int H, W;
     hw(l - 1, H, W);
-    Src src = l == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
+    Src src = l == 1 ? Src{n->x_in, c.in_ch, xin_ld(n), false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
     ConvArgs fa = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, nullptr, 0);
     conv_wgrad(fa, n->gzd[l], cw, n->G + dl.woff, s);
     const int ldD = src.c + c.context[l - 1];
@@ -624,7 +638,7 @@ static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool ad
     if (cs != cudaStreamCaptureStatusNone) { set_error("U-Net workspace not prepared before capture"); return HELM_EINVAL; }
     UTRY(ensure_ws(n, nrhs, ny, nx));
   }
-  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, 4, n->scale, n->part, gate, s);
+  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, xin_ld(n), n->scale, n->part, gate, s);
   UTRY(forward_impl(n, false, s));
   write_output(n->out, real_bytes == 8, nrhs, ny, nx, n->scale, e, add, gate, s);
   UCHECK(cudaGetLastError());
@@ -824,7 +838,7 @@ int unet_time_layer(unet_t n, int layer, int reps, helm_stream_t stream, float* 
   ConvArgs a{};
   if (cl.kind == 0) {
     H = n->ny >> (lvl - 1); W = n->nx >> (lvl - 1);
-    Src src = lvl == 1 ? Src{n->x_in, c.in_ch, c.in_ch, false} : Src{n->cat[lvl - 1] + w[lvl - 2], w[lvl - 2], 2 * w[lvl - 2], false};
+    Src src = lvl == 1 ? Src{n->x_in, c.in_ch, xin_ld(n), false} : Src{n->cat[lvl - 1] + w[lvl - 2], w[lvl - 2], 2 * w[lvl - 2], false};
     a = conv_args(n, cl, src, feat_of(n, lvl - 1), false, H, W, n->zdown[lvl], w[lvl - 1]);
   } else if (cl.kind == 1) {
     H = n->ny >> lvl; W = n->nx >> lvl;
@@ -842,13 +856,28 @@ int unet_time_layer(unet_t n, int layer, int reps, helm_stream_t stream, float* 
   }
   const double taps_eff = cl.kind == 2 ? (double)cl.k * cl.k / 4.0 : (double)cl.k * cl.k;
   *flops = 2.0 * (double)n->B * a.Ho * a.Wo * taps_eff * cl.cin * cl.cout;
-  *tc = (n->use_tc && conv_tc_eligible(a)) ? 1 : 0;
-  run_conv(n, a, s);  // warm-up
+  // the inference form of the layer: BatchNorm (+ eLU) into BF16 as the forward does it
+  // (this overwrites the layer's activation buffer; the next forward rewrites it)
+  const int Ml = n->B * a.Ho * a.Wo;
+  auto launch = [&] {
+    if (cl.kind == 0) conv_bn(n, a, cl.name + ".bn", true, n->h0[lvl], w[lvl - 1], Ml, false, s);
+    else if (cl.kind == 1) {
+      const bool second = cl.name.compare(cl.name.size() - 2, 2, "k2") == 0;
+      conv_bn(n, a, cl.name.substr(0, cl.name.size() - 2) + (second ? "bn2" : "bn1"), true, n->a1[lvl][0],
+              w[lvl - 1], Ml, false, s);
+    } else if (lvl >= 2) {
+      conv_bn(n, a, cl.name + ".bn", false, n->cat[lvl - 1], 2 * w[lvl - 2], Ml, false, s);
+    } else {
+      run_conv(n, a, s);
+    }
+  };
+  launch();  // warm-up
+  *tc = n->last_path;
   cudaEvent_t e0, e1;
   UCHECK(cudaEventCreate(&e0));
   UCHECK(cudaEventCreate(&e1));
   UCHECK(cudaEventRecord(e0, s));
-  for (int r = 0; r < reps; ++r) run_conv(n, a, s);
+  for (int r = 0; r < reps; ++r) launch();
   UCHECK(cudaEventRecord(e1, s));
   UCHECK(cudaEventSynchronize(e1));
   float t = 0;
@@ -893,7 +922,7 @@ int unet_forward(unet_t n, const float* x, float* out, int B, int ny, int nx, in
   }
   cudaStream_t s = (cudaStream_t)stream;
   UTRY(ensure_ws(n, B, ny, nx));
-  to_bf16_slice(x, n->cfg.in_ch, n->x_in, n->cfg.in_ch, n->cfg.in_ch, B * ny * nx, s);
+  to_bf16_slice(x, n->cfg.in_ch, n->x_in, xin_ld(n), n->cfg.in_ch, B * ny * nx, s);
   UTRY(forward_impl(n, train != 0, s));
   if (out) UCHECK(cudaMemcpyAsync(out, n->out, (size_t)B * ny * nx * n->cfg.out_ch * 4, cudaMemcpyDeviceToDevice, s));
   return HELM_OK;
@@ -944,6 +973,7 @@ int unet_attach_encoder(unet_t solver, unet_t encoder) {
     }
   }
   solver->encoder = encoder;
+  if (encoder) encoder->is_encoder = true;
   return HELM_OK;
 }
 
@@ -960,7 +990,7 @@ int unet_encode(unet_t solver, helm_t h, int train, helm_stream_t stream) {
   float* med = e->xin32;  // [ny*nx][2] float32 staging
   UCHECK(cudaMemcpy2DAsync(med, 8, k2f, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
   UCHECK(cudaMemcpy2DAsync(med + 1, 8, gam, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
-  to_bf16_slice(med, 2, e->x_in, 2, 2, nx * ny, s);
+  to_bf16_slice(med, 2, e->x_in, xin_ld(e), 2, nx * ny, s);
   return forward_impl(e, train != 0, s);
 }
 

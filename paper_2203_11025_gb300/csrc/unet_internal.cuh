@@ -41,6 +41,8 @@ void conv_forward_tc(const ConvArgs& a, int* err, cudaStream_t s);
 void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int cout, cudaStream_t s);
 // TMA-fed tensor-core path (conv_tma.cu); false if the convolution does not fit it.
 bool conv_forward_tma(const ConvArgs& a, int* err, cudaStream_t s);
+int conv_tma_split(const ConvArgs& a);
+const char* conv_tma_last_reject();      // why the last conv_forward_tma call declined ("" if it launched)   // > 1: the TMA path splits K (FP32 atomics, no fused epilogue)
 size_t conv_tma_weight_elems(int k, int c0, int c1, int cout);
 void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, int cout, cudaStream_t s);
 void elu_copy_bf16(const __nv_bfloat16* src, int lds, int C, size_t M, __nv_bfloat16* dst, int ldd, cudaStream_t s);

@@ -421,11 +421,12 @@ class UNet:
         return bool(f.value)
 
     def time_layer(self, layer, reps=20, stream=None):
-        """(ms per launch, flops per launch, ran on tensor cores) of convolution `layer`."""
+        """(ms per repetition, flops, kernel: 2 TMA tensor core, 1 cp.async tensor core, 0 CUDA cores)
+        of convolution `layer` in its inference form."""
         ms, fl, tc = ctypes.c_float(), ctypes.c_double(), ctypes.c_int()
         _check(self.lib.unet_time_layer(self.handle, layer, reps, _stream(stream), ctypes.byref(ms), ctypes.byref(fl),
                                         ctypes.byref(tc)), "unet_time_layer")
-        return ms.value, fl.value, bool(tc.value)
+        return ms.value, fl.value, int(tc.value)
 
     def zero_grad(self, stream=None):
         _check(self.lib.unet_zero_grad(self.handle, _stream(stream)), "unet_zero_grad")

@@ -3,6 +3,8 @@
   python -m paper_2203_11025_gb300.profcase unet 256 8     # one U-Net forward, 8 images of 256^2
   python -m paper_2203_11025_gb300.profcase coarse 256 8   # one coarsest-grid solve (fine grid 256^2, 8 RHS)
   python -m paper_2203_11025_gb300.profcase layers 256 8   # per-layer times of the U-Net forward
+  python -m paper_2203_11025_gb300.profcase mvu 256 8      # one FGMRES(10) restart cycle with M_VU
+                                                           # (profiler range = that cycle)
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -36,13 +38,30 @@ def main(argv):
             for i, nm in enumerate(names):
                 ms, fl, tc = net.time_layer(i, reps=10)
                 tot += ms
-                print(f"{nm:12s} {ms * 1e3:8.1f} us {fl / ms / 1e9:7.1f} TFLOP/s {'tc' if tc else 'cuda-core'}")
+                kind = {2: "tma-tc", 1: "cpasync-tc"}.get(tc, "cuda-core")
+                print(f"{nm:12s} {ms * 1e3:8.1f} us {fl / ms / 1e9:7.1f} TFLOP/s {kind}")
             print(f"total {tot * 1e3:.1f} us")
     elif what == "coarse":
         k2 = synth.grf_kappa2(n, n, 1000)
         hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
         ms, _ = hz.time_kernel(5, b, reps=3)
         print(f"coarse solve {ms * 1e3:.1f} us")
+    elif what == "mvu":
+        k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+        pos = synth.source_positions(n, n, b, synth.rhs_seed(0), 16)
+        rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n).astype(np.complex128)).cuda()
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=1)
+        x = torch.zeros_like(rhs)
+        for _ in range(2):   # warm-up: workspaces, graphs
+            hz.fgmres(rhs, x, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=10, restart=10,
+                      flags=lib.HELM_FLAG_X0_ZERO)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        hz.fgmres(rhs, x, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=10, restart=10,
+                  flags=lib.HELM_FLAG_X0_ZERO)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     else:
         raise SystemExit(f"unknown case {what}")
 
