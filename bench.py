@@ -284,7 +284,7 @@ def run_ours(args):
         layers.append((lms, fl, tc, net_layer_names(net)[li]))
     tot_conv_ms = sum(l[0] for l in layers)
     top = max(layers, key=lambda l: l[0])
-    tc_layers = [l for l in layers if l[2]]
+    tc_layers = [l for l in layers if l[2] in (1, 2)]     # tensor-core kernels (TMA or cp.async fed)
     tc_ms = sum(l[0] for l in tc_layers)
     tc_fl = sum(l[1] for l in tc_layers)
     k_ms, k_bytes = hz.time_kernel(3, NRHS, reps=50)

@@ -113,12 +113,15 @@ int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int coun
                     const double* coef, float* x, float* target, helm_stream_t stream);
 
 /* Measurement hook (no counterpart in the paper): time one convolution layer
- * (index in layer order) of the last forward's geometry `reps` times with CUDA
- * events on `stream`, in its inference form (BatchNorm and eLU applied as the
- * forward applies them); *ms = mean device time per repetition (all launches
+ * (index in layer order) of the last forward's geometry, in its inference form
+ * (BatchNorm and eLU applied as the forward applies them): `reps` repetitions
+ * captured in one CUDA graph on an internal stream and replayed, timed with CUDA
+ * events (device time without host launch overhead; `stream` runs the warm-up);
+ * *ms = mean device time per repetition (all launches
  * of the layer), *flops = 2 * MACs of the layer (structural zeros of transposed
- * convolutions excluded), *tc = the convolution kernel that ran: 2 TMA-fed
- * tensor core, 1 cp.async-fed tensor core, 0 CUDA cores.  Needs a prior
+ * convolutions excluded), *tc = the convolution kernel that ran: 3 direct
+ * CUDA-core kernel for thin layers, 2 TMA-fed tensor core, 1 cp.async-fed tensor
+ * core, 0 generic CUDA-core kernel.  Needs a prior
  * unet_forward of that shape; overwrites that layer's activation buffer. */
 int unet_time_layer(unet_t net, int layer, int reps, helm_stream_t stream, float* ms, double* flops, int* tc);
 

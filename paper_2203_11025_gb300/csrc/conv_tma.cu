@@ -17,14 +17,19 @@
 // stage back to the producer; warps 0-3 read the finished accumulator and
 // apply bias / residual / BatchNorm / eLU while the next item accumulates in
 // the other buffer.  Convolutions with too few tiles to fill the GPU split K
-// across items and accumulate with FP32 atomics.  All waits are bounded.
+// across items: each split stores its partial tile to its own FP32 slice and a
+// second kernel adds the slices and applies the epilogue.  Eight epilogue warps
+// (two column groups per TMEM lane quadrant) take per-channel constants from
+// shared memory.  All waits are bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <functional>
 #include <mutex>
+#include <unordered_map>
 
 #include "unet_internal.cuh"
 
@@ -35,16 +40,20 @@ namespace {
 constexpr int TM = 128;
 constexpr int TK = 64;
 constexpr int MAXST = 8;           // stage ring capacity (the host picks nst <= MAXST)
-constexpr int NTHR = 192;          // warps 0-3 epilogue, 4 TMA, 5 MMA
-constexpr long long kWait = 1ll << 24;
+constexpr int NEPI = 8;                  // epilogue warps: 2 column groups x 4 TMEM lane quadrants
+constexpr int WPROD = NEPI, WMMA = NEPI + 1;
+constexpr int NTHR = 32 * (NEPI + 2);    // + the TMA producer warp and the MMA warp
+constexpr long long kWait = 1ll << 26;   // polls before a wait gives up (about a second)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mb_init(uint32_t a, int c) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(c) : "memory");
 }
-__device__ __forceinline__ bool mb_try(uint32_t a, uint32_t par) {
+// Non-suspending poll: a thread parked by try_wait was measured to resume about a
+// microsecond after the phase completed, which dominated the stage hand-offs.
+__device__ __forceinline__ bool mb_test(uint32_t a, uint32_t par) {
   uint32_t ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+  asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                : "=r"(ok)
                : "r"(a), "r"(par)
                : "memory");
@@ -52,7 +61,7 @@ __device__ __forceinline__ bool mb_try(uint32_t a, uint32_t par) {
 }
 __device__ __forceinline__ bool mb_wait(uint32_t a, uint32_t par) {
   for (long long i = 0; i < kWait; ++i)
-    if (mb_try(a, par)) return true;
+    if (mb_test(a, par)) return true;
   return false;
 }
 __device__ __forceinline__ void mb_expect_tx(uint32_t a, uint32_t bytes) {
@@ -94,23 +103,26 @@ struct TmaArgs {
   int tx, ty, tb;                 // tiles along x, y and images
   int nch0, nch1;                 // 64-channel chunks per source
   int bcast1;                     // source 1 is one image shared by the batch
-  int ksplit;                     // K-block ranges per tile; > 1: atomic FP32 accumulation
+  int ksplit;                     // K-block ranges per tile; > 1: FP32 atomic accumulation
   int nitems;                     // tiles x phases x ksplit
   int nst;                        // pipeline stages (<= MAXST)
   int colsz;                      // TMEM columns of one accumulator (power of two >= 32)
-  int vec;                        // every row pointer of out / ybf / res is 16-byte aligned
+  int vec;                        // every row pointer of out / ybf / res / part is 16-byte aligned
   int kpad;                       // padded K per tap = 64 (nch0 + nch1)
   float* out; int ldo;
   const float* bias;
   const __nv_bfloat16* res; int ldr;
   const float* scale; const float* shift; int act;
   __nv_bfloat16* ybf; int ldy;
+  // split-K: split s stores its partial sums to part + s * slice ([pixels][Cout], FP32);
+  // k_splitk_finish adds the slices and applies the epilogue
+  float* part; size_t slice;
   int* err;
 };
 
 // One work item: an output tile of one phase, reduced over one K range.
 struct Item {
-  int x0, y0, b0, py, px, ky0, kx0, dk, ntx, nchk, kbeg, nkb, lead;
+  int x0, y0, b0, py, px, ky0, kx0, dk, ntx, nchk, kbeg, nkb, split;
 };
 
 __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
@@ -131,7 +143,7 @@ __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
   // balanced K ranges; the host keeps ksplit <= nkb_all, so nkb >= 1
   it.kbeg = ys * nkb_all / a.ksplit;
   it.nkb = (ys + 1) * nkb_all / a.ksplit - it.kbeg;
-  it.lead = ys == 0;
+  it.split = ys;
   const int tix = t % a.tx; t /= a.tx;
   const int tiy = t % a.ty; t /= a.ty;
   it.x0 = tix * a.BX; it.y0 = tiy * a.BY; it.b0 = t * a.BB;
@@ -140,16 +152,90 @@ __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
 
 __device__ __forceinline__ bool failed(const volatile int* f) { return *f != 0; }
 
-// Persistent: CTA c takes items c, c + gridDim.x, ...  Warp 4 streams K-blocks
-// through the stage ring across item boundaries, warp 5 accumulates item i in
-// TMEM buffer i & 1, warps 0-3 drain buffer i & 1 while the MMAs of item i + 1 run.
-__global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CUtensorMap mA0,
+// OR of a predicate over the epilogue warps (named barrier 1): a uniform decision.
+__device__ __forceinline__ bool epi_any(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(NEPI * 32)
+      : "memory");
+  return r != 0;
+}
+
+// Bias, residual, BatchNorm and eLU on 16 consecutive channels [cb, cb + 16) of one
+// pixel, then the store (BF16 y, or FP32 out).  k: per-channel constants in shared memory.
+__device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix, int cb, bool add_lin,
+                                         const uint4* r4, const float* kb, const float* ks, const float* kh) {
+  if (cb + 16 <= a.Cout && a.vec) {
+    if (add_lin) {
+      if (a.bias) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) f[j] += kb[cb + j];
+      }
+      if (a.res) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&r4[h]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float2 rf = __bfloat1622float2(r2[j]);
+            f[8 * h + 2 * j] += rf.x;
+            f[8 * h + 2 * j + 1] += rf.y;
+          }
+        }
+      }
+    }
+    if (a.ybf) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (a.scale) f[j] = f[j] * ks[cb + j] + kh[cb + j];
+        if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
+      }
+      uint4 o4[2];
+      __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(o4);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+      uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + cb);
+      yp[0] = o4[0];
+      yp[1] = o4[1];
+    } else {
+      float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int co = cb + j;
+    if (co >= a.Cout) break;
+    float g = f[j];
+    if (add_lin && a.bias) g += kb[co];
+    if (add_lin && a.res) g += __bfloat162float(a.res[pix * a.ldr + co]);
+    if (a.ybf) {
+      if (a.scale) g = g * ks[co] + kh[co];
+      if (a.act) g = g > 0.f ? g : expm1f(g);
+      a.ybf[pix * a.ldy + co] = __float2bfloat16_rn(g);
+    } else {
+      a.out[pix * a.ldo + co] = g;
+    }
+  }
+}
+
+// Persistent: CTA c takes items c, c + gridDim.x, ...  The producer warp streams
+// K-blocks through the stage ring across item boundaries, the MMA warp accumulates
+// item i in TMEM buffer i & 1, the epilogue warps drain buffer i & 1 while the MMAs
+// of item i + 1 run.
+// (two CTAs per SM for N <= 64 need <= 102 registers per thread at 320 threads)
+__global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CUtensorMap mA0,
                                                       const __grid_constant__ CUtensorMap mA1,
                                                       const __grid_constant__ CUtensorMap mB, TmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
+  __shared__ float s_bias[256], s_scale[256], s_shift[256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.NT, NS = a.nst;
 
@@ -157,10 +243,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
   const uint32_t a_bytes = TM * 128, b_bytes = (uint32_t)N * 128, stage = a_bytes + b_bytes;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
-    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), 4); }
+    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), NEPI); }
     mb_init(su32(&drain), 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
+    s_bias[c] = a.bias ? a.bias[c] : 0.f;
+    s_scale[c] = a.scale ? a.scale[c] : 1.f;
+    s_shift[c] = a.shift ? a.shift[c] : 0.f;
   }
   const uint32_t ncols = 2u * (uint32_t)a.colsz;
   if (warp == 0) {
@@ -175,7 +266,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
   const uint32_t tmem = tmem_slot;
   volatile int* fail = &s_fail;
 
-  if (warp == 4) {
+  if (warp == WPROD) {
     if (lane == 0) {
       uint32_t g = 0;   // K-blocks issued by this CTA
       for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x) {
@@ -204,7 +295,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
       for (uint32_t j = g > (uint32_t)NS ? g - (uint32_t)NS : 0u; j < g; ++j)
         mb_wait(su32(&full[j % (uint32_t)NS]), (j / (uint32_t)NS) & 1u);
     }
-  } else if (warp == 5) {
+  } else if (warp == WMMA) {
     if (lane == 0) {
       const uint32_t id = idesc(N);
       uint32_t g = 0;
@@ -247,95 +338,62 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
       mb_wait(su32(&drain), 0);
     }
   } else {
-    // epilogue: warps 0-3, tile row = tid
-    int li = 0;
-    const int m = tid;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the
+    // 16-column chunks grp, grp + 2, ... of the accumulator (grp = w / 4)
+    const int q4 = warp & 3, grp = warp >> 2;
+    const int m = q4 * 32 + lane;
     const int bb = m / (a.BY * a.BX), rr = m - bb * a.BY * a.BX, by = rr / a.BX, bx = rr - by * a.BX;
+    int li = 0;
     for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
-      if (failed(fail)) break;
+      if (epi_any(failed(fail))) break;
       const Item it = decode(a, w);
       const int acc = li & 1;
-      if (!mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+      const bool ok = mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u);
+      if (epi_any(!ok)) { atomicExch(&s_fail, 1); break; }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
       const int oy = a.transposed ? 2 * qy + it.py : qy, ox = a.transposed ? 2 * qx + it.px : qx;
       const bool rv = it.nkb > 0 && b < a.B && oy < a.Ho && ox < a.Wo;
-      const bool lead = it.lead;   // the first K range adds bias and residual
       const size_t pix = ((size_t)b * a.Ho + oy) * a.Wo + ox;
-      for (int c0 = 0; c0 < N; c0 += 16) {
+      // residual of the next chunk is requested before the current chunk's TMEM read
+      const bool pre = rv && a.ksplit <= 1 && a.res && a.vec;
+      uint4 rn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      if (pre && 16 * grp + 16 <= a.Cout) {
+        const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + 16 * grp);
+        rn[0] = rp[0]; rn[1] = rp[1];
+      }
+      for (int c0 = 16 * grp; c0 < N; c0 += 32) {
+        const uint4 rc[2] = {rn[0], rn[1]};
+        if (pre && c0 + 48 <= a.Cout) {
+          const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + 32);
+          rn[0] = rp[0]; rn[1] = rp[1];
+        }
         uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (rv) {
-          const int cb = c0;
-          float f[16];
+        if (!rv) continue;
+        float f[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int co = cb + j < a.Cout ? cb + j : a.Cout - 1;
-            f[j] = __uint_as_float(v[j]);
-            if (lead && a.bias) f[j] += a.bias[co];
-          }
-          if (cb + 16 <= a.Cout && a.vec) {
-            // full 16-channel chunk: 16-byte loads and stores along the pixel's channel row
-            if (lead && a.res) {
-              const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + cb);
+        for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
+        if (a.ksplit > 1) {
+          // partial sums of this K range into the split's slice (plain stores)
+          float* dst = a.part + (size_t)it.split * a.slice + pix * a.Cout + c0;
+          if (c0 + 16 <= a.Cout && a.vec) {
+            float4* op = reinterpret_cast<float4*>(dst);
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const uint4 r4 = rp[h];
-                const __nv_bfloat162* r2 = reinterpret_cast<const __nv_bfloat162*>(&r4);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const float2 rf = __bfloat1622float2(r2[j]);
-                  f[8 * h + 2 * j] += rf.x;
-                  f[8 * h + 2 * j + 1] += rf.y;
-                }
-              }
-            }
-            if (a.ksplit > 1) {
-              float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) atomicAdd(op + q, make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]));
-            } else if (a.ybf) {
-              uint4 o4[2];
-              __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(o4);
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if (a.scale) f[j] = f[j] * a.scale[cb + j] + a.shift[cb + j];
-                if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-              uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + cb);
-              yp[0] = o4[0];
-              yp[1] = o4[1];
-            } else {
-              float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
-            }
+            for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int co = cb + j;
-              if (co >= a.Cout) break;
-              float g = f[j];
-              if (lead && a.res) g += __bfloat162float(a.res[pix * a.ldr + co]);
-              if (a.ksplit > 1) {
-                atomicAdd(&a.out[pix * a.ldo + co], g);
-              } else if (a.ybf) {
-                if (a.scale) g = g * a.scale[co] + a.shift[co];
-                if (a.act) g = g > 0.f ? g : expm1f(g);
-                a.ybf[pix * a.ldy + co] = __float2bfloat16_rn(g);
-              } else {
-                a.out[pix * a.ldo + co] = g;
-              }
-            }
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < a.Cout) dst[j] = f[j];
           }
+        } else {
+          finish16(a, f, pix, c0, true, rc, s_bias, s_scale, s_shift);
         }
       }
       // accumulator read: hand buffer acc back to the MMA warp
@@ -350,6 +408,39 @@ __global__ void __launch_bounds__(NTHR, 1) k_conv_tma(const __grid_constant__ CU
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// Split-K epilogue: y[p][c] = act(BN(sum_s part[s][p][c] + bias[c] + res[p][c])), four
+// channels per thread (Cout % 4 == 0), BF16 into y or FP32 into out.
+__global__ void __launch_bounds__(256) k_splitk_finish(TmaArgs a, int M) {
+  const int C4 = a.Cout / 4;
+  const size_t n = (size_t)M * C4;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i / C4;
+    const int c = (int)(i - p * C4) * 4;
+    float4 t = __ldcg(reinterpret_cast<const float4*>(a.part + p * a.Cout + c));
+    for (int sp = 1; sp < a.ksplit; ++sp) {
+      const float4 u = __ldcg(reinterpret_cast<const float4*>(a.part + (size_t)sp * a.slice + p * a.Cout + c));
+      t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+    }
+    float f[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (a.bias) f[j] += a.bias[c + j];
+      if (a.res) f[j] += __bfloat162float(a.res[p * a.ldr + c + j]);
+      if (a.ybf) {
+        if (a.scale) f[j] = f[j] * a.scale[c + j] + a.shift[c + j];
+        if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
+      }
+    }
+    if (a.ybf) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a.ybf[p * a.ldy + c + j] = __float2bfloat16_rn(f[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a.out[p * a.ldo + c + j] = f[j];
+    }
   }
 }
 
@@ -425,26 +516,70 @@ void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, 
 }
 
 int sm_count() {
-  int dev = 0, n = 0;
+  static int cache[64] = {0};
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 1;
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 1;
+  }
+  return cache[dev];
+}
+
+// Encoded tensor maps, keyed by every argument of the encoding (a map only holds the
+// address and the geometry, so a hit is valid whatever happened to the buffer since).
+struct MapKey {
+  const void* p;
+  int v[10];
+  bool operator==(const MapKey& o) const {
+    if (p != o.p) return false;
+    for (int i = 0; i < 10; ++i)
+      if (v[i] != o.v[i]) return false;
+    return true;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    size_t h = std::hash<const void*>()(k.p);
+    for (int i = 0; i < 10; ++i) h = h * 1000003u ^ (size_t)(unsigned)k.v[i];
+    return h;
+  }
+};
+std::mutex g_maps_mu;
+std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_maps;
+
+template <typename F>
+bool cached_map(const MapKey& key, CUtensorMap* out, F encode) {
+  {
+    std::lock_guard<std::mutex> lk(g_maps_mu);
+    auto it = g_maps.find(key);
+    if (it != g_maps.end()) { *out = it->second; return true; }
+  }
+  if (!encode(out)) return false;
+  std::lock_guard<std::mutex> lk(g_maps_mu);
+  if (g_maps.size() > 4096) g_maps.clear();
+  g_maps.emplace(key, *out);
+  return true;
 }
 int ctas_per_sm(int nt) { return nt <= 64 ? 2 : 1; }
 
 // K split for convolutions whose pixel tiles leave most SMs idle (1 = none).
 int conv_tma_split(const ConvArgs& c) {
   const int Wq = c.transposed ? c.Wo / 2 : c.Wo, Hq = c.transposed ? c.Ho / 2 : c.Ho;
-  if (!pow2(Wq) || !pow2(Hq) || c.ldo != c.Cout || c.ybf) return 1;
+  // partial sums go to FP32 slices of the split scratch (capacity splitcnt_n floats)
+  if (!pow2(Wq) || !pow2(Hq) || !c.splitbuf || c.Cout % 4) return 1;
   const int BX = Wq < 128 ? Wq : 128;
   const int BY = Hq < 128 / BX ? Hq : 128 / BX;
   const int BB = 128 / (BX * BY);
   const int tiles = (Wq / BX) * (Hq / BY) * ((c.B + BB - 1) / BB) * (c.transposed ? 4 : 1);
+  const long long outsz = (long long)c.B * c.Ho * c.Wo * c.Cout;
   const int taps = c.transposed ? (c.k * c.k + 3) / 4 : c.k * c.k;
   const int nkb = taps * ((c.c0 + 63) / 64 + (c.in1 ? (c.c1 + 63) / 64 : 0));
   const int slots = sm_count() * ctas_per_sm(((c.Cout + 15) / 16) * 16);
   int sp = 1;
-  while (tiles * sp * 2 <= slots && nkb / (sp * 2) >= 4 && sp < 16) sp *= 2;
+  while (tiles * sp * 2 <= slots && nkb / (sp * 2) >= 4 && sp < 16 && outsz * sp * 2 <= c.splitcnt_n) sp *= 2;
   return sp;
 }
 
@@ -467,10 +602,13 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   if (c.in1 && c.bcast1 && BB > 1) TMA_REJECT("broadcast source with several images per tile");
   const int es = c.transposed ? 1 : c.stride;
   CUtensorMap mA0, mA1, mB;
-  if (!encode_act(&mA0, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY, BB, es)) TMA_REJECT("source 0 map");
+  auto act_map = [&](CUtensorMap* m, const void* p, int C, int ld, int nb) {
+    const MapKey key{p, {0, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es}};
+    return cached_map(key, m, [&](CUtensorMap* o) { return encode_act(o, p, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es); });
+  };
+  if (!act_map(&mA0, c.in0, c.c0, c.ld0, c.B)) TMA_REJECT("source 0 map");
   if (c.in1) {
-    if (!encode_act(&mA1, c.in1, c.c1, c.ld1, c.Wi, c.Hi, c.bcast1 ? 1 : c.B, BX, BY, BB, es))
-      TMA_REJECT("source 1 map");
+    if (!act_map(&mA1, c.in1, c.c1, c.ld1, c.bcast1 ? 1 : c.B)) TMA_REJECT("source 1 map");
   } else {
     mA1 = mA0;
   }
@@ -485,21 +623,30 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.bcast1 = (c.in1 && c.bcast1) ? 1 : 0;
   a.ksplit = conv_tma_split(c);
   a.kpad = 64 * (a.nch0 + a.nch1);
-  if (!encode_w(&mB, c.WP, c.k * c.k * a.kpad, c.Cout, a.NT)) TMA_REJECT("weight map");
+  {
+    const int K = c.k * c.k * a.kpad;
+    const MapKey key{c.WP, {1, K, c.Cout, a.NT, 0, 0, 0, 0, 0, 0}};
+    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, a.NT); }))
+      TMA_REJECT("weight map");
+  }
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
   a.scale = c.scale; a.shift = c.shift; a.act = c.ep_act; a.ybf = c.ybf; a.ldy = c.ldy;
   a.err = err;
+  a.part = a.ksplit > 1 ? c.splitbuf : nullptr;
+  a.slice = (size_t)c.B * c.Ho * c.Wo * c.Cout;
   a.vec = ((c.ldo % 4 == 0) && !((uintptr_t)c.out & 15) && (c.ldy % 8 == 0) && !((uintptr_t)c.ybf & 15) &&
-           (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15)))) ? 1 : 0;
+           (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15))) &&
+           (!a.part || (c.Cout % 4 == 0 && !((uintptr_t)a.part & 15)))) ? 1 : 0;
   const int nph = c.transposed ? 4 : 1;
   a.tb = (c.B + BB - 1) / BB;
   a.nitems = a.tx * a.ty * a.tb * nph * a.ksplit;
   a.colsz = a.NT <= 32 ? 32 : (a.NT <= 64 ? 64 : (a.NT <= 128 ? 128 : 256));
-  // stage ring sized to the shared memory left per CTA (228 KB per SM, 1 KB reserved per CTA,
-  // barriers and 1 KB alignment slack): 4-8 stages
+  // stage ring sized to the shared memory left per CTA (228 KB per SM; per CTA 1 KB
+  // reserved, 4 KB of static barriers and epilogue constants, 1 KB alignment slack, 1 KB
+  // margin): 4-8 stages
   const int per_sm = ctas_per_sm(a.NT);
   const size_t stage = (size_t)TM * 128 + (size_t)a.NT * 128;
-  const size_t budget = (size_t)228 * 1024 / per_sm - 1024 - 2048;
+  const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
   a.nst = (int)std::min<size_t>(MAXST, budget / stage);
   if (a.nst < 2) TMA_REJECT("shared memory");
   const size_t smem = (size_t)a.nst * stage + 1024;
@@ -518,10 +665,13 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
       max_dyn = optin - (int)fa.sharedSizeBytes;
   }
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
-  if (a.ksplit > 1 && cudaMemsetAsync(c.out, 0, (size_t)c.B * c.Ho * c.Wo * c.ldo * 4, s) != cudaSuccess)
-    TMA_REJECT("split-K clear");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
   k_conv_tma<<<grid, NTHR, smem, s>>>(mA0, mA1, mB, a);
+  if (a.ksplit > 1) {
+    const int M = c.B * c.Ho * c.Wo;
+    const size_t n4 = (size_t)M * (c.Cout / 4);
+    k_splitk_finish<<<(unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8), 256, 0, s>>>(a, M);
+  }
   g_tma_reject = "";
   return true;
 #undef TMA_REJECT

@@ -81,7 +81,10 @@ struct unet_ctx {
   int adam_t = 0;
   unet_ctx* encoder = nullptr;
   bool is_encoder = false;                         // attached to a solver: keep a BF16 copy of the output
-  int last_path = 0;                               // kernel of the last convolution: 2 TMA, 1 cp.async, 0 CUDA cores
+  float* splitbuf = nullptr;                       // split-K partial-sum slices (TMA path)
+  int* splitcnt = nullptr;
+  long long splitcnt_n = 0;                        // floats in splitbuf
+  int last_path = 0;   // kernel of the last convolution: 3 CUDA-core direct, 2 TMA, 1 cp.async, 0 generic SIMT
   bool last_train = false;
   // activation workspace for (B, ny, nx)
   int B = 0, ny = 0, nx = 0;
@@ -236,6 +239,18 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
   n->hL = a.take<__nv_bfloat16>(M(L) * w[L - 1]);
   n->out = a.take<float>(M(0) * c.out_ch);
   n->out_bf = a.take<__nv_bfloat16>(M(0) * out_ld(n));
+  {
+    // split-K partial sums: room for 4x the largest convolution output (splits only
+    // run on layers with few pixels, whose outputs are small)
+    size_t smax = 0;
+    for (int l = 1; l <= L; ++l) {
+      smax = std::max(smax, M(l) * (size_t)w[l - 1]);
+      smax = std::max(smax, M(l - 1) * (size_t)(l >= 2 ? w[l - 2] : c.out_ch));
+    }
+    n->splitcnt_n = (long long)(4 * smax);
+    n->splitbuf = a.take<float>((size_t)n->splitcnt_n);
+    n->splitcnt = nullptr;
+  }
   n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
   n->sums = a.take<double>(2 * 512);
   n->xin32 = a.take<float>(M(0) * c.in_ch);
@@ -292,10 +307,12 @@ ConvArgs conv_args(const unet_ctx* n, const ConvL& cl, Src a, Src b, bool act, i
   // the padded copy matches the layer's fixed (main, context) split
   c.WP = (a.c == cl.c0 && (b.p ? b.c : 0) == cl.c1) ? n->WPb + cl.wpoff : nullptr;
   c.out = out; c.ldo = ldo;
+  c.splitbuf = n->splitbuf; c.splitcnt = n->splitcnt; c.splitcnt_n = n->splitcnt_n;
   return c;
 }
 
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (n->use_tc && conv_forward_small(a, s)) { n->last_path = 3; return; }
   if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) { n->last_path = 2; return; }
   if (n->use_tc && conv_tc_eligible(a)) { conv_forward_tc(a, n->d_err, s); n->last_path = 1; }
   else { conv_forward(a, s); n->last_path = 0; }
@@ -361,9 +378,8 @@ void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s) {
 // tensor-core path the normalisation is applied in the convolution's epilogue.
 void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bfloat16* y, int ldy, int M, bool train,
              cudaStream_t s) {
-  // inference: BatchNorm and eLU fused into the tensor-core epilogue, unless the
-  // TMA path splits K (partial sums are accumulated in FP32 first)
-  if (!train && n->use_tc && !(n->use_tma && conv_tma_split(a) > 1)) {
+  // inference: BatchNorm and eLU fused into the convolution's epilogue
+  if (!train && n->use_tc) {
     ConvArgs f = a;
     const BnL& b = bn_of(n, bn);
     ensure_eval_coeffs(n, s);
@@ -372,6 +388,7 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     f.ep_act = act ? 1 : 0;
     f.ybf = y;
     f.ldy = ldy;
+    if (conv_forward_small(f, s)) { n->last_path = 3; return; }
     if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; return; }
     if (conv_tc_eligible(f)) {
       conv_forward_tc(f, n->d_err, s);
@@ -385,7 +402,7 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
 
 // Materialise eLU of an up convolution's inputs for the tensor-core gather.
 ConvArgs act_inputs(unet_ctx* n, ConvArgs a, int l, const Src& u, const Src& f, int H, int W, int M, cudaStream_t s) {
-  if (!n->use_tc) return a;
+  if (!n->use_tc || conv_small_eligible(a)) return a;   // the direct kernel applies eLU while staging
   ConvArgs t = a;
   t.in_act = 0;
   if (!conv_tc_eligible(t)) return a;
@@ -846,44 +863,61 @@ int unet_time_layer(unet_t n, int layer, int reps, helm_stream_t stream, float* 
                   n->t1[lvl][0], w[lvl - 1]);
   } else {
     H = n->ny >> lvl; W = n->nx >> lvl;
-    const int cu = lvl == L ? w[L - 1] : 2 * w[lvl - 1];
-    Src u{n->uact[lvl], cu, cu, false};
-    Src f = feat_of(n, lvl);
-    if (f.p) f = Src{n->fact[lvl], f.c, f.c, f.bcast};
-    a = conv_args(n, cl, u, f, false, H, W, lvl >= 2 ? n->zup[lvl] : n->out, lvl >= 2 ? w[lvl - 2] : c.out_ch);
+    // the forward's sources (eLU on load), then the same materialisation decision
+    const Src u = lvl == L ? Src{n->hL, w[L - 1], w[L - 1], false}
+                           : Src{n->cat[lvl], 2 * w[lvl - 1], 2 * w[lvl - 1], false};
+    const Src f = feat_of(n, lvl);
+    a = conv_args(n, cl, u, f, true, H, W, lvl >= 2 ? n->zup[lvl] : n->out, lvl >= 2 ? w[lvl - 2] : c.out_ch);
     if (lvl == 1) a.bias = n->P + n->bias_off;
-    if (!(n->use_tc && conv_tc_eligible(a))) a.in_act = 1;
+    a = act_inputs(n, a, lvl, u, f, H, W, n->B * H * W, s);
   }
   const double taps_eff = cl.kind == 2 ? (double)cl.k * cl.k / 4.0 : (double)cl.k * cl.k;
   *flops = 2.0 * (double)n->B * a.Ho * a.Wo * taps_eff * cl.cin * cl.cout;
   // the inference form of the layer: BatchNorm (+ eLU) into BF16 as the forward does it
   // (this overwrites the layer's activation buffer; the next forward rewrites it)
   const int Ml = n->B * a.Ho * a.Wo;
-  auto launch = [&] {
-    if (cl.kind == 0) conv_bn(n, a, cl.name + ".bn", true, n->h0[lvl], w[lvl - 1], Ml, false, s);
+  auto launch = [&](cudaStream_t st) {
+    if (cl.kind == 0) conv_bn(n, a, cl.name + ".bn", true, n->h0[lvl], w[lvl - 1], Ml, false, st);
     else if (cl.kind == 1) {
       const bool second = cl.name.compare(cl.name.size() - 2, 2, "k2") == 0;
       conv_bn(n, a, cl.name.substr(0, cl.name.size() - 2) + (second ? "bn2" : "bn1"), true, n->a1[lvl][0],
-              w[lvl - 1], Ml, false, s);
+              w[lvl - 1], Ml, false, st);
     } else if (lvl >= 2) {
-      conv_bn(n, a, cl.name + ".bn", false, n->cat[lvl - 1], 2 * w[lvl - 2], Ml, false, s);
+      conv_bn(n, a, cl.name + ".bn", false, n->cat[lvl - 1], 2 * w[lvl - 2], Ml, false, st);
     } else {
-      run_conv(n, a, s);
+      run_conv(n, a, st);
     }
   };
-  launch();  // warm-up
+  launch(s);  // warm-up (also settles the inference BatchNorm coefficients)
   *tc = n->last_path;
-  cudaEvent_t e0, e1;
-  UCHECK(cudaEventCreate(&e0));
-  UCHECK(cudaEventCreate(&e1));
-  UCHECK(cudaEventRecord(e0, s));
-  for (int r = 0; r < reps; ++r) launch();
-  UCHECK(cudaEventRecord(e1, s));
-  UCHECK(cudaEventSynchronize(e1));
+  UCHECK(cudaStreamSynchronize(s));
+  // device time without host launch overhead: the repetitions replay as one CUDA graph
+  cudaStream_t cs = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   float t = 0;
-  UCHECK(cudaEventElapsedTime(&t, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int r = 0; r < reps; ++r) launch(cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, cs);   // warm replay
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  UCHECK(e);
   *ms = t / reps;
   UCHECK(cudaGetLastError());
   return HELM_OK;

@@ -31,9 +31,16 @@ struct ConvArgs {
   // fused inference BatchNorm epilogue (tensor-core path only): y = act((conv + res) * scale + shift)
   const float* scale; const float* shift; int ep_act;
   __nv_bfloat16* ybf; int ldy;       // BF16 destination; when set, `out` is not written
+  // split-K scratch of the TMA path: splitcnt_n floats for the FP32 partial-sum slices
+  // (null: not split)
+  float* splitbuf; int* splitcnt; long long splitcnt_n;
 };
 
 void conv_forward(const ConvArgs& a, cudaStream_t s);
+// CUDA-core direct convolutions (conv_small.cu) for the 5x5 stride-2 layer from <= 8
+// input channels and the transposed 5x5 stride-2 layer to <= 4 outputs.
+bool conv_small_eligible(const ConvArgs& a);
+bool conv_forward_small(const ConvArgs& a, cudaStream_t s);
 // Tensor-core path (conv_tc.cu): eligible when inputs are BF16 without on-load
 // activation, channel counts are multiples of 8, Cout a multiple of 16 (<= 256).
 bool conv_tc_eligible(const ConvArgs& a);

@@ -421,7 +421,8 @@ class UNet:
         return bool(f.value)
 
     def time_layer(self, layer, reps=20, stream=None):
-        """(ms per repetition, flops, kernel: 2 TMA tensor core, 1 cp.async tensor core, 0 CUDA cores)
+        """(ms per repetition, flops, kernel: 3 direct CUDA-core, 2 TMA tensor core, 1 cp.async tensor core,
+        0 generic CUDA-core)
         of convolution `layer` in its inference form."""
         ms, fl, tc = ctypes.c_float(), ctypes.c_double(), ctypes.c_int()
         _check(self.lib.unet_time_layer(self.handle, layer, reps, _stream(stream), ctypes.byref(ms), ctypes.byref(fl),

@@ -5,6 +5,8 @@
   python -m paper_2203_11025_gb300.profcase layers 256 8   # per-layer times of the U-Net forward
   python -m paper_2203_11025_gb300.profcase mvu 256 8      # one FGMRES(10) restart cycle with M_VU
                                                            # (profiler range = that cycle)
+  python -m paper_2203_11025_gb300.profcase train 256 16   # one training step (forward, MSE, backward,
+                                                           # Adam; profiler range = that step)
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -38,7 +40,7 @@ def main(argv):
             for i, nm in enumerate(names):
                 ms, fl, tc = net.time_layer(i, reps=10)
                 tot += ms
-                kind = {2: "tma-tc", 1: "cpasync-tc"}.get(tc, "cuda-core")
+                kind = {3: "direct", 2: "tma-tc", 1: "cpasync-tc"}.get(tc, "cuda-core")
                 print(f"{nm:12s} {ms * 1e3:8.1f} us {fl / ms / 1e9:7.1f} TFLOP/s {kind}")
             print(f"total {tot * 1e3:.1f} us")
     elif what == "coarse":
@@ -60,6 +62,28 @@ def main(argv):
         torch.cuda.profiler.start()
         hz.fgmres(rhs, x, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=10, restart=10,
                   flags=lib.HELM_FLAG_X0_ZERO)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    elif what == "train":
+        from paper_2203_11025_gb300 import train as T
+        k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=1)
+        r, e = hz.gen_pairs(b, 5151, 10)
+        idx, coef = next(T.batches(np.random.default_rng(0), b, b, 2))
+        x, t = hz.make_batch(r, e, idx, coef)
+
+        def step():
+            net.zero_grad()
+            out = net.forward(x, train=True)
+            _, g = net.mse(out, t)
+            net.backward(g)
+            net.adam_step(lr=1e-4)
+        step()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     else:
