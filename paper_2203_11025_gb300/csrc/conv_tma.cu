@@ -500,7 +500,34 @@ __global__ void k_weights_padded(const float* __restrict__ P, __nv_bfloat16* __r
   }
 }
 
+// Adjoint copy for data gradients: the convolution of dL/dy with W^T, as a forward
+// convolution with Cin' = cout inputs and Cout' = cin outputs:
+// WPA[ci][tap'][kpad'] = W[tap][ci][co] (co < cout), tap = taps - 1 - tap' when flipped.
+__global__ void k_weights_adjoint(const float* __restrict__ P, __nv_bfloat16* __restrict__ WPA, int taps, int cin,
+                                  int cout, int kpad, int flip) {
+  const size_t n = (size_t)cin * taps * kpad;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(i % kpad);
+    const size_t r = i / kpad;
+    const int tp = (int)(r % taps), ci = (int)(r / taps);
+    const int tap = flip ? taps - 1 - tp : tp;
+    WPA[i] = __float2bfloat16_rn(co < cout ? P[((size_t)tap * cin + ci) * cout + co] : 0.f);
+  }
+}
+
 }  // namespace
+
+size_t conv_tma_weight_adj_elems(int k, int cin, int cout) {
+  return (size_t)cin * k * k * 64 * ((cout + 63) / 64);
+}
+
+void conv_tma_weights_adjoint(const float* P, __nv_bfloat16* WPA, int k, int cin, int cout, bool flip,
+                              cudaStream_t s) {
+  const int kpad = 64 * ((cout + 63) / 64);
+  const size_t n = (size_t)cin * k * k * kpad;
+  k_weights_adjoint<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WPA, k * k, cin, cout, kpad,
+                                                                                     flip ? 1 : 0);
+}
 
 size_t conv_tma_weight_elems(int k, int c0, int c1, int cout) {
   const int kpad = 64 * ((c0 + 63) / 64 + (c1 + 63) / 64);
@@ -675,6 +702,295 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   g_tma_reject = "";
   return true;
 #undef TMA_REJECT
+}
+
+// ===========================================================================
+// Weight gradients on the tensor cores:
+//   dW[tap][ci][co] = sum over pixels p of X_tap(p)[ci] * G(p)[co]
+// as a GEMM with M = 128 input channels, N = Cout (padded to 64), K = 64-pixel
+// blocks.  Both operands come from the NHWC tensors as TMA boxes {64 channels,
+// 64 pixels}, i.e. MN-major (channels contiguous) in shared memory; the tap's
+// offset, the stride and the transposed convolution's output parity are box
+// coordinates and element strides on the pixel dimensions.  Items (tap, channel
+// block, pixel chunk) run on a persistent grid; each adds its FP32 tile into dW
+// with vector atomics.
+// ===========================================================================
+namespace {
+
+constexpr int WG_THR = 192;   // warps 0-3 epilogue, 4 TMA, 5 MMA
+
+struct WgArgs {
+  int k, pad, kind;           // kind 0: 5x5 stride 2, 1: stride 1, 2: transposed stride 2
+  int B, tx, ty, bx, by;      // K grid: tx * ty blocks of bx x by pixels per image
+  int cin, cout, mblk, NT;    // 128-channel blocks of cin; N = Cout padded to 64
+  int nchunks, nitems, nst, colsz;
+  uint32_t lbo, sbo;          // MN-major descriptor strides (bytes)
+  int vec;                    // gW rows 16-byte aligned (float4 atomics)
+  float* gW;
+  int* err;
+};
+
+__device__ __forceinline__ uint64_t desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+// kind::f16, FP32 accumulate, BF16 A and B, both MN-major (transpose bits 15, 16)
+__host__ __device__ constexpr uint32_t idesc_mn(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+struct WgItem { int tap, mb, kb0, nkb; };
+
+__device__ __forceinline__ WgItem wg_decode(const WgArgs& a, int w) {
+  WgItem it;
+  const int chunk = w % a.nchunks, r = w / a.nchunks;
+  it.mb = r % a.mblk;
+  it.tap = r / a.mblk;
+  const int KB = a.B * a.tx * a.ty;
+  it.kb0 = (int)((long long)chunk * KB / a.nchunks);
+  it.nkb = (int)((long long)(chunk + 1) * KB / a.nchunks) - it.kb0;
+  return it;
+}
+
+__global__ void __launch_bounds__(WG_THR, 1) k_wgrad_tma(const __grid_constant__ CUtensorMap mX,
+                                                         const __grid_constant__ CUtensorMap mG, WgArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.NT, NS = a.nst;
+  const uint32_t base = (su32(smem) + 1023u) & ~1023u;
+  const uint32_t a_bytes = 2 * 8192, b_bytes = (uint32_t)(N / 64) * 8192, stage = a_bytes + b_bytes;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
+    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), 4); }
+    mb_init(su32(&drain), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  const uint32_t ncols = 2u * (uint32_t)a.colsz;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* fail = &s_fail;
+  const int kbi = a.tx * a.ty;   // K-blocks per image
+
+  if (warp == 4) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x) {
+        const WgItem it = wg_decode(a, w);
+        const int ky = it.tap / a.k, kx = it.tap - ky * a.k;
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+          const int s = (int)(g % (uint32_t)NS);
+          const uint32_t use = g / (uint32_t)NS;
+          if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
+          const int kg = it.kb0 + kb;
+          const int b = kg / kbi, r = kg - b * kbi, tyi = r / a.tx, txi = r - tyi * a.tx;
+          const int x0 = txi * a.bx, y0 = tyi * a.by;
+          int xx, xy, gx, gy;   // box origins of X and G (TMA coordinates of the pixel dims)
+          if (a.kind == 1) { xx = x0 + kx - a.pad; xy = y0 + ky - a.pad; gx = x0; gy = y0; }
+          else if (a.kind == 0) { xx = 2 * x0 + kx - a.pad; xy = 2 * y0 + ky - a.pad; gx = x0; gy = y0; }
+          else { xx = x0; xy = y0; gx = 2 * x0 + kx - a.pad; gy = 2 * y0 + ky - a.pad; }
+          const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
+          mb_expect_tx(su32(&full[s]), stage);
+          tma_load_4d(sA, &mX, it.mb * 128, xx, xy, b, su32(&full[s]));
+          tma_load_4d(sA + 8192, &mX, it.mb * 128 + 64, xx, xy, b, su32(&full[s]));
+          for (int nb = 0; nb < N / 64; ++nb) tma_load_4d(sB + nb * 8192, &mG, nb * 64, gx, gy, b, su32(&full[s]));
+        }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
+      }
+      for (uint32_t j = g > (uint32_t)NS ? g - (uint32_t)NS : 0u; j < g; ++j)
+        mb_wait(su32(&full[j % (uint32_t)NS]), (j / (uint32_t)NS) & 1u);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t id = idesc_mn(128, N);
+      uint32_t g = 0;
+      int li = 0;
+      for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x, ++li) {
+        const WgItem it = wg_decode(a, w);
+        const int acc = li & 1;
+        if (li >= 2 && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> 1) - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+          const int s = (int)(g % (uint32_t)NS);
+          if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {   // 16 pixels (two 8-row groups) per MMA
+            const uint64_t da = desc_mn(sA + (uint32_t)k4 * 2048u, a.lbo, a.sbo);
+            const uint64_t db = desc_mn(sB + (uint32_t)k4 * 2048u, a.lbo, a.sbo);
+            const uint32_t accum = (kb > 0 || k4 > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(da), "l"(db), "r"(id), "r"(accum)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           su32(&empty[s]))
+                       : "memory");
+        }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         su32(&tfull[acc]))
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
+                   : "memory");
+      mb_wait(su32(&drain), 0);
+    }
+  } else {
+    // epilogue: row m = input channel mb * 128 + m, columns = output channels
+    int li = 0;
+    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
+      if (failed(fail)) break;
+      const WgItem it = wg_decode(a, w);
+      const int acc = li & 1;
+      if (!mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int ci = it.mb * 128 + warp * 32 + lane;
+      float* row = a.gW + ((size_t)it.tap * a.cin + ci) * a.cout;
+      const bool vec = a.vec != 0;
+      for (int c0 = 0; c0 < N && c0 < a.cout; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (ci >= a.cin || it.nkb <= 0) continue;
+        if (vec && c0 + 16 <= a.cout) {
+          float4* op = reinterpret_cast<float4*>(row + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            atomicAdd(op + q, make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                          __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < a.cout) atomicAdd(row + c0 + j, __uint_as_float(v[j]));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&tempty[acc])) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && s_fail && a.err) atomicExch(a.err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// MN-major descriptor strides: (LBO, SBO) = (channel-atom stride, 8-pixel-group stride)
+// when wg_desc_order == 0, swapped otherwise.
+int g_wg_desc_order = 0;
+
+}  // namespace
+
+void conv_wgrad_tma_set_desc_order(int order) { g_wg_desc_order = order; }
+
+// dW += weight gradient of the forward convolution c (single BF16 source, no on-load
+// activation) from g = dL/dy (BF16 [pixels][Cout], ld ldg).  False: not eligible.
+bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s) {
+  if (c.in1 || c.in_act || c.in_f32 || c.Cout > 256 || c.ld0 % 8 || ldg % 8) return false;
+  if (c.k != 3 && c.k != 5) return false;
+  if (!get_encoder()) return false;
+  const int kind = c.transposed ? 2 : (c.stride == 2 ? 0 : 1);
+  if (kind == 1 && c.stride != 1) return false;
+  // K grid: output pixels (kinds 0, 1) or input pixels (transposed)
+  const int Wk = kind == 2 ? c.Wi : c.Wo, Hk = kind == 2 ? c.Hi : c.Ho;
+  if (!pow2(Wk) || !pow2(Hk) || Wk * Hk < 64) return false;
+  if (kind == 2 && (c.Wo != 2 * c.Wi || c.Ho != 2 * c.Hi)) return false;
+  WgArgs a;
+  a.k = c.k; a.pad = c.pad; a.kind = kind; a.B = c.B;
+  a.bx = Wk < 64 ? Wk : 64;
+  a.by = 64 / a.bx;
+  a.tx = Wk / a.bx; a.ty = Hk / a.by;
+  a.cin = c.c0; a.cout = c.Cout;
+  a.mblk = (c.c0 + 127) / 128;
+  a.NT = 64 * ((c.Cout + 63) / 64);
+  a.colsz = a.NT <= 64 ? 64 : (a.NT <= 128 ? 128 : 256);
+  const int taps = c.k * c.k;
+  const int KB = c.B * a.tx * a.ty;
+  const int per_sm = a.NT <= 64 ? 2 : 1;
+  const int slots = sm_count() * per_sm;
+  int nch = (2 * slots + taps * a.mblk - 1) / (taps * a.mblk);
+  nch = std::max(1, std::min(nch, KB / 8 > 0 ? KB / 8 : 1));
+  a.nchunks = nch;
+  a.nitems = taps * a.mblk * nch;
+  a.lbo = g_wg_desc_order == 0 ? 8192u : 1024u;
+  a.sbo = g_wg_desc_order == 0 ? 1024u : 8192u;
+  a.gW = gW;
+  a.err = err;
+  a.vec = (c.Cout % 4 == 0 && !((uintptr_t)gW & 15)) ? 1 : 0;
+  // the ring, 1 KB alignment slack and 16 KB past the last stage (descriptor strides
+  // reach at most 16 KB beyond a stage's start whichever field carries which stride)
+  const size_t stage = 2 * 8192 + (size_t)(a.NT / 64) * 8192;
+  const size_t budget = (size_t)228 * 1024 / per_sm - 21 * 1024;
+  a.nst = (int)std::min<size_t>(MAXST, budget / stage);
+  if (a.nst < 2) return false;
+  const size_t smem = (size_t)a.nst * stage + 1024 + 16 * 1024;
+  static int max_dyn = -1;
+  if (max_dyn < 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_wgrad_tma) != cudaSuccess ||
+        cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+      max_dyn = 0;
+    else
+      max_dyn = optin - (int)fa.sharedSizeBytes;
+  }
+  if ((long long)smem > max_dyn) return false;
+  // X: box {64 channels, bx (x es), by (x es), 1}; G likewise (element stride 2 on G for
+  // transposed convolutions, on X for stride-2 ones)
+  const int ex = kind == 0 ? 2 : 1, eg = kind == 2 ? 2 : 1;
+  CUtensorMap mX, mG;
+  {
+    const MapKey key{c.in0, {2, c.c0, c.ld0, c.Wi, c.Hi, c.B, a.bx, a.by, ex, 0}};
+    if (!cached_map(key, &mX, [&](CUtensorMap* o) {
+          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, a.bx, a.by, 1, ex);
+        }))
+      return false;
+  }
+  {
+    const MapKey key{g, {3, c.Cout, ldg, c.Wo, c.Ho, c.B, a.bx, a.by, eg, 0}};
+    if (!cached_map(key, &mG, [&](CUtensorMap* o) {
+          return encode_act(o, g, c.Cout, ldg, c.Wo, c.Ho, c.B, a.bx, a.by, 1, eg);
+        }))
+      return false;
+  }
+  const int grid = std::min(a.nitems, slots);
+  k_wgrad_tma<<<grid, WG_THR, smem, s>>>(mX, mG, a);
+  return true;
 }
 
 }  // namespace helm

@@ -44,6 +44,7 @@ struct ConvL {
   size_t woff;              // offset in the flat parameter vector
   int c0, c1;               // input split: main source, encoder context
   size_t wpoff;             // offset of the padded weight copy (TMA path)
+  size_t wpaoff;            // offset of the padded adjoint copy (data gradients on the TMA path)
 };
 struct BnL { std::string name; int c; size_t goff; size_t soff; };
 
@@ -71,6 +72,9 @@ struct unet_ctx {
   __nv_bfloat16* WTb = nullptr;                    // K-major weight copies (tensor-core path)
   __nv_bfloat16* WPb = nullptr;                    // padded K-major weight copies (TMA path)
   size_t nwp = 0;
+  __nv_bfloat16* WPAb = nullptr;                   // padded adjoint copies (data gradients, TMA path)
+  size_t nwpa = 0;
+  __nv_bfloat16* gbf = nullptr;                    // BF16 copy of a layer's output gradient
   bool use_tma = true;
   int* d_err = nullptr;                            // failure record of the tensor-core kernel
   bool use_tc = true;
@@ -99,14 +103,15 @@ struct unet_ctx {
   __nv_bfloat16* hL = nullptr;                     // coarsest output
   std::vector<float*> zup;                         // [l] (2..L) raw up conv output at level l-1
   std::vector<__nv_bfloat16*> uact, fact;          // eLU'd up-conv inputs (tensor-core path)
+  std::vector<char> uact_ok;                       // uact[l] holds the last forward's eLU'd input
   float* out = nullptr;                            // final output (FP32)
   __nv_bfloat16* out_bf = nullptr;                 // BF16 copy (encoder feature f^(0))
   // backward buffers
   std::vector<float*> gU, gzup, gD, gzd, gfeat;
   std::vector<std::vector<float*>> gS, gA1, gT1, gH2;
   float* part = nullptr;                           // reduction partials
-  double* sums = nullptr;
-  int nblk = 64;
+  float* bncoef = nullptr;                         // per-channel BatchNorm backward coefficients
+  int nblk = 1024;                                 // pixel blocks of the per-channel reductions
   // preconditioner scratch
   float *xin32 = nullptr, *scale = nullptr;
   void* tmp_e = nullptr;
@@ -118,6 +123,8 @@ namespace {
 // Row stride of the network input and output copies: padded to 8 channels so that
 // rows are 16-byte aligned (the TMA path zero-fills the channels past the real ones).
 int xin_ld(const unet_ctx* n) { return (n->cfg.in_ch + 7) / 8 * 8; }
+// Row stride of the BF16 copy of a layer's output gradient (channels past cout unused).
+int gbf_ld(int cout) { return (cout + 7) / 8 * 8; }
 int out_ld(const unet_ctx* n) { return (n->cfg.out_ch + 7) / 8 * 8; }
 
 int level_ch_in(const unet_ctx* n, int l) {  // channels of the down-conv source at level l-1
@@ -129,11 +136,12 @@ void build_layout(unet_ctx* n) {
   const int L = c.levels;
   n->L = L;
   size_t off = 0, soff = 0;
-  size_t wpo = 0;
+  size_t wpo = 0, wpao = 0;
   auto conv = [&](const std::string& nm, int kind, int k, int ci, int co, int c1) {
-    n->convs.push_back({nm, kind, k, ci, co, off, ci - c1, c1, wpo});
+    n->convs.push_back({nm, kind, k, ci, co, off, ci - c1, c1, wpo, wpao});
     off += (size_t)k * k * ci * co;
     wpo += conv_tma_weight_elems(k, ci - c1, c1, co);
+    wpao += conv_tma_weight_adj_elems(k, ci, co);
   };
   std::vector<std::pair<std::string, int>> bnl;
   int cin = c.in_ch;
@@ -160,6 +168,7 @@ void build_layout(unet_ctx* n) {
   }
   conv("up1", 2, 5, ucin + c.context[1], c.out_ch, c.context[1]);
   n->nwp = wpo;
+  n->nwpa = wpao;
   n->bias_off = off;
   off += c.out_ch;
   for (auto& b : bnl) {
@@ -250,9 +259,10 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
     n->splitcnt_n = (long long)(4 * smax);
     n->splitbuf = a.take<float>((size_t)n->splitcnt_n);
     n->splitcnt = nullptr;
+    n->gbf = a.take<__nv_bfloat16>(std::max(smax, M(0) * (size_t)gbf_ld(c.out_ch)));
   }
   n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
-  n->sums = a.take<double>(2 * 512);
+  n->bncoef = a.take<float>(5 * 512);
   n->xin32 = a.take<float>(M(0) * c.in_ch);
   n->scale = a.take<float>((size_t)B + 8);
 }
@@ -334,6 +344,48 @@ ConvArgs dgrad_args(const unet_ctx* n, const ConvL& cl, const float* g, int ldg,
   return c;
 }
 
+// Data gradient dL/dx of convolution cl from g = dL/dy (FP32, ld ldg, grid Hg x Wg): on
+// the TMA tensor-core path as a forward convolution of a BF16 copy of g with the
+// adjoint weights (3x3 stride 1: taps reversed; 5x5 stride 2: transposed stride 2;
+// transposed 5x5: stride 2), else on the generic kernel.
+void run_dgrad(unet_ctx* n, const ConvL& cl, const float* g, int ldg, int Hg, int Wg, float* out, int ldo,
+               cudaStream_t s, bool have_gbf = false) {
+  if (n->use_tc && n->use_tma) {
+    const int Mg = n->B * Hg * Wg;
+    ConvArgs c{};
+    c.in0 = n->gbf; c.c0 = cl.cout; c.ld0 = gbf_ld(cl.cout); c.in1 = nullptr; c.c1 = 0;
+    c.B = n->B; c.Hi = Hg; c.Wi = Wg; c.k = cl.k;
+    if (cl.kind == 0) { c.stride = 2; c.pad = 2; c.transposed = 1; c.Ho = 2 * Hg; c.Wo = 2 * Wg; }
+    else if (cl.kind == 1) { c.stride = 1; c.pad = 1; c.transposed = 0; c.Ho = Hg; c.Wo = Wg; }
+    else { c.stride = 2; c.pad = 2; c.transposed = 0; c.Ho = Hg / 2; c.Wo = Wg / 2; }
+    c.Cout = cl.cin;
+    c.WP = n->WPAb + cl.wpaoff;
+    c.out = out; c.ldo = ldo;
+    c.splitbuf = n->splitbuf; c.splitcnt = n->splitcnt; c.splitcnt_n = n->splitcnt_n;
+    if (!have_gbf) to_bf16_slice(g, ldg, n->gbf, gbf_ld(cl.cout), cl.cout, Mg, s);
+    if (conv_forward_tma(c, n->d_err, s)) return;
+  }
+  conv_forward(dgrad_args(n, cl, g, ldg, Hg, Wg, out, ldo), s);
+}
+
+// Weight gradient gW += dW of the forward convolution fa from g = dL/dy (FP32, ld ldg)
+// and, when dx is set, the data gradient into dx: both from one BF16 copy of g on the
+// tensor-core path.  `act_src`: the materialised eLU copy of fa's input, if any.
+void backprop_conv(unet_ctx* n, const ConvL& cl, ConvArgs fa, const float* g, int ldg, float* gW, int Hg, int Wg,
+                   float* dx, int lddx, cudaStream_t s, const __nv_bfloat16* act_src = nullptr) {
+  bool have = false;
+  if (n->use_tc && n->use_tma) {
+    to_bf16_slice(g, ldg, n->gbf, gbf_ld(cl.cout), cl.cout, n->B * Hg * Wg, s);
+    have = true;
+    ConvArgs t = fa;
+    if (t.in_act && act_src && !t.in1) { t.in0 = act_src; t.ld0 = t.c0; t.in_act = 0; }
+    if (!conv_wgrad_tma(t, n->gbf, gbf_ld(cl.cout), gW, n->d_err, s)) conv_wgrad(fa, g, ldg, gW, s);
+  } else {
+    conv_wgrad(fa, g, ldg, gW, s);
+  }
+  if (dx) run_dgrad(n, cl, g, ldg, Hg, Wg, dx, lddx, s, have);
+}
+
 void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s);
 
 // BatchNorm (train: batch statistics, running update; eval: running statistics),
@@ -363,7 +415,7 @@ void run_bn_bwd(unet_ctx* n, const std::string& nm, const float* g, int ldg, con
   const BnL& b = bn_of(n, nm);
   bn_backward(g, ldg, z, ldz, b.c, M, n->bn_mean + b.soff, n->bn_var + b.soff, n->bn_scale + b.soff,
               n->bn_shift + b.soff, act, n->P + b.goff, n->G + b.goff, n->G + b.goff + b.c, n->part, n->nblk,
-              n->sums, gz, ldo, s);
+              n->bncoef, gz, ldo, s);
 }
 
 void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s) {
@@ -407,6 +459,7 @@ ConvArgs act_inputs(unet_ctx* n, ConvArgs a, int l, const Src& u, const Src& f, 
   t.in_act = 0;
   if (!conv_tc_eligible(t)) return a;
   elu_copy_bf16((const __nv_bfloat16*)u.p, u.ld, u.c, (size_t)M, n->uact[l], u.c, s);
+  if ((int)n->uact_ok.size() > l) n->uact_ok[l] = 1;
   t.in0 = n->uact[l];
   t.ld0 = u.c;
   if (f.p) {
@@ -421,6 +474,7 @@ ConvArgs act_inputs(unet_ctx* n, ConvArgs a, int l, const Src& u, const Src& f, 
 int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
   const unet_cfg& c = n->cfg;
   const int L = n->L;
+  n->uact_ok.assign(L + 1, 0);
   const int* w = c.widths;
   auto hw = [&](int l, int& H, int& W) { H = n->ny >> l; W = n->nx >> l; };
   auto M = [&](int l) { return n->B * (n->ny >> l) * (n->nx >> l); };
@@ -499,9 +553,9 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     hw(1, H, W);
     Src u = L > 1 ? Src{n->cat[1], 2 * w[0], 2 * w[0], false} : Src{n->hL, w[0], w[0], false};
     ConvArgs fa = conv_args(n, cl, u, feat_of(n, 1), true, H, W, nullptr, 0);
-    conv_wgrad(fa, gout, c.out_ch, n->G + cl.woff, s);
     const int cu = u.c, ldU = cu + c.context[1];
-    conv_forward(dgrad_args(n, cl, gout, c.out_ch, n->ny, n->nx, n->gU[1], ldU), s);
+    backprop_conv(n, cl, fa, gout, c.out_ch, n->G + cl.woff, n->ny, n->nx, n->gU[1], ldU, s,
+                  n->uact_ok[1] ? n->uact[1] : nullptr);
     elu_backward_inplace(n->gU[1], ldU, (const __nv_bfloat16*)u.p, u.ld, cu, M(1), 0, s);
     if (c.context[1]) {
       Src f = feat_of(n, 1);
@@ -522,11 +576,11 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     hw(l, H, W);
     Src u = (l == L) ? Src{n->hL, w[L - 1], w[L - 1], false} : Src{n->cat[l], 2 * w[l - 1], 2 * w[l - 1], false};
     ConvArgs fa = conv_args(n, cl, u, feat_of(n, l), true, H, W, nullptr, 0);
-    conv_wgrad(fa, n->gzup[l], cz, n->G + cl.woff, s);
     const int ldU = u.c + c.context[l];
     int Hg, Wg;
     hw(l - 1, Hg, Wg);
-    conv_forward(dgrad_args(n, cl, n->gzup[l], cz, Hg, Wg, n->gU[l], ldU), s);
+    backprop_conv(n, cl, fa, n->gzup[l], cz, n->G + cl.woff, Hg, Wg, n->gU[l], ldU, s,
+                  n->uact_ok[l] ? n->uact[l] : nullptr);
     elu_backward_inplace(n->gU[l], ldU, (const __nv_bfloat16*)u.p, u.ld, u.c, M(l), 0, s);
     if (c.context[l]) {
       Src f = feat_of(n, l);
@@ -557,13 +611,11 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
       run_bn_bwd(n, pre + ".bn2", gh, ldgh, n->sres[l][r], cw, M(l), true, n->gS[l][r], cw, s);
       const ConvL& k2 = conv_of(n, pre + ".k2");
       ConvArgs fa2 = conv_args(n, k2, Src{n->a1[l][r], cw, cw, false}, Src{nullptr, 0, 0, false}, false, Hl, Wl, nullptr, 0);
-      conv_wgrad(fa2, n->gS[l][r], cw, n->G + k2.woff, s);
-      conv_forward(dgrad_args(n, k2, n->gS[l][r], cw, Hl, Wl, n->gA1[l][r], cw), s);
+      backprop_conv(n, k2, fa2, n->gS[l][r], cw, n->G + k2.woff, Hl, Wl, n->gA1[l][r], cw, s);
       run_bn_bwd(n, pre + ".bn1", n->gA1[l][r], cw, n->t1[l][r], cw, M(l), true, n->gT1[l][r], cw, s);
       const ConvL& k1 = conv_of(n, pre + ".k1");
       ConvArgs fa1 = conv_args(n, k1, Src{hin, cw, cw, false}, Src{nullptr, 0, 0, false}, false, Hl, Wl, nullptr, 0);
-      conv_wgrad(fa1, n->gT1[l][r], cw, n->G + k1.woff, s);
-      conv_forward(dgrad_args(n, k1, n->gT1[l][r], cw, Hl, Wl, n->gH2[l][r], cw), s);
+      backprop_conv(n, k1, fa1, n->gT1[l][r], cw, n->G + k1.woff, Hl, Wl, n->gH2[l][r], cw, s);
       add_slice(n->gH2[l][r], cw, n->gS[l][r], cw, cw, M(l), s);   // identity branch
       gh = n->gH2[l][r];
       ldgh = cw;
@@ -574,9 +626,8 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     hw(l - 1, H, W);
     Src src = l == 1 ? Src{n->x_in, c.in_ch, xin_ld(n), false} : Src{n->cat[l - 1] + w[l - 2], w[l - 2], 2 * w[l - 2], false};
     ConvArgs fa = conv_args(n, dl, src, feat_of(n, l - 1), false, H, W, nullptr, 0);
-    conv_wgrad(fa, n->gzd[l], cw, n->G + dl.woff, s);
     const int ldD = src.c + c.context[l - 1];
-    conv_forward(dgrad_args(n, dl, n->gzd[l], cw, Hl, Wl, n->gD[l], ldD), s);
+    backprop_conv(n, dl, fa, n->gzd[l], cw, n->G + dl.woff, Hl, Wl, n->gD[l], ldD, s);
     if (c.context[l - 1]) add_slice(n->gfeat[l - 1], c.context[l - 1], n->gD[l] + src.c, ldD, c.context[l - 1], M(l - 1), s);
     if (l == 1 && gx) UCHECK(cudaMemcpy2DAsync(gx, c.in_ch * 4, n->gD[1], ldD * 4, c.in_ch * 4, M(0),
                                                 cudaMemcpyDeviceToDevice, s));
@@ -618,6 +669,7 @@ void refresh_bf16(unet_ctx* n, cudaStream_t s) {
   for (auto& cl : n->convs) {
     weights_kmajor(n->P + cl.woff, n->WTb + cl.woff, cl.k * cl.k, cl.cin, cl.cout, s);
     conv_tma_weights(n->P + cl.woff, n->WPb + cl.wpoff, cl.k, cl.c0, cl.c1, cl.cout, s);
+    conv_tma_weights_adjoint(n->P + cl.woff, n->WPAb + cl.wpaoff, cl.k, cl.cin, cl.cout, cl.kind == 1, s);
   }
 }
 
@@ -745,6 +797,7 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   UCHECK(cudaMalloc(&n->Wb, np * 2));
   UCHECK(cudaMalloc(&n->WTb, np * 2));
   UCHECK(cudaMalloc(&n->WPb, n->nwp * 2));
+  UCHECK(cudaMalloc(&n->WPAb, n->nwpa * 2));
   UCHECK(cudaMalloc(&n->d_err, sizeof(int)));
   UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
   n->use_tc = !(cfg->flags & UNET_FLAG_SIMT);
@@ -797,7 +850,7 @@ void unet_destroy(unet_t n) {
   if (!n) return;
   cudaDeviceSynchronize();
   free_ws(n);
-  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb,
+  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb,
                   (void*)n->d_err, (void*)n->rstats,
                   (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
                   (void*)n->ev_shift, n->tmp_e})

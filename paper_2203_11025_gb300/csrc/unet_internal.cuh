@@ -49,6 +49,14 @@ void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int co
 // TMA-fed tensor-core path (conv_tma.cu); false if the convolution does not fit it.
 bool conv_forward_tma(const ConvArgs& a, int* err, cudaStream_t s);
 int conv_tma_split(const ConvArgs& a);
+// adjoint (data-gradient) weight copies for the TMA path: [cin][tap][64-chunks of cout],
+// taps reversed for stride-1 convolutions
+size_t conv_tma_weight_adj_elems(int k, int cin, int cout);
+// weight gradient on the tensor cores (TMA path): gW += dW of the forward convolution a
+// (one BF16 source, no on-load activation) from g = dL/dy, BF16 [pixels][Cout] with ld ldg
+bool conv_wgrad_tma(const ConvArgs& a, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s);
+void conv_wgrad_tma_set_desc_order(int order);
+void conv_tma_weights_adjoint(const float* P, __nv_bfloat16* WPA, int k, int cin, int cout, bool flip, cudaStream_t s);
 const char* conv_tma_last_reject();      // why the last conv_forward_tma call declined ("" if it launched)   // > 1: the TMA path splits K (FP32 atomics, no fused epilogue)
 size_t conv_tma_weight_elems(int k, int c0, int c1, int cout);
 void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, int cout, cudaStream_t s);
@@ -64,7 +72,7 @@ void bn_act(const float* z, int ldz, int C, int M, const float* scale, const flo
             __nv_bfloat16* y, int ldy, cudaStream_t s);
 void bn_backward(const float* g, int ldg, const float* z, int ldz, int C, int M, const double* mean, const double* var,
                  const float* scale, const float* shift, bool act, const float* gamma, float* ggamma, float* gbeta,
-                 float* part, int nblk, double* sums, float* gz, int ldo, cudaStream_t s);
+                 float* part, int nblk, float* coef, float* gz, int ldo, cudaStream_t s);
 // g *= eLU'(u); plane != 0: u is one image of `plane` pixels shared by the batch.
 void elu_backward_inplace(float* g, int ldg, const __nv_bfloat16* u, int ldu, int C, int M, size_t plane,
                           cudaStream_t s);

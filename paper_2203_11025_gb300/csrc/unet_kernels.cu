@@ -247,13 +247,25 @@ __global__ void __launch_bounds__(256) k_chan_partial(const float* __restrict__ 
   }
 }
 
+// Sum of the nblk partials part[b * stride + off] of one channel by one warp: FP32 per
+// lane, FP64 across lanes (the result is in every lane).
+__device__ __forceinline__ double warp_partials(const float* __restrict__ part, int nblk, size_t stride, size_t off) {
+  const int lane = threadIdx.x & 31;
+  float t = 0.f;
+  for (int b = lane; b < nblk; b += 32) t += part[(size_t)b * stride + off];
+  double d = t;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  return d;
+}
+
+// One warp per channel (blockDim 128: four channels per block).
 __global__ void k_chan_finalize(const float* __restrict__ part, int nblk, int C, double scale,
                                 double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (c >= C) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * C + c];
-  out[c] = s * scale;
+  const double s = warp_partials(part, nblk, C, c);
+  if ((threadIdx.x & 31) == 0) out[c] = s * scale;
 }
 
 // scale = gamma / sqrt(var + eps), shift = beta - mean * scale; running-stat update.
@@ -329,24 +341,31 @@ __global__ void __launch_bounds__(256) k_bn_bwd_partial(const float* __restrict_
   }
 }
 
-__global__ void k_bn_bwd_finalize(const float* __restrict__ part, int nblk, int C, double* __restrict__ sums,
+// Per-channel totals (gamma, beta gradients) and the FP32 coefficients of pass 2:
+// coef[c] = {gamma rstd, s1 / M, s2 / M, mean, rstd}.
+__global__ void k_bn_bwd_finalize(const float* __restrict__ part, int nblk, int C, int M,
+                                  const double* __restrict__ mean, const double* __restrict__ var,
+                                  const float* __restrict__ gamma, float* __restrict__ coef,
                                   float* __restrict__ ggamma, float* __restrict__ gbeta) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);   // one warp per channel
   if (c >= C) return;
-  double s1 = 0.0, s2 = 0.0;
-  for (int b = 0; b < nblk; ++b) { s1 += part[((size_t)b * C + c) * 2]; s2 += part[((size_t)b * C + c) * 2 + 1]; }
-  sums[2 * c] = s1;
-  sums[2 * c + 1] = s2;
+  const double s1 = warp_partials(part, nblk, 2 * (size_t)C, 2 * (size_t)c);
+  const double s2 = warp_partials(part, nblk, 2 * (size_t)C, 2 * (size_t)c + 1);
+  if ((threadIdx.x & 31) != 0) return;
   gbeta[c] += (float)s1;
   ggamma[c] += (float)s2;
+  const double rs = 1.0 / sqrt(var[c] + (double)kBnEps);
+  coef[5 * c] = (float)(gamma[c] * rs);
+  coef[5 * c + 1] = (float)(s1 / M);
+  coef[5 * c + 2] = (float)(s2 / M);
+  coef[5 * c + 3] = (float)mean[c];
+  coef[5 * c + 4] = (float)rs;
 }
 
-// BatchNorm backward, pass 2: gz = gamma rstd (gy - s1/M - xhat s2/M).
+// BatchNorm backward, pass 2: gz = gamma rstd (gy - s1/M - xhat s2/M), FP32 throughout.
 __global__ void k_bn_bwd_apply(const float* __restrict__ g, int ldg, const float* __restrict__ z, int ldz, int C,
-                               int M, const double* __restrict__ mean, const double* __restrict__ var,
-                               const float* __restrict__ scale, const float* __restrict__ shift, int act,
-                               const float* __restrict__ gamma, const double* __restrict__ sums,
-                               float* __restrict__ gz, int ldo) {
+                               int M, const float* __restrict__ coef, const float* __restrict__ scale,
+                               const float* __restrict__ shift, int act, float* __restrict__ gz, int ldo) {
   const size_t n = (size_t)M * C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const size_t m = i / C;
@@ -354,9 +373,9 @@ __global__ void k_bn_bwd_apply(const float* __restrict__ g, int ldg, const float
     const float zz = z[m * ldz + c];
     float gy = g[m * ldg + c];
     if (act) gy *= elu_grad(zz * scale[c] + shift[c]);
-    const float rs = (float)(1.0 / sqrt(var[c] + (double)kBnEps));
-    const float xhat = (zz - (float)mean[c]) * rs;
-    gz[m * ldo + c] = gamma[c] * rs * (gy - (float)(sums[2 * c] / M) - xhat * (float)(sums[2 * c + 1] / M));
+    const float* k = coef + 5 * c;
+    const float xhat = (zz - k[3]) * k[4];
+    gz[m * ldo + c] = k[0] * (gy - k[1] - xhat * k[2]);
   }
 }
 
@@ -522,11 +541,10 @@ __global__ void k_gamma_field(int ny, int nx, int width, float gmax, float* __re
 }
 
 __global__ void k_chan_finalize_add(const float* __restrict__ part, int nblk, int C, float* __restrict__ dst) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);   // one warp per channel
   if (c >= C) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * C + c];
-  dst[c] += (float)s;
+  const double s = warp_partials(part, nblk, C, c);
+  if ((threadIdx.x & 31) == 0) dst[c] += (float)s;
 }
 
 // dst[p][c] (+)= sum_b src[b][p][c]: gradient of a tensor shared by the whole batch.
@@ -692,9 +710,9 @@ void conv_wgrad(const ConvArgs& a, const float* G, int ldg, float* gW, cudaStrea
 void bn_batch_stats(const float* z, int ldz, int C, int M, double* mean, double* var, float* part, int nblk,
                     cudaStream_t s) {
   k_chan_partial<<<dim3((C + 31) / 32, nblk), 256, 0, s>>>(z, ldz, C, M, nullptr, 0, part);
-  k_chan_finalize<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, 1.0 / M, mean);
+  k_chan_finalize<<<(C + 3) / 4, 128, 0, s>>>(part, nblk, C, 1.0 / M, mean);
   k_chan_partial<<<dim3((C + 31) / 32, nblk), 256, 0, s>>>(z, ldz, C, M, mean, 1, part);
-  k_chan_finalize<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, 1.0 / M, var);
+  k_chan_finalize<<<(C + 3) / 4, 128, 0, s>>>(part, nblk, C, 1.0 / M, var);
 }
 
 void bn_coeffs(const double* mean, const double* var, const float* gamma, const float* beta, int C, float* scale,
@@ -715,12 +733,12 @@ void bn_act(const float* z, int ldz, int C, int M, const float* scale, const flo
 
 void bn_backward(const float* g, int ldg, const float* z, int ldz, int C, int M, const double* mean, const double* var,
                  const float* scale, const float* shift, bool act, const float* gamma, float* ggamma, float* gbeta,
-                 float* part, int nblk, double* sums, float* gz, int ldo, cudaStream_t s) {
+                 float* part, int nblk, float* coef, float* gz, int ldo, cudaStream_t s) {
   k_bn_bwd_partial<<<dim3((C + 31) / 32, nblk), 256, 0, s>>>(g, ldg, z, ldz, C, M, mean, var, scale, shift,
                                                             act ? 1 : 0, part);
-  k_bn_bwd_finalize<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, sums, ggamma, gbeta);
-  k_bn_bwd_apply<<<grid_for((size_t)M * C), 256, 0, s>>>(g, ldg, z, ldz, C, M, mean, var, scale, shift, act ? 1 : 0,
-                                                         gamma, sums, gz, ldo);
+  k_bn_bwd_finalize<<<(C + 3) / 4, 128, 0, s>>>(part, nblk, C, M, mean, var, gamma, coef, ggamma, gbeta);
+  k_bn_bwd_apply<<<grid_for((size_t)M * C), 256, 0, s>>>(g, ldg, z, ldz, C, M, coef, scale, shift, act ? 1 : 0, gz,
+                                                         ldo);
 }
 
 void elu_backward_inplace(float* g, int ldg, const __nv_bfloat16* u, int ldu, int C, int M, size_t plane,
@@ -775,7 +793,7 @@ void write_output(const float* out, bool fp64, int B, int ny, int nx, const floa
 
 void chan_sum_add(const float* g, int ld, int C, int M, float* dst, float* part, int nblk, cudaStream_t s) {
   k_chan_partial<<<dim3((C + 31) / 32, nblk), 256, 0, s>>>(g, ld, C, M, nullptr, 0, part);
-  k_chan_finalize_add<<<(C + 127) / 128, 128, 0, s>>>(part, nblk, C, dst);
+  k_chan_finalize_add<<<(C + 3) / 4, 128, 0, s>>>(part, nblk, C, dst);
 }
 
 void batch_sum(const float* src, int lds, int B, size_t P, int C, float* dst, int ldd, bool accumulate,
