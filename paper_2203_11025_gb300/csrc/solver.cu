@@ -78,16 +78,21 @@ struct Work {
   int* maxit_rhs = nullptr;          // per right-hand-side iteration caps (pair generator)
 };
 
+// A captured cycle bakes in every device pointer it touches: the solver's work arena
+// (graphs are dropped when it is reallocated), b and x, and the network's weights and
+// workspace -- identified by the network's unique id and workspace generation rather
+// than its address, which a later network may reuse.
 struct GraphKey {
   int dtype, precond, nrhs, m, maxit;
   const void* b;
   const void* x;
-  const void* net;
+  unsigned long long net[4];
   bool operator<(const GraphKey& o) const {
-    return std::tie(dtype, precond, nrhs, m, maxit, b, x, net) <
-           std::tie(o.dtype, o.precond, o.nrhs, o.m, o.maxit, o.b, o.x, o.net);
+    return std::tie(dtype, precond, nrhs, m, maxit, b, x, net[0], net[1], net[2], net[3]) <
+           std::tie(o.dtype, o.precond, o.nrhs, o.m, o.maxit, o.b, o.x, o.net[0], o.net[1], o.net[2], o.net[3]);
   }
 };
+constexpr size_t kMaxGraphs = 64;   // cached cycles (older ones belong to released buffers)
 
 }  // namespace
 
@@ -386,8 +391,10 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   long long per_cycle = -1;
   const bool use_graph = !(o.flags & HELM_FLAG_NO_GRAPH);
   if (use_graph) {
-    GraphKey key{(int)sizeof(T), precond, nrhs, m, o.maxit, b, x, net};
+    GraphKey key{(int)sizeof(T), precond, nrhs, m, o.maxit, b, x, {0, 0, 0, 0}};
+    if (net) unet_graph_ids(net, key.net);
     if (maxit_rhs_host) key.maxit = -1 - o.maxit;
+    if (c->graphs.size() >= kMaxGraphs && !c->graphs.count(key)) drop_graphs(c);
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
       exec = it->second;

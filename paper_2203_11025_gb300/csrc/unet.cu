@@ -4,6 +4,8 @@
 // preconditioners M_JU (Alg. 2) and M_VU (Eq. 3.4).
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -64,6 +66,9 @@ struct DevArena {
 struct unet_ctx {
   unet_cfg cfg{};
   int L = 0;
+  // identity of the buffers a captured solve cycle references: a process-unique id and
+  // the generation of the workspace (bumped on every reallocation)
+  unsigned long long uid = 0, ws_gen = 0;
   std::vector<ConvL> convs;
   std::vector<BnL> bns;
   size_t bias_off = 0, nparams = 0, nbn = 0;
@@ -279,6 +284,7 @@ int ensure_ws(unet_ctx* n, int B, int ny, int nx) {
     return HELM_ENOMEM;
   }
   n->ws_bytes = bytes;
+  ++n->ws_gen;
   DevArena a{(char*)n->ws, bytes, 0};
   carve(n, a, B, ny, nx);
   n->B = B; n->ny = ny; n->nx = nx;
@@ -742,6 +748,14 @@ int unet_precond_impl(helm_ctx* hc, void* netp, int kind, const void* v, void* z
 
 void unet_release_ctx(helm_ctx*) {}
 
+void unet_graph_ids(void* netp, unsigned long long ids[4]) {
+  const unet_ctx* n = (const unet_ctx*)netp;
+  ids[0] = n ? n->uid : 0;
+  ids[1] = n ? n->ws_gen : 0;
+  ids[2] = (n && n->encoder) ? n->encoder->uid : 0;
+  ids[3] = (n && n->encoder) ? n->encoder->ws_gen : 0;
+}
+
 int unet_prepare_impl(helm_ctx* hc, void* netp, int nrhs) {
   unet_ctx* n = (unet_ctx*)netp;
   if (!n) { set_error("null net"); return HELM_EINVAL; }
@@ -786,7 +800,9 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   }
   for (int l = 0; l < cfg->levels; ++l)
     if (cfg->widths[l] < 1 || cfg->widths[l] > 512) { set_error("bad width"); return HELM_EINVAL; }
+  static std::atomic<unsigned long long> next_uid{1};
   unet_ctx* n = new unet_ctx();
+  n->uid = next_uid++;
   n->cfg = *cfg;
   build_layout(n);
   const size_t np = n->nparams, nb = n->nbn;

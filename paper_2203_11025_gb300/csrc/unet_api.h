@@ -12,3 +12,7 @@ int unet_precond_impl(helm_ctx* c, void* net, int kind, const void* v, void* z, 
 void unet_release_ctx(helm_ctx* c);
 // Allocate the network's workspace for nrhs right-hand sides on c's grid (before graph capture).
 int unet_prepare_impl(helm_ctx* c, void* net, int nrhs);
+// Identity of the device buffers a captured cycle with this network references: {network
+// id, workspace generation, encoder id, encoder workspace generation}; ids are never
+// reused, generations change whenever a workspace is reallocated.
+void unet_graph_ids(void* net, unsigned long long ids[4]);

@@ -318,3 +318,29 @@ def test_fgmres_vu_with_silent_network_equals_sl(lib):
     bb = b.cpu().numpy()
     for j in range(2):
         assert np.linalg.norm(H.residual(prob.A, bb[j], x[j])) / np.linalg.norm(bb[j]) <= 1e-7
+
+
+def test_solve_cycles_follow_network_buffers(lib):
+    """A captured FGMRES cycle references the network's weights and workspace.  A forward
+    at another batch size (workspace reallocated) between two solves, and a new network
+    created after the previous one was released, must each be solved with their own
+    buffers: the three solves agree."""
+    import gc
+    n = 64
+    hz, _ = _helm(lib, n)
+    c, oc = make_cfgs(lib)
+    pos = synth.source_positions(n, n, 2, 5, 16)
+    b = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n)).cuda()
+    net = lib.UNet(c, seed=21)
+    x1, i1 = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=3000)
+    x1 = x1.cpu().numpy()
+    net.forward(cuda(np.random.default_rng(3).standard_normal((3, n, n, 4))))   # batch 3: new workspace
+    x2, i2 = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=3000)
+    assert i2["iters"] == i1["iters"]
+    assert np.allclose(x2.cpu().numpy(), x1, rtol=0, atol=1e-12 * np.abs(x1).max())
+    del net
+    gc.collect()
+    net2 = lib.UNet(c, seed=21)
+    x3, i3 = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net2, tol=1e-7, maxit=3000)
+    assert i3["iters"] == i1["iters"]
+    assert np.allclose(x3.cpu().numpy(), x1, rtol=0, atol=1e-12 * np.abs(x1).max())
