@@ -114,6 +114,7 @@ struct TmaArgs {
   const __nv_bfloat16* res; int ldr;
   const float* scale; const float* shift; int act;
   __nv_bfloat16* ybf; int ldy;
+  __nv_bfloat16* y2; int ldy2;    // optional: eLU of the BF16 result as well (next layer's activated input)
   // split-K: split s stores its partial sums to part + s * slice ([pixels][Cout], FP32);
   // k_splitk_finish adds the slices and applies the epilogue
   float* part; size_t slice;
@@ -199,6 +200,17 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
       uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + cb);
       yp[0] = o4[0];
       yp[1] = o4[1];
+      if (a.y2) {
+        // eLU of the value as stored (rounded to BF16), as the consumer would compute it
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2 t = __bfloat1622float2(o2[j]);
+          o2[j] = __floats2bfloat162_rn(t.x > 0.f ? t.x : expm1f(t.x), t.y > 0.f ? t.y : expm1f(t.y));
+        }
+        uint4* zp = reinterpret_cast<uint4*>(a.y2 + pix * a.ldy2 + cb);
+        zp[0] = o4[0];
+        zp[1] = o4[1];
+      }
     } else {
       float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
 #pragma unroll
@@ -216,7 +228,12 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
     if (a.ybf) {
       if (a.scale) g = g * ks[co] + kh[co];
       if (a.act) g = g > 0.f ? g : expm1f(g);
-      a.ybf[pix * a.ldy + co] = __float2bfloat16_rn(g);
+      const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+      a.ybf[pix * a.ldy + co] = gb;
+      if (a.y2) {
+        const float t = __bfloat162float(gb);
+        a.y2[pix * a.ldy2 + co] = __float2bfloat16_rn(t > 0.f ? t : expm1f(t));
+      }
     } else {
       a.out[pix * a.ldo + co] = g;
     }
@@ -436,7 +453,14 @@ __global__ void __launch_bounds__(256) k_splitk_finish(TmaArgs a, int M) {
     }
     if (a.ybf) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) a.ybf[p * a.ldy + c + j] = __float2bfloat16_rn(f[j]);
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 yb = __float2bfloat16_rn(f[j]);
+        a.ybf[p * a.ldy + c + j] = yb;
+        if (a.y2) {
+          const float t = __bfloat162float(yb);
+          a.y2[p * a.ldy2 + c + j] = __float2bfloat16_rn(t > 0.f ? t : expm1f(t));
+        }
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j) a.out[p * a.ldo + c + j] = f[j];
@@ -658,10 +682,12 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   }
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
   a.scale = c.scale; a.shift = c.shift; a.act = c.ep_act; a.ybf = c.ybf; a.ldy = c.ldy;
+  a.y2 = c.ybf ? c.y2 : nullptr; a.ldy2 = c.ldy2;
   a.err = err;
   a.part = a.ksplit > 1 ? c.splitbuf : nullptr;
   a.slice = (size_t)c.B * c.Ho * c.Wo * c.Cout;
   a.vec = ((c.ldo % 4 == 0) && !((uintptr_t)c.out & 15) && (c.ldy % 8 == 0) && !((uintptr_t)c.ybf & 15) &&
+           (!a.y2 || ((c.ldy2 % 8 == 0) && !((uintptr_t)a.y2 & 15))) &&
            (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15))) &&
            (!a.part || (c.Cout % 4 == 0 && !((uintptr_t)a.part & 15)))) ? 1 : 0;
   const int nph = c.transposed ? 4 : 1;

@@ -435,8 +435,10 @@ void ensure_eval_coeffs(unet_ctx* n, cudaStream_t s) {
 // Convolution followed by BatchNorm (+ eLU) into a BF16 slice.  At inference on the
 // tensor-core path the normalisation is applied in the convolution's epilogue.
 void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bfloat16* y, int ldy, int M, bool train,
-             cudaStream_t s) {
-  // inference: BatchNorm and eLU fused into the convolution's epilogue
+             cudaStream_t s, __nv_bfloat16* y2 = nullptr, int ldy2 = 0) {
+  // inference: BatchNorm and eLU fused into the convolution's epilogue; y2 (optional):
+  // eLU of y, the activated input of the next up convolution (written by the TMA
+  // epilogue, else copied)
   if (!train && n->use_tc) {
     ConvArgs f = a;
     const BnL& b = bn_of(n, bn);
@@ -446,16 +448,24 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     f.ep_act = act ? 1 : 0;
     f.ybf = y;
     f.ldy = ldy;
-    if (conv_forward_small(f, s)) { n->last_path = 3; return; }
-    if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; return; }
-    if (conv_tc_eligible(f)) {
+    f.y2 = y2;
+    f.ldy2 = ldy2;
+    bool done = false, wrote2 = false;
+    if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }
+    else if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; done = wrote2 = true; }
+    else if (conv_tc_eligible(f)) {
       conv_forward_tc(f, n->d_err, s);
       n->last_path = 1;
+      done = true;
+    }
+    if (done) {
+      if (y2 && !wrote2) elu_copy_bf16(y, ldy, a.Cout, (size_t)M, y2, ldy2, s);
       return;
     }
   }
   run_conv(n, a, s);
   run_bn(n, bn, a.out, a.ldo, M, act, y, ldy, train, s);
+  if (y2) elu_copy_bf16(y, ldy, a.Cout, (size_t)M, y2, ldy2, s);
 }
 
 // Materialise eLU of an up convolution's inputs for the tensor-core gather.
@@ -481,6 +491,9 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
   const unet_cfg& c = n->cfg;
   const int L = n->L;
   n->uact_ok.assign(L + 1, 0);
+  // inference: epilogues write the eLU'd inputs of the up convolutions (levels without
+  // encoder context; with context those levels keep the explicit copy)
+  const bool direct = !train && n->use_tc;
   const int* w = c.widths;
   auto hw = [&](int l, int& H, int& W) { H = n->ny >> l; W = n->nx >> l; };
   auto M = [&](int l) { return n->B * (n->ny >> l) * (n->nx >> l); };
@@ -509,29 +522,41 @@ int forward_impl(unet_ctx* n, bool train, cudaStream_t s) {
       if (r == nres - 1 && l < L) { dst = n->cat[l] + w[l - 1]; ldd = 2 * w[l - 1]; }
       else if (r == nres - 1) { dst = n->hL; ldd = w[L - 1]; }
       else { dst = n->hres[l][r]; ldd = w[l - 1]; }
-      conv_bn(n, k2, pre + ".bn2", true, dst, ldd, M(l), train, s);
+      // inference without context at this level: also the eLU'd copy the up convolution reads
+      __nv_bfloat16* d2 = nullptr;
+      if (direct && r == nres - 1) d2 = l < L ? n->uact[l] + w[l - 1] : n->uact[L];
+      conv_bn(n, k2, pre + ".bn2", true, dst, ldd, M(l), train, s, d2, ldd);
       h = dst;
       ldh = ldd;
     }
   }
+  // up convolutions read eLU(u): the eLU'd copy written by the producing epilogues
+  // (inference without context), else materialised here
+  auto up_args = [&](const ConvL& ul, int l, const Src& u, const Src& f, int H, int W, float* out, int ldo) {
+    if (direct && !f.p) {
+      n->uact_ok[l] = 1;
+      return conv_args(n, ul, Src{n->uact[l], u.c, u.c, false}, f, false, H, W, out, ldo);
+    }
+    ConvArgs a = conv_args(n, ul, u, f, true, H, W, out, ldo);
+    return act_inputs(n, a, l, u, f, H, W, M(l), s);   // the tensor-core gather copies raw bytes
+  };
   Src u{n->hL, w[L - 1], w[L - 1], false};
   for (int l = L; l >= 2; --l) {
     int H, W;
     hw(l, H, W);
     const ConvL& ul = conv_of(n, "up" + std::to_string(l));
     Src f = feat_of(n, l);
-    ConvArgs a = conv_args(n, ul, u, f, true, H, W, n->zup[l], w[l - 2]);
-    a = act_inputs(n, a, l, u, f, H, W, M(l), s);   // the tensor-core gather copies raw bytes
-    conv_bn(n, a, "up" + std::to_string(l) + ".bn", false, n->cat[l - 1], 2 * w[l - 2], M(l - 1), train, s);
+    ConvArgs a = up_args(ul, l, u, f, H, W, n->zup[l], w[l - 2]);
+    conv_bn(n, a, "up" + std::to_string(l) + ".bn", false, n->cat[l - 1], 2 * w[l - 2], M(l - 1), train, s,
+            direct ? n->uact[l - 1] : nullptr, 2 * w[l - 2]);
     u = Src{n->cat[l - 1], 2 * w[l - 2], 2 * w[l - 2], false};
   }
   {
     int H, W;
     hw(1, H, W);
     Src f = feat_of(n, 1);
-    ConvArgs a = conv_args(n, conv_of(n, "up1"), u, f, true, H, W, n->out, c.out_ch);
+    ConvArgs a = up_args(conv_of(n, "up1"), 1, u, f, H, W, n->out, c.out_ch);
     a.bias = n->P + n->bias_off;
-    a = act_inputs(n, a, 1, u, f, H, W, M(1), s);
     run_conv(n, a, s);
     if (n->is_encoder) to_bf16_slice(n->out, c.out_ch, n->out_bf, out_ld(n), c.out_ch, M(0), s);
   }

@@ -31,6 +31,7 @@ struct ConvArgs {
   // fused inference BatchNorm epilogue (tensor-core path only): y = act((conv + res) * scale + shift)
   const float* scale; const float* shift; int ep_act;
   __nv_bfloat16* ybf; int ldy;       // BF16 destination; when set, `out` is not written
+  __nv_bfloat16* y2; int ldy2;       // optional second BF16 destination: eLU of what ybf receives (TMA path)
   // split-K scratch of the TMA path: splitcnt_n floats for the FP32 partial-sum slices
   // (null: not split)
   float* splitbuf; int* splitcnt; long long splitcnt_n;
