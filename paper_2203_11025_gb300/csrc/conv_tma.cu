@@ -43,14 +43,13 @@ constexpr int MAXST = 8;           // stage ring capacity (the host picks nst <=
 constexpr int NEPI = 8;                  // epilogue warps: 2 column groups x 4 TMEM lane quadrants
 constexpr int WPROD = NEPI, WMMA = NEPI + 1;
 constexpr int NTHR = 32 * (NEPI + 2);    // + the TMA producer warp and the MMA warp
-constexpr long long kWait = 1ll << 26;   // polls before a wait gives up (about a second)
+constexpr long long kWait = 1ll << 24;       // try_wait rounds before a wait gives up (seconds at most)
+constexpr long long kWaitSleep = 1ll << 23;  // sleeping polls before an epilogue wait gives up (~1 s)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mb_init(uint32_t a, int c) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(c) : "memory");
 }
-// Non-suspending poll: a thread parked by try_wait was measured to resume about a
-// microsecond after the phase completed, which dominated the stage hand-offs.
 __device__ __forceinline__ bool mb_test(uint32_t a, uint32_t par) {
   uint32_t ok;
   asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -59,9 +58,28 @@ __device__ __forceinline__ bool mb_test(uint32_t a, uint32_t par) {
                : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mb_try(uint32_t a, uint32_t par) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok)
+               : "r"(a), "r"(par)
+               : "memory");
+  return ok != 0;
+}
+// Critical-path waits (TMA producer, MMA issuer): try_wait suspends the thread in
+// hardware until the phase completes, so a waiting warp takes no issue slots.
 __device__ __forceinline__ bool mb_wait(uint32_t a, uint32_t par) {
   for (long long i = 0; i < kWait; ++i)
+    if (mb_try(a, par)) return true;
+  return false;
+}
+// Epilogue waits (an item's whole MMA time): poll with a sleep in between, so that
+// the epilogue warps leave the issue slots to the producer and MMA threads.
+__device__ __forceinline__ bool mb_wait_sleep(uint32_t a, uint32_t par) {
+  for (long long i = 0; i < kWaitSleep; ++i) {
     if (mb_test(a, par)) return true;
+    __nanosleep(128);
+  }
   return false;
 }
 __device__ __forceinline__ void mb_expect_tx(uint32_t a, uint32_t bytes) {
@@ -102,6 +120,8 @@ struct TmaArgs {
   int BX, BY, BB;                 // output tile (pixels of the output or phase grid)
   int tx, ty, tb;                 // tiles along x, y and images
   int nch0, nch1;                 // 64-channel chunks per source
+  int c0, c1;                     // real channels per source (MMAs skip the zero-filled K)
+  int shuf, cr;                   // sub-pixel output: column n = phase * cr + channel, pixel (2y + py, 2x + px)
   int bcast1;                     // source 1 is one image shared by the batch
   int ksplit;                     // K-block ranges per tile; > 1: FP32 atomic accumulation
   int nitems;                     // tiles x phases x ksplit
@@ -120,6 +140,10 @@ struct TmaArgs {
   float* part; size_t slice;
   int* err;
 };
+
+// eLU for BF16 results: exp(x) - 1 with the fast exponential (absolute error ~1e-7,
+// far below the BF16 rounding of the stored value; expm1f made the epilogue issue-bound).
+__device__ __forceinline__ float elu_bf(float x) { return x > 0.f ? x : __expf(x) - 1.f; }
 
 // One work item: an output tile of one phase, reduced over one K range.
 struct Item {
@@ -166,8 +190,9 @@ __device__ __forceinline__ bool epi_any(bool p) {
 
 // Bias, residual, BatchNorm and eLU on 16 consecutive channels [cb, cb + 16) of one
 // pixel, then the store (BF16 y, or FP32 out).  k: per-channel constants in shared memory.
-__device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix, int cb, bool add_lin,
+__device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix, int cb, int sc, bool add_lin,
                                          const uint4* r4, const float* kb, const float* ks, const float* kh) {
+  // cb: first column (per-column constants), sc: first channel of the stored pixel
   if (cb + 16 <= a.Cout && a.vec) {
     if (add_lin) {
       if (a.bias) {
@@ -191,13 +216,13 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         if (a.scale) f[j] = f[j] * ks[cb + j] + kh[cb + j];
-        if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
+        if (a.act) f[j] = elu_bf(f[j]);
       }
       uint4 o4[2];
       __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(o4);
 #pragma unroll
       for (int j = 0; j < 8; ++j) o2[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-      uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + cb);
+      uint4* yp = reinterpret_cast<uint4*>(a.ybf + pix * a.ldy + sc);
       yp[0] = o4[0];
       yp[1] = o4[1];
       if (a.y2) {
@@ -205,14 +230,14 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float2 t = __bfloat1622float2(o2[j]);
-          o2[j] = __floats2bfloat162_rn(t.x > 0.f ? t.x : expm1f(t.x), t.y > 0.f ? t.y : expm1f(t.y));
+          o2[j] = __floats2bfloat162_rn(elu_bf(t.x), elu_bf(t.y));
         }
-        uint4* zp = reinterpret_cast<uint4*>(a.y2 + pix * a.ldy2 + cb);
+        uint4* zp = reinterpret_cast<uint4*>(a.y2 + pix * a.ldy2 + sc);
         zp[0] = o4[0];
         zp[1] = o4[1];
       }
     } else {
-      float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + cb);
+      float4* op = reinterpret_cast<float4*>(a.out + pix * a.ldo + sc);
 #pragma unroll
       for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
     }
@@ -220,23 +245,125 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
   }
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const int co = cb + j;
+    const int co = cb + j, so = sc + j;
     if (co >= a.Cout) break;
     float g = f[j];
     if (add_lin && a.bias) g += kb[co];
-    if (add_lin && a.res) g += __bfloat162float(a.res[pix * a.ldr + co]);
+    if (add_lin && a.res) g += __bfloat162float(a.res[pix * a.ldr + so]);
     if (a.ybf) {
       if (a.scale) g = g * ks[co] + kh[co];
-      if (a.act) g = g > 0.f ? g : expm1f(g);
+      if (a.act) g = elu_bf(g);
       const __nv_bfloat16 gb = __float2bfloat16_rn(g);
-      a.ybf[pix * a.ldy + co] = gb;
+      a.ybf[pix * a.ldy + so] = gb;
       if (a.y2) {
         const float t = __bfloat162float(gb);
-        a.y2[pix * a.ldy2 + co] = __float2bfloat16_rn(t > 0.f ? t : expm1f(t));
+        a.y2[pix * a.ldy2 + so] = __float2bfloat16_rn(elu_bf(t));
       }
     } else {
-      a.out[pix * a.ldo + co] = g;
+      a.out[pix * a.ldo + so] = g;
     }
+  }
+}
+
+// One value of column n stored as channel sc of pixel pix (bias, BatchNorm, eLU as finish16).
+__device__ __forceinline__ void finish1(const TmaArgs& a, float g, size_t pix, int n, int sc, const float* kb,
+                                        const float* ks, const float* kh) {
+  if (a.bias) g += kb[n];
+  if (a.ybf) {
+    if (a.scale) g = g * ks[n] + kh[n];
+    if (a.act) g = elu_bf(g);
+    const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+    a.ybf[pix * a.ldy + sc] = gb;
+    if (a.y2) a.y2[pix * a.ldy2 + sc] = __float2bfloat16_rn(elu_bf(__bfloat162float(gb)));
+  } else {
+    a.out[pix * a.ldo + sc] = g;
+  }
+}
+
+// Epilogue warps (0 .. NEPI-1) of both convolution kernels: drain TMEM accumulator
+// buffer i & 1 of item i into the destination, then hand the buffer back.
+__device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
+                                              int* s_fail, const float* s_bias, const float* s_scale,
+                                              const float* s_shift) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.NT;
+  volatile int* fail = s_fail;
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the
+  // 16-column chunks grp, grp + 2, ... of the accumulator (grp = w / 4)
+  const int q4 = warp & 3, grp = warp >> 2;
+  const int m = q4 * 32 + lane;
+  const int bb = m / (a.BY * a.BX), rr = m - bb * a.BY * a.BX, by = rr / a.BX, bx = rr - by * a.BX;
+  int li = 0;
+  for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
+    if (epi_any(failed(fail))) break;
+    const Item it = decode(a, w);
+    const int acc = li & 1;
+    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u);
+    if (epi_any(!ok)) { atomicExch(s_fail, 1); break; }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
+    const int oy = a.transposed ? 2 * qy + it.py : qy, ox = a.transposed ? 2 * qx + it.px : qx;
+    const bool rv = it.nkb > 0 && b < a.B && oy < a.Ho && ox < a.Wo;
+    const size_t pix = ((size_t)b * a.Ho + oy) * a.Wo + ox;
+    // residual of the next chunk is requested before the current chunk's TMEM read
+    const bool pre = rv && a.ksplit <= 1 && a.res && a.vec;
+    uint4 rn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+    if (pre && 16 * grp + 16 <= a.Cout) {
+      const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + 16 * grp);
+      rn[0] = rp[0]; rn[1] = rp[1];
+    }
+    for (int c0 = 16 * grp; c0 < N; c0 += 32) {
+      const uint4 rc[2] = {rn[0], rn[1]};
+      if (pre && c0 + 48 <= a.Cout) {
+        const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + 32);
+        rn[0] = rp[0]; rn[1] = rp[1];
+      }
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (!rv) continue;
+      float f[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
+      if (a.ksplit > 1) {
+        // partial sums of this K range into the split's slice (plain stores)
+        float* dst = a.part + (size_t)it.split * a.slice + pix * a.Cout + c0;
+        if (c0 + 16 <= a.Cout && a.vec) {
+          float4* op = reinterpret_cast<float4*>(dst);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < a.Cout) dst[j] = f[j];
+        }
+      } else if (!a.shuf) {
+        finish16(a, f, pix, c0, c0, true, rc, s_bias, s_scale, s_shift);
+      } else if (a.cr % 16 == 0) {
+        // sub-pixel: the chunk is one phase's channels [co0, co0 + 16)
+        const int ph = c0 / a.cr, co0 = c0 - ph * a.cr;
+        const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
+        finish16(a, f, opix, c0, co0, true, rc, s_bias, s_scale, s_shift);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          if (n >= a.Cout) break;
+          const int ph = n / a.cr, co = n - ph * a.cr;
+          const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
+          finish1(a, f[j], opix, n, co, s_bias, s_scale, s_shift);
+        }
+      }
+    }
+    // accumulator read: hand buffer acc back to the MMA warp
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&tempty[acc])) : "memory");
   }
 }
 
@@ -246,8 +373,8 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
 // of item i + 1 run.
 // (two CTAs per SM for N <= 64 need <= 102 registers per thread at 320 threads)
 __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CUtensorMap mA0,
-                                                      const __grid_constant__ CUtensorMap mA1,
-                                                      const __grid_constant__ CUtensorMap mB, TmaArgs a) {
+                                                    const __grid_constant__ CUtensorMap mA1,
+                                                    const __grid_constant__ CUtensorMap mB, TmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain;
   __shared__ uint32_t tmem_slot;
@@ -266,15 +393,16 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
-    s_bias[c] = a.bias ? a.bias[c] : 0.f;
-    s_scale[c] = a.scale ? a.scale[c] : 1.f;
-    s_shift[c] = a.shift ? a.shift[c] : 0.f;
+    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
+    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
+    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
+    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
   }
   const uint32_t ncols = 2u * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
-                 "r"(ncols)
-                 : "memory");
+        "r"(ncols)
+        : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -289,13 +417,13 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
       for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x) {
         const Item it = decode(a, w);
         bool ok = true;
+        // K-block kbeg + kb = (tap ty * ntx + tx, chunk ch), stepped without divisions
+        int ch = it.kbeg % it.nchk, tap = it.kbeg / it.nchk;
+        int ty = tap / it.ntx, tx = tap - ty * it.ntx;
         for (int kb = 0; kb < it.nkb; ++kb, ++g) {
           const int s = (int)(g % (uint32_t)NS);
           const uint32_t use = g / (uint32_t)NS;
           if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
-          const int kg = it.kbeg + kb;
-          const int tap = kg / it.nchk, ch = kg - tap * it.nchk;
-          const int ty = tap / it.ntx, tx = tap - ty * it.ntx;
           const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
           int ix, iy;
           if (!a.transposed) { ix = it.x0 * a.stride + kx - a.pad; iy = it.y0 * a.stride + ky - a.pad; }
@@ -305,6 +433,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
           if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, it.b0, su32(&full[s]));
           else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : it.b0, su32(&full[s]));
           tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, 0, su32(&full[s]));
+          if (++ch == it.nchk) {
+            ch = 0;
+            if (++tx == it.ntx) { tx = 0; ++ty; }
+          }
         }
         if (!ok) { atomicExch(&s_fail, 1); break; }
       }
@@ -325,14 +457,19 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
         bool ok = true;
-        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+        int kch = it.kbeg % it.nchk;   // chunk of K-block kbeg + kb, stepped below
+        for (int kb = 0; kb < it.nkb; ++kb, ++g, kch = (kch + 1 == it.nchk) ? 0 : kch + 1) {
           const int s = (int)(g % (uint32_t)NS);
           if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sA = base + (uint32_t)s * stage;
           const uint64_t da = desc128(sA), db = desc128(sA + a_bytes);
+          // K-steps of 16 that hold real channels (the rest of a 64-channel chunk is zero fill)
+          const int cval = kch < a.nch0 ? min(TK, a.c0 - kch * TK) : min(TK, a.c1 - (kch - a.nch0) * TK);
+          const int nk4 = (cval + 15) / 16;
 #pragma unroll
           for (int k4 = 0; k4 < TK / 16; ++k4) {
+            if (k4 >= nk4) break;
             const uint32_t accum = (kb > 0 || k4 > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -341,83 +478,185 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
                 : "memory");
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                           su32(&empty[s]))
-                       : "memory");
+              su32(&empty[s]))
+              : "memory");
         }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            su32(&tfull[acc]))
+            : "memory");
+      }
+      // every MMA issued above completes before tensor memory is released (bounded)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
+          : "memory");
+      mb_wait(su32(&drain), 0);
+    }
+  } else {
+    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_bias, s_scale, s_shift);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && s_fail && a.err) atomicExch(a.err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// Column-reuse variant, for layers whose whole padded weight copy fits in shared
+// memory next to the stage ring (one 128-pixel tile of BX x BY pixels, BX in {8, 16}):
+// the weights are loaded once per CTA, and per (x-tap, channel chunk) one TMA box of
+// (BY + nyt - 1) rows of BX pixels serves every y-tap of that column -- y-tap j is the
+// box from row j * BX on, i.e. BX * 128 bytes further, a whole number of 1024-byte
+// swizzle atoms.  Stride-2 convolutions split their y-taps into even and odd classes
+// (element stride 2 along y); transposed stride-2 convolutions use their phase's taps.
+// A K-block stage therefore holds one input box only.
+struct ReuseArgs {
+  int nyt;        // y-taps one box serves at most (box height BY + nyt - 1)
+  int bres;       // bytes of the resident weights (all taps x chunks, NT rows each)
+};
+
+__global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constant__ CUtensorMap mA,
+                                                            const __grid_constant__ CUtensorMap mB, TmaArgs a,
+                                                            ReuseArgs r) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain, wres;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  __shared__ float s_bias[256], s_scale[256], s_shift[256];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.NT, NS = a.nst;
+  const uint32_t wbase = (su32(smem) + 1023u) & ~1023u;          // resident weights
+  const uint32_t base = wbase + (((uint32_t)r.bres + 1023u) & ~1023u);
+  const uint32_t stage = (uint32_t)((a.BY + r.nyt - 1) * a.BX * 128);
+  const uint32_t wtile = (uint32_t)N * 128;                       // one (tap, chunk) weight tile
+  const int nch = a.nch0;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) { mb_init(su32(&full[q]), 1); mb_init(su32(&empty[q]), 1); }
+    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), NEPI); }
+    mb_init(su32(&drain), 1);
+    mb_init(su32(&wres), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
+    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
+    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
+    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
+    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
+  }
+  const uint32_t ncols = 2u * (uint32_t)a.colsz;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* fail = &s_fail;
+  const bool tr = a.transposed != 0;
+  const int ncls = (!tr && a.stride == 2) ? 2 : 1;
+
+  if (warp == WPROD) {
+    if (lane == 0) {
+      // the weights, once
+      mb_expect_tx(su32(&wres), (uint32_t)r.bres);
+      for (int tap = 0; tap < a.k * a.k; ++tap)
+        for (int ch = 0; ch < nch; ++ch)
+          tma_load_2d(wbase + (uint32_t)(tap * nch + ch) * wtile, &mB, tap * a.kpad + ch * TK, 0, su32(&wres));
+      uint32_t g = 0;
+      for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x) {
+        const Item it = decode(a, w);
+        const int nxt = tr ? it.ntx : a.k;
+        const int nty = tr ? (a.k - it.ky0 + 1) / 2 : 0;
+        bool ok = true;
+        for (int ch = 0; ch < nch && ok; ++ch)
+          for (int cls = 0; cls < ncls && ok; ++cls)
+            for (int xt = 0; xt < nxt; ++xt, ++g) {
+              const int s = (int)(g % (uint32_t)NS);
+              const uint32_t use = g / (uint32_t)NS;
+              if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
+              int ix, iy;
+              if (!tr) {
+                ix = it.x0 * a.stride + xt - a.pad;
+                iy = a.stride == 1 ? it.y0 - a.pad : 2 * it.y0 + cls - a.pad;
+              } else {
+                const int kx = it.kx0 + 2 * xt;
+                ix = it.x0 + (it.px + a.pad - kx) / 2;
+                iy = it.y0 + (it.py + a.pad - it.ky0) / 2 - (nty - 1);
+              }
+              const uint32_t sA = base + (uint32_t)s * stage;
+              mb_expect_tx(su32(&full[s]), stage);
+              tma_load_4d(sA, &mA, ch * TK, ix, iy, it.b0, su32(&full[s]));
+            }
+        if (!ok) { atomicExch(&s_fail, 1); break; }
+      }
+      for (uint32_t j = g > (uint32_t)NS ? g - (uint32_t)NS : 0u; j < g; ++j)
+        mb_wait(su32(&full[j % (uint32_t)NS]), (j / (uint32_t)NS) & 1u);
+      mb_wait(su32(&wres), 0);
+    }
+  } else if (warp == WMMA) {
+    if (lane == 0) {
+      const uint32_t id = idesc(N);
+      const bool wok = mb_wait(su32(&wres), 0);
+      if (!wok) atomicExch(&s_fail, 1);
+      uint32_t g = 0;
+      int li = 0;
+      for (int w = blockIdx.x; w < a.nitems && wok && !failed(fail); w += gridDim.x, ++li) {
+        const Item it = decode(a, w);
+        const int acc = li & 1;
+        if (li >= 2 && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> 1) - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
+        const int nxt = tr ? it.ntx : a.k;
+        const int nty = tr ? (a.k - it.ky0 + 1) / 2 : 0;
+        bool ok = true, first = true;
+        for (int ch = 0; ch < nch && ok; ++ch)
+          for (int cls = 0; cls < ncls && ok; ++cls)
+            for (int xt = 0; xt < nxt; ++xt, ++g) {
+              const int s = (int)(g % (uint32_t)NS);
+              if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+              const uint32_t sA = base + (uint32_t)s * stage;
+              const int kx = tr ? it.kx0 + 2 * xt : xt;
+              const int nk4 = (min(TK, a.c0 - ch * TK) + 15) / 16;   // K-steps with real channels
+              // y-taps served by this box: j = 0 .. nj-1, box row j * BX (transposed: reversed)
+              const int nj = tr ? nty : (a.stride == 1 ? a.k : (a.k - cls + 1) / 2);
+              for (int j = 0; j < nj; ++j) {
+                const int ky = tr ? it.ky0 + 2 * j : (a.stride == 1 ? j : cls + 2 * j);
+                const int row = tr ? (nty - 1 - j) : j;
+                const uint64_t da = desc128(sA + (uint32_t)(row * a.BX * 128));
+                const uint64_t db = desc128(wbase + (uint32_t)((ky * a.k + kx) * nch + ch) * wtile);
+#pragma unroll
+                for (int k4 = 0; k4 < TK / 16; ++k4) {
+                  if (k4 >= nk4) break;
+                  const uint32_t accum = first ? 0u : 1u;
+                  first = false;
+                  asm volatile(
+                      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                      "l"(da + (uint64_t)(2 * k4)), "l"(db + (uint64_t)(2 * k4)), "r"(id), "r"(accum)
+                      : "memory");
+                }
+              }
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                               su32(&empty[s]))
+                           : "memory");
+            }
         if (!ok) { atomicExch(&s_fail, 1); break; }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                          su32(&tfull[acc]))
                      : "memory");
       }
-      // every MMA issued above completes before tensor memory is released (bounded)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
                    : "memory");
       mb_wait(su32(&drain), 0);
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the
-    // 16-column chunks grp, grp + 2, ... of the accumulator (grp = w / 4)
-    const int q4 = warp & 3, grp = warp >> 2;
-    const int m = q4 * 32 + lane;
-    const int bb = m / (a.BY * a.BX), rr = m - bb * a.BY * a.BX, by = rr / a.BX, bx = rr - by * a.BX;
-    int li = 0;
-    for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
-      if (epi_any(failed(fail))) break;
-      const Item it = decode(a, w);
-      const int acc = li & 1;
-      const bool ok = mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u);
-      if (epi_any(!ok)) { atomicExch(&s_fail, 1); break; }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
-      const int oy = a.transposed ? 2 * qy + it.py : qy, ox = a.transposed ? 2 * qx + it.px : qx;
-      const bool rv = it.nkb > 0 && b < a.B && oy < a.Ho && ox < a.Wo;
-      const size_t pix = ((size_t)b * a.Ho + oy) * a.Wo + ox;
-      // residual of the next chunk is requested before the current chunk's TMEM read
-      const bool pre = rv && a.ksplit <= 1 && a.res && a.vec;
-      uint4 rn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-      if (pre && 16 * grp + 16 <= a.Cout) {
-        const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + 16 * grp);
-        rn[0] = rp[0]; rn[1] = rp[1];
-      }
-      for (int c0 = 16 * grp; c0 < N; c0 += 32) {
-        const uint4 rc[2] = {rn[0], rn[1]};
-        if (pre && c0 + 48 <= a.Cout) {
-          const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + 32);
-          rn[0] = rp[0]; rn[1] = rp[1];
-        }
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (!rv) continue;
-        float f[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
-        if (a.ksplit > 1) {
-          // partial sums of this K range into the split's slice (plain stores)
-          float* dst = a.part + (size_t)it.split * a.slice + pix * a.Cout + c0;
-          if (c0 + 16 <= a.Cout && a.vec) {
-            float4* op = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) op[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + j < a.Cout) dst[j] = f[j];
-          }
-        } else {
-          finish16(a, f, pix, c0, true, rc, s_bias, s_scale, s_shift);
-        }
-      }
-      // accumulator read: hand buffer acc back to the MMA warp
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&tempty[acc])) : "memory");
-    }
+    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_bias, s_scale, s_shift);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -442,28 +681,39 @@ __global__ void __launch_bounds__(256) k_splitk_finish(TmaArgs a, int M) {
       t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
     }
     float f[4] = {t.x, t.y, t.z, t.w};
+    const int cc = a.shuf ? c % a.cr : c;   // channel of the column (sub-pixel: within its phase)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      if (a.bias) f[j] += a.bias[c + j];
+      if (a.bias) f[j] += a.bias[cc + j];
       if (a.res) f[j] += __bfloat162float(a.res[p * a.ldr + c + j]);
       if (a.ybf) {
-        if (a.scale) f[j] = f[j] * a.scale[c + j] + a.shift[c + j];
-        if (a.act) f[j] = f[j] > 0.f ? f[j] : expm1f(f[j]);
+        if (a.scale) f[j] = f[j] * a.scale[cc + j] + a.shift[cc + j];
+        if (a.act) f[j] = elu_bf(f[j]);
       }
+    }
+    // destination pixel and channel of column c + j (sub-pixel: phase scatter)
+    size_t q = p;
+    int sc = c;
+    if (a.shuf) {
+      const int ph = c / a.cr;   // cr % 4 == 0: the four columns share the phase
+      const size_t wq = (size_t)a.Wo, hq = (size_t)a.Ho;
+      const size_t bq = p / (hq * wq), rq = p - bq * hq * wq, yq = rq / wq, xq = rq - yq * wq;
+      q = (bq * 2 * hq + 2 * yq + (ph >> 1)) * (2 * wq) + 2 * xq + (ph & 1);
+      sc = c - ph * a.cr;
     }
     if (a.ybf) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const __nv_bfloat16 yb = __float2bfloat16_rn(f[j]);
-        a.ybf[p * a.ldy + c + j] = yb;
+        a.ybf[q * a.ldy + sc + j] = yb;
         if (a.y2) {
           const float t = __bfloat162float(yb);
-          a.y2[p * a.ldy2 + c + j] = __float2bfloat16_rn(t > 0.f ? t : expm1f(t));
+          a.y2[q * a.ldy2 + sc + j] = __float2bfloat16_rn(elu_bf(t));
         }
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) a.out[p * a.ldo + c + j] = f[j];
+      for (int j = 0; j < 4; ++j) a.out[q * a.ldo + sc + j] = f[j];
     }
   }
 }
@@ -539,7 +789,43 @@ __global__ void k_weights_adjoint(const float* __restrict__ P, __nv_bfloat16* __
   }
 }
 
+// Sub-pixel copy of a transposed 5x5 stride-2 (pad 2) convolution: a 3x3 stride-1
+// convolution over the input grid with 4 * cout outputs, column n = (2 py + px) * cout + co:
+// WS[n][(dy + 1) * 3 + dx + 1][chunked ci] = W[py + 2 - 2 dy][px + 2 - 2 dx][ci][co], zero
+// where the tap falls outside the 5x5 kernel.  Chunks as the padded copy (c0, then c1).
+__global__ void k_weights_subpixel(const float* __restrict__ P, __nv_bfloat16* __restrict__ WS, int c0, int c1,
+                                   int cout, int kpad, int off1) {
+  const int cin = c0 + c1;
+  const size_t n = (size_t)4 * cout * 9 * kpad;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % kpad);
+    const size_t r = i / kpad;
+    const int t3 = (int)(r % 9), col = (int)(r / 9);
+    const int ph = col / cout, co = col - ph * cout, py = ph >> 1, px = ph & 1;
+    const int dy = t3 / 3 - 1, dx = t3 % 3 - 1;
+    const int ky = py + 2 - 2 * dy, kx = px + 2 - 2 * dx;
+    int ci = -1;
+    if (k < c0) ci = k;
+    else if (k >= off1 && k < off1 + c1) ci = c0 + (k - off1);
+    float v = 0.f;
+    if (ci >= 0 && ky >= 0 && ky < 5 && kx >= 0 && kx < 5) v = P[((size_t)(ky * 5 + kx) * cin + ci) * cout + co];
+    WS[i] = __float2bfloat16_rn(v);
+  }
+}
+
 }  // namespace
+
+size_t conv_tma_weight_sub_elems(int c0, int c1, int cout) {
+  return (size_t)4 * cout * 9 * 64 * ((c0 + 63) / 64 + (c1 + 63) / 64);
+}
+
+void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1, int cout, cudaStream_t s) {
+  const int nch0 = (c0 + 63) / 64;
+  const int kpad = 64 * (nch0 + (c1 + 63) / 64);
+  const size_t n = (size_t)4 * cout * 9 * kpad;
+  k_weights_subpixel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WS, c0, c1, cout, kpad,
+                                                                                      64 * nch0);
+}
 
 size_t conv_tma_weight_adj_elems(int k, int cin, int cout) {
   return (size_t)cin * k * k * 64 * ((cout + 63) / 64);
@@ -620,7 +906,7 @@ int ctas_per_sm(int nt) { return nt <= 64 ? 2 : 1; }
 int conv_tma_split(const ConvArgs& c) {
   const int Wq = c.transposed ? c.Wo / 2 : c.Wo, Hq = c.transposed ? c.Ho / 2 : c.Ho;
   // partial sums go to FP32 slices of the split scratch (capacity splitcnt_n floats)
-  if (!pow2(Wq) || !pow2(Hq) || !c.splitbuf || c.Cout % 4) return 1;
+  if (!pow2(Wq) || !pow2(Hq) || !c.splitbuf || c.Cout % 4 || (c.shuffle && c.cr % 4)) return 1;
   const int BX = Wq < 128 ? Wq : 128;
   const int BY = Hq < 128 / BX ? Hq : 128 / BX;
   const int BB = 128 / (BX * BY);
@@ -634,6 +920,89 @@ int conv_tma_split(const ConvArgs& c) {
   return sp;
 }
 
+// The column-reuse kernel for a layer that qualifies (single source, N <= 64, all
+// weights plus >= 2 stages in shared memory, tile width 8 or 16); false otherwise.
+bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
+  if (c.in1 || c.Cout > 64) return false;
+  const bool tr = c.transposed != 0;
+  if (tr ? (c.k != 5 || c.pad != 2) : !((c.k == 3 && c.stride == 1 && c.pad == 1) || (c.k == 5 && c.stride == 2 && c.pad == 2)))
+    return false;
+  const int Wq = tr ? c.Wo / 2 : c.Wo, Hq = tr ? c.Ho / 2 : c.Ho;
+  if (!pow2(Wq) || !pow2(Hq) || Wq < 8) return false;
+  const int BX = Wq < 16 ? Wq : 16, BY = 128 / BX;
+  if (Hq < BY || (tr && (c.Wo % 2 || c.Ho % 2))) return false;
+  const int NT = ((c.Cout + 15) / 16) * 16;
+  const int nch = (c.c0 + 63) / 64;
+  const int nyt = (!tr && c.stride == 1) ? c.k : (c.k + 1) / 2;
+  const int es = (!tr && c.stride == 2) ? 2 : 1;
+  const size_t bres = (size_t)c.k * c.k * nch * NT * 128;
+  const size_t bres_al = (bres + 1023) / 1024 * 1024;
+  const size_t stage = (size_t)(BY + nyt - 1) * BX * 128;
+  // these layers are bound by MMA issue rather than loads: worth it only at two CTAs per SM
+  const int per_sm = 2;
+  if (bres_al + 3 * stage + 8 * 1024 > 112 * 1024) return false;
+  const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
+  if (bres_al + 2 * stage > budget) return false;
+  const int nst = (int)std::min<size_t>(MAXST, (budget - bres_al) / stage);
+  const size_t smem = 1024 + bres_al + (size_t)nst * stage;
+  static int max_dyn = -1;
+  if (max_dyn < 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_conv_tma_reuse) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_tma_reuse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
+      max_dyn = 0;
+    else
+      max_dyn = optin - (int)fa.sharedSizeBytes;
+  }
+  if ((long long)smem > max_dyn) return false;
+  // input boxes: BX x (BY + nyt - 1) pixels of 64 channels, element stride es
+  CUtensorMap mA, mB;
+  {
+    const MapKey key{c.in0, {4, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, es, 0}};
+    if (!cached_map(key, &mA, [&](CUtensorMap* o) {
+          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, 1, es);
+        }))
+      return false;
+  }
+  const int kpad = 64 * nch;
+  {
+    const int K = c.k * c.k * kpad;
+    const MapKey key{c.WP, {1, K, c.Cout, NT, 0, 0, 0, 0, 0, 0}};
+    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, NT); })) return false;
+  }
+  TmaArgs a{};
+  a.B = c.B; a.Ho = c.Ho; a.Wo = c.Wo; a.Cout = c.Cout; a.NT = NT;
+  a.k = c.k; a.stride = c.stride; a.pad = c.pad; a.transposed = c.transposed;
+  a.BX = BX; a.BY = BY; a.BB = 1;
+  a.tx = Wq / BX; a.ty = Hq / BY; a.tb = c.B;
+  a.nch0 = nch; a.nch1 = 0; a.bcast1 = 0;
+  a.c0 = c.c0; a.c1 = 0;
+  a.shuf = c.shuffle; a.cr = c.cr;
+  a.ksplit = 1;
+  a.nitems = a.tx * a.ty * a.tb * (tr ? 4 : 1);
+  a.nst = nst;
+  a.colsz = NT <= 32 ? 32 : 64;
+  a.kpad = kpad;
+  a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
+  a.scale = c.scale; a.shift = c.shift; a.act = c.ep_act; a.ybf = c.ybf; a.ldy = c.ldy;
+  a.y2 = c.ybf ? c.y2 : nullptr; a.ldy2 = c.ldy2;
+  a.part = nullptr; a.slice = 0;
+  a.err = err;
+  a.vec = ((c.ldo % 4 == 0) && !((uintptr_t)c.out & 15) && (c.ldy % 8 == 0) && !((uintptr_t)c.ybf & 15) &&
+           (!a.y2 || ((c.ldy2 % 8 == 0) && !((uintptr_t)a.y2 & 15))) &&
+           (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15)))) ? 1 : 0;
+  ReuseArgs r;
+  r.nyt = nyt;
+  r.bres = (int)bres;
+  const int grid = std::min(a.nitems, sm_count() * per_sm);
+  k_conv_tma_reuse<<<grid, NTHR, smem, s>>>(mA, mB, a, r);
+  return true;
+}
+
 const char* g_tma_reject = "";
 const char* conv_tma_last_reject() { return g_tma_reject; }
 
@@ -645,6 +1014,10 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   if (!c.transposed && c.stride != 1 && c.stride != 2) TMA_REJECT("stride");
   if (c.ld0 % 8 || (c.in1 && c.ld1 % 8)) TMA_REJECT("row stride");   // TMA zero-fills channels past c0 / c1
   if (!get_encoder()) TMA_REJECT("no tensor-map encoder");
+  if (launch_reuse(c, err, s)) {
+    g_tma_reject = "";
+    return true;
+  }
   const int Wq = c.transposed ? c.Wo / 2 : c.Wo, Hq = c.transposed ? c.Ho / 2 : c.Ho;
   if (!pow2(Wq) || !pow2(Hq) || (c.transposed && (c.Wo % 2 || c.Ho % 2))) TMA_REJECT("grid not a power of two");
   const int BX = Wq < 128 ? Wq : 128;
@@ -671,6 +1044,9 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.tx = Wq / BX; a.ty = Hq / BY;
   a.nch0 = (c.c0 + 63) / 64;
   a.nch1 = c.in1 ? (c.c1 + 63) / 64 : 0;
+  a.c0 = c.c0;
+  a.c1 = c.in1 ? c.c1 : 0;
+  a.shuf = c.shuffle; a.cr = c.cr;
   a.bcast1 = (c.in1 && c.bcast1) ? 1 : 0;
   a.ksplit = conv_tma_split(c);
   a.kpad = 64 * (a.nch0 + a.nch1);
@@ -892,7 +1268,7 @@ __global__ void __launch_bounds__(WG_THR, 1) k_wgrad_tma(const __grid_constant__
       if (failed(fail)) break;
       const WgItem it = wg_decode(a, w);
       const int acc = li & 1;
-      if (!mb_wait(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+      if (!mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int ci = it.mb * 128 + warp * 32 + lane;
       float* row = a.gW + ((size_t)it.tap * a.cin + ci) * a.cout;

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -47,6 +48,7 @@ struct ConvL {
   int c0, c1;               // input split: main source, encoder context
   size_t wpoff;             // offset of the padded weight copy (TMA path)
   size_t wpaoff;            // offset of the padded adjoint copy (data gradients on the TMA path)
+  size_t wsoff;             // offset of the sub-pixel copy (transposed layers with 4 cout <= 256), or SIZE_MAX
 };
 struct BnL { std::string name; int c; size_t goff; size_t soff; };
 
@@ -79,6 +81,8 @@ struct unet_ctx {
   size_t nwp = 0;
   __nv_bfloat16* WPAb = nullptr;                   // padded adjoint copies (data gradients, TMA path)
   size_t nwpa = 0;
+  __nv_bfloat16* WSb = nullptr;                    // sub-pixel copies of transposed layers (TMA path)
+  size_t nws = 0;
   __nv_bfloat16* gbf = nullptr;                    // BF16 copy of a layer's output gradient
   bool use_tma = true;
   int* d_err = nullptr;                            // failure record of the tensor-core kernel
@@ -141,12 +145,14 @@ void build_layout(unet_ctx* n) {
   const int L = c.levels;
   n->L = L;
   size_t off = 0, soff = 0;
-  size_t wpo = 0, wpao = 0;
+  size_t wpo = 0, wpao = 0, wso = 0;
   auto conv = [&](const std::string& nm, int kind, int k, int ci, int co, int c1) {
-    n->convs.push_back({nm, kind, k, ci, co, off, ci - c1, c1, wpo, wpao});
+    const bool sub = kind == 2 && k == 5 && 4 * co <= 256;
+    n->convs.push_back({nm, kind, k, ci, co, off, ci - c1, c1, wpo, wpao, sub ? wso : SIZE_MAX});
     off += (size_t)k * k * ci * co;
     wpo += conv_tma_weight_elems(k, ci - c1, c1, co);
     wpao += conv_tma_weight_adj_elems(k, ci, co);
+    if (sub) wso += conv_tma_weight_sub_elems(ci - c1, c1, co);
   };
   std::vector<std::pair<std::string, int>> bnl;
   int cin = c.in_ch;
@@ -174,6 +180,7 @@ void build_layout(unet_ctx* n) {
   conv("up1", 2, 5, ucin + c.context[1], c.out_ch, c.context[1]);
   n->nwp = wpo;
   n->nwpa = wpao;
+  n->nws = wso;
   n->bias_off = off;
   off += c.out_ch;
   for (auto& b : bnl) {
@@ -322,12 +329,34 @@ ConvArgs conv_args(const unet_ctx* n, const ConvL& cl, Src a, Src b, bool act, i
   c.WT = n->WTb + cl.woff;
   // the padded copy matches the layer's fixed (main, context) split
   c.WP = (a.c == cl.c0 && (b.p ? b.c : 0) == cl.c1) ? n->WPb + cl.wpoff : nullptr;
+  c.WS = (c.WP && cl.wsoff != SIZE_MAX) ? n->WSb + cl.wsoff : nullptr;
   c.out = out; c.ldo = ldo;
   c.splitbuf = n->splitbuf; c.splitcnt = n->splitcnt; c.splitcnt_n = n->splitcnt_n;
   return c;
 }
 
+// The sub-pixel form of a transposed 5x5 stride-2 convolution: the 3x3 stride-1
+// convolution over the input grid whose 4 Cout columns are the output phases.
+ConvArgs subpixel_args(const ConvArgs& a) {
+  ConvArgs c = a;
+  c.k = 3; c.stride = 1; c.pad = 1; c.transposed = 0;
+  c.Ho = a.Hi; c.Wo = a.Wi;
+  c.Cout = 4 * a.Cout;
+  c.WP = a.WS;
+  c.shuffle = 1; c.cr = a.Cout;
+  return c;
+}
+
+// The TMA kernel on the sub-pixel form when the layer has one (fewer, wider MMAs).
+bool try_subpixel(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (!(n->use_tc && n->use_tma && a.WS && a.transposed && a.k == 5 && a.pad == 2 && !a.in_act && !a.in_f32 &&
+        a.Ho == 2 * a.Hi && a.Wo == 2 * a.Wi && !a.res))
+    return false;
+  return conv_forward_tma(subpixel_args(a), n->d_err, s);
+}
+
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (try_subpixel(n, a, s)) { n->last_path = 2; return; }
   if (n->use_tc && conv_forward_small(a, s)) { n->last_path = 3; return; }
   if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) { n->last_path = 2; return; }
   if (n->use_tc && conv_tc_eligible(a)) { conv_forward_tc(a, n->d_err, s); n->last_path = 1; }
@@ -451,7 +480,8 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     f.y2 = y2;
     f.ldy2 = ldy2;
     bool done = false, wrote2 = false;
-    if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }
+    if (try_subpixel(n, f, s)) { n->last_path = 2; done = wrote2 = true; }
+    else if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }
     else if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; done = wrote2 = true; }
     else if (conv_tc_eligible(f)) {
       conv_forward_tc(f, n->d_err, s);
@@ -701,6 +731,7 @@ void refresh_bf16(unet_ctx* n, cudaStream_t s) {
     weights_kmajor(n->P + cl.woff, n->WTb + cl.woff, cl.k * cl.k, cl.cin, cl.cout, s);
     conv_tma_weights(n->P + cl.woff, n->WPb + cl.wpoff, cl.k, cl.c0, cl.c1, cl.cout, s);
     conv_tma_weights_adjoint(n->P + cl.woff, n->WPAb + cl.wpaoff, cl.k, cl.cin, cl.cout, cl.kind == 1, s);
+    if (cl.wsoff != SIZE_MAX) conv_tma_weights_subpixel(n->P + cl.woff, n->WSb + cl.wsoff, cl.c0, cl.c1, cl.cout, s);
   }
 }
 
@@ -839,6 +870,7 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   UCHECK(cudaMalloc(&n->WTb, np * 2));
   UCHECK(cudaMalloc(&n->WPb, n->nwp * 2));
   UCHECK(cudaMalloc(&n->WPAb, n->nwpa * 2));
+  UCHECK(cudaMalloc(&n->WSb, std::max<size_t>(n->nws, 1) * 2));
   UCHECK(cudaMalloc(&n->d_err, sizeof(int)));
   UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
   n->use_tc = !(cfg->flags & UNET_FLAG_SIMT);
@@ -891,7 +923,7 @@ void unet_destroy(unet_t n) {
   if (!n) return;
   cudaDeviceSynchronize();
   free_ws(n);
-  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb,
+  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb, (void*)n->WSb,
                   (void*)n->d_err, (void*)n->rstats,
                   (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
                   (void*)n->ev_shift, n->tmp_e})

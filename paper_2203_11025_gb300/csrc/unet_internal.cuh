@@ -35,6 +35,10 @@ struct ConvArgs {
   // split-K scratch of the TMA path: splitcnt_n floats for the FP32 partial-sum slices
   // (null: not split)
   float* splitbuf; int* splitcnt; long long splitcnt_n;
+  // sub-pixel form of a transposed 5x5 stride-2 convolution (TMA path): the weights
+  // [4 cout][3x3][chunks]; with shuffle = 1 the arguments describe the 3x3 convolution
+  // over the input grid with Cout = 4 cr columns scattered to the 2x output
+  const __nv_bfloat16* WS; int shuffle, cr;
 };
 
 void conv_forward(const ConvArgs& a, cudaStream_t s);
@@ -53,6 +57,8 @@ int conv_tma_split(const ConvArgs& a);
 // adjoint (data-gradient) weight copies for the TMA path: [cin][tap][64-chunks of cout],
 // taps reversed for stride-1 convolutions
 size_t conv_tma_weight_adj_elems(int k, int cin, int cout);
+size_t conv_tma_weight_sub_elems(int c0, int c1, int cout);
+void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1, int cout, cudaStream_t s);
 // weight gradient on the tensor cores (TMA path): gW += dW of the forward convolution a
 // (one BF16 source, no on-load activation) from g = dL/dy, BF16 [pixels][Cout] with ld ldg
 bool conv_wgrad_tma(const ConvArgs& a, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s);
