@@ -32,6 +32,12 @@ N_GRID = 256
 NRHS = 8
 TOL = 1e-7
 RESTART = 10
+# DRAM bytes (read + write) of the tensor-core convolution launches of one U-Net forward at
+# 256^2 x 8, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (the same
+# launches the tensor roofline's FLOPs and times cover); re-measure when those kernels change
+CONV_DRAM_BYTES = 116537344
+CONV_DRAM_SCOPE = ("sum over the 19 tensor-core convolution launches of one 256x256x8 U-Net forward "
+                   "(ncu dram__bytes_read.sum + dram__bytes_write.sum); algorithmic: every layer input read once + weights ~93 MB")
 TRAIN_PAIRS = 1024       # Eq. 3.8-3.9 pairs of the benchmark medium (single-model training, Sec. 4)
 TRAIN_EPOCHS = 96
 TRAIN_LR = 1e-3          # constant; measured fastest at this size (3e-3 stalls; Sec. 4 starts at 1e-4)
@@ -289,10 +295,11 @@ def run_ours(args):
                        "graph": "one CUDA graph per restart cycle"},
             "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b.nbytes),
                     "d2h_bytes_per_step": int(b.nbytes)},
-            "roofline": {"bound": "tensor", "kernel": "k_conv_tc (tcgen05 implicit-GEMM convolutions, all "
-                                                      "tensor-core U-Net layers of one forward)",
+            "roofline": {"bound": "tensor", "kernel": "k_conv_tma / k_conv_tma_reuse (tcgen05 implicit-GEMM "
+                                                      "convolutions: all tensor-core layers of one U-Net forward)",
                          "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s", "frac": achieved / tc_peak,
-                         "traffic": None, "peak_kind": peak_kind + " bf16 burst",
+                         "traffic": CONV_DRAM_BYTES, "traffic_scope": CONV_DRAM_SCOPE,
+                         "peak_kind": peak_kind + " bf16 burst",
                          "layer_ms_total": tot_conv_ms, "top_layer": {"name": top[3], "ms": top[0],
                                                                       "tflops": top[1] / top[0] / 1e9}},
             "roofline_hbm": {"bound": "hbm", "kernel": "k_mgs<float> (Arnoldi MGS pass)", "achieved": mgs_gbs,

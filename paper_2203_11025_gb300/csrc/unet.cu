@@ -357,7 +357,7 @@ bool try_subpixel(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
 
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
   if (try_subpixel(n, a, s)) { n->last_path = 2; return; }
-  if (n->use_tc && conv_forward_small(a, s)) { n->last_path = 3; return; }
+  if (n->use_tc && conv_forward_small(a, s)) { n->last_path = 3; return; }   // 4-channel input layer
   if (n->use_tc && n->use_tma && conv_forward_tma(a, n->d_err, s)) { n->last_path = 2; return; }
   if (n->use_tc && conv_tc_eligible(a)) { conv_forward_tc(a, n->d_err, s); n->last_path = 1; }
   else { conv_forward(a, s); n->last_path = 0; }
@@ -481,7 +481,7 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     f.ldy2 = ldy2;
     bool done = false, wrote2 = false;
     if (try_subpixel(n, f, s)) { n->last_path = 2; done = wrote2 = true; }
-    else if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }
+    else if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }   // measured faster than TMA here
     else if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; done = wrote2 = true; }
     else if (conv_tc_eligible(f)) {
       conv_forward_tc(f, n->d_err, s);

@@ -5,6 +5,7 @@
   python -m paper_2203_11025_gb300.profcase layers 256 8   # per-layer times of the U-Net forward
   python -m paper_2203_11025_gb300.profcase mvu 256 8      # one FGMRES(10) restart cycle with M_VU
                                                            # (profiler range = that cycle)
+  python -m paper_2203_11025_gb300.profcase mv 256 8       # the same with the plain SL V-cycle (M_V)
   python -m paper_2203_11025_gb300.profcase train 256 16   # one training step (forward, MSE, backward,
                                                            # Adam; profiler range = that step)
 
@@ -48,20 +49,19 @@ def main(argv):
         hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
         ms, _ = hz.time_kernel(5, b, reps=3)
         print(f"coarse solve {ms * 1e3:.1f} us")
-    elif what == "mvu":
+    elif what in ("mvu", "mv"):
         k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
         pos = synth.source_positions(n, n, b, synth.rhs_seed(0), 16)
         rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n).astype(np.complex128)).cuda()
         hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
-        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=1)
+        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=1) if what == "mvu" else None
+        pc = lib.HELM_PREC_VU if what == "mvu" else lib.HELM_PREC_V
         x = torch.zeros_like(rhs)
         for _ in range(2):   # warm-up: workspaces, graphs
-            hz.fgmres(rhs, x, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=10, restart=10,
-                      flags=lib.HELM_FLAG_X0_ZERO)
+            hz.fgmres(rhs, x, precond=pc, net=net, tol=1e-7, maxit=10, restart=10, flags=lib.HELM_FLAG_X0_ZERO)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        hz.fgmres(rhs, x, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=10, restart=10,
-                  flags=lib.HELM_FLAG_X0_ZERO)
+        hz.fgmres(rhs, x, precond=pc, net=net, tol=1e-7, maxit=10, restart=10, flags=lib.HELM_FLAG_X0_ZERO)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     elif what == "train":
