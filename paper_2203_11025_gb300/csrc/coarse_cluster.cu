@@ -53,18 +53,18 @@ __device__ __forceinline__ T2 zmul2(T2 a, T2 b) {
 __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
 __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
 
-template <typename T>
+template <typename T, int NT>
 struct ClusterRed {
   typedef typename vec2<T>::type T2;
-  T2 wsum[KT / 32][KMAX + 2];   // per-warp partials
+  T2 wsum[NT / 32][KMAX + 2];   // per-warp partials
   T2 csum[2][KMAX + 2];         // this CTA's totals, double-buffered across reductions
 };
 
 // Sum K complex values over the cluster: `vals(k, x, y)` gives this thread's partial
 // of value k (already summed over its points).  Result, identical in every CTA, in out[k].
 // Values are reduced two at a time so that the two shuffle chains overlap.
-template <typename T, int MK, typename F>
-__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed<T>& R, int buf, int K, F vals,
+template <typename T, int MK, int NT, typename F>
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed<T, NT>& R, int buf, int K, F vals,
                                                typename vec2<T>::type* out) {
   typedef typename vec2<T>::type T2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -87,7 +87,7 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed
   __syncthreads();
   if (threadIdx.x < K) {
     T2 t = zz<T>(0, 0);
-    for (int w = 0; w < KT / 32; ++w) { t.x += R.wsum[w][threadIdx.x].x; t.y += R.wsum[w][threadIdx.x].y; }
+    for (int w = 0; w < NT / 32; ++w) { t.x += R.wsum[w][threadIdx.x].x; t.y += R.wsum[w][threadIdx.x].y; }
     R.csum[buf][threadIdx.x] = t;
   }
   cl.sync();
@@ -95,7 +95,7 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed
     T2 t = zz<T>(0, 0);
     const int C = (int)cl.num_blocks();
     for (int r = 0; r < C; ++r) {
-      const ClusterRed<T>* rem = cl.map_shared_rank(&R, r);
+      const ClusterRed<T, NT>* rem = cl.map_shared_rank(&R, r);
       const T2 v = rem->csum[buf][threadIdx.x];
       t.x += v.x; t.y += v.y;
     }
@@ -104,11 +104,15 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed
   __syncthreads();
 }
 
-template <typename T, int PPT, int MK>
-__global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename vec2<T>::type* __restrict__ f,
+// NT threads per CTA; GB: the Krylov basis lives in global memory (gV, vectors vstride
+// apart, [vector][rhs][point]) and D^-1 is recomputed, for grids whose basis does not
+// fit in the cluster's shared memory; the halo vector u stays in shared memory.
+template <typename T, int PPT, int MK, int NT, bool GB>
+__global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename vec2<T>::type* __restrict__ f,
                                                        typename vec2<T>::type* __restrict__ out, int m, int rows,
-                                                       const int* gate) {
+                                                       const int* gate, typename vec2<T>::type* gV, size_t vstride) {
   typedef typename vec2<T>::type T2;
+  constexpr int KT = NT;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -118,10 +122,21 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
   const int NP = rows * nx;                            // points of this CTA
   const int p0 = rank * NP;                            // first global point
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* V = reinterpret_cast<T2*>(smem_raw);             // [(m+1)][NP]
-  T2* U = V + (size_t)(m + 1) * NP;                    // u = D^-1 v_j, [NP]
-  T2* DI = U + NP;                                     // D^-1, [NP]
-  __shared__ ClusterRed<T> R;
+  T2* Vs = reinterpret_cast<T2*>(smem_raw);            // [(m+1)][NP] (shared-memory basis)
+  T2* U = GB ? Vs : Vs + (size_t)(m + 1) * NP;         // u = D^-1 v_j, [NP]
+  T2* DI = U + NP;                                     // D^-1, [NP] (shared-memory basis only)
+  // basis vector i of this CTA's points
+  auto Vp = [&](int i) -> T2* {
+    return GB ? gV + (size_t)i * vstride + (size_t)rhs * N + p0 : Vs + (size_t)i * NP;
+  };
+  auto dinv = [&](int lp) -> T2 {
+    if (GB) {
+      const int gp = p0 + lp, y = gp / nx, x = gp - y * nx;
+      return cinv(diag_at(op, x, y));
+    }
+    return DI[lp];
+  };
+  __shared__ ClusterRed<T, NT> R;
   __shared__ T2 H[(KMAX + 1) * KMAX];
   __shared__ T2 hv[KMAX + 2];
   __shared__ T2 ys[KMAX];
@@ -140,13 +155,13 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     const int lp = tid + q * KT;
     if (lp < NP) {
       const int gp = p0 + lp, y = gp / nx, x = gp - y * nx;
-      DI[lp] = cinv(diag_at(op, x, y));
+      if (!GB) DI[lp] = cinv(diag_at(op, x, y));
       w[q] = fr[lp];
     } else {
       w[q] = czero<T2>();
     }
   }
-  cluster_reduce<T, MK>(cl, R, buf, 1, [&](int, T& a, T& b) {
+  cluster_reduce<T, MK, NT>(cl, R, buf, 1, [&](int, T& a, T& b) {
     a = 0; b = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) a += w[q].x * w[q].x + w[q].y * w[q].y;
@@ -170,18 +185,18 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const int lp = tid + q * KT;
-      if (lp < NP) V[lp] = cscale(w[q], inv);
+      if (lp < NP) Vp(0)[lp] = cscale(w[q], inv);
     }
   }
   const T ih2 = op.inv_h2;
   int k = 0;
   for (int j = 0; j < m; ++j) {
-    const T2* vj = V + (size_t)j * NP;
+    const T2* vj = Vp(j);
     // u = D^-1 v_j, then halo exchange
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const int lp = tid + q * KT;
-      if (lp < NP) U[lp] = cmul(vj[lp], DI[lp]);
+      if (lp < NP) U[lp] = cmul(vj[lp], dinv(lp));
     }
     cl.sync();
     const T2* Uup = rank > 0 ? cl.map_shared_rank(U, rank - 1) : nullptr;       // row above: its last row
@@ -204,9 +219,9 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
       w[q] = r;
     }
     // CGS pass 1: h1_i = <v_i, w>
-    cluster_reduce<T, MK>(cl, R, buf, j + 1, [&](int i, T& a, T& b) {
+    cluster_reduce<T, MK, NT>(cl, R, buf, j + 1, [&](int i, T& a, T& b) {
       a = 0; b = 0;
-      const T2* vi = V + (size_t)i * NP;
+      const T2* vi = Vp(i);
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         const int lp = tid + q * KT;
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     if (tid <= j) H[tid * m + j] = hv[tid];
     for (int i = 0; i <= j; ++i) {
       const T hx = hv[i].x, hy = hv[i].y;
-      const T2* vi = V + (size_t)i * NP;
+      const T2* vi = Vp(i);
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         const int lp = tid + q * KT;
@@ -226,10 +241,10 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     }
     __syncthreads();   // hv is rewritten by the next reduction
     // CGS pass 2: h2_i = <v_i, w> and ||w||^2 in one reduction (value j+1)
-    cluster_reduce<T, MK>(cl, R, buf, j + 2, [&](int i, T& a, T& b) {
+    cluster_reduce<T, MK, NT>(cl, R, buf, j + 2, [&](int i, T& a, T& b) {
       a = 0; b = 0;
       if (i <= j) {
-        const T2* vi = V + (size_t)i * NP;
+        const T2* vi = Vp(i);
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
           const int lp = tid + q * KT;
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     if (tid == 0) H[(j + 1) * m + j] = zz<T>(nrm, 0);
     for (int i = 0; i <= j; ++i) {
       const T hx = hv[i].x, hy = hv[i].y;
-      const T2* vi = V + (size_t)i * NP;
+      const T2* vi = Vp(i);
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         const int lp = tid + q * KT;
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     if (nrm == (T)0) break;                            // happy breakdown (identical in every CTA)
     if (j + 1 < m) {
       const T inv = (T)1 / nrm;
-      T2* vn = V + (size_t)(j + 1) * NP;
+      T2* vn = Vp(j + 1);
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         const int lp = tid + q * KT;
@@ -316,17 +331,17 @@ __global__ void __launch_bounds__(KT) k_coarse_cluster(Op<T> op, const typename 
     const int lp = tid + q * KT;
     if (lp >= NP) continue;
     T2 a = czero<T2>();
-    for (int i = 0; i < kk; ++i) a = cadd(a, cmul(ys[i], V[(size_t)i * NP + lp]));
-    outr[lp] = cmul(a, DI[lp]);
+    for (int i = 0; i < kk; ++i) a = cadd(a, cmul(ys[i], Vp(i)[lp]));
+    outr[lp] = cmul(a, dinv(lp));
   }
   cl.sync();   // keep shared memory alive until every CTA is done with remote reads
 }
 
-template <typename T, int PPT, int MK>
+template <typename T, int PPT, int MK, int NT, bool GB>
 bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, const int* gate, int C, int rows,
-                    size_t smem, cudaStream_t s) {
+                    size_t smem, void* gV, size_t vstride, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  auto kern = k_coarse_cluster<T, PPT, MK>;
+  auto kern = k_coarse_cluster<T, PPT, MK, NT, GB>;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -335,7 +350,7 @@ bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, 
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, nrhs, 1);
-  cfg.blockDim = dim3(KT, 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -345,19 +360,22 @@ bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, op, (const T2*)f, (T2*)out, m, rows, gate) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, kern, op, (const T2*)f, (T2*)out, m, rows, gate, (T2*)gV, vstride) == cudaSuccess;
 }
 
 }  // namespace
 
-// Cluster geometry: rows per CTA so that each CTA holds <= 1024 points, C <= 16, and
-// the CTA's basis fits in shared memory.  Returns false if the grid does not fit.
+// Cluster geometry.  Shared-memory basis: rows per CTA so that each CTA holds <= 1024
+// points (256 threads), C <= 16, and the CTA's basis fits in shared memory.  Otherwise,
+// with a global basis gV (vectors vstride apart, [vector][rhs][point]): 1024 threads per
+// CTA, C chosen so that the clusters of all right-hand sides fit in one wave, and only
+// u (one vector) in shared memory.  Returns false if the grid fits neither.
 template <typename T>
 bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, const int* gate,
-                                 cudaStream_t s) {
+                                 void* gV, size_t vstride, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
   const int nx = op.nx, ny = op.ny;
-  if (m > KMAX || nx > 1024) return false;
+  if (m > KMAX || nx > 1024 || m + 2 > 34) return false;
   int C = 0, rows = 0;
   for (int target : {2 * KT, 4 * KT}) {       // prefer <= 2 points per thread (more SMs per solve)
     for (int c = 1; c <= 16 && !C; c *= 2) {
@@ -366,25 +384,41 @@ bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int 
     }
     if (C) break;
   }
-  if (!C) return false;
-  if (m + 2 > 34) return false;
-  const int NP = rows * nx;
-  const size_t smem = ((size_t)(m + 1) + 2) * NP * sizeof(T2);
-  if (smem > 180 * 1024) return false;
-  const int ppt = (NP + KT - 1) / KT;
-  if (m + 2 <= 12) {
-    if (ppt <= 1) return launch_cluster<T, 1, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
-    if (ppt <= 2) return launch_cluster<T, 2, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
-    return launch_cluster<T, 4, 12>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+  if (C) {
+    const int NP = rows * nx;
+    const size_t smem = ((size_t)(m + 1) + 2) * NP * sizeof(T2);
+    if (smem <= 180 * 1024) {
+      const int ppt = (NP + KT - 1) / KT;
+      if (m + 2 <= 12) {
+        if (ppt <= 1) return launch_cluster<T, 1, 12, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+        if (ppt <= 2) return launch_cluster<T, 2, 12, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+        return launch_cluster<T, 4, 12, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+      }
+      if (ppt <= 1) return launch_cluster<T, 1, 34, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+      if (ppt <= 2) return launch_cluster<T, 2, 34, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+      return launch_cluster<T, 4, 34, KT, false>(op, f, out, nrhs, m, gate, C, rows, smem, nullptr, 0, s);
+    }
   }
-  if (ppt <= 1) return launch_cluster<T, 1, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
-  if (ppt <= 2) return launch_cluster<T, 2, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
-  return launch_cluster<T, 4, 34>(op, f, out, nrhs, m, gate, C, rows, smem, s);
+  // global basis: clusters of C CTAs x 1024 threads, C * nrhs <= 152 where possible
+  if (!gV || m + 2 > 12) return false;
+  constexpr int NTG = 1024;
+  C = 16;
+  while (C > 2 && (C * nrhs > 152 || ny % C)) C /= 2;
+  if (ny % C) return false;
+  rows = ny / C;
+  const int NP = rows * nx;
+  const size_t smem = (size_t)NP * sizeof(T2);
+  if (smem > 180 * 1024) return false;
+  const int ppt = (NP + NTG - 1) / NTG;
+  if (ppt <= 4) return launch_cluster<T, 4, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
+  if (ppt <= 8) return launch_cluster<T, 8, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
+  if (ppt <= 16) return launch_cluster<T, 16, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
+  return false;
 }
 
-template bool launch_coarse_gmres_cluster<float>(const Op<float>&, const void*, void*, int, int, const int*,
-                                                 cudaStream_t);
-template bool launch_coarse_gmres_cluster<double>(const Op<double>&, const void*, void*, int, int, const int*,
-                                                  cudaStream_t);
+template bool launch_coarse_gmres_cluster<float>(const Op<float>&, const void*, void*, int, int, const int*, void*,
+                                                 size_t, cudaStream_t);
+template bool launch_coarse_gmres_cluster<double>(const Op<double>&, const void*, void*, int, int, const int*, void*,
+                                                  size_t, cudaStream_t);
 
 }  // namespace helm

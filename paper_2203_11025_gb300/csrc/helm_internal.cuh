@@ -182,7 +182,7 @@ template <typename T> bool launch_coarse_gmres_fused(const Op<T>& op, const void
 // Coarsest GMRES(m) on one thread-block cluster per right-hand side (coarse_cluster.cu);
 // false if the grid does not fit (C <= 16 CTAs of <= 1024 points, basis in shared memory).
 template <typename T> bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m,
-                                                       const int* gate, cudaStream_t s);
+                                                       const int* gate, void* gbasis, size_t vstride, cudaStream_t s);
 
 // FGMRES (outer solver)
 void launch_bnorm(const double2* b, size_t N, int nrhs, SolveState& ss, ArnoldiState& st, int nb, double tol,

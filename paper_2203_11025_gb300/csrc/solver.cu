@@ -232,7 +232,7 @@ int coarse_gmres(helm_ctx* c, const void* f, void* out, int nrhs, const int* gat
   const size_t vstride = (size_t)nrhs * Nc;
   char* CV = (char*)W.CV;
   Op<T> op = op_on<T>(c, lc, c->d.beta);
-  if (c->cluster_coarse && launch_coarse_gmres_cluster<T>(op, f, out, nrhs, mc, gate, s)) {
+  if (c->cluster_coarse && launch_coarse_gmres_cluster<T>(op, f, out, nrhs, mc, gate, CV, vstride, s)) {
     HLAUNCH();
     return HELM_OK;
   }

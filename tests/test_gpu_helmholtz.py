@@ -206,10 +206,12 @@ def test_fgmres_host_io_matches_device(lib):
     assert torch.equal(xh, xd.cpu())
 
 
-def test_coarse_gmres_large_grid_uses_multikernel_path(lib):
-    """A coarsest grid too large for the one-launch kernel (144x144 complex64 > 160 KB)
-    takes the multi-kernel path automatically; parity holds there too."""
-    hz, prob = make(lib, 576, 576, abc=16)
+@pytest.mark.parametrize("n", [576, 1024])
+def test_coarse_gmres_large_grid_parity(lib, n):
+    """Coarsest grids whose Krylov basis does not fit in a cluster's shared memory (144²
+    and 256²) take the cluster kernel with the basis in global memory (1024 threads per
+    CTA); parity with the oracle's GMRES(10) holds there too."""
+    hz, prob = make(lib, n, n, abc=16)
     lc = prob.hierarchy[-1]
     f = crandn(19, (2, lc.ny, lc.nx))
     x = hz.coarse_solve(dev(f, torch.complex64)).cpu().numpy()
