@@ -70,7 +70,9 @@ int unet_zero_grad(unet_t net, helm_stream_t stream);
  * [B][ny][nx][out_ch]).  train != 0 uses batch statistics, updates the running
  * statistics and keeps what unet_backward needs.  A solver with context reads
  * the features of its attached encoder's last forward (unet_attach_encoder).
- * ny, nx must be multiples of 2^levels. */
+ * ny, nx must be multiples of 2^levels; B*ny*nx*2*widths[0] must stay below 2^31
+ * (HELM_EUNSUPPORTED otherwise, also from unet_precond and the U-Net preconditioned
+ * solves). */
 int unet_forward(unet_t net, const float* x, float* out, int B, int ny, int nx, int train, helm_stream_t stream);
 /* Backward of the last train-mode forward for the loss sum(gout * out): adds
  * parameter gradients; writes d loss / d x into gx if not null (device float32

@@ -281,6 +281,12 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
 
 int ensure_ws(unet_ctx* n, int B, int ny, int nx) {
   if (n->ws && n->B == B && n->ny == ny && n->nx == nx) return HELM_OK;
+  // Not every kernel forms element offsets in 64-bit arithmetic: keep the widest tensor (twice
+  // the first level's width at full resolution) below 2^31 elements.
+  if ((long long)B * ny * nx * 2 * n->cfg.widths[0] >= (1ll << 31)) {
+    set_error("U-Net batch too large: B*ny*nx*" + std::to_string(2 * n->cfg.widths[0]) + " must stay below 2^31");
+    return HELM_EUNSUPPORTED;
+  }
   free_ws(n);
   DevArena m;
   carve(n, m, B, ny, nx);
