@@ -813,7 +813,33 @@ __global__ void k_weights_subpixel(const float* __restrict__ P, __nv_bfloat16* _
   }
 }
 
+// Space-to-depth form of the 5x5 stride-2 input convolution (pad 2) from cin <= 4
+// channels: on the grid of 2x2 input blocks it is a 3x3 stride-1 convolution (pad 1)
+// whose input pixel holds the block's 4 cin values, channel (dy * 2 + dx) * cin + c.
+// Block tap (by, bx) and sub-pixel (dy, dx) meet the original tap (2 by + dy, 2 bx + dx);
+// taps 5 of that 6x6 footprint are zero.  WD[co][t3][k] (K-major, K padded to 64).
+__global__ void k_weights_s2d_in(const float* __restrict__ P, __nv_bfloat16* __restrict__ WD, int cin, int cout) {
+  const size_t n = (size_t)cout * 9 * 64;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i % 64);
+    const size_t r = i / 64;
+    const int t3 = (int)(r % 9), co = (int)(r / 9);
+    const int sub = k / cin, c = k - sub * cin;
+    const int ky = 2 * (t3 / 3) + (sub >> 1), kx = 2 * (t3 % 3) + (sub & 1);
+    float v = 0.f;
+    if (sub < 4 && ky < 5 && kx < 5) v = P[((size_t)(ky * 5 + kx) * cin + c) * cout + co];
+    WD[i] = __float2bfloat16_rn(v);
+  }
+}
+
 }  // namespace
+
+size_t conv_tma_weight_s2d_elems(int cout) { return (size_t)cout * 9 * 64; }
+
+void conv_tma_weights_s2d_in(const float* P, __nv_bfloat16* WD, int cin, int cout, cudaStream_t s) {
+  const size_t n = conv_tma_weight_s2d_elems(cout);
+  k_weights_s2d_in<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WD, cin, cout);
+}
 
 size_t conv_tma_weight_sub_elems(int c0, int c1, int cout) {
   return (size_t)4 * cout * 9 * 64 * ((c0 + 63) / 64 + (c1 + 63) / 64);

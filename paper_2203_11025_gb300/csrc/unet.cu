@@ -83,6 +83,7 @@ struct unet_ctx {
   size_t nwpa = 0;
   __nv_bfloat16* WSb = nullptr;                    // sub-pixel copies of transposed layers (TMA path)
   size_t nws = 0;
+  __nv_bfloat16* WDb = nullptr;                    // space-to-depth copy of a 4-channel input layer
   __nv_bfloat16* gbf = nullptr;                    // BF16 copy of a layer's output gradient
   bool use_tma = true;
   int* d_err = nullptr;                            // failure record of the tensor-core kernel
@@ -104,6 +105,8 @@ struct unet_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   __nv_bfloat16* x_in = nullptr;
+  __nv_bfloat16* xs2d = nullptr;                   // inference input in the space-to-depth layout
+  bool xs2d_valid = false;                         // the last input was written there (not to x_in)
   std::vector<float*> zdown;                       // [l] raw down conv output
   std::vector<__nv_bfloat16*> h0;                  // [l] after down BN + eLU
   std::vector<std::vector<float*>> t1, sres;       // [l][r] raw ResNet convs (s includes the residual)
@@ -217,6 +220,8 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
   auto M = [&](int l) { return (size_t)B * (ny >> l) * (nx >> l); };
   const int* w = c.widths;
   n->x_in = a.take<__nv_bfloat16>(M(0) * xin_ld(n));
+  n->xs2d = c.in_ch == 4 ? a.take<__nv_bfloat16>(M(0) * 4) : nullptr;
+  n->xs2d_valid = false;
   n->zdown.assign(L + 1, nullptr); n->h0.assign(L + 1, nullptr);
   n->t1.assign(L + 1, {}); n->sres.assign(L + 1, {}); n->a1.assign(L + 1, {}); n->hres.assign(L + 1, {});
   n->cat.assign(L + 1, nullptr); n->zup.assign(L + 1, nullptr);
@@ -279,11 +284,23 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
   n->scale = a.take<float>((size_t)B + 8);
 }
 
+// Not every kernel forms element offsets in 64-bit arithmetic: the widest tensor (twice the
+// first level's width at full resolution) stays below 2^31 elements.
+bool batch_fits(const unet_ctx* n, int B, int ny, int nx) {
+  return (long long)B * ny * nx * 2 * n->cfg.widths[0] < (1ll << 31);
+}
+
+// Images per network pass when a preconditioner applies the U-Net to nrhs right-hand sides:
+// the largest divisor of nrhs within the size limit (0 if not even one image fits).
+int apply_chunk(const unet_ctx* n, int nrhs, int ny, int nx) {
+  for (int c = nrhs; c >= 1; --c)
+    if (nrhs % c == 0 && batch_fits(n, c, ny, nx)) return c;
+  return 0;
+}
+
 int ensure_ws(unet_ctx* n, int B, int ny, int nx) {
   if (n->ws && n->B == B && n->ny == ny && n->nx == nx) return HELM_OK;
-  // Not every kernel forms element offsets in 64-bit arithmetic: keep the widest tensor (twice
-  // the first level's width at full resolution) below 2^31 elements.
-  if ((long long)B * ny * nx * 2 * n->cfg.widths[0] >= (1ll << 31)) {
+  if (!batch_fits(n, B, ny, nx)) {
     set_error("U-Net batch too large: B*ny*nx*" + std::to_string(2 * n->cfg.widths[0]) + " must stay below 2^31");
     return HELM_EUNSUPPORTED;
   }
@@ -359,6 +376,27 @@ bool try_subpixel(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
         a.Ho == 2 * a.Hi && a.Wo == 2 * a.Wi && !a.res))
     return false;
   return conv_forward_tma(subpixel_args(a), n->d_err, s);
+}
+
+// Inference inputs go to the space-to-depth layout when the input layer can run there:
+// 4 input channels, no encoder context, the TMA tensor-core path.
+bool s2d_input(const unet_ctx* n) {
+  const int hx = n->nx / 2, hy = n->ny / 2;   // the TMA kernel tiles power-of-two grids
+  return n->WDb && n->xs2d && n->use_tc && n->use_tma && hx > 0 && hy > 0 && !(hx & (hx - 1)) && !(hy & (hy - 1));
+}
+
+// The 5x5 stride-2 input layer as a 3x3 stride-1 convolution over 2x2 input blocks of
+// 16 channels (one K-step per tap on the tensor cores instead of CUDA-core FMAs).
+bool try_s2d_input(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
+  if (a.in1 || a.transposed || a.k != 5 || a.stride != 2 || a.pad != 2 || a.c0 != 4 || a.in_act || a.in_f32 ||
+      a.Hi != 2 * a.Ho || a.Wi != 2 * a.Wo)
+    return false;
+  ConvArgs c = a;
+  c.in0 = n->xs2d; c.c0 = 16; c.ld0 = 16;
+  c.Hi = a.Ho; c.Wi = a.Wo;
+  c.k = 3; c.stride = 1; c.pad = 1;
+  c.WP = n->WDb; c.WS = nullptr;
+  return conv_forward_tma(c, n->d_err, s);
 }
 
 void run_conv(unet_ctx* n, const ConvArgs& a, cudaStream_t s) {
@@ -486,7 +524,12 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
     f.y2 = y2;
     f.ldy2 = ldy2;
     bool done = false, wrote2 = false;
-    if (try_subpixel(n, f, s)) { n->last_path = 2; done = wrote2 = true; }
+    if (a.in0 == n->x_in && n->xs2d_valid) {
+      if (try_s2d_input(n, f, s)) { n->last_path = 2; done = wrote2 = true; }
+      else { s2d_to_std(n->xs2d, n->x_in, xin_ld(n), n->B, n->ny, n->nx, s); n->xs2d_valid = false; }
+    }
+    if (done) {
+    } else if (try_subpixel(n, f, s)) { n->last_path = 2; done = wrote2 = true; }
     else if (conv_forward_small(f, s)) { n->last_path = 3; done = true; }   // measured faster than TMA here
     else if (n->use_tma && conv_forward_tma(f, n->d_err, s)) { n->last_path = 2; done = wrote2 = true; }
     else if (conv_tc_eligible(f)) {
@@ -498,6 +541,10 @@ void conv_bn(unet_ctx* n, ConvArgs a, const std::string& bn, bool act, __nv_bflo
       if (y2 && !wrote2) elu_copy_bf16(y, ldy, a.Cout, (size_t)M, y2, ldy2, s);
       return;
     }
+  }
+  if (a.in0 == n->x_in && n->xs2d_valid) {
+    s2d_to_std(n->xs2d, n->x_in, xin_ld(n), n->B, n->ny, n->nx, s);
+    n->xs2d_valid = false;
   }
   run_conv(n, a, s);
   run_bn(n, bn, a.out, a.ldo, M, act, y, ldy, train, s);
@@ -739,6 +786,10 @@ void refresh_bf16(unet_ctx* n, cudaStream_t s) {
     conv_tma_weights_adjoint(n->P + cl.woff, n->WPAb + cl.wpaoff, cl.k, cl.cin, cl.cout, cl.kind == 1, s);
     if (cl.wsoff != SIZE_MAX) conv_tma_weights_subpixel(n->P + cl.woff, n->WSb + cl.wsoff, cl.c0, cl.c1, cl.cout, s);
   }
+  if (n->WDb) {
+    const ConvL& d1 = conv_of(n, "down1");
+    conv_tma_weights_s2d_in(n->P + d1.woff, n->WDb, d1.cin, d1.cout, s);
+  }
 }
 
 }  // namespace
@@ -769,15 +820,27 @@ static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool ad
   const int div = 1 << n->L;
   if (nx % div || ny % div) { set_error("grid not divisible by 2^levels of the U-Net"); return HELM_EINVAL; }
   if (n->cfg.in_ch != 4 || n->cfg.out_ch != 2) { set_error("preconditioner net needs 4 inputs, 2 outputs"); return HELM_EINVAL; }
-  if (n->ws == nullptr || n->B != nrhs || n->ny != ny || n->nx != nx) {
+  const int cb = apply_chunk(n, nrhs, ny, nx);
+  if (cb == 0) { set_error("grid too large for one U-Net image"); return HELM_EUNSUPPORTED; }
+  if (n->ws == nullptr || n->B != cb || n->ny != ny || n->nx != nx) {
     cudaStreamCaptureStatus cs;
     cudaStreamIsCapturing(s, &cs);
     if (cs != cudaStreamCaptureStatusNone) { set_error("U-Net workspace not prepared before capture"); return HELM_EINVAL; }
-    UTRY(ensure_ws(n, nrhs, ny, nx));
+    UTRY(ensure_ws(n, cb, ny, nx));
   }
-  make_input(r, real_bytes == 8, nrhs, ny, nx, h, k2f, gam, n->x_in, xin_ld(n), n->scale, n->part, gate, s);
-  UTRY(forward_impl(n, false, s));
-  write_output(n->out, real_bytes == 8, nrhs, ny, nx, n->scale, e, add, gate, s);
+  // right-hand sides in chunks of cb images (one chunk unless the size limit splits them)
+  const size_t vec_bytes = (size_t)nx * ny * 2 * real_bytes;
+  for (int c0 = 0; c0 < nrhs; c0 += cb) {
+    const void* rc = (const char*)r + c0 * vec_bytes;
+    void* ec = (char*)e + c0 * vec_bytes;
+    const int* gc = gate ? gate + c0 : nullptr;
+    const bool s2d = s2d_input(n);
+    make_input(rc, real_bytes == 8, cb, ny, nx, h, k2f, gam, s2d ? n->xs2d : n->x_in, xin_ld(n), n->scale, n->part,
+               gc, s, s2d);
+    n->xs2d_valid = s2d;
+    UTRY(forward_impl(n, false, s));
+    write_output(n->out, real_bytes == 8, cb, ny, nx, n->scale, ec, add, gc, s);
+  }
   UCHECK(cudaGetLastError());
   return HELM_OK;
 }
@@ -825,7 +888,9 @@ int unet_prepare_impl(helm_ctx* hc, void* netp, int nrhs) {
   double h, gmax;
   const float *k2f, *gam;
   helm_geometry(hc, &nx, &ny, &h, &abc_w, &gmax, &k2f, &gam);
-  UTRY(ensure_ws(n, nrhs, ny, nx));
+  const int cb = apply_chunk(n, nrhs, ny, nx);
+  if (cb == 0) { set_error("grid too large for one U-Net image"); return HELM_EUNSUPPORTED; }
+  UTRY(ensure_ws(n, cb, ny, nx));
   ensure_eval_coeffs(n, 0);
   if (n->encoder) ensure_eval_coeffs(n->encoder, 0);
   UCHECK(cudaDeviceSynchronize());
@@ -877,6 +942,8 @@ int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out) {
   UCHECK(cudaMalloc(&n->WPb, n->nwp * 2));
   UCHECK(cudaMalloc(&n->WPAb, n->nwpa * 2));
   UCHECK(cudaMalloc(&n->WSb, std::max<size_t>(n->nws, 1) * 2));
+  if (cfg->in_ch == 4 && cfg->context[0] == 0)
+    UCHECK(cudaMalloc(&n->WDb, conv_tma_weight_s2d_elems(cfg->widths[0]) * 2));
   UCHECK(cudaMalloc(&n->d_err, sizeof(int)));
   UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
   n->use_tc = !(cfg->flags & UNET_FLAG_SIMT);
@@ -929,7 +996,7 @@ void unet_destroy(unet_t n) {
   if (!n) return;
   cudaDeviceSynchronize();
   free_ws(n);
-  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb, (void*)n->WSb,
+  for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb, (void*)n->WSb, (void*)n->WDb,
                   (void*)n->d_err, (void*)n->rstats,
                   (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
                   (void*)n->ev_shift, n->tmp_e})
@@ -1088,7 +1155,13 @@ int unet_forward(unet_t n, const float* x, float* out, int B, int ny, int nx, in
   }
   cudaStream_t s = (cudaStream_t)stream;
   UTRY(ensure_ws(n, B, ny, nx));
-  to_bf16_slice(x, n->cfg.in_ch, n->x_in, xin_ld(n), n->cfg.in_ch, B * ny * nx, s);
+  if (!train && s2d_input(n)) {
+    to_bf16_s2d(x, n->cfg.in_ch, n->xs2d, B, ny, nx, s);
+    n->xs2d_valid = true;
+  } else {
+    to_bf16_slice(x, n->cfg.in_ch, n->x_in, xin_ld(n), n->cfg.in_ch, B * ny * nx, s);
+    n->xs2d_valid = false;
+  }
   UTRY(forward_impl(n, train != 0, s));
   if (out) UCHECK(cudaMemcpyAsync(out, n->out, (size_t)B * ny * nx * n->cfg.out_ch * 4, cudaMemcpyDeviceToDevice, s));
   return HELM_OK;
@@ -1157,6 +1230,7 @@ int unet_encode(unet_t solver, helm_t h, int train, helm_stream_t stream) {
   UCHECK(cudaMemcpy2DAsync(med, 8, k2f, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
   UCHECK(cudaMemcpy2DAsync(med + 1, 8, gam, 4, 4, (size_t)nx * ny, cudaMemcpyDeviceToDevice, s));
   to_bf16_slice(med, 2, e->x_in, xin_ld(e), 2, nx * ny, s);
+  e->xs2d_valid = false;
   return forward_impl(e, train != 0, s);
 }
 

@@ -57,6 +57,10 @@ int conv_tma_split(const ConvArgs& a);
 // adjoint (data-gradient) weight copies for the TMA path: [cin][tap][64-chunks of cout],
 // taps reversed for stride-1 convolutions
 size_t conv_tma_weight_adj_elems(int k, int cin, int cout);
+size_t conv_tma_weight_s2d_elems(int cout);
+// Space-to-depth copy WD of a 5x5 stride-2 input convolution from cin <= 4 channels:
+// 3x3 stride-1 taps over 2x2 input blocks of 4 * cin channels (K padded to 64).
+void conv_tma_weights_s2d_in(const float* P, __nv_bfloat16* WD, int cin, int cout, cudaStream_t s);
 size_t conv_tma_weight_sub_elems(int c0, int c1, int cout);
 void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1, int cout, cudaStream_t s);
 // weight gradient on the tensor cores (TMA path): gW += dW of the forward convolution a
@@ -90,8 +94,14 @@ void mse_loss(const float* out, const float* tgt, size_t n, int B, float* gout, 
 void adam_update(float* p, const float* g, float* m1, float* m2, size_t n, float lr, float b1, float b2, float eps,
                  int t, cudaStream_t s);
 void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);
+// Network input (Sec. 3.4): Re r, Im r divided by rms(r), kappa^2, gamma; s2d: into the
+// space-to-depth layout [b][y/2][x/2][2x2 block][4] (ny, nx even), else ldx-channel pixels.
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s);
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d);
+// FP32 4-channel pixels [M][lds] into the space-to-depth BF16 layout, and that layout back to
+// ldd-channel pixels (channels past 4 zeroed).
+void to_bf16_s2d(const float* src, int lds, __nv_bfloat16* dst, int B, int ny, int nx, cudaStream_t s);
+void s2d_to_std(const __nv_bfloat16* xs, __nv_bfloat16* dst, int ldd, int B, int ny, int nx, cudaStream_t s);
 void write_output(const float* out, bool fp64, int B, int ny, int nx, const float* sc, void* e, bool add,
                   const int* gate, cudaStream_t s);
 void gamma_field(int ny, int nx, int width, float gmax, float* g, cudaStream_t s);

@@ -484,8 +484,16 @@ __global__ void __launch_bounds__(256) k_input_partial(const T2* __restrict__ r,
   if (threadIdx.x == 0) part[b * kInBlocks + blockIdx.x] = sm[0];
 }
 
-template <typename T2>
-__global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, int N, double h2,
+// Offset of channel 0 of pixel (b, y, x) in the space-to-depth layout of a 4-channel
+// image: [b][y / 2][x / 2][(y % 2) * 2 + x % 2][4] (16 channels per 2x2 block).
+__device__ __forceinline__ size_t s2d_off(int b, int y, int x, int ny, int nx) {
+  return ((((size_t)b * (ny >> 1) + (y >> 1)) * (nx >> 1) + (x >> 1)) * 4 + ((y & 1) * 2 + (x & 1))) * 4;
+}
+
+// S2D: x holds the space-to-depth layout (nx columns per image row, 4 channels), else
+// ldx-channel pixels with channels 4.. zeroed.
+template <typename T2, bool S2D>
+__global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, int N, int nx, double h2,
                                                      const float* __restrict__ k2, const float* __restrict__ gam,
                                                      const float* __restrict__ part, __nv_bfloat16* __restrict__ x,
                                                      int ldx, float* __restrict__ sc, const int* gate) {
@@ -504,12 +512,48 @@ __global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, i
   const T2* rb = r + (size_t)b * N;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
     T2 v = rb[p];
+    if (S2D) {
+      const int y = p / nx, xx = p - y * nx;
+      __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(x + s2d_off(b, y, xx, N / nx, nx));
+      o[0] = __floats2bfloat162_rn((float)v.x * f, (float)v.y * f);
+      o[1] = __floats2bfloat162_rn(k2[p], gam[p]);
+      continue;
+    }
     __nv_bfloat16* o = x + ((size_t)b * N + p) * ldx;
     o[0] = __float2bfloat16_rn((float)v.x * f);
     o[1] = __float2bfloat16_rn((float)v.y * f);
     o[2] = __float2bfloat16_rn(k2[p]);
     o[3] = __float2bfloat16_rn(gam[p]);
     for (int c = 4; c < ldx; ++c) o[c] = __float2bfloat16_rn(0.f);
+  }
+}
+
+// FP32 [M][lds] (4 channels) into the space-to-depth BF16 layout.
+__global__ void k_to_bf16_s2d(const float* __restrict__ src, int lds, __nv_bfloat16* __restrict__ dst, int B,
+                              int ny, int nx) {
+  const size_t M = (size_t)B * ny * nx;
+  for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(m % nx);
+    const size_t r = m / nx;
+    const int y = (int)(r % ny), b = (int)(r / ny);
+    const float* q = src + m * lds;
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dst + s2d_off(b, y, x, ny, nx));
+    o[0] = __floats2bfloat162_rn(q[0], q[1]);
+    o[1] = __floats2bfloat162_rn(q[2], q[3]);
+  }
+}
+
+// Space-to-depth BF16 layout back to ldd-channel pixels (channels 4.. zeroed).
+__global__ void k_s2d_to_std(const __nv_bfloat16* __restrict__ xs, __nv_bfloat16* __restrict__ dst, int ldd, int B,
+                             int ny, int nx) {
+  const size_t M = (size_t)B * ny * nx;
+  for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(m % nx);
+    const size_t r = m / nx;
+    const int y = (int)(r % ny), b = (int)(r / ny);
+    const __nv_bfloat16* q = xs + s2d_off(b, y, x, ny, nx);
+    __nv_bfloat16* o = dst + m * ldd;
+    for (int c = 0; c < ldd; ++c) o[c] = c < 4 ? q[c] : __float2bfloat16_rn(0.f);
   }
 }
 
@@ -772,16 +816,26 @@ void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s)
 }
 
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s) {
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d) {
   const int N = nx * ny;
   const dim3 grid(kInBlocks, B);
   if (fp64) {
     k_input_partial<double2><<<grid, 256, 0, s>>>((const double2*)r, N, part, gate);
-    k_input_write<double2><<<grid, 256, 0, s>>>((const double2*)r, N, h * h, k2, gam, part, x, ldx, sc, gate);
+    if (s2d) k_input_write<double2, true><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
+    else k_input_write<double2, false><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
   } else {
     k_input_partial<float2><<<grid, 256, 0, s>>>((const float2*)r, N, part, gate);
-    k_input_write<float2><<<grid, 256, 0, s>>>((const float2*)r, N, h * h, k2, gam, part, x, ldx, sc, gate);
+    if (s2d) k_input_write<float2, true><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
+    else k_input_write<float2, false><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
   }
+}
+
+void to_bf16_s2d(const float* src, int lds, __nv_bfloat16* dst, int B, int ny, int nx, cudaStream_t s) {
+  k_to_bf16_s2d<<<grid_for((size_t)B * ny * nx), 256, 0, s>>>(src, lds, dst, B, ny, nx);
+}
+
+void s2d_to_std(const __nv_bfloat16* xs, __nv_bfloat16* dst, int ldd, int B, int ny, int nx, cudaStream_t s) {
+  k_s2d_to_std<<<grid_for((size_t)B * ny * nx), 256, 0, s>>>(xs, dst, ldd, B, ny, nx);
 }
 
 void write_output(const float* out, bool fp64, int B, int ny, int nx, const float* sc, void* e, bool add,

@@ -264,6 +264,22 @@ def test_unet_preconditioner_parity(lib, kind):
     assert nrel(e, ref) < 2e-2
 
 
+def test_unet_preconditioner_chunks_large_batches(lib):
+    # 2048^2 x 8 images of a 32-channel first level exceed the U-Net's 2^31-element tensor
+    # limit: the preconditioner runs the network on chunks of 4 right-hand sides, which must
+    # give exactly what two separate 4-RHS applications give
+    n = 2048
+    hz = lib.Helmholtz(torch.from_numpy(medium(n, n, 1001)).cuda())
+    c, _ = make_cfgs(lib, widths=(32, 64))
+    net = lib.UNet(c, seed=19)
+    r = torch.from_numpy(crandn(20, (8, n, n)).astype(np.complex64)).cuda()
+    e = hz.unet_precond(net, r, kind=lib.HELM_PREC_VU)
+    e0 = hz.unet_precond(net, r[:4].contiguous(), kind=lib.HELM_PREC_VU)
+    e1 = hz.unet_precond(net, r[4:].contiguous(), kind=lib.HELM_PREC_VU)
+    assert torch.isfinite(torch.view_as_real(e)).all()
+    assert torch.equal(e[:4], e0) and torch.equal(e[4:], e1)
+
+
 def test_encoder_solver_preconditioner(lib):
     n = 64
     hz, prob = _helm(lib, n)
