@@ -38,8 +38,7 @@ namespace helm {
 namespace {
 
 constexpr int TM = 128;
-constexpr int TK = 64;
-constexpr int MAXST = 8;           // stage ring capacity (the host picks nst <= MAXST)
+constexpr int MAXST = 12;          // stage ring capacity (the host picks nst <= MAXST)
 constexpr int NEPI = 8;                  // epilogue warps: 2 column groups x 4 TMEM lane quadrants
 constexpr int WPROD = NEPI, WMMA = NEPI + 1;
 constexpr int NTHR = 32 * (NEPI + 2);    // + the TMA producer warp and the MMA warp
@@ -101,13 +100,19 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
       : "memory");
 }
-__device__ __forceinline__ uint64_t desc128(uint32_t saddr) {
+// Shared-memory descriptor of a K-major operand whose rows (one pixel or one output
+// column) hold tk = 16, 32 or 64 BF16 channels: rows of 32, 64 or 128 bytes written by
+// TMA with the matching swizzle, 8-row groups 8 rows apart (stride byte offset), layout
+// type SWIZZLE_32B (6), SWIZZLE_64B (4) or SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t desc_k(uint32_t saddr, int tk) {
+  const uint32_t row = 2u * (uint32_t)tk;
+  const uint64_t lay = tk == 64 ? 2u : (tk == 32 ? 4u : 6u);
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)((8u * row) >> 4) << 32;
   d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
+  d |= lay << 61;
   return d;
 }
 __host__ __device__ constexpr uint32_t idesc(int n) {
@@ -119,7 +124,7 @@ struct TmaArgs {
   int k, stride, pad, transposed;
   int BX, BY, BB;                 // output tile (pixels of the output or phase grid)
   int tx, ty, tb;                 // tiles along x, y and images
-  int nch0, nch1;                 // 64-channel chunks per source
+  int nch0, nch1;                 // tk-channel chunks per source
   int c0, c1;                     // real channels per source (MMAs skip the zero-filled K)
   int shuf, cr;                   // sub-pixel output: column n = phase * cr + channel, pixel (2y + py, 2x + px)
   int bcast1;                     // source 1 is one image shared by the batch
@@ -128,7 +133,8 @@ struct TmaArgs {
   int nst;                        // pipeline stages (<= MAXST)
   int colsz;                      // TMEM columns of one accumulator (power of two >= 32)
   int vec;                        // every row pointer of out / ybf / res / part is 16-byte aligned
-  int kpad;                       // padded K per tap = 64 (nch0 + nch1)
+  int kpad;                       // padded K per tap = tk (nch0 + nch1)
+  int tk;                         // channels per K-chunk (stage row): 16, 32 or 64
   float* out; int ldo;
   const float* bias;
   const __nv_bfloat16* res; int ldr;
@@ -384,7 +390,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
   const int N = a.NT, NS = a.nst;
 
   const uint32_t base = (su32(smem) + 1023u) & ~1023u;
-  const uint32_t a_bytes = TM * 128, b_bytes = (uint32_t)N * 128, stage = a_bytes + b_bytes;
+  const int TK = a.tk;
+  const uint32_t a_bytes = TM * 2 * TK, b_bytes = (uint32_t)N * 2 * TK, stage = a_bytes + b_bytes;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
     for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), NEPI); }
@@ -463,12 +470,12 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
           if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sA = base + (uint32_t)s * stage;
-          const uint64_t da = desc128(sA), db = desc128(sA + a_bytes);
-          // K-steps of 16 that hold real channels (the rest of a 64-channel chunk is zero fill)
+          const uint64_t da = desc_k(sA, TK), db = desc_k(sA + a_bytes, TK);
+          // K-steps of 16 that hold real channels (the rest of a chunk is zero fill)
           const int cval = kch < a.nch0 ? min(TK, a.c0 - kch * TK) : min(TK, a.c1 - (kch - a.nch0) * TK);
           const int nk4 = (cval + 15) / 16;
 #pragma unroll
-          for (int k4 = 0; k4 < TK / 16; ++k4) {
+          for (int k4 = 0; k4 < 4; ++k4) {
             if (k4 >= nk4) break;
             const uint32_t accum = (kb > 0 || k4 > 0) ? 1u : 0u;
             asm volatile(
@@ -507,7 +514,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
 // memory next to the stage ring (one 128-pixel tile of BX x BY pixels, BX in {8, 16}):
 // the weights are loaded once per CTA, and per (x-tap, channel chunk) one TMA box of
 // (BY + nyt - 1) rows of BX pixels serves every y-tap of that column -- y-tap j is the
-// box from row j * BX on, i.e. BX * 128 bytes further, a whole number of 1024-byte
+// box from row j * BX on, i.e. BX * 2 tk bytes further, a whole number of 8-row
 // swizzle atoms.  Stride-2 convolutions split their y-taps into even and odd classes
 // (element stride 2 along y); transposed stride-2 convolutions use their phase's taps.
 // A K-block stage therefore holds one input box only.
@@ -528,8 +535,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
   const int N = a.NT, NS = a.nst;
   const uint32_t wbase = (su32(smem) + 1023u) & ~1023u;          // resident weights
   const uint32_t base = wbase + (((uint32_t)r.bres + 1023u) & ~1023u);
-  const uint32_t stage = (uint32_t)((a.BY + r.nyt - 1) * a.BX * 128);
-  const uint32_t wtile = (uint32_t)N * 128;                       // one (tap, chunk) weight tile
+  const int TK = a.tk;
+  const uint32_t stage = (uint32_t)((a.BY + r.nyt - 1) * a.BX * 2 * TK);
+  const uint32_t wtile = (uint32_t)N * 2 * TK;                    // one (tap, chunk) weight tile
   const int nch = a.nch0;
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) { mb_init(su32(&full[q]), 1); mb_init(su32(&empty[q]), 1); }
@@ -628,10 +636,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
               for (int j = 0; j < nj; ++j) {
                 const int ky = tr ? it.ky0 + 2 * j : (a.stride == 1 ? j : cls + 2 * j);
                 const int row = tr ? (nty - 1 - j) : j;
-                const uint64_t da = desc128(sA + (uint32_t)(row * a.BX * 128));
-                const uint64_t db = desc128(wbase + (uint32_t)((ky * a.k + kx) * nch + ch) * wtile);
+                const uint64_t da = desc_k(sA + (uint32_t)(row * a.BX * 2 * TK), TK);
+                const uint64_t db = desc_k(wbase + (uint32_t)((ky * a.k + kx) * nch + ch) * wtile, TK);
 #pragma unroll
-                for (int k4 = 0; k4 < TK / 16; ++k4) {
+                for (int k4 = 0; k4 < 4; ++k4) {
                   if (k4 >= nk4) break;
                   const uint32_t accum = first ? 0u : 1u;
                   first = false;
@@ -735,27 +743,32 @@ bool get_encoder() {
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// 4-D map over an NHWC BF16 source slice: (channels, x, y, image), box (64, BX*s, BY*s, BB).
-bool encode_act(CUtensorMap* m, const void* ptr, int C, int ld, int W, int H, int B, int BX, int BY, int BB, int es) {
+CUtensorMapSwizzle swizzle_for(int tk) {
+  return tk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (tk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+// 4-D map over an NHWC BF16 source slice: (channels, x, y, image), box (tk, BX*s, BY*s, BB).
+bool encode_act(CUtensorMap* m, const void* ptr, int C, int ld, int W, int H, int B, int BX, int BY, int BB, int es,
+                int tk) {
   if (((uintptr_t)ptr & 15) || (ld * 2) % 16) return false;
   cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
   cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * W, (cuuint64_t)ld * 2 * W * H};
-  cuuint32_t box[4] = {64, (cuuint32_t)(BX * es), (cuuint32_t)(BY * es), (cuuint32_t)BB};
+  cuuint32_t box[4] = {(cuuint32_t)tk, (cuuint32_t)(BX * es), (cuuint32_t)(BY * es), (cuuint32_t)BB};
   cuuint32_t estr[4] = {1, (cuuint32_t)es, (cuuint32_t)es, 1};
   if (box[1] > 256 || box[2] > 256) return false;
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(tk), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_w(CUtensorMap* m, const void* ptr, int K, int cout, int NT) {
+bool encode_w(CUtensorMap* m, const void* ptr, int K, int cout, int NT, int tk) {
   if (((uintptr_t)ptr & 15) || (K * 2) % 16) return false;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)cout};
   cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)NT};
+  cuuint32_t box[2] = {(cuuint32_t)tk, (cuuint32_t)NT};
   cuuint32_t estr[2] = {1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(tk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -817,12 +830,12 @@ __global__ void k_weights_subpixel(const float* __restrict__ P, __nv_bfloat16* _
 // channels: on the grid of 2x2 input blocks it is a 3x3 stride-1 convolution (pad 1)
 // whose input pixel holds the block's 4 cin values, channel (dy * 2 + dx) * cin + c.
 // Block tap (by, bx) and sub-pixel (dy, dx) meet the original tap (2 by + dy, 2 bx + dx);
-// taps 5 of that 6x6 footprint are zero.  WD[co][t3][k] (K-major, K padded to 64).
+// taps 5 of that 6x6 footprint are zero.  WD[co][t3][k] (K-major, 16 channels per tap).
 __global__ void k_weights_s2d_in(const float* __restrict__ P, __nv_bfloat16* __restrict__ WD, int cin, int cout) {
-  const size_t n = (size_t)cout * 9 * 64;
+  const size_t n = (size_t)cout * 9 * 16;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(i % 64);
-    const size_t r = i / 64;
+    const int k = (int)(i % 16);
+    const size_t r = i / 16;
     const int t3 = (int)(r % 9), co = (int)(r / 9);
     const int sub = k / cin, c = k - sub * cin;
     const int ky = 2 * (t3 / 3) + (sub >> 1), kx = 2 * (t3 % 3) + (sub & 1);
@@ -834,48 +847,56 @@ __global__ void k_weights_s2d_in(const float* __restrict__ P, __nv_bfloat16* __r
 
 }  // namespace
 
-size_t conv_tma_weight_s2d_elems(int cout) { return (size_t)cout * 9 * 64; }
+size_t conv_tma_weight_s2d_elems(int cout) { return (size_t)cout * 9 * 16; }
 
 void conv_tma_weights_s2d_in(const float* P, __nv_bfloat16* WD, int cin, int cout, cudaStream_t s) {
   const size_t n = conv_tma_weight_s2d_elems(cout);
   k_weights_s2d_in<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WD, cin, cout);
 }
 
-size_t conv_tma_weight_sub_elems(int c0, int c1, int cout) {
-  return (size_t)4 * cout * 9 * 64 * ((c0 + 63) / 64 + (c1 + 63) / 64);
+// Channels per K-chunk (one stage row per pixel) of a layer with sources of c0 and c1
+// channels: the narrowest of 16, 32, 64 that holds the wider source, so that narrow
+// layers stage no zero-filled channels (rows of 32, 64 or 128 bytes, swizzled to match).
+// The padded weight copies and the launchers both follow this rule.
+static int conv_tk(int c0, int c1) {
+  const int m = std::max(c0, c1);
+  return m <= 16 ? 16 : (m <= 32 ? 32 : 64);
 }
+
+// Padded K per tap of a two-source layer: each source in whole tk-channel chunks.
+static int kpad_of(int c0, int c1) {
+  const int tk = conv_tk(c0, c1);
+  return tk * ((c0 + tk - 1) / tk + (c1 + tk - 1) / tk);
+}
+
+size_t conv_tma_weight_sub_elems(int c0, int c1, int cout) { return (size_t)4 * cout * 9 * kpad_of(c0, c1); }
 
 void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1, int cout, cudaStream_t s) {
-  const int nch0 = (c0 + 63) / 64;
-  const int kpad = 64 * (nch0 + (c1 + 63) / 64);
+  const int tk = conv_tk(c0, c1);
+  const int kpad = kpad_of(c0, c1);
   const size_t n = (size_t)4 * cout * 9 * kpad;
   k_weights_subpixel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WS, c0, c1, cout, kpad,
-                                                                                      64 * nch0);
+                                                                                      tk * ((c0 + tk - 1) / tk));
 }
 
-size_t conv_tma_weight_adj_elems(int k, int cin, int cout) {
-  return (size_t)cin * k * k * 64 * ((cout + 63) / 64);
-}
+size_t conv_tma_weight_adj_elems(int k, int cin, int cout) { return (size_t)cin * k * k * kpad_of(cout, 0); }
 
 void conv_tma_weights_adjoint(const float* P, __nv_bfloat16* WPA, int k, int cin, int cout, bool flip,
                               cudaStream_t s) {
-  const int kpad = 64 * ((cout + 63) / 64);
+  const int kpad = kpad_of(cout, 0);
   const size_t n = (size_t)cin * k * k * kpad;
   k_weights_adjoint<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WPA, k * k, cin, cout, kpad,
                                                                                      flip ? 1 : 0);
 }
 
-size_t conv_tma_weight_elems(int k, int c0, int c1, int cout) {
-  const int kpad = 64 * ((c0 + 63) / 64 + (c1 + 63) / 64);
-  return (size_t)cout * k * k * kpad;
-}
+size_t conv_tma_weight_elems(int k, int c0, int c1, int cout) { return (size_t)cout * k * k * kpad_of(c0, c1); }
 
 void conv_tma_weights(const float* P, __nv_bfloat16* WP, int k, int c0, int c1, int cout, cudaStream_t s) {
-  const int nch0 = (c0 + 63) / 64;
-  const int kpad = 64 * (nch0 + (c1 + 63) / 64);
+  const int tk = conv_tk(c0, c1);
+  const int kpad = kpad_of(c0, c1);
   const size_t n = (size_t)cout * k * k * kpad;
   k_weights_padded<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(P, WP, k * k, c0, c1, cout, kpad,
-                                                                                     64 * nch0);
+                                                                                     tk * ((c0 + tk - 1) / tk));
 }
 
 int sm_count() {
@@ -939,7 +960,8 @@ int conv_tma_split(const ConvArgs& c) {
   const int tiles = (Wq / BX) * (Hq / BY) * ((c.B + BB - 1) / BB) * (c.transposed ? 4 : 1);
   const long long outsz = (long long)c.B * c.Ho * c.Wo * c.Cout;
   const int taps = c.transposed ? (c.k * c.k + 3) / 4 : c.k * c.k;
-  const int nkb = taps * ((c.c0 + 63) / 64 + (c.in1 ? (c.c1 + 63) / 64 : 0));
+  const int c1 = c.in1 ? c.c1 : 0, tk = conv_tk(c.c0, c1);
+  const int nkb = taps * ((c.c0 + tk - 1) / tk + (c1 + tk - 1) / tk);
   const int slots = sm_count() * ctas_per_sm(((c.Cout + 15) / 16) * 16);
   int sp = 1;
   while (tiles * sp * 2 <= slots && nkb / (sp * 2) >= 4 && sp < 16 && outsz * sp * 2 <= c.splitcnt_n) sp *= 2;
@@ -958,12 +980,13 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   const int BX = Wq < 16 ? Wq : 16, BY = 128 / BX;
   if (Hq < BY || (tr && (c.Wo % 2 || c.Ho % 2))) return false;
   const int NT = ((c.Cout + 15) / 16) * 16;
-  const int nch = (c.c0 + 63) / 64;
+  const int tk = conv_tk(c.c0, 0);
+  const int nch = (c.c0 + tk - 1) / tk;
   const int nyt = (!tr && c.stride == 1) ? c.k : (c.k + 1) / 2;
   const int es = (!tr && c.stride == 2) ? 2 : 1;
-  const size_t bres = (size_t)c.k * c.k * nch * NT * 128;
+  const size_t bres = (size_t)c.k * c.k * nch * NT * 2 * tk;
   const size_t bres_al = (bres + 1023) / 1024 * 1024;
-  const size_t stage = (size_t)(BY + nyt - 1) * BX * 128;
+  const size_t stage = (size_t)(BY + nyt - 1) * BX * 2 * tk;
   // these layers are bound by MMA issue rather than loads: worth it only at two CTAs per SM
   const int per_sm = 2;
   if (bres_al + 3 * stage + 8 * 1024 > 112 * 1024) return false;
@@ -985,20 +1008,20 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
       max_dyn = optin - (int)fa.sharedSizeBytes;
   }
   if ((long long)smem > max_dyn) return false;
-  // input boxes: BX x (BY + nyt - 1) pixels of 64 channels, element stride es
+  // input boxes: BX x (BY + nyt - 1) pixels of tk channels, element stride es
   CUtensorMap mA, mB;
   {
-    const MapKey key{c.in0, {4, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, es, 0}};
+    const MapKey key{c.in0, {4 + 16 * tk, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, es, 0}};
     if (!cached_map(key, &mA, [&](CUtensorMap* o) {
-          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, 1, es);
+          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, BX, BY + nyt - 1, 1, es, tk);
         }))
       return false;
   }
-  const int kpad = 64 * nch;
+  const int kpad = tk * nch;
   {
     const int K = c.k * c.k * kpad;
-    const MapKey key{c.WP, {1, K, c.Cout, NT, 0, 0, 0, 0, 0, 0}};
-    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, NT); })) return false;
+    const MapKey key{c.WP, {1 + 16 * tk, K, c.Cout, NT, 0, 0, 0, 0, 0, 0}};
+    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, NT, tk); })) return false;
   }
   TmaArgs a{};
   a.B = c.B; a.Ho = c.Ho; a.Wo = c.Wo; a.Cout = c.Cout; a.NT = NT;
@@ -1013,6 +1036,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   a.nst = nst;
   a.colsz = NT <= 32 ? 32 : 64;
   a.kpad = kpad;
+  a.tk = tk;
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
   a.scale = c.scale; a.shift = c.shift; a.act = c.ep_act; a.ybf = c.ybf; a.ldy = c.ldy;
   a.y2 = c.ybf ? c.y2 : nullptr; a.ldy2 = c.ldy2;
@@ -1051,10 +1075,12 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   const int BB = 128 / (BX * BY);
   if (c.in1 && c.bcast1 && BB > 1) TMA_REJECT("broadcast source with several images per tile");
   const int es = c.transposed ? 1 : c.stride;
+  const int tk = conv_tk(c.c0, c.in1 ? c.c1 : 0);
   CUtensorMap mA0, mA1, mB;
   auto act_map = [&](CUtensorMap* m, const void* p, int C, int ld, int nb) {
-    const MapKey key{p, {0, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es}};
-    return cached_map(key, m, [&](CUtensorMap* o) { return encode_act(o, p, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es); });
+    const MapKey key{p, {16 * tk, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es}};
+    return cached_map(key, m,
+                      [&](CUtensorMap* o) { return encode_act(o, p, C, ld, c.Wi, c.Hi, nb, BX, BY, BB, es, tk); });
   };
   if (!act_map(&mA0, c.in0, c.c0, c.ld0, c.B)) TMA_REJECT("source 0 map");
   if (c.in1) {
@@ -1068,18 +1094,19 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.k = c.k; a.stride = c.stride; a.pad = c.pad; a.transposed = c.transposed;
   a.BX = BX; a.BY = BY; a.BB = BB;
   a.tx = Wq / BX; a.ty = Hq / BY;
-  a.nch0 = (c.c0 + 63) / 64;
-  a.nch1 = c.in1 ? (c.c1 + 63) / 64 : 0;
+  a.tk = tk;
+  a.nch0 = (c.c0 + tk - 1) / tk;
+  a.nch1 = c.in1 ? (c.c1 + tk - 1) / tk : 0;
   a.c0 = c.c0;
   a.c1 = c.in1 ? c.c1 : 0;
   a.shuf = c.shuffle; a.cr = c.cr;
   a.bcast1 = (c.in1 && c.bcast1) ? 1 : 0;
   a.ksplit = conv_tma_split(c);
-  a.kpad = 64 * (a.nch0 + a.nch1);
+  a.kpad = tk * (a.nch0 + a.nch1);
   {
     const int K = c.k * c.k * a.kpad;
-    const MapKey key{c.WP, {1, K, c.Cout, a.NT, 0, 0, 0, 0, 0, 0}};
-    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, a.NT); }))
+    const MapKey key{c.WP, {1 + 16 * tk, K, c.Cout, a.NT, 0, 0, 0, 0, 0, 0}};
+    if (!cached_map(key, &mB, [&](CUtensorMap* o) { return encode_w(o, c.WP, K, c.Cout, a.NT, tk); }))
       TMA_REJECT("weight map");
   }
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
@@ -1100,7 +1127,7 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   // reserved, 4 KB of static barriers and epilogue constants, 1 KB alignment slack, 1 KB
   // margin): 4-8 stages
   const int per_sm = ctas_per_sm(a.NT);
-  const size_t stage = (size_t)TM * 128 + (size_t)a.NT * 128;
+  const size_t stage = ((size_t)TM + a.NT) * 2 * tk;
   const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
   a.nst = (int)std::min<size_t>(MAXST, budget / stage);
   if (a.nst < 2) TMA_REJECT("shared memory");
@@ -1405,14 +1432,14 @@ bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* g
   {
     const MapKey key{c.in0, {2, c.c0, c.ld0, c.Wi, c.Hi, c.B, a.bx, a.by, ex, 0}};
     if (!cached_map(key, &mX, [&](CUtensorMap* o) {
-          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, a.bx, a.by, 1, ex);
+          return encode_act(o, c.in0, c.c0, c.ld0, c.Wi, c.Hi, c.B, a.bx, a.by, 1, ex, 64);
         }))
       return false;
   }
   {
     const MapKey key{g, {3, c.Cout, ldg, c.Wo, c.Ho, c.B, a.bx, a.by, eg, 0}};
     if (!cached_map(key, &mG, [&](CUtensorMap* o) {
-          return encode_act(o, g, c.Cout, ldg, c.Wo, c.Ho, c.B, a.bx, a.by, 1, eg);
+          return encode_act(o, g, c.Cout, ldg, c.Wo, c.Ho, c.B, a.bx, a.by, 1, eg, 64);
         }))
       return false;
   }
