@@ -30,6 +30,7 @@
 #include <functional>
 #include <mutex>
 #include <unordered_map>
+#include <utility>
 
 #include "unet_internal.cuh"
 
@@ -81,6 +82,14 @@ __device__ __forceinline__ bool mb_wait_sleep(uint32_t a, uint32_t par) {
   }
   return false;
 }
+// Programmatic dependent launch: kernels launched with programmatic stream serialisation
+// may start while the previous kernel in the stream finishes; griddep_wait() blocks until
+// that kernel has completed and its writes are visible (a no-op without the attribute).
+// griddep_launch() lets the next such kernel be scheduled once every CTA of this grid has
+// issued it or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 __device__ __forceinline__ void mb_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
                : "memory");
@@ -399,18 +408,21 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
-    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
-    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
-    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
-    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
-  }
   const uint32_t ncols = 2u * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
         "r"(ncols)
         : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  // everything above overlaps the previous kernel; global memory is read from here on
+  griddep_wait();
+  griddep_launch();
+  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
+    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
+    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
+    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
+    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -547,18 +559,21 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
-    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
-    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
-    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
-    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
-  }
   const uint32_t ncols = 2u * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
                  "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  // everything above overlaps the previous kernel; global memory is read from here on
+  griddep_wait();
+  griddep_launch();
+  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
+    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
+    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
+    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
+    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -678,6 +693,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
 // Split-K epilogue: y[p][c] = act(BN(sum_s part[s][p][c] + bias[c] + res[p][c])), four
 // channels per thread (Cout % 4 == 0), BF16 into y or FP32 into out.
 __global__ void __launch_bounds__(256) k_splitk_finish(TmaArgs a, int M) {
+  griddep_wait();
+  griddep_launch();
   const int C4 = a.Cout / 4;
   const size_t n = (size_t)M * C4;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -968,6 +985,26 @@ int conv_tma_split(const ConvArgs& c) {
   return sp;
 }
 
+// Launch with programmatic stream serialisation (the kernel starts with griddep_wait());
+// a plain launch when the attribute is refused.
+template <typename... P, typename... A>
+void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) != cudaSuccess) {
+    cudaGetLastError();
+    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+  }
+}
+
 // The column-reuse kernel for a layer that qualifies (single source, N <= 64, all
 // weights plus >= 2 stages in shared memory, tile width 8 or 16); false otherwise.
 bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
@@ -1049,7 +1086,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   r.nyt = nyt;
   r.bres = (int)bres;
   const int grid = std::min(a.nitems, sm_count() * per_sm);
-  k_conv_tma_reuse<<<grid, NTHR, smem, s>>>(mA, mB, a, r);
+  launch_pdl(k_conv_tma_reuse, (unsigned)grid, NTHR, smem, s, mA, mB, a, r);
   return true;
 }
 
@@ -1148,11 +1185,12 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   }
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
-  k_conv_tma<<<grid, NTHR, smem, s>>>(mA0, mA1, mB, a);
+  launch_pdl(k_conv_tma, (unsigned)grid, NTHR, smem, s, mA0, mA1, mB, a);
   if (a.ksplit > 1) {
     const int M = c.B * c.Ho * c.Wo;
     const size_t n4 = (size_t)M * (c.Cout / 4);
-    k_splitk_finish<<<(unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8), 256, 0, s>>>(a, M);
+    launch_pdl(k_splitk_finish, (unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8), 256, 0, s, a,
+               M);
   }
   g_tma_reject = "";
   return true;

@@ -297,6 +297,27 @@ def test_encoder_solver_preconditioner(lib):
     assert nrel(e, ref) < 2e-2
 
 
+def test_encoder_solver_fgmres_512_32rhs(lib):
+    """512^2, 32 right-hand sides (16 point sources, 16 complex Gaussian), the default
+    encoder-solver pair (Sec. 3.3) as the M_VU network and plain SL on the same inputs:
+    every solution's FP64 residual, recomputed by the oracle's operator, is <= 1e-7."""
+    n = 512
+    hz, prob = _helm(lib, n)
+    enc = lib.UNet(lib.unet_cfg_default(lib.UNET_ENCODER), seed=21)
+    sol = lib.UNet(lib.unet_cfg_default(lib.UNET_SOLVER), seed=22)
+    sol.attach_encoder(enc)
+    sol.encode(hz)
+    pos = synth.source_positions(n, n, 16, synth.rhs_seed(3), 16)
+    b = np.concatenate([synth.point_sources(n, n, pos, 1.0 / n), synth.gaussian_rhs(n, n, 16, 2003)])
+    bd = torch.from_numpy(b.astype(np.complex128)).cuda()
+    for pc, net in ((lib.HELM_PREC_VU, sol), (lib.HELM_PREC_V, None)):
+        x, info = hz.fgmres(bd, precond=pc, net=net, tol=1e-7, maxit=20000)
+        assert info["status"] == 0
+        x = x.cpu().numpy()
+        for k in range(32):
+            assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])
+
+
 def test_gen_pairs_parity(lib):
     n = 32
     hz, prob = _helm(lib, n)
