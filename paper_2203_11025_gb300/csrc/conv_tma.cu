@@ -32,6 +32,7 @@
 #include <unordered_map>
 #include <utility>
 
+#include "pdl.cuh"
 #include "unet_internal.cuh"
 
 namespace helm {
@@ -82,14 +83,6 @@ __device__ __forceinline__ bool mb_wait_sleep(uint32_t a, uint32_t par) {
   }
   return false;
 }
-// Programmatic dependent launch: kernels launched with programmatic stream serialisation
-// may start while the previous kernel in the stream finishes; griddep_wait() blocks until
-// that kernel has completed and its writes are visible (a no-op without the attribute).
-// griddep_launch() lets the next such kernel be scheduled once every CTA of this grid has
-// issued it or exited.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
-
 __device__ __forceinline__ void mb_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
                : "memory");
@@ -985,26 +978,6 @@ int conv_tma_split(const ConvArgs& c) {
   return sp;
 }
 
-// Launch with programmatic stream serialisation (the kernel starts with griddep_wait());
-// a plain launch when the attribute is refused.
-template <typename... P, typename... A>
-void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, A&&... args) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...) != cudaSuccess) {
-    cudaGetLastError();
-    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
-  }
-}
-
 // The column-reuse kernel for a layer that qualifies (single source, N <= 64, all
 // weights plus >= 2 stages in shared memory, tile width 8 or 16); false otherwise.
 bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
@@ -1086,7 +1059,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   r.nyt = nyt;
   r.bres = (int)bres;
   const int grid = std::min(a.nitems, sm_count() * per_sm);
-  launch_pdl(k_conv_tma_reuse, (unsigned)grid, NTHR, smem, s, mA, mB, a, r);
+  launch_pdl(k_conv_tma_reuse, dim3(grid), dim3(NTHR), smem, s, mA, mB, a, r);
   return true;
 }
 
@@ -1185,12 +1158,12 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   }
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
-  launch_pdl(k_conv_tma, (unsigned)grid, NTHR, smem, s, mA0, mA1, mB, a);
+  launch_pdl(k_conv_tma, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
   if (a.ksplit > 1) {
     const int M = c.B * c.Ho * c.Wo;
     const size_t n4 = (size_t)M * (c.Cout / 4);
-    launch_pdl(k_splitk_finish, (unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8), 256, 0, s, a,
-               M);
+    launch_pdl(k_splitk_finish, dim3((unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8)), dim3(256),
+               0, s, a, M);
   }
   g_tma_reject = "";
   return true;
