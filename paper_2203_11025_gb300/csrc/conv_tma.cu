@@ -41,7 +41,8 @@ namespace {
 
 constexpr int TM = 128;
 constexpr int MAXST = 12;          // stage ring capacity (the host picks nst <= MAXST)
-constexpr int NEPI = 8;                  // epilogue warps: 2 column groups x 4 TMEM lane quadrants
+constexpr int NEPI = 8;                  // epilogue warps: 2 groups (alternate tiles) x 4 TMEM lane quadrants
+constexpr int NACC = 4;                  // TMEM accumulator buffers at most (the host picks nacc <= NACC)
 constexpr int WPROD = NEPI, WMMA = NEPI + 1;
 constexpr int NTHR = 32 * (NEPI + 2);    // + the TMA producer warp and the MMA warp
 constexpr long long kWait = 1ll << 24;       // try_wait rounds before a wait gives up (seconds at most)
@@ -137,6 +138,8 @@ struct TmaArgs {
   int vec;                        // every row pointer of out / ybf / res / part is 16-byte aligned
   int kpad;                       // padded K per tap = tk (nch0 + nch1)
   int tk;                         // channels per K-chunk (stage row): 16, 32 or 64
+  int nacc;                       // TMEM accumulator buffers (2 or 4; item i uses buffer i % nacc)
+  int epig;                       // epilogue: 1 = warp groups on alternate items, 0 = on alternate columns
   float* out; int ldo;
   const float* bias;
   const __nv_bfloat16* res; int ldr;
@@ -185,14 +188,28 @@ __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
 
 __device__ __forceinline__ bool failed(const volatile int* f) { return *f != 0; }
 
-// OR of a predicate over the epilogue warps (named barrier 1): a uniform decision.
-__device__ __forceinline__ bool epi_any(bool p) {
+// OR of a predicate over the epilogue warps that share an item: all 8 (named barrier 1),
+// or with alt the 4 of group g (named barrier 1 + g).  A uniform decision among them.
+__device__ __forceinline__ bool epi_any(bool p, int g, bool alt) {
   uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)p), "r"(NEPI * 32)
-      : "memory");
+  if (!alt)
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(NEPI * 32)
+        : "memory");
+  else if (g == 0)
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(NEPI / 2 * 32)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "n"(NEPI / 2 * 32)
+        : "memory");
   return r != 0;
 }
 
@@ -289,25 +306,30 @@ __device__ __forceinline__ void finish1(const TmaArgs& a, float g, size_t pix, i
 }
 
 // Epilogue warps (0 .. NEPI-1) of both convolution kernels: drain TMEM accumulator
-// buffer i & 1 of item i into the destination, then hand the buffer back.
+// buffer i % nacc of item i into the destination, then hand the buffer back.  Warp w reads
+// TMEM lanes 32 (w % 4) .. + 31 (the tile rows it may access).  With a.epig warps 0-3 take
+// the CTA's even items and warps 4-7 the odd ones, every column each (two narrow tiles
+// drain at a time); otherwise group w / 4 takes the 16-column chunks w / 4, w / 4 + 2, ...
+// of every item (wide tiles).
 __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
                                               int* s_fail, const float* s_bias, const float* s_scale,
                                               const float* s_shift) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.NT;
   volatile int* fail = s_fail;
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the
-  // 16-column chunks grp, grp + 2, ... of the accumulator (grp = w / 4)
   const int q4 = warp & 3, grp = warp >> 2;
   const int m = q4 * 32 + lane;
   const int bb = m / (a.BY * a.BX), rr = m - bb * a.BY * a.BX, by = rr / a.BX, bx = rr - by * a.BX;
-  int li = 0;
-  for (int w = blockIdx.x; w < a.nitems; w += gridDim.x, ++li) {
-    if (epi_any(failed(fail))) break;
+  const bool alt = a.epig != 0;
+  const int cfirst = alt ? 0 : 16 * grp, cstep = alt ? 16 : 32;
+  const int istep = alt ? 2 : 1;
+  int li = alt ? grp : 0;
+  for (int w = blockIdx.x + (alt ? grp : 0) * gridDim.x; w < a.nitems; w += istep * gridDim.x, li += istep) {
+    if (epi_any(failed(fail), grp, alt)) break;
     const Item it = decode(a, w);
-    const int acc = li & 1;
-    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u);
-    if (epi_any(!ok)) { atomicExch(s_fail, 1); break; }
+    const int acc = li % a.nacc;
+    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li / a.nacc) & 1u);
+    if (epi_any(!ok, grp, alt)) { atomicExch(s_fail, 1); break; }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
     const int oy = a.transposed ? 2 * qy + it.py : qy, ox = a.transposed ? 2 * qx + it.px : qx;
@@ -316,14 +338,14 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
     // residual of the next chunk is requested before the current chunk's TMEM read
     const bool pre = rv && a.ksplit <= 1 && a.res && a.vec;
     uint4 rn[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-    if (pre && 16 * grp + 16 <= a.Cout) {
-      const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + 16 * grp);
+    if (pre && cfirst + 16 <= a.Cout) {
+      const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + cfirst);
       rn[0] = rp[0]; rn[1] = rp[1];
     }
-    for (int c0 = 16 * grp; c0 < N; c0 += 32) {
+    for (int c0 = cfirst; c0 < N; c0 += cstep) {
       const uint4 rc[2] = {rn[0], rn[1]};
-      if (pre && c0 + 48 <= a.Cout) {
-        const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + 32);
+      if (pre && c0 + cstep + 16 <= a.Cout) {
+        const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + cstep);
         rn[0] = rp[0]; rn[1] = rp[1];
       }
       uint32_t v[16];
@@ -384,7 +406,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
                                                     const __grid_constant__ CUtensorMap mA1,
                                                     const __grid_constant__ CUtensorMap mB, TmaArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain;
+  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[NACC], tempty[NACC], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ float s_bias[256], s_scale[256], s_shift[256];
@@ -396,12 +418,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
   const uint32_t a_bytes = TM * 2 * TK, b_bytes = (uint32_t)N * 2 * TK, stage = a_bytes + b_bytes;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
-    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), NEPI); }
+    for (int q = 0; q < a.nacc; ++q) {
+      mb_init(su32(&tfull[q]), 1);
+      mb_init(su32(&tempty[q]), a.epig ? NEPI / 2 : NEPI);   // lane 0 of each draining warp
+    }
     mb_init(su32(&drain), 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  const uint32_t ncols = 2u * (uint32_t)a.colsz;
+  const uint32_t ncols = (uint32_t)a.nacc * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
         "r"(ncols)
@@ -463,9 +488,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
       int li = 0;
       for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x, ++li) {
         const Item it = decode(a, w);
-        const int acc = li & 1;
-        const uint32_t use = (uint32_t)(li >> 1);
-        if (li >= 2 && !mb_wait(su32(&tempty[acc]), (use - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+        const int acc = li % a.nacc;
+        const uint32_t use = (uint32_t)(li / a.nacc);
+        if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (use - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
         bool ok = true;
@@ -532,7 +557,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
                                                             const __grid_constant__ CUtensorMap mB, TmaArgs a,
                                                             ReuseArgs r) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[2], tempty[2], drain, wres;
+  __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[NACC], tempty[NACC], drain, wres;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ float s_bias[256], s_scale[256], s_shift[256];
@@ -546,13 +571,16 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
   const int nch = a.nch0;
   if (tid == 0) {
     for (int q = 0; q < NS; ++q) { mb_init(su32(&full[q]), 1); mb_init(su32(&empty[q]), 1); }
-    for (int q = 0; q < 2; ++q) { mb_init(su32(&tfull[q]), 1); mb_init(su32(&tempty[q]), NEPI); }
+    for (int q = 0; q < a.nacc; ++q) {
+      mb_init(su32(&tfull[q]), 1);
+      mb_init(su32(&tempty[q]), a.epig ? NEPI / 2 : NEPI);   // lane 0 of each draining warp
+    }
     mb_init(su32(&drain), 1);
     mb_init(su32(&wres), 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  const uint32_t ncols = 2u * (uint32_t)a.colsz;
+  const uint32_t ncols = (uint32_t)a.nacc * (uint32_t)a.colsz;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
                  "r"(ncols)
@@ -623,8 +651,11 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
       int li = 0;
       for (int w = blockIdx.x; w < a.nitems && wok && !failed(fail); w += gridDim.x, ++li) {
         const Item it = decode(a, w);
-        const int acc = li & 1;
-        if (li >= 2 && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> 1) - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
+        const int acc = li % a.nacc;
+        if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (uint32_t)(li / a.nacc - 1) & 1u)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
         const int nxt = tr ? it.ntx : a.k;
@@ -1045,6 +1076,8 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   a.nitems = a.tx * a.ty * a.tb * (tr ? 4 : 1);
   a.nst = nst;
   a.colsz = NT <= 32 ? 32 : 64;
+  a.nacc = NACC;                                     // 4 x <= 64 columns per CTA, two CTAs per SM
+  a.epig = 1;
   a.kpad = kpad;
   a.tk = tk;
   a.out = c.out; a.ldo = c.ldo; a.bias = c.bias; a.res = c.res; a.ldr = c.ldr;
@@ -1133,6 +1166,10 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.tb = (c.B + BB - 1) / BB;
   a.nitems = a.tx * a.ty * a.tb * nph * a.ksplit;
   a.colsz = a.NT <= 32 ? 32 : (a.NT <= 64 ? 64 : (a.NT <= 128 ? 128 : 256));
+  // accumulator buffers within the 512 TMEM columns of the SM's CTAs
+  a.nacc = NACC * a.colsz * ctas_per_sm(a.NT) <= 512 ? NACC : 2;
+  // narrow tiles drain two at a time (measured faster up to 64 columns, slower at 256)
+  a.epig = a.NT <= 64 ? 1 : 0;
   // stage ring sized to the shared memory left per CTA (228 KB per SM; per CTA 1 KB
   // reserved, 4 KB of static barriers and epilogue constants, 1 KB alignment slack, 1 KB
   // margin): 4-8 stages
