@@ -10,6 +10,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   network runs in inference mode (BatchNorm with running statistics).
   Pairs (Eq. 3.8-3.9): b = A x, x~ = k iterations of FGMRES(10) + M_V from 0,
   r = b - A x~, e = x - x~.
+  Residual loss (Remark after Eq. 3.7): |h^2 A e_net - h^2 r|^2 per sample, scaled by 1/s.
 """
 from __future__ import annotations
 
@@ -58,6 +59,26 @@ def gen_pairs(prob: H.Problem, x, ks, m=10):
         rs.append(b - H.apply_op(A, xt))
         es.append(x[j] - xt)
     return np.stack(rs), np.stack(es)
+
+
+def residual_loss(prob: H.Problem, y, x):
+    """Unsupervised residual loss (the Remark following Eq. 3.7): the norm of A e_net - r
+    in place of the error norm.  y: network outputs (B, ny, nx, 2) in target units
+    (e / s), x: network inputs (B, ny, nx, 4) whose channels 0, 1 are h^2 r / s, so that
+        rho = h^2 A (y0 + i y1) - (x0 + i x1) = h^2 (A e_net - r) / s.
+    Loss: sum over the grid of |rho|^2, mean over the batch (the convention of Eq. 3.7
+    here).  Gradient with respect to (Re y, Im y): (2 / B) conj(h^2 A conj(rho)), since
+    the gradient of |K y - x|^2 with respect to conj(y) is K^H (K y - x) and A is complex
+    symmetric (A^H = conj(A)).  Returns (loss, gradient (B, ny, nx, 2))."""
+    A = prob.A
+    h2 = A.h ** 2
+    yc = y[..., 0] + 1j * y[..., 1]
+    xc = x[..., 0] + 1j * x[..., 1]
+    rho = h2 * H.apply_op(A, yc) - xc
+    B = y.shape[0]
+    loss = float(np.sum(np.abs(rho) ** 2) / B)
+    g = (2.0 / B) * np.conj(h2 * H.apply_op(A, np.conj(rho)))
+    return loss, np.stack([g.real, g.imag], axis=-1)
 
 
 def flatten_params(cfg, P):

@@ -184,3 +184,41 @@ def test_encoder_solver_backward_matches_finite_differences():
     assert _fd_check(total, P, G, ["down1", "down2", "up2", "up1", "res2.0.k1"], rng, n=3) < 1e-6
     Ge = U.backward_features(enc_cfg, Pe, ce, gfe)
     assert _fd_check(total, Pe, Ge, ["down1", "res2.0.k2", "up2", "up1", "up2.bn.gamma"], rng, n=3) < 1e-6
+
+
+def _small_problem(n=8, seed=3):
+    rng = np.random.default_rng(seed)
+    k2 = rng.uniform(0.25, 1.0, (n, n))
+    return H.Problem(k2, omega=0.2 * np.pi * n, h=1.0 / n, abc_width=2, levels=1), rng
+
+
+def test_residual_loss_gradient_matches_finite_differences():
+    # the residual-loss gradient (Remark after Eq. 3.7) against central differences of the loss
+    from oracle import precond as PR
+    prob, rng = _small_problem()
+    y = rng.standard_normal((2, 8, 8, 2))
+    x = rng.standard_normal((2, 8, 8, 4))
+    loss, g = PR.residual_loss(prob, y, x)
+    for _ in range(4):
+        d = rng.standard_normal(y.shape)
+        eps = 1e-6
+        fd = (PR.residual_loss(prob, y + eps * d, x)[0] - PR.residual_loss(prob, y - eps * d, x)[0]) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-7 * max(1.0, abs(fd))
+    # and against the closed form sum |K y - x|^2 / B with the dense operator
+    K = H.assemble_dense(prob.A) * prob.h ** 2
+    yc = (y[..., 0] + 1j * y[..., 1]).reshape(2, -1)
+    xc = (x[..., 0] + 1j * x[..., 1]).reshape(2, -1)
+    ref = sum(np.linalg.norm(K @ yc[b] - xc[b]) ** 2 for b in range(2)) / 2
+    assert abs(loss - ref) <= 1e-10 * ref
+
+
+def test_residual_loss_vanishes_at_the_error():
+    # y = e / s with A e = r: rho = 0 (the unsupervised loss is minimal at the exact error)
+    from oracle import precond as PR
+    prob, rng = _small_problem(seed=4)
+    x = rng.standard_normal((1, 8, 8, 4))
+    K = H.assemble_dense(prob.A) * prob.h ** 2
+    e = np.linalg.solve(K, (x[0, ..., 0] + 1j * x[0, ..., 1]).ravel()).reshape(8, 8)
+    y = np.stack([e.real, e.imag], axis=-1)[None]
+    loss, g = PR.residual_loss(prob, y, x)
+    assert loss <= 1e-20 * np.sum(x[..., :2] ** 2) and np.abs(g).max() <= 1e-9
