@@ -39,7 +39,7 @@ RESTART = 10
 # DRAM bytes (read + write) of the tensor-core convolution launches of one U-Net forward at
 # 256^2 x 8, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum (the same
 # launches the tensor roofline's FLOPs and times cover); re-measure when those kernels change
-CONV_DRAM_BYTES = 120686592
+CONV_DRAM_BYTES = 120704512
 CONV_DRAM_SCOPE = ("sum over the 20 tensor-core convolution launches of one 256x256x8 U-Net forward "
                    "(ncu dram__bytes_read.sum + dram__bytes_write.sum); algorithmic: every layer input read once + weights ~93 MB")
 TRAIN_PAIRS = 1024       # Eq. 3.8-3.9 pairs of the benchmark medium (single-model training, Sec. 4)

@@ -512,6 +512,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
   *k2f = c->L[0].k2f;
   *gam = c->gam0;
 }
+double helm_omega(helm_ctx* c) { return c->d.omega; }
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
   const int r = real_bytes == 8 ? ensure_work<double>(c, nrhs, c->d.coarse_its)
                                 : ensure_work<float>(c, nrhs, c->d.coarse_its);

@@ -808,6 +808,7 @@ int residual_public(helm_ctx* c, int op, const void* b, const void* x, void* r, 
 void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double* gmax, const float** k2f,
                    const float** gam);
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs);
+double helm_omega(helm_ctx* c);
 }  // namespace helm
 
 // e = U-Net(r) (inference), with the network input built on the fly.
@@ -1259,6 +1260,28 @@ int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int coun
   cudaFreeAsync(d_coef, s);
   UCHECK(cudaGetLastError());
   UCHECK(cudaStreamSynchronize(s));   // the host arrays may be released by the caller
+  return HELM_OK;
+}
+
+int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float* gout, float* loss_dev,
+                       helm_stream_t stream) {
+  if (!h || !out || !x || !gout || !loss_dev || B < 1 || out == gout) {
+    set_error("bad arguments");
+    return HELM_EINVAL;
+  }
+  int nx, ny, abc_w;
+  double hh, gmax;
+  const float *k2f, *gam;
+  helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  const double om = helm_omega(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  float *rho = nullptr, *part = nullptr;
+  UCHECK(cudaMallocAsync(&rho, (size_t)B * nx * ny * 2 * sizeof(float), s));
+  UCHECK(cudaMallocAsync(&part, 256 * sizeof(float), s));
+  residual_loss(out, x, B, ny, nx, (float)(hh * hh * om * om), k2f, gam, rho, gout, part, loss_dev, s);
+  cudaFreeAsync(rho, s);
+  cudaFreeAsync(part, s);
+  UCHECK(cudaGetLastError());
   return HELM_OK;
 }
 

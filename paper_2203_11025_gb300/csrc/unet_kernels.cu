@@ -438,6 +438,65 @@ __global__ void k_sum_partials(const float* __restrict__ part, int n, int B, flo
   }
 }
 
+// Unsupervised residual loss (the Remark following Eq. 3.7) on network outputs y
+// [B][ny][nx][2] (units e / s) and inputs x [B][ny][nx][4] (channels 0, 1 = h^2 r / s):
+//   rho = h^2 A y - x_r,  (h^2 A y)_p = 4 y_p - (sum of the 4 neighbours, zero outside)
+//                                      - c kappa2_p (1 - i gamma_p) y_p,  c = h^2 omega^2.
+// Per-block sums of |rho|^2 go to part.
+__global__ void __launch_bounds__(256) k_resloss_rho(const float2* __restrict__ y, const float* __restrict__ x,
+                                                     int B, int ny, int nx, float c, const float* __restrict__ k2,
+                                                     const float* __restrict__ gam, float2* __restrict__ rho,
+                                                     float* __restrict__ part) {
+  const size_t N = (size_t)nx * ny, M = N * B;
+  float s = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i % N;
+    const int iy = (int)(p / nx), ix = (int)(p - (size_t)iy * nx);
+    const float2 v = y[i];
+    float2 nb = make_float2(0.f, 0.f);
+    if (ix > 0) { nb.x += y[i - 1].x; nb.y += y[i - 1].y; }
+    if (ix < nx - 1) { nb.x += y[i + 1].x; nb.y += y[i + 1].y; }
+    if (iy > 0) { nb.x += y[i - nx].x; nb.y += y[i - nx].y; }
+    if (iy < ny - 1) { nb.x += y[i + nx].x; nb.y += y[i + nx].y; }
+    const float d = c * k2[p], g = gam[p];
+    // -d (1 - i g)(a + i b) = -d (a + g b) - i d (b - g a)
+    const float rx = 4.f * v.x - nb.x - d * (v.x + g * v.y) - x[i * 4];
+    const float ry = 4.f * v.y - nb.y - d * (v.y - g * v.x) - x[i * 4 + 1];
+    rho[i] = make_float2(rx, ry);
+    s += rx * rx + ry * ry;
+  }
+  __shared__ float sm[256];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+// d loss / d (Re y, Im y) = (2 / B) conj(h^2 A conj(rho)): A is complex symmetric, so the
+// adjoint is the same stencil with the diagonal's imaginary part negated.
+__global__ void __launch_bounds__(256) k_resloss_grad(const float2* __restrict__ rho, int B, int ny, int nx, float c,
+                                                      const float* __restrict__ k2, const float* __restrict__ gam,
+                                                      float2* __restrict__ gout) {
+  const size_t N = (size_t)nx * ny, M = N * B;
+  const float sc = 2.f / B;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = i % N;
+    const int iy = (int)(p / nx), ix = (int)(p - (size_t)iy * nx);
+    const float2 v = rho[i];
+    float2 nb = make_float2(0.f, 0.f);
+    if (ix > 0) { nb.x += rho[i - 1].x; nb.y += rho[i - 1].y; }
+    if (ix < nx - 1) { nb.x += rho[i + 1].x; nb.y += rho[i + 1].y; }
+    if (iy > 0) { nb.x += rho[i - nx].x; nb.y += rho[i - nx].y; }
+    if (iy < ny - 1) { nb.x += rho[i + nx].x; nb.y += rho[i + nx].y; }
+    const float d = c * k2[p], g = gam[p];
+    // -d (1 + i g)(a + i b) = -d (a - g b) - i d (b + g a)
+    gout[i] = make_float2(sc * (4.f * v.x - nb.x - d * (v.x - g * v.y)), sc * (4.f * v.y - nb.y - d * (v.y + g * v.x)));
+  }
+}
+
 // Adam (Kingma & Ba) with bias correction on the flat FP32 parameter vector.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, size_t n, float lr, float b1, float b2, float eps, float c1,
@@ -803,6 +862,15 @@ void mse_loss(const float* out, const float* tgt, size_t n, int B, float* gout, 
   const int nb = 256;
   k_mse<<<nb, 256, 0, s>>>(out, tgt, n, B, gout, part);
   k_sum_partials<<<1, 32, 0, s>>>(part, nb, B, loss);
+}
+
+void residual_loss(const float* y, const float* x, int B, int ny, int nx, float c, const float* k2, const float* gam,
+                   float* rho, float* gout, float* part, float* loss, cudaStream_t s) {
+  const int nb = 256;
+  k_resloss_rho<<<nb, 256, 0, s>>>((const float2*)y, x, B, ny, nx, c, k2, gam, (float2*)rho, part);
+  k_sum_partials<<<1, 32, 0, s>>>(part, nb, B, loss);
+  k_resloss_grad<<<grid_for((size_t)B * ny * nx), 256, 0, s>>>((const float2*)rho, B, ny, nx, c, k2, gam,
+                                                               (float2*)gout);
 }
 
 void adam_update(float* p, const float* g, float* m1, float* m2, size_t n, float lr, float b1, float b2, float eps,

@@ -32,7 +32,7 @@ ABI_SYMBOLS = [
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
     "unet_mse", "unet_adam_step", "unet_attach_encoder", "unet_encode", "unet_precond", "helm_gen_pairs",
-    "unet_make_batch", "unet_status", "unet_time_layer",
+    "unet_make_batch", "unet_status", "unet_time_layer", "unet_residual_loss",
 ]
 UNET_FLAG_SIMT, UNET_FLAG_NO_TMA = 1, 2
 UNET_STANDALONE, UNET_ENCODER, UNET_SOLVER = 0, 1, 2
@@ -104,6 +104,7 @@ def load():
         "unet_forward": (I, [P, P, P, I, I, I, I, P]),
         "unet_backward": (I, [P, P, P, P]),
         "unet_mse": (I, [P, P, ctypes.c_longlong, I, P, P, P]),
+        "unet_residual_loss": (I, [P, P, P, I, P, P, P]),
         "unet_adam_step": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, P]),
         "unet_attach_encoder": (I, [P, P]),
         "unet_encode": (I, [P, P, I, P]),
@@ -320,6 +321,16 @@ class Helmholtz:
         _check(self.lib.unet_make_batch(self.h, _ptr(r), _ptr(e), r.shape[0], count, nmix, idx.ctypes.data,
                                         coef.ctypes.data, _ptr(x), _ptr(t), _stream(stream)), "unet_make_batch")
         return x, t
+
+    def residual_loss(self, out, x, stream=None):
+        """Unsupervised residual loss of network outputs out [B, ny, nx, 2] for inputs x
+        [B, ny, nx, 4] on this medium; returns (loss tensor [1] on device, gout)."""
+        import torch
+        gout = torch.empty_like(out)
+        loss = torch.empty(1, dtype=torch.float32, device=out.device)
+        _check(self.lib.unet_residual_loss(self.h, _ptr(out), _ptr(x.contiguous()), out.shape[0], _ptr(gout),
+                                           _ptr(loss), _stream(stream)), "unet_residual_loss")
+        return loss, gout
 
     def unet_precond(self, net, r, kind=HELM_PREC_VU, out=None, stream=None):
         import torch

@@ -38,11 +38,16 @@ def batches(rng, npairs: int, batch: int, nmix: int):
 
 
 def train(hz, net, pairs=None, npairs: int = 256, epochs: int = 10, batch: int = 16, lr: float = 1e-3,
-          seed: int = 0, nmix: int = 2, kmax: int = 10, schedule_t0: int | None = None, log=None):
+          seed: int = 0, nmix: int = 2, kmax: int = 10, schedule_t0: int | None = None, log=None,
+          loss: str = "error"):
     """Train `net` on pairs of one medium (hz).  With an attached encoder the pair is
-    trained jointly (encoder forward in training mode before each step).
+    trained jointly (encoder forward in training mode before each step).  loss="error"
+    is Eq. 3.7 (supervised, the error of each pair); loss="residual" is the unsupervised
+    residual norm of the Remark following Eq. 3.7 (only the residuals are used).
     Returns the per-epoch mean loss."""
     import torch
+    if loss not in ("error", "residual"):
+        raise ValueError(f"unknown loss {loss!r}")
     if pairs is None:
         pairs = hz.gen_pairs(npairs, seed, kmax)
     r, e = pairs
@@ -57,10 +62,10 @@ def train(hz, net, pairs=None, npairs: int = 256, epochs: int = 10, batch: int =
                 net.encode(hz, train=True)
             net.zero_grad()
             out = net.forward(x, train=True)
-            loss, gout = net.mse(out, t)
+            lv, gout = net.mse(out, t) if loss == "error" else hz.residual_loss(out, x)
             net.backward(gout)
             net.adam_step(lr=cur)
-            losses.append(loss)
+            losses.append(lv)
         m = float(torch.stack(losses).mean().item()) if losses else float("nan")
         history.append(m)
         if log:

@@ -327,6 +327,30 @@ def test_encoder_solver_fgmres_512_32rhs(lib):
         assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])
 
 
+def test_residual_loss_parity(lib):
+    # the unsupervised residual loss (Remark after Eq. 3.7) and its gradient vs the oracle
+    n = 64
+    hz, prob = _helm(lib, n)
+    rng = np.random.default_rng(31)
+    y = rng.standard_normal((2, n, n, 2)).astype(np.float32)
+    x = rng.standard_normal((2, n, n, 4)).astype(np.float32)
+    loss, g = hz.residual_loss(torch.from_numpy(y).cuda(), torch.from_numpy(x).cuda())
+    ref_loss, ref_g = PR.residual_loss(prob, y.astype(np.float64), x.astype(np.float64))
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * ref_loss
+    assert nrel(g.cpu().numpy(), ref_g) < 1e-5
+
+
+def test_residual_loss_training_lowers_the_residual(lib):
+    # unsupervised training (loss="residual") on pairs of one medium lowers the loss
+    from paper_2203_11025_gb300 import train as T
+    n = 64
+    hz, _ = _helm(lib, n)
+    c, _ = make_cfgs(lib, widths=(8, 16))
+    net = lib.UNet(c, seed=33)
+    hist = T.train(hz, net, pairs=hz.gen_pairs(32, 34, 10), epochs=6, batch=8, lr=1e-3, seed=35, loss="residual")
+    assert all(np.isfinite(hist)) and hist[-1] < 0.8 * hist[0]
+
+
 def test_gen_pairs_parity(lib):
     n = 32
     hz, prob = _helm(lib, n)
