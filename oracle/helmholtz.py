@@ -371,6 +371,71 @@ def fgmres(A: Level, precond, b: np.ndarray, x0: np.ndarray | None = None, m: in
             x = x + y[i] * Z[i]
 
 
+@dataclass
+class BlockFgmresResult:
+    X: np.ndarray               # (p, ny, nx) solutions
+    iters: int                  # block iterations (each applies the preconditioner to p vectors)
+    relres: np.ndarray          # (p,) final true relative residuals
+    converged: bool
+    true_history: list          # largest true relative residual at each restart
+    estimates: list             # per block iteration: the p least-squares residual estimates / ||b_k||
+
+
+def block_fgmres(A: Level, precond, B: np.ndarray, X0: np.ndarray | None = None, m: int = 10,
+                 tol: float = 1e-7, maxit: int = 2000) -> BlockFgmresResult:
+    """Block flexible GMRES(m) for the p right-hand sides B (p, ny, nx): one block
+    Krylov space shared by all of them (the CPU solver of Sec. 4, after Calandra et al.).
+
+    Each cycle: R = B - A X = V_1 S (thin QR); for j = 1..m: Z_j = precond(V_j), column
+    by column; W = A Z_j; block modified Gram-Schmidt H_ij = V_i^H W, W -= V_i H_ij
+    (i = 1..j); thin QR W = V_{j+1} H_{j+1,j}.  The least-squares problem
+    min_Y ||E_1 S - Hbar_j Y||_F gives each column's residual estimate; the cycle ends
+    after m block steps or when every estimate is <= tol ||b_k||; then X += [Z_1..Z_j] Y.
+    Converged when every true relative residual is <= tol."""
+    p = B.shape[0]
+    shape = B.shape[1:]
+    n = int(np.prod(shape))
+    X = np.zeros_like(B, dtype=np.complex128) if X0 is None else X0.astype(np.complex128).copy()
+    bn = np.array([_norm(B[k]) for k in range(p)])
+    bn[bn == 0.0] = 1.0
+    iters = 0
+    true_history, estimates = [], []
+    while True:
+        R = B - apply_op(A, X)
+        rr = np.array([_norm(R[k]) for k in range(p)]) / bn
+        true_history.append(float(rr.max()))
+        if rr.max() <= tol:
+            return BlockFgmresResult(X, iters, rr, True, true_history, estimates)
+        if iters >= maxit:
+            return BlockFgmresResult(X, iters, rr, False, true_history, estimates)
+        V1, S = np.linalg.qr(R.reshape(p, n).T)
+        Vs, Zs = [V1], []
+        Hbar = np.zeros(((m + 1) * p, m * p), dtype=np.complex128)
+        Y = None
+        for j in range(m):
+            Zj = np.stack([precond(Vs[j][:, c].reshape(shape)).ravel() for c in range(p)], axis=1)
+            Zs.append(Zj)
+            W = np.stack([apply_op(A, Zj[:, c].reshape(shape)).ravel() for c in range(p)], axis=1)
+            for i in range(j + 1):
+                Hij = Vs[i].conj().T @ W
+                W = W - Vs[i] @ Hij
+                Hbar[i * p:(i + 1) * p, j * p:(j + 1) * p] = Hij
+            Vn, Hn = np.linalg.qr(W)
+            Hbar[(j + 1) * p:(j + 2) * p, j * p:(j + 1) * p] = Hn
+            iters += 1
+            k = j + 1
+            E = np.zeros(((k + 1) * p, p), dtype=np.complex128)
+            E[:p] = S
+            Hk = Hbar[:(k + 1) * p, :k * p]
+            Y = np.linalg.lstsq(Hk, E, rcond=None)[0]
+            est = np.linalg.norm(E - Hk @ Y, axis=0) / bn
+            estimates.append(est)
+            if est.max() <= tol or iters >= maxit:
+                break
+            Vs.append(Vn)
+        X = X + (np.concatenate(Zs, axis=1) @ Y).T.reshape(p, *shape)
+
+
 def convergence_factor(history_true0: float, final: float, iters: int) -> float:
     """Eq. 4.1: rho = (||r_T|| / ||r_0||)^(1/T)."""
     if iters <= 0:

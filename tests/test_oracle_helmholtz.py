@@ -369,3 +369,44 @@ def test_sl_iterations_in_paper_regime():
     assert res.converged
     assert 80 <= res.iters <= 200, res.iters
     assert 0.84 <= rho <= 0.95, rho
+
+
+# ---------------------------------------------------------------- block FGMRES
+def test_block_fgmres_one_column_is_fgmres():
+    """With one right-hand side the block method is FGMRES: same iterations and solution."""
+    prob = _small_problem()
+    b = _crandn(np.random.default_rng(40), (16, 16))
+    r1 = H.fgmres(prob.A, H.precond_v(prob), b, m=10, tol=1e-9)
+    rb = H.block_fgmres(prob.A, H.precond_v(prob), b[None], m=10, tol=1e-9)
+    assert rb.converged and rb.iters == r1.iters
+    assert np.linalg.norm(rb.X[0] - r1.x) / np.linalg.norm(r1.x) < 1e-7
+
+
+def test_block_fgmres_exact_on_full_block_krylov_space():
+    """p = 2 columns and m p >= n unknowns: one cycle spans the whole space."""
+    lv = _level(4, 4, seed=41, omega=6.0, beta=0.0)
+    B = _crandn(np.random.default_rng(42), (2, 4, 4))
+    res = H.block_fgmres(lv, lambda v: v, B, m=8, tol=1e-11)
+    assert res.converged and res.iters <= 8
+    for k in range(2):
+        assert np.linalg.norm(H.apply_op(lv, res.X[k]) - B[k]) / np.linalg.norm(B[k]) < 1e-10
+
+
+def test_block_gmres_minimises_over_explicit_block_krylov_space():
+    """Identity preconditioner, first cycle: after j block steps each column's residual
+    estimate equals min ||r_c - K y|| over y in span{R, K R, ..., K^(j-1) R} (all p
+    columns of R), from a least-squares solve over an explicitly built block basis."""
+    n, p, j = 8, 3, 3
+    lv = _level(n, n, seed=43, omega=9.0, beta=0.0, width=2)
+    B = _crandn(np.random.default_rng(44), (p, n, n))
+    res = H.block_fgmres(lv, lambda v: v, B, m=j, tol=1e-30, maxit=j)
+    K = H.assemble_dense(lv)
+    R = B.reshape(p, -1).T
+    blocks, Q = [R], None
+    for _ in range(j - 1):
+        blocks.append(K @ blocks[-1])
+    Q, _ = np.linalg.qr(np.concatenate(blocks, axis=1))
+    for c in range(p):
+        y, *_ = np.linalg.lstsq(K @ Q, R[:, c], rcond=None)
+        ref = np.linalg.norm(R[:, c] - K @ Q @ y) / np.linalg.norm(R[:, c])
+        assert abs(res.estimates[j - 1][c] - ref) <= 1e-9 * max(ref, 1e-3)
