@@ -146,6 +146,18 @@ typedef struct {
 int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
                  fgmres_result* result, helm_stream_t stream);
 
+/* Block flexible GMRES(m) (the CPU solver of Sec. 4): one block Krylov space for all
+ * nrhs right-hand sides (block size p = nrhs <= 16, (restart + 1) p^2 <= 4608).  Each
+ * cycle: R = b - A x in FP64 = V_1 S; per block step Z_j = M(V_j) on the p vectors,
+ * W = A Z_j, block classical Gram-Schmidt applied twice against V_1..V_j, W = V_{j+1}
+ * H_{j+1,j} by Cholesky QR applied twice; the least-squares problem runs on the host in
+ * FP64 and ends the cycle when every right-hand side's estimate is <= tol (or after
+ * `restart` block steps); then x += Z Y.  Same arguments, flags and results as
+ * fgmres_solve; iterations are block iterations (equal for every right-hand side), and
+ * result->launches is -1.  Synchronises with the host at every block step. */
+int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
+                  fgmres_result* result, helm_stream_t stream);
+
 /* Measurement hook (no counterpart in the paper): launch one of the solver's
  * internal kernels `reps` times back to back on `stream` over the FP32
  * workspace of nrhs right-hand sides (fine grid) and return the mean device

@@ -194,4 +194,16 @@ template <typename T> void launch_scale_v0(void* v0, size_t N, int nrhs, Arnoldi
 template <typename T> void launch_update_x(const void* Z, size_t vstride, size_t N, int nrhs, ArnoldiState& st,
                                            double2* x, int nb, cudaStream_t s);
 
+// Block kernels (block.cu) of block FGMRES.  Vectors [vector][point], `stride` apart.
+// out[i * p + k] = sum over N points of conj(U_i) W_k (q x p, FP64), via block_gram_parts(nsm)
+// per-CTA partials in `part` (q * p each); returns -1 if p > 16 or q * p > 4608.
+int block_gram_parts(int nsm);
+template <typename T2>
+int block_gram(const T2* U, size_t ustride, int q, const T2* W, size_t wstride, int p, size_t N, double2* part,
+               double2* out, int nsm, cudaStream_t s);
+// out_k (+)= sum_i in_i C[i * p + k] (C device FP64, q x p); in may equal out when q == p.
+template <typename TI, typename TO>
+int block_combine(const TI* in, size_t istride, int q, const double2* C, TO* out, size_t ostride, int p, size_t N,
+                  bool accumulate, int nsm, cudaStream_t s);
+
 }  // namespace helm

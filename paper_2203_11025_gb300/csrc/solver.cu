@@ -1,6 +1,8 @@
 // libhelm driver: handle, workspace, V-cycle orchestration, coarsest GMRES,
 // restarted FGMRES with one CUDA graph per restart cycle, and the C ABI
 // declared in include/helm.h.
+#include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -467,6 +469,302 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   return st;
 }
 
+// ===========================================================================
+// Block flexible GMRES(m) (the CPU solver of Sec. 4): one block Krylov space for the p
+// right-hand sides.  N-length work on the GPU (block Gram matrices, block combinations,
+// the operator and the preconditioner on p vectors at once); the small dense algebra in
+// FP64 on the host: QR factors of p-vector blocks by Cholesky of their Gram matrix, applied
+// twice (CholeskyQR2), block classical Gram-Schmidt applied twice against the basis, and
+// the least-squares problem min ||E_1 S - Hbar Y|| by Householder reflections added one
+// block column at a time.
+// ===========================================================================
+typedef std::complex<double> cd;
+
+// G = R^H R for the Hermitian p x p Gram matrix G (row-major); R upper triangular.  A
+// pivot below 1e-12 of its column's squared norm marks a column that depends on the
+// previous ones: its row of R is zero, and column k of Rinv (the inverse of R on the
+// independent columns) is zero, so W Rinv has a zero column there and W = (W Rinv) R.
+void chol_upper(const std::vector<cd>& G, int p, std::vector<cd>& R, std::vector<cd>& Rinv) {
+  R.assign((size_t)p * p, cd(0));
+  Rinv.assign((size_t)p * p, cd(0));
+  std::vector<char> dep(p, 0);
+  for (int j = 0; j < p; ++j) {
+    double d = G[(size_t)j * p + j].real();
+    for (int i = 0; i < j; ++i) d -= std::norm(R[(size_t)i * p + j]);
+    if (!(d > 1e-12 * G[(size_t)j * p + j].real())) { dep[j] = 1; continue; }
+    const double rjj = std::sqrt(d);
+    R[(size_t)j * p + j] = rjj;
+    for (int k = j + 1; k < p; ++k) {
+      cd t = G[(size_t)j * p + k];
+      for (int i = 0; i < j; ++i) t -= std::conj(R[(size_t)i * p + j]) * R[(size_t)i * p + k];
+      R[(size_t)j * p + k] = t / rjj;
+    }
+  }
+  for (int k = 0; k < p; ++k) {
+    if (dep[k]) continue;
+    for (int i = k; i >= 0; --i) {
+      if (dep[i]) continue;
+      cd t = i == k ? cd(1) : cd(0);
+      for (int l = i + 1; l <= k; ++l) t -= R[(size_t)i * p + l] * Rinv[(size_t)l * p + k];
+      Rinv[(size_t)i * p + k] = t / R[(size_t)i * p + i];
+    }
+  }
+}
+
+// Least squares of block FGMRES: Hbar ((m+1)p x mp, block upper Hessenberg with upper
+// triangular subdiagonal blocks) reduced to upper triangular form by one Householder
+// reflection per column (column c touches rows c .. c + p), applied to g = Q^H E_1 S too.
+struct BlockLS {
+  int p = 0, m = 0, rows = 0;
+  std::vector<cd> H;      // column-major, rows x (m p)
+  std::vector<cd> g;      // column-major, rows x p
+  std::vector<cd> refl;   // reflector of column c: p + 1 entries
+  void reset(int p_, int m_, const std::vector<cd>& S) {
+    p = p_; m = m_; rows = (m + 1) * p;
+    H.assign((size_t)rows * m * p, cd(0));
+    g.assign((size_t)rows * p, cd(0));
+    refl.assign((size_t)m * p * (p + 1), cd(0));
+    for (int i = 0; i < p; ++i)
+      for (int k = 0; k < p; ++k) g[(size_t)k * rows + i] = S[(size_t)i * p + k];
+  }
+  cd& h(int r, int c) { return H[(size_t)c * rows + r]; }
+  // col <- (I - 2 v v^H) col on rows c .. c + p (reflector of column c)
+  void apply(int c, cd* col) {
+    const cd* v = &refl[(size_t)c * (p + 1)];
+    cd t = 0;
+    for (int i = 0; i <= p; ++i) t += std::conj(v[i]) * col[c + i];
+    for (int i = 0; i <= p; ++i) col[c + i] -= 2.0 * v[i] * t;
+  }
+  // Block column j (rows 0 .. (j+2)p - 1 of Hbar, row-major hb[(j+2)p][p]); returns the
+  // least-squares residual norm of each right-hand side after j + 1 block steps.
+  std::vector<double> add(int j, const std::vector<cd>& hb) {
+    const int c0 = j * p;
+    for (int k = 0; k < p; ++k)
+      for (int r = 0; r < (j + 2) * p; ++r) h(r, c0 + k) = hb[(size_t)r * p + k];
+    for (int c = 0; c < c0; ++c)
+      for (int k = 0; k < p; ++k) apply(c, &H[(size_t)(c0 + k) * rows]);
+    for (int t = 0; t < p; ++t) {
+      const int c = c0 + t;
+      cd* x = &H[(size_t)c * rows];
+      double sig = 0;
+      for (int i = 0; i <= p; ++i) sig += std::norm(x[c + i]);
+      sig = std::sqrt(sig);
+      cd* v = &refl[(size_t)c * (p + 1)];
+      if (sig == 0.0) {
+        for (int i = 0; i <= p; ++i) v[i] = 0;
+        continue;
+      }
+      const cd ph = std::abs(x[c]) > 0 ? x[c] / std::abs(x[c]) : cd(1);
+      const cd alpha = -ph * sig;
+      for (int i = 0; i <= p; ++i) v[i] = x[c + i];
+      v[0] -= alpha;
+      double vn = 0;
+      for (int i = 0; i <= p; ++i) vn += std::norm(v[i]);
+      vn = std::sqrt(vn);
+      for (int i = 0; i <= p; ++i) v[i] /= vn;
+      for (int k = t; k < p; ++k) apply(c, &H[(size_t)(c0 + k) * rows]);
+      for (int k = 0; k < p; ++k) apply(c, &g[(size_t)k * rows]);
+    }
+    std::vector<double> est(p);
+    for (int k = 0; k < p; ++k) {
+      double e = 0;
+      for (int r = (j + 1) * p; r < (j + 2) * p; ++r) e += std::norm(g[(size_t)k * rows + r]);
+      est[k] = std::sqrt(e);
+    }
+    return est;
+  }
+  // Y = R^-1 g over the first n = (j+1) p rows (row-major n x p); zero where R is singular.
+  std::vector<cd> solve(int nblk) {
+    const int n = nblk * p;
+    std::vector<cd> Y((size_t)n * p, cd(0));
+    for (int k = 0; k < p; ++k)
+      for (int i = n - 1; i >= 0; --i) {
+        cd t = g[(size_t)k * rows + i];
+        for (int l = i + 1; l < n; ++l) t -= h(i, l) * Y[(size_t)l * p + k];
+        const cd d = h(i, i);
+        Y[(size_t)i * p + k] = std::abs(d) > 1e-300 ? t / d : cd(0);
+      }
+    return Y;
+  }
+};
+
+// Device buffers of one block solve, released (stream-ordered) on every return path.
+struct BlockBufs {
+  cudaStream_t s = nullptr;
+  std::vector<void*> ptrs;
+  ~BlockBufs() {
+    for (void* q : ptrs) cudaFreeAsync(q, s);
+  }
+  template <typename P>
+  cudaError_t get(P** out, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, bytes, s);
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *out = (P*)q;
+    return e;
+  }
+};
+
+template <typename T>
+int bfgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int p, const fgmres_opts& o,
+                fgmres_result* res, cudaStream_t caller) {
+  typedef typename vec2<T>::type T2;
+  const size_t N = level_points(c, 0);
+  const int m = o.restart;
+  HTRY(ensure_work<T>(c, p, m));
+  cudaStream_t s = c->own;
+  HCHECK(cudaEventRecord(c->ev_in, caller));
+  HCHECK(cudaStreamWaitEvent(s, c->ev_in, 0));
+  BlockBufs bb;
+  bb.s = s;
+  T2 *V, *Z, *Wb;
+  double2 *R64, *part, *gram, *dC;
+  const int qmax = (m + 1) * p;
+  HCHECK(bb.get(&V, (size_t)qmax * N * sizeof(T2)));
+  HCHECK(bb.get(&Z, (size_t)m * p * N * sizeof(T2)));
+  HCHECK(bb.get(&Wb, (size_t)p * N * sizeof(T2)));
+  HCHECK(bb.get(&R64, (size_t)p * N * sizeof(double2)));
+  HCHECK(bb.get(&part, (size_t)block_gram_parts(c->nsm) * qmax * p * sizeof(double2)));
+  HCHECK(bb.get(&gram, (size_t)qmax * p * sizeof(double2)));
+  HCHECK(bb.get(&dC, (size_t)qmax * p * sizeof(double2)));
+  if (o.flags & HELM_FLAG_X0_ZERO) HCHECK(cudaMemsetAsync(x, 0, (size_t)p * N * 16, s));
+  if (precond == HELM_PREC_JU || precond == HELM_PREC_VU) HTRY(unet_prepare_impl(c, net, p));
+  const Op<double> A64 = op_on<double>(c, 0, 0.0);
+  const Op<T> AT = op_on<T>(c, 0, 0.0);
+  std::vector<double2> hbuf((size_t)qmax * p);
+  // Gram matrix U^H W (q x p) to the host
+  auto gram_host = [&](auto* U, int q, auto* Wv, std::vector<cd>& G) -> int {
+    if (block_gram(U, N, q, Wv, N, p, N, part, gram, c->nsm, s) < 0) { g_err = "block Gram: sizes"; return HELM_EINVAL; }
+    HLAUNCH();
+    HCHECK(cudaMemcpyAsync(hbuf.data(), gram, (size_t)q * p * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    HCHECK(cudaStreamSynchronize(s));
+    G.resize((size_t)q * p);
+    for (size_t i = 0; i < G.size(); ++i) G[i] = cd(hbuf[i].x, hbuf[i].y);
+    return HELM_OK;
+  };
+  // coefficients (q x p, host) to the device
+  auto upload = [&](const std::vector<cd>& C, int q) -> int {
+    for (size_t i = 0; i < (size_t)q * p; ++i) hbuf[i] = make_double2(C[i].real(), C[i].imag());
+    HCHECK(cudaMemcpyAsync(dC, hbuf.data(), (size_t)q * p * sizeof(double2), cudaMemcpyHostToDevice, s));
+    HCHECK(cudaStreamSynchronize(s));   // hbuf is reused by the next call
+    return HELM_OK;
+  };
+  // blk (p vectors, in place) <- blk R^-1 twice; returns R = R2 R1 (row-major p x p)
+  auto qr_block = [&](T2* blk, std::vector<cd>& Rtot) -> int {
+    std::vector<cd> G, R1, R1i, R2, R2i;
+    HTRY(gram_host(blk, p, blk, G));
+    chol_upper(G, p, R1, R1i);
+    HTRY(upload(R1i, p));
+    if (block_combine(blk, N, p, dC, blk, N, p, N, false, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+    HLAUNCH();
+    HTRY(gram_host(blk, p, blk, G));
+    chol_upper(G, p, R2, R2i);
+    HTRY(upload(R2i, p));
+    if (block_combine(blk, N, p, dC, blk, N, p, N, false, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+    HLAUNCH();
+    Rtot.assign((size_t)p * p, cd(0));
+    for (int i = 0; i < p; ++i)
+      for (int k = 0; k < p; ++k) {
+        cd t = 0;
+        for (int l = 0; l < p; ++l) t += R2[(size_t)i * p + l] * R1[(size_t)l * p + k];
+        Rtot[(size_t)i * p + k] = t;
+      }
+    return HELM_OK;
+  };
+  // right-hand-side norms
+  std::vector<cd> G;
+  HTRY(gram_host(b, p, b, G));
+  std::vector<double> bn(p), rr(p, 0.0);
+  for (int k = 0; k < p; ++k) {
+    bn[k] = std::sqrt(std::max(0.0, G[(size_t)k * p + k].real()));
+    if (bn[k] == 0.0) bn[k] = 1.0;
+  }
+  std::vector<cd> ident((size_t)p * p, cd(0));
+  for (int k = 0; k < p; ++k) ident[(size_t)k * p + k] = 1.0;
+  int iters = 0, cycles = 0, st = HELM_OK;
+  BlockLS ls;
+  for (;;) {
+    // true residual in FP64 and its norms
+    launch_apply<double>(A64, x, b, R64, p, nullptr, s);
+    HLAUNCH();
+    HTRY(gram_host(R64, p, R64, G));
+    double worst = 0;
+    bool finite = true;
+    for (int k = 0; k < p; ++k) {
+      const double g2 = G[(size_t)k * p + k].real();
+      finite = finite && std::isfinite(g2);
+      rr[k] = std::sqrt(std::max(0.0, g2)) / bn[k];
+      worst = std::max(worst, rr[k]);
+    }
+    if (!finite) { st = HELM_ENAN; g_err = "non-finite residual in block FGMRES"; break; }
+    if (worst <= o.tol) break;
+    if (iters >= o.maxit) { st = HELM_MAXIT; break; }
+    if (++cycles > o.maxit + 3) { g_err = "block FGMRES cycle guard tripped"; return HELM_ECUDA; }
+    // V_1 S = R
+    HTRY(upload(ident, p));
+    if (block_combine(R64, N, p, dC, V, N, p, N, false, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+    HLAUNCH();
+    std::vector<cd> S;
+    HTRY(qr_block(V, S));
+    ls.reset(p, m, S);
+    int used = 0;
+    for (int j = 0; j < m; ++j) {
+      T2* Vj = V + (size_t)j * p * N;
+      T2* Zj = Z + (size_t)j * p * N;
+      HTRY(precond_apply<T>(c, precond, net, Vj, Zj, p, nullptr, s));
+      launch_apply<T>(AT, Zj, nullptr, Wb, p, nullptr, s);
+      HLAUNCH();
+      const int q = (j + 1) * p;
+      std::vector<cd> Hc((size_t)q * p, cd(0)), C;
+      for (int pass = 0; pass < 2; ++pass) {   // block classical Gram-Schmidt, twice
+        HTRY(gram_host(V, q, Wb, C));
+        for (size_t i = 0; i < C.size(); ++i) Hc[i] += C[i];
+        for (auto& v : C) v = -v;
+        HTRY(upload(C, q));
+        if (block_combine(V, N, q, dC, Wb, N, p, N, true, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+        HLAUNCH();
+      }
+      T2* Vn = V + (size_t)(j + 1) * p * N;
+      HTRY(upload(ident, p));
+      if (block_combine(Wb, N, p, dC, Vn, N, p, N, false, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+      HLAUNCH();
+      std::vector<cd> Hn;
+      HTRY(qr_block(Vn, Hn));
+      std::vector<cd> hb((size_t)(j + 2) * p * p, cd(0));
+      for (size_t i = 0; i < Hc.size(); ++i) hb[i] = Hc[i];
+      for (int i = 0; i < p; ++i)
+        for (int k = 0; k < p; ++k) hb[(size_t)(q + i) * p + k] = Hn[(size_t)i * p + k];
+      const std::vector<double> est = ls.add(j, hb);
+      ++iters;
+      used = j + 1;
+      bool conv = true;
+      for (int k = 0; k < p; ++k) conv = conv && est[k] / bn[k] <= o.tol;
+      if (conv || iters >= o.maxit) break;
+    }
+    // x += [Z_1 .. Z_used] Y
+    const std::vector<cd> Y = ls.solve(used);
+    HTRY(upload(Y, used * p));
+    if (block_combine(Z, N, used * p, dC, x, N, p, N, true, c->nsm, s) < 0) { g_err = "block combine"; return HELM_EINVAL; }
+    HLAUNCH();
+  }
+  HCHECK(cudaStreamSynchronize(s));
+  HCHECK(cudaEventRecord(c->ev_out, s));
+  HCHECK(cudaStreamWaitEvent(caller, c->ev_out, 0));
+  if (res) {
+    res->iters_max = iters;
+    res->cycles = cycles;
+    res->relres_max = 0;
+    res->status = st;
+    res->launches = -1;   // the preconditioner's launches are not counted here
+    for (int k = 0; k < p; ++k) {
+      res->relres_max = std::max(res->relres_max, rr[k]);
+      if (res->iters) res->iters[k] = iters;
+      if (res->relres) res->relres[k] = rr[k];
+    }
+  }
+  return st;
+}
+
 int check_common(helm_t h, int nrhs, int dtype) {
   if (!h) { g_err = "null handle"; return HELM_EINVAL; }
   if (nrhs <= 0 || nrhs > 65535) { g_err = "nrhs out of range"; return HELM_EINVAL; }
@@ -755,6 +1053,42 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
   }
   int r = fp64 ? fgmres_run<double>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller)
                : fgmres_run<float>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller);
+  if (r < 0 && r != HELM_ENAN) return r;
+  if (o.flags & HELM_FLAG_HOST_IO) {
+    HCHECK(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, caller));
+    HCHECK(cudaStreamSynchronize(caller));
+  }
+  return r;
+}
+
+int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
+                  fgmres_result* result, helm_stream_t stream) {
+  HTRY(check_common(h, nrhs, HELM_C32));
+  if (!b || !x || !opts) { g_err = "null argument"; return HELM_EINVAL; }
+  fgmres_opts o = *opts;
+  if (nrhs > 16) { g_err = "block size (nrhs) must be at most 16"; return HELM_EINVAL; }
+  if (o.restart < 1 || o.restart > 32 || (o.restart + 1) * nrhs * nrhs > 4608) {
+    g_err = "restart must be in 1..32 with (restart + 1) nrhs^2 <= 4608";
+    return HELM_EINVAL;
+  }
+  if (!(o.tol >= 0) || o.maxit < 0) { g_err = "bad tol/maxit"; return HELM_EINVAL; }
+  if ((precond == HELM_PREC_JU || precond == HELM_PREC_VU) && !net) { g_err = "U-Net preconditioner needs net"; return HELM_EINVAL; }
+  cudaStream_t caller = (cudaStream_t)stream;
+  const size_t bytes = (size_t)nrhs * h->d.nx * h->d.ny * 16;
+  const bool fp64 = (o.flags & HELM_FLAG_FP64) != 0;
+  const void* bd = b;
+  void* xd = x;
+  if (o.flags & HELM_FLAG_HOST_IO) {
+    if (fp64) HTRY(ensure_work<double>(h, nrhs, o.restart));
+    else HTRY(ensure_work<float>(h, nrhs, o.restart));
+    Work& W = fp64 ? h->w64 : h->w32;
+    HCHECK(cudaMemcpyAsync(W.bx, b, bytes, cudaMemcpyHostToDevice, caller));
+    if (!(o.flags & HELM_FLAG_X0_ZERO)) HCHECK(cudaMemcpyAsync(W.xx, x, bytes, cudaMemcpyHostToDevice, caller));
+    bd = W.bx;
+    xd = W.xx;
+  }
+  int r = fp64 ? bfgmres_run<double>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller)
+               : bfgmres_run<float>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller);
   if (r < 0 && r != HELM_ENAN) return r;
   if (o.flags & HELM_FLAG_HOST_IO) {
     HCHECK(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, caller));

@@ -26,7 +26,7 @@ HELM_DESC_MULTIKERNEL_COARSE, HELM_DESC_SINGLE_CTA_COARSE = 1, 2
 ABI_SYMBOLS = [
     "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
     "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
-    "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "helm_time_kernel",
+    "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "bfgmres_solve", "helm_time_kernel",
     "helm_coarse_solve_static",
     # include/unet.h
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
@@ -89,6 +89,7 @@ def load():
         "helm_coarse_solve": (I, [P, P, P, I, I, P]),
         "sl_vcycle": (I, [P, P, P, I, I, I, P]),
         "fgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
+        "bfgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
         "helm_time_kernel": (I, [P, I, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D)]),
         "helm_coarse_solve_static": (I, [I, I, D, D, D, I, D, P, P, P, I, I, P]),
         "unet_cfg_default": (I, [ctypes.POINTER(unet_cfg), I]),
@@ -341,8 +342,9 @@ class Helmholtz:
         return e
 
     def fgmres(self, b, x=None, precond=HELM_PREC_V, net=None, restart=10, tol=1e-7, maxit=5000, flags=0,
-               stream=None):
+               stream=None, block=False):
         """Solve A x = b (complex128 tensors, CUDA or pinned host with HELM_FLAG_HOST_IO).
+        block=True: block FGMRES (one Krylov space for all right-hand sides, <= 16 of them).
         Returns (x, info dict)."""
         import torch
         ny, nx = self.level_shape(0)
@@ -357,9 +359,10 @@ class Helmholtz:
         relres = (ctypes.c_double * n)()
         res = fgmres_result(0, 0, 0.0, 0, iters, relres, 0)
         netp = net.handle if net is not None and hasattr(net, "handle") else net
-        code = self.lib.fgmres_solve(self.h, precond, netp, _ptr(b), _ptr(x), n, ctypes.byref(opts),
-                                     ctypes.byref(res), _stream(stream))
-        _check(code, "fgmres_solve", ok=(HELM_OK, HELM_MAXIT))
+        solve = self.lib.bfgmres_solve if block else self.lib.fgmres_solve
+        code = solve(self.h, precond, netp, _ptr(b), _ptr(x), n, ctypes.byref(opts), ctypes.byref(res),
+                     _stream(stream))
+        _check(code, "bfgmres_solve" if block else "fgmres_solve", ok=(HELM_OK, HELM_MAXIT))
         return x, {"status": code, "iters": list(iters), "relres": list(relres), "iters_max": res.iters_max,
                    "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches}
 

@@ -232,3 +232,43 @@ def test_fgmres_full_size_bench_config(lib):
     assert info["status"] == 0
     for k in range(8):
         assert _oracle_relres(prob, b[k], x[k]) <= 1e-7
+
+
+# ---------------------------------------------------------------- block FGMRES
+def _block_rhs(n, count, seed):
+    pos = synth.source_positions(n, n, count - 1, seed, 4)
+    return np.concatenate([synth.point_sources(n, n, pos, 1.0 / n), crandn(seed + 1, (1, n, n))])
+
+
+def test_block_fgmres_fp64_matches_oracle(lib):
+    """Block FGMRES(10) + M_V with FP64 Krylov vectors: the oracle's block iterations (its
+    QR by Householder, ours by Cholesky QR twice) and FP64 residuals <= tol."""
+    n = 32
+    hz, prob = make(lib, n, n, abc=4)
+    b = _block_rhs(n, 3, 51)
+    x, info = hz.fgmres(dev(b, torch.complex128), tol=1e-9, maxit=500, flags=8, block=True)
+    ref = H.block_fgmres(prob.A, H.precond_v(prob), b, m=10, tol=1e-9, maxit=500)
+    assert info["status"] == 0 and ref.converged
+    assert abs(info["iters_max"] - ref.iters) <= 1
+    x = x.cpu().numpy()
+    for k in range(3):
+        assert _oracle_relres(prob, b[k], x[k]) <= 1e-9
+
+
+@pytest.mark.parametrize("p", [1, 8])
+def test_block_fgmres_fp32(lib, p):
+    """FP32 block FGMRES(10) + M_V on 64^2: converged FP64 residuals <= 1e-7 (oracle
+    recomputed), block iterations within 15 % of the oracle's; one column matches FGMRES."""
+    n = 64
+    hz, prob = make(lib, n, n, abc=16)
+    b = _block_rhs(n, p, 52)
+    x, info = hz.fgmres(dev(b, torch.complex128), tol=1e-7, maxit=2000, block=True)
+    ref = H.block_fgmres(prob.A, H.precond_v(prob), b, m=10, tol=1e-7, maxit=2000)
+    assert info["status"] == 0
+    assert abs(info["iters_max"] - ref.iters) <= max(1, 0.15 * ref.iters)
+    x = x.cpu().numpy()
+    for k in range(p):
+        assert _oracle_relres(prob, b[k], x[k]) <= 1e-7
+    if p == 1:
+        _, i1 = hz.fgmres(dev(b, torch.complex128), tol=1e-7, maxit=2000)
+        assert abs(i1["iters_max"] - info["iters_max"]) <= 1

@@ -390,6 +390,29 @@ def test_fgmres_vu_with_silent_network_equals_sl(lib):
         assert np.linalg.norm(H.residual(prob.A, bb[j], x[j])) / np.linalg.norm(bb[j]) <= 1e-7
 
 
+def test_block_fgmres_vu_with_silent_network_equals_block_sl(lib):
+    """Block FGMRES with M_VU whose output layer is zeroed takes block FGMRES(M_V)'s
+    iterations; every FP64 residual <= 1e-7."""
+    n = 64
+    hz, prob = _helm(lib, n)
+    c, oc = make_cfgs(lib)
+    net = lib.UNet(c, seed=38)
+    P, S = randomise(lib, net, oc, 38)
+    P["up1"][:] = 0.0
+    P["up1.bias"][:] = 0.0
+    net.set_params(PR.flatten_params(oc, P))
+    pos = synth.source_positions(n, n, 4, 39, 16)
+    b = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n)).cuda()
+    _, iv = hz.fgmres(b, precond=lib.HELM_PREC_V, tol=1e-7, maxit=3000, block=True)
+    x, iu = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=3000, block=True)
+    assert iv["status"] == 0 and iu["status"] == 0
+    assert abs(iu["iters_max"] - iv["iters_max"]) <= 2
+    x = x.cpu().numpy()
+    bb = b.cpu().numpy()
+    for j in range(4):
+        assert np.linalg.norm(H.residual(prob.A, bb[j], x[j])) / np.linalg.norm(bb[j]) <= 1e-7
+
+
 def test_solve_cycles_follow_network_buffers(lib):
     """A captured FGMRES cycle references the network's weights and workspace.  A forward
     at another batch size (workspace reallocated) between two solves, and a new network
