@@ -8,6 +8,8 @@
   python -m paper_2203_11025_gb300.profcase mv 256 8       # the same with the plain SL V-cycle (M_V)
   python -m paper_2203_11025_gb300.profcase train 256 16   # one training step (forward, MSE, backward,
                                                            # Adam; profiler range = that step)
+  python -m paper_2203_11025_gb300.profcase sweep 256 16   # block FGMRES + M_V: block iterations and time
+                                                           # for block sizes 1..16 and restarts 5, 10, 20
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -86,6 +88,29 @@ def main(argv):
         step()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+    elif what == "sweep":
+        # the influence of the block size and of the Krylov subspace size (Sec. 4): block
+        # FGMRES(m) with M_V on the first `bs` of b point sources, and independent FGMRES
+        import json
+        k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        pos = synth.source_positions(n, n, b, synth.rhs_seed(0), 16)
+        rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n).astype(np.complex128)).cuda()
+        for m in (5, 10, 20):
+            bs = 1
+            while bs <= b:
+                for block in (True, False):
+                    if (not block and bs != b) or (block and (m + 1) * bs * bs > 4608):
+                        continue
+                    sub = rhs[:bs].contiguous()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, info = hz.fgmres(sub, tol=1e-7, maxit=20000, restart=m, block=block)
+                    e1.record()
+                    e1.synchronize()
+                    print(json.dumps({"restart": m, "rhs": bs, "block": block, "iters": info["iters_max"],
+                                      "ms": round(e0.elapsed_time(e1), 2), "relres_max": info["relres_max"]}))
+                bs *= 2
     else:
         raise SystemExit(f"unknown case {what}")
 
