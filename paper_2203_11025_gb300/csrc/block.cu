@@ -4,10 +4,11 @@
 // [vector][point] complex, `stride` elements apart.
 //
 // Gram: every CTA walks a contiguous range of points in tiles of kTile points staged in
-// shared memory; each thread owns a few (i, k) pairs and sums conj(u_i) w_k over a tile in
-// FP32, then adds the tile's sum into FP64 accumulators (FP64 is a small fraction of the
-// FP32 rate on this GPU); per-CTA partials are reduced by a second kernel in a fixed
-// order.  Combine: one thread per point holds the p outputs in registers and streams the
+// shared memory; thread t owns pair t mod (q p) (and more pairs when q p > 256) and, when
+// q p < 256, one of 256 / (q p) interleaved slices of each tile; it sums conj(u_i) w_k over
+// its part of a tile in FP32 and adds that into FP64 accumulators (FP64 is a small
+// fraction of the FP32 rate on this GPU).  The slices of a pair are added in shared memory
+// in a fixed order, and the per-CTA partials by a second kernel, one warp per pair.  Combine: one thread per point holds the p outputs in registers and streams the
 // q inputs of that point, so in-place use (Out == In, q == p) is safe.
 #include <cuda_runtime.h>
 
@@ -39,6 +40,9 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram_partial(const T2* __rest
   T2* su = reinterpret_cast<T2*>(sm_raw);          // [q][kRow]
   T2* sw = su + (size_t)q * kRow;                   // [p][kRow]
   const int npair = q * p;
+  const int nsl = npair >= kGramThreads ? 1 : kGramThreads / npair;   // tile slices per pair
+  const int sl = npair >= kGramThreads ? 0 : (int)threadIdx.x / npair;
+  const int tpr = npair >= kGramThreads ? (int)threadIdx.x : (int)threadIdx.x - sl * npair;
   const size_t per = (N + gridDim.x - 1) / gridDim.x;
   const size_t n0 = (size_t)blockIdx.x * per, n1 = n0 + per < N ? n0 + per : N;
   double ax[kMaxPairs], ay[kMaxPairs];
@@ -56,39 +60,64 @@ __global__ void __launch_bounds__(kGramThreads) k_bgram_partial(const T2* __rest
       sw[k * kRow + j] = j < len ? W[(size_t)k * wstride + t0 + j] : T2{0, 0};
     }
     __syncthreads();
+    if (sl < nsl) {
 #pragma unroll
-    for (int t = 0; t < kMaxPairs; ++t) {
-      const int pr = threadIdx.x + t * kGramThreads;
-      if (pr >= npair) break;
-      const int i = pr / p, k = pr - i * p;
-      const T2* a = su + (size_t)i * kRow;
-      const T2* b = sw + (size_t)k * kRow;
-      R sx = 0, sy = 0;
-      for (int j = 0; j < kTile; ++j) {   // conj(a) * b
-        sx += a[j].x * b[j].x + a[j].y * b[j].y;
-        sy += a[j].x * b[j].y - a[j].y * b[j].x;
+      for (int t = 0; t < kMaxPairs; ++t) {
+        const int pr = tpr + t * kGramThreads;
+        if (pr >= npair) break;
+        const int i = pr / p, k = pr - i * p;
+        const T2* a = su + (size_t)i * kRow;
+        const T2* b = sw + (size_t)k * kRow;
+        R sx = 0, sy = 0;
+        for (int j = sl; j < kTile; j += nsl) {   // conj(a) * b
+          sx += a[j].x * b[j].x + a[j].y * b[j].y;
+          sy += a[j].x * b[j].y - a[j].y * b[j].x;
+        }
+        ax[t] += (double)sx;
+        ay[t] += (double)sy;
       }
-      ax[t] += (double)sx;
-      ay[t] += (double)sy;
     }
   }
+  if (nsl == 1) {
 #pragma unroll
-  for (int t = 0; t < kMaxPairs; ++t) {
-    const int pr = threadIdx.x + t * kGramThreads;
-    if (pr >= npair) break;
-    part[(size_t)blockIdx.x * npair + pr] = make_double2(ax[t], ay[t]);
+    for (int t = 0; t < kMaxPairs; ++t) {
+      const int pr = tpr + t * kGramThreads;
+      if (pr >= npair) break;
+      part[(size_t)blockIdx.x * npair + pr] = make_double2(ax[t], ay[t]);
+    }
+    return;
+  }
+  // slices of one pair (npair < 256): add them in slice order through shared memory
+  __syncthreads();
+  double2* red = reinterpret_cast<double2*>(sm_raw);   // [nsl][npair], reuses the tiles
+  if (sl < nsl) red[sl * npair + tpr] = make_double2(ax[0], ay[0]);
+  __syncthreads();
+  if ((int)threadIdx.x < npair) {
+    double x = 0.0, y = 0.0;
+    for (int q2 = 0; q2 < nsl; ++q2) {
+      x += red[q2 * npair + threadIdx.x].x;
+      y += red[q2 * npair + threadIdx.x].y;
+    }
+    part[(size_t)blockIdx.x * npair + threadIdx.x] = make_double2(x, y);
   }
 }
 
+// One warp per pair: lanes take every 32nd partial, then a fixed shuffle tree.
 __global__ void k_bgram_reduce(const double2* __restrict__ part, int nparts, int npair, double2* __restrict__ out) {
-  for (int pr = blockIdx.x * blockDim.x + threadIdx.x; pr < npair; pr += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int pr = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pr < npair; pr += (gridDim.x * blockDim.x) >> 5) {
     double x = 0.0, y = 0.0;
-    for (int b = 0; b < nparts; ++b) {
+    for (int b = lane; b < nparts; b += 32) {
       const double2 v = part[(size_t)b * npair + pr];
       x += v.x;
       y += v.y;
     }
-    out[pr] = make_double2(x, y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) out[pr] = make_double2(x, y);
   }
 }
 
@@ -98,8 +127,11 @@ __global__ void __launch_bounds__(256) k_bcombine(const TI* in, size_t istride, 
                                                   size_t N, int accumulate) {
   typedef typename Real<TO>::type R;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  double2* sc = reinterpret_cast<double2*>(sm_raw);   // [q][p]
-  for (int e = threadIdx.x; e < q * p; e += blockDim.x) sc[e] = C[e];
+  TO* sc = reinterpret_cast<TO*>(sm_raw);   // [q][p], in the output precision
+  for (int e = threadIdx.x; e < q * p; e += blockDim.x) {
+    sc[e].x = (R)C[e].x;
+    sc[e].y = (R)C[e].y;
+  }
   __syncthreads();
   for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     R ox[kMaxP], oy[kMaxP];
@@ -111,9 +143,9 @@ __global__ void __launch_bounds__(256) k_bcombine(const TI* in, size_t istride, 
 #pragma unroll
       for (int k = 0; k < kMaxP; ++k) {
         if (k >= p) break;
-        const double2 c = sc[i * p + k];
-        ox[k] += vx * (R)c.x - vy * (R)c.y;
-        oy[k] += vx * (R)c.y + vy * (R)c.x;
+        const TO c = sc[i * p + k];
+        ox[k] += vx * c.x - vy * c.y;
+        oy[k] += vx * c.y + vy * c.x;
       }
     }
 #pragma unroll
@@ -136,12 +168,13 @@ int block_gram(const T2* U, size_t ustride, int q, const T2* W, size_t wstride, 
                double2* out, int nsm, cudaStream_t s) {
   if (q < 1 || p < 1 || p > kMaxP || q * p > kMaxPairs * kGramThreads) return -1;
   const int nparts = block_gram_parts(nsm);
-  const size_t smem = (size_t)(q + p) * kRow * sizeof(T2);
+  // the tiles, and the slice sums of the pairs (<= 256 double2) that reuse them
+  const size_t smem = std::max((size_t)(q + p) * kRow * sizeof(T2), (size_t)kGramThreads * sizeof(double2));
   if (smem > 48 * 1024 &&
       cudaFuncSetAttribute(k_bgram_partial<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -1;
   k_bgram_partial<T2><<<nparts, kGramThreads, smem, s>>>(U, ustride, q, W, wstride, p, N, part);
-  k_bgram_reduce<<<(q * p + 255) / 256, 256, 0, s>>>(part, nparts, q * p, out);
+  k_bgram_reduce<<<(q * p + 7) / 8, 256, 0, s>>>(part, nparts, q * p, out);
   return 0;
 }
 template int block_gram<float2>(const float2*, size_t, int, const float2*, size_t, int, size_t, double2*, double2*, int,

@@ -592,8 +592,13 @@ struct BlockLS {
 struct BlockBufs {
   cudaStream_t s = nullptr;
   std::vector<void*> ptrs;
+  void* pinned = nullptr;
   ~BlockBufs() {
     for (void* q : ptrs) cudaFreeAsync(q, s);
+    if (pinned) {
+      cudaStreamSynchronize(s);
+      cudaFreeHost(pinned);
+    }
   }
   template <typename P>
   cudaError_t get(P** out, size_t bytes) {
@@ -632,6 +637,14 @@ int bfgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* 
   const Op<double> A64 = op_on<double>(c, 0, 0.0);
   const Op<T> AT = op_on<T>(c, 0, 0.0);
   std::vector<double2> hbuf((size_t)qmax * p);
+  // coefficient uploads go through a ring of pinned host slots: asynchronous copies, and a
+  // slot is rewritten only after a later Gram read has synchronised the stream (at most two
+  // uploads happen between two Gram reads)
+  constexpr int kRing = 3;
+  const size_t slot = (size_t)qmax * p;
+  HCHECK(cudaMallocHost(&bb.pinned, kRing * slot * sizeof(double2)));
+  double2* ring = (double2*)bb.pinned;
+  int ring_i = 0;
   // Gram matrix U^H W (q x p) to the host
   auto gram_host = [&](auto* U, int q, auto* Wv, std::vector<cd>& G) -> int {
     if (block_gram(U, N, q, Wv, N, p, N, part, gram, c->nsm, s) < 0) { g_err = "block Gram: sizes"; return HELM_EINVAL; }
@@ -642,11 +655,12 @@ int bfgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* 
     for (size_t i = 0; i < G.size(); ++i) G[i] = cd(hbuf[i].x, hbuf[i].y);
     return HELM_OK;
   };
-  // coefficients (q x p, host) to the device
+  // coefficients (q x p, host) to the device (stream-ordered: the previous combine has read
+  // dC before this copy lands)
   auto upload = [&](const std::vector<cd>& C, int q) -> int {
-    for (size_t i = 0; i < (size_t)q * p; ++i) hbuf[i] = make_double2(C[i].real(), C[i].imag());
-    HCHECK(cudaMemcpyAsync(dC, hbuf.data(), (size_t)q * p * sizeof(double2), cudaMemcpyHostToDevice, s));
-    HCHECK(cudaStreamSynchronize(s));   // hbuf is reused by the next call
+    double2* h = ring + (size_t)(ring_i++ % kRing) * slot;
+    for (size_t i = 0; i < (size_t)q * p; ++i) h[i] = make_double2(C[i].real(), C[i].imag());
+    HCHECK(cudaMemcpyAsync(dC, h, (size_t)q * p * sizeof(double2), cudaMemcpyHostToDevice, s));
     return HELM_OK;
   };
   // blk (p vectors, in place) <- blk R^-1 twice; returns R = R2 R1 (row-major p x p)

@@ -10,6 +10,8 @@
                                                            # Adam; profiler range = that step)
   python -m paper_2203_11025_gb300.profcase sweep 256 16   # block FGMRES + M_V: block iterations and time
                                                            # for block sizes 1..16 and restarts 5, 10, 20
+  python -m paper_2203_11025_gb300.profcase block 256 8    # one block FGMRES(10) cycle with M_V
+  python -m paper_2203_11025_gb300.profcase resloss 256 16 # the residual loss of a batch of 16
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -88,6 +90,21 @@ def main(argv):
         step()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+    elif what == "block":
+        k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        pos = synth.source_positions(n, n, b, synth.rhs_seed(0), 16)
+        rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n).astype(np.complex128)).cuda()
+        hz.fgmres(rhs, tol=1e-7, maxit=10, block=True)
+    elif what == "resloss":
+        k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        rng = np.random.default_rng(0)
+        y = torch.from_numpy(rng.standard_normal((b, n, n, 2)).astype(np.float32)).cuda()
+        x = torch.from_numpy(rng.standard_normal((b, n, n, 4)).astype(np.float32)).cuda()
+        for _ in range(2):
+            hz.residual_loss(y, x)
+        torch.cuda.synchronize()
     elif what == "sweep":
         # the influence of the block size and of the Krylov subspace size (Sec. 4): block
         # FGMRES(m) with M_V on the first `bs` of b point sources, and independent FGMRES
