@@ -70,6 +70,18 @@ def max_batch(want: int) -> int:
     return bs
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the job's wall time when
+    every rank solves its own problem: replicas, no data exchange); identity on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def build_problem(rank: int):
     import numpy as np
     from paper_2203_11025_gb300 import synth
@@ -289,10 +301,7 @@ def run_ours(args):
     ck = clocks.stop()
     ms_v, it_v, _ = timed("M_V", args.steps)
     ms_ju, it_ju, _ = timed("M_JU", args.steps)
-    if world > 1:
-        t = torch.tensor([ms, ms_v, ms_ju], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_v, ms_ju = (float(v) for v in t.tolist())
+    ms, ms_v, ms_ju = max_over_ranks([ms, ms_v, ms_ju], dev)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     bh = torch.from_numpy(b).pin_memory()
