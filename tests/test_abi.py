@@ -48,3 +48,25 @@ def test_binding_signatures_load(built_lib):
     L = lib.load()
     for name in lib.ABI_SYMBOLS:
         assert getattr(L, name).argtypes is not None or name == "helm_last_error"
+
+
+def test_null_arguments_fail_with_einval(built_lib):
+    """Entry points reject null handles and pointers with HELM_EINVAL and a message before
+    touching the GPU (so this runs without one)."""
+    from paper_2203_11025_gb300 import lib
+    L = lib.load()
+    opts = lib.fgmres_opts(10, 1e-7, 100, 0)
+    res = lib.fgmres_result(0, 0, 0.0, 0, None, None, 0)
+    calls = {
+        "fgmres_solve": lambda: L.fgmres_solve(None, lib.HELM_PREC_V, None, None, None, 1, ctypes.byref(opts),
+                                               ctypes.byref(res), None),
+        "bfgmres_solve": lambda: L.bfgmres_solve(None, lib.HELM_PREC_V, None, None, None, 1, ctypes.byref(opts),
+                                                 ctypes.byref(res), None),
+        "unet_residual_loss": lambda: L.unet_residual_loss(None, None, None, 1, None, None, None),
+        "unet_mse": lambda: L.unet_mse(None, None, 0, 1, None, None, None),
+        "unet_forward": lambda: L.unet_forward(None, None, None, 1, 16, 16, 0, None),
+        "unet_precond": lambda: L.unet_precond(None, None, lib.HELM_PREC_VU, None, None, 1, 0, None),
+    }
+    for name, call in calls.items():
+        assert call() == lib.HELM_EINVAL, name
+        assert L.helm_last_error(), name
