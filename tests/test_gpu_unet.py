@@ -297,6 +297,27 @@ def test_encoder_solver_preconditioner(lib):
     assert nrel(e, ref) < 2e-2
 
 
+def test_full_size_bench_batch_forward_and_preconditioner(lib):
+    """The benchmark's launch configuration, 256^2 x 8 with the default network: the
+    inference forward (space-to-depth input layer, column-reuse, split-K and sub-pixel
+    kernels) and the M_VU application, each against the FP64 oracle."""
+    n, B = 256, 8
+    c = lib.unet_cfg_default(lib.UNET_STANDALONE)
+    oc = U.UNetConfig()
+    net = lib.UNet(c, seed=41)
+    P, S = randomise(lib, net, oc, 41)
+    x = np.random.default_rng(42).standard_normal((B, n, n, 4))
+    out = net.forward(cuda(x)).cpu().numpy()
+    assert not net.status()
+    ref, _, _, _ = U.forward(oc, P, S, x, train=False)
+    assert nrel(out, ref) < 3e-2
+    hz, prob = _helm(lib, n)
+    r = crandn(43, (B, n, n))
+    e = hz.unet_precond(net, torch.from_numpy(r).cuda(), kind=lib.HELM_PREC_VU).cpu().numpy()
+    ref_e = PR.precond_vu(prob, oc, P, S, r)
+    assert nrel(e, ref_e) < 2e-2
+
+
 def test_encoder_solver_fgmres_512_32rhs(lib):
     """512^2, 32 right-hand sides (16 point sources, 16 complex Gaussian) through the
     default-size encoder-solver pair (Sec. 3.3) as the M_VU network, its output layer
