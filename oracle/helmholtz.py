@@ -7,7 +7,9 @@ does, and it shares no code with the CUDA library.
 
 All arithmetic is complex128 / float64.  Arrays are (..., ny, nx), row-major,
 unknown (iy, ix) at node index (iy, ix); values outside the grid are zero
-(zero padding of size 1 = Dirichlet, Sec. 2.4).
+(zero padding of size 1 = Dirichlet, Sec. 2.4); Level.bc = "reflect" or "replicate"
+pads the operator's stencil by reflection or replication instead (Neumann, Sec. 2.4),
+while the transfer kernels of Eq. 2.9 keep their zero padding.
 
 Readings of points the paper leaves open (each also listed in the design doc):
   * A = L - w^2 k^2 (1 - g i) with L the 5-point negative Laplacian (Eq. 2.1,
@@ -60,9 +62,10 @@ class Level:
     kappa2: np.ndarray          # (ny, nx) float64
     gamma: np.ndarray           # (ny, nx) float64
     beta: float = 0.0           # shift of the operator (0 -> A, 0.5 -> M)
+    bc: str = "dirichlet"       # stencil padding: "dirichlet" (zero), "reflect" or "replicate"
 
     def with_shift(self, beta: float) -> "Level":
-        return Level(self.ny, self.nx, self.h, self.omega, self.kappa2, self.gamma, beta)
+        return Level(self.ny, self.nx, self.h, self.omega, self.kappa2, self.gamma, beta, self.bc)
 
 
 @dataclass
@@ -79,6 +82,7 @@ class Problem:
     nu2: int = 1
     jacobi_w: float = 0.8
     coarse_its: int = 10
+    bc: str = "dirichlet"
     hierarchy: list = field(default_factory=list)
 
     def __post_init__(self):
@@ -90,7 +94,7 @@ class Problem:
                 k2 = coarsen_kappa2(k2)
             lny, lnx = ny >> l, nx >> l
             g = abc_gamma(lny, lnx, self.abc_width >> l, self.gamma_max)
-            self.hierarchy.append(Level(lny, lnx, self.h * (1 << l), self.omega, k2, g, self.beta))
+            self.hierarchy.append(Level(lny, lnx, self.h * (1 << l), self.omega, k2, g, self.beta, self.bc))
 
     @property
     def A(self) -> Level:
@@ -106,19 +110,51 @@ class Problem:
 # ----------------------------------------------------------------------------
 # Operators (Eq. 2.2, 2.4), Jacobi
 # ----------------------------------------------------------------------------
-def diagonal(lv: Level) -> np.ndarray:
-    """Diagonal of the operator: 4/h^2 - w^2 k^2 (1 - (g + beta) i)."""
+def _center(lv: Level) -> np.ndarray:
+    """Centre weight of the stencil: 4/h^2 - w^2 k^2 (1 - (g + beta) i)."""
     return 4.0 / lv.h ** 2 - lv.omega ** 2 * lv.kappa2 * (1.0 - (lv.gamma + lv.beta) * 1j)
 
 
+def _ghost(i: int, n: int, bc: str):
+    """Node whose value a neighbour index i outside 0..n-1 takes (None: zero), for the
+    padding of the stencil's convolution (Sec. 2.4: zero padding = Dirichlet; reflection
+    or replication padding = Neumann)."""
+    if 0 <= i < n:
+        return i
+    if bc == "reflect":
+        return 1 if i < 0 else n - 2
+    if bc == "replicate":
+        return 0 if i < 0 else n - 1
+    return None
+
+
+def diagonal(lv: Level) -> np.ndarray:
+    """Diagonal of the operator: the centre weight, less 1/h^2 for every neighbour that
+    replication padding maps back onto the node itself."""
+    d = _center(lv)
+    if lv.bc == "replicate":
+        iy = np.arange(lv.ny)[:, None]
+        ix = np.arange(lv.nx)[None, :]
+        edges = (iy == 0).astype(float) + (iy == lv.ny - 1) + (ix == 0) + (ix == lv.nx - 1)
+        d = d - edges / lv.h ** 2
+    return d
+
+
 def apply_op(lv: Level, u: np.ndarray) -> np.ndarray:
-    """y = K u for the 5-point stencil of Eq. 2.2 (with shift beta), zero outside."""
-    up = np.zeros_like(u)
-    up[..., 1:, :] += u[..., :-1, :]
-    up[..., :-1, :] += u[..., 1:, :]
-    up[..., :, 1:] += u[..., :, :-1]
-    up[..., :, :-1] += u[..., :, 1:]
-    return diagonal(lv) * u - up / lv.h ** 2
+    """y = K u for the 5-point stencil of Eq. 2.2 (with shift beta); neighbours outside
+    the grid are zero (Dirichlet) or taken by reflection / replication (Neumann)."""
+    if lv.bc == "dirichlet":
+        up = np.zeros_like(u)
+        up[..., 1:, :] += u[..., :-1, :]
+        up[..., :-1, :] += u[..., 1:, :]
+        up[..., :, 1:] += u[..., :, :-1]
+        up[..., :, :-1] += u[..., :, 1:]
+    else:
+        mode = {"reflect": "reflect", "replicate": "edge"}[lv.bc]
+        pw = [(0, 0)] * (u.ndim - 2) + [(1, 1), (1, 1)]
+        p = np.pad(u, pw, mode=mode)
+        up = p[..., :-2, 1:-1] + p[..., 2:, 1:-1] + p[..., 1:-1, :-2] + p[..., 1:-1, 2:]
+    return _center(lv) * u - up / lv.h ** 2
 
 
 def residual(lv: Level, f: np.ndarray, u: np.ndarray) -> np.ndarray:
@@ -135,16 +171,20 @@ def assemble_dense(lv: Level) -> np.ndarray:
     ny, nx = lv.ny, lv.nx
     n = ny * nx
     K = np.zeros((n, n), dtype=np.complex128)
-    d = diagonal(lv)
+    c = _center(lv)
     off = -1.0 / lv.h ** 2
     for iy in range(ny):
         for ix in range(nx):
             p = iy * nx + ix
-            K[p, p] = d[iy, ix]
+            K[p, p] += c[iy, ix]
             for dy, dx in ((-1, 0), (1, 0), (0, -1), (0, 1)):
                 jy, jx = iy + dy, ix + dx
                 if 0 <= jy < ny and 0 <= jx < nx:
-                    K[p, jy * nx + jx] = off
+                    K[p, jy * nx + jx] += off
+                    continue
+                gy, gx = _ghost(jy, ny, lv.bc), _ghost(jx, nx, lv.bc)
+                if gy is not None and gx is not None:
+                    K[p, gy * nx + gx] += off
     return K
 
 

@@ -410,3 +410,90 @@ def test_block_gmres_minimises_over_explicit_block_krylov_space():
         y, *_ = np.linalg.lstsq(K @ Q, R[:, c], rcond=None)
         ref = np.linalg.norm(R[:, c] - K @ Q @ y) / np.linalg.norm(R[:, c])
         assert abs(res.estimates[j - 1][c] - ref) <= 1e-9 * max(ref, 1e-3)
+
+
+# ---------------------------------------------------------------- Neumann boundaries
+# Sec. 2.4: the stencil's convolution with reflection or replication padding in place
+# of zero padding gives Neumann boundaries.  The closed forms below are the discrete
+# cosine eigenbases of the two second-difference operators (DCT-I for reflection about
+# the boundary node, DCT-II for replication across a half-cell boundary).
+def _neumann_modes(n, bc):
+    p = np.arange(n)
+    if bc == "reflect":
+        th = np.arange(n) * np.pi / (n - 1)
+        return [(j, np.cos(th[j] * p), 4 * np.sin(th[j] / 2) ** 2) for j in range(n)]
+    th = np.arange(n) * np.pi / n
+    return [(j, np.cos(th[j] * (p + 0.5)), 4 * np.sin(th[j] / 2) ** 2) for j in range(n)]
+
+
+@pytest.mark.parametrize("bc", ["reflect", "replicate"])
+@pytest.mark.parametrize("ny,nx", [(8, 8), (6, 11)])
+def test_neumann_laplacian_eigenpairs(bc, ny, nx):
+    """Constant medium, no attenuation: tensor products of the cosine modes are
+    eigenvectors with eigenvalue (mu_j + mu_k)/h^2 - w^2 k^2 (the constant mode, j = k = 0,
+    gives L 1 = 0)."""
+    h, omega, k2 = 1.0 / nx, 9.0, 0.6
+    lv = H.Level(ny, nx, h, omega, np.full((ny, nx), k2), np.zeros((ny, nx)), 0.0, bc)
+    my, mx = _neumann_modes(ny, bc), _neumann_modes(nx, bc)
+    for (j, vy, ly) in my:
+        for (k, vx, lx) in mx[:: max(1, nx // 4)]:
+            v = np.outer(vy, vx) + 0j
+            lam = (ly + lx) / h ** 2 - omega ** 2 * k2
+            assert np.allclose(H.apply_op(lv, v), lam * v, rtol=1e-12, atol=1e-9 * (abs(lam) + 1 / h ** 2))
+
+
+@pytest.mark.parametrize("bc", ["reflect", "replicate"])
+def test_neumann_constant_is_in_laplacian_kernel(bc):
+    lv = H.Level(7, 9, 0.1, 0.0, np.ones((7, 9)), np.zeros((7, 9)), 0.0, bc)
+    assert np.abs(H.apply_op(lv, np.ones((7, 9), complex))).max() < 1e-10
+
+
+@pytest.mark.parametrize("bc", ["reflect", "replicate"])
+def test_neumann_apply_diagonal_and_assembly_agree(bc):
+    """Padded-array formulation == node-by-node ghost mapping; the Jacobi diagonal is
+    the assembled matrix's diagonal (replication folds one neighbour per boundary side
+    onto the node itself)."""
+    lv = _level(7, 10, seed=3)
+    lv = H.Level(lv.ny, lv.nx, lv.h, lv.omega, lv.kappa2, lv.gamma, lv.beta, bc)
+    K = H.assemble_dense(lv)
+    u = _crandn(np.random.default_rng(4), (2, 7, 10))
+    for t in range(2):
+        assert np.allclose(H.apply_op(lv, u)[t].ravel(), K @ u[t].ravel(), rtol=1e-14, atol=1e-12)
+    assert np.allclose(np.diag(K).reshape(7, 10), H.diagonal(lv) * np.ones((7, 10)), rtol=1e-14)
+    if bc == "replicate":
+        # corner: two sides fold back -> 2/h^2 off the centre weight
+        assert np.isclose((4 / lv.h ** 2 - K[0, 0].real) * lv.h ** 2,
+                          2 + lv.omega ** 2 * lv.kappa2[0, 0] * lv.h ** 2, rtol=1e-12)
+
+
+def test_neumann_reflect_symmetric_under_trapezoid_weights():
+    """Reflection doubles the inward coupling of boundary rows; the operator is complex
+    symmetric after scaling rows by the trapezoidal weights (1/2 per boundary side),
+    replication's operator is complex symmetric as it stands."""
+    lv = _level(6, 9, seed=5)
+    refl = H.Level(lv.ny, lv.nx, lv.h, lv.omega, lv.kappa2, lv.gamma, lv.beta, "reflect")
+    rep = H.Level(lv.ny, lv.nx, lv.h, lv.omega, lv.kappa2, lv.gamma, lv.beta, "replicate")
+    wy = np.ones(6); wy[[0, -1]] = 0.5
+    wx = np.ones(9); wx[[0, -1]] = 0.5
+    W = np.diag(np.outer(wy, wx).ravel())
+    Kr = W @ H.assemble_dense(refl)
+    assert np.allclose(Kr, Kr.T, atol=1e-10)
+    assert not np.allclose(H.assemble_dense(refl), H.assemble_dense(refl).T)
+    Kp = H.assemble_dense(rep)
+    assert np.allclose(Kp, Kp.T, atol=1e-10)
+
+
+@pytest.mark.parametrize("bc", ["reflect", "replicate"])
+def test_neumann_fgmres_vcycle_matches_dense_direct(bc):
+    """The whole hierarchy carries the boundary mode; FGMRES(10) + M_V reaches the
+    dense LU solution of the Neumann problem."""
+    k2 = synth.grf_kappa2(16, 16, 14, sigma=2.0).astype(np.float64)
+    prob = H.Problem(k2, omega=synth.omega_for(16), h=1.0 / 16, abc_width=4, levels=3, bc=bc)
+    assert all(lv.bc == bc for lv in prob.hierarchy)
+    b = _crandn(np.random.default_rng(16), (16, 16))
+    res = H.fgmres(prob.A, H.precond_v(prob), b, tol=1e-12, maxit=400)
+    x_ref = H.lu_solve(H.assemble_dense(prob.A), b.ravel()).reshape(16, 16)
+    assert res.converged
+    assert np.linalg.norm(res.x - x_ref) / np.linalg.norm(x_ref) < 1e-9
+    dir_prob = H.Problem(k2, omega=synth.omega_for(16), h=1.0 / 16, abc_width=4, levels=3)
+    assert not np.allclose(H.assemble_dense(dir_prob.A), H.assemble_dense(prob.A))
