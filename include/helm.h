@@ -63,7 +63,15 @@ typedef struct {
   double jacobi_w;         /* Jacobi damping (Sec. 4: 0.8)                     */
   int coarse_its;          /* GMRES steps on the coarsest grid (Sec. 4: 10)   */
   int flags;               /* HELM_DESC_* implementation switches (0 = default) */
+  int bc;                  /* HELM_BC_* boundary condition (0 = Dirichlet)     */
 } helm_desc;
+/* Boundary conditions (Sec. 2.4: the 5-point stencil applied as a convolution,
+ * whose padding sets the boundary).  DIRICHLET pads with zeros; REFLECT mirrors
+ * about the boundary node (ghost u_-1 = u_1) and REPLICATE copies it (ghost
+ * u_-1 = u_0), both Neumann conditions.  The mode holds on every level of the
+ * hierarchy; the transfer operators of Eq. 2.9 keep zero padding.  REFLECT
+ * needs every level at least 2 nodes wide in each direction. */
+enum { HELM_BC_DIRICHLET = 0, HELM_BC_REFLECT = 1, HELM_BC_REPLICATE = 2 };
 /* Coarsest-GMRES implementation switches (default: a thread-block cluster per
  * right-hand side with the Krylov basis in distributed shared memory when the
  * grid fits, else one CTA per right-hand side when the grid fits in one CTA's

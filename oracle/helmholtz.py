@@ -157,6 +157,30 @@ def apply_op(lv: Level, u: np.ndarray) -> np.ndarray:
     return _center(lv) * u - up / lv.h ** 2
 
 
+def apply_op_T(lv: Level, u: np.ndarray) -> np.ndarray:
+    """y = K^T u.  K = C - (1/h^2) S P, with P the padding (grid -> grid plus one ghost
+    layer), S the sum of the four neighbours read from the padded array and C the centre
+    weight, so K^T = C - (1/h^2) P^T S^T: scatter every value to its four neighbours on
+    the padded array, then fold each ghost back onto the node it copies.  Zero padding
+    and replication give a symmetric K; reflection does not."""
+    if lv.bc == "dirichlet":
+        return apply_op(lv, u)
+    ny, nx = u.shape[-2:]
+    q = np.zeros(u.shape[:-2] + (ny + 2, nx + 2), dtype=np.result_type(u, np.complex128))
+    q[..., 0:ny, 1:-1] += u        # value at node (i, j) -> padded (i - 1, j)
+    q[..., 2:, 1:-1] += u          #                      -> padded (i + 1, j)
+    q[..., 1:-1, 0:nx] += u
+    q[..., 1:-1, 2:] += u
+    src_lo, src_hi = (1, -2) if lv.bc == "reflect" else (0, -1)   # node a ghost copies
+    t = q[..., :, 1:-1].copy()     # fold the ghost columns (padded 0 and nx + 1)
+    t[..., :, src_lo] += q[..., :, 0]
+    t[..., :, src_hi] += q[..., :, -1]
+    s = t[..., 1:-1, :].copy()     # fold the ghost rows
+    s[..., src_lo, :] += t[..., 0, :]
+    s[..., src_hi, :] += t[..., -1, :]
+    return _center(lv) * u - s / lv.h ** 2
+
+
 def residual(lv: Level, f: np.ndarray, u: np.ndarray) -> np.ndarray:
     return f - apply_op(lv, u)
 

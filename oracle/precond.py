@@ -67,9 +67,10 @@ def residual_loss(prob: H.Problem, y, x):
     (e / s), x: network inputs (B, ny, nx, 4) whose channels 0, 1 are h^2 r / s, so that
         rho = h^2 A (y0 + i y1) - (x0 + i x1) = h^2 (A e_net - r) / s.
     Loss: sum over the grid of |rho|^2, mean over the batch (the convention of Eq. 3.7
-    here).  Gradient with respect to (Re y, Im y): (2 / B) conj(h^2 A conj(rho)), since
-    the gradient of |K y - x|^2 with respect to conj(y) is K^H (K y - x) and A is complex
-    symmetric (A^H = conj(A)).  Returns (loss, gradient (B, ny, nx, 2))."""
+    here).  Gradient with respect to (Re y, Im y): (2 / B) conj(h^2 A^T conj(rho)), since
+    the gradient of |K y - x|^2 with respect to conj(y) is K^H (K y - x) and
+    K^H = conj(K^T) (A^T = A but for reflection boundaries).  Returns (loss, gradient
+    (B, ny, nx, 2))."""
     A = prob.A
     h2 = A.h ** 2
     yc = y[..., 0] + 1j * y[..., 1]
@@ -77,7 +78,7 @@ def residual_loss(prob: H.Problem, y, x):
     rho = h2 * H.apply_op(A, yc) - xc
     B = y.shape[0]
     loss = float(np.sum(np.abs(rho) ** 2) / B)
-    g = (2.0 / B) * np.conj(h2 * H.apply_op(A, np.conj(rho)))
+    g = (2.0 / B) * np.conj(h2 * H.apply_op_T(A, np.conj(rho)))
     return loss, np.stack([g.real, g.imag], axis=-1)
 
 

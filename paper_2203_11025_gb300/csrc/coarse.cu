@@ -107,11 +107,11 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
     for (int p = tid; p < N; p += CT) {
       const int y = p / nx, x = p - y * nx;
       T2 c = scaled_by_dinv(op, vj, x, y);
-      T2 s = czero<T2>();
-      if (x > 0) s = cadd(s, scaled_by_dinv(op, vj, x - 1, y));
-      if (x < nx - 1) s = cadd(s, scaled_by_dinv(op, vj, x + 1, y));
-      if (y > 0) s = cadd(s, scaled_by_dinv(op, vj, x, y - 1));
-      if (y < ny - 1) s = cadd(s, scaled_by_dinv(op, vj, x, y + 1));
+      const T2 l = x > 0 ? scaled_by_dinv(op, vj, x - 1, y) : czero<T2>();
+      const T2 rt = x < nx - 1 ? scaled_by_dinv(op, vj, x + 1, y) : czero<T2>();
+      const T2 dn = y > 0 ? scaled_by_dinv(op, vj, x, y - 1) : czero<T2>();
+      const T2 up = y < ny - 1 ? scaled_by_dinv(op, vj, x, y + 1) : czero<T2>();
+      T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
       T2 r = cmul(diag_at(op, x, y), c);
       r.x -= s.x * op.inv_h2;
       r.y -= s.y * op.inv_h2;
@@ -281,7 +281,7 @@ extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, 
     basis = helm::g_static_ptr[dev];
   }
   helm::Op<float> op;
-  op.nx = nx; op.ny = ny; op.abc_w = abc_width;
+  op.nx = nx; op.ny = ny; op.abc_w = abc_width; op.bc = helm::kBcDirichlet;
   op.inv_h2 = (float)(1.0 / (h * h));
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gamma_max;

@@ -206,13 +206,11 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
       const int lp = tid + q * KT;
       if (lp >= NP) continue;
       const int ly = lp / nx, x = lp - ly * nx;
-      T2 s = czero<T2>();
-      if (x > 0) s = cadd(s, U[lp - 1]);
-      if (x < nx - 1) s = cadd(s, U[lp + 1]);
-      if (ly > 0) s = cadd(s, U[lp - nx]);
-      else if (Uup) s = cadd(s, Uup[(rows - 1) * nx + x]);
-      if (ly < rows - 1) s = cadd(s, U[lp + nx]);
-      else if (Udn) s = cadd(s, Udn[x]);
+      const T2 l = x > 0 ? U[lp - 1] : czero<T2>();
+      const T2 rt = x < nx - 1 ? U[lp + 1] : czero<T2>();
+      const T2 dn = ly > 0 ? U[lp - nx] : (Uup ? Uup[(rows - 1) * nx + x] : czero<T2>());
+      const T2 up = ly < rows - 1 ? U[lp + nx] : (Udn ? Udn[x] : czero<T2>());
+      const T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, rank * rows + ly, l, rt, dn, up));
       T2 r = vj[lp];
       r.x -= s.x * ih2;
       r.y -= s.y * ih2;

@@ -16,16 +16,23 @@ template <> struct vec2<double> { typedef double2 type; };
 // K = (1/h^2)(5-point negative Laplacian) - w^2 k^2 (1 - (g + beta) i),
 // g the quadratic absorbing-layer profile of width abc_w on this level
 // (Eq. 2.1, 2.2; Eq. 2.4 with alpha = 1 for the shifted operator).
+// Boundary (Sec. 2.4, the stencil as a convolution and its padding): bc 0 pads
+// with zeros (Dirichlet); bc 1 reflects about the boundary node (ghost u_-1 =
+// u_1), so the inward neighbour of a boundary node couples twice; bc 2
+// replicates the boundary node (ghost u_-1 = u_0), which folds that coupling
+// into the diagonal: -1/h^2 per boundary side.  Both are Neumann conditions.
 // ---------------------------------------------------------------------------
+enum { kBcDirichlet = 0, kBcReflect = 1, kBcReplicate = 2 };
+
 template <typename T> struct Op {
-  int nx, ny, abc_w;
+  int nx, ny, abc_w, bc;
   T inv_h2, omega2, gmax, beta;
   const T* k2;  // kappa^2 on this level, [ny][nx]
 };
 
 // Per-level storage owned by the handle.
 struct Level {
-  int nx, ny, abc_w;
+  int nx, ny, abc_w, bc;
   double h;
   float* k2f;   // kappa^2 (float32)
   double* k2d;  // kappa^2 (float64)
@@ -34,7 +41,7 @@ struct Level {
 template <typename T>
 inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
   Op<T> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
   op.inv_h2 = (T)(1.0 / (L.h * L.h));
   op.omega2 = (T)(omega * omega);
   op.gmax = (T)gmax;
@@ -44,7 +51,7 @@ inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
 }
 template <> inline Op<float> make_op<float>(const Level& L, double omega, double gmax, double beta) {
   Op<float> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
   op.inv_h2 = (float)(1.0 / (L.h * L.h));
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gmax; op.beta = (float)beta; op.k2 = L.k2f;
@@ -52,7 +59,7 @@ template <> inline Op<float> make_op<float>(const Level& L, double omega, double
 }
 template <> inline Op<double> make_op<double>(const Level& L, double omega, double gmax, double beta) {
   Op<double> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
   op.inv_h2 = 1.0 / (L.h * L.h);
   op.omega2 = omega * omega;
   op.gmax = gmax; op.beta = beta; op.k2 = L.k2d;
@@ -81,14 +88,31 @@ template <typename T> __device__ __forceinline__ T gamma_at(const Op<T>& op, int
   return t * t * op.gmax;
 }
 
-// Diagonal of K at (x, y): 4/h^2 - w^2 k^2 + i w^2 k^2 (g + beta).
+// Diagonal of K at (x, y): 4/h^2 - w^2 k^2 + i w^2 k^2 (g + beta), less 1/h^2
+// per boundary side under replication padding.
 template <typename T>
 __device__ __forceinline__ typename vec2<T>::type diag_at(const Op<T>& op, int x, int y) {
   T wk = op.omega2 * op.k2[(size_t)y * op.nx + x];
   typename vec2<T>::type d;
-  d.x = T(4) * op.inv_h2 - wk;
+  T c = T(4);
+  if (op.bc == kBcReplicate)
+    c -= T((x == 0) + (x == op.nx - 1) + (y == 0) + (y == op.ny - 1));
+  d.x = c * op.inv_h2 - wk;
   d.y = wk * (gamma_at(op, x, y) + op.beta);
   return d;
+}
+
+// The part of the neighbour sum that reflection padding adds at a boundary node:
+// the inward neighbour once more per boundary side.  l, r, d, u are the values at
+// (x-1, y), (x+1, y), (x, y-1), (x, y+1) (zero outside the grid); grids are at
+// least 2 nodes wide under reflection, so the inward neighbour always exists.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 reflect_extra(const Op<T>& op, int x, int y, T2 l, T2 r, T2 d, T2 u) {
+  T2 e = czero<T2>();
+  if (op.bc != kBcReflect) return e;
+  if (x == 0) e = cadd(e, r); else if (x == op.nx - 1) e = cadd(e, l);
+  if (y == 0) e = cadd(e, u); else if (y == op.ny - 1) e = cadd(e, d);
+  return e;
 }
 #endif
 

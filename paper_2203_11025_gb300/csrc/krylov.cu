@@ -176,20 +176,21 @@ __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, co
   T ax = 0, ay = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
-    T2 c, s = czero<T2>();
+    T2 c, l = czero<T2>(), rt = czero<T2>(), dn = czero<T2>(), up = czero<T2>();
     if (diag_precond) {
       c = cmul(zr[p], cinv(diag_at(op, x, y)));
-      if (x > 0) s = cadd(s, cmul(zr[p - 1], cinv(diag_at(op, x - 1, y))));
-      if (x < nx - 1) s = cadd(s, cmul(zr[p + 1], cinv(diag_at(op, x + 1, y))));
-      if (y > 0) s = cadd(s, cmul(zr[p - nx], cinv(diag_at(op, x, y - 1))));
-      if (y < ny - 1) s = cadd(s, cmul(zr[p + nx], cinv(diag_at(op, x, y + 1))));
+      if (x > 0) l = cmul(zr[p - 1], cinv(diag_at(op, x - 1, y)));
+      if (x < nx - 1) rt = cmul(zr[p + 1], cinv(diag_at(op, x + 1, y)));
+      if (y > 0) dn = cmul(zr[p - nx], cinv(diag_at(op, x, y - 1)));
+      if (y < ny - 1) up = cmul(zr[p + nx], cinv(diag_at(op, x, y + 1)));
     } else {
       c = zr[p];
-      if (x > 0) s = cadd(s, zr[p - 1]);
-      if (x < nx - 1) s = cadd(s, zr[p + 1]);
-      if (y > 0) s = cadd(s, zr[p - nx]);
-      if (y < ny - 1) s = cadd(s, zr[p + nx]);
+      if (x > 0) l = zr[p - 1];
+      if (x < nx - 1) rt = zr[p + 1];
+      if (y > 0) dn = zr[p - nx];
+      if (y < ny - 1) up = zr[p + nx];
     }
+    const T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
     T2 r = cmul(diag_at(op, x, y), c);
     r.x -= s.x * op.inv_h2;
     r.y -= s.y * op.inv_h2;
@@ -337,11 +338,9 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
   double acc = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), xx = (int)(p - (size_t)y * nx);
-    double2 s = d2(0, 0);
-    if (xx > 0) s = dadd(s, xr[p - 1]);
-    if (xx < nx - 1) s = dadd(s, xr[p + 1]);
-    if (y > 0) s = dadd(s, xr[p - nx]);
-    if (y < ny - 1) s = dadd(s, xr[p + nx]);
+    const double2 l = xx > 0 ? xr[p - 1] : d2(0, 0), rr = xx < nx - 1 ? xr[p + 1] : d2(0, 0);
+    const double2 dn = y > 0 ? xr[p - nx] : d2(0, 0), up = y < ny - 1 ? xr[p + nx] : d2(0, 0);
+    const double2 s = dadd(dadd(dadd(l, rr), dadd(dn, up)), reflect_extra(A, xx, y, l, rr, dn, up));
     double2 ax = dmul(diag_at(A, xx, y), xr[p]);
     double2 bb = b[off + p];
     double2 r = d2(bb.x - (ax.x - s.x * A.inv_h2), bb.y - (ax.y - s.y * A.inv_h2));

@@ -825,6 +825,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
   *gam = c->gam0;
 }
 double helm_omega(helm_ctx* c) { return c->d.omega; }
+int helm_bc(helm_ctx* c) { return c->d.bc; }
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
   const int r = real_bytes == 8 ? ensure_work<double>(c, nrhs, c->d.coarse_its)
                                 : ensure_work<float>(c, nrhs, c->d.coarse_its);
@@ -889,6 +890,11 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   }
   if (d.coarse_its < 1 || d.coarse_its > 32) { g_err = "coarse_its must be in 1..32"; return HELM_EINVAL; }
   if (d.nu1 < 0 || d.nu2 < 0 || d.h <= 0 || d.abc_width < 0) { g_err = "bad smoothing/mesh/layer parameter"; return HELM_EINVAL; }
+  if (d.bc < HELM_BC_DIRICHLET || d.bc > HELM_BC_REPLICATE) { g_err = "bc must be a HELM_BC_* value"; return HELM_EINVAL; }
+  if (d.bc == HELM_BC_REFLECT && ((d.nx >> (d.levels - 1)) < 2 || (d.ny >> (d.levels - 1)) < 2)) {
+    g_err = "reflection boundaries need the coarsest level at least 2 x 2";
+    return HELM_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   helm_ctx* c = new helm_ctx();
   c->d = d;
@@ -910,6 +916,7 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
     L.nx = d.nx >> l; L.ny = d.ny >> l;
     L.h = d.h * (double)(1 << l);
     L.abc_w = d.abc_width >> l;
+    L.bc = d.bc;
     size_t n = (size_t)L.nx * L.ny;
     L.k2f = (float*)a.take(n * 4);
     L.k2d = (double*)a.take(n * 8);

@@ -24,11 +24,11 @@ __device__ __forceinline__ typename vec2<T>::type apply_at(const Op<T>& op, cons
   typedef typename vec2<T>::type T2;
   size_t p = (size_t)y * op.nx + x;
   T2 c = u[p];
-  T2 s = czero<T2>();
-  if (x > 0) s = cadd(s, u[p - 1]);
-  if (x < op.nx - 1) s = cadd(s, u[p + 1]);
-  if (y > 0) s = cadd(s, u[p - op.nx]);
-  if (y < op.ny - 1) s = cadd(s, u[p + op.nx]);
+  const T2 l = x > 0 ? u[p - 1] : czero<T2>();
+  const T2 rt = x < op.nx - 1 ? u[p + 1] : czero<T2>();
+  const T2 dn = y > 0 ? u[p - op.nx] : czero<T2>();
+  const T2 up = y < op.ny - 1 ? u[p + op.nx] : czero<T2>();
+  T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
   T2 d = diag_at(op, x, y);
   T2 r = cmul(d, c);
   r.x -= s.x * op.inv_h2;
@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typ
       int sy = ry + 1, sx = rx + 1;
       T2 c = s_v[sy][sx];
       T2 s = cadd(cadd(s_v[sy][sx - 1], s_v[sy][sx + 1]), cadd(s_v[sy - 1][sx], s_v[sy + 1][sx]));
-      // neighbours outside the grid hold 0 in s_v (zero padding)
+      // neighbours outside the grid hold 0 in s_v (zero padding); reflection adds the
+      // inward neighbour once more, replication lives in the diagonal
+      s = cadd(s, reflect_extra(op, x, y, s_v[sy][sx - 1], s_v[sy][sx + 1], s_v[sy - 1][sx], s_v[sy + 1][sx]));
       T2 kv = cmul(diag_at(op, x, y), c);
       kv.x -= s.x * op.inv_h2;
       kv.y -= s.y * op.inv_h2;
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typ
     const int sy = threadIdx.y + 1, sx = threadIdx.x + 1;
     T2 c = s_x[sy][sx];
     T2 s = cadd(cadd(s_x[sy][sx - 1], s_x[sy][sx + 1]), cadd(s_x[sy - 1][sx], s_x[sy + 1][sx]));
+    s = cadd(s, reflect_extra(op, x, y, s_x[sy][sx - 1], s_x[sy][sx + 1], s_x[sy - 1][sx], s_x[sy + 1][sx]));
     T2 d = diag_at(op, x, y);
     T2 kx = cmul(d, c);
     kx.x -= s.x * op.inv_h2;

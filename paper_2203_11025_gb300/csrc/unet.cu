@@ -809,6 +809,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
                    const float** gam);
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs);
 double helm_omega(helm_ctx* c);
+int helm_bc(helm_ctx* c);
 }  // namespace helm
 
 // e = U-Net(r) (inference), with the network input built on the fly.
@@ -1278,7 +1279,7 @@ int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float*
   float *rho = nullptr, *part = nullptr;
   UCHECK(cudaMallocAsync(&rho, (size_t)B * nx * ny * 2 * sizeof(float), s));
   UCHECK(cudaMallocAsync(&part, 256 * sizeof(float), s));
-  residual_loss(out, x, B, ny, nx, (float)(hh * hh * om * om), k2f, gam, rho, gout, part, loss_dev, s);
+  residual_loss(out, x, B, ny, nx, (float)(hh * hh * om * om), k2f, gam, helm_bc(h), rho, gout, part, loss_dev, s);
   cudaFreeAsync(rho, s);
   cudaFreeAsync(part, s);
   UCHECK(cudaGetLastError());

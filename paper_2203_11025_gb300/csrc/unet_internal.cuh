@@ -92,9 +92,10 @@ void to_bf16_slice(const float* src, int lds, __nv_bfloat16* dst, int ldd, int C
 void mse_loss(const float* out, const float* tgt, size_t n, int B, float* gout, float* part, float* loss,
               cudaStream_t s);
 // Residual loss sum |h^2 A y - x_r|^2 / B and its gradient (float2 outputs y, inputs x with
-// 4 channels); rho: scratch of B*ny*nx float2; part: 256 floats; c = h^2 omega^2.
+// 4 channels); rho: scratch of B*ny*nx float2; part: 256 floats; c = h^2 omega^2; bc the
+// boundary mode (0 zero, 1 reflection, 2 replication padding; 1 needs nx, ny >= 2).
 void residual_loss(const float* y, const float* x, int B, int ny, int nx, float c, const float* k2, const float* gam,
-                   float* rho, float* gout, float* part, float* loss, cudaStream_t s);
+                   int bc, float* rho, float* gout, float* part, float* loss, cudaStream_t s);
 void adam_update(float* p, const float* g, float* m1, float* m2, size_t n, float lr, float b1, float b2, float eps,
                  int t, cudaStream_t s);
 void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s);

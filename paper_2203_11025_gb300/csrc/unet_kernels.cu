@@ -438,14 +438,35 @@ __global__ void k_sum_partials(const float* __restrict__ part, int n, int B, flo
   }
 }
 
+// Boundary terms of h^2 A for the residual loss (Sec. 2.4's padding modes: bc 0 zero,
+// 1 reflection, 2 replication).  Centre weight: 4, less one per boundary side under
+// replication.  Reflection adds the inward neighbour once more at a boundary node, so
+// A is not symmetric there; its transpose instead adds, at the inward neighbour of a
+// boundary node, that boundary node once more.
+__device__ __forceinline__ float resloss_centre(int bc, int ix, int iy, int nx, int ny) {
+  return bc == 2 ? 4.f - (float)((ix == 0) + (ix == nx - 1) + (iy == 0) + (iy == ny - 1)) : 4.f;
+}
+__device__ __forceinline__ float2 resloss_reflect(const float2* v, size_t i, int ix, int iy, int nx, int ny,
+                                                  bool transpose) {
+  float2 e = make_float2(0.f, 0.f);
+  const int lo = transpose ? 1 : 0, hi = transpose ? 2 : 1;   // node at which the extra term enters
+  // forward: at x = 0 add x + 1, at x = nx - 1 add x - 1; transpose: at x = 1 add x - 1,
+  // at x = nx - 2 add x + 1 (likewise in y)
+  if (ix == lo) { const float2 a = v[transpose ? i - 1 : i + 1]; e.x += a.x; e.y += a.y; }
+  if (ix == nx - hi) { const float2 a = v[transpose ? i + 1 : i - 1]; e.x += a.x; e.y += a.y; }
+  if (iy == lo) { const float2 a = v[transpose ? i - nx : i + nx]; e.x += a.x; e.y += a.y; }
+  if (iy == ny - hi) { const float2 a = v[transpose ? i + nx : i - nx]; e.x += a.x; e.y += a.y; }
+  return e;
+}
+
 // Unsupervised residual loss (the Remark following Eq. 3.7) on network outputs y
 // [B][ny][nx][2] (units e / s) and inputs x [B][ny][nx][4] (channels 0, 1 = h^2 r / s):
 //   rho = h^2 A y - x_r,  (h^2 A y)_p = 4 y_p - (sum of the 4 neighbours, zero outside)
-//                                      - c kappa2_p (1 - i gamma_p) y_p,  c = h^2 omega^2.
-// Per-block sums of |rho|^2 go to part.
+//                                      - c kappa2_p (1 - i gamma_p) y_p,  c = h^2 omega^2,
+// with the boundary terms above.  Per-block sums of |rho|^2 go to part.
 __global__ void __launch_bounds__(256) k_resloss_rho(const float2* __restrict__ y, const float* __restrict__ x,
                                                      int B, int ny, int nx, float c, const float* __restrict__ k2,
-                                                     const float* __restrict__ gam, float2* __restrict__ rho,
+                                                     const float* __restrict__ gam, int bc, float2* __restrict__ rho,
                                                      float* __restrict__ part) {
   const size_t N = (size_t)nx * ny, M = N * B;
   float s = 0.f;
@@ -458,10 +479,12 @@ __global__ void __launch_bounds__(256) k_resloss_rho(const float2* __restrict__ 
     if (ix < nx - 1) { nb.x += y[i + 1].x; nb.y += y[i + 1].y; }
     if (iy > 0) { nb.x += y[i - nx].x; nb.y += y[i - nx].y; }
     if (iy < ny - 1) { nb.x += y[i + nx].x; nb.y += y[i + nx].y; }
+    if (bc == 1) { const float2 e = resloss_reflect(y, i, ix, iy, nx, ny, false); nb.x += e.x; nb.y += e.y; }
+    const float cw = resloss_centre(bc, ix, iy, nx, ny);
     const float d = c * k2[p], g = gam[p];
     // -d (1 - i g)(a + i b) = -d (a + g b) - i d (b - g a)
-    const float rx = 4.f * v.x - nb.x - d * (v.x + g * v.y) - x[i * 4];
-    const float ry = 4.f * v.y - nb.y - d * (v.y - g * v.x) - x[i * 4 + 1];
+    const float rx = cw * v.x - nb.x - d * (v.x + g * v.y) - x[i * 4];
+    const float ry = cw * v.y - nb.y - d * (v.y - g * v.x) - x[i * 4 + 1];
     rho[i] = make_float2(rx, ry);
     s += rx * rx + ry * ry;
   }
@@ -475,11 +498,12 @@ __global__ void __launch_bounds__(256) k_resloss_rho(const float2* __restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
 
-// d loss / d (Re y, Im y) = (2 / B) conj(h^2 A conj(rho)): A is complex symmetric, so the
-// adjoint is the same stencil with the diagonal's imaginary part negated.
+// d loss / d (Re y, Im y) = (2 / B) conj(h^2 A^T conj(rho)) = (2 / B) h^2 A^H rho: the
+// stencil of A^T (A itself but for reflection's boundary terms) with the diagonal's
+// imaginary part negated.
 __global__ void __launch_bounds__(256) k_resloss_grad(const float2* __restrict__ rho, int B, int ny, int nx, float c,
                                                       const float* __restrict__ k2, const float* __restrict__ gam,
-                                                      float2* __restrict__ gout) {
+                                                      int bc, float2* __restrict__ gout) {
   const size_t N = (size_t)nx * ny, M = N * B;
   const float sc = 2.f / B;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
@@ -491,9 +515,11 @@ __global__ void __launch_bounds__(256) k_resloss_grad(const float2* __restrict__
     if (ix < nx - 1) { nb.x += rho[i + 1].x; nb.y += rho[i + 1].y; }
     if (iy > 0) { nb.x += rho[i - nx].x; nb.y += rho[i - nx].y; }
     if (iy < ny - 1) { nb.x += rho[i + nx].x; nb.y += rho[i + nx].y; }
+    if (bc == 1) { const float2 e = resloss_reflect(rho, i, ix, iy, nx, ny, true); nb.x += e.x; nb.y += e.y; }
+    const float cw = resloss_centre(bc, ix, iy, nx, ny);
     const float d = c * k2[p], g = gam[p];
     // -d (1 + i g)(a + i b) = -d (a - g b) - i d (b + g a)
-    gout[i] = make_float2(sc * (4.f * v.x - nb.x - d * (v.x - g * v.y)), sc * (4.f * v.y - nb.y - d * (v.y + g * v.x)));
+    gout[i] = make_float2(sc * (cw * v.x - nb.x - d * (v.x - g * v.y)), sc * (cw * v.y - nb.y - d * (v.y + g * v.x)));
   }
 }
 
@@ -865,11 +891,11 @@ void mse_loss(const float* out, const float* tgt, size_t n, int B, float* gout, 
 }
 
 void residual_loss(const float* y, const float* x, int B, int ny, int nx, float c, const float* k2, const float* gam,
-                   float* rho, float* gout, float* part, float* loss, cudaStream_t s) {
+                   int bc, float* rho, float* gout, float* part, float* loss, cudaStream_t s) {
   const int nb = 256;
-  k_resloss_rho<<<nb, 256, 0, s>>>((const float2*)y, x, B, ny, nx, c, k2, gam, (float2*)rho, part);
+  k_resloss_rho<<<nb, 256, 0, s>>>((const float2*)y, x, B, ny, nx, c, k2, gam, bc, (float2*)rho, part);
   k_sum_partials<<<1, 32, 0, s>>>(part, nb, B, loss);
-  k_resloss_grad<<<grid_for((size_t)B * ny * nx), 256, 0, s>>>((const float2*)rho, B, ny, nx, c, k2, gam,
+  k_resloss_grad<<<grid_for((size_t)B * ny * nx), 256, 0, s>>>((const float2*)rho, B, ny, nx, c, k2, gam, bc,
                                                                (float2*)gout);
 }
 

@@ -497,3 +497,14 @@ def test_neumann_fgmres_vcycle_matches_dense_direct(bc):
     assert np.linalg.norm(res.x - x_ref) / np.linalg.norm(x_ref) < 1e-9
     dir_prob = H.Problem(k2, omega=synth.omega_for(16), h=1.0 / 16, abc_width=4, levels=3)
     assert not np.allclose(H.assemble_dense(dir_prob.A), H.assemble_dense(prob.A))
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "reflect", "replicate"])
+def test_transpose_action_matches_assembled_transpose(bc):
+    """K^T u by scatter-and-fold equals the transposed node-wise assembly."""
+    lv = _level(6, 9, seed=7)
+    lv = H.Level(lv.ny, lv.nx, lv.h, lv.omega, lv.kappa2, lv.gamma, lv.beta, bc)
+    K = H.assemble_dense(lv)
+    u = _crandn(np.random.default_rng(8), (2, 6, 9))
+    for t in range(2):
+        assert np.allclose(H.apply_op_T(lv, u)[t].ravel(), K.T @ u[t].ravel(), rtol=1e-14, atol=1e-11)

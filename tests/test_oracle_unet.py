@@ -186,16 +186,18 @@ def test_encoder_solver_backward_matches_finite_differences():
     assert _fd_check(total, Pe, Ge, ["down1", "res2.0.k2", "up2", "up1", "up2.bn.gamma"], rng, n=3) < 1e-6
 
 
-def _small_problem(n=8, seed=3):
+def _small_problem(n=8, seed=3, bc="dirichlet"):
     rng = np.random.default_rng(seed)
     k2 = rng.uniform(0.25, 1.0, (n, n))
-    return H.Problem(k2, omega=0.2 * np.pi * n, h=1.0 / n, abc_width=2, levels=1), rng
+    return H.Problem(k2, omega=0.2 * np.pi * n, h=1.0 / n, abc_width=2, levels=1, bc=bc), rng
 
 
-def test_residual_loss_gradient_matches_finite_differences():
-    # the residual-loss gradient (Remark after Eq. 3.7) against central differences of the loss
+@pytest.mark.parametrize("bc", ["dirichlet", "reflect", "replicate"])
+def test_residual_loss_gradient_matches_finite_differences(bc):
+    # the residual-loss gradient (Remark after Eq. 3.7) against central differences of the
+    # loss, for every boundary mode (reflection makes A unsymmetric: the gradient needs A^T)
     from oracle import precond as PR
-    prob, rng = _small_problem()
+    prob, rng = _small_problem(bc=bc)
     y = rng.standard_normal((2, 8, 8, 2))
     x = rng.standard_normal((2, 8, 8, 4))
     loss, g = PR.residual_loss(prob, y, x)
