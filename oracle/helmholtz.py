@@ -63,9 +63,10 @@ class Level:
     gamma: np.ndarray           # (ny, nx) float64
     beta: float = 0.0           # shift of the operator (0 -> A, 0.5 -> M)
     bc: str = "dirichlet"       # stencil padding: "dirichlet" (zero), "reflect" or "replicate"
+    order: int = 2              # 2: 5-point stencil (Eq. 2.2); 4: compact 9-point scheme
 
     def with_shift(self, beta: float) -> "Level":
-        return Level(self.ny, self.nx, self.h, self.omega, self.kappa2, self.gamma, beta, self.bc)
+        return Level(self.ny, self.nx, self.h, self.omega, self.kappa2, self.gamma, beta, self.bc, self.order)
 
 
 @dataclass
@@ -83,6 +84,7 @@ class Problem:
     jacobi_w: float = 0.8
     coarse_its: int = 10
     bc: str = "dirichlet"
+    order: int = 2
     hierarchy: list = field(default_factory=list)
 
     def __post_init__(self):
@@ -94,7 +96,8 @@ class Problem:
                 k2 = coarsen_kappa2(k2)
             lny, lnx = ny >> l, nx >> l
             g = abc_gamma(lny, lnx, self.abc_width >> l, self.gamma_max)
-            self.hierarchy.append(Level(lny, lnx, self.h * (1 << l), self.omega, k2, g, self.beta, self.bc))
+            self.hierarchy.append(Level(lny, lnx, self.h * (1 << l), self.omega, k2, g, self.beta, self.bc,
+                                        self.order))
 
     @property
     def A(self) -> Level:
@@ -128,9 +131,67 @@ def _ghost(i: int, n: int, bc: str):
     return None
 
 
+# Compact fourth-order scheme (the higher-order operators Sec. 2.4 says the convolution
+# form carries over to).  For -Lap u = g the compact fourth-order difference is
+#   (1/(6h^2)) [-1 -4 -1; -4 20 -4; -1 -4 -1] u = (1/12) [0 1 0; 1 8 1; 0 1 0] g,
+# and the Helmholtz equation is that with g = f + m u, m = w^2 k^2 (1 - (g + beta) i):
+#   K u = L9 u - (1/12) M5 (m u),   right-hand side (1/12) M5 f.
+LAP9 = np.array([[-1.0, -4.0, -1.0], [-4.0, 20.0, -4.0], [-1.0, -4.0, -1.0]]) / 6.0   # times 1/h^2
+MASS5 = np.array([[0.0, 1.0, 0.0], [1.0, 8.0, 1.0], [0.0, 1.0, 0.0]]) / 12.0
+
+
+def _mass(lv: Level) -> np.ndarray:
+    """m = w^2 k^2 (1 - (g + beta) i), the mass term of Eq. 2.2 / 2.4."""
+    return lv.omega ** 2 * lv.kappa2 * (1.0 - (lv.gamma + lv.beta) * 1j)
+
+
+def _pad(lv: Level, u: np.ndarray) -> np.ndarray:
+    mode = {"dirichlet": "constant", "reflect": "reflect", "replicate": "edge"}[lv.bc]
+    return np.pad(u, [(0, 0)] * (u.ndim - 2) + [(1, 1), (1, 1)], mode=mode)
+
+
+def _conv3(p: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """sum_{a,b} w[a+1, b+1] p(i+a, j+b) over the interior of a 1-padded array."""
+    ny, nx = p.shape[-2] - 2, p.shape[-1] - 2
+    out = np.zeros(p.shape[:-2] + (ny, nx), dtype=p.dtype)
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            if w[a + 1, b + 1] != 0.0:
+                out += w[a + 1, b + 1] * p[..., 1 + a:1 + a + ny, 1 + b:1 + b + nx]
+    return out
+
+
+def _apply_compact4(lv: Level, u: np.ndarray) -> np.ndarray:
+    return _conv3(_pad(lv, u), LAP9) / lv.h ** 2 - _conv3(_pad(lv, _mass(lv) * u), MASS5)
+
+
+def rhs_weight(lv: Level, f: np.ndarray) -> np.ndarray:
+    """Right-hand side of the discrete equation for a source f: f itself for the 5-point
+    scheme, (1/12) M5 f for the compact fourth-order one."""
+    return f if lv.order == 2 else _conv3(_pad(lv, f), MASS5)
+
+
+def _diagonal_compact4(lv: Level) -> np.ndarray:
+    """Diagonal of the compact operator: every stencil entry whose (padded) neighbour is
+    the node itself (the centre; also folded ghosts under replication)."""
+    m = _mass(lv)
+    d = np.zeros((lv.ny, lv.nx), dtype=np.complex128)
+    iy = np.arange(lv.ny)[:, None]
+    ix = np.arange(lv.nx)[None, :]
+    for a in (-1, 0, 1):
+        for b in (-1, 0, 1):
+            gy = np.array([_ghost(i + a, lv.ny, lv.bc) for i in range(lv.ny)], dtype=object)[:, None]
+            gx = np.array([_ghost(j + b, lv.nx, lv.bc) for j in range(lv.nx)], dtype=object)[None, :]
+            self_ = (gy == iy) & (gx == ix)
+            d = d + self_ * (LAP9[a + 1, b + 1] / lv.h ** 2 - MASS5[a + 1, b + 1] * m)
+    return d
+
+
 def diagonal(lv: Level) -> np.ndarray:
     """Diagonal of the operator: the centre weight, less 1/h^2 for every neighbour that
     replication padding maps back onto the node itself."""
+    if lv.order == 4:
+        return _diagonal_compact4(lv)
     d = _center(lv)
     if lv.bc == "replicate":
         iy = np.arange(lv.ny)[:, None]
@@ -141,8 +202,11 @@ def diagonal(lv: Level) -> np.ndarray:
 
 
 def apply_op(lv: Level, u: np.ndarray) -> np.ndarray:
-    """y = K u for the 5-point stencil of Eq. 2.2 (with shift beta); neighbours outside
-    the grid are zero (Dirichlet) or taken by reflection / replication (Neumann)."""
+    """y = K u for the 5-point stencil of Eq. 2.2 (with shift beta), or the compact
+    fourth-order scheme when lv.order == 4; neighbours outside the grid are zero
+    (Dirichlet) or taken by reflection / replication (Neumann)."""
+    if lv.order == 4:
+        return _apply_compact4(lv, u)
     if lv.bc == "dirichlet":
         up = np.zeros_like(u)
         up[..., 1:, :] += u[..., :-1, :]
@@ -163,6 +227,8 @@ def apply_op_T(lv: Level, u: np.ndarray) -> np.ndarray:
     weight, so K^T = C - (1/h^2) P^T S^T: scatter every value to its four neighbours on
     the padded array, then fold each ghost back onto the node it copies.  Zero padding
     and replication give a symmetric K; reflection does not."""
+    if lv.order != 2:
+        raise NotImplementedError("transpose of the compact fourth-order operator")
     if lv.bc == "dirichlet":
         return apply_op(lv, u)
     ny, nx = u.shape[-2:]
@@ -191,10 +257,23 @@ def jacobi(lv: Level, u: np.ndarray, f: np.ndarray, w: float) -> np.ndarray:
 
 
 def assemble_dense(lv: Level) -> np.ndarray:
-    """Dense matrix of the operator, assembled node by node from the stencil (Eq. 2.2)."""
+    """Dense matrix of the operator, assembled node by node from the stencil (Eq. 2.2,
+    or the compact fourth-order scheme), ghost neighbours mapped to the nodes they copy."""
     ny, nx = lv.ny, lv.nx
     n = ny * nx
     K = np.zeros((n, n), dtype=np.complex128)
+    if lv.order == 4:
+        m = _mass(lv)
+        for iy in range(ny):
+            for ix in range(nx):
+                p = iy * nx + ix
+                for a in (-1, 0, 1):
+                    for b in (-1, 0, 1):
+                        gy, gx = _ghost(iy + a, ny, lv.bc), _ghost(ix + b, nx, lv.bc)
+                        if gy is None or gx is None:
+                            continue
+                        K[p, gy * nx + gx] += LAP9[a + 1, b + 1] / lv.h ** 2 - MASS5[a + 1, b + 1] * m[gy, gx]
+        return K
     c = _center(lv)
     off = -1.0 / lv.h ** 2
     for iy in range(ny):
