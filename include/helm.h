@@ -46,7 +46,8 @@ enum {
   HELM_ENOMEM = -5,        /* device allocation failed                         */
   HELM_EUNSUPPORTED = -6   /* feature not built for this configuration         */
 };
-enum { HELM_OP_A = 0, HELM_OP_M = 1 };       /* Helmholtz A (Eq. 2.2) / shifted M (Eq. 2.4) */
+enum { HELM_OP_A = 0, HELM_OP_M = 1,        /* Helmholtz A (Eq. 2.2) / shifted M (Eq. 2.4) */
+       HELM_OP_RHS = 2 };                    /* right-hand side of a source (helm_apply only) */
 enum { HELM_C32 = 0, HELM_C64 = 1 };
 enum { HELM_PREC_NONE = 0, HELM_PREC_V = 1, HELM_PREC_JU = 2, HELM_PREC_VU = 3 };
 
@@ -64,7 +65,16 @@ typedef struct {
   int coarse_its;          /* GMRES steps on the coarsest grid (Sec. 4: 10)   */
   int flags;               /* HELM_DESC_* implementation switches (0 = default) */
   int bc;                  /* HELM_BC_* boundary condition (0 = Dirichlet)     */
+  int stencil;             /* HELM_STENCIL_* discretisation (0 = 5-point)      */
 } helm_desc;
+/* Discretisations.  5PT is Eq. 2.2.  COMPACT4 is the compact fourth-order 9-point
+ * scheme, one of the higher-order operators that Sec. 2.4 says the convolution form
+ * admits: with m = w^2 k^2 (1 - (g + beta) i),
+ *   K u = (1/(6h^2)) [-1 -4 -1; -4 20 -4; -1 -4 -1] u - (1/12) [0 1 0; 1 8 1; 0 1 0] (m u),
+ * and the discrete equation for a source f is K u = (1/12) [0 1 0; 1 8 1; 0 1 0] f
+ * (helm_apply with HELM_OP_RHS computes that right-hand side).  Every level
+ * rediscretises with the same scheme.  COMPACT4 needs HELM_BC_DIRICHLET. */
+enum { HELM_STENCIL_5PT = 0, HELM_STENCIL_COMPACT4 = 1 };
 /* Boundary conditions (Sec. 2.4: the 5-point stencil applied as a convolution,
  * whose padding sets the boundary).  DIRICHLET pads with zeros; REFLECT mirrors
  * about the boundary node (ghost u_-1 = u_1) and REPLICATE copies it (ghost
@@ -96,7 +106,10 @@ int helm_level_shape(helm_t h, int level, int* nx, int* ny);
 /* Copy the level's kappa^2 (float64, [ny][nx]) into a device buffer. */
 int helm_level_kappa2(helm_t h, int level, double* out);
 
-/* y = K x on `level`, K = A (op HELM_OP_A) or M (HELM_OP_M), Eq. 2.2 / 2.4. */
+/* y = K x on `level`, K = A (op HELM_OP_A) or M (HELM_OP_M), Eq. 2.2 / 2.4; with
+ * op HELM_OP_RHS, y = the discrete right-hand side of the source x (x itself for the
+ * 5-point stencil, (1/12) [0 1 0; 1 8 1; 0 1 0] x for COMPACT4); y must not alias x.
+ * An op outside these is HELM_EINVAL (helm_residual and helm_jacobi take A or M). */
 int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream);
 /* r = b - K x. */
 int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,

@@ -89,7 +89,8 @@ int unet_mse(const float* out, const float* target, long long n, int B, float* g
  *   rho = h^2 A (y0 + i y1) - (x0 + i x1),  loss = sum |rho|^2 / B,
  * gout = d loss / d y = (2 / B) conj(h^2 A^T conj(rho)) (device, like y; must differ from
  * out; A^T = A but for reflection boundaries), A with the boundary mode of h; the loss
- * goes to *loss_dev.  Allocates its scratch stream-ordered. */
+ * goes to *loss_dev.  Allocates its scratch stream-ordered.  HELM_EUNSUPPORTED for a
+ * handle with the compact fourth-order stencil. */
 int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float* gout, float* loss_dev,
                        helm_stream_t stream);
 /* One Adam step (bias-corrected) on every parameter of net (and of its attached encoder). */

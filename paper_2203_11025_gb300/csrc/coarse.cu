@@ -61,7 +61,7 @@ __device__ __forceinline__ typename vec2<T>::type scaled_by_dinv(const Op<T>& op
   return cmul(v[(size_t)y * op.nx + x], cinv(diag_at(op, x, y)));
 }
 
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename vec2<T>::type* __restrict__ f,
                                                      typename vec2<T>::type* __restrict__ out,
                                                      typename vec2<T>::type* __restrict__ Vg, size_t vstride, int m,
@@ -107,11 +107,7 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
     for (int p = tid; p < N; p += CT) {
       const int y = p / nx, x = p - y * nx;
       T2 c = scaled_by_dinv(op, vj, x, y);
-      const T2 l = x > 0 ? scaled_by_dinv(op, vj, x - 1, y) : czero<T2>();
-      const T2 rt = x < nx - 1 ? scaled_by_dinv(op, vj, x + 1, y) : czero<T2>();
-      const T2 dn = y > 0 ? scaled_by_dinv(op, vj, x, y - 1) : czero<T2>();
-      const T2 up = y < ny - 1 ? scaled_by_dinv(op, vj, x, y + 1) : czero<T2>();
-      T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
+      const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return scaled_by_dinv(op, vj, x + dx, y + dy); });
       T2 r = cmul(diag_at(op, x, y), c);
       r.x -= s.x * op.inv_h2;
       r.y -= s.y * op.inv_h2;
@@ -213,10 +209,12 @@ bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* 
   if (m > CMAX || smem > 160 * 1024) return false;
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_coarse_gmres<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_coarse_gmres<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_coarse_gmres<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     configured = true;
   }
-  k_coarse_gmres<T><<<nrhs, CT, smem, s>>>(op, (const T2*)f, (T2*)out, (T2*)V, vstride, m, gate);
+  auto k = op.order == 4 ? k_coarse_gmres<T, 4> : k_coarse_gmres<T, 2>;
+  k<<<nrhs, CT, smem, s>>>(op, (const T2*)f, (T2*)out, (T2*)V, vstride, m, gate);
   return true;
 }
 
@@ -281,8 +279,9 @@ extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, 
     basis = helm::g_static_ptr[dev];
   }
   helm::Op<float> op;
-  op.nx = nx; op.ny = ny; op.abc_w = abc_width; op.bc = helm::kBcDirichlet;
+  op.nx = nx; op.ny = ny; op.abc_w = abc_width; op.bc = helm::kBcDirichlet; op.order = 2;
   op.inv_h2 = (float)(1.0 / (h * h));
+  op.h2 = (float)(h * h);
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gamma_max;
   op.beta = (float)beta;

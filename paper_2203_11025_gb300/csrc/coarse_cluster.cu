@@ -206,11 +206,14 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
       const int lp = tid + q * KT;
       if (lp >= NP) continue;
       const int ly = lp / nx, x = lp - ly * nx;
-      const T2 l = x > 0 ? U[lp - 1] : czero<T2>();
-      const T2 rt = x < nx - 1 ? U[lp + 1] : czero<T2>();
-      const T2 dn = ly > 0 ? U[lp - nx] : (Uup ? Uup[(rows - 1) * nx + x] : czero<T2>());
-      const T2 up = ly < rows - 1 ? U[lp + nx] : (Udn ? Udn[x] : czero<T2>());
-      const T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, rank * rows + ly, l, rt, dn, up));
+      // rows beyond this CTA's come from the neighbours' shared memory; stencil_sum asks for
+      // them only inside the grid, where those neighbours exist
+      const T2 s = stencil_sum<2>(op, x, rank * rows + ly, [&](int dx, int dy) -> T2 {
+        const int yy = ly + dy, xx = x + dx;
+        if (yy < 0) return Uup[(rows - 1) * nx + xx];
+        if (yy >= rows) return Udn[xx];
+        return U[yy * nx + xx];
+      });
       T2 r = vj[lp];
       r.x -= s.x * ih2;
       r.y -= s.y * ih2;
@@ -373,7 +376,9 @@ bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int 
                                  void* gV, size_t vstride, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
   const int nx = op.nx, ny = op.ny;
-  if (m > KMAX || nx > 1024 || m + 2 > 34) return false;
+  // 5-point stencil only: the compact scheme's coarsest solve takes the one-CTA or the
+  // multi-kernel path
+  if (op.order != 2 || m > KMAX || nx > 1024 || m + 2 > 34) return false;
   int C = 0, rows = 0;
   for (int target : {2 * KT, 4 * KT}) {       // prefer <= 2 points per thread (more SMs per solve)
     for (int c = 1; c <= 16 && !C; c *= 2) {

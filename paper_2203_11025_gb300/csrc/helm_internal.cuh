@@ -21,18 +21,24 @@ template <> struct vec2<double> { typedef double2 type; };
 // u_1), so the inward neighbour of a boundary node couples twice; bc 2
 // replicates the boundary node (ghost u_-1 = u_0), which folds that coupling
 // into the diagonal: -1/h^2 per boundary side.  Both are Neumann conditions.
+// Stencil: order 2 is the 5-point scheme above; order 4 the compact fourth-order
+// 9-point scheme (the higher-order operators the convolution form of Sec. 2.4
+// admits): with m = w^2 k^2 (1 - (g + beta) i),
+//   K u = (1/(6h^2)) [-1 -4 -1; -4 20 -4; -1 -4 -1] u - (1/12) [0 1 0; 1 8 1; 0 1 0] (m u),
+// the compact fourth-order Laplacian with the mass term weighted like its right-hand
+// side; Dirichlet boundaries only.
 // ---------------------------------------------------------------------------
 enum { kBcDirichlet = 0, kBcReflect = 1, kBcReplicate = 2 };
 
 template <typename T> struct Op {
-  int nx, ny, abc_w, bc;
-  T inv_h2, omega2, gmax, beta;
+  int nx, ny, abc_w, bc, order;
+  T inv_h2, h2, omega2, gmax, beta;
   const T* k2;  // kappa^2 on this level, [ny][nx]
 };
 
 // Per-level storage owned by the handle.
 struct Level {
-  int nx, ny, abc_w, bc;
+  int nx, ny, abc_w, bc, order;
   double h;
   float* k2f;   // kappa^2 (float32)
   double* k2d;  // kappa^2 (float64)
@@ -41,7 +47,8 @@ struct Level {
 template <typename T>
 inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
   Op<T> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc; op.order = L.order;
+  op.h2 = (T)(L.h * L.h);
   op.inv_h2 = (T)(1.0 / (L.h * L.h));
   op.omega2 = (T)(omega * omega);
   op.gmax = (T)gmax;
@@ -51,7 +58,8 @@ inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
 }
 template <> inline Op<float> make_op<float>(const Level& L, double omega, double gmax, double beta) {
   Op<float> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc; op.order = L.order;
+  op.h2 = (float)(L.h * L.h);
   op.inv_h2 = (float)(1.0 / (L.h * L.h));
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gmax; op.beta = (float)beta; op.k2 = L.k2f;
@@ -59,7 +67,8 @@ template <> inline Op<float> make_op<float>(const Level& L, double omega, double
 }
 template <> inline Op<double> make_op<double>(const Level& L, double omega, double gmax, double beta) {
   Op<double> op;
-  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc;
+  op.nx = L.nx; op.ny = L.ny; op.abc_w = L.abc_w; op.bc = L.bc; op.order = L.order;
+  op.h2 = L.h * L.h;
   op.inv_h2 = 1.0 / (L.h * L.h);
   op.omega2 = omega * omega;
   op.gmax = gmax; op.beta = beta; op.k2 = L.k2d;
@@ -89,11 +98,18 @@ template <typename T> __device__ __forceinline__ T gamma_at(const Op<T>& op, int
 }
 
 // Diagonal of K at (x, y): 4/h^2 - w^2 k^2 + i w^2 k^2 (g + beta), less 1/h^2
-// per boundary side under replication padding.
+// per boundary side under replication padding; (20/6)/h^2 - (8/12) m for the compact
+// scheme.
 template <typename T>
 __device__ __forceinline__ typename vec2<T>::type diag_at(const Op<T>& op, int x, int y) {
   T wk = op.omega2 * op.k2[(size_t)y * op.nx + x];
   typename vec2<T>::type d;
+  if (op.order == 4) {
+    const T wm = wk * T(8) / T(12);
+    d.x = T(20) / T(6) * op.inv_h2 - wm;
+    d.y = wm * (gamma_at(op, x, y) + op.beta);
+    return d;
+  }
   T c = T(4);
   if (op.bc == kBcReplicate)
     c -= T((x == 0) + (x == op.nx - 1) + (y == 0) + (y == op.ny - 1));
@@ -114,6 +130,46 @@ __device__ __forceinline__ T2 reflect_extra(const Op<T>& op, int x, int y, T2 l,
   if (y == 0) e = cadd(e, u); else if (y == op.ny - 1) e = cadd(e, d);
   return e;
 }
+
+// m u at (x, y): w^2 k^2 (1 - (g + beta) i) u.
+template <typename T, typename T2>
+__device__ __forceinline__ T2 mass_times(const Op<T>& op, int x, int y, T2 u) {
+  const T wk = op.omega2 * op.k2[(size_t)y * op.nx + x];
+  T2 m;
+  m.x = wk;
+  m.y = -wk * (gamma_at(op, x, y) + op.beta);
+  return cmul(m, u);
+}
+
+// Off-diagonal part s of K at (x, y) in the form K u = D u - s / h^2, with at(dx, dy)
+// the value at (x + dx, y + dy), called only for nodes inside the grid.  ORD 2 (5-point):
+// the four neighbours (plus the reflection term); ORD 4 (compact scheme): (4 edges +
+// corners) / 6 + (h^2 / 12) sum over the edges of m_q u_q.  The order is a template
+// parameter so that the 5-point kernels carry none of the 9-point registers; launchers
+// pick the instantiation from op.order.
+template <int ORD, typename T, typename F>
+__device__ __forceinline__ typename vec2<T>::type stencil_sum(const Op<T>& op, int x, int y, F at) {
+  typedef typename vec2<T>::type T2;
+  const bool xl = x > 0, xr = x < op.nx - 1, yd = y > 0, yu = y < op.ny - 1;
+  const T2 l = xl ? at(-1, 0) : czero<T2>();
+  const T2 rt = xr ? at(1, 0) : czero<T2>();
+  const T2 dn = yd ? at(0, -1) : czero<T2>();
+  const T2 up = yu ? at(0, 1) : czero<T2>();
+  const T2 e = cadd(cadd(l, rt), cadd(dn, up));
+  if (ORD != 4) return cadd(e, reflect_extra(op, x, y, l, rt, dn, up));
+  T2 c = czero<T2>();
+  if (yd && xl) c = cadd(c, at(-1, -1));
+  if (yd && xr) c = cadd(c, at(1, -1));
+  if (yu && xl) c = cadd(c, at(-1, 1));
+  if (yu && xr) c = cadd(c, at(1, 1));
+  T2 mq = czero<T2>();
+  if (xl) mq = cadd(mq, mass_times(op, x - 1, y, l));
+  if (xr) mq = cadd(mq, mass_times(op, x + 1, y, rt));
+  if (yd) mq = cadd(mq, mass_times(op, x, y - 1, dn));
+  if (yu) mq = cadd(mq, mass_times(op, x, y + 1, up));
+  T2 s = cscale(cadd(cscale(e, T(4)), c), T(1) / T(6));
+  return cadd(s, cscale(mq, op.h2 / T(12)));
+}
 #endif
 
 // Block sizes shared by launchers.
@@ -125,6 +181,8 @@ constexpr int kVecThreads = 256;
 // ---------------------------------------------------------------------------
 template <typename T> void launch_apply(const Op<T>& op, const void* x, const void* b, void* y, int nrhs,
                                         const int* active, cudaStream_t s);
+// y = (1/12) [0 1 0; 1 8 1; 0 1 0] x (the compact scheme's right-hand side); y != x.
+template <typename T> void launch_rhs_weight(const Op<T>& op, const void* x, void* y, int nrhs, cudaStream_t s);
 template <typename T> void launch_jacobi(const Op<T>& op, T w, const void* f, const void* x_in, void* x_out,
                                          int nrhs, const int* active, cudaStream_t s);
 template <typename T> void launch_restrict(int nx, int ny, const void* rf, void* rc, int nrhs,

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(NT) k_scale(const typename vec2<T>::type* __re
 }
 
 // w = K z (diag_precond: w = K D^-1 z), then h_{0j} = <v_0, w>.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, const typename vec2<T>::type* __restrict__ z,
                                                   typename vec2<T>::type* __restrict__ w,
                                                   const typename vec2<T>::type* __restrict__ v0, ArnoldiState st,
@@ -176,21 +176,16 @@ __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, co
   T ax = 0, ay = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
-    T2 c, l = czero<T2>(), rt = czero<T2>(), dn = czero<T2>(), up = czero<T2>();
+    T2 c, s;
     if (diag_precond) {
       c = cmul(zr[p], cinv(diag_at(op, x, y)));
-      if (x > 0) l = cmul(zr[p - 1], cinv(diag_at(op, x - 1, y)));
-      if (x < nx - 1) rt = cmul(zr[p + 1], cinv(diag_at(op, x + 1, y)));
-      if (y > 0) dn = cmul(zr[p - nx], cinv(diag_at(op, x, y - 1)));
-      if (y < ny - 1) up = cmul(zr[p + nx], cinv(diag_at(op, x, y + 1)));
+      s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) {
+        return cmul(zr[(ptrdiff_t)p + (ptrdiff_t)dy * nx + dx], cinv(diag_at(op, x + dx, y + dy)));
+      });
     } else {
       c = zr[p];
-      if (x > 0) l = zr[p - 1];
-      if (x < nx - 1) rt = zr[p + 1];
-      if (y > 0) dn = zr[p - nx];
-      if (y < ny - 1) up = zr[p + nx];
+      s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return zr[(ptrdiff_t)p + (ptrdiff_t)dy * nx + dx]; });
     }
-    const T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
     T2 r = cmul(diag_at(op, x, y), c);
     r.x -= s.x * op.inv_h2;
     r.y -= s.y * op.inv_h2;
@@ -325,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_bnorm(const double2* __restrict__ b, siz
 }
 
 // r0 = b - A x in FP64 (stored as T in v0 slot); beta = ||r0||; decides convergence.
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double2* __restrict__ b,
                                                       const double2* __restrict__ x,
                                                       typename vec2<T>::type* __restrict__ r0, SolveState ss,
@@ -338,9 +333,7 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
   double acc = 0;
   for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
     const int y = (int)(p / nx), xx = (int)(p - (size_t)y * nx);
-    const double2 l = xx > 0 ? xr[p - 1] : d2(0, 0), rr = xx < nx - 1 ? xr[p + 1] : d2(0, 0);
-    const double2 dn = y > 0 ? xr[p - nx] : d2(0, 0), up = y < ny - 1 ? xr[p + nx] : d2(0, 0);
-    const double2 s = dadd(dadd(dadd(l, rr), dadd(dn, up)), reflect_extra(A, xx, y, l, rr, dn, up));
+    const double2 s = stencil_sum<ORD>(A, xx, y, [&](int dx, int dy) { return xr[(ptrdiff_t)p + (ptrdiff_t)dy * nx + dx]; });
     double2 ax = dmul(diag_at(A, xx, y), xr[p]);
     double2 bb = b[off + p];
     double2 r = d2(bb.x - (ax.x - s.x * A.inv_h2), bb.y - (ax.y - s.y * A.inv_h2));
@@ -416,8 +409,8 @@ template <typename T>
 void launch_apply_dot(const Op<T>& op, bool diag_precond, const void* z, void* w, const void* v0, int nrhs,
                       ArnoldiState& st, int j, int nb, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_apply_dot<T><<<dim3(nb, nrhs), NT, 0, s>>>(op, diag_precond ? 1 : 0, (const T2*)z, (T2*)w, (const T2*)v0, st, j,
-                                                nb);
+  auto k = op.order == 4 ? k_apply_dot<T, 4> : k_apply_dot<T, 2>;
+  k<<<dim3(nb, nrhs), NT, 0, s>>>(op, diag_precond ? 1 : 0, (const T2*)z, (T2*)w, (const T2*)v0, st, j, nb);
 }
 template <typename T>
 void launch_mgs(const void* V, size_t vstride, void* w, size_t N, int nrhs, int j, int i, ArnoldiState& st, int nb,
@@ -449,7 +442,8 @@ template <typename T>
 void launch_true_residual(const Op<double>& A, const double2* b, const double2* x, void* r0, int nrhs,
                           SolveState& ss, ArnoldiState& st, int nb, int maxit, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_true_residual<T><<<dim3(nb, nrhs), NT, 0, s>>>(A, b, x, (T2*)r0, ss, st, nb, maxit);
+  auto k = A.order == 4 ? k_true_residual<T, 4> : k_true_residual<T, 2>;
+  k<<<dim3(nb, nrhs), NT, 0, s>>>(A, b, x, (T2*)r0, ss, st, nb, maxit);
 }
 template <typename T>
 void launch_scale_v0(void* v0, size_t N, int nrhs, ArnoldiState& st, int nb, cudaStream_t s) {

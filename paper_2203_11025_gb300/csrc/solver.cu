@@ -826,6 +826,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
 }
 double helm_omega(helm_ctx* c) { return c->d.omega; }
 int helm_bc(helm_ctx* c) { return c->d.bc; }
+int helm_stencil(helm_ctx* c) { return c->d.stencil; }
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
   const int r = real_bytes == 8 ? ensure_work<double>(c, nrhs, c->d.coarse_its)
                                 : ensure_work<float>(c, nrhs, c->d.coarse_its);
@@ -891,6 +892,14 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   if (d.coarse_its < 1 || d.coarse_its > 32) { g_err = "coarse_its must be in 1..32"; return HELM_EINVAL; }
   if (d.nu1 < 0 || d.nu2 < 0 || d.h <= 0 || d.abc_width < 0) { g_err = "bad smoothing/mesh/layer parameter"; return HELM_EINVAL; }
   if (d.bc < HELM_BC_DIRICHLET || d.bc > HELM_BC_REPLICATE) { g_err = "bc must be a HELM_BC_* value"; return HELM_EINVAL; }
+  if (d.stencil != HELM_STENCIL_5PT && d.stencil != HELM_STENCIL_COMPACT4) {
+    g_err = "stencil must be a HELM_STENCIL_* value";
+    return HELM_EINVAL;
+  }
+  if (d.stencil == HELM_STENCIL_COMPACT4 && d.bc != HELM_BC_DIRICHLET) {
+    g_err = "the compact fourth-order stencil is built for Dirichlet boundaries only";
+    return HELM_EUNSUPPORTED;
+  }
   if (d.bc == HELM_BC_REFLECT && ((d.nx >> (d.levels - 1)) < 2 || (d.ny >> (d.levels - 1)) < 2)) {
     g_err = "reflection boundaries need the coarsest level at least 2 x 2";
     return HELM_EINVAL;
@@ -917,6 +926,7 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
     L.h = d.h * (double)(1 << l);
     L.abc_w = d.abc_width >> l;
     L.bc = d.bc;
+    L.order = d.stencil == HELM_STENCIL_COMPACT4 ? 4 : 2;
     size_t n = (size_t)L.nx * L.ny;
     L.k2f = (float*)a.take(n * 4);
     L.k2d = (double*)a.take(n * 8);
@@ -971,13 +981,24 @@ int helm_level_kappa2(helm_t h, int level, double* out) {
 }
 
 int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream) {
-  return helm_residual(h, op, level, nullptr, x, y, nrhs, dtype, stream);
+  if (op != HELM_OP_RHS) return helm_residual(h, op, level, nullptr, x, y, nrhs, dtype, stream);
+  HTRY(check_common(h, nrhs, dtype));
+  HTRY(check_level(h, level, 0));
+  if (!x || !y || x == y) { g_err = "bad vectors (y must not alias x)"; return HELM_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)nrhs * level_points(h, level) * (dtype == HELM_C32 ? 8 : 16);
+  if (h->d.stencil != HELM_STENCIL_COMPACT4) HCHECK(cudaMemcpyAsync(y, x, bytes, cudaMemcpyDeviceToDevice, s));
+  else if (dtype == HELM_C32) launch_rhs_weight<float>(op_on<float>(h, level, 0.0), x, y, nrhs, s);
+  else launch_rhs_weight<double>(op_on<double>(h, level, 0.0), x, y, nrhs, s);
+  HLAUNCH();
+  return HELM_OK;
 }
 
 int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,
                   helm_stream_t stream) {
   HTRY(check_common(h, nrhs, dtype));
   HTRY(check_level(h, level, 0));
+  if (op != HELM_OP_A && op != HELM_OP_M) { g_err = "op must be HELM_OP_A or HELM_OP_M"; return HELM_EINVAL; }
   if (!x || !r) { g_err = "null vector"; return HELM_EINVAL; }
   const double beta = (op == HELM_OP_M) ? h->d.beta : 0.0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -991,6 +1012,7 @@ int helm_jacobi(helm_t h, int op, int level, const void* b, const void* x_in, vo
                 helm_stream_t stream) {
   HTRY(check_common(h, nrhs, dtype));
   HTRY(check_level(h, level, 0));
+  if (op != HELM_OP_A && op != HELM_OP_M) { g_err = "op must be HELM_OP_A or HELM_OP_M"; return HELM_EINVAL; }
   if (!b || !x_out || x_in == x_out) { g_err = "bad vectors (x_out must not alias x_in)"; return HELM_EINVAL; }
   const double beta = (op == HELM_OP_M) ? h->d.beta : 0.0;
   cudaStream_t s = (cudaStream_t)stream;

@@ -18,17 +18,13 @@ namespace {
 
 constexpr int BX = 32, BY = 8;  // 256 threads, one point (fine or coarse) per thread
 
-template <typename T>
+template <int ORD, typename T>
 __device__ __forceinline__ typename vec2<T>::type apply_at(const Op<T>& op, const typename vec2<T>::type* u,
                                                            int x, int y) {
   typedef typename vec2<T>::type T2;
   size_t p = (size_t)y * op.nx + x;
   T2 c = u[p];
-  const T2 l = x > 0 ? u[p - 1] : czero<T2>();
-  const T2 rt = x < op.nx - 1 ? u[p + 1] : czero<T2>();
-  const T2 dn = y > 0 ? u[p - op.nx] : czero<T2>();
-  const T2 up = y < op.ny - 1 ? u[p + op.nx] : czero<T2>();
-  T2 s = cadd(cadd(cadd(l, rt), cadd(dn, up)), reflect_extra(op, x, y, l, rt, dn, up));
+  const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return u[(ptrdiff_t)p + (ptrdiff_t)dy * op.nx + dx]; });
   T2 d = diag_at(op, x, y);
   T2 r = cmul(d, c);
   r.x -= s.x * op.inv_h2;
@@ -37,7 +33,7 @@ __device__ __forceinline__ typename vec2<T>::type apply_at(const Op<T>& op, cons
 }
 
 // y = K x  (b == nullptr)   or   y = b - K x
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(256) k_apply(Op<T> op, const typename vec2<T>::type* __restrict__ x,
                                                const typename vec2<T>::type* __restrict__ b,
                                                typename vec2<T>::type* __restrict__ y, const int* active) {
@@ -46,13 +42,30 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, const typename vec2<T>:
   const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= op.nx || iy >= op.ny) return;
   const size_t N = (size_t)op.nx * op.ny, off = (size_t)rhs * N, p = (size_t)iy * op.nx + ix;
-  auto ku = apply_at(op, x + off, ix, iy);
+  auto ku = apply_at<ORD>(op, x + off, ix, iy);
   if (b) ku = csub(b[off + p], ku);
   y[off + p] = ku;
 }
 
-// x_out = x_in + w D^-1 (f - K x_in);   x_in == nullptr means a zero guess: x_out = w D^-1 f
+// Right-hand side of the compact fourth-order scheme for a source x:
+// y = (1/12) [0 1 0; 1 8 1; 0 1 0] x, zero outside the grid.
 template <typename T>
+__global__ void __launch_bounds__(256) k_rhs_weight(int nx, int ny, const typename vec2<T>::type* __restrict__ x,
+                                                    typename vec2<T>::type* __restrict__ y) {
+  typedef typename vec2<T>::type T2;
+  const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
+  if (ix >= nx || iy >= ny) return;
+  const size_t off = (size_t)blockIdx.z * nx * ny, p = off + (size_t)iy * nx + ix;
+  T2 e = czero<T2>();
+  if (ix > 0) e = cadd(e, x[p - 1]);
+  if (ix < nx - 1) e = cadd(e, x[p + 1]);
+  if (iy > 0) e = cadd(e, x[p - nx]);
+  if (iy < ny - 1) e = cadd(e, x[p + nx]);
+  y[p] = cscale(cadd(cscale(x[p], T(8)), e), T(1) / T(12));
+}
+
+// x_out = x_in + w D^-1 (f - K x_in);   x_in == nullptr means a zero guess: x_out = w D^-1 f
+template <typename T, int ORD>
 __global__ void __launch_bounds__(256) k_jacobi(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                 const typename vec2<T>::type* __restrict__ xin,
                                                 typename vec2<T>::type* __restrict__ xout, const int* active) {
@@ -63,7 +76,7 @@ __global__ void __launch_bounds__(256) k_jacobi(Op<T> op, T w, const typename ve
   if (ix >= op.nx || iy >= op.ny) return;
   const size_t N = (size_t)op.nx * op.ny, off = (size_t)rhs * N, p = (size_t)iy * op.nx + ix;
   T2 r = f[off + p];
-  if (xin) r = csub(r, apply_at(op, xin + off, ix, iy));
+  if (xin) r = csub(r, apply_at<ORD>(op, xin + off, ix, iy));
   T2 c = cscale(cmul(r, cinv(diag_at(op, ix, iy))), w);
   if (xin) c = cadd(c, xin[off + p]);
   xout[off + p] = c;
@@ -146,7 +159,7 @@ __global__ void __launch_bounds__(256) k_prolong_add(int nxc, int nyc, int nx, i
 constexpr int RR_Y = 2 * BY + 3, RR_X = 2 * BX + 3;  // v region (fine), halo 2
 constexpr int RI_Y = 2 * BY + 1, RI_X = 2 * BX + 1;  // residual region, halo 1
 
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                         const typename vec2<T>::type* __restrict__ v,
                                                         typename vec2<T>::type* __restrict__ fc,
@@ -184,10 +197,8 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typ
     if (y >= 0 && y < ny && x >= 0 && x < nx) {
       int sy = ry + 1, sx = rx + 1;
       T2 c = s_v[sy][sx];
-      T2 s = cadd(cadd(s_v[sy][sx - 1], s_v[sy][sx + 1]), cadd(s_v[sy - 1][sx], s_v[sy + 1][sx]));
-      // neighbours outside the grid hold 0 in s_v (zero padding); reflection adds the
-      // inward neighbour once more, replication lives in the diagonal
-      s = cadd(s, reflect_extra(op, x, y, s_v[sy][sx - 1], s_v[sy][sx + 1], s_v[sy - 1][sx], s_v[sy + 1][sx]));
+      // neighbours inside the grid, from the tile (boundary terms in stencil_sum / diag_at)
+      const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return s_v[sy + dy][sx + dx]; });
       T2 kv = cmul(diag_at(op, x, y), c);
       kv.x -= s.x * op.inv_h2;
       kv.y -= s.y * op.inv_h2;
@@ -220,7 +231,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typ
 // v == nullptr: v = w D^-1 f when implicit_v (the pre-smoothing result from a
 // zero guess), else v = 0.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int ORD>
 __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                         const typename vec2<T>::type* __restrict__ v,
                                                         int implicit_v, const typename vec2<T>::type* __restrict__ ec,
@@ -253,8 +264,7 @@ __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typ
   if (y < ny && x < nx) {
     const int sy = threadIdx.y + 1, sx = threadIdx.x + 1;
     T2 c = s_x[sy][sx];
-    T2 s = cadd(cadd(s_x[sy][sx - 1], s_x[sy][sx + 1]), cadd(s_x[sy - 1][sx], s_x[sy + 1][sx]));
-    s = cadd(s, reflect_extra(op, x, y, s_x[sy][sx - 1], s_x[sy][sx + 1], s_x[sy - 1][sx], s_x[sy + 1][sx]));
+    const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return s_x[sy + dy][sx + dx]; });
     T2 d = diag_at(op, x, y);
     T2 kx = cmul(d, c);
     kx.x -= s.x * op.inv_h2;
@@ -301,14 +311,20 @@ inline dim3 grid2(int nx, int ny, int nrhs) { return dim3((nx + BX - 1) / BX, (n
 template <typename T>
 void launch_apply(const Op<T>& op, const void* x, const void* b, void* y, int nrhs, const int* active, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_apply<T><<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, (const T2*)x, (const T2*)b, (T2*)y, active);
+  auto k = op.order == 4 ? k_apply<T, 4> : k_apply<T, 2>;
+  k<<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, (const T2*)x, (const T2*)b, (T2*)y, active);
+}
+template <typename T>
+void launch_rhs_weight(const Op<T>& op, const void* x, void* y, int nrhs, cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  k_rhs_weight<T><<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op.nx, op.ny, (const T2*)x, (T2*)y);
 }
 template <typename T>
 void launch_jacobi(const Op<T>& op, T w, const void* f, const void* x_in, void* x_out, int nrhs, const int* active,
                    cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_jacobi<T><<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, w, (const T2*)f, (const T2*)x_in, (T2*)x_out,
-                                                                   active);
+  auto k = op.order == 4 ? k_jacobi<T, 4> : k_jacobi<T, 2>;
+  k<<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, w, (const T2*)f, (const T2*)x_in, (T2*)x_out, active);
 }
 template <typename T>
 void launch_restrict(int nx, int ny, const void* rf, void* rc, int nrhs, const int* active, cudaStream_t s) {
@@ -325,15 +341,17 @@ template <typename T>
 void launch_resid_restrict(const Op<T>& fine, T w, const void* f, const void* v, void* fc, int nrhs,
                            const int* active, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_resid_restrict<T><<<grid2(fine.nx / 2, fine.ny / 2, nrhs), dim3(BX, BY), 0, s>>>(
-      fine, w, (const T2*)f, (const T2*)v, (T2*)fc, active);
+  auto k = fine.order == 4 ? k_resid_restrict<T, 4> : k_resid_restrict<T, 2>;
+  k<<<grid2(fine.nx / 2, fine.ny / 2, nrhs), dim3(BX, BY), 0, s>>>(fine, w, (const T2*)f, (const T2*)v, (T2*)fc,
+                                                                   active);
 }
 template <typename T>
 void launch_prolong_jacobi(const Op<T>& fine, T w, const void* f, const void* v, bool implicit_v, const void* ec,
                            int nxc, int nyc, void* out, int nrhs, const int* active, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  k_prolong_jacobi<T><<<grid2(fine.nx, fine.ny, nrhs), dim3(BX, BY), 0, s>>>(
-      fine, w, (const T2*)f, (const T2*)v, implicit_v ? 1 : 0, (const T2*)ec, nxc, nyc, (T2*)out, active);
+  auto k = fine.order == 4 ? k_prolong_jacobi<T, 4> : k_prolong_jacobi<T, 2>;
+  k<<<grid2(fine.nx, fine.ny, nrhs), dim3(BX, BY), 0, s>>>(fine, w, (const T2*)f, (const T2*)v, implicit_v ? 1 : 0,
+                                                           (const T2*)ec, nxc, nyc, (T2*)out, active);
 }
 void launch_coarsen_kappa2(const double* k2d_fine, int nx, int ny, double* k2d_coarse, float* k2f_coarse,
                            cudaStream_t s) {
@@ -345,6 +363,7 @@ void launch_widen_kappa2(const float* k2f, double* k2d, size_t n, cudaStream_t s
 
 #define INST(T)                                                                                                 \
   template void launch_apply<T>(const Op<T>&, const void*, const void*, void*, int, const int*, cudaStream_t); \
+  template void launch_rhs_weight<T>(const Op<T>&, const void*, void*, int, cudaStream_t);                    \
   template void launch_jacobi<T>(const Op<T>&, T, const void*, const void*, void*, int, const int*,            \
                                  cudaStream_t);                                                               \
   template void launch_restrict<T>(int, int, const void*, void*, int, const int*, cudaStream_t);              \

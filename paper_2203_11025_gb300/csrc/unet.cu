@@ -810,6 +810,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs);
 double helm_omega(helm_ctx* c);
 int helm_bc(helm_ctx* c);
+int helm_stencil(helm_ctx* c);
 }  // namespace helm
 
 // e = U-Net(r) (inference), with the network input built on the fly.
@@ -1269,6 +1270,10 @@ int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float*
   if (!h || !out || !x || !gout || !loss_dev || B < 1 || out == gout) {
     set_error("bad arguments");
     return HELM_EINVAL;
+  }
+  if (helm_stencil(h) != HELM_STENCIL_5PT) {
+    set_error("the residual loss is built for the 5-point stencil only");
+    return HELM_EUNSUPPORTED;
   }
   int nx, ny, abc_w;
   double hh, gmax;

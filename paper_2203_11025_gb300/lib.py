@@ -22,6 +22,8 @@ HELM_PREC_NONE, HELM_PREC_V, HELM_PREC_JU, HELM_PREC_VU = 0, 1, 2, 3
 HELM_FLAG_X0_ZERO, HELM_FLAG_HOST_IO, HELM_FLAG_NO_GRAPH, HELM_FLAG_FP64 = 1, 2, 4, 8
 HELM_DESC_MULTIKERNEL_COARSE, HELM_DESC_SINGLE_CTA_COARSE = 1, 2
 HELM_BC_DIRICHLET, HELM_BC_REFLECT, HELM_BC_REPLICATE = 0, 1, 2
+HELM_STENCIL_5PT, HELM_STENCIL_COMPACT4 = 0, 1
+HELM_OP_RHS = 2
 
 # Every symbol include/helm.h declares (checked by the CPU test suite).
 ABI_SYMBOLS = [
@@ -44,7 +46,7 @@ class helm_desc(ctypes.Structure):
                 ("beta", ctypes.c_double), ("abc_width", ctypes.c_int), ("abc_gamma_max", ctypes.c_double),
                 ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("jacobi_w", ctypes.c_double), ("coarse_its", ctypes.c_int), ("flags", ctypes.c_int),
-                ("bc", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("stencil", ctypes.c_int)]
 
 
 class unet_cfg(ctypes.Structure):
