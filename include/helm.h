@@ -10,7 +10,9 @@
  * unknowns with spacing h and zero (Dirichlet) values outside the grid; g is
  * an absorbing layer (quadratic profile, width abc_width cells, peak
  * abc_gamma_max).  The shifted Laplacian M replaces (1 - g i) by
- * (1 - (g + beta) i) (Eq. 2.4, alpha = 1).
+ * (1 - (g + beta) i) (Eq. 2.4, alpha = 1).  helm_desc.bc selects Neumann
+ * boundaries by reflection or replication padding instead, and
+ * helm_desc.stencil the compact fourth-order 9-point scheme (Sec. 2.4).
  *
  * Conventions for every entry point
  *   - Vectors are complex, interleaved (re, im), row-major [rhs][y][x];
@@ -108,10 +110,11 @@ int helm_level_kappa2(helm_t h, int level, double* out);
 
 /* y = K x on `level`, K = A (op HELM_OP_A) or M (HELM_OP_M), Eq. 2.2 / 2.4; with
  * op HELM_OP_RHS, y = the discrete right-hand side of the source x (x itself for the
- * 5-point stencil, (1/12) [0 1 0; 1 8 1; 0 1 0] x for COMPACT4); y must not alias x.
- * An op outside these is HELM_EINVAL (helm_residual and helm_jacobi take A or M). */
+ * 5-point stencil, (1/12) [0 1 0; 1 8 1; 0 1 0] x for COMPACT4).  y must not alias x
+ * (HELM_EINVAL).  An op outside these is HELM_EINVAL (helm_residual and helm_jacobi
+ * take A or M). */
 int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream);
-/* r = b - K x. */
+/* r = b - K x (op HELM_OP_A or HELM_OP_M); r must not alias b or x (HELM_EINVAL). */
 int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,
                   helm_stream_t stream);
 /* One damped Jacobi sweep x_out = x_in + w D^-1 (b - K x_in) (Sec. 4, w = desc.jacobi_w);

@@ -1000,6 +1000,7 @@ int helm_residual(helm_t h, int op, int level, const void* b, const void* x, voi
   HTRY(check_level(h, level, 0));
   if (op != HELM_OP_A && op != HELM_OP_M) { g_err = "op must be HELM_OP_A or HELM_OP_M"; return HELM_EINVAL; }
   if (!x || !r) { g_err = "null vector"; return HELM_EINVAL; }
+  if (r == x || r == b) { g_err = "the output must not alias an input"; return HELM_EINVAL; }
   const double beta = (op == HELM_OP_M) ? h->d.beta : 0.0;
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == HELM_C32) launch_apply<float>(op_on<float>(h, level, beta), x, b, r, nrhs, nullptr, s);

@@ -78,7 +78,11 @@ def test_setup_and_entry_points_reject_unsupported_combinations(lib):
         hz.residual_loss(y, x)
     v = dev(crandn(3, (1, 32, 32)), torch.complex64)
     with pytest.raises(Exception):      # helm_residual takes A or M only
-        hz.residual(v, v, op=lib.HELM_OP_RHS)
+        hz.residual(v, v.clone(), op=lib.HELM_OP_RHS)
+    with pytest.raises(Exception):      # outputs must not alias inputs
+        hz.apply(v, out=v)
+    with pytest.raises(Exception):
+        hz.residual(v, v.clone(), out=v)
 
 
 @pytest.mark.parametrize("path", [0, 1, 2])   # cluster (declines: one-CTA kernel), multi-kernel, one CTA
