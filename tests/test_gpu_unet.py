@@ -458,3 +458,22 @@ def test_solve_cycles_follow_network_buffers(lib):
     x3, i3 = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net2, tol=1e-7, maxit=3000)
     assert i3["iters"] == i1["iters"]
     assert np.allclose(x3.cpu().numpy(), x1, rtol=0, atol=1e-12 * np.abs(x1).max())
+
+
+def test_checkpoint_round_trip_reproduces_the_network(lib, tmp_path):
+    # a saved network, loaded into a fresh handle, gives bit-identical inference outputs
+    from paper_2203_11025_gb300 import checkpoint as CK
+    c, oc = make_cfgs(lib, widths=(16, 32))
+    net = lib.UNet(c, seed=21)
+    randomise(lib, net, oc, 21)
+    x = torch.from_numpy(np.random.default_rng(22).standard_normal((2, 64, 64, 4)).astype(np.float32)).cuda()
+    y0 = net.forward(x).cpu().numpy()
+    path = str(tmp_path / "net.ckpt")
+    CK.save(net, path, meta={"seed": 21})
+    net2, meta = CK.load(path)
+    assert meta == {"seed": 21}
+    y1 = net2.forward(x).cpu().numpy()
+    assert np.array_equal(y0.view(np.uint32), y1.view(np.uint32))
+    other = lib.UNet(make_cfgs(lib, widths=(8, 16))[0], seed=1)
+    with pytest.raises(ValueError):
+        CK.load_into(other, path)
