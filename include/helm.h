@@ -142,7 +142,12 @@ enum {
   HELM_FLAG_X0_ZERO = 1,   /* start from x = 0 (x content ignored)              */
   HELM_FLAG_HOST_IO = 2,   /* b and x are HOST pointers (copied in and out)      */
   HELM_FLAG_NO_GRAPH = 4,  /* launch kernels directly instead of a CUDA graph    */
-  HELM_FLAG_FP64 = 8       /* FP64 Krylov vectors and preconditioner (checking)  */
+  HELM_FLAG_FP64 = 8,      /* FP64 Krylov vectors and preconditioner (checking)  */
+  HELM_FLAG_FALLBACK_V = 16 /* U-Net preconditioners (fgmres_solve only): every
+                              right-hand side that ends above tol (the iteration
+                              cap, or a non-finite residual) is solved again with
+                              plain M_V, from its iterate (from zero if that is
+                              not finite), with the same restart, tol and maxit */
 };
 typedef struct {
   int restart;             /* m (Sec. 4: 10), 1..32                             */
@@ -159,6 +164,9 @@ typedef struct {
   double* relres;          /* optional host array [nrhs], may be NULL            */
   long long launches;      /* kernels this library launched for the solve (-1 if
                               not counted: HELM_FLAG_NO_GRAPH)                  */
+  int fallbacks;           /* right-hand sides re-solved with M_V under
+                              HELM_FLAG_FALLBACK_V (their iters count both
+                              solves; relres and status are the M_V solve's)    */
 } fgmres_result;
 
 /* Solve A x = b for nrhs right-hand sides.  b, x: complex FP64 ([rhs][y][x]),

@@ -1095,8 +1095,63 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
     bd = W.bx;
     xd = W.xx;
   }
-  int r = fp64 ? fgmres_run<double>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller)
-               : fgmres_run<float>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller);
+  auto run = [&](int pc, void* nt, const fgmres_opts& oo, fgmres_result* rs) {
+    return fp64 ? fgmres_run<double>(h, pc, nt, (const double2*)bd, (double2*)xd, nrhs, oo, rs, caller)
+                : fgmres_run<float>(h, pc, nt, (const double2*)bd, (double2*)xd, nrhs, oo, rs, caller);
+  };
+  const bool fallback =
+      (o.flags & HELM_FLAG_FALLBACK_V) && (precond == HELM_PREC_JU || precond == HELM_PREC_VU);
+  int r;
+  if (!fallback) {
+    r = run(precond, net, o, result);
+    if (result) result->fallbacks = 0;
+  } else {
+    // U-Net solve first; right-hand sides left above tol are solved again with M_V from
+    // their iterate (zeroed where it is not finite), the others finish at the first check
+    std::vector<int> it1(nrhs), it2(nrhs);
+    std::vector<double> rr1(nrhs), rr2(nrhs);
+    fgmres_result r1{}, r2{};
+    r1.iters = it1.data(); r1.relres = rr1.data();
+    r2.iters = it2.data(); r2.relres = rr2.data();
+    r = run(precond, net, o, &r1);
+    if (r < 0 && r != HELM_ENAN) return r;
+    const size_t N = (size_t)h->d.nx * h->d.ny;
+    int nfail = 0;
+    for (int k = 0; k < nrhs; ++k) {
+      if (rr1[k] <= o.tol) continue;
+      ++nfail;
+      if (!std::isfinite(rr1[k])) HCHECK(cudaMemsetAsync((double2*)xd + (size_t)k * N, 0, N * 16, caller));
+    }
+    fgmres_result fin = r1;
+    if (nfail) {
+      fgmres_opts o2 = o;
+      o2.flags &= ~(HELM_FLAG_X0_ZERO | HELM_FLAG_HOST_IO | HELM_FLAG_FALLBACK_V);
+      r = run(HELM_PREC_V, nullptr, o2, &r2);
+      if (r < 0 && r != HELM_ENAN) return r;
+      fin = r2;
+      fin.cycles = r1.cycles + r2.cycles;
+      fin.launches = (r1.launches < 0 || r2.launches < 0) ? -1 : r1.launches + r2.launches;
+      fin.iters_max = 0;
+      for (int k = 0; k < nrhs; ++k) {
+        it2[k] += it1[k];
+        fin.iters_max = std::max(fin.iters_max, it2[k]);
+      }
+    }
+    if (result) {
+      const std::vector<int>& it = nfail ? it2 : it1;
+      const std::vector<double>& rr = nfail ? rr2 : rr1;
+      for (int k = 0; k < nrhs; ++k) {
+        if (result->iters) result->iters[k] = it[k];
+        if (result->relres) result->relres[k] = rr[k];
+      }
+      result->iters_max = fin.iters_max;
+      result->cycles = fin.cycles;
+      result->relres_max = fin.relres_max;
+      result->status = fin.status;
+      result->launches = fin.launches;
+      result->fallbacks = nfail;
+    }
+  }
   if (r < 0 && r != HELM_ENAN) return r;
   if (o.flags & HELM_FLAG_HOST_IO) {
     HCHECK(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, caller));
@@ -1111,6 +1166,7 @@ int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int 
   if (!b || !x || !opts) { g_err = "null argument"; return HELM_EINVAL; }
   fgmres_opts o = *opts;
   if (nrhs > 16) { g_err = "block size (nrhs) must be at most 16"; return HELM_EINVAL; }
+  if (o.flags & HELM_FLAG_FALLBACK_V) { g_err = "HELM_FLAG_FALLBACK_V is for fgmres_solve"; return HELM_EUNSUPPORTED; }
   if (o.restart < 1 || o.restart > 32 || (o.restart + 1) * nrhs * nrhs > 4608) {
     g_err = "restart must be in 1..32 with (restart + 1) nrhs^2 <= 4608";
     return HELM_EINVAL;

@@ -20,6 +20,7 @@ HELM_OP_A, HELM_OP_M = 0, 1
 HELM_C32, HELM_C64 = 0, 1
 HELM_PREC_NONE, HELM_PREC_V, HELM_PREC_JU, HELM_PREC_VU = 0, 1, 2, 3
 HELM_FLAG_X0_ZERO, HELM_FLAG_HOST_IO, HELM_FLAG_NO_GRAPH, HELM_FLAG_FP64 = 1, 2, 4, 8
+HELM_FLAG_FALLBACK_V = 16
 HELM_DESC_MULTIKERNEL_COARSE, HELM_DESC_SINGLE_CTA_COARSE = 1, 2
 HELM_BC_DIRICHLET, HELM_BC_REFLECT, HELM_BC_REPLICATE = 0, 1, 2
 HELM_STENCIL_5PT, HELM_STENCIL_COMPACT4 = 0, 1
@@ -63,7 +64,8 @@ class fgmres_opts(ctypes.Structure):
 class fgmres_result(ctypes.Structure):
     _fields_ = [("iters_max", ctypes.c_int), ("cycles", ctypes.c_int), ("relres_max", ctypes.c_double),
                 ("status", ctypes.c_int), ("iters", ctypes.POINTER(ctypes.c_int)),
-                ("relres", ctypes.POINTER(ctypes.c_double)), ("launches", ctypes.c_longlong)]
+                ("relres", ctypes.POINTER(ctypes.c_double)), ("launches", ctypes.c_longlong),
+                ("fallbacks", ctypes.c_int)]
 
 
 _lib = None
@@ -368,7 +370,8 @@ class Helmholtz:
                      _stream(stream))
         _check(code, "bfgmres_solve" if block else "fgmres_solve", ok=(HELM_OK, HELM_MAXIT))
         return x, {"status": code, "iters": list(iters), "relres": list(relres), "iters_max": res.iters_max,
-                   "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches}
+                   "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches,
+                   "fallbacks": res.fallbacks}
 
 
 def unet_cfg_default(kind=UNET_STANDALONE):

@@ -477,3 +477,33 @@ def test_checkpoint_round_trip_reproduces_the_network(lib, tmp_path):
     other = lib.UNet(make_cfgs(lib, widths=(8, 16))[0], seed=1)
     with pytest.raises(ValueError):
         CK.load_into(other, path)
+
+
+def test_fallback_to_plain_sl_when_the_network_fails(lib):
+    # plain SL-FGMRES stays as the fallback of the network: with HELM_FLAG_FALLBACK_V a solve
+    # whose U-Net preconditioner breaks (here a network that returns NaN) is finished by M_V
+    n = 64
+    hz, prob = _helm(lib, n)
+    c, oc = make_cfgs(lib, widths=(16, 32))
+    net = lib.UNet(c, seed=5)
+    net.set_params(np.full(net.n_params, np.nan, np.float32))
+    b = torch.from_numpy(synth.complex_normal(41, (2, n, n))).cuda()
+    with pytest.raises(lib.HelmError) as e:
+        hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, maxit=40)
+    assert e.value.code == lib.HELM_ENAN
+    x, info = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=net, maxit=2000, flags=lib.HELM_FLAG_FALLBACK_V)
+    assert info["status"] == lib.HELM_OK and info["fallbacks"] == 2
+    _, ref = hz.fgmres(b, precond=lib.HELM_PREC_V, maxit=2000)
+    x = x.cpu().numpy()
+    bb = b.cpu().numpy()
+    for k in range(2):
+        assert np.linalg.norm(H.residual(prob.A, bb[k], x[k])) <= 1e-7 * np.linalg.norm(bb[k])
+        assert info["iters"][k] > ref["iters"][k]          # the failed attempt's steps are counted too
+    # a working network (here a silent one: M_VU acts as M_V) needs no fallback
+    good = lib.UNet(c, seed=6)
+    P, _ = randomise(lib, good, oc, 6)
+    P["up1"][:] = 0.0
+    P["up1.bias"][:] = 0.0
+    good.set_params(PR.flatten_params(oc, P))
+    _, info = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=good, maxit=2000, flags=lib.HELM_FLAG_FALLBACK_V)
+    assert info["status"] == lib.HELM_OK and info["fallbacks"] == 0
