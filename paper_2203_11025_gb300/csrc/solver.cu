@@ -1187,6 +1187,7 @@ int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int 
     bd = W.bx;
     xd = W.xx;
   }
+  if (result) result->fallbacks = 0;
   int r = fp64 ? bfgmres_run<double>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller)
                : bfgmres_run<float>(h, precond, net, (const double2*)bd, (double2*)xd, nrhs, o, result, caller);
   if (r < 0 && r != HELM_ENAN) return r;
