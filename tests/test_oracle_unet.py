@@ -224,3 +224,85 @@ def test_residual_loss_vanishes_at_the_error():
     y = np.stack([e.real, e.imag], axis=-1)[None]
     loss, g = PR.residual_loss(prob, y, x)
     assert loss <= 1e-20 * np.sum(x[..., :2] ** 2) and np.abs(g).max() <= 1e-9
+
+
+# ---------------------------------------------------------------- preconditioners and pairs
+def _precond_problem(n=16, seed=11):
+    k2 = _rng(seed).uniform(0.25, 1.0, (n, n))
+    return H.Problem(k2, omega=0.2 * np.pi * n, h=1.0 / n, abc_width=3, levels=2)
+
+
+def _net(seed, silent=False):
+    cfg = _tiny()
+    P = U.init_params(cfg, seed)
+    S = U.init_bn_stats(cfg)
+    if silent:
+        P["up1"][:] = 0.0
+        P["up1.bias"][:] = 0.0
+    return cfg, P, S
+
+
+def _crandn(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def test_silent_network_reduces_the_preconditioners_to_their_multigrid_parts():
+    """A network whose output layer is zero returns 0: M_VU (Eq. 3.4) is then the SL
+    V-cycle from zero (M_V), and M_JU (Alg. 2) two damped Jacobi sweeps on A."""
+    from oracle import precond as PR
+    prob = _precond_problem()
+    cfg, P, S = _net(1, silent=True)
+    r = _crandn(_rng(12), (2, 16, 16))
+    assert np.array_equal(PR.unet_apply(prob, cfg, P, S, r), np.zeros_like(r))
+    vu = PR.precond_vu(prob, cfg, P, S, r)
+    ju = PR.precond_ju(prob, cfg, P, S, r)
+    w = prob.jacobi_w
+    for k in range(2):
+        assert np.allclose(vu[k], H.vcycle(prob, r[k]), rtol=1e-14, atol=0)
+        e1 = H.jacobi(prob.A, np.zeros_like(r[k]), r[k], w)
+        assert np.allclose(ju[k], H.jacobi(prob.A, e1, r[k], w), rtol=1e-14, atol=0)
+
+
+def test_network_preconditioner_is_positively_homogeneous():
+    """The input is h^2 r / s with s = RMS(h^2 r) and the output is scaled back by s, so
+    U-Net(c r) = c U-Net(r) for c > 0, whatever the weights; M_VU and M_JU inherit it
+    (their multigrid parts are linear)."""
+    from oracle import precond as PR
+    prob = _precond_problem()
+    cfg, P, S = _net(2)
+    r = _crandn(_rng(13), (2, 16, 16))
+    for c in (1e-6, 3.7, 1e5):
+        assert np.allclose(PR.unet_apply(prob, cfg, P, S, c * r), c * PR.unet_apply(prob, cfg, P, S, r), rtol=1e-9)
+        assert np.allclose(PR.precond_vu(prob, cfg, P, S, c * r), c * PR.precond_vu(prob, cfg, P, S, r), rtol=1e-9)
+        assert np.allclose(PR.precond_ju(prob, cfg, P, S, c * r), c * PR.precond_ju(prob, cfg, P, S, r), rtol=1e-9)
+    # and not in the phase: the network sees Re and Im as separate channels
+    assert not np.allclose(PR.unet_apply(prob, cfg, P, S, 1j * r), 1j * PR.unet_apply(prob, cfg, P, S, r))
+
+
+def test_network_input_channels():
+    """Channels 0-1 of the input have unit mean square per sample; 2-3 carry the medium;
+    a zero residual gives a zero input (s = 1)."""
+    lv = _precond_problem().A
+    r = _crandn(_rng(14), (3, 16, 16)) * np.array([1e-3, 1.0, 1e4])[:, None, None]
+    r[1] = 0.0
+    x, s = U.make_input(r, lv.kappa2, lv.gamma, lv.h)
+    ms = np.mean(x[..., 0] ** 2 + x[..., 1] ** 2, axis=(1, 2))
+    assert np.allclose(ms[[0, 2]], 1.0, rtol=1e-12) and ms[1] == 0.0 and s[1] == 1.0
+    assert np.allclose(s[0], lv.h ** 2 * np.sqrt(np.mean(np.abs(r[0]) ** 2)), rtol=1e-12)
+    assert np.array_equal(x[0, ..., 2], lv.kappa2) and np.array_equal(x[2, ..., 3], lv.gamma)
+
+
+def test_generated_pairs_satisfy_the_error_equation():
+    """Eq. 3.8-3.9: A e = r for every pair; k = 0 leaves x~ = 0 (r = A x, e = x); the
+    FGMRES residual, and so ||r||, does not grow with k."""
+    from oracle import precond as PR
+    prob = _precond_problem()
+    x = np.repeat(_crandn(_rng(15), (1, 16, 16)), 6, axis=0)
+    ks = np.array([0, 1, 3, 9, 10, 14])
+    r, e = PR.gen_pairs(prob, x, ks)
+    for j in range(len(ks)):
+        assert np.allclose(H.apply_op(prob.A, e[j]), r[j], rtol=1e-10, atol=1e-10 * np.abs(r[j]).max())
+    assert np.array_equal(e[0], x[0]) and np.allclose(r[0], H.apply_op(prob.A, x[0]))
+    norms = [np.linalg.norm(r[j]) for j in range(len(ks))]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(norms, norms[1:]))
+    assert norms[-1] < 0.5 * norms[0]
