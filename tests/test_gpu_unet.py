@@ -507,3 +507,36 @@ def test_fallback_to_plain_sl_when_the_network_fails(lib):
     good.set_params(PR.flatten_params(oc, P))
     _, info = hz.fgmres(b, precond=lib.HELM_PREC_VU, net=good, maxit=2000, flags=lib.HELM_FLAG_FALLBACK_V)
     assert info["status"] == lib.HELM_OK and info["fallbacks"] == 0
+
+
+@pytest.mark.slow
+def test_trained_network_gains_over_plain_sl(lib):
+    # what the learned part buys: a network trained with the benchmark's single-model recipe
+    # (Sec. 4: Eq. 3.8-3.9 pairs of one 256^2 medium from the library's SL-FGMRES, MSE of
+    # Eq. 3.7, Adam) makes FGMRES + M_VU converge in far fewer iterations than FGMRES + M_V
+    # on right-hand sides it never saw (point sources and Gaussian noise); every solution is
+    # checked by the oracle's FP64 residual
+    import bench
+    from paper_2203_11025_gb300 import train as T
+    n = 256
+    k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
+    hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+    d = hz.desc
+    prob = H.Problem(k2.astype(np.float64), omega=d.omega, h=d.h, abc_width=d.abc_width, levels=d.levels)
+    net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=7)
+    pairs = hz.gen_pairs(bench.TRAIN_PAIRS, 5151, 10)
+    T.train(hz, net, pairs=pairs, epochs=bench.TRAIN_EPOCHS, batch=16, lr=bench.TRAIN_LR, seed=11)
+    del pairs
+    pos = synth.source_positions(n, n, 4, synth.rhs_seed(7), 16)
+    b = np.concatenate([synth.point_sources(n, n, pos, 1.0 / n), synth.complex_normal(77, (4, n, n))])
+    bt = torch.from_numpy(b).cuda()
+    _, iv = hz.fgmres(bt, precond=lib.HELM_PREC_V, tol=1e-7, maxit=20000)
+    x, iu = hz.fgmres(bt, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=20000)
+    assert iv["status"] == lib.HELM_OK and iu["status"] == lib.HELM_OK
+    for k in range(4):      # point sources, the benchmark's kind: at least twice as fast
+        assert iu["iters"][k] <= 0.5 * iv["iters"][k], (k, iu["iters"], iv["iters"])
+    for k in range(4, 8):   # white-noise right-hand sides, unlike the training residuals: still fewer
+        assert iu["iters"][k] < iv["iters"][k], (k, iu["iters"], iv["iters"])
+    x = x.cpu().numpy()
+    for k in range(8):
+        assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])
