@@ -36,3 +36,17 @@ def test_matches_the_oracle_solve():
     assert abs(rho - H.convergence_factor(res.true_history[0], res.true_history[-1], res.iters)) < 1e-14
     assert 0.0 < rho < 1.0 and rho ** res.iters <= 1e-7 * (1 + 1e-9)
     assert M.iterations_for_reduction(rho) <= res.iters
+
+
+def test_jsonl_log_round_trip(tmp_path):
+    path = str(tmp_path / "run.jsonl")
+    log = M.JsonlLog(path)
+    info = {"status": 0, "iters": [35, 30], "relres": [9e-8, 8e-8], "fallbacks": 0}
+    log.solve("M_VU", info, seconds=0.021)
+    log.epoch("epoch 0 lr 1.00e-03 loss 12.5")
+    recs = M.read_jsonl(path)
+    assert [r["kind"] for r in recs] == ["solve", "train"]
+    s = recs[0]
+    assert s["label"] == "M_VU" and s["iters"] == [35, 30] and "fallbacks" not in s
+    assert abs(s["rho_max"] - max(9e-8 ** (1 / 35), 8e-8 ** (1 / 30))) < 1e-15
+    assert abs(s["ms_per_iteration"] - 21.0 / 35) < 1e-12 and s["t"] > 0
