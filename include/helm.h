@@ -208,7 +208,8 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
  * callers cannot call cudaMalloc: code that runs while a CUDA graph is being
  * captured, real-time loops that must not trigger the implicit device-wide
  * synchronisation of cudaMalloc/cudaFree, and hosts whose memory budget is
- * fixed up front.  They pass the coarse problem itself -- nx x ny grid, mesh
+ * fixed up front.  The operator is the 5-point stencil with Dirichlet
+ * boundaries.  They pass the coarse problem itself -- nx x ny grid, mesh
  * width h, omega, shift beta, layer width (in this grid's cells) and peak,
  * kappa2 (device float32 [ny][nx]) -- and complex64 right-hand sides f and
  * outputs x ([nrhs][ny][nx], device, distinct); the Krylov basis lives in a
