@@ -11,7 +11,7 @@ unknown (iy, ix) at node index (iy, ix); values outside the grid are zero
 pads the operator's stencil by reflection or replication instead (Neumann, Sec. 2.4),
 while the transfer kernels of Eq. 2.9 keep their zero padding.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * A = L - w^2 k^2 (1 - g i) with L the 5-point negative Laplacian (Eq. 2.1,
     2.2); the shifted Laplacian is M = L - w^2 k^2 (1 - (g + beta) i)
     (Eq. 2.4 with alpha = 1, the shift added to the attenuation).
