@@ -25,6 +25,11 @@ Readings of points the paper leaves open:
     only on breakdown), no relaxation on that level.
   * Prolongation: the transposed stride-2 convolution with output size n
     (Eq. 2.9), so that R = P^T / 4 exactly.
+  * Neumann padding: "reflect" mirrors about the boundary node (ghost u_-1 = u_1),
+    "replicate" copies it (ghost u_-1 = u_0); every level carries the mode.
+  * Higher-order operator (Level.order = 4): the compact fourth-order 9-point
+    scheme, K u = L9 u - (1/12) M5 (m u) with right-hand side (1/12) M5 f (derived
+    with the definitions below), rediscretised on every level.
 """
 from __future__ import annotations
 
