@@ -12,6 +12,8 @@
                                                            # for block sizes 1..16 and restarts 5, 10, 20
   python -m paper_2203_11025_gb300.profcase block 256 8    # one block FGMRES(10) cycle with M_V
   python -m paper_2203_11025_gb300.profcase resloss 256 16 # the residual loss of a batch of 16
+  python -m paper_2203_11025_gb300.profcase variants 1024 8 # stencil-kernel times and the M_V solve per
+                                                           # boundary mode and stencil
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -128,6 +130,31 @@ def main(argv):
                     print(json.dumps({"restart": m, "rhs": bs, "block": block, "iters": info["iters_max"],
                                       "ms": round(e0.elapsed_time(e1), 2), "relres_max": info["relres_max"]}))
                 bs *= 2
+    elif what == "variants":
+        # boundary modes and stencils side by side: per-launch time and algorithmic GB/s of
+        # the stencil kernels (helm_time_kernel 0-3) and the M_V solve of b point sources
+        import json
+        k2 = torch.from_numpy(synth.grf_kappa2(n, n, synth.medium_seed(0))).cuda()
+        pos = synth.source_positions(n, n, b, synth.rhs_seed(0), 16)
+        rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n).astype(np.complex128)).cuda()
+        for bc, st in ((lib.HELM_BC_DIRICHLET, lib.HELM_STENCIL_5PT), (lib.HELM_BC_REFLECT, lib.HELM_STENCIL_5PT),
+                       (lib.HELM_BC_REPLICATE, lib.HELM_STENCIL_5PT),
+                       (lib.HELM_BC_DIRICHLET, lib.HELM_STENCIL_COMPACT4)):
+            hz = lib.Helmholtz(k2, bc=bc, stencil=st)
+            rec = {"bc": bc, "stencil": st}
+            for kern in range(4):
+                ms, nbytes = hz.time_kernel(kern, b, reps=50)
+                rec[f"kernel{kern}_us"] = round(ms * 1e3, 2)
+                rec[f"kernel{kern}_gbs"] = round(nbytes / (ms * 1e-3) / 1e9, 1) if nbytes else None
+            hz.fgmres(rhs, tol=1e-7, maxit=20000)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = hz.fgmres(rhs, tol=1e-7, maxit=20000)
+            e1.record()
+            e1.synchronize()
+            rec.update({"mv_ms": round(e0.elapsed_time(e1), 2), "mv_iters": info["iters_max"]})
+            print(json.dumps(rec), flush=True)
+            hz.close()
     else:
         raise SystemExit(f"unknown case {what}")
 
