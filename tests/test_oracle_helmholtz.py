@@ -34,6 +34,13 @@ def test_stencil_matches_printed_kernel():
     assert np.allclose(off, gold, atol=1e-14)
     k2, g = lv.kappa2[4, 5], lv.gamma[4, 5]
     assert np.isclose(centre, 4 - lv.omega ** 2 * k2 * lv.h ** 2 * (1 - g * 1j), rtol=1e-14)
+    # a node inside the absorbing layer (g > 0): the attenuation enters as (1 - g i)
+    u = np.zeros((9, 11), complex)
+    u[1, 5] = 1.0
+    k2, g = lv.kappa2[1, 5], lv.gamma[1, 5]
+    assert g > 0
+    c = (H.apply_op(lv, u) * lv.h ** 2)[1, 5]
+    assert np.isclose(c, 4 - lv.omega ** 2 * k2 * lv.h ** 2 * (1 - g * 1j), rtol=1e-14)
 
 
 def test_apply_matches_nodewise_assembly():
