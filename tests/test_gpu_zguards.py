@@ -5,7 +5,6 @@ every boundary mode and both stencils, FP32 and FP64 vectors.  (Reads out of bou
 not visible this way; the parity tests compare every written value.)"""
 import math
 
-import numpy as np
 import pytest
 
 from gpu_util import crandn, medium
