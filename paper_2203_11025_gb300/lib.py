@@ -198,6 +198,23 @@ def helm_coarse_solve_static(nx, ny, h, omega, beta, abc_width, gamma_max, kappa
     return x
 
 
+_NAMED = {
+    "bc": {"dirichlet": HELM_BC_DIRICHLET, "reflect": HELM_BC_REFLECT, "replicate": HELM_BC_REPLICATE},
+    "stencil": {"5pt": HELM_STENCIL_5PT, "compact4": HELM_STENCIL_COMPACT4},
+}
+
+
+def desc_value(field: str, value):
+    """A helm_desc field value; `bc` and `stencil` also accept their names
+    ("dirichlet", "reflect", "replicate"; "5pt", "compact4")."""
+    if isinstance(value, str):
+        names = _NAMED.get(field)
+        if names is None or value not in names:
+            raise ValueError(f"unknown value {value!r} for helm_desc.{field}")
+        return names[value]
+    return value
+
+
 class Helmholtz:
     """A solver handle: medium kappa^2 (float32 CUDA tensor [ny, nx]) plus desc."""
 
@@ -208,7 +225,7 @@ class Helmholtz:
         ny, nx = kappa2.shape
         self.desc = desc if desc is not None else helm_desc_default(nx, ny)
         for k, v in overrides.items():
-            setattr(self.desc, k, v)
+            setattr(self.desc, k, desc_value(k, v))
         self.kappa2 = kappa2.contiguous()
         self.h = helm_setup(self.desc, self.kappa2)
         self.lib = load()

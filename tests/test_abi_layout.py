@@ -62,3 +62,14 @@ def test_struct_layout_matches(probe, struct):
     assert int(probe[f"sizeof.{struct}"]) == ctypes.sizeof(cls)
     for fname, *_ in cls._fields_:
         assert int(probe[f"{struct}.{fname}"]) == getattr(cls, fname).offset, f"{struct}.{fname}"
+
+
+def test_named_desc_values():
+    lib = _binding()
+    assert lib.desc_value("bc", "reflect") == lib.HELM_BC_REFLECT
+    assert lib.desc_value("stencil", "compact4") == lib.HELM_STENCIL_COMPACT4
+    assert lib.desc_value("levels", 4) == 4
+    with pytest.raises(ValueError):
+        lib.desc_value("bc", "periodic")
+    with pytest.raises(ValueError):
+        lib.desc_value("levels", "three")
