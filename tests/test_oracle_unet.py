@@ -306,3 +306,32 @@ def test_generated_pairs_satisfy_the_error_equation():
     norms = [np.linalg.norm(r[j]) for j in range(len(ks))]
     assert all(b <= a * (1 + 1e-12) for a, b in zip(norms, norms[1:]))
     assert norms[-1] < 0.5 * norms[0]
+
+
+def test_solver_with_silent_context_is_the_standalone_network():
+    """Eq. 3.5: the solver network sees cat(own channels, f^(l)) at every level.  With the
+    weights on the context channels zero, it equals the standalone network built from its
+    other weights, whatever the encoder features are."""
+    ctx = (3, 5, 6)
+    solver = U.UNetConfig(in_ch=4, out_ch=2, widths=(4, 8), coarse_resnets=2, context=ctx)
+    plain = _tiny()
+    Pp = U.init_params(plain, 4)
+    S = U.init_bn_stats(plain)
+    rng = _rng(31)
+    for k in S:
+        S[k] = 0.1 * rng.standard_normal(S[k].shape) if k.endswith(".mean") else rng.uniform(0.5, 2.0, S[k].shape)
+    Ps = dict(Pp)
+    convs_s, _ = U.layer_specs(solver)
+    convs_p = {c[0]: c for c in U.layer_specs(plain)[0]}
+    for name, kind, k, cin, cout in convs_s:
+        cin_plain = convs_p[name][3]
+        W = np.zeros((k, k, cin, cout))
+        W[:, :, :cin_plain, :] = Pp[name]
+        Ps[name] = W
+    x = rng.standard_normal((2, 8, 8, 4))
+    feats = [rng.standard_normal((2, 8 >> l, 8 >> l, c)) for l, c in enumerate(ctx)]
+    out_s, _, _, _ = U.forward(solver, Ps, S, x, train=False, feats=feats)
+    out_p, _, _, _ = U.forward(plain, Pp, S, x, train=False)
+    assert np.allclose(out_s, out_p, rtol=1e-13, atol=1e-13)
+    Ps["down1"][:, :, 4:, :] = 1.0              # and the context does enter once its weights do
+    assert not np.allclose(U.forward(solver, Ps, S, x, train=False, feats=feats)[0], out_p)
