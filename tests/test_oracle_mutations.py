@@ -79,6 +79,10 @@ def _unweighted_coarse_medium(mp):
     mp.setattr(H, "coarsen_kappa2", lambda k2: k2[::2, ::2].copy())     # injection, not full weighting
 
 
+def _inner_product_without_conjugate(mp):
+    mp.setattr(H, "_dot", lambda u, v: complex(np.sum(u.ravel() * v.ravel())))
+
+
 def _elu_without_minus_one(mp):
     mp.setattr(U, "elu", lambda x: np.where(x > 0, x, np.exp(np.minimum(x, 0.0))))
 
@@ -126,6 +130,10 @@ CASES = [
     ("Givens rotation without the phase", _givens_without_phase, TH.test_givens_least_squares_matches_lstsq, ()),
     ("coarse-grid correction subtracted", _coarse_correction_subtracted, TH.test_two_grid_poisson_contracts, ()),
     ("coarse medium by injection", _unweighted_coarse_medium, TH.test_coarse_medium_is_weighted_average, ()),
+    ("Arnoldi inner product without the conjugate", _inner_product_without_conjugate,
+     TH.test_gmres_minimises_over_explicit_krylov_space, ()),
+    ("Arnoldi inner product without the conjugate (FGMRES)", _inner_product_without_conjugate,
+     TH.test_fgmres_estimates_monotone_and_match_true_residual, ()),
     ("eLU without the -1", _elu_without_minus_one, TU.test_elu_values, ()),
     ("BatchNorm backward without the mean term", _bn_backward_without_mean_term,
      TU.test_backward_matches_finite_differences, ()),
