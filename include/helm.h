@@ -103,9 +103,11 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
 void helm_destroy(helm_t h);
 const char* helm_last_error(void);
 
-/* Level sizes (level 0 = fine grid). */
+/* Level sizes of the multigrid hierarchy (Sec. 2.2: H = 2h per level; level 0 = fine grid).
+ * HELM_EINVAL for a level outside 0..levels-1. */
 int helm_level_shape(helm_t h, int level, int* nx, int* ny);
-/* Copy the level's kappa^2 (float64, [ny][nx]) into a device buffer. */
+/* Copy the level's kappa^2 (the rediscretised medium of Sec. 2.2; float64, [ny][nx]) into
+ * a caller-owned device buffer. */
 int helm_level_kappa2(helm_t h, int level, double* out);
 
 /* y = K x on `level`, K = A (op HELM_OP_A) or M (HELM_OP_M), Eq. 2.2 / 2.4; with
@@ -114,7 +116,8 @@ int helm_level_kappa2(helm_t h, int level, double* out);
  * (HELM_EINVAL).  An op outside these is HELM_EINVAL (helm_residual and helm_jacobi
  * take A or M). */
 int helm_apply(helm_t h, int op, int level, const void* x, void* y, int nrhs, int dtype, helm_stream_t stream);
-/* r = b - K x (op HELM_OP_A or HELM_OP_M); r must not alias b or x (HELM_EINVAL). */
+/* r = b - K x (Eq. 2.2 / 2.4; op HELM_OP_A or HELM_OP_M); r must not alias b or x
+ * (HELM_EINVAL). */
 int helm_residual(helm_t h, int op, int level, const void* b, const void* x, void* r, int nrhs, int dtype,
                   helm_stream_t stream);
 /* One damped Jacobi sweep x_out = x_in + w D^-1 (b - K x_in) (Sec. 4, w = desc.jacobi_w);
@@ -169,7 +172,8 @@ typedef struct {
                               solves; relres and status are the M_V solve's)    */
 } fgmres_result;
 
-/* Solve A x = b for nrhs right-hand sides.  b, x: complex FP64 ([rhs][y][x]),
+/* Solve A x = b (Eq. 2.5, FGMRES(m) of Sec. 2.2 and 4) for nrhs right-hand sides, each
+ * with its own Krylov space.  b, x: complex FP64 ([rhs][y][x]),
  * device pointers unless HELM_FLAG_HOST_IO.  x holds x0 on entry (unless
  * HELM_FLAG_X0_ZERO) and the solution on return.  precond: HELM_PREC_V
  * (one SL V-cycle, M_V), HELM_PREC_NONE, or a U-Net preconditioner (needs

@@ -47,13 +47,24 @@ enum { UNET_FLAG_SIMT = 1, UNET_FLAG_NO_TMA = 2 };
 
 enum { UNET_STANDALONE = 0, UNET_ENCODER = 1, UNET_SOLVER = 2 };
 
-/* Defaults of the given kind; UNET_SOLVER fills `context` for the default encoder. */
+/* Defaults of the given kind: the U-Net of Sec. 3.1 (Eq. 3.1-3.3; 4 levels, 32-256
+ * channels, 3 ResNet blocks at the coarsest level), the encoder of Sec. 3.3, or the solver
+ * with context channels (Eq. 3.5; `context` filled for the default encoder).  HELM_EINVAL
+ * for a NULL cfg; a kind other than UNET_ENCODER or UNET_SOLVER gives the standalone net. */
 int unet_cfg_default(unet_cfg* cfg, int kind);
-/* Create a network with He-normal weights drawn from `seed` (SplitMix64 +
- * Box-Muller), BN gamma 1, beta 0, running mean 0, var 1. */
+/* Create the network of cfg (Sec. 3.1; Eq. 3.5 with context channels) with He-normal
+ * weights drawn from `seed` (SplitMix64 + Box-Muller; the paper gives no initialisation),
+ * BN gamma 1, beta 0, running mean 0, var 1.  The handle owns its device memory; free it
+ * with unet_destroy.  HELM_EINVAL for a bad cfg; an error code (message in
+ * helm_last_error) if a device allocation fails. */
 int unet_create(const unet_cfg* cfg, unsigned long long seed, unet_t* out);
 void unet_destroy(unet_t net);
-/* Sizes of the flat parameter vector and of the BN running-stat vector (means then vars). */
+/* Network state (no counterpart in the paper: access for checkpoints and tests).  Sizes
+ * of the flat FP32 parameter vector (convolution weights [ky][kx][cin][cout] layer by layer,
+ * the output bias, then BN gamma/beta per layer) and of the BN running-stat vector (means
+ * then variances).  set/get copy between that layout and caller-owned HOST arrays of exactly
+ * n elements (HELM_EINVAL otherwise); set also refreshes the BF16 working copies.  The
+ * copies are synchronous. */
 int unet_sizes(unet_t net, long long* n_params, long long* n_bn);
 int unet_set_params(unet_t net, const float* host, long long n);
 int unet_get_params(unet_t net, float* host, long long n);
@@ -62,11 +73,13 @@ int unet_get_bn_stats(unet_t net, float* host, long long n);
 /* Synchronise and report a failure recorded by a tensor-core kernel (a bounded
  * wait that expired): 0 if none.  Clears the record. */
 int unet_status(unet_t net, int* failed);
-/* Parameter gradients accumulated since the last unet_zero_grad (flat, host). */
+/* Parameter gradients of the training loss (Sec. 3.4, Eq. 3.7) accumulated since the last
+ * unet_zero_grad, in the flat parameter layout, into a HOST array of n elements. */
 int unet_get_grads(unet_t net, float* host, long long n);
 int unet_zero_grad(unet_t net, helm_stream_t stream);
 
-/* Forward pass on x (device float32 [B][ny][nx][in_ch]) into out (device float32
+/* Forward pass (Eq. 3.1-3.3; Eq. 3.5 for a solver with context) on x (device float32
+ * [B][ny][nx][in_ch]) into out (device float32
  * [B][ny][nx][out_ch]).  train != 0 uses batch statistics, updates the running
  * statistics and keeps what unet_backward needs.  A solver with context reads
  * the features of its attached encoder's last forward (unet_attach_encoder).
@@ -74,7 +87,8 @@ int unet_zero_grad(unet_t net, helm_stream_t stream);
  * (HELM_EUNSUPPORTED otherwise, also from unet_precond and the U-Net preconditioned
  * solves). */
 int unet_forward(unet_t net, const float* x, float* out, int B, int ny, int nx, int train, helm_stream_t stream);
-/* Backward of the last train-mode forward for the loss sum(gout * out): adds
+/* Backward of the last train-mode forward (the gradients of Sec. 3.4's training) for the
+ * loss sum(gout * out): adds
  * parameter gradients; writes d loss / d x into gx if not null (device float32
  * like x).  A solver with an attached encoder also back-propagates into the
  * encoder (whose own last forward must be train-mode). */
@@ -93,10 +107,12 @@ int unet_mse(const float* out, const float* target, long long n, int B, float* g
  * handle with the compact fourth-order stencil. */
 int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float* gout, float* loss_dev,
                        helm_stream_t stream);
-/* One Adam step (bias-corrected) on every parameter of net (and of its attached encoder). */
+/* One Adam step (Sec. 3.4 and 4: the paper trains with Adam), bias-corrected, on every
+ * parameter of net (and of its attached encoder), from the accumulated gradients. */
 int unet_adam_step(unet_t net, float lr, float beta1, float beta2, float eps, helm_stream_t stream);
 
-/* Attach an encoder to a solver net built with context channels; detach with NULL. */
+/* Attach an encoder (Sec. 3.3) to a solver net built with context channels (Eq. 3.5);
+ * detach with NULL.  HELM_EINVAL if the encoder's feature channels do not match. */
 int unet_attach_encoder(unet_t solver, unet_t encoder);
 /* Run the attached encoder on the medium of h (kappa^2 and the layer
  * attenuation of the fine grid, batch 1) and keep its features for the
