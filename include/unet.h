@@ -70,8 +70,9 @@ int unet_set_params(unet_t net, const float* host, long long n);
 int unet_get_params(unet_t net, float* host, long long n);
 int unet_set_bn_stats(unet_t net, const float* host, long long n);
 int unet_get_bn_stats(unet_t net, float* host, long long n);
-/* Synchronise and report a failure recorded by a tensor-core kernel (a bounded
- * wait that expired): 0 if none.  Clears the record. */
+/* Failure detection (no counterpart in the paper): synchronise and report a failure
+ * recorded by a tensor-core kernel (a bounded wait that expired): *failed = 0 if none.
+ * Clears the record. */
 int unet_status(unet_t net, int* failed);
 /* Parameter gradients of the training loss (Sec. 3.4, Eq. 3.7) accumulated since the last
  * unet_zero_grad, in the flat parameter layout, into a HOST array of n elements. */
