@@ -73,3 +73,14 @@ def test_named_desc_values():
         lib.desc_value("bc", "periodic")
     with pytest.raises(ValueError):
         lib.desc_value("levels", "three")
+
+
+def test_headers_compile_as_cpp(tmp_path):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "probe.cpp"
+    src.write_text('#include "unet.h"\nint main() { helm_desc d{}; unet_cfg c{}; return d.nx + c.levels; }\n')
+    r = subprocess.run([cxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
