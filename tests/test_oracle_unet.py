@@ -335,3 +335,21 @@ def test_solver_with_silent_context_is_the_standalone_network():
     assert np.allclose(out_s, out_p, rtol=1e-13, atol=1e-13)
     Ps["down1"][:, :, 4:, :] = 1.0              # and the context does enter once its weights do
     assert not np.allclose(U.forward(solver, Ps, S, x, train=False, feats=feats)[0], out_p)
+
+
+def test_flat_parameter_layout_round_trips():
+    """The flat layouts the library's state functions use (weights layer by layer, the
+    output bias, BN gamma/beta; BN means then variances) invert exactly, with the sizes
+    the layer list implies."""
+    from oracle import precond as PR
+    for cfg in (_tiny(), _tiny(context=(3, 5, 6)), U.UNetConfig()):
+        P = U.init_params(cfg, 9)
+        flat = PR.flatten_params(cfg, P)
+        convs, bns = U.layer_specs(cfg)
+        assert flat.size == sum(k * k * ci * co for _, _, k, ci, co in convs) + cfg.out_ch + 2 * sum(c for _, c in bns)
+        back = PR.unflatten_params(cfg, flat)
+        assert back.keys() == P.keys() and all(np.array_equal(back[k], P[k]) for k in P)
+        S = {k: _rng(10).standard_normal(v.shape) for k, v in U.init_bn_stats(cfg).items()}
+        Sb = PR.unflatten_bn(cfg, PR.flatten_bn(cfg, S))
+        assert all(np.array_equal(Sb[k], S[k]) for k in S)
+        assert np.array_equal(PR.flatten_bn(cfg, S)[:bns[0][1]], S[bns[0][0] + ".mean"])
