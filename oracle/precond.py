@@ -11,6 +11,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   Pairs (Eq. 3.8-3.9): b = A x, x~ = k iterations of FGMRES(10) + M_V from 0,
   r = b - A x~, e = x - x~.
   Residual loss (Remark after Eq. 3.7): |h^2 A e_net - h^2 r|^2 per sample, scaled by 1/s.
+  Training batch (Sec. 3.4): pairs of one medium mixed by complex coefficients
+  (augmentation by linear combinations), then the network input of the mixed residual
+  and the mixed error in the same units as the network output (e / s).
 """
 from __future__ import annotations
 
@@ -59,6 +62,24 @@ def gen_pairs(prob: H.Problem, x, ks, m=10):
         rs.append(b - H.apply_op(A, xt))
         es.append(x[j] - xt)
     return np.stack(rs), np.stack(es)
+
+
+def make_batch(prob: H.Problem, r, e, idx, coef):
+    """Training batch of Sec. 3.4 from pairs (r, e) (npairs, ny, nx) complex of one medium.
+    Sample i mixes the pairs idx[i, q] with coefficients coef[i, q] (the augmentation by
+    linear combinations; one term with coefficient 1 = the pair itself):
+        r' = sum_q coef[i, q] r[idx[i, q]],   e' likewise,
+    input x[i] = ([Re, Im](h^2 r' / s), kappa^2, gamma) with s = RMS(h^2 r') (the network
+    input of the preconditioners), target t[i] = [Re, Im](e' / s), the error in the units
+    the network output is scaled back from.  Returns (x (B, ny, nx, 4), t (B, ny, nx, 2))."""
+    lv = prob.hierarchy[0]
+    idx = np.asarray(idx)
+    coef = np.asarray(coef, dtype=np.complex128)
+    rm = np.stack([sum(coef[i, q] * r[idx[i, q]] for q in range(idx.shape[1])) for i in range(idx.shape[0])])
+    em = np.stack([sum(coef[i, q] * e[idx[i, q]] for q in range(idx.shape[1])) for i in range(idx.shape[0])])
+    x, s = U.make_input(rm, lv.kappa2, lv.gamma, lv.h)
+    t = np.stack([em.real, em.imag], axis=-1) / s[:, None, None, None]
+    return x, t
 
 
 def residual_loss(prob: H.Problem, y, x):

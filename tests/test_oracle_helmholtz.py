@@ -214,6 +214,95 @@ def test_two_grid_equals_error_propagation_matrix():
     assert np.abs((np.eye(N) - B @ M) - E).max() < 1e-12
 
 
+def _prolongation_matrix(n_f, n_c):
+    """Dense P of Eq. 2.9 (column k = P applied to the k-th coarse unit vector)."""
+    P = np.zeros((n_f * n_f, n_c * n_c))
+    for k in range(n_c * n_c):
+        e = np.zeros(n_c * n_c)
+        e[k] = 1
+        P[:, k] = H.prolong_bilinear(e.reshape(n_c, n_c), n_f, n_f).ravel()
+    return P
+
+
+def _vcycle_inverse_dense(prob, level=0):
+    """The V-cycle of Alg. 1 with an exact coarsest solve as a dense matrix B_l (the cycle
+    from a zero guess maps f to B_l f), built level by level from assembled matrices:
+    B_L = M_L^-1 on the coarsest level, and on level l
+        E_l = S_l (I - P_l B_{l+1} R_l M_l) S_l,   B_l = (I - E_l) M_l^-1,
+    S_l = I - w D_l^-1 M_l one damped Jacobi sweep, R_l = P_l^T / 4 (V(1,1))."""
+    lv = prob.hierarchy[level]
+    M = H.assemble_dense(lv)
+    if level == len(prob.hierarchy) - 1:
+        return np.linalg.inv(M)
+    N = M.shape[0]
+    P = _prolongation_matrix(lv.nx, prob.hierarchy[level + 1].nx)
+    S = np.eye(N) - prob.jacobi_w * M / np.diag(M)[:, None]
+    E = S @ (np.eye(N) - P @ _vcycle_inverse_dense(prob, level + 1) @ (P.T / 4) @ M) @ S
+    return (np.eye(N) - E) @ np.linalg.inv(M)
+
+
+def _sl_problem(n, levels=3):
+    k2 = synth.grf_kappa2(n, n, 7, sigma=2.0).astype(np.float64)
+    return H.Problem(k2, omega=synth.omega_for(n), h=1.0 / n, abc_width=4, levels=levels)
+
+
+def test_three_level_vcycle_equals_error_propagation_matrix():
+    """Alg. 1 with three levels (16, 8, 4) and an exact coarsest solve: the oracle's
+    recursion, applied to every unit vector, is the dense map B built from the level
+    matrices, so its error propagation I - B M equals S (I - P B_1 R M) S with B_1 the
+    two-grid cycle of level 1 (the recursion the solver uses, one level deeper than the
+    two-grid pin)."""
+    n = 16
+    prob = _sl_problem(n)
+    B = _vcycle_inverse_dense(prob)
+    N = n * n
+    Bo = np.zeros((N, N), complex)
+    for k in range(N):
+        e = np.zeros(N, complex)
+        e[k] = 1
+        Bo[:, k] = H.vcycle(prob, e.reshape(n, n), coarse="direct").ravel()
+    M = H.assemble_dense(prob.hierarchy[0])
+    assert np.abs(Bo - B).max() <= 1e-12 * np.abs(B).max()
+    E = np.eye(N) - B @ M
+    assert np.abs((np.eye(N) - Bo @ M) - E).max() < 1e-11
+
+
+@pytest.mark.parametrize("n,rho_lo,rho_hi", [(16, 0.58, 0.63), (32, 0.57, 0.61)])
+def test_three_level_sl_factor_is_the_epm_spectral_radius(n, rho_lo, rho_hi):
+    """The asymptotic convergence factor of the 3-level SL V-cycle (shift 0.5, the
+    benchmark's medium generator, a 4-cell layer) is the spectral radius of its exact
+    error-propagation matrix: repeated oracle cycles on e_{k+1} = e_k - V(M e_k) settle at
+    rho(E) (power iteration).  Measured here: 0.606 at 16^2 and 0.590 at 32^2, the same at
+    both sizes, as a multigrid factor should be."""
+    prob = _sl_problem(n)
+    M = H.assemble_dense(prob.hierarchy[0])
+    B = _vcycle_inverse_dense(prob)
+    rho = np.abs(np.linalg.eigvals(np.eye(n * n) - B @ M)).max()
+    assert rho_lo < rho < rho_hi
+    e = np.random.default_rng(3).standard_normal((n, n)) + 0j
+    norms = []
+    for _ in range(70):
+        e = e - H.vcycle(prob, H.apply_op(prob.M, e), coarse="direct")
+        norms.append(np.linalg.norm(e))
+    measured = (norms[-1] / norms[-31]) ** (1 / 30)
+    assert abs(measured - rho) < 0.01 * rho
+
+
+def test_poisson_vcycle_under_the_grid_alignment():
+    """Unshifted Poisson (w = 0, no layer) under the stride-2 / pad-1 alignment of Eq. 2.9
+    on an even grid: coarse node I sits on fine node 2I, so the coarse grid's low-side
+    boundary lies one fine cell beyond the fine grid's.  The interior LFA factor (mu^2 =
+    0.36 for V(1,1) with w = 0.8) is then not reached: the exact two-grid factor is 0.470
+    at 16^2 and 0.559 at 32^2, and the 3-level factor 0.842 at 16^2 and 1.18 at 32^2 (the
+    3-level Poisson cycle diverges).  The shifted Laplacian of the solver is not affected
+    in this way (the 3-level SL factor above is 0.59-0.61)."""
+    for n, levels, lo, hi in ((16, 2, 0.46, 0.48), (32, 2, 0.55, 0.57), (16, 3, 0.83, 0.85), (32, 3, 1.15, 1.21)):
+        prob = H.Problem(np.ones((n, n)), omega=0.0, h=1.0 / n, abc_width=0, beta=0.0, levels=levels)
+        M = H.assemble_dense(prob.hierarchy[0])
+        rho = np.abs(np.linalg.eigvals(np.eye(n * n) - _vcycle_inverse_dense(prob) @ M)).max()
+        assert lo < rho < hi, (n, levels, rho)
+
+
 def test_two_grid_poisson_contracts():
     """Two-grid Poisson cycle with exact coarse solve contracts (rho < 0.5 at n = 16).
     (With the stride-2 / pad-1 grid alignment the low-side boundaries of fine and

@@ -308,6 +308,58 @@ def test_generated_pairs_satisfy_the_error_equation():
     assert norms[-1] < 0.5 * norms[0]
 
 
+def test_training_batch_keeps_the_error_equation_in_network_units():
+    """Sec. 3.4's batch: mixing pairs of one medium by the same complex coefficients keeps
+    A e' = r' (linearity), and the target is the error in the units of the network output,
+    so h^2 A (t0 + i t1) = x0 + i x1 exactly: the residual loss of the target is zero.  A
+    coefficient applied to r but not to e (or conjugated for one of them), or a target
+    without the 1/s or with an extra h^2, breaks it."""
+    from oracle import precond as PR
+    prob = _precond_problem()
+    A = prob.A
+    rng = _rng(21)
+    e = _crandn(rng, (5, 16, 16))
+    r = np.stack([H.apply_op(A, e[j]) for j in range(5)])
+    idx = np.array([[0, 3], [4, 4], [2, 1]])
+    coef = _crandn(rng, (3, 2)) / np.sqrt(2)
+    x, t = PR.make_batch(prob, r, e, idx, coef)
+    assert x.shape == (3, 16, 16, 4) and t.shape == (3, 16, 16, 2)
+    h2 = A.h ** 2
+    for i in range(3):
+        tc = t[i, ..., 0] + 1j * t[i, ..., 1]
+        xc = x[i, ..., 0] + 1j * x[i, ..., 1]
+        assert np.abs(h2 * H.apply_op(A, tc) - xc).max() <= 1e-11 * np.abs(xc).max()
+    loss, _ = PR.residual_loss(prob, t, x)
+    assert loss <= 1e-20 * np.sum(x[..., :2] ** 2)
+    # channels 0-1 of the mixed input have unit mean square; 2-3 carry the medium
+    ms = np.mean(x[..., 0] ** 2 + x[..., 1] ** 2, axis=(1, 2))
+    assert np.allclose(ms, 1.0, rtol=1e-12)
+    assert np.array_equal(x[1, ..., 2], A.kappa2) and np.array_equal(x[2, ..., 3], A.gamma)
+
+
+def test_training_batch_selects_and_mixes_the_named_pairs():
+    """One term with coefficient 1 is the pair itself (the network input of the
+    preconditioners and e / s); a zero coefficient drops its pair; the mixture with
+    coefficients (a, b) is a r_i + b r_j, scaled by its own RMS."""
+    from oracle import precond as PR
+    prob = _precond_problem()
+    lv = prob.A
+    rng = _rng(22)
+    r, e = _crandn(rng, (4, 16, 16)), _crandn(rng, (4, 16, 16))
+    x, t = PR.make_batch(prob, r, e, np.array([[2]]), np.ones((1, 1)))
+    xr, s = U.make_input(r[2:3], lv.kappa2, lv.gamma, lv.h)
+    assert np.array_equal(x, xr)
+    assert np.allclose(t[0, ..., 0] + 1j * t[0, ..., 1], e[2] / s[0], rtol=1e-15, atol=0)
+    x2, t2 = PR.make_batch(prob, r, e, np.array([[2, 0]]), np.array([[1.0, 0.0]]))
+    assert np.allclose(x2, x, rtol=1e-14, atol=0) and np.allclose(t2, t, rtol=1e-14, atol=0)
+    a, b = 0.3 - 1.1j, -0.7 + 0.2j
+    x3, t3 = PR.make_batch(prob, r, e, np.array([[1, 3]]), np.array([[a, b]]))
+    mix = a * r[1] + b * r[3]
+    s3 = lv.h ** 2 * np.sqrt(np.mean(np.abs(mix) ** 2))
+    assert np.allclose(x3[0, ..., 0] + 1j * x3[0, ..., 1], lv.h ** 2 * mix / s3, rtol=1e-13, atol=0)
+    assert np.allclose(t3[0, ..., 0] + 1j * t3[0, ..., 1], (a * e[1] + b * e[3]) / s3, rtol=1e-13, atol=0)
+
+
 def test_solver_with_silent_context_is_the_standalone_network():
     """Eq. 3.5: the solver network sees cat(own channels, f^(l)) at every level.  With the
     weights on the context channels zero, it equals the standalone network built from its
