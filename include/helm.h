@@ -202,9 +202,12 @@ int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int 
  *   kernel 0: operator apply y = A x            (20 B per point)
  *   kernel 1: fused residual + full weighting   (8+4 B read per fine point + 8 B per coarse point)
  *   kernel 2: fused prolongation + Jacobi       (8+4+8 B per fine point + 8 B per coarse point)
- *   kernel 3: MGS pass, dot + axpy              (32 B per point)
+ *   kernel 3: Arnoldi update sweep at step 4, w -= sum c_i v_i over 5 basis vectors
+ *                                                (56 B per point)
  *   kernel 4: one whole V-cycle (M_V)            (bytes: not reported, 0)
- *   kernel 5: the coarsest-grid GMRES solve      (bytes: not reported, 0)      */
+ *   kernel 5: the coarsest-grid GMRES solve      (bytes: not reported, 0)
+ *   kernel 6: Arnoldi projection sweep at step 4, w = A z with the 5 inner products
+ *             <v_i, w> and ||w||^2               (60 B per point)               */
 int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes);
 
 /* Coarsest-grid GMRES solve that allocates nothing (no counterpart in the

@@ -74,6 +74,13 @@ int unet_get_bn_stats(unet_t net, float* host, long long n);
  * recorded by a tensor-core kernel (a bounded wait that expired): *failed = 0 if none.
  * Clears the record. */
 int unet_status(unet_t net, int* failed);
+/* Failure-detection probe (no counterpart in the paper; for tests): one GPU thread waits,
+ * through the same bounded mbarrier wait the tensor-core kernels use, on a barrier that
+ * expects one arrival.  arrive = 0: nothing arrives, the wait gives up after `rounds`
+ * polls (1 <= rounds <= 2^20, well under a second) and records the failure that
+ * unet_status then reports; arrive = 1: the thread arrives first and nothing is recorded.
+ * The kernel returns either way; the context stays usable.  Asynchronous on `stream`. */
+int unet_wait_probe(unet_t net, long long rounds, int arrive, helm_stream_t stream);
 /* Parameter gradients of the training loss (Sec. 3.4, Eq. 3.7) accumulated since the last
  * unet_zero_grad, in the flat parameter layout, into a HOST array of n elements. */
 int unet_get_grads(unet_t net, float* host, long long n);
@@ -98,6 +105,35 @@ int unet_backward(unet_t net, const float* gout, float* gx, helm_stream_t stream
  * samples): writes gout = d loss / d out (device) and the loss into *loss_dev. */
 int unet_mse(const float* out, const float* target, long long n, int B, float* gout, float* loss_dev,
              helm_stream_t stream);
+/* One training step (Sec. 3.4; the paper trains with Adam on the loss of Eq. 3.7): with an
+ * attached encoder, the encoder's train-mode forward on the medium of h (the pair is
+ * trained jointly); then zeroed gradients, the train-mode forward on x (device float32
+ * [B][ny][nx][in_ch], h's fine grid, e.g. from unet_make_batch), the loss, the backward
+ * pass and one Adam step on every parameter.  opt->loss selects the MSE of Eq. 3.7 against
+ * target (device float32 [B][ny][nx][out_ch]) or the unsupervised residual loss of the
+ * Remark following Eq. 3.7 (target unused, may be NULL).  The loss value goes to
+ * loss_dev (device float, nullable).  Asynchronous on `stream`; the network keeps the
+ * output-gradient buffer it needs (allocated on the first call of a size). */
+enum { UNET_LOSS_MSE = 0, UNET_LOSS_RESIDUAL = 1 };
+typedef struct {
+  float lr, beta1, beta2, eps;   /* Adam: learning rate (Sec. 4: 1e-4), moment decays, epsilon */
+  int loss;                      /* UNET_LOSS_MSE or UNET_LOSS_RESIDUAL                       */
+} unet_train_opts;
+int unet_train_step(unet_t net, helm_t h, const float* x, const float* target, int B, const unet_train_opts* opt,
+                    float* loss_dev, helm_stream_t stream);
+
+/* Network checkpoints (no counterpart in the paper: persistence of the trained state).
+ * unet_save writes the FP32 master weights and the BatchNorm running statistics of net
+ * (device state, read back synchronously) to the file `path`: 8-byte magic "HLMUNET1",
+ * uint32 header length, a JSON header {"cfg": the unet_cfg fields, "crc32": CRC-32 of the
+ * payload, "meta": meta_json (one JSON object, NULL for {}), "n_bn", "n_params",
+ * "version": 1}, zero padding to 16 bytes, then float32 weights (flat order above) and
+ * float32 BN means and variances.  unet_load restores such a file into net, which must
+ * have the same configuration; a bad magic, version, size, CRC or configuration is
+ * HELM_EINVAL with a message, and net is then unchanged.  Adam moments are not stored. */
+int unet_save(unet_t net, const char* path, const char* meta_json);
+int unet_load(unet_t net, const char* path);
+
 /* Unsupervised residual loss (the Remark following Eq. 3.7) on the medium of h: with
  * the network output y (device float32 [B][ny][nx][2], units e / s) and its input x
  * (device float32 [B][ny][nx][4] as unet_make_batch writes it, channels 0, 1 = h^2 r / s),

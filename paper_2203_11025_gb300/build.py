@@ -34,7 +34,8 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OBJ_DIR, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "helm.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                if f.endswith(".h")]
     hdr_mtime = max(os.path.getmtime(h) for h in headers if os.path.exists(h))
 
     def compile_one(src):

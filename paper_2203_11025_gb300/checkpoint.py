@@ -14,6 +14,10 @@ File layout (little-endian):
 Adam moments are not part of the file: resuming training from a checkpoint restarts
 the optimiser state.  Reading checks the magic, the version, the sizes and the CRC
 and raises ValueError on any mismatch.
+
+save / load_into / load go through the library's own reader and writer (unet_save,
+unet_load in include/unet.h); encode / decode are the same layout in Python, for host-side
+inspection and for checking the two against each other.
 """
 from __future__ import annotations
 
@@ -91,10 +95,8 @@ def decode(blob: bytes):
 
 
 def save(net, path: str, meta: dict | None = None) -> None:
-    """Write net's weights and BatchNorm statistics (device state, read back to the host)."""
-    blob = encode(cfg_to_dict(net.cfg), net.get_params(), net.get_bn_stats(), meta)
-    with open(path, "wb") as f:
-        f.write(blob)
+    """Write net's weights and BatchNorm statistics (device state) with unet_save."""
+    net.save(path, meta)
 
 
 def read(path: str):
@@ -103,25 +105,24 @@ def read(path: str):
 
 
 def load_into(net, path: str) -> dict:
-    """Restore a checkpoint into an existing network of the same configuration; returns meta."""
-    cfg, params, bn, meta = read(path)
-    if cfg != cfg_to_dict(net.cfg):
-        raise ValueError(f"checkpoint configuration {cfg} differs from the network's {cfg_to_dict(net.cfg)}")
-    if params.size != net.n_params or bn.size != net.n_bn:
-        raise ValueError("checkpoint sizes differ from the network's")
-    net.set_params(params)
-    net.set_bn_stats(bn)
-    return meta
+    """Restore a checkpoint into an existing network of the same configuration (unet_load);
+    returns meta."""
+    from . import lib
+    try:
+        net.load(path)
+    except lib.HelmError as exc:
+        raise ValueError(str(exc)) from None
+    return read(path)[3]
 
 
 def load(path: str):
     """A new network (libhelm U-Net on the current GPU) restored from a checkpoint; returns (net, meta)."""
     from . import lib
-    cfg, params, bn, meta = read(path)
+    cfg, _, _, meta = read(path)
     net = lib.UNet(dict_to_cfg(cfg))
-    if params.size != net.n_params or bn.size != net.n_bn:
+    try:
+        net.load(path)
+    except lib.HelmError as exc:
         net.close()
-        raise ValueError("checkpoint sizes differ from the network its configuration builds")
-    net.set_params(params)
-    net.set_bn_stats(bn)
+        raise ValueError(str(exc)) from None
     return net, meta

@@ -15,6 +15,7 @@
 #include <string>
 
 #include "../../include/helm.h"
+#include "devonce.cuh"
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -203,18 +204,25 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
 
 template <typename T>
 bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* V, size_t vstride, int nrhs, int m,
-                               const int* gate, cudaStream_t s) {
+                               const int* gate, cudaStream_t s, cudaError_t* launch_err) {
   typedef typename vec2<T>::type T2;
+  if (launch_err) *launch_err = cudaSuccess;
   const size_t smem = (size_t)op.nx * op.ny * sizeof(T2);
   if (m > CMAX || smem > 160 * 1024) return false;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_coarse_gmres<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    cudaFuncSetAttribute(k_coarse_gmres<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    configured = true;
-  }
+  // the shared-memory opt-in is a per-device attribute: raised once on each device
+  static DeviceOnce once2, once4;
   auto k = op.order == 4 ? k_coarse_gmres<T, 4> : k_coarse_gmres<T, 2>;
-  k<<<nrhs, CT, smem, s>>>(op, (const T2*)f, (T2*)out, (T2*)V, vstride, m, gate);
+  if (!set_dynamic_smem(op.order == 4 ? once4 : once2, k, 160 * 1024)) {
+    if (launch_err) *launch_err = cudaErrorInvalidValue;
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nrhs, 1, 1);
+  cfg.blockDim = dim3(CT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k, op, (const T2*)f, (T2*)out, (T2*)V, vstride, m, gate);
+  if (launch_err) *launch_err = e;
   return true;
 }
 
@@ -235,19 +243,27 @@ void* g_static_ptr[kMaxDevices] = {};
 }  // namespace
 
 template bool launch_coarse_gmres_fused<float>(const Op<float>&, const void*, void*, void*, size_t, int, int,
-                                               const int*, cudaStream_t);
+                                               const int*, cudaStream_t, cudaError_t*);
 template bool launch_coarse_gmres_fused<double>(const Op<double>&, const void*, void*, void*, size_t, int, int,
-                                                const int*, cudaStream_t);
+                                                const int*, cudaStream_t, cudaError_t*);
 
 }  // namespace helm
 
 extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, double beta, int abc_width,
                                         double gamma_max, const float* kappa2, const void* f, void* x, int nrhs,
                                         int m, helm_stream_t stream) {
-  if (nx <= 0 || ny <= 0 || nrhs < 1 || m < 1 || m > 32 || !(h > 0) || abc_width < 0 || !kappa2 || !f || !x ||
-      f == x) {
+  if (nx <= 0 || ny <= 0 || nrhs < 1 || m < 1 || m > 32 || !(h > 0) || abc_width < 0 || !kappa2 || !f || !x) {
     helm::set_error("helm_coarse_solve_static: bad arguments");
     return HELM_EINVAL;
+  }
+  {
+    // f is read by every block while others write x: the byte ranges must not meet
+    const size_t bytes = (size_t)nrhs * (size_t)nx * (size_t)ny * sizeof(float2);
+    const uintptr_t fa = (uintptr_t)f, xa = (uintptr_t)x;
+    if (fa < xa + bytes && xa < fa + bytes) {
+      helm::set_error("helm_coarse_solve_static: f and x overlap");
+      return HELM_EINVAL;
+    }
   }
   const size_t need = (size_t)(m + 1) * (size_t)nrhs * (size_t)nx * (size_t)ny;
   if (need > helm::kStaticBasisElems) {
@@ -285,15 +301,18 @@ extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, 
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gamma_max;
   op.beta = (float)beta;
+  op.inv_w = abc_width > 0 ? (float)(1.0 / abc_width) : 0.f;
   op.k2 = kappa2;
-  if (!helm::launch_coarse_gmres_fused<float>(op, f, x, basis, (size_t)nrhs * nx * ny, nrhs, m, nullptr,
-                                              (cudaStream_t)stream)) {
-    helm::set_error("helm_coarse_solve_static: configuration not supported by the one-launch kernel");
-    return HELM_EINVAL;
+  cudaError_t le = cudaSuccess;
+  const bool launched = helm::launch_coarse_gmres_fused<float>(op, f, x, basis, (size_t)nrhs * nx * ny, nrhs, m,
+                                                               nullptr, (cudaStream_t)stream, &le);
+  if (!launched) {
+    // the sizes were checked above, so only the shared-memory opt-in can have failed
+    helm::set_error("helm_coarse_solve_static: raising the kernel's shared-memory limit failed on this device");
+    return HELM_ECUDA;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    helm::set_error(std::string("helm_coarse_solve_static launch: ") + cudaGetErrorString(e));
+  if (le != cudaSuccess) {   // this launch's own result (an earlier, unrelated error is left pending)
+    helm::set_error(std::string("helm_coarse_solve_static launch: ") + cudaGetErrorString(le));
     return HELM_ECUDA;
   }
   return HELM_OK;

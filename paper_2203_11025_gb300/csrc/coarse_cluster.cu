@@ -26,6 +26,7 @@
 // another.
 #include <cooperative_groups.h>
 
+#include "devonce.cuh"
 #include "helm_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -343,12 +344,17 @@ bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, 
                     size_t smem, void* gV, size_t vstride, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
   auto kern = k_coarse_cluster<T, PPT, MK, NT, GB>;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    configured = true;
-  }
+  // kernel attributes hold per device: set once on each device
+  static DeviceOnce once;
+  const bool ok = device_once(once, [&]() -> long long {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return 1;
+  }, 0) == 1;
+  if (!ok) return false;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, nrhs, 1);
   cfg.blockDim = dim3(NT, 1, 1);

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "devonce.cuh"
 #include "unet_internal.cuh"
 
 namespace helm {
@@ -349,11 +350,8 @@ void conv_forward_tc(const ConvArgs& c, int* err, cudaStream_t s) {
   a.NT = nt;
   const int nchunk = (c.Cout + nt - 1) / nt;
   const size_t smem = conv_tc_smem(nt);
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_tc_smem(256));
-    configured = true;
-  }
+  static DeviceOnce once;   // the opt-in is a per-device kernel attribute
+  set_dynamic_smem(once, k_conv_tc, (int)conv_tc_smem(256));
   if (!c.transposed) {
     k_conv_tc<<<dim3((M + TM - 1) / TM, nchunk, 1), NTHREADS, smem, s>>>(a);
   } else {

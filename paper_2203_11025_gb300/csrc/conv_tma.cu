@@ -32,6 +32,7 @@
 #include <unordered_map>
 #include <utility>
 
+#include "devonce.cuh"
 #include "pdl.cuh"
 #include "unet_internal.cuh"
 
@@ -70,8 +71,8 @@ __device__ __forceinline__ bool mb_try(uint32_t a, uint32_t par) {
 }
 // Critical-path waits (TMA producer, MMA issuer): try_wait suspends the thread in
 // hardware until the phase completes, so a waiting warp takes no issue slots.
-__device__ __forceinline__ bool mb_wait(uint32_t a, uint32_t par) {
-  for (long long i = 0; i < kWait; ++i)
+__device__ __forceinline__ bool mb_wait(uint32_t a, uint32_t par, long long bound = kWait) {
+  for (long long i = 0; i < bound; ++i)
     if (mb_try(a, par)) return true;
   return false;
 }
@@ -88,6 +89,21 @@ __device__ __forceinline__ void mb_expect_tx(uint32_t a, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(a), "r"(bytes)
                : "memory");
 }
+// Failure-detection probe: one thread waits, through the pipeline's bounded wait, on an
+// mbarrier that expects one arrival.  With arrive = 0 nothing arrives, the wait gives up
+// after `rounds` polls and the failure is recorded in err exactly as the convolution
+// kernels record an expired wait; with arrive = 1 the thread arrives first and the wait
+// succeeds.  Either way the kernel returns.
+__global__ void k_wait_probe(int* err, long long rounds, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t a = su32(&bar);
+  mb_init(a, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (arrive) asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(a) : "memory");
+  if (!mb_wait(a, 0, rounds) && err) atomicExch(err, 1);
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t mbar) {
   asm volatile(
@@ -1035,19 +1051,8 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   if (bres_al + 2 * stage > budget) return false;
   const int nst = (int)std::min<size_t>(MAXST, (budget - bres_al) / stage);
   const size_t smem = 1024 + bres_al + (size_t)nst * stage;
-  static int max_dyn = -1;
-  if (max_dyn < 0) {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa{};
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_conv_tma_reuse) != cudaSuccess ||
-        cudaFuncSetAttribute(k_conv_tma_reuse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
-      max_dyn = 0;
-    else
-      max_dyn = optin - (int)fa.sharedSizeBytes;
-  }
+  static DeviceOnce once;   // per-device opt-in (kernel attributes hold per device)
+  const long long max_dyn = opt_in_dynamic_smem(once, k_conv_tma_reuse);
   if ((long long)smem > max_dyn) return false;
   // input boxes: BX x (BY + nyt - 1) pixels of tk channels, element stride es
   CUtensorMap mA, mB;
@@ -1098,6 +1103,11 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
 
 const char* g_tma_reject = "";
 const char* conv_tma_last_reject() { return g_tma_reject; }
+
+bool conv_wait_probe(int* err, long long rounds, int arrive, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(err, rounds, arrive);
+  return cudaGetLastError() == cudaSuccess;
+}
 
 bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
 #define TMA_REJECT(why) do { g_tma_reject = why; return false; } while (0)
@@ -1180,19 +1190,8 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   if (a.nst < 2) TMA_REJECT("shared memory");
   const size_t smem = (size_t)a.nst * stage + 1024;
   // dynamic shared memory opt-in: the per-block limit less the kernel's static barriers
-  static int max_dyn = -1;
-  if (max_dyn < 0) {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa{};
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_conv_tma) != cudaSuccess ||
-        cudaFuncSetAttribute(k_conv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
-      max_dyn = 0;
-    else
-      max_dyn = optin - (int)fa.sharedSizeBytes;
-  }
+  static DeviceOnce once;   // per-device opt-in (kernel attributes hold per device)
+  const long long max_dyn = opt_in_dynamic_smem(once, k_conv_tma);
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
   launch_pdl(k_conv_tma, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
@@ -1459,19 +1458,8 @@ bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* g
   a.nst = (int)std::min<size_t>(MAXST, budget / stage);
   if (a.nst < 2) return false;
   const size_t smem = (size_t)a.nst * stage + 1024 + 16 * 1024;
-  static int max_dyn = -1;
-  if (max_dyn < 0) {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa{};
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_wgrad_tma) != cudaSuccess ||
-        cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes) != cudaSuccess)
-      max_dyn = 0;
-    else
-      max_dyn = optin - (int)fa.sharedSizeBytes;
-  }
+  static DeviceOnce once;   // per-device opt-in (kernel attributes hold per device)
+  const long long max_dyn = opt_in_dynamic_smem(once, k_wgrad_tma);
   if ((long long)smem > max_dyn) return false;
   // X: box {64 channels, bx (x es), by (x es), 1}; G likewise (element stride 2 on G for
   // transposed convolutions, on X for stride-2 ones)

@@ -33,6 +33,7 @@ enum { kBcDirichlet = 0, kBcReflect = 1, kBcReplicate = 2 };
 template <typename T> struct Op {
   int nx, ny, abc_w, bc, order;
   T inv_h2, h2, omega2, gmax, beta;
+  T inv_w;      // 1 / abc_w (0 without a layer)
   const T* k2;  // kappa^2 on this level, [ny][nx]
 };
 
@@ -53,6 +54,7 @@ inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
   op.omega2 = (T)(omega * omega);
   op.gmax = (T)gmax;
   op.beta = (T)beta;
+  op.inv_w = L.abc_w > 0 ? (T)(1.0 / L.abc_w) : T(0);
   op.k2 = nullptr;
   return op;
 }
@@ -63,6 +65,7 @@ template <> inline Op<float> make_op<float>(const Level& L, double omega, double
   op.inv_h2 = (float)(1.0 / (L.h * L.h));
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gmax; op.beta = (float)beta; op.k2 = L.k2f;
+  op.inv_w = L.abc_w > 0 ? (float)(1.0 / L.abc_w) : 0.f;
   return op;
 }
 template <> inline Op<double> make_op<double>(const Level& L, double omega, double gmax, double beta) {
@@ -72,6 +75,7 @@ template <> inline Op<double> make_op<double>(const Level& L, double omega, doub
   op.inv_h2 = 1.0 / (L.h * L.h);
   op.omega2 = omega * omega;
   op.gmax = gmax; op.beta = beta; op.k2 = L.k2d;
+  op.inv_w = L.abc_w > 0 ? 1.0 / L.abc_w : 0.0;
   return op;
 }
 
@@ -93,39 +97,57 @@ template <typename T2> __device__ __forceinline__ T2 cinv(T2 a) {
 template <typename T> __device__ __forceinline__ T gamma_at(const Op<T>& op, int x, int y) {
   int d = min(min(x, op.nx - 1 - x), min(y, op.ny - 1 - y));
   if (d >= op.abc_w) return T(0);
-  T t = T(1) - T(d) / T(op.abc_w);
+  T t = T(1) - T(d) * op.inv_w;
   return t * t * op.gmax;
 }
 
-// Diagonal of K at (x, y): 4/h^2 - w^2 k^2 + i w^2 k^2 (g + beta), less 1/h^2
-// per boundary side under replication padding; (20/6)/h^2 - (8/12) m for the compact
-// scheme.
-template <typename T>
-__device__ __forceinline__ typename vec2<T>::type diag_at(const Op<T>& op, int x, int y) {
-  T wk = op.omega2 * op.k2[(size_t)y * op.nx + x];
+// Diagonal of K at (x, y) for a stored kappa^2 value k2: 4/h^2 - w^2 k^2 + i w^2 k^2 (g +
+// beta), less 1/h^2 per boundary side under replication padding; (20/6)/h^2 - (8/12) m for
+// the compact scheme.  BC and ORD as template arguments fix the boundary mode and the
+// stencil at compile time (-1: read them from op).
+template <int BC = -1, int ORD = -1, typename T>
+__device__ __forceinline__ typename vec2<T>::type diag_k2(const Op<T>& op, int x, int y, T k2) {
+  const int order = ORD >= 0 ? ORD : op.order;
+  const int bc = BC >= 0 ? BC : op.bc;
+  T wk = op.omega2 * k2;
   typename vec2<T>::type d;
-  if (op.order == 4) {
+  if (order == 4) {
     const T wm = wk * T(8) / T(12);
     d.x = T(20) / T(6) * op.inv_h2 - wm;
     d.y = wm * (gamma_at(op, x, y) + op.beta);
     return d;
   }
   T c = T(4);
-  if (op.bc == kBcReplicate)
+  if (bc == kBcReplicate)
     c -= T((x == 0) + (x == op.nx - 1) + (y == 0) + (y == op.ny - 1));
   d.x = c * op.inv_h2 - wk;
   d.y = wk * (gamma_at(op, x, y) + op.beta);
   return d;
+}
+template <int BC = -1, int ORD = -1, typename T>
+__device__ __forceinline__ typename vec2<T>::type diag_at(const Op<T>& op, int x, int y) {
+  return diag_k2<BC, ORD>(op, x, y, op.k2[(size_t)y * op.nx + x]);
+}
+
+// 1 / d for a complex d with one reciprocal of |d|^2 (FP32: the intrinsic reciprocal).
+template <typename T2> __device__ __forceinline__ T2 crecip(T2 a);
+template <> __device__ __forceinline__ float2 crecip<float2>(float2 a) {
+  const float r = __frcp_rn(a.x * a.x + a.y * a.y);
+  return make_float2(a.x * r, -a.y * r);
+}
+template <> __device__ __forceinline__ double2 crecip<double2>(double2 a) {
+  const double r = 1.0 / (a.x * a.x + a.y * a.y);
+  return make_double2(a.x * r, -a.y * r);
 }
 
 // The part of the neighbour sum that reflection padding adds at a boundary node:
 // the inward neighbour once more per boundary side.  l, r, d, u are the values at
 // (x-1, y), (x+1, y), (x, y-1), (x, y+1) (zero outside the grid); grids are at
 // least 2 nodes wide under reflection, so the inward neighbour always exists.
-template <typename T, typename T2>
+template <int BC = -1, typename T, typename T2>
 __device__ __forceinline__ T2 reflect_extra(const Op<T>& op, int x, int y, T2 l, T2 r, T2 d, T2 u) {
   T2 e = czero<T2>();
-  if (op.bc != kBcReflect) return e;
+  if ((BC >= 0 ? BC : op.bc) != kBcReflect) return e;
   if (x == 0) e = cadd(e, r); else if (x == op.nx - 1) e = cadd(e, l);
   if (y == 0) e = cadd(e, u); else if (y == op.ny - 1) e = cadd(e, d);
   return e;
@@ -147,7 +169,7 @@ __device__ __forceinline__ T2 mass_times(const Op<T>& op, int x, int y, T2 u) {
 // corners) / 6 + (h^2 / 12) sum over the edges of m_q u_q.  The order is a template
 // parameter so that the 5-point kernels carry none of the 9-point registers; launchers
 // pick the instantiation from op.order.
-template <int ORD, typename T, typename F>
+template <int ORD, int BC = -1, typename T, typename F>
 __device__ __forceinline__ typename vec2<T>::type stencil_sum(const Op<T>& op, int x, int y, F at) {
   typedef typename vec2<T>::type T2;
   const bool xl = x > 0, xr = x < op.nx - 1, yd = y > 0, yu = y < op.ny - 1;
@@ -156,7 +178,7 @@ __device__ __forceinline__ typename vec2<T>::type stencil_sum(const Op<T>& op, i
   const T2 dn = yd ? at(0, -1) : czero<T2>();
   const T2 up = yu ? at(0, 1) : czero<T2>();
   const T2 e = cadd(cadd(l, rt), cadd(dn, up));
-  if (ORD != 4) return cadd(e, reflect_extra(op, x, y, l, rt, dn, up));
+  if (ORD != 4) return cadd(e, reflect_extra<BC>(op, x, y, l, rt, dn, up));
   T2 c = czero<T2>();
   if (yd && xl) c = cadd(c, at(-1, -1));
   if (yd && xr) c = cadd(c, at(1, -1));
@@ -189,11 +211,15 @@ template <typename T> void launch_restrict(int nx, int ny, const void* rf, void*
                                            const int* active, cudaStream_t s);
 template <typename T> void launch_prolong_add(int nxc, int nyc, int nx, int ny, const void* ec, void* xf,
                                               int nrhs, const int* active, cudaStream_t s);
+// The fused cycle kernels.  seg: the segment height of the FP32 column-strip form (4, 8,
+// 16 or 32 rows; 0 = pick by occupancy), or -1 for the shared-memory tile form; FP64,
+// the compact scheme and pointers that are not 16-byte aligned always take the tile form.
 template <typename T> void launch_resid_restrict(const Op<T>& fine, T w, const void* f, const void* v,
-                                                 void* fc, int nrhs, const int* active, cudaStream_t s);
+                                                 void* fc, int nrhs, const int* active, cudaStream_t s,
+                                                 int seg = 0);
 template <typename T> void launch_prolong_jacobi(const Op<T>& fine, T w, const void* f, const void* v,
                                                  bool implicit_v, const void* ec, int nxc, int nyc, void* out,
-                                                 int nrhs, const int* active, cudaStream_t s);
+                                                 int nrhs, const int* active, cudaStream_t s, int seg = 0);
 void launch_coarsen_kappa2(const double* k2d_fine, int nx, int ny, double* k2d_coarse, float* k2f_coarse,
                            cudaStream_t s);
 void launch_widen_kappa2(const float* k2f, double* k2d, size_t n, cudaStream_t s);
@@ -221,7 +247,12 @@ struct ArnoldiState {      // device arrays, per right-hand side
   int* counter;            // [nrhs]   arrival tickets of the last-block reduction
   int nbmax;
   int m;
+  // classical Gram-Schmidt Arnoldi (launch_arnoldi)
+  double2* proj;           // [nrhs][kProjMax] coefficients of the pending projection
+  double2* mpart;          // [nrhs][kProjMax + 1][mcap] block partials of the multi-value reductions
+  int mcap;                // block capacity of mpart (>= every nb used with this state)
 };
+constexpr int kProjMax = 32;   // longest Arnoldi column (restart length) the projections handle
 
 struct SolveState {         // FGMRES, per right-hand side, device
   double* bnorm;
@@ -248,6 +279,16 @@ template <typename T> void launch_mgs(const void* V, size_t vstride, void* w, si
                                       ArnoldiState& st, int nb, cudaStream_t s);
 template <typename T> void launch_normalize(void* w, size_t N, int nrhs, int j, ArnoldiState& st, int nb,
                                             cudaStream_t s);
+// Arnoldi step j by classical Gram-Schmidt applied twice (three sweeps instead of MGS's
+// j + 3): w = K z (or K D^-1 z) written to V slot j+1, column j of the Hessenberg matrix,
+// the Givens step and, if j + 1 < m, v_{j+1} = w / h_{j+1,j} in place.  V: [slot][rhs][N]
+// with slots vstride elements apart.
+template <typename T> void launch_arnoldi(const Op<T>& op, bool diag_precond, const void* z, void* V, size_t vstride,
+                                          int nrhs, ArnoldiState& st, int j, int m, int nb, cudaStream_t s);
+// One sweep of launch_arnoldi alone (timing hook): which 0 = the projection sweep
+// (w = K z and the j + 2 reductions), 1 = the update sweep (w -= sum_i c_i v_i, i <= j).
+template <typename T> void launch_arnoldi_sweep(int which, const Op<T>& op, const void* z, void* V, size_t vstride,
+                                                int nrhs, ArnoldiState& st, int j, int nb, cudaStream_t s);
 // y = R^-1 g per right-hand side; iters (nullable) += steps taken.
 void launch_backsolve(ArnoldiState& st, int nrhs, int* iters, cudaStream_t s);
 // out = (D^-1) sum_i y_i V_i over the k steps of each right-hand side (0 if k = 0);
@@ -256,10 +297,12 @@ template <typename T> void launch_combine(const void* V, size_t vstride, size_t 
                                           const Op<T>* dinv_op, void* out, const int* gate, int nb,
                                           cudaStream_t s);
 
-// Coarsest GMRES(m) in one launch (coarse.cu); false if the grid does not fit.
+// Coarsest GMRES(m) in one launch (coarse.cu); false (nothing launched) if the grid does
+// not fit or the kernel's shared-memory opt-in failed on this device.  launch_err
+// (nullable) receives the launch's own result (or the opt-in failure).
 template <typename T> bool launch_coarse_gmres_fused(const Op<T>& op, const void* f, void* out, void* V,
                                                      size_t vstride, int nrhs, int m, const int* gate,
-                                                     cudaStream_t s);
+                                                     cudaStream_t s, cudaError_t* launch_err = nullptr);
 
 // Coarsest GMRES(m) on one thread-block cluster per right-hand side (coarse_cluster.cu);
 // false if the grid does not fit (C <= 16 CTAs of <= 1024 points, basis in shared memory).

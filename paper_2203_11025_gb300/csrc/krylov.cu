@@ -3,8 +3,9 @@
 // GMRES(m) on the coarsest grid (Sec. 2.4 and 4: diagonal-Jacobi right
 // preconditioning, x0 = 0) and restarted FGMRES(m) for A M^-1 u = g (Eq. 2.5;
 // the flexible variant of Saad 1993 that the paper cites) share this code:
-// modified Gram-Schmidt Arnoldi, complex Givens rotations on the Hessenberg
-// matrix, back substitution, x += Z y.
+// Arnoldi by classical Gram-Schmidt applied twice (launch_arnoldi; the modified
+// Gram-Schmidt kernels remain for the block and timing paths), complex Givens
+// rotations on the Hessenberg matrix, back substitution, x += Z y.
 //
 // Precision: vectors are stored in T (float for the solver); every inner
 // product and norm is accumulated per thread in T over four elements, then in
@@ -15,6 +16,9 @@
 // A reduction's blocks write their partial sums; the last block to arrive (an
 // atomic ticket) adds them in a fixed order, so results are deterministic and
 // no separate reduction launch is needed.
+#include <cstdint>
+#include <type_traits>
+
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -246,6 +250,378 @@ __global__ void __launch_bounds__(NT) k_normalize(typename vec2<T>::type* __rest
   for (size_t e = (size_t)blockIdx.x * NT + threadIdx.x; e < N; e += (size_t)nb * NT) w[off + e] = cscale(w[off + e], inv);
 }
 
+// ---------------------------------------------------------------------------
+// Arnoldi step by classical Gram-Schmidt applied twice (CGS2).
+//
+// MGS orthogonalises w against v_0..v_j one vector per sweep (j + 1 sweeps over w and
+// one more to normalise).  CGS takes every projection coefficient from one sweep and
+// subtracts them in the next; applied twice it keeps the basis as orthogonal as MGS
+// does ("twice is enough": Giraud, Langou, Rozloznik 2005), whereas a single CGS pass
+// loses orthogonality geometrically in FP32 when most of w lies in the basis (as it
+// does with a good preconditioner):
+//   A  w = K z;  c_i = <v_i, w>                                  (one sweep, also the operator)
+//   B  w' = w - sum c_i v_i;  d_i = <v_i, w'>;  ||w'||^2         (one sweep)
+//   C  v_{j+1} = (w' - sum d_i v_i) / nu,  nu^2 = ||w'||^2 - sum |d_i|^2
+// Column j of the Hessenberg matrix is c + d with h_{j+1,j} = nu.  The second
+// coefficients are small, so nu^2 by Pythagoras has no cancellation.  In exact
+// arithmetic this is MGS's Arnoldi process.  Every reduction is deterministic (fixed
+// order over blocks); the last block of sweep B completes column j and runs the Givens
+// step; sweep C is skipped after the last step of a cycle.
+// ---------------------------------------------------------------------------
+
+// Reduce per-thread values over the block and publish this block's totals to mpart;
+// returns true in every thread of the last block to arrive, which then holds the grand
+// totals (fixed order) in tot[].  Values 0..j are reduced, and with with_norm also the
+// value in slot NV - 1 (it lands in tot[j + 1]).
+template <int NV, typename T>
+__device__ bool reduce_many(T (&ax)[NV], T (&ay)[NV], int j, bool with_norm, const ArnoldiState& st, int rhs,
+                            int nb, double2* tot) {
+  __shared__ double2 sm[NT / 32][NV];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = j + 1 + (with_norm ? 1 : 0);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v <= j || (with_norm && v == NV - 1)) {
+      T x = ax[v], y = ay[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+      }
+      if (lane == 0) sm[warp][v <= j ? v : j + 1] = d2((double)x, (double)y);
+    }
+  }
+  __syncthreads();
+  double2* base = st.mpart + (size_t)rhs * (kProjMax + 1) * st.mcap;
+  if (threadIdx.x < nv) {
+    double2 acc = d2(0, 0);
+    for (int w = 0; w < NT / 32; ++w) acc = dadd(acc, sm[w][threadIdx.x]);
+    base[(size_t)threadIdx.x * st.mcap + blockIdx.x] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(st.counter + rhs, 1) == nb - 1);
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  for (int v = warp; v < nv; v += NT / 32) {
+    double x = 0, y = 0;
+    for (int b = lane; b < nb; b += 32) {
+      const double2 q = __ldcg(base + (size_t)v * st.mcap + b);
+      x += q.x;
+      y += q.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_down_sync(0xffffffffu, x, o);
+      y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    if (lane == 0) tot[v] = d2(x, y);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st.counter[rhs] = 0;
+  return true;
+}
+
+// Sweep A: w = K z (diag_precond: K D^-1 z), c_i = <v_i, w> for i <= j.
+template <typename T, int ORD, int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_project(Op<T> op, int diag_precond,
+                                                        const typename vec2<T>::type* __restrict__ z,
+                                                        const typename vec2<T>::type* __restrict__ V, size_t vstride,
+                                                        typename vec2<T>::type* __restrict__ wbase, ArnoldiState st,
+                                                        int j, int nb) {
+  typedef typename vec2<T>::type T2;
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int nx = op.nx, ny = op.ny;
+  const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
+  const T2* zr = z + off;
+  T2* w = wbase + off;
+  T ax[JB], ay[JB];
+#pragma unroll
+  for (int i = 0; i < JB; ++i) { ax[i] = 0; ay[i] = 0; }
+  for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
+    const int y = (int)(p / nx), x = (int)(p - (size_t)y * nx);
+    T2 c, sn;
+    if (diag_precond) {
+      c = cmul(zr[p], crecip(diag_at(op, x, y)));
+      sn = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) {
+        return cmul(zr[(ptrdiff_t)p + (ptrdiff_t)dy * nx + dx], crecip(diag_at(op, x + dx, y + dy)));
+      });
+    } else {
+      c = zr[p];
+      sn = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return zr[(ptrdiff_t)p + (ptrdiff_t)dy * nx + dx]; });
+    }
+    T2 r = cmul(diag_at(op, x, y), c);
+    r.x -= sn.x * op.inv_h2;
+    r.y -= sn.y * op.inv_h2;
+    w[p] = r;
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) cdot_acc(ax[i], ay[i], V[(size_t)i * vstride + off + p], r);
+  }
+  __shared__ double2 tot[JB + 1];
+  if (!reduce_many<JB, T>(ax, ay, j, false, st, rhs, nb, tot) || threadIdx.x != 0) return;
+  const int m = st.m;
+  double2* Hc = st.H + (size_t)rhs * (m + 1) * m;
+  double2* proj = st.proj + (size_t)rhs * kProjMax;
+  for (int i = 0; i <= j; ++i) {
+    Hc[(size_t)i * m + j] = tot[i];
+    proj[i] = tot[i];
+  }
+}
+
+// Sweep B: w' = w - sum_{i<=j} c_i v_i (written back when write_next), d_i = <v_i, w'>,
+// ||w'||^2; the last block completes column j and runs the Givens step.
+// only_update: the subtraction alone, written back, no reductions (timing hook).
+template <typename T, int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_update(const typename vec2<T>::type* __restrict__ V, size_t vstride,
+                                                       typename vec2<T>::type* __restrict__ wbase, size_t N,
+                                                       ArnoldiState st, int j, int nb, int write_next,
+                                                       int only_update) {
+  typedef typename vec2<T>::type T2;
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int m = st.m;
+  __shared__ T2 cf[JB];
+  if (threadIdx.x <= j && threadIdx.x < JB) {
+    const double2 q = st.proj[(size_t)rhs * kProjMax + threadIdx.x];
+    cf[threadIdx.x].x = (T)q.x;
+    cf[threadIdx.x].y = (T)q.y;
+  }
+  __syncthreads();
+  const size_t off = (size_t)rhs * N;
+  T2* w = wbase + off;
+  T ax[JB + 1], ay[JB + 1];
+#pragma unroll
+  for (int i = 0; i <= JB; ++i) { ax[i] = 0; ay[i] = 0; }
+  for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
+    T2 wv = w[p];
+    T2 vv[JB];
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) {
+        vv[i] = V[(size_t)i * vstride + off + p];
+        wv = csub(wv, cmul(cf[i], vv[i]));
+      }
+    if (write_next || only_update) w[p] = wv;
+    if (!only_update) {
+#pragma unroll
+      for (int i = 0; i < JB; ++i)
+        if (i <= j) cdot_acc(ax[i], ay[i], vv[i], wv);
+      ax[JB] += wv.x * wv.x + wv.y * wv.y;
+    }
+  }
+  if (only_update) return;
+  __shared__ double2 tot[JB + 2];
+  if (!reduce_many<JB + 1, T>(ax, ay, j, true, st, rhs, nb, tot) || threadIdx.x != 0) return;
+  double2* Hw = st.H + (size_t)rhs * (m + 1) * m;
+  double2* proj = st.proj + (size_t)rhs * kProjMax;
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    Hw[(size_t)i * m + j] = dadd(Hw[(size_t)i * m + j], tot[i]);
+    proj[i] = tot[i];
+    s += tot[i].x * tot[i].x + tot[i].y * tot[i].y;
+  }
+  const double nu2 = tot[j + 1].x - s;
+  Hw[(size_t)(j + 1) * m + j] = d2(nu2 > 0.0 ? sqrt(nu2) : 0.0, 0);
+  givens_step(st, rhs, j);
+}
+
+// Sweep C: v_{j+1} = (w' - sum d_i v_i) / h_{j+1,j} for right-hand sides that continue.
+template <typename T, int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_finish(const typename vec2<T>::type* __restrict__ V, size_t vstride,
+                                                       typename vec2<T>::type* __restrict__ wbase, size_t N,
+                                                       ArnoldiState st, int j, int nb) {
+  typedef typename vec2<T>::type T2;
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int m = st.m;
+  __shared__ T2 cf[JB];
+  if (threadIdx.x <= j && threadIdx.x < JB) {
+    const double2 q = st.proj[(size_t)rhs * kProjMax + threadIdx.x];
+    cf[threadIdx.x].x = (T)q.x;
+    cf[threadIdx.x].y = (T)q.y;
+  }
+  __syncthreads();
+  const T inv = (T)(1.0 / st.H[(size_t)rhs * (m + 1) * m + (size_t)(j + 1) * m + j].x);
+  const size_t off = (size_t)rhs * N;
+  T2* w = wbase + off;
+  for (size_t p = (size_t)blockIdx.x * NT + threadIdx.x; p < N; p += (size_t)nb * NT) {
+    T2 wv = w[p];
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) wv = csub(wv, cmul(cf[i], V[(size_t)i * vstride + off + p]));
+    w[p] = cscale(wv, inv);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 forms of the three CGS2 sweeps for the 5-point operator: each thread takes two
+// consecutive nodes per visit (16-byte loads and stores; nx even, so a pair never
+// crosses a row), which halves the load instructions and doubles the bytes in flight.
+// Same arithmetic as the generic kernels above.
+// ---------------------------------------------------------------------------
+struct F2x2 { float2 a, b; };
+__device__ __forceinline__ F2x2 ldp(const float2* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+__device__ __forceinline__ void stp(float2* p, F2x2 v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
+
+template <int BC, int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_project2(Op<float> op, const float2* __restrict__ z,
+                                                         const float2* __restrict__ V, size_t vstride,
+                                                         float2* __restrict__ wbase, ArnoldiState st, int j, int nb) {
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int nx = op.nx, ny = op.ny;
+  const unsigned N = (unsigned)nx * (unsigned)ny, half = N / 2;
+  const size_t off = (size_t)rhs * N;
+  const float2* zr = z + off;
+  float2* w = wbase + off;
+  float ax[JB], ay[JB];
+#pragma unroll
+  for (int i = 0; i < JB; ++i) { ax[i] = 0; ay[i] = 0; }
+  for (unsigned q = blockIdx.x * NT + threadIdx.x; q < half; q += (unsigned)nb * NT) {
+    const unsigned p = 2 * q;
+    const int y = (int)(p / (unsigned)nx), x = (int)(p - (unsigned)y * nx);
+    const F2x2 c = ldp(zr + p);
+    const F2x2 dn = y > 0 ? ldp(zr + p - nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const F2x2 up = y < ny - 1 ? ldp(zr + p + nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float2 lf = x > 0 ? zr[p - 1] : make_float2(0.f, 0.f);
+    const float2 rt = x + 2 < nx ? zr[p + 2] : make_float2(0.f, 0.f);
+    const float2 kk = *reinterpret_cast<const float2*>(op.k2 + p);
+    F2x2 r;
+    {
+      const float2 s = stencil_sum<2, BC>(op, x, y, [&](int dx, int dy) {
+        return dx < 0 ? lf : dx > 0 ? c.b : dy < 0 ? dn.a : up.a;
+      });
+      r.a = cmul(diag_k2<BC, 2>(op, x, y, kk.x), c.a);
+      r.a.x -= s.x * op.inv_h2;
+      r.a.y -= s.y * op.inv_h2;
+    }
+    {
+      const float2 s = stencil_sum<2, BC>(op, x + 1, y, [&](int dx, int dy) {
+        return dx < 0 ? c.a : dx > 0 ? rt : dy < 0 ? dn.b : up.b;
+      });
+      r.b = cmul(diag_k2<BC, 2>(op, x + 1, y, kk.y), c.b);
+      r.b.x -= s.x * op.inv_h2;
+      r.b.y -= s.y * op.inv_h2;
+    }
+    stp(w + p, r);
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) {
+        const F2x2 vi = ldp(V + (size_t)i * vstride + off + p);
+        cdot_acc(ax[i], ay[i], vi.a, r.a);
+        cdot_acc(ax[i], ay[i], vi.b, r.b);
+      }
+  }
+  __shared__ double2 tot[JB + 1];
+  if (!reduce_many<JB, float>(ax, ay, j, false, st, rhs, nb, tot) || threadIdx.x != 0) return;
+  const int m = st.m;
+  double2* Hc = st.H + (size_t)rhs * (m + 1) * m;
+  double2* proj = st.proj + (size_t)rhs * kProjMax;
+  for (int i = 0; i <= j; ++i) {
+    Hc[(size_t)i * m + j] = tot[i];
+    proj[i] = tot[i];
+  }
+}
+
+template <int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_update2(const float2* __restrict__ V, size_t vstride,
+                                                        float2* __restrict__ wbase, unsigned N, ArnoldiState st, int j,
+                                                        int nb, int write_next, int only_update) {
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int m = st.m;
+  __shared__ float2 cf[JB];
+  if (threadIdx.x <= j && threadIdx.x < JB) {
+    const double2 q = st.proj[(size_t)rhs * kProjMax + threadIdx.x];
+    cf[threadIdx.x] = make_float2((float)q.x, (float)q.y);
+  }
+  __syncthreads();
+  const size_t off = (size_t)rhs * N;
+  float2* w = wbase + off;
+  float ax[JB + 1], ay[JB + 1];
+#pragma unroll
+  for (int i = 0; i <= JB; ++i) { ax[i] = 0; ay[i] = 0; }
+  const unsigned half = N / 2;
+  for (unsigned q = blockIdx.x * NT + threadIdx.x; q < half; q += (unsigned)nb * NT) {
+    const unsigned p = 2 * q;
+    F2x2 wv = ldp(w + p);
+    F2x2 vv[JB];
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) {
+        vv[i] = ldp(V + (size_t)i * vstride + off + p);
+        wv.a = csub(wv.a, cmul(cf[i], vv[i].a));
+        wv.b = csub(wv.b, cmul(cf[i], vv[i].b));
+      }
+    if (write_next || only_update) stp(w + p, wv);
+    if (!only_update) {
+#pragma unroll
+      for (int i = 0; i < JB; ++i)
+        if (i <= j) {
+          cdot_acc(ax[i], ay[i], vv[i].a, wv.a);
+          cdot_acc(ax[i], ay[i], vv[i].b, wv.b);
+        }
+      ax[JB] += wv.a.x * wv.a.x + wv.a.y * wv.a.y + wv.b.x * wv.b.x + wv.b.y * wv.b.y;
+    }
+  }
+  if (only_update) return;
+  __shared__ double2 tot[JB + 2];
+  if (!reduce_many<JB + 1, float>(ax, ay, j, true, st, rhs, nb, tot) || threadIdx.x != 0) return;
+  double2* Hw = st.H + (size_t)rhs * (m + 1) * m;
+  double2* proj = st.proj + (size_t)rhs * kProjMax;
+  double s = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    Hw[(size_t)i * m + j] = dadd(Hw[(size_t)i * m + j], tot[i]);
+    proj[i] = tot[i];
+    s += tot[i].x * tot[i].x + tot[i].y * tot[i].y;
+  }
+  const double nu2 = tot[j + 1].x - s;
+  Hw[(size_t)(j + 1) * m + j] = d2(nu2 > 0.0 ? sqrt(nu2) : 0.0, 0);
+  givens_step(st, rhs, j);
+}
+
+template <int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_finish2(const float2* __restrict__ V, size_t vstride,
+                                                        float2* __restrict__ wbase, unsigned N, ArnoldiState st, int j,
+                                                        int nb) {
+  const int rhs = blockIdx.y;
+  if (!st.active[rhs]) return;
+  const int m = st.m;
+  __shared__ float2 cf[JB];
+  if (threadIdx.x <= j && threadIdx.x < JB) {
+    const double2 q = st.proj[(size_t)rhs * kProjMax + threadIdx.x];
+    cf[threadIdx.x] = make_float2((float)q.x, (float)q.y);
+  }
+  __syncthreads();
+  const float inv = (float)(1.0 / st.H[(size_t)rhs * (m + 1) * m + (size_t)(j + 1) * m + j].x);
+  const size_t off = (size_t)rhs * N;
+  float2* w = wbase + off;
+  const unsigned half = N / 2;
+  for (unsigned q = blockIdx.x * NT + threadIdx.x; q < half; q += (unsigned)nb * NT) {
+    const unsigned p = 2 * q;
+    F2x2 wv = ldp(w + p);
+#pragma unroll
+    for (int i = 0; i < JB; ++i)
+      if (i <= j) {
+        const F2x2 vi = ldp(V + (size_t)i * vstride + off + p);
+        wv.a = csub(wv.a, cmul(cf[i], vi.a));
+        wv.b = csub(wv.b, cmul(cf[i], vi.b));
+      }
+    wv.a = cscale(wv.a, inv);
+    wv.b = cscale(wv.b, inv);
+    stp(w + p, wv);
+  }
+}
+
 // y = R^-1 g over the k steps taken (one thread per right-hand side).
 __global__ void k_backsolve(ArnoldiState st, int nrhs, int* iters) {
   const int rhs = blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,6 +799,92 @@ void launch_normalize(void* w, size_t N, int nrhs, int j, ArnoldiState& st, int 
   typedef typename vec2<T>::type T2;
   k_normalize<T><<<dim3(nb, nrhs), NT, 0, s>>>((T2*)w, N, j, st, nb);
 }
+namespace {
+// Basis-length bucket of an Arnoldi column with j + 1 coefficients.
+template <typename F> void with_jb(int j, F f) {
+  if (j < 4) f(std::integral_constant<int, 4>());
+  else if (j < 8) f(std::integral_constant<int, 8>());
+  else if (j < 12) f(std::integral_constant<int, 12>());
+  else if (j < 16) f(std::integral_constant<int, 16>());
+  else if (j < 24) f(std::integral_constant<int, 24>());
+  else f(std::integral_constant<int, 32>());
+}
+}  // namespace
+
+// The pair kernels apply: FP32, the 5-point stencil, no diagonal scaling, an even point
+// count and 16-byte aligned vectors.
+template <typename T>
+bool use_pairs(const Op<T>& op, bool diag_precond, const void* z, const void* V, size_t vstride) {
+  const size_t N = (size_t)op.nx * op.ny;
+  return sizeof(T) == 4 && !diag_precond && op.order == 2 && (op.nx % 2) == 0 && N < (1u << 31) &&
+         (vstride % 2) == 0 && (!z || ((uintptr_t)z & 15u) == 0) && ((uintptr_t)V & 15u) == 0;
+}
+template <typename F> void with_bc(int bc, F f) {
+  if (bc == kBcReflect) f(std::integral_constant<int, kBcReflect>());
+  else if (bc == kBcReplicate) f(std::integral_constant<int, kBcReplicate>());
+  else f(std::integral_constant<int, kBcDirichlet>());
+}
+
+template <typename T>
+void launch_arnoldi(const Op<T>& op, bool diag_precond, const void* z, void* V, size_t vstride, int nrhs,
+                    ArnoldiState& st, int j, int m, int nb, cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  const size_t N = (size_t)op.nx * op.ny;
+  const int write_next = j + 1 < m ? 1 : 0;
+  if (use_pairs(op, diag_precond, z, V, vstride)) {
+    const Op<float>& opf = reinterpret_cast<const Op<float>&>(op);
+    float2* w = (float2*)V + (size_t)(j + 1) * vstride;
+    with_jb(j, [&](auto jb) {
+      constexpr int JB = decltype(jb)::value;
+      with_bc(op.bc, [&](auto bc) {
+        k_arnoldi_project2<decltype(bc)::value, JB><<<dim3(nb, nrhs), NT, 0, s>>>(
+            opf, (const float2*)z, (const float2*)V, vstride, w, st, j, nb);
+      });
+      k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb,
+                                                          write_next, 0);
+      if (write_next)
+        k_arnoldi_finish2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb);
+    });
+    return;
+  }
+  with_jb(j, [&](auto jb) {
+    constexpr int JB = decltype(jb)::value;
+    T2* w = (T2*)V + (size_t)(j + 1) * vstride;
+    auto ka = op.order == 4 ? k_arnoldi_project<T, 4, JB> : k_arnoldi_project<T, 2, JB>;
+    ka<<<dim3(nb, nrhs), NT, 0, s>>>(op, diag_precond ? 1 : 0, (const T2*)z, (const T2*)V, vstride, w, st, j, nb);
+    k_arnoldi_update<T, JB><<<dim3(nb, nrhs), NT, 0, s>>>((const T2*)V, vstride, w, N, st, j, nb, write_next, 0);
+    if (write_next) k_arnoldi_finish<T, JB><<<dim3(nb, nrhs), NT, 0, s>>>((const T2*)V, vstride, w, N, st, j, nb);
+  });
+}
+
+template <typename T>
+void launch_arnoldi_sweep(int which, const Op<T>& op, const void* z, void* V, size_t vstride, int nrhs,
+                          ArnoldiState& st, int j, int nb, cudaStream_t s) {
+  typedef typename vec2<T>::type T2;
+  const size_t N = (size_t)op.nx * op.ny;
+  T2* w = (T2*)V + (size_t)(j + 1) * vstride;
+  const bool pairs = use_pairs(op, false, z, V, vstride);
+  with_jb(j, [&](auto jb) {
+    constexpr int JB = decltype(jb)::value;
+    if (pairs) {
+      const Op<float>& opf = reinterpret_cast<const Op<float>&>(op);
+      if (which == 0)
+        with_bc(op.bc, [&](auto bc) {
+          k_arnoldi_project2<decltype(bc)::value, JB><<<dim3(nb, nrhs), NT, 0, s>>>(
+              opf, (const float2*)z, (const float2*)V, vstride, (float2*)w, st, j, nb);
+        });
+      else
+        k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, (float2*)w, (unsigned)N, st,
+                                                            j, nb, 0, 1);
+    } else if (which == 0) {
+      auto ka = op.order == 4 ? k_arnoldi_project<T, 4, JB> : k_arnoldi_project<T, 2, JB>;
+      ka<<<dim3(nb, nrhs), NT, 0, s>>>(op, 0, (const T2*)z, (const T2*)V, vstride, w, st, j, nb);
+    } else {
+      k_arnoldi_update<T, JB><<<dim3(nb, nrhs), NT, 0, s>>>((const T2*)V, vstride, w, N, st, j, nb, 0, 1);
+    }
+  });
+}
+
 void launch_backsolve(ArnoldiState& st, int nrhs, int* iters, cudaStream_t s) {
   k_backsolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st, nrhs, iters);
 }
@@ -464,6 +926,10 @@ void launch_update_x(const void* Z, size_t vstride, size_t N, int nrhs, ArnoldiS
   template void launch_mgs<T>(const void*, size_t, void*, size_t, int, int, int, ArnoldiState&, int,            \
                               cudaStream_t);                                                                    \
   template void launch_normalize<T>(void*, size_t, int, int, ArnoldiState&, int, cudaStream_t);                 \
+  template void launch_arnoldi<T>(const Op<T>&, bool, const void*, void*, size_t, int, ArnoldiState&, int, int, \
+                                  int, cudaStream_t);                                                           \
+  template void launch_arnoldi_sweep<T>(int, const Op<T>&, const void*, void*, size_t, int, ArnoldiState&, int,  \
+                                        int, cudaStream_t);                                                     \
   template void launch_combine<T>(const void*, size_t, size_t, int, ArnoldiState&, const Op<T>*, void*,        \
                                   const int*, int, cudaStream_t);                                               \
   template void launch_true_residual<T>(const Op<double>&, const double2*, const double2*, void*, int,          \

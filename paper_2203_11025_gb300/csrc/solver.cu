@@ -148,9 +148,11 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
   const size_t N0 = level_points(c, 0), Nc = level_points(c, L - 1);
   const int mc = c->d.coarse_its;
   const int nbmax = 4096;
+  const int mcap = c->nsm * 8 + 8;   // >= every vec_blocks() count
   auto st_bytes = [&](int mm) {
     return (size_t)nrhs * ((size_t)(mm + 1) * mm * 16 * 2 + mm * 8 + mm * 16 + (mm + 1) * 16 + mm * 16 + 8 * 3 +
-                           4 * 4 + (size_t)nbmax * 16) + 256 * 16;
+                           4 * 4 + (size_t)nbmax * 16 + (size_t)kProjMax * 16 +
+                           (size_t)(kProjMax + 1) * mcap * 16) + 256 * 20;
   };
   size_t total = 0;
   for (int l = 0; l < L; ++l) total += 4 * (nrhs * level_points(c, l) * es + 256);
@@ -199,6 +201,9 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
     st.kmax = (int*)W.arena.take((size_t)nrhs * 4);
     st.counter = (int*)W.arena.take((size_t)nrhs * 4);
     st.part = (double2*)W.arena.take((size_t)nrhs * nbmax * 16);
+    st.proj = (double2*)W.arena.take((size_t)nrhs * kProjMax * 16);
+    st.mcap = mcap;
+    st.mpart = (double2*)W.arena.take((size_t)nrhs * (kProjMax + 1) * mcap * 16);
   };
   make_st(W.cst, mc);
   make_st(W.fst, m);
@@ -208,7 +213,7 @@ int ensure_work(helm_ctx* c, int nrhs, int m) {
   W.ss.iters = (int*)W.arena.take((size_t)nrhs * 4);
   W.ss.status = (int*)W.arena.take((size_t)nrhs * 4);
   W.ss.maxit_rhs = nullptr;
-  if (!W.ss.status || !W.fst.part) {
+  if (!W.ss.status || !W.fst.part || !W.fst.mpart || !W.cst.mpart) {
     g_err = "workspace layout overflow";
     free_work(W);
     return HELM_ENOMEM;
@@ -246,12 +251,8 @@ int coarse_gmres(helm_ctx* c, const void* f, void* out, int nrhs, const int* gat
   ArnoldiState& st = W.cst;
   const int nb = vec_blocks(Nc, nrhs, c->nsm);
   launch_start<T>(f, CV, Nc, nrhs, st, nb, gate, s);
-  for (int j = 0; j < mc; ++j) {
-    void* w = CV + (size_t)(j + 1) * vstride * es;
-    launch_apply_dot<T>(op, true, CV + (size_t)j * vstride * es, w, CV, nrhs, st, j, nb, s);
-    for (int i = 1; i <= j + 1; ++i) launch_mgs<T>(CV, vstride, w, Nc, nrhs, j, i, st, nb, s);
-    if (j + 1 < mc) launch_normalize<T>(w, Nc, nrhs, j, st, nb, s);
-  }
+  for (int j = 0; j < mc; ++j)
+    launch_arnoldi<T>(op, true, CV + (size_t)j * vstride * es, CV, vstride, nrhs, st, j, mc, nb, s);
   launch_backsolve(st, nrhs, nullptr, s);
   launch_combine<T>(CV, vstride, Nc, nrhs, st, &op, out, gate, nb, s);
   HLAUNCH();
@@ -358,9 +359,7 @@ int fgmres_cycle(helm_ctx* c, int precond, void* net, double2* x, int nrhs, int 
     void* zj = Z + (size_t)j * vstride * es;
     void* w = V + (size_t)(j + 1) * vstride * es;
     HTRY(precond_apply<T>(c, precond, net, vj, zj, nrhs, st.active, s));
-    launch_apply_dot<T>(A, false, zj, w, V, nrhs, st, j, nb, s);
-    for (int i = 1; i <= j + 1; ++i) launch_mgs<T>(V, vstride, w, N, nrhs, j, i, st, nb, s);
-    if (j + 1 < m) launch_normalize<T>(w, N, nrhs, j, st, nb, s);
+    launch_arnoldi<T>(A, false, zj, V, vstride, nrhs, st, j, m, nb, s);
   }
   launch_backsolve(st, nrhs, W.ss.iters, s);
   launch_update_x<T>(Z, vstride, N, nrhs, st, x, nb, s);
@@ -1139,9 +1138,12 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
     const int lc = h->d.levels - 1;
     HCHECK(cudaMemcpyAsync(W.F[lc], V, (size_t)nrhs * level_points(h, lc) * es, cudaMemcpyDeviceToDevice, s));
   }
-  std::vector<int> ones(nrhs, 1);
+  std::vector<int> ones(nrhs, 1), many(nrhs, 1 << 30);
   HCHECK(cudaMemcpyAsync(W.fst.active, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
-  HCHECK(cudaMemcpyAsync(W.fst.kmax, ones.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  // a step limit never reached and a zero tolerance keep every right-hand side active
+  HCHECK(cudaMemcpyAsync(W.fst.kmax, many.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, s));
+  HCHECK(cudaMemsetAsync(W.fst.tol_abs, 0, (size_t)nrhs * sizeof(double), s));
+  HCHECK(cudaMemsetAsync(W.fst.proj, 0, (size_t)nrhs * kProjMax * sizeof(double2), s));
   HCHECK(cudaStreamSynchronize(s));
   auto run = [&](void) -> int {
     switch (kernel) {
@@ -1149,7 +1151,8 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
       case 1: launch_resid_restrict<float>(M, 0.8f, V, nullptr, W.F[1], nrhs, nullptr, s); break;
       case 2: launch_prolong_jacobi<float>(M, 0.8f, V, nullptr, true, W.E[1], h->L[1].nx, h->L[1].ny,
                                            V + vstride * es, nrhs, nullptr, s); break;
-      case 3: launch_mgs<float>(V, vstride, V + 5 * vstride * es, N, nrhs, 4, 2, W.fst, nb, s); break;
+      case 3: launch_arnoldi_sweep<float>(1, A, nullptr, V, vstride, nrhs, W.fst, 4, nb, s); break;
+      case 6: launch_arnoldi_sweep<float>(0, A, V + 6 * vstride * es, V, vstride, nrhs, W.fst, 4, nb, s); break;
       case 4: return vcycle<float>(h, 0, V, nullptr, V + vstride * es, nrhs, nullptr, s);
       case 5: return coarse_gmres<float>(h, W.F[h->d.levels - 1], W.E[h->d.levels - 1], nrhs, nullptr, s);
       default: g_err = "unknown kernel id"; return HELM_EINVAL;
@@ -1161,7 +1164,8 @@ int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t str
     case 0: *bytes = 20.0 * n; break;
     case 1: *bytes = 12.0 * n + 8.0 * nc; break;
     case 2: *bytes = 20.0 * n + 8.0 * nc; break;
-    case 3: *bytes = 32.0 * n; break;
+    case 3: *bytes = 56.0 * n; break;   // w and v_0..v_4 read, w written
+    case 6: *bytes = 60.0 * n; break;   // z, kappa^2 and v_0..v_4 read, w written
     default: *bytes = 0.0; break;
   }
   HTRY(run());  // warm-up

@@ -10,22 +10,36 @@
 //                        followed by the post-smoothing sweep
 // Every kernel is templated on the real type T (float for the solver, double
 // for FP64 verification runs).  Layout: complex interleaved, [rhs][y][x].
+#include <cstdint>
+#include <type_traits>
+
 #include "helm_internal.cuh"
 
 namespace helm {
 
 namespace {
 
-constexpr int BX = 32, BY = 8;  // 256 threads, one point (fine or coarse) per thread
+constexpr int BX = 32, BY = 8;  // 256 threads
 
-template <int ORD, typename T>
+// Boundary mode and stencil order as template arguments: every operator kernel is
+// instantiated for the 5-point stencil with each boundary mode and for the compact
+// scheme (Dirichlet), so no runtime branch on either remains in the inner loops.
+template <int O, int B> struct Kind { static constexpr int ORD = O, BC = B; };
+template <typename F> void with_kind(int order, int bc, F f) {
+  if (order == 4) f(Kind<4, kBcDirichlet>());
+  else if (bc == kBcReflect) f(Kind<2, kBcReflect>());
+  else if (bc == kBcReplicate) f(Kind<2, kBcReplicate>());
+  else f(Kind<2, kBcDirichlet>());
+}
+
+template <int ORD, int BC, typename T>
 __device__ __forceinline__ typename vec2<T>::type apply_at(const Op<T>& op, const typename vec2<T>::type* u,
                                                            int x, int y) {
   typedef typename vec2<T>::type T2;
   size_t p = (size_t)y * op.nx + x;
   T2 c = u[p];
-  const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return u[(ptrdiff_t)p + (ptrdiff_t)dy * op.nx + dx]; });
-  T2 d = diag_at(op, x, y);
+  const T2 s = stencil_sum<ORD, BC>(op, x, y, [&](int dx, int dy) { return u[(ptrdiff_t)p + (ptrdiff_t)dy * op.nx + dx]; });
+  T2 d = diag_at<BC, ORD>(op, x, y);
   T2 r = cmul(d, c);
   r.x -= s.x * op.inv_h2;
   r.y -= s.y * op.inv_h2;
@@ -33,7 +47,7 @@ __device__ __forceinline__ typename vec2<T>::type apply_at(const Op<T>& op, cons
 }
 
 // y = K x  (b == nullptr)   or   y = b - K x
-template <typename T, int ORD>
+template <typename T, int ORD, int BC>
 __global__ void __launch_bounds__(256) k_apply(Op<T> op, const typename vec2<T>::type* __restrict__ x,
                                                const typename vec2<T>::type* __restrict__ b,
                                                typename vec2<T>::type* __restrict__ y, const int* active) {
@@ -42,7 +56,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, const typename vec2<T>:
   const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= op.nx || iy >= op.ny) return;
   const size_t N = (size_t)op.nx * op.ny, off = (size_t)rhs * N, p = (size_t)iy * op.nx + ix;
-  auto ku = apply_at<ORD>(op, x + off, ix, iy);
+  auto ku = apply_at<ORD, BC>(op, x + off, ix, iy);
   if (b) ku = csub(b[off + p], ku);
   y[off + p] = ku;
 }
@@ -65,7 +79,7 @@ __global__ void __launch_bounds__(256) k_rhs_weight(int nx, int ny, const typena
 }
 
 // x_out = x_in + w D^-1 (f - K x_in);   x_in == nullptr means a zero guess: x_out = w D^-1 f
-template <typename T, int ORD>
+template <typename T, int ORD, int BC>
 __global__ void __launch_bounds__(256) k_jacobi(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                 const typename vec2<T>::type* __restrict__ xin,
                                                 typename vec2<T>::type* __restrict__ xout, const int* active) {
@@ -76,8 +90,8 @@ __global__ void __launch_bounds__(256) k_jacobi(Op<T> op, T w, const typename ve
   if (ix >= op.nx || iy >= op.ny) return;
   const size_t N = (size_t)op.nx * op.ny, off = (size_t)rhs * N, p = (size_t)iy * op.nx + ix;
   T2 r = f[off + p];
-  if (xin) r = csub(r, apply_at<ORD>(op, xin + off, ix, iy));
-  T2 c = cscale(cmul(r, cinv(diag_at(op, ix, iy))), w);
+  if (xin) r = csub(r, apply_at<ORD, BC>(op, xin + off, ix, iy));
+  T2 c = cscale(cmul(r, crecip(diag_at<BC, ORD>(op, ix, iy))), w);
   if (xin) c = cadd(c, xin[off + p]);
   xout[off + p] = c;
 }
@@ -152,54 +166,62 @@ __global__ void __launch_bounds__(256) k_prolong_add(int nxc, int nyc, int nx, i
 }
 
 // ---------------------------------------------------------------------------
-// Fused: f_c = R (f - K v) over a coarse tile of BY x BX points.
+// Fused: f_c = R (f - K v) over a coarse tile of (BY RPT) x BX points.
 // v == nullptr: v = w D^-1 f (one Jacobi sweep from a zero guess), computed in
 // shared memory for the tile plus a 2-node halo, never written to memory.
+// Shared memory: v on the fine region (halo 2), f and kappa^2 on the residual region
+// (halo 1); the residual overwrites f.  Each fine node's diagonal is formed twice
+// (for v and for the residual) from kappa^2 without a division; D^-1 costs one
+// reciprocal.  RPT (coarse rows per thread) sets the tile height.
 // ---------------------------------------------------------------------------
-constexpr int RR_Y = 2 * BY + 3, RR_X = 2 * BX + 3;  // v region (fine), halo 2
-constexpr int RI_Y = 2 * BY + 1, RI_X = 2 * BX + 1;  // residual region, halo 1
-
-template <typename T, int ORD>
+template <typename T, int ORD, int BC, int RPT>
 __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                         const typename vec2<T>::type* __restrict__ v,
                                                         typename vec2<T>::type* __restrict__ fc,
                                                         const int* active) {
   typedef typename vec2<T>::type T2;
-  __shared__ T2 s_v[RR_Y][RR_X];
-  __shared__ T2 s_r[RI_Y][RI_X];
+  constexpr int TY = BY * RPT;                     // coarse rows per tile
+  constexpr int RY = 2 * TY + 3, RX = 2 * BX + 3;  // v region (fine), halo 2
+  constexpr int IY = 2 * TY + 1, IX = 2 * BX + 1;  // residual region, halo 1
+  __shared__ T2 s_v[RY][RX];
+  __shared__ T2 s_r[IY][IX];
+  __shared__ T s_k[IY][IX];
   const int rhs = blockIdx.z;
   if (active && !active[rhs]) return;
   const int nx = op.nx, ny = op.ny, nxc = nx / 2, nyc = ny / 2;
   const size_t N = (size_t)nx * ny;
   const T2* fr = f + (size_t)rhs * N;
   const T2* vr = v ? v + (size_t)rhs * N : nullptr;
-  const int I0 = blockIdx.y * BY, J0 = blockIdx.x * BX;
+  const int I0 = blockIdx.y * TY, J0 = blockIdx.x * BX;
   const int fy0 = 2 * I0 - 2, fx0 = 2 * J0 - 2;
   const int tid = threadIdx.y * BX + threadIdx.x;
-  // 1) v on the region, f on the inner (residual) region
-  for (int q = tid; q < RR_Y * RR_X; q += BX * BY) {
-    int ry = q / RR_X, rx = q - ry * RR_X;
-    int y = fy0 + ry, x = fx0 + rx;
+  // 1) v on the region; f and kappa^2 on the inner (residual) region
+  for (int q = tid; q < RY * RX; q += BX * BY) {
+    const int ry = q / RX, rx = q - ry * RX;
+    const int y = fy0 + ry, x = fx0 + rx;
     T2 vv = czero<T2>(), ff = czero<T2>();
+    T kk = T(0);
     if (y >= 0 && y < ny && x >= 0 && x < nx) {
-      size_t p = (size_t)y * nx + x;
+      const size_t p = (size_t)y * nx + x;
       ff = fr[p];
-      vv = vr ? vr[p] : cscale(cmul(ff, cinv(diag_at(op, x, y))), w);
+      kk = op.k2[p];
+      vv = vr ? vr[p] : cscale(cmul(ff, crecip(diag_k2<BC, ORD>(op, x, y, kk))), w);
     }
     s_v[ry][rx] = vv;
-    if (ry >= 1 && ry <= RI_Y && rx >= 1 && rx <= RI_X) s_r[ry - 1][rx - 1] = ff;
+    if (ry >= 1 && ry <= IY && rx >= 1 && rx <= IX) {
+      s_r[ry - 1][rx - 1] = ff;
+      s_k[ry - 1][rx - 1] = kk;
+    }
   }
   __syncthreads();
   // 2) r = f - K v on the inner region (zero outside the grid)
-  for (int q = tid; q < RI_Y * RI_X; q += BX * BY) {
-    int ry = q / RI_X, rx = q - ry * RI_X;
-    int y = fy0 + 1 + ry, x = fx0 + 1 + rx;
+  for (int q = tid; q < IY * IX; q += BX * BY) {
+    const int ry = q / IX, rx = q - ry * IX;
+    const int y = fy0 + 1 + ry, x = fx0 + 1 + rx;
     if (y >= 0 && y < ny && x >= 0 && x < nx) {
-      int sy = ry + 1, sx = rx + 1;
-      T2 c = s_v[sy][sx];
-      // neighbours inside the grid, from the tile (boundary terms in stencil_sum / diag_at)
-      const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return s_v[sy + dy][sx + dx]; });
-      T2 kv = cmul(diag_at(op, x, y), c);
+      const int sy = ry + 1, sx = rx + 1;
+      const T2 s = stencil_sum<ORD, BC>(op, x, y, [&](int dx, int dy) { return s_v[sy + dy][sx + dx]; });
+      T2 kv = cmul(diag_k2<BC, ORD>(op, x, y, s_k[ry][rx]), s_v[sy][sx]);
       kv.x -= s.x * op.inv_h2;
       kv.y -= s.y * op.inv_h2;
       s_r[ry][rx] = csub(s_r[ry][rx], kv);
@@ -207,38 +229,46 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typ
   }
   __syncthreads();
   // 3) full weighting
-  const int I = I0 + threadIdx.y, J = J0 + threadIdx.x;
-  if (I < nyc && J < nxc) {
-    const int cy = 2 * threadIdx.y + 1, cx = 2 * threadIdx.x + 1;
-    T2 acc = czero<T2>();
+  const int J = J0 + threadIdx.x;
 #pragma unroll
-    for (int a = -1; a <= 1; ++a) {
-      T wy = (a == 0) ? T(2) : T(1);
+  for (int k = 0; k < RPT; ++k) {
+    const int ty = threadIdx.y + k * BY, I = I0 + ty;
+    if (I < nyc && J < nxc) {
+      const int cy = 2 * ty + 1, cx = 2 * threadIdx.x + 1;
+      T2 acc = czero<T2>();
 #pragma unroll
-      for (int b = -1; b <= 1; ++b) {
-        T wgt = wy * ((b == 0) ? T(2) : T(1)) * T(0.0625);
-        T2 r = s_r[cy + a][cx + b];
-        acc.x += wgt * r.x;
-        acc.y += wgt * r.y;
+      for (int a = -1; a <= 1; ++a) {
+        const T wy = (a == 0) ? T(2) : T(1);
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+          const T wgt = wy * ((b == 0) ? T(2) : T(1)) * T(0.0625);
+          const T2 r = s_r[cy + a][cx + b];
+          acc.x += wgt * r.x;
+          acc.y += wgt * r.y;
+        }
       }
+      fc[(size_t)rhs * nxc * nyc + (size_t)I * nxc + J] = acc;
     }
-    fc[(size_t)rhs * nxc * nyc + (size_t)I * nxc + J] = acc;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Fused: out = x + w D^-1 (f - K x) with x = v + P e_c, on a fine BY x BX tile.
+// Fused: out = x + w D^-1 (f - K x) with x = v + P e_c, on a fine (BY RPT) x BX tile.
 // v == nullptr: v = w D^-1 f when implicit_v (the pre-smoothing result from a
-// zero guess), else v = 0.
+// zero guess), else v = 0.  x on the tile plus a 1-node halo in shared memory; f
+// and kappa^2 of the tile's own nodes too.
 // ---------------------------------------------------------------------------
-template <typename T, int ORD>
+template <typename T, int ORD, int BC, int RPT>
 __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typename vec2<T>::type* __restrict__ f,
                                                         const typename vec2<T>::type* __restrict__ v,
                                                         int implicit_v, const typename vec2<T>::type* __restrict__ ec,
                                                         int nxc, int nyc, typename vec2<T>::type* __restrict__ out,
                                                         const int* active) {
   typedef typename vec2<T>::type T2;
-  __shared__ T2 s_x[BY + 2][BX + 2];
+  constexpr int TY = BY * RPT;
+  __shared__ T2 s_x[TY + 2][BX + 2];
+  __shared__ T2 s_f[TY][BX];
+  __shared__ T s_k[TY][BX];
   const int rhs = blockIdx.z;
   if (active && !active[rhs]) return;
   const int nx = op.nx, ny = op.ny;
@@ -246,32 +276,259 @@ __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typ
   const T2* fr = f + (size_t)rhs * N;
   const T2* vr = v ? v + (size_t)rhs * N : nullptr;
   const T2* er = ec + (size_t)rhs * nxc * nyc;
-  const int y0 = blockIdx.y * BY - 1, x0 = blockIdx.x * BX - 1;
+  const int y0 = blockIdx.y * TY - 1, x0 = blockIdx.x * BX - 1;
   const int tid = threadIdx.y * BX + threadIdx.x;
-  for (int q = tid; q < (BY + 2) * (BX + 2); q += BX * BY) {
-    int ry = q / (BX + 2), rx = q - ry * (BX + 2);
-    int y = y0 + ry, x = x0 + rx;
+  for (int q = tid; q < (TY + 2) * (BX + 2); q += BX * BY) {
+    const int ry = q / (BX + 2), rx = q - ry * (BX + 2);
+    const int y = y0 + ry, x = x0 + rx;
     T2 xv = czero<T2>();
     if (y >= 0 && y < ny && x >= 0 && x < nx) {
-      size_t p = (size_t)y * nx + x;
-      T2 base = vr ? vr[p] : (implicit_v ? cscale(cmul(fr[p], cinv(diag_at(op, x, y))), w) : czero<T2>());
+      const size_t p = (size_t)y * nx + x;
+      const bool inner = ry >= 1 && ry <= TY && rx >= 1 && rx <= BX;
+      T2 ff = czero<T2>();
+      T kk = T(0);
+      if (implicit_v || inner) ff = fr[p];
+      if (implicit_v || inner) kk = op.k2[p];
+      const T2 base = vr ? vr[p]
+                         : (implicit_v ? cscale(cmul(ff, crecip(diag_k2<BC, ORD>(op, x, y, kk))), w) : czero<T2>());
       xv = cadd(base, prolong_at<T>(er, nxc, nyc, y, x));
+      if (inner) {
+        s_f[ry - 1][rx - 1] = ff;
+        s_k[ry - 1][rx - 1] = kk;
+      }
     }
     s_x[ry][rx] = xv;
   }
   __syncthreads();
-  const int y = blockIdx.y * BY + threadIdx.y, x = blockIdx.x * BX + threadIdx.x;
-  if (y < ny && x < nx) {
-    const int sy = threadIdx.y + 1, sx = threadIdx.x + 1;
-    T2 c = s_x[sy][sx];
-    const T2 s = stencil_sum<ORD>(op, x, y, [&](int dx, int dy) { return s_x[sy + dy][sx + dx]; });
-    T2 d = diag_at(op, x, y);
-    T2 kx = cmul(d, c);
-    kx.x -= s.x * op.inv_h2;
-    kx.y -= s.y * op.inv_h2;
-    size_t p = (size_t)y * nx + x;
-    T2 r = csub(fr[p], kx);
-    out[(size_t)rhs * N + p] = cadd(c, cscale(cmul(r, cinv(d)), w));
+  const int x = blockIdx.x * BX + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int ty = threadIdx.y + k * BY, y = blockIdx.y * TY + ty;
+    if (y < ny && x < nx) {
+      const int sy = ty + 1, sx = threadIdx.x + 1;
+      const T2 c = s_x[sy][sx];
+      const T2 s = stencil_sum<ORD, BC>(op, x, y, [&](int dx, int dy) { return s_x[sy + dy][sx + dx]; });
+      const T2 d = diag_k2<BC, ORD>(op, x, y, s_k[ty][threadIdx.x]);
+      T2 kx = cmul(d, c);
+      kx.x -= s.x * op.inv_h2;
+      kx.y -= s.y * op.inv_h2;
+      const T2 r = csub(s_f[ty][threadIdx.x], kx);
+      out[(size_t)rhs * N + (size_t)y * nx + x] = cadd(c, cscale(cmul(r, crecip(d)), w));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column-strip ("marching") forms of the two fused cycle kernels, FP32, 5-point
+// stencil.  A warp holds 64 consecutive fine columns (two per lane, 16-byte loads)
+// and walks down the rows of its segment, keeping the rows the stencil needs in
+// registers: left and right neighbours come from the adjacent lanes by shuffles,
+// those above and below from the previous and next rows.  No shared memory, no
+// block barrier, and each node's diagonal and Jacobi value are formed once.  The
+// strip's outer lanes 0 and 31 only supply the halo: a strip produces 60 fine
+// columns (30 coarse ones), strips start every 60 fine columns, and a segment
+// recomputes 2-3 halo rows.  The segment height (TI coarse rows for the
+// restriction, TY fine rows for the prolongation) trades that row halo against
+// the number of warps; the launchers take it from the tile tuner.
+// ---------------------------------------------------------------------------
+constexpr int kStripW = 60;          // fine columns a strip produces
+constexpr int kStripWarps = 4;       // warps (strips) per block
+
+struct CPair { float2 a, b; };       // complex values of columns c0 and c0 + 1
+
+__device__ __forceinline__ CPair cp_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+__device__ __forceinline__ CPair ld_pair(const float2* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+}
+__device__ __forceinline__ void st_pair(float2* p, CPair v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
+__device__ __forceinline__ float2 shfl_up1(float2 v) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
+}
+__device__ __forceinline__ float2 shfl_dn1(float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+// w f / D with one approximate reciprocal of |D|^2 (2 ulp; the FP32 stencils' tolerance is 1e-5).
+__device__ __forceinline__ float2 jacobi_from_zero(float2 f, float2 d, float w) {
+  const float r = __fdividef(w, d.x * d.x + d.y * d.y);
+  return make_float2((f.x * d.x + f.y * d.y) * r, (f.y * d.x - f.x * d.y) * r);
+}
+// K u at (x, y) = D u - s / h^2 from the node's value c and its four neighbours.
+template <int BC>
+__device__ __forceinline__ float2 op_at(const Op<float>& op, int x, int y, float2 d, float2 c, float2 l, float2 r,
+                                        float2 dn, float2 up) {
+  const float2 s = stencil_sum<2, BC>(op, x, y, [&](int dx, int dy) {
+    return dx < 0 ? l : dx > 0 ? r : dy < 0 ? dn : up;
+  });
+  float2 k = cmul(d, c);
+  k.x -= s.x * op.inv_h2;
+  k.y -= s.y * op.inv_h2;
+  return k;
+}
+
+// f_c = R (f - K v) (v == nullptr: v = w D^-1 f) for coarse rows [I0, I0 + TI) of one strip.
+template <int BC, int TI>
+__global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float> op, float w,
+                                                                     const float2* __restrict__ f,
+                                                                     const float2* __restrict__ v,
+                                                                     float2* __restrict__ fc, const int* active,
+                                                                     int nstrips) {
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+  if (strip >= nstrips) return;                  // uniform per warp
+  const int lane = threadIdx.x & 31;
+  const int nx = op.nx, ny = op.ny, nxc = nx >> 1, nyc = ny >> 1;
+  const int c0 = strip * kStripW - 2 + 2 * lane;   // even
+  const bool colin = c0 >= 0 && c0 < nx;           // both columns in or both out (nx even)
+  const size_t N = (size_t)nx * ny;
+  const float2* fr = f + (size_t)rhs * N;
+  const float2* vr = v ? v + (size_t)rhs * N : nullptr;
+  const int I0 = blockIdx.y * TI;
+  // raw row data, fetched one row ahead so that a row's loads are in flight while the
+  // previous row is computed
+  struct Raw { CPair f, v; float2 k; };
+  auto fetch = [&](int yy) {
+    Raw q;
+    q.f = q.v = cp_zero();
+    q.k = make_float2(0.f, 0.f);
+    if (colin && yy >= 0 && yy < ny) {
+      const size_t p = (size_t)yy * nx + c0;
+      q.f = ld_pair(fr + p);
+      q.k = *reinterpret_cast<const float2*>(op.k2 + p);
+      if (vr) q.v = ld_pair(vr + p);
+    }
+    return q;
+  };
+  auto prep = [&](int yy, const Raw& q, CPair& vv, CPair& dd) {
+    vv = q.v;
+    dd = cp_zero();
+    if (colin && yy >= 0 && yy < ny) {
+      dd.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
+      dd.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      if (!vr) {
+        vv.a = jacobi_from_zero(q.f.a, dd.a, w);
+        vv.b = jacobi_from_zero(q.f.b, dd.b, w);
+      }
+    }
+  };
+  CPair vm = cp_zero(), v0, d0, vp, dp, ra = cp_zero(), rb = cp_zero();
+  Raw q0 = fetch(2 * I0 - 2), qn = fetch(2 * I0 - 1);
+  CPair f0 = q0.f;
+  prep(2 * I0 - 2, q0, v0, d0);
+  float2* fco = fc + (size_t)rhs * nxc * nyc;
+  for (int yy = 2 * I0 - 1; yy <= 2 * I0 + 2 * TI; ++yy) {
+    const Raw q = qn;
+    if (yy < 2 * I0 + 2 * TI) qn = fetch(yy + 1);
+    prep(yy, q, vp, dp);
+    if (yy >= 2 * I0) {
+      const int y = yy - 1;
+      const float2 lft = shfl_up1(v0.b), rgt = shfl_dn1(v0.a);
+      CPair rc = cp_zero();
+      if (colin && y >= 0 && y < ny) {
+        rc.a = csub(f0.a, op_at<BC>(op, c0, y, d0.a, v0.a, lft, v0.b, vm.a, vp.a));
+        rc.b = csub(f0.b, op_at<BC>(op, c0 + 1, y, d0.b, v0.b, v0.a, rgt, vm.b, vp.b));
+      }
+      if ((y & 1) && y >= 2 * I0 + 1) {          // coarse row (y - 1) / 2 is complete
+        CPair rv;
+        rv.a = cadd(cadd(ra.a, rc.a), cscale(rb.a, 2.f));
+        rv.b = cadd(cadd(ra.b, rc.b), cscale(rb.b, 2.f));
+        const float2 left = shfl_up1(rv.b);
+        const int I = (y - 1) >> 1, J = c0 >> 1;
+        if (lane >= 1 && lane <= 30 && I < nyc && J < nxc)
+          fco[(size_t)I * nxc + J] = cscale(cadd(cadd(left, rv.b), cscale(rv.a, 2.f)), 0.0625f);
+      }
+      ra = rb;
+      rb = rc;
+    }
+    vm = v0; v0 = vp; f0 = q.f; d0 = dp;
+  }
+}
+
+// out = x + w D^-1 (f - K x), x = v + P e_c (v == nullptr: v = w D^-1 f if implicit_v,
+// else 0), for fine rows [Y0, Y0 + TY) of one strip.
+template <int BC, int TY>
+__global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float> op, float w,
+                                                                     const float2* __restrict__ f,
+                                                                     const float2* __restrict__ v, int implicit_v,
+                                                                     const float2* __restrict__ ec, int nxc, int nyc,
+                                                                     float2* __restrict__ out, const int* active,
+                                                                     int nstrips) {
+  const int rhs = blockIdx.z;
+  if (active && !active[rhs]) return;
+  const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+  if (strip >= nstrips) return;
+  const int lane = threadIdx.x & 31;
+  const int nx = op.nx, ny = op.ny;
+  const int c0 = strip * kStripW - 2 + 2 * lane;
+  const bool colin = c0 >= 0 && c0 < nx;
+  const int J = c0 >> 1;                           // coarse column of c0 (c0 + 1 lies between J and J + 1)
+  const size_t N = (size_t)nx * ny;
+  const float2* fr = f + (size_t)rhs * N;
+  const float2* vr = v ? v + (size_t)rhs * N : nullptr;
+  const float2* er = ec + (size_t)rhs * nxc * nyc;
+  const int Y0 = blockIdx.y * TY;
+  // coarse row I at columns J and J + 1 (zero outside the coarse grid)
+  auto ec_row = [&](int I, float2& e0, float2& e1) {
+    const bool rin = I >= 0 && I < nyc;
+    e0 = (rin && J >= 0 && J < nxc) ? er[(size_t)I * nxc + J] : make_float2(0.f, 0.f);
+    e1 = shfl_dn1(e0);
+    if (lane == 31) e1 = (rin && J + 1 < nxc) ? er[(size_t)I * nxc + J + 1] : make_float2(0.f, 0.f);
+  };
+  float2 elo0, elo1, ehi0, ehi1;
+  ec_row((Y0 - 1) >> 1, elo0, elo1);
+  ec_row(((Y0 - 1) >> 1) + 1, ehi0, ehi1);
+  struct Raw { CPair f, v; float2 k; };
+  auto fetch = [&](int yy) {
+    Raw q;
+    q.f = q.v = cp_zero();
+    q.k = make_float2(0.f, 0.f);
+    if (colin && yy >= 0 && yy < ny) {
+      const size_t p = (size_t)yy * nx + c0;
+      q.k = *reinterpret_cast<const float2*>(op.k2 + p);
+      if (implicit_v || (yy >= Y0 && yy < Y0 + TY)) q.f = ld_pair(fr + p);
+      if (vr) q.v = ld_pair(vr + p);
+    }
+    return q;
+  };
+  CPair xm = cp_zero(), x0 = cp_zero(), f0 = cp_zero(), d0 = cp_zero();
+  float2* o = out + (size_t)rhs * N;
+  Raw qn = fetch(Y0 - 1);
+  for (int yy = Y0 - 1; yy <= Y0 + TY; ++yy) {
+    const Raw q = qn;
+    if (yy < Y0 + TY) qn = fetch(yy + 1);
+    if (yy > Y0 - 1 && !(yy & 1)) {               // entering coarse row yy / 2
+      elo0 = ehi0; elo1 = ehi1;
+      ec_row((yy >> 1) + 1, ehi0, ehi1);
+    }
+    CPair xp = cp_zero(), dp = cp_zero();
+    if (colin && yy >= 0 && yy < ny) {
+      dp.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
+      dp.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      CPair base = q.v;
+      if (!vr && implicit_v) { base.a = jacobi_from_zero(q.f.a, dp.a, w); base.b = jacobi_from_zero(q.f.b, dp.b, w); }
+      // P e_c: even rows take coarse row yy / 2, odd rows the mean of two coarse rows;
+      // column c0 = 2J takes coarse column J, column c0 + 1 the mean of J and J + 1
+      float2 e0 = elo0, e1 = elo1;
+      if (yy & 1) { e0 = cscale(cadd(elo0, ehi0), 0.5f); e1 = cscale(cadd(elo1, ehi1), 0.5f); }
+      xp.a = cadd(base.a, e0);
+      xp.b = cadd(base.b, cscale(cadd(e0, e1), 0.5f));
+    }
+    if (yy >= Y0 + 1) {
+      const int y = yy - 1;
+      const float2 lft = shfl_up1(x0.b), rgt = shfl_dn1(x0.a);
+      if (colin && lane >= 1 && lane <= 30 && y < ny) {
+        const float2 ka = op_at<BC>(op, c0, y, d0.a, x0.a, lft, x0.b, xm.a, xp.a);
+        const float2 kb = op_at<BC>(op, c0 + 1, y, d0.b, x0.b, x0.a, rgt, xm.b, xp.b);
+        CPair r;
+        r.a = cadd(x0.a, jacobi_from_zero(csub(f0.a, ka), d0.a, w));
+        r.b = cadd(x0.b, jacobi_from_zero(csub(f0.b, kb), d0.b, w));
+        st_pair(o + (size_t)y * nx + c0, r);
+      }
+    }
+    xm = x0; x0 = xp; f0 = q.f; d0 = dp;
   }
 }
 
@@ -311,8 +568,10 @@ inline dim3 grid2(int nx, int ny, int nrhs) { return dim3((nx + BX - 1) / BX, (n
 template <typename T>
 void launch_apply(const Op<T>& op, const void* x, const void* b, void* y, int nrhs, const int* active, cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  auto k = op.order == 4 ? k_apply<T, 4> : k_apply<T, 2>;
-  k<<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, (const T2*)x, (const T2*)b, (T2*)y, active);
+  with_kind(op.order, op.bc, [&](auto kd) {
+    k_apply<T, decltype(kd)::ORD, decltype(kd)::BC><<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(
+        op, (const T2*)x, (const T2*)b, (T2*)y, active);
+  });
 }
 template <typename T>
 void launch_rhs_weight(const Op<T>& op, const void* x, void* y, int nrhs, cudaStream_t s) {
@@ -323,8 +582,10 @@ template <typename T>
 void launch_jacobi(const Op<T>& op, T w, const void* f, const void* x_in, void* x_out, int nrhs, const int* active,
                    cudaStream_t s) {
   typedef typename vec2<T>::type T2;
-  auto k = op.order == 4 ? k_jacobi<T, 4> : k_jacobi<T, 2>;
-  k<<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(op, w, (const T2*)f, (const T2*)x_in, (T2*)x_out, active);
+  with_kind(op.order, op.bc, [&](auto kd) {
+    k_jacobi<T, decltype(kd)::ORD, decltype(kd)::BC><<<grid2(op.nx, op.ny, nrhs), dim3(BX, BY), 0, s>>>(
+        op, w, (const T2*)f, (const T2*)x_in, (T2*)x_out, active);
+  });
 }
 template <typename T>
 void launch_restrict(int nx, int ny, const void* rf, void* rc, int nrhs, const int* active, cudaStream_t s) {
@@ -337,21 +598,89 @@ void launch_prolong_add(int nxc, int nyc, int nx, int ny, const void* ec, void* 
   typedef typename vec2<T>::type T2;
   k_prolong_add<T><<<grid2(nx, ny, nrhs), dim3(BX, BY), 0, s>>>(nxc, nyc, nx, ny, (const T2*)ec, (T2*)xf, active);
 }
+
+// Rows per thread of the fused cycle kernels: taller tiles share their halo over more
+// nodes (FP64 keeps one row: its tiles would not fit in static shared memory).
+template <typename T> constexpr int fused_rpt() { return sizeof(T) == 4 ? 2 : 1; }
+
+// Segment heights the marching kernels are built for.
+template <typename F> bool with_seg(int seg, F f) {
+  switch (seg) {
+    case 4: f(std::integral_constant<int, 4>()); return true;
+    case 8: f(std::integral_constant<int, 8>()); return true;
+    case 16: f(std::integral_constant<int, 16>()); return true;
+    case 32: f(std::integral_constant<int, 32>()); return true;
+    default: return false;
+  }
+}
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Segment height for a marching launch: the chosen one if it is built, else the
+// tallest that still gives about 16 warps per SM.
+int march_seg(int chosen, int strips, int rows, int nrhs) {
+  if (chosen == 4 || chosen == 8 || chosen == 16 || chosen == 32) return chosen;
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = 16ll * (nsm > 0 ? nsm : 148);
+  for (int seg : {32, 16, 8})
+    if ((long long)strips * ((rows + seg - 1) / seg) * nrhs >= want) return seg;
+  return 4;
+}
+
 template <typename T>
 void launch_resid_restrict(const Op<T>& fine, T w, const void* f, const void* v, void* fc, int nrhs,
-                           const int* active, cudaStream_t s) {
+                           const int* active, cudaStream_t s, int seg) {
   typedef typename vec2<T>::type T2;
-  auto k = fine.order == 4 ? k_resid_restrict<T, 4> : k_resid_restrict<T, 2>;
-  k<<<grid2(fine.nx / 2, fine.ny / 2, nrhs), dim3(BX, BY), 0, s>>>(fine, w, (const T2*)f, (const T2*)v, (T2*)fc,
-                                                                   active);
+  if (sizeof(T) == 4 && fine.order == 2 && seg >= 0 && aligned16(f) && (!v || aligned16(v))) {
+    const Op<float>& op = reinterpret_cast<const Op<float>&>(fine);
+    const int nstrips = (fine.nx / 2 + kStripW / 2 - 1) / (kStripW / 2);
+    const int ti = march_seg(seg, nstrips, fine.ny / 2, nrhs);
+    with_kind(2, fine.bc, [&](auto kd) {
+      constexpr int BCk = decltype(kd)::BC;
+      with_seg(ti, [&](auto tv) {
+        constexpr int TI = decltype(tv)::value;
+        const dim3 grid((nstrips + kStripWarps - 1) / kStripWarps, (fine.ny / 2 + TI - 1) / TI, nrhs);
+        k_resid_restrict_m<BCk, TI><<<grid, 32 * kStripWarps, 0, s>>>(op, (float)w, (const float2*)f,
+                                                                      (const float2*)v, (float2*)fc, active,
+                                                                      nstrips);
+      });
+    });
+    return;
+  }
+  constexpr int RPT = fused_rpt<T>();
+  with_kind(fine.order, fine.bc, [&](auto kd) {
+    const dim3 grid((fine.nx / 2 + BX - 1) / BX, (fine.ny / 2 + BY * RPT - 1) / (BY * RPT), nrhs);
+    k_resid_restrict<T, decltype(kd)::ORD, decltype(kd)::BC, RPT><<<grid, dim3(BX, BY), 0, s>>>(
+        fine, w, (const T2*)f, (const T2*)v, (T2*)fc, active);
+  });
 }
 template <typename T>
 void launch_prolong_jacobi(const Op<T>& fine, T w, const void* f, const void* v, bool implicit_v, const void* ec,
-                           int nxc, int nyc, void* out, int nrhs, const int* active, cudaStream_t s) {
+                           int nxc, int nyc, void* out, int nrhs, const int* active, cudaStream_t s, int seg) {
   typedef typename vec2<T>::type T2;
-  auto k = fine.order == 4 ? k_prolong_jacobi<T, 4> : k_prolong_jacobi<T, 2>;
-  k<<<grid2(fine.nx, fine.ny, nrhs), dim3(BX, BY), 0, s>>>(fine, w, (const T2*)f, (const T2*)v, implicit_v ? 1 : 0,
-                                                           (const T2*)ec, nxc, nyc, (T2*)out, active);
+  if (sizeof(T) == 4 && fine.order == 2 && seg >= 0 && aligned16(f) && aligned16(out) && (!v || aligned16(v))) {
+    const Op<float>& op = reinterpret_cast<const Op<float>&>(fine);
+    const int nstrips = (fine.nx + kStripW - 1) / kStripW;
+    const int ty = march_seg(seg, nstrips, fine.ny, nrhs);
+    with_kind(2, fine.bc, [&](auto kd) {
+      constexpr int BCk = decltype(kd)::BC;
+      with_seg(ty, [&](auto tv) {
+        constexpr int TY = decltype(tv)::value;
+        const dim3 grid((nstrips + kStripWarps - 1) / kStripWarps, (fine.ny + TY - 1) / TY, nrhs);
+        k_prolong_jacobi_m<BCk, TY><<<grid, 32 * kStripWarps, 0, s>>>(
+            op, (float)w, (const float2*)f, (const float2*)v, implicit_v ? 1 : 0, (const float2*)ec, nxc, nyc,
+            (float2*)out, active, nstrips);
+      });
+    });
+    return;
+  }
+  constexpr int RPT = fused_rpt<T>();
+  with_kind(fine.order, fine.bc, [&](auto kd) {
+    const dim3 grid((fine.nx + BX - 1) / BX, (fine.ny + BY * RPT - 1) / (BY * RPT), nrhs);
+    k_prolong_jacobi<T, decltype(kd)::ORD, decltype(kd)::BC, RPT><<<grid, dim3(BX, BY), 0, s>>>(
+        fine, w, (const T2*)f, (const T2*)v, implicit_v ? 1 : 0, (const T2*)ec, nxc, nyc, (T2*)out, active);
+  });
 }
 void launch_coarsen_kappa2(const double* k2d_fine, int nx, int ny, double* k2d_coarse, float* k2f_coarse,
                            cudaStream_t s) {
@@ -369,9 +698,9 @@ void launch_widen_kappa2(const float* k2f, double* k2d, size_t n, cudaStream_t s
   template void launch_restrict<T>(int, int, const void*, void*, int, const int*, cudaStream_t);              \
   template void launch_prolong_add<T>(int, int, int, int, const void*, void*, int, const int*, cudaStream_t);  \
   template void launch_resid_restrict<T>(const Op<T>&, T, const void*, const void*, void*, int, const int*,    \
-                                         cudaStream_t);                                                       \
+                                         cudaStream_t, int);                                                  \
   template void launch_prolong_jacobi<T>(const Op<T>&, T, const void*, const void*, bool, const void*, int,   \
-                                         int, void*, int, const int*, cudaStream_t);
+                                         int, void*, int, const int*, cudaStream_t, int);
 INST(float)
 INST(double)
 #undef INST

@@ -15,6 +15,7 @@
 
 #include "../../include/helm.h"
 #include "../../include/unet.h"
+#include "devonce.cuh"
 #include "helm_internal.cuh"
 #include "unet_api.h"
 #include "unet_internal.cuh"
@@ -93,6 +94,8 @@ struct unet_ctx {
   float *ev_scale = nullptr, *ev_shift = nullptr;  // inference BN coefficients from running statistics
   bool ev_dirty = true;
   int adam_t = 0;
+  float* gout = nullptr;                           // output gradient of unet_train_step (+1 spare float)
+  size_t gout_n = 0;
   unet_ctx* encoder = nullptr;
   bool is_encoder = false;                         // attached to a solver: keep a BF16 copy of the output
   float* splitbuf = nullptr;                       // split-K partial-sum slices (TMA path)
@@ -903,6 +906,10 @@ int unet_prepare_impl(helm_ctx* hc, void* netp, int nrhs) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+void unet_cfg_of(unet_t n, unet_cfg* cfg) {
+  if (n && cfg) *cfg = n->cfg;
+}
+
 extern "C" {
 
 int unet_cfg_default(unet_cfg* cfg, int kind) {
@@ -1002,7 +1009,7 @@ void unet_destroy(unet_t n) {
   for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Wb, (void*)n->WTb, (void*)n->WPb, (void*)n->WPAb, (void*)n->WSb, (void*)n->WDb,
                   (void*)n->d_err, (void*)n->rstats,
                   (void*)n->bn_scale, (void*)n->bn_shift, (void*)n->bn_mean, (void*)n->bn_var, (void*)n->ev_scale,
-                  (void*)n->ev_shift, n->tmp_e})
+                  (void*)n->ev_shift, n->tmp_e, (void*)n->gout})
     if (p) cudaFree(p);
   delete n;
 }
@@ -1133,6 +1140,50 @@ int unet_status(unet_t n, int* failed) {
   return HELM_OK;
 }
 
+int unet_wait_probe(unet_t n, long long rounds, int arrive, helm_stream_t stream) {
+  if (!n || rounds < 1 || rounds > (1ll << 20) || (arrive != 0 && arrive != 1)) {
+    set_error("unet_wait_probe: bad arguments (1 <= rounds <= 2^20, arrive 0 or 1)");
+    return HELM_EINVAL;
+  }
+  if (!conv_wait_probe(n->d_err, rounds, arrive, (cudaStream_t)stream)) {
+    set_error("unet_wait_probe: launch failed");
+    return HELM_ECUDA;
+  }
+  return HELM_OK;
+}
+
+int unet_train_step(unet_t n, helm_t h, const float* x, const float* target, int B, const unet_train_opts* opt,
+                    float* loss_dev, helm_stream_t stream) {
+  if (!n || !h || !x || !opt || B < 1 || (opt->loss != UNET_LOSS_MSE && opt->loss != UNET_LOSS_RESIDUAL) ||
+      (opt->loss == UNET_LOSS_MSE && !target) || !(opt->lr > 0.f)) {
+    set_error("unet_train_step: bad arguments");
+    return HELM_EINVAL;
+  }
+  int nx, ny, abc_w;
+  double hh, gmax;
+  const float *k2f, *gam;
+  helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n->encoder) UTRY(unet_encode(n, h, 1, stream));
+  UTRY(unet_zero_grad(n, stream));
+  UTRY(unet_forward(n, x, nullptr, B, ny, nx, 1, stream));
+  const size_t nout = (size_t)B * ny * nx * n->cfg.out_ch;
+  if (n->gout_n < nout) {
+    if (n->gout) cudaFree(n->gout);
+    n->gout = nullptr;
+    n->gout_n = 0;
+    UCHECK(cudaMalloc(&n->gout, nout * sizeof(float) + 256));
+    n->gout_n = nout;
+  }
+  float* loss = loss_dev ? loss_dev : n->gout + nout;   // the spare float past the gradient
+  if (opt->loss == UNET_LOSS_MSE) UTRY(unet_mse(n->out, target, (long long)nout, B, n->gout, loss, stream));
+  else UTRY(unet_residual_loss(h, n->out, x, B, n->gout, loss, stream));
+  UTRY(unet_backward(n, n->gout, nullptr, stream));
+  UTRY(unet_adam_step(n, opt->lr, opt->beta1, opt->beta2, opt->eps, stream));
+  (void)s;
+  return HELM_OK;
+}
+
 int unet_get_grads(unet_t n, float* host, long long cnt) {
   if (!n || !host || cnt != (long long)n->nparams) { set_error("bad gradient vector"); return HELM_EINVAL; }
   UCHECK(cudaMemcpy(host, n->G, cnt * 4, cudaMemcpyDeviceToHost));
@@ -1182,8 +1233,14 @@ int unet_backward(unet_t n, const float* gout, float* gx, helm_stream_t stream) 
 int unet_mse(const float* out, const float* target, long long cnt, int B, float* gout, float* loss_dev,
              helm_stream_t stream) {
   if (!out || !target || !gout || !loss_dev || cnt <= 0 || B < 1) { set_error("bad arguments"); return HELM_EINVAL; }
-  static float* part = nullptr;
-  if (!part) UCHECK(cudaMalloc(&part, 256 * 4));
+  // reduction scratch: one buffer per device (a device pointer is valid on its own device only)
+  static DeviceOnce once;
+  float* part = (float*)(uintptr_t)device_once(once, []() -> long long {
+    void* p = nullptr;
+    if (cudaMalloc(&p, 256 * 4) != cudaSuccess) { cudaGetLastError(); return 0; }
+    return (long long)(uintptr_t)p;
+  }, 0);
+  if (!part) { set_error("unet_mse: scratch allocation failed"); return HELM_ENOMEM; }
   mse_loss(out, target, (size_t)cnt, B, gout, part, loss_dev, (cudaStream_t)stream);
   UCHECK(cudaGetLastError());
   return HELM_OK;

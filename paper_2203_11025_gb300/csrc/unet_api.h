@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "../../include/unet.h"
+
 struct helm_ctx;
 
 // z = U-Net-based preconditioner applied to v (Alg. 2 for HELM_PREC_JU,
@@ -16,3 +18,5 @@ int unet_prepare_impl(helm_ctx* c, void* net, int nrhs);
 // id, workspace generation, encoder id, encoder workspace generation}; ids are never
 // reused, generations change whenever a workspace is reallocated.
 void unet_graph_ids(void* net, unsigned long long ids[4]);
+// The configuration a network was created with.
+void unet_cfg_of(unet_t net, unet_cfg* cfg);

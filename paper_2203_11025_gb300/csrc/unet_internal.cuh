@@ -53,6 +53,9 @@ void conv_forward_tc(const ConvArgs& a, int* err, cudaStream_t s);
 void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int cout, cudaStream_t s);
 // TMA-fed tensor-core path (conv_tma.cu); false if the convolution does not fit it.
 bool conv_forward_tma(const ConvArgs& a, int* err, cudaStream_t s);
+// One-thread kernel that waits on an mbarrier through the convolution pipeline's bounded
+// wait (at most `rounds` polls); without an arrival the wait expires and err records it.
+bool conv_wait_probe(int* err, long long rounds, int arrive, cudaStream_t s);
 int conv_tma_split(const ConvArgs& a);
 // adjoint (data-gradient) weight copies for the TMA path: [cin][tap][64-chunks of cout],
 // taps reversed for stride-1 convolutions

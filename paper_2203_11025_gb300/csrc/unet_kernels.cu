@@ -11,6 +11,7 @@
 
 #include <algorithm>
 
+#include "devonce.cuh"
 #include "unet_internal.cuh"
 
 namespace helm {
@@ -805,14 +806,14 @@ bool conv_thin(const ConvArgs& a, cudaStream_t s) {
   const int M = a.B * a.Ho * a.Wo;
   const int grid = (M + 127) / 128;
   if (a.Cout <= 2 && wbytes * 2 <= 96 * 1024) {
-    static bool cfg2 = false;
-    if (!cfg2) { cudaFuncSetAttribute(k_conv_thin<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); cfg2 = true; }
+    static DeviceOnce once2;   // per-device kernel attribute
+    if (!set_dynamic_smem(once2, k_conv_thin<2>, 96 * 1024)) return false;
     k_conv_thin<2><<<grid, 128, wbytes * 2, s>>>(a);
     return true;
   }
   if (Cin <= 8 && a.Cout <= 32 && wbytes * 32 <= 96 * 1024) {
-    static bool cfg32 = false;
-    if (!cfg32) { cudaFuncSetAttribute(k_conv_thin<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024); cfg32 = true; }
+    static DeviceOnce once32;
+    if (!set_dynamic_smem(once32, k_conv_thin<32>, 96 * 1024)) return false;
     k_conv_thin<32><<<grid, 128, wbytes * 32, s>>>(a);
     return true;
   }

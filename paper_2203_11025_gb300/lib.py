@@ -36,7 +36,8 @@ ABI_SYMBOLS = [
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
     "unet_mse", "unet_adam_step", "unet_attach_encoder", "unet_encode", "unet_precond", "helm_gen_pairs",
-    "unet_make_batch", "unet_status", "unet_time_layer", "unet_residual_loss",
+    "unet_make_batch", "unet_status", "unet_time_layer", "unet_residual_loss", "unet_wait_probe",
+    "unet_train_step", "unet_save", "unet_load",
 ]
 UNET_FLAG_SIMT, UNET_FLAG_NO_TMA = 1, 2
 UNET_STANDALONE, UNET_ENCODER, UNET_SOLVER = 0, 1, 2
@@ -54,6 +55,14 @@ class unet_cfg(ctypes.Structure):
     _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("levels", ctypes.c_int),
                 ("coarse_resnets", ctypes.c_int), ("widths", ctypes.c_int * 8), ("context", ctypes.c_int * 9),
                 ("flags", ctypes.c_int)]
+
+
+class unet_train_opts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("loss", ctypes.c_int)]
+
+
+UNET_LOSS_MSE, UNET_LOSS_RESIDUAL = 0, 1
 
 
 class fgmres_opts(ctypes.Structure):
@@ -119,6 +128,10 @@ def load():
         "helm_gen_pairs": (I, [P, I, ctypes.c_ulonglong, I, P, P, P]),
         "unet_make_batch": (I, [P, P, P, I, I, I, P, P, P, P, P]),
         "unet_status": (I, [P, ctypes.POINTER(I)]),
+        "unet_wait_probe": (I, [P, ctypes.c_longlong, I, P]),
+        "unet_train_step": (I, [P, P, P, P, I, ctypes.POINTER(unet_train_opts), P, P]),
+        "unet_save": (I, [P, ctypes.c_char_p, ctypes.c_char_p]),
+        "unet_load": (I, [P, ctypes.c_char_p]),
         "unet_time_layer": (I, [P, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
@@ -458,6 +471,12 @@ class UNet:
         _check(self.lib.unet_status(self.handle, ctypes.byref(f)), "unet_status")
         return bool(f.value)
 
+    def wait_probe(self, rounds, arrive=False, stream=None):
+        """Launch the failure-detection probe: a bounded mbarrier wait that expires
+        (arrive=False, recorded for status()) or completes (arrive=True)."""
+        _check(self.lib.unet_wait_probe(self.handle, int(rounds), 1 if arrive else 0, _stream(stream)),
+               "unet_wait_probe")
+
     def time_layer(self, layer, reps=20, stream=None):
         """(ms per repetition, flops, kernel: 3 direct CUDA-core, 2 TMA tensor core, 1 cp.async tensor core,
         0 generic CUDA-core)
@@ -504,6 +523,32 @@ class UNet:
         _check(self.lib.unet_mse(_ptr(out), _ptr(target.contiguous()), out.numel(), out.shape[0], _ptr(gout),
                                  _ptr(loss), _stream(stream)), "unet_mse")
         return loss, gout
+
+    def train_step(self, hz, x, target=None, lr=1e-4, loss="error", b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        """One training step through the C ABI (encoder forward if attached, forward, loss,
+        backward, Adam); loss "error" (Eq. 3.7, needs target) or "residual".  Returns the
+        loss as a one-element device tensor."""
+        import torch
+        if loss not in ("error", "residual"):
+            raise ValueError(f"unknown loss {loss!r}")
+        opts = unet_train_opts(lr, b1, b2, eps, UNET_LOSS_MSE if loss == "error" else UNET_LOSS_RESIDUAL)
+        lv = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(self.lib.unet_train_step(self.handle, hz.h, _ptr(x.contiguous()),
+                                        _ptr(target.contiguous()) if target is not None else None, x.shape[0],
+                                        ctypes.byref(opts), _ptr(lv), _stream(stream)), "unet_train_step")
+        return lv
+
+    def save(self, path, meta=None):
+        """Write the weights and BatchNorm statistics to `path` (unet_save); meta: a dict
+        stored as JSON in the header."""
+        import json
+        m = json.dumps(meta or {}, sort_keys=True).encode()
+        _check(self.lib.unet_save(self.handle, os.fsencode(path), m), "unet_save")
+
+    def load(self, path):
+        """Restore weights and BatchNorm statistics from `path` (unet_load); the file's
+        configuration must equal this network's."""
+        _check(self.lib.unet_load(self.handle, os.fsencode(path)), "unet_load")
 
     def adam_step(self, lr=1e-4, b1=0.9, b2=0.999, eps=1e-8, stream=None):
         _check(self.lib.unet_adam_step(self.handle, lr, b1, b2, eps, _stream(stream)), "unet_adam_step")

@@ -2,8 +2,9 @@
 
 Host-side orchestration only: choosing which pairs form a batch, the
 augmentation coefficients, epochs and the learning-rate schedule.  Pair
-generation (Eq. 3.8-3.9), batch assembly, forward, MSE loss (Eq. 3.7),
-backward and Adam all run in the library's CUDA kernels.
+generation (Eq. 3.8-3.9), batch assembly (unet_make_batch) and the training
+step (unet_train_step: forward, MSE loss of Eq. 3.7 or the residual loss,
+backward, Adam) run in the library's CUDA kernels.
 """
 from __future__ import annotations
 
@@ -58,14 +59,8 @@ def train(hz, net, pairs=None, npairs: int = 256, epochs: int = 10, batch: int =
         losses = []
         for idx, coef in batches(rng, r.shape[0], batch, nmix):
             x, t = hz.make_batch(r, e, idx, coef)
-            if net.encoder is not None:
-                net.encode(hz, train=True)
-            net.zero_grad()
-            out = net.forward(x, train=True)
-            lv, gout = net.mse(out, t) if loss == "error" else hz.residual_loss(out, x)
-            net.backward(gout)
-            net.adam_step(lr=cur)
-            losses.append(lv)
+            # encoder forward (if attached), forward, loss, backward and Adam in one C-ABI call
+            losses.append(net.train_step(hz, x, t if loss == "error" else None, lr=cur, loss=loss))
         m = float(torch.stack(losses).mean().item()) if losses else float("nan")
         history.append(m)
         if log:

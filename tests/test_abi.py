@@ -66,6 +66,10 @@ def test_null_arguments_fail_with_einval(built_lib):
         "unet_mse": lambda: L.unet_mse(None, None, 0, 1, None, None, None),
         "unet_forward": lambda: L.unet_forward(None, None, None, 1, 16, 16, 0, None),
         "unet_precond": lambda: L.unet_precond(None, None, lib.HELM_PREC_VU, None, None, 1, 0, None),
+        "unet_train_step": lambda: L.unet_train_step(None, None, None, None, 1, None, None, None),
+        "unet_save": lambda: L.unet_save(None, b"x.ckpt", None),
+        "unet_load": lambda: L.unet_load(None, b"x.ckpt"),
+        "unet_wait_probe": lambda: L.unet_wait_probe(None, 10, 0, None),
     }
     for name, call in calls.items():
         assert call() == lib.HELM_EINVAL, name

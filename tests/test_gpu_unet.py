@@ -5,9 +5,10 @@ training-pair generator.
 
 Tolerance: the network runs in BF16 (weights and activations, 8-bit mantissa,
 unit roundoff 2^-9) with FP32 accumulation; over ~20 layers the normwise
-relative error of the output stays near 1e-2, so forward checks use 2e-2
-normwise (3e-2 for the full-width default network) and gradient checks 5e-2
-per parameter group."""
+relative error of the output stays near 5e-3 (measured on the full-width default
+network: 5.3e-3 at 64^2, 5.8e-3 at 128^2), so forward checks use 2e-2 normwise
+(the BF16 tolerance the design states) and gradient checks 5e-2 per parameter
+group."""
 import numpy as np
 import pytest
 
@@ -109,7 +110,7 @@ def test_forward_default_architecture(lib, simt):
     out = net.forward(cuda(x)).cpu().numpy()
     assert not net.status()
     ref, _, _, _ = U.forward(oc, P, S, x, train=False)
-    assert nrel(out, ref) < 3e-2
+    assert nrel(out, ref) < 2e-2
 
 
 @pytest.mark.parametrize("shape", [(3, 96, 64), (2, 256, 256), (5, 32, 32)])
@@ -150,6 +151,43 @@ def test_train_forward_backward_parity(lib):
     Sg = PR.unflatten_bn(oc, net.get_bn_stats())
     for k in new_stats:
         assert nrel(Sg[k], new_stats[k]) < 1e-2, k
+
+
+@pytest.mark.parametrize("simt", [False, True])
+def test_default_network_backward_matches_oracle(lib, simt):
+    """Full-width network (32..256 channels, the preconditioners' default) in training
+    mode on 2 x 32 x 32: loss, every parameter group's gradient, the input gradient and
+    the BatchNorm running statistics against the FP64 oracle's backward (Eq. 3.7 loss,
+    Sec. 3.4 training), on the tensor-core path (adjoint-weight data gradients, MN-major
+    weight-gradient GEMMs, the widest layer with Cin = 256 and two M blocks) and on CUDA
+    cores.  Tolerances as for the small network: 2e-2 forward, 5e-2 per gradient group."""
+    c = lib.unet_cfg_default(lib.UNET_STANDALONE)
+    c.flags = lib.UNET_FLAG_SIMT if simt else 0
+    oc = U.UNetConfig()
+    net = lib.UNet(c, seed=8)
+    P, S = randomise(lib, net, oc, 8)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((2, 32, 32, 4))
+    tgt = rng.standard_normal((2, 32, 32, 2))
+    net.zero_grad()
+    out = net.forward(cuda(x), train=True)
+    loss, gout = net.mse(out, cuda(tgt))
+    gx = net.backward(gout, want_gx=True)
+    assert not net.status()
+    ref, cache, new_stats, _ = U.forward(oc, P, S, x, train=True)
+    rloss, rgout = U.mse_loss(ref, tgt)
+    G, rgx, _ = U.backward(oc, P, cache, rgout)
+    assert nrel(out.cpu().numpy(), ref) < 2e-2
+    assert abs(loss.item() - rloss) / rloss < 2e-2
+    Gg = PR.unflatten_params(oc, net.get_grads())
+    worst = {k: nrel(Gg[k], G[k]) for k in G}
+    for k, v in worst.items():
+        assert v < 5e-2, (k, v)
+    assert nrel(gx.cpu().numpy(), rgx) < 5e-2
+    Sg = PR.unflatten_bn(oc, net.get_bn_stats())
+    for k in new_stats:
+        assert nrel(Sg[k], new_stats[k]) < 1e-2, k
+    print("worst gradient group", max(worst.items(), key=lambda kv: kv[1]))
 
 
 def test_backward_tensor_core_matches_cuda_core(lib):
@@ -310,7 +348,7 @@ def test_full_size_bench_batch_forward_and_preconditioner(lib):
     out = net.forward(cuda(x)).cpu().numpy()
     assert not net.status()
     ref, _, _, _ = U.forward(oc, P, S, x, train=False)
-    assert nrel(out, ref) < 3e-2
+    assert nrel(out, ref) < 2e-2
     hz, prob = _helm(lib, n)
     r = crandn(43, (B, n, n))
     e = hz.unet_precond(net, torch.from_numpy(r).cuda(), kind=lib.HELM_PREC_VU).cpu().numpy()
@@ -386,6 +424,29 @@ def test_gen_pairs_parity(lib):
         # loses the digits x and x~ share (|e| ~ 1e-2 |x| after a few steps); r = A e
         # amplifies the high-frequency part of that difference by up to ||A|| ~ 8/h^2
         assert nrel(e[j], er[j]) < 5e-4 and nrel(r[j], rr[j]) < 1e-2
+
+
+@pytest.mark.parametrize("n,nmix", [(48, 2), (64, 3), (32, 1)])
+def test_make_batch_parity(lib, n, nmix):
+    """Training-batch assembly (Sec. 3.4: linear combinations of pairs, input h^2 r' / s,
+    target e' / s) against the oracle's make_batch, on pairs the GPU generated; FP32
+    outputs of FP64 inputs (relative 1e-6), the medium channels bit for bit."""
+    hz, prob = _helm(lib, n)
+    r, e = hz.gen_pairs(6, seed=77, kmax=10)
+    rng = np.random.default_rng(78)
+    count = 5
+    idx = rng.integers(0, 6, (count, nmix)).astype(np.int32)
+    coef = (rng.standard_normal((count, nmix)) + 1j * rng.standard_normal((count, nmix))) / np.sqrt(2)
+    if nmix == 1:
+        coef[:] = 1.0
+    x, t = hz.make_batch(r, e, idx, coef)
+    x, t = x.cpu().numpy(), t.cpu().numpy()
+    xr, tr = PR.make_batch(prob, r.cpu().numpy(), e.cpu().numpy(), idx, coef)
+    for i in range(count):
+        assert nrel(x[i, ..., :2], xr[i, ..., :2]) < 1e-6, i
+        assert nrel(t[i], tr[i]) < 1e-6, i
+        assert np.array_equal(x[i, ..., 2], prob.A.kappa2.astype(np.float32))
+        assert nrel(x[i, ..., 3], prob.A.gamma) < 1e-6
 
 
 def test_fgmres_vu_with_silent_network_equals_sl(lib):
@@ -477,6 +538,49 @@ def test_checkpoint_round_trip_reproduces_the_network(lib, tmp_path):
     other = lib.UNet(make_cfgs(lib, widths=(8, 16))[0], seed=1)
     with pytest.raises(ValueError):
         CK.load_into(other, path)
+
+
+@pytest.mark.parametrize("loss", ["error", "residual"])
+def test_train_step_equals_the_step_by_step_sequence(lib, loss):
+    """unet_train_step (one C-ABI call) performs the training step of Sec. 3.4: the Adam
+    update it makes equals the one of the separate forward, loss (Eq. 3.7 or the residual
+    loss), backward and Adam calls from the same state, and it reports the same loss."""
+    n = 64
+    hz, prob = _helm(lib, n)
+    c, oc = make_cfgs(lib, widths=(16, 32))
+    nets = [lib.UNet(c, seed=50), lib.UNet(c, seed=50)]
+    r, e = hz.gen_pairs(8, seed=51, kmax=10)
+    idx = np.arange(4, dtype=np.int32)[:, None]
+    x, t = hz.make_batch(r, e, idx, np.ones((4, 1), complex))
+    p0 = nets[0].get_params()
+    lv_a = nets[0].train_step(hz, x, t if loss == "error" else None, lr=1e-3, loss=loss)
+    nets[1].zero_grad()
+    out = nets[1].forward(x, train=True)
+    lv_b, gout = nets[1].mse(out, t) if loss == "error" else hz.residual_loss(out, x)
+    nets[1].backward(gout)
+    nets[1].adam_step(lr=1e-3)
+    da, db = nets[0].get_params() - p0, nets[1].get_params() - p0
+    assert abs(lv_a.item() - lv_b.item()) <= 1e-5 * abs(lv_b.item())
+    assert nrel(da, db) < 1e-2 and np.abs(da).max() > 0
+    assert not nets[0].status()
+
+
+def test_checkpoint_written_by_the_library_reads_in_python(lib, tmp_path):
+    """unet_save writes the layout that checkpoint.decode describes (and unet_load reads
+    what checkpoint.encode writes), with the device weights and statistics."""
+    from paper_2203_11025_gb300 import checkpoint as CK
+    c, oc = make_cfgs(lib, widths=(16, 32))
+    net = lib.UNet(c, seed=61)
+    randomise(lib, net, oc, 61)
+    path = str(tmp_path / "lib.ckpt")
+    net.save(path, {"k": 1})
+    cfg, p, b, meta = CK.read(path)
+    assert meta == {"k": 1} and cfg == CK.cfg_to_dict(net.cfg)
+    assert np.array_equal(p, net.get_params()) and np.array_equal(b, net.get_bn_stats())
+    other = lib.UNet(c, seed=62)
+    (tmp_path / "py.ckpt").write_bytes(CK.encode(cfg, p * 2, b, {}))
+    other.load(str(tmp_path / "py.ckpt"))
+    assert np.array_equal(other.get_params(), p * 2)
 
 
 def test_fallback_to_plain_sl_when_the_network_fails(lib):
