@@ -210,6 +210,19 @@ int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int 
  *             <v_i, w> and ||w||^2               (60 B per point)               */
 int helm_time_kernel(helm_t h, int kernel, int nrhs, int reps, helm_stream_t stream, float* ms, double* bytes);
 
+/* Tile tuner report (no counterpart in the paper): the segment height the tuner chose
+ * for a fused cycle kernel of `level` (kernel 0: residual + full weighting to level+1;
+ * kernel 1: prolongation + correction + Jacobi from level+1) with nrhs right-hand sides:
+ * 4, 8, 16 or 32 rows of the FP32 column-strip form, -1 for the shared-memory tile form,
+ * 0 if not tuned yet (the launch then picks by occupancy).  fgmres_solve tunes every level
+ * once per nrhs before it captures its first cycle, timing each candidate on the
+ * handle's workspace.  HELM_EINVAL for a level without a coarser one. */
+int helm_tile_choice(helm_t h, int kernel, int level, int nrhs, int* seg);
+/* Set that choice instead of the tuner (seg as above; 0 forgets it, so that the next
+ * fgmres_solve tunes again).  Also used by the tests to run every tile form.  Drops the
+ * handle's captured cycles.  HELM_EINVAL for other values. */
+int helm_set_tile_choice(helm_t h, int kernel, int level, int nrhs, int seg);
+
 /* Coarsest-grid GMRES solve that allocates nothing (no counterpart in the
  * paper; the arithmetic is helm_coarse_solve's one-launch kernel).  Some
  * callers cannot call cudaMalloc: code that runs while a CUDA graph is being

@@ -106,12 +106,13 @@ __device__ __forceinline__ void cluster_reduce(cg::cluster_group& cl, ClusterRed
 }
 
 // NT threads per CTA; GB: the Krylov basis lives in global memory (gV, vectors vstride
-// apart, [vector][rhs][point]) and D^-1 is recomputed, for grids whose basis does not
-// fit in the cluster's shared memory; the halo vector u stays in shared memory.
+// apart, [vector][rhs][point]), for grids whose basis does not fit in the cluster's
+// shared memory; the halo vector u and D^-1 stay in shared memory.
 template <typename T, int PPT, int MK, int NT, bool GB>
 __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename vec2<T>::type* __restrict__ f,
                                                        typename vec2<T>::type* __restrict__ out, int m, int rows,
-                                                       const int* gate, typename vec2<T>::type* gV, size_t vstride) {
+                                                       const int* gate, typename vec2<T>::type* gV, size_t vstride,
+                                                       int di_smem) {
   typedef typename vec2<T>::type T2;
   constexpr int KT = NT;
   cg::cluster_group cl = cg::this_cluster();
@@ -125,17 +126,26 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2* Vs = reinterpret_cast<T2*>(smem_raw);            // [(m+1)][NP] (shared-memory basis)
   T2* U = GB ? Vs : Vs + (size_t)(m + 1) * NP;         // u = D^-1 v_j, [NP]
-  T2* DI = U + NP;                                     // D^-1, [NP] (shared-memory basis only)
+  T2* DI = U + NP;                                     // D^-1, [NP] (both layouts)
   // basis vector i of this CTA's points
   auto Vp = [&](int i) -> T2* {
     return GB ? gV + (size_t)i * vstride + (size_t)rhs * N + p0 : Vs + (size_t)i * NP;
   };
-  auto dinv = [&](int lp) -> T2 {
-    if (GB) {
-      const int gp = p0 + lp, y = gp / nx, x = gp - y * nx;
-      return cinv(diag_at(op, x, y));
-    }
-    return DI[lp];
+  // this thread's points: column and CTA-local row, computed once (kept in registers up to
+  // 8 points per thread; beyond that they would spill, and are recomputed instead)
+  constexpr bool kKeep = PPT <= 8;
+  int qxs[kKeep ? PPT : 1], qys[kKeep ? PPT : 1];
+#pragma unroll
+  for (int q = 0; q < (kKeep ? PPT : 0); ++q) {
+    const int lp = threadIdx.x + q * NT;
+    qys[q] = lp / nx;
+    qxs[q] = lp - qys[q] * nx;
+  }
+  auto qy = [&](int q) { return kKeep ? qys[q] : (int)(threadIdx.x + q * NT) / nx; };
+  auto qx = [&](int q) { return kKeep ? qxs[q] : (int)(threadIdx.x + q * NT) - qy(q) * nx; };
+  // D^-1: kept in shared memory when it fits (di_smem), else formed again when needed
+  auto dinv = [&](int q, int lp) -> T2 {
+    return di_smem ? DI[lp] : crecip(diag_at(op, qx(q), rank * rows + qy(q)));
   };
   __shared__ ClusterRed<T, NT> R;
   __shared__ T2 H[(KMAX + 1) * KMAX];
@@ -155,8 +165,7 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
   for (int q = 0; q < PPT; ++q) {
     const int lp = tid + q * KT;
     if (lp < NP) {
-      const int gp = p0 + lp, y = gp / nx, x = gp - y * nx;
-      if (!GB) DI[lp] = cinv(diag_at(op, x, y));
+      if (di_smem) DI[lp] = crecip(diag_at(op, qx(q), rank * rows + qy(q)));
       w[q] = fr[lp];
     } else {
       w[q] = czero<T2>();
@@ -197,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const int lp = tid + q * KT;
-      if (lp < NP) U[lp] = cmul(vj[lp], dinv(lp));
+      if (lp < NP) U[lp] = cmul(vj[lp], dinv(q, lp));
     }
     cl.sync();
     const T2* Uup = rank > 0 ? cl.map_shared_rank(U, rank - 1) : nullptr;       // row above: its last row
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
     for (int q = 0; q < PPT; ++q) {
       const int lp = tid + q * KT;
       if (lp >= NP) continue;
-      const int ly = lp / nx, x = lp - ly * nx;
+      const int ly = qy(q), x = qx(q);
       // rows beyond this CTA's come from the neighbours' shared memory; stencil_sum asks for
       // them only inside the grid, where those neighbours exist
       const T2 s = stencil_sum<2>(op, x, rank * rows + ly, [&](int dx, int dy) -> T2 {
@@ -334,14 +343,14 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
     if (lp >= NP) continue;
     T2 a = czero<T2>();
     for (int i = 0; i < kk; ++i) a = cadd(a, cmul(ys[i], Vp(i)[lp]));
-    outr[lp] = cmul(a, dinv(lp));
+    outr[lp] = cmul(a, dinv(q, lp));
   }
   cl.sync();   // keep shared memory alive until every CTA is done with remote reads
 }
 
 template <typename T, int PPT, int MK, int NT, bool GB>
 bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, const int* gate, int C, int rows,
-                    size_t smem, void* gV, size_t vstride, cudaStream_t s) {
+                    size_t smem, void* gV, size_t vstride, cudaStream_t s, int di_smem = 1) {
   typedef typename vec2<T>::type T2;
   auto kern = k_coarse_cluster<T, PPT, MK, NT, GB>;
   // kernel attributes hold per device: set once on each device
@@ -367,7 +376,8 @@ bool launch_cluster(const Op<T>& op, const void* f, void* out, int nrhs, int m, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, op, (const T2*)f, (T2*)out, m, rows, gate, (T2*)gV, vstride) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, kern, op, (const T2*)f, (T2*)out, m, rows, gate, (T2*)gV, vstride, di_smem) ==
+         cudaSuccess;
 }
 
 }  // namespace
@@ -416,12 +426,15 @@ bool launch_coarse_gmres_cluster(const Op<T>& op, const void* f, void* out, int 
   if (ny % C) return false;
   rows = ny / C;
   const int NP = rows * nx;
-  const size_t smem = (size_t)NP * sizeof(T2);
+  // u in shared memory, and D^-1 beside it when both fit
+  const int di = (size_t)2 * NP * sizeof(T2) <= 180 * 1024 ? 1 : 0;
+  const size_t smem = (size_t)(1 + di) * NP * sizeof(T2);
   if (smem > 180 * 1024) return false;
   const int ppt = (NP + NTG - 1) / NTG;
-  if (ppt <= 4) return launch_cluster<T, 4, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
-  if (ppt <= 8) return launch_cluster<T, 8, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
-  if (ppt <= 16) return launch_cluster<T, 16, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s);
+  if (ppt <= 4) return launch_cluster<T, 4, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s, di);
+  if (ppt <= 8) return launch_cluster<T, 8, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s, di);
+  if (ppt <= 16)
+    return launch_cluster<T, 16, 12, NTG, true>(op, f, out, nrhs, m, gate, C, rows, smem, gV, vstride, s, di);
   return false;
 }
 

@@ -41,6 +41,7 @@ namespace helm {
 namespace {
 
 constexpr int TM = 128;
+constexpr bool kSplitFixupInKernel = false;
 constexpr int MAXST = 12;          // stage ring capacity (the host picks nst <= MAXST)
 constexpr int NEPI = 8;                  // epilogue warps: 2 groups (alternate tiles) x 4 TMEM lane quadrants
 constexpr int NACC = 4;                  // TMEM accumulator buffers at most (the host picks nacc <= NACC)
@@ -163,8 +164,10 @@ struct TmaArgs {
   __nv_bfloat16* ybf; int ldy;
   __nv_bfloat16* y2; int ldy2;    // optional: eLU of the BF16 result as well (next layer's activated input)
   // split-K: split s stores its partial sums to part + s * slice ([pixels][Cout], FP32);
-  // k_splitk_finish adds the slices and applies the epilogue
+  // the last split of a tile to finish (ticket cnt[tile]) adds the slices and applies the
+  // epilogue, and puts the ticket back to 0 (cnt null: k_splitk_finish does it instead)
   float* part; size_t slice;
+  int* cnt;
   int* err;
 };
 
@@ -321,6 +324,37 @@ __device__ __forceinline__ void finish1(const TmaArgs& a, float g, size_t pix, i
   }
 }
 
+// Barrier of the epilogue warps that share an item (ids and counts as in epi_any).
+__device__ __forceinline__ void epi_sync(int g, bool alt) {
+  if (!alt) asm volatile("bar.sync 1, %0;\n" ::"n"(NEPI * 32) : "memory");
+  else if (g == 0) asm volatile("bar.sync 1, %0;\n" ::"n"(NEPI / 2 * 32) : "memory");
+  else asm volatile("bar.sync 2, %0;\n" ::"n"(NEPI / 2 * 32) : "memory");
+}
+
+// The epilogue of columns [c0, c0 + 16) of pixel pix of an item (non-split layout rules:
+// plain, or the sub-pixel scatter of transposed layers), from accumulated values f.
+__device__ __forceinline__ void finish_chunk(const TmaArgs& a, float* f, size_t pix, int b, int oy, int ox, int c0,
+                                             const uint4* rc, const float* s_bias, const float* s_scale,
+                                             const float* s_shift) {
+  if (!a.shuf) {
+    finish16(a, f, pix, c0, c0, true, rc, s_bias, s_scale, s_shift);
+  } else if (a.cr % 16 == 0) {
+    // sub-pixel: the chunk is one phase's channels [co0, co0 + 16)
+    const int ph = c0 / a.cr, co0 = c0 - ph * a.cr;
+    const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
+    finish16(a, f, opix, c0, co0, true, rc, s_bias, s_scale, s_shift);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = c0 + j;
+      if (n >= a.Cout) break;
+      const int ph = n / a.cr, co = n - ph * a.cr;
+      const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
+      finish1(a, f[j], opix, n, co, s_bias, s_scale, s_shift);
+    }
+  }
+}
+
 // Epilogue warps (0 .. NEPI-1) of both convolution kernels: drain TMEM accumulator
 // buffer i % nacc of item i into the destination, then hand the buffer back.  Warp w reads
 // TMEM lanes 32 (w % 4) .. + 31 (the tile rows it may access).  With a.epig warps 0-3 take
@@ -388,28 +422,57 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
           for (int j = 0; j < 16; ++j)
             if (c0 + j < a.Cout) dst[j] = f[j];
         }
-      } else if (!a.shuf) {
-        finish16(a, f, pix, c0, c0, true, rc, s_bias, s_scale, s_shift);
-      } else if (a.cr % 16 == 0) {
-        // sub-pixel: the chunk is one phase's channels [co0, co0 + 16)
-        const int ph = c0 / a.cr, co0 = c0 - ph * a.cr;
-        const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
-        finish16(a, f, opix, c0, co0, true, rc, s_bias, s_scale, s_shift);
       } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
-          if (n >= a.Cout) break;
-          const int ph = n / a.cr, co = n - ph * a.cr;
-          const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
-          finish1(a, f[j], opix, n, co, s_bias, s_scale, s_shift);
-        }
+        finish_chunk(a, f, pix, b, oy, ox, c0, rc, s_bias, s_scale, s_shift);
       }
     }
     // accumulator read: hand buffer acc back to the MMA warp
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&tempty[acc])) : "memory");
+    if (a.ksplit > 1 && a.cnt) {
+      // split-K fix-up: the last split of this tile to store its partial sums adds every
+      // split's slice and applies the epilogue (no separate finishing launch)
+      __shared__ int s_last[2];
+      __threadfence();                                   // this thread's partial sums, device-wide
+      epi_sync(grp, alt);
+      const int tile = w % (a.tx * a.ty * a.tb * (a.transposed ? 4 : 1));
+      if ((warp & 3) == 0 && lane == 0 && (alt || grp == 0))
+        s_last[grp] = atomicAdd(a.cnt + tile, 1) == a.ksplit - 1;
+      epi_sync(grp, alt);
+      if (s_last[alt ? grp : 0]) {
+        __threadfence();
+        for (int c0 = cfirst; c0 < N && rv; c0 += cstep) {
+          float f[16];
+          const float* src = a.part + pix * a.Cout + c0;
+          if (c0 + 16 <= a.Cout && a.vec) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              float4 t = __ldcg(reinterpret_cast<const float4*>(src) + q);
+              for (int sp = 1; sp < a.ksplit; ++sp) {
+                const float4 u = __ldcg(reinterpret_cast<const float4*>(src + (size_t)sp * a.slice) + q);
+                t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+              }
+              f[4 * q] = t.x; f[4 * q + 1] = t.y; f[4 * q + 2] = t.z; f[4 * q + 3] = t.w;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              f[j] = 0.f;
+              if (c0 + j < a.Cout)
+                for (int sp = 0; sp < a.ksplit; ++sp) f[j] += __ldcg(src + (size_t)sp * a.slice + j);
+            }
+          }
+          uint4 rc[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+          if (a.res && a.vec && c0 + 16 <= a.Cout) {
+            const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0);
+            rc[0] = rp[0]; rc[1] = rp[1];
+          }
+          finish_chunk(a, f, pix, b, oy, ox, c0, rc, s_bias, s_scale, s_shift);
+        }
+        if ((warp & 3) == 0 && lane == 0 && (alt || grp == 0)) a.cnt[tile] = 0;   // ready for the next launch
+      }
+    }
   }
 }
 
@@ -1167,6 +1230,10 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   a.y2 = c.ybf ? c.y2 : nullptr; a.ldy2 = c.ldy2;
   a.err = err;
   a.part = a.ksplit > 1 ? c.splitbuf : nullptr;
+  // in-kernel split-K fix-up (the last split of a tile adds the slices): measured slower than
+  // the finishing launch on the level-3/4 layers (one CTA per tile reads every slice), so off
+  a.cnt = (kSplitFixupInKernel && a.ksplit > 1 && c.splitcnt &&
+           a.tx * a.ty * a.tb * (c.transposed ? 4 : 1) <= kSplitTickets) ? c.splitcnt : nullptr;
   a.slice = (size_t)c.B * c.Ho * c.Wo * c.Cout;
   a.vec = ((c.ldo % 4 == 0) && !((uintptr_t)c.out & 15) && (c.ldy % 8 == 0) && !((uintptr_t)c.ybf & 15) &&
            (!a.y2 || ((c.ldy2 % 8 == 0) && !((uintptr_t)a.y2 & 15))) &&
@@ -1195,7 +1262,7 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
   launch_pdl(k_conv_tma, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
-  if (a.ksplit > 1) {
+  if (a.ksplit > 1 && !a.cnt) {
     const int M = c.B * c.Ho * c.Wo;
     const size_t n4 = (size_t)M * (c.Cout / 4);
     launch_pdl(k_splitk_finish, dim3((unsigned)std::min<size_t>((n4 + 255) / 256, (size_t)sm_count() * 8)), dim3(256),

@@ -113,6 +113,9 @@ struct helm_ctx {
   float* gam0 = nullptr;             // absorbing-layer attenuation on the fine grid (float32)
   bool fused_coarse = true;          // one-launch coarsest GMRES when the grid fits in shared memory
   bool cluster_coarse = true;        // cluster-resident coarsest GMRES when the grid fits
+  // tile tuner: segment height of the fused cycle kernels per (kernel, level, nrhs), chosen
+  // by timing the candidates once (see tune_cycle_tiles); absent: chosen by occupancy
+  std::map<std::tuple<int, int, int>, int> seg;
 };
 
 namespace {
@@ -295,7 +298,12 @@ int vcycle(helm_ctx* c, int level, const void* f, const void* v_in, void* out, i
   }
   // residual, restriction, coarse correction
   void* fc = W.F[level + 1];
-  if (implicit || cur) launch_resid_restrict<T>(op, w, f, implicit ? nullptr : cur, fc, nrhs, gate, s);
+  auto seg_of = [&](int kind) {
+    auto it = c->seg.find(std::make_tuple(kind, level, nrhs));
+    return it == c->seg.end() ? 0 : it->second;
+  };
+  if (implicit || cur)
+    launch_resid_restrict<T>(op, w, f, implicit ? nullptr : cur, fc, nrhs, gate, s, seg_of(0));
   else launch_restrict<T>(Lv.nx, Lv.ny, f, fc, nrhs, gate, s);
   void* ec = W.E[level + 1];
   HTRY(vcycle<T>(c, level + 1, fc, nullptr, ec, nrhs, gate, s));
@@ -309,7 +317,8 @@ int vcycle(helm_ctx* c, int level, const void* f, const void* v_in, void* out, i
   } else {
     int nu2 = d.nu2;
     void* dst = (nu2 == 1) ? out : (sa != cur ? sa : sb);
-    launch_prolong_jacobi<T>(op, w, f, implicit ? nullptr : cur, implicit, ec, nxc, nyc, dst, nrhs, gate, s);
+    launch_prolong_jacobi<T>(op, w, f, implicit ? nullptr : cur, implicit, ec, nxc, nyc, dst, nrhs, gate, s,
+                             seg_of(1));
     const void* x = dst;
     for (--nu2; nu2 > 0; --nu2) {
       void* nxt = (nu2 == 1) ? out : (x == sa ? sb : sa);
@@ -367,6 +376,53 @@ int fgmres_cycle(helm_ctx* c, int precond, void* net, double2* x, int nrhs, int 
   return HELM_OK;
 }
 
+// Tile tuner of the fused cycle kernels (FP32): for every level with a coarser one, time
+// each segment height of the column-strip form (4, 8, 16, 32 rows) and the shared-memory
+// tile form (-1) on the workspace vectors of nrhs right-hand sides (contents irrelevant)
+// and keep the fastest, once per (level, nrhs).  Runs outside graph capture; the choices
+// then hold for every captured cycle.
+int tune_cycle_tiles(helm_ctx* c, int nrhs, cudaStream_t s) {
+  if (c->d.stencil != HELM_STENCIL_5PT) return HELM_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HCHECK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return HELM_OK;
+  Work& W = c->w32;
+  if (W.cap < nrhs) return HELM_OK;
+  cudaEvent_t e0, e1;
+  HCHECK(cudaEventCreate(&e0));
+  HCHECK(cudaEventCreate(&e1));
+  const float w = (float)c->d.jacobi_w;
+  for (int l = 0; l + 1 < c->d.levels; ++l) {
+    const Op<float> op = op_on<float>(c, l, c->d.beta);
+    const int nxc = c->L[l + 1].nx, nyc = c->L[l + 1].ny;
+    for (int kind = 0; kind < 2; ++kind) {
+      if (c->seg.count(std::make_tuple(kind, l, nrhs))) continue;   // tuned, or set by the caller
+      int best = 0;
+      float best_ms = 1e30f;
+      for (int seg : {4, 8, 16, 32, -1}) {
+        auto run = [&] {
+          if (kind == 0) launch_resid_restrict<float>(op, w, W.T1[l], nullptr, W.F[l + 1], nrhs, nullptr, s, seg);
+          else launch_prolong_jacobi<float>(op, w, W.T1[l], nullptr, true, W.E[l + 1], nxc, nyc, W.T2[l], nrhs,
+                                            nullptr, s, seg);
+        };
+        run();
+        HCHECK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) run();
+        HCHECK(cudaEventRecord(e1, s));
+        HCHECK(cudaEventSynchronize(e1));
+        float ms = 0;
+        HCHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = seg; }
+      }
+      c->seg[std::make_tuple(kind, l, nrhs)] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HLAUNCH();
+  return HELM_OK;
+}
+
 template <typename T>
 int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int nrhs, const fgmres_opts& o,
                fgmres_result* res, cudaStream_t caller, const int* maxit_rhs_host = nullptr) {
@@ -389,6 +445,7 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   launch_bnorm(b, N, nrhs, W.ss, W.fst, nb, o.tol, s);
   HLAUNCH();
   if (precond == HELM_PREC_JU || precond == HELM_PREC_VU) HTRY(unet_prepare_impl(c, net, nrhs));
+  if (sizeof(T) == 4 && !(o.flags & HELM_FLAG_NO_GRAPH)) HTRY(tune_cycle_tiles(c, nrhs, s));
   cudaGraphExec_t exec = nullptr;
   long long per_cycle = -1;
   const bool use_graph = !(o.flags & HELM_FLAG_NO_GRAPH);
@@ -1117,6 +1174,29 @@ int helm_gen_pairs(helm_t h, int count, unsigned long long seed, int kmax, void*
   launch_apply<double>(op_on<double>(h, 0, 0.0), W.xx, r, r, count, nullptr, s);
   k_sub_inplace<<<1024, 256, 0, s>>>((double2*)e, W.xx, (size_t)count * N);
   HLAUNCH();
+  return HELM_OK;
+}
+
+int helm_tile_choice(helm_t h, int kernel, int level, int nrhs, int* seg) {
+  if (!h || !seg || (kernel != 0 && kernel != 1) || level < 0 || level + 1 >= h->d.levels || nrhs < 1) {
+    g_err = "helm_tile_choice: bad arguments";
+    return HELM_EINVAL;
+  }
+  auto it = h->seg.find(std::make_tuple(kernel, level, nrhs));
+  *seg = it == h->seg.end() ? 0 : it->second;
+  return HELM_OK;
+}
+
+int helm_set_tile_choice(helm_t h, int kernel, int level, int nrhs, int seg) {
+  if (!h || (kernel != 0 && kernel != 1) || level < 0 || level + 1 >= h->d.levels || nrhs < 1 ||
+      !(seg == -1 || seg == 0 || seg == 4 || seg == 8 || seg == 16 || seg == 32)) {
+    g_err = "helm_set_tile_choice: bad arguments";
+    return HELM_EINVAL;
+  }
+  const auto key = std::make_tuple(kernel, level, nrhs);
+  if (seg == 0) h->seg.erase(key);
+  else h->seg[key] = seg;
+  drop_graphs(h);   // captured cycles baked in the previous choice
   return HELM_OK;
 }
 

@@ -278,7 +278,7 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
     }
     n->splitcnt_n = (long long)(4 * smax);
     n->splitbuf = a.take<float>((size_t)n->splitcnt_n);
-    n->splitcnt = nullptr;
+    n->splitcnt = a.take<int>(kSplitTickets);   // zeroed with the workspace; each fix-up puts its ticket back
     n->gbf = a.take<__nv_bfloat16>(std::max(smax, M(0) * (size_t)gbf_ld(c.out_ch)));
   }
   n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
@@ -1137,6 +1137,8 @@ int unet_status(unet_t n, int* failed) {
   UCHECK(cudaDeviceSynchronize());
   UCHECK(cudaMemcpy(failed, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   UCHECK(cudaMemset(n->d_err, 0, sizeof(int)));
+  // a kernel that gave up may have left split-K tickets taken
+  if (*failed && n->splitcnt) UCHECK(cudaMemset(n->splitcnt, 0, kSplitTickets * sizeof(int)));
   return HELM_OK;
 }
 

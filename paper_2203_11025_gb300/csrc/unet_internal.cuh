@@ -34,7 +34,7 @@ struct ConvArgs {
   __nv_bfloat16* y2; int ldy2;       // optional second BF16 destination: eLU of what ybf receives (TMA path)
   // split-K scratch of the TMA path: splitcnt_n floats for the FP32 partial-sum slices
   // (null: not split)
-  float* splitbuf; int* splitcnt; long long splitcnt_n;
+  float* splitbuf; int* splitcnt; long long splitcnt_n;   // splitcnt: kSplitTickets zeroed tickets
   // sub-pixel form of a transposed 5x5 stride-2 convolution (TMA path): the weights
   // [4 cout][3x3][chunks]; with shuffle = 1 the arguments describe the 3x3 convolution
   // over the input grid with Cout = 4 cr columns scattered to the 2x output
@@ -52,6 +52,8 @@ bool conv_tc_eligible(const ConvArgs& a);
 void conv_forward_tc(const ConvArgs& a, int* err, cudaStream_t s);
 void weights_kmajor(const float* P, __nv_bfloat16* WT, int taps, int cin, int cout, cudaStream_t s);
 // TMA-fed tensor-core path (conv_tma.cu); false if the convolution does not fit it.
+// Tickets of the split-K fix-up (one per output tile and phase of a launch).
+constexpr int kSplitTickets = 4096;
 bool conv_forward_tma(const ConvArgs& a, int* err, cudaStream_t s);
 // One-thread kernel that waits on an mbarrier through the convolution pipeline's bounded
 // wait (at most `rounds` polls); without an arrival the wait expires and err records it.

@@ -31,7 +31,7 @@ ABI_SYMBOLS = [
     "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
     "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
     "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "bfgmres_solve", "helm_time_kernel",
-    "helm_coarse_solve_static",
+    "helm_coarse_solve_static", "helm_tile_choice", "helm_set_tile_choice",
     # include/unet.h
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
@@ -107,6 +107,8 @@ def load():
         "bfgmres_solve": (I, [P, I, P, P, P, I, ctypes.POINTER(fgmres_opts), ctypes.POINTER(fgmres_result), P]),
         "helm_time_kernel": (I, [P, I, I, I, P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(D)]),
         "helm_coarse_solve_static": (I, [I, I, D, D, D, I, D, P, P, P, I, I, P]),
+        "helm_tile_choice": (I, [P, I, I, I, ctypes.POINTER(I)]),
+        "helm_set_tile_choice": (I, [P, I, I, I, I]),
         "unet_cfg_default": (I, [ctypes.POINTER(unet_cfg), I]),
         "unet_create": (I, [ctypes.POINTER(unet_cfg), ctypes.c_ulonglong, ctypes.POINTER(P)]),
         "unet_destroy": (None, [P]),
@@ -333,6 +335,16 @@ class Helmholtz:
         _check(self.lib.helm_time_kernel(self.h, kernel, nrhs, reps, _stream(stream), ctypes.byref(ms),
                                          ctypes.byref(nbytes)), "helm_time_kernel")
         return ms.value, nbytes.value
+
+    def tile_choice(self, kernel, level, nrhs):
+        """Segment height the tile tuner chose for fused cycle kernel 0 (residual + restriction)
+        or 1 (prolongation + Jacobi) of `level` at nrhs right-hand sides (0: not tuned)."""
+        v = ctypes.c_int()
+        _check(self.lib.helm_tile_choice(self.h, kernel, level, nrhs, ctypes.byref(v)), "helm_tile_choice")
+        return v.value
+
+    def set_tile_choice(self, kernel, level, nrhs, seg):
+        _check(self.lib.helm_set_tile_choice(self.h, kernel, level, nrhs, seg), "helm_set_tile_choice")
 
     def gen_pairs(self, count, seed, kmax=10, stream=None):
         """Training pairs (r, e) of Eq. 3.8-3.9 (complex128 CUDA tensors [count, ny, nx])."""

@@ -62,14 +62,17 @@ class Preset:
 
 PRESETS = {p.name: p for p in (
     Preset("plain_128", 128, 1, "M_V", notes="plain SL-FGMRES, the oracle's full-solve size"),
-    Preset("unet_256", 256, 8, "M_VU", train_pairs=1024, train_epochs=96,
-           notes="the benchmark: single-model training on the medium, U-Net then V-cycle"),
+    Preset("general_256", 256, 8, "M_VU", train_pairs=1024, train_epochs=96,
+           notes="the general network: 16 random media x 64 pairs (Sec. 3.4.1), solved on an unseen medium"),
+    Preset("unet_256", 256, 8, "M_VU", train_pairs=300, train_epochs=20, train_lr=5e-4, retrain_from=256,
+           notes="general network mini-retrained on the medium (the benchmark's 256^2 case)"),
     Preset("encoder_solver_512", 512, 32, "encoder-solver M_VU", rhs_kind="points+gaussian",
            train_pairs=512, train_epochs=40, notes="encoder on the medium once, solver network per call"),
     Preset("retrain_1024", 1024, 16, "M_VU", train_pairs=300, train_epochs=20, train_lr=5e-4, retrain_from=256,
            notes="network trained at 256^2, mini-retrained on the target medium"),
-    Preset("retrain_2048", 2048, 4, "M_VU", train_pairs=300, train_epochs=20, train_lr=5e-4, train_batch=4,
-           retrain_from=256, notes="as retrain_1024; batch 4 by the network tensor limit"),
+    Preset("retrain_2048", 2048, 16, "M_VU", train_pairs=300, train_epochs=20, train_lr=5e-4, train_batch=4,
+           retrain_from=256, notes="the benchmark's headline case; training batch 4 by the network tensor limit "
+                                   "(the solves run the network on chunks of 4 right-hand sides)"),
 )}
 
 

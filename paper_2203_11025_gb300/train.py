@@ -68,6 +68,37 @@ def train(hz, net, pairs=None, npairs: int = 256, epochs: int = 10, batch: int =
     return history
 
 
+def train_media(media, net, epochs: int = 10, batch: int = 16, lr: float = 1e-3, seed: int = 0, nmix: int = 2,
+                schedule_t0: int | None = None, log=None, loss: str = "error"):
+    """Train `net` on pairs of many media (the general network of Sec. 3.4.1 / 4, trained on
+    pairs generated on random media): media is a list of (hz, (r, e)), one Helmholtz handle
+    per medium with its Eq. 3.8-3.9 pairs.  An epoch takes every medium's batches (pairs of
+    one medium mixed with each other, as the augmentation reads) in a random interleaving,
+    so consecutive steps see different media.  Returns the per-epoch mean loss."""
+    import torch
+    if loss not in ("error", "residual"):
+        raise ValueError(f"unknown loss {loss!r}")
+    rng = np.random.default_rng(seed + 1)
+    history = []
+    for ep in range(epochs):
+        cur = lr if schedule_t0 is None else lr_at(ep, lr, schedule_t0)
+        plan = []
+        for mi, (_, (r, _)) in enumerate(media):
+            plan += [(mi, idx, coef) for idx, coef in batches(rng, r.shape[0], batch, nmix)]
+        order = rng.permutation(len(plan))
+        losses = []
+        for o in order:
+            mi, idx, coef = plan[o]
+            hz, (r, e) = media[mi]
+            x, t = hz.make_batch(r, e, idx, coef)
+            losses.append(net.train_step(hz, x, t if loss == "error" else None, lr=cur, loss=loss))
+        m = float(torch.stack(losses).mean().item()) if losses else float("nan")
+        history.append(m)
+        if log:
+            log(f"epoch {ep} lr {cur:.2e} loss {m:.4f}")
+    return history
+
+
 def relative_error(hz, net, pairs, count: int = 16) -> float:
     """Mean ||U-Net(r) - e|| / ||e|| over the first `count` pairs (the 'average relative
     error' of Sec. 4), with the network in inference mode."""

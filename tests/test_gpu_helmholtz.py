@@ -112,6 +112,36 @@ def test_coarse_gmres_parity(lib, dtype, tol, path, shape):
             assert relerr(x[k], ref) < tol
 
 
+@pytest.mark.parametrize("seg", [4, 8, 16, 32, -1])
+@pytest.mark.parametrize("ny,nx", [(96, 160), (128, 128), (40, 248)])
+def test_vcycle_parity_every_tile_form(lib, ny, nx, seg):
+    """Each form of the fused cycle kernels (column strips with segments of 4-32 rows, the
+    shared-memory tile) gives the oracle's V-cycle in FP32 (ragged strips: 160, 248 are no
+    multiples of the 60-column strip, 96 / 40 rows no multiples of the segment)."""
+    hz, prob = make(lib, ny, nx, abc=16)
+    nrhs = 3
+    for lev in range(prob.levels - 1):
+        for kern in (0, 1):
+            hz.set_tile_choice(kern, lev, nrhs, seg)
+            assert hz.tile_choice(kern, lev, nrhs) == seg
+    f = crandn(12, (nrhs, ny, nx))
+    z = hz.vcycle(dev(f, torch.complex64)).cpu().numpy()
+    for k in range(nrhs):
+        assert relerr(z[k], H.vcycle(prob, f[k])) < 1e-4
+
+
+def test_tuner_picks_a_tile_form_per_level(lib):
+    hz, prob = make(lib, 128, 128, abc=16)
+    b = crandn(13, (4, 128, 128))
+    x, info = hz.fgmres(dev(b, torch.complex128), tol=1e-7, maxit=2000)
+    for lev in range(prob.levels - 1):
+        for kern in (0, 1):
+            assert hz.tile_choice(kern, lev, 4) in (4, 8, 16, 32, -1)
+    xs = x.cpu().numpy()
+    for k in range(4):
+        assert np.linalg.norm(H.residual(prob.A, b[k], xs[k])) / np.linalg.norm(b[k]) <= 1e-7
+
+
 @pytest.mark.parametrize("ny,nx,path", [(64, 64, 0), (96, 160, 0), (96, 160, 1), (96, 160, 2), (256, 256, 0)])
 @pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-11), (torch.complex64, 1e-4)])
 def test_vcycle_parity_zero_guess(lib, ny, nx, path, dtype, tol):

@@ -620,7 +620,6 @@ def test_trained_network_gains_over_plain_sl(lib):
     # Eq. 3.7, Adam) makes FGMRES + M_VU converge in far fewer iterations than FGMRES + M_V
     # on right-hand sides it never saw (point sources and Gaussian noise); every solution is
     # checked by the oracle's FP64 residual
-    import bench
     from paper_2203_11025_gb300 import train as T
     n = 256
     k2 = synth.grf_kappa2(n, n, synth.medium_seed(0))
@@ -628,8 +627,8 @@ def test_trained_network_gains_over_plain_sl(lib):
     d = hz.desc
     prob = H.Problem(k2.astype(np.float64), omega=d.omega, h=d.h, abc_width=d.abc_width, levels=d.levels)
     net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=7)
-    pairs = hz.gen_pairs(bench.TRAIN_PAIRS, 5151, 10)
-    T.train(hz, net, pairs=pairs, epochs=bench.TRAIN_EPOCHS, batch=16, lr=bench.TRAIN_LR, seed=11)
+    pairs = hz.gen_pairs(1024, 5151, 10)
+    T.train(hz, net, pairs=pairs, epochs=96, batch=16, lr=1e-3, seed=11)
     del pairs
     pos = synth.source_positions(n, n, 4, synth.rhs_seed(7), 16)
     b = np.concatenate([synth.point_sources(n, n, pos, 1.0 / n), synth.complex_normal(77, (4, n, n))])

@@ -45,9 +45,10 @@ def test_mixing_coefficients_are_complex_normal():
 
 
 def test_bench_batch_limit_and_default_rhs():
+    # the network's tensor limit B*n*n*64 < 2^31 sets the training batch and the solve's
+    # network chunk; the benchmark's default case is 2048^2 with 16 right-hand sides
     import bench
     for n, want in ((256, 16), (1024, 16), (2048, 4)):
-        bench.N_GRID = n
-        b = bench.max_batch(16)
+        b = bench.max_batch(n, 16)
         assert b == want and b * n * n * 64 < 2 ** 31
-    bench.N_GRID = 256
+    assert (bench.N_GRID, bench.NRHS) == (2048, 16)

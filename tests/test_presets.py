@@ -21,14 +21,22 @@ def test_every_preset_is_well_formed():
 
 def test_benchmark_preset_matches_the_benchmark_problem():
     import bench
-    p = presets.get("unet_256")
+    p = presets.get("retrain_2048")
     assert (p.n, p.nrhs) == (bench.N_GRID, bench.NRHS)
-    assert (p.train_pairs, p.train_epochs, p.train_lr) == (bench.TRAIN_PAIRS, bench.TRAIN_EPOCHS, bench.TRAIN_LR)
+    assert (p.train_pairs, p.train_epochs, p.train_lr) == (bench.RETRAIN_PAIRS, bench.RETRAIN_EPOCHS,
+                                                           bench.RETRAIN_LR)
+    assert p.train_batch == bench.max_batch(p.n, 16)
     k2, b = bench.build_problem(0)
     assert np.array_equal(p.medium(0), k2) and np.array_equal(p.rhs(0), b)
-    r = presets.get("retrain_1024")
-    assert (r.train_pairs, r.train_epochs, r.train_lr) == (bench.RETRAIN_PAIRS, bench.RETRAIN_EPOCHS,
-                                                           bench.RETRAIN_LR)
+    for name in ("retrain_1024", "unet_256"):
+        r = presets.get(name)
+        assert (r.n, r.nrhs) in bench.EXTRAS
+        k2, b = bench.build_problem(0, r.n, r.nrhs)
+        assert np.array_equal(r.medium(0), k2) and np.array_equal(r.rhs(0), b)
+        assert (r.train_pairs, r.train_epochs, r.train_lr) == (bench.RETRAIN_PAIRS, bench.RETRAIN_EPOCHS,
+                                                               bench.RETRAIN_LR)
+    g = presets.get("general_256")
+    assert g.train_pairs == bench.TRAIN_MEDIA * bench.TRAIN_PAIRS_PER_MEDIUM and g.train_epochs == bench.TRAIN_EPOCHS
 
 
 def test_mixed_right_hand_sides():
