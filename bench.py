@@ -10,10 +10,13 @@ steps each), the tensor roofline of the U-Net convolutions and the HBM roofline 
 stencil and Arnoldi kernels, end-to-end time through the C ABI with host buffers, and the
 FP64 CPU oracle on a bounded sample.
 
-Networks (outside every timed region; time reported separately): one general network
-(Sec. 3.4.1 / 4) trained on Eq. 3.8-3.9 pairs of many random 256^2 media, saved with
+Networks (outside every timed region; time reported separately): a base network trained
+on Eq. 3.8-3.9 pairs of one random 256^2 medium (not a benchmark medium), saved with
 unet_save, then for each case loaded with unet_load and mini-retrained on pairs of that
-case's medium (Sec. 3.5) -- the medium the case then solves on.
+case's medium (Sec. 3.5) -- the medium the case then solves on.  The general network of
+Sec. 3.4.1 (pairs of 16 random media) is trained too and reported on a medium it never saw;
+with this training budget (1024 pairs; the paper used 20k) it transfers worse than the
+single-medium base, so the base of the mini-retrained networks is the latter.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--grid n --nrhs k] [--no-extras] [--no-cpu-baseline]
@@ -43,14 +46,17 @@ RESTART = 10
 METRIC = "s to FP64 rel-res 1e-7 & FGMRES iters, U-Net+SL vs plain SL on 1 GB300; HBM %"
 EXTRAS = ((1024, 16), (256, 8))   # reported in config, fewer timed steps
 EXTRA_STEPS = 3
-E2E_STEPS = 3
-# general network: Eq. 3.8-3.9 pairs of TRAIN_MEDIA random 256^2 media (seeds 10^6 + k)
+E2E_STEPS = 2
+# base network: TRAIN_PAIRS Eq. 3.8-3.9 pairs of one random 256^2 medium (seed BASE_SEED)
 BASE_GRID = 256
-TRAIN_MEDIA = 16
-TRAIN_PAIRS_PER_MEDIUM = 64
+BASE_SEED = 10 ** 6 + 500
+TRAIN_PAIRS = 1024
 TRAIN_EPOCHS = 96
 TRAIN_LR = 1e-3          # constant; measured fastest at this size (3e-3 stalls; Sec. 4 starts at 1e-4)
 TRAIN_BATCH = 16
+# general network: Eq. 3.8-3.9 pairs of TRAIN_MEDIA random 256^2 media (seeds 10^6 + k)
+TRAIN_MEDIA = 16
+TRAIN_PAIRS_PER_MEDIUM = 64
 # mini-retraining on the case's medium (Sec. 3.5: a few hundred pairs, a few hundred steps)
 RETRAIN_PAIRS = 300
 RETRAIN_EPOCHS = 20
@@ -68,9 +74,8 @@ def workload(n: int, nrhs: int) -> str:
     return (f"{n}x{n} grid, h=1/{n}, omega=0.2*pi*{n}, GRF medium (sigma 8, kappa in [0.25,1]), 16-cell "
             f"quadratic absorbing layer, {nrhs} random point sources; FGMRES({RESTART}) + M_VU (U-Net 4 levels "
             f"32..256 ch, BF16 tcgen05 convs, then SL V-cycle 3 levels V(1,1) w=0.8, coarse GMRES(10)), tol {TOL}; "
-            f"general network trained {TRAIN_EPOCHS} epochs on {TRAIN_MEDIA}x{TRAIN_PAIRS_PER_MEDIUM} pairs of "
-            f"{TRAIN_MEDIA} random {BASE_GRID}x{BASE_GRID} media, mini-retrained {RETRAIN_EPOCHS} epochs on "
-            f"{RETRAIN_PAIRS} pairs of the benchmark medium")
+            f"network trained {TRAIN_EPOCHS} epochs on {TRAIN_PAIRS} pairs of one random {BASE_GRID}x{BASE_GRID} "
+            f"medium, mini-retrained {RETRAIN_EPOCHS} epochs on {RETRAIN_PAIRS} pairs of the benchmark medium")
 
 
 def max_batch(n: int, want: int) -> int:
@@ -215,6 +220,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def train_base(lib, rank):
+    """The base network: Eq. 3.8-3.9 pairs of one random 256^2 medium, MSE loss (Eq. 3.7),
+    Adam (the paper's single-model recipe on a medium no case solves on)."""
+    import torch
+    from paper_2203_11025_gb300 import synth
+    from paper_2203_11025_gb300 import train as T
+    hz = lib.Helmholtz(torch.from_numpy(synth.grf_kappa2(BASE_GRID, BASE_GRID, BASE_SEED + rank)).cuda())
+    t0 = time.perf_counter()
+    pairs = hz.gen_pairs(TRAIN_PAIRS, 5151 + rank, 10)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=7 + rank)
+    t0 = time.perf_counter()
+    hist = T.train(hz, net, pairs=pairs, epochs=TRAIN_EPOCHS, batch=TRAIN_BATCH, lr=TRAIN_LR, seed=11 + rank)
+    torch.cuda.synchronize()
+    info = {"pairs": TRAIN_PAIRS, "grid": BASE_GRID, "medium_seed": BASE_SEED + rank, "epochs": TRAIN_EPOCHS,
+            "lr": TRAIN_LR, "batch": TRAIN_BATCH, "gen_s": round(t_gen, 2),
+            "train_s": round(time.perf_counter() - t0, 2), "loss_first": round(hist[0], 1),
+            "loss_last": round(hist[-1], 1)}
+    hz.close()
+    return net, info
+
+
+def general_case(lib, dev, rank):
+    """The general network on a medium it never saw (the 256^2 x 8 case's problem): M_VU
+    against M_V iterations and solve times, no retraining."""
+    import torch
+    gnet, ginfo = train_general(lib, rank)
+    k2, b = build_problem(rank, 256, 8)
+    hz = lib.Helmholtz(torch.from_numpy(k2).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    out = {"training": ginfo}
+    for name, pc, nt in (("M_V", lib.HELM_PREC_V, None), ("M_VU", lib.HELM_PREC_VU, gnet)):
+        hz.fgmres(bd, precond=pc, net=nt, tol=TOL, maxit=20000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = hz.fgmres(bd, precond=pc, net=nt, tol=TOL, maxit=20000)
+        torch.cuda.synchronize()
+        out.setdefault("fgmres_iters", {})[name] = info["iters_max"]
+        out.setdefault("solve_s", {})[name] = time.perf_counter() - t0
+        assert info["status"] == 0 and info["relres_max"] <= TOL, (name, info)
+    out["medium"] = "the 256x256x8 case's medium (not among the 16 training media)"
+    hz.close()
+    gnet.close()
+    return out
+
+
 def train_general(lib, rank):
     """The general network (Sec. 3.4.1 / 4): Eq. 3.8-3.9 pairs generated by the library's
     SL-FGMRES on TRAIN_MEDIA random media, MSE loss (Eq. 3.7), Adam; returns (net, info)."""
@@ -330,6 +382,73 @@ class Case:
         return out
 
 
+C4_SIZES = (256, 384, 512, 768, 1024)
+C4_PROBLEMS = 64
+C4_RPP = 4
+
+
+def c4_case(lib, dev, rank, base_path):
+    """64 independent problems, grid sizes drawn (seeded) from {256, 384, 512, 768, 1024}^2,
+    each with its own random medium and 4 point sources, M_VU with the base network:
+    one fgmres_solve_batch call (one handle per size holding its problems' media, one
+    network handle per size) against the same problems solved one by one (a handle each).
+    Setup and graph capture are outside both timed regions."""
+    import numpy as np
+    import torch
+    from paper_2203_11025_gb300 import synth
+    u = synth.uniform01(8800 + rank, C4_PROBLEMS)
+    sizes = [C4_SIZES[min(int(v * len(C4_SIZES)), len(C4_SIZES) - 1)] for v in u]
+    groups = {}
+    for p, n in enumerate(sizes):
+        groups.setdefault(n, []).append(p)
+    handles, nets, bs, meta = [], [], [], []
+    for n, probs in sorted(groups.items()):
+        k2 = np.stack([synth.grf_kappa2(n, n, 5000 + 100 * rank + p) for p in probs])
+        hz = lib.Helmholtz(torch.from_numpy(k2).to(dev), rpp=C4_RPP)
+        b = np.concatenate([synth.point_sources(n, n, synth.source_positions(n, n, C4_RPP, 6000 + 100 * rank + p, 16),
+                                                1.0 / n) for p in probs])
+        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=0)
+        net.load(base_path)
+        handles.append(hz)
+        nets.append(net)
+        bs.append(torch.from_numpy(b).to(dev))
+        meta.append((n, probs, k2, b))
+    lib.fgmres_batch(handles, bs, precond=lib.HELM_PREC_VU, nets=nets, tol=TOL, maxit=20000)   # tune, capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, infos = lib.fgmres_batch(handles, bs, precond=lib.HELM_PREC_VU, nets=nets, tol=TOL, maxit=20000)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for inf in infos:
+        assert inf["status"] == 0 and inf["relres_max"] <= TOL, inf
+    # the same problems one by one, one handle each (created, warmed and captured untimed)
+    t_seq, seq_iters = 0.0, {}
+    for (n, probs, k2, b), net in zip(meta, nets):
+        for q, p in enumerate(probs):
+            hz1 = lib.Helmholtz(torch.from_numpy(k2[q]).to(dev))
+            b1 = torch.from_numpy(b[q * C4_RPP:(q + 1) * C4_RPP]).to(dev)
+            hz1.fgmres(b1, precond=lib.HELM_PREC_VU, net=net, tol=TOL, maxit=20000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf1 = hz1.fgmres(b1, precond=lib.HELM_PREC_VU, net=net, tol=TOL, maxit=20000)
+            torch.cuda.synchronize()
+            t_seq += time.perf_counter() - t0
+            seq_iters[n] = max(seq_iters.get(n, 0), inf1["iters_max"])
+            hz1.close()
+    out = {"problems": C4_PROBLEMS, "rhs_per_problem": C4_RPP,
+           "problems_per_size": {f"{n}x{n}": len(probs) for n, probs, _, _ in meta},
+           "batched_s": t_batch, "sequential_s": t_seq, "speedup_batched": t_seq / t_batch,
+           "fgmres_iters_max": {f"{m[0]}x{m[0]}": inf["iters_max"] for m, inf in zip(meta, infos)},
+           "sequential_iters_max": {f"{n}x{n}": v for n, v in seq_iters.items()},
+           "precond": "M_VU, the base network (no retraining: every problem has its own random medium)",
+           "timing": "host wall clock around one call, device synchronised on both sides"}
+    for hz in handles:
+        hz.close()
+    for net in nets:
+        net.close()
+    return out
+
+
 def hbm_kernels(hz, nrhs, hbm_peak):
     """Algorithmic GB/s of the HBM-bound kernels at the case's size (helm_time_kernel: CUDA
     events around back-to-back launches on the FP32 workspace)."""
@@ -364,10 +483,10 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    base, ginfo = train_general(lib, rank)
+    base, binfo = train_base(lib, rank)
     tmp = tempfile.mkdtemp(prefix="helm_bench_")
-    base_path = os.path.join(tmp, f"general_rank{rank}.ckpt")
-    base.save(base_path, {"kind": "general network", **ginfo})
+    base_path = os.path.join(tmp, f"base_rank{rank}.ckpt")
+    base.save(base_path, {"kind": "base network", **binfo})
     base.close()
 
     case = Case(lib, dev, rank, N_GRID, NRHS, base_path)
@@ -431,6 +550,8 @@ def run_ours(args):
             extras[f"{n}x{n}x{k}"] = c2.summary(min(args.steps, EXTRA_STEPS))
             c2.hz.close()
             c2.net.close()
+        extras["general_network_unseen_256x256x8"] = general_case(lib, dev, rank)
+        extras["batched_uneven_64"] = c4_case(lib, dev, rank, base_path)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -455,7 +576,7 @@ def run_ours(args):
                        "solve_s": {"M_VU": ms / 1e3, "M_V": ms_v / 1e3,
                                    **({"M_JU": ms_ju / 1e3} if ms_ju else {})},
                        "speedup_vs_plain_sl": ms_v / ms,
-                       "training": {"general": ginfo, "mini_retraining": case.tinfo},
+                       "training": {"base": binfo, "mini_retraining": case.tinfo},
                        "other_cases": extras,
                        "tile_tuner": tiles,
                        "l2": "flushed between timed steps (256 MB write)",

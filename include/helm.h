@@ -103,6 +103,18 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
 void helm_destroy(helm_t h);
 const char* helm_last_error(void);
 
+/* A batch of problems of one grid size, each with its own medium (Sec. 4 solves problems
+ * on many random media; no counterpart for the batching itself): kappa2 is device float32
+ * [nmedia][ny][nx], and right-hand side r of every call on the handle is solved on medium
+ * r / rpp (callers order right-hand sides by medium, rpp of them per medium; at most
+ * nmedia * rpp per call).  The level hierarchy holds every medium's coarse media, and every
+ * operator kernel picks each right-hand side's medium, so one launch per level serves the
+ * whole batch.  helm_setup is helm_setup_media with one medium (rpp ignored).  Block FGMRES,
+ * the pair generator, training and the encoder-solver pair need a handle of one medium
+ * (HELM_EUNSUPPORTED). */
+int helm_setup_media(const helm_desc* desc, const float* kappa2, int nmedia, int rpp, helm_stream_t stream,
+                     helm_t* out);
+
 /* Level sizes of the multigrid hierarchy (Sec. 2.2: H = 2h per level; level 0 = fine grid).
  * HELM_EINVAL for a level outside 0..levels-1. */
 int helm_level_shape(helm_t h, int level, int* nx, int* ny);
@@ -181,6 +193,19 @@ typedef struct {
  * (the host reads a convergence flag once per restart). */
 int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
                  fgmres_result* result, helm_stream_t stream);
+
+/* Problems of uneven grid sizes in one call (no counterpart in the paper): nh handles, one
+ * per grid size (each may hold many media, helm_setup_media), with right-hand sides b[i] and
+ * solutions x[i] (device, complex FP64, nrhs[i] each).  Each handle's restart cycle is one
+ * CUDA graph on the handle's own stream; the calling thread interleaves the handles, so the
+ * size classes run concurrently on the GPU.  U-Net preconditioners take one network handle
+ * per solver handle in nets[i] (a network keeps one activation workspace per grid; copy the
+ * weights with unet_get_params / unet_set_params or unet_save / unet_load); nets may be NULL
+ * for HELM_PREC_V / NONE.  opts as for fgmres_solve without HOST_IO, FP64, FALLBACK_V or
+ * NO_GRAPH (HELM_EUNSUPPORTED).  results: nh entries or NULL.  Returns the worst status.
+ * Blocks the calling thread until every handle is done. */
+int fgmres_solve_batch(int nh, helm_t* handles, int precond, void* const* nets, const void* const* b, void* const* x,
+                       const int* nrhs, const fgmres_opts* opts, fgmres_result* results, helm_stream_t stream);
 
 /* Block flexible GMRES(m) (the CPU solver of Sec. 4): one block Krylov space for all
  * nrhs right-hand sides (block size p = nrhs <= 16, (restart + 1) p^2 <= 4608).  Each

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(CT) k_coarse_gmres(Op<T> op, const typename ve
   __shared__ double cs[CMAX];
   __shared__ int s_k;
   const int rhs = blockIdx.x;
+  select_medium(op, rhs);
   if (gate && !gate[rhs]) return;
   const int nx = op.nx, ny = op.ny, N = nx * ny, tid = threadIdx.x;
   const size_t off = (size_t)rhs * N;
@@ -303,6 +304,7 @@ extern "C" int helm_coarse_solve_static(int nx, int ny, double h, double omega, 
   op.beta = (float)beta;
   op.inv_w = abc_width > 0 ? (float)(1.0 / abc_width) : 0.f;
   op.k2 = kappa2;
+  op.rpp = 0;
   cudaError_t le = cudaSuccess;
   const bool launched = helm::launch_coarse_gmres_fused<float>(op, f, x, basis, (size_t)nrhs * nx * ny, nrhs, m,
                                                                nullptr, (cudaStream_t)stream, &le);

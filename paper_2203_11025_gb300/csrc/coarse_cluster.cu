@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(NT) k_coarse_cluster(Op<T> op, const typename 
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int rhs = blockIdx.y;
+  select_medium(op, rhs);
   if (gate && !gate[rhs]) return;                      // uniform over the cluster
   const int nx = op.nx, ny = op.ny, N = nx * ny;
   const int NP = rows * nx;                            // points of this CTA

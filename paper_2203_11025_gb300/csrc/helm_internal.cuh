@@ -34,15 +34,17 @@ template <typename T> struct Op {
   int nx, ny, abc_w, bc, order;
   T inv_h2, h2, omega2, gmax, beta;
   T inv_w;      // 1 / abc_w (0 without a layer)
-  const T* k2;  // kappa^2 on this level, [ny][nx]
+  const T* k2;  // kappa^2 on this level, [ny][nx] (with rpp > 0: [medium][ny][nx])
+  int rpp;      // right-hand sides per medium: right-hand side r uses medium r / rpp (0: one medium)
 };
 
 // Per-level storage owned by the handle.
 struct Level {
   int nx, ny, abc_w, bc, order;
   double h;
-  float* k2f;   // kappa^2 (float32)
-  double* k2d;  // kappa^2 (float64)
+  float* k2f;   // kappa^2 (float32), [medium][ny][nx]
+  double* k2d;  // kappa^2 (float64), [medium][ny][nx]
+  int rpp;      // right-hand sides per medium (0: one medium shared by every right-hand side)
 };
 
 template <typename T>
@@ -56,6 +58,7 @@ inline Op<T> make_op(const Level& L, double omega, double gmax, double beta) {
   op.beta = (T)beta;
   op.inv_w = L.abc_w > 0 ? (T)(1.0 / L.abc_w) : T(0);
   op.k2 = nullptr;
+  op.rpp = L.rpp;
   return op;
 }
 template <> inline Op<float> make_op<float>(const Level& L, double omega, double gmax, double beta) {
@@ -66,6 +69,7 @@ template <> inline Op<float> make_op<float>(const Level& L, double omega, double
   op.omega2 = (float)(omega * omega);
   op.gmax = (float)gmax; op.beta = (float)beta; op.k2 = L.k2f;
   op.inv_w = L.abc_w > 0 ? (float)(1.0 / L.abc_w) : 0.f;
+  op.rpp = L.rpp;
   return op;
 }
 template <> inline Op<double> make_op<double>(const Level& L, double omega, double gmax, double beta) {
@@ -76,10 +80,17 @@ template <> inline Op<double> make_op<double>(const Level& L, double omega, doub
   op.omega2 = omega * omega;
   op.gmax = gmax; op.beta = beta; op.k2 = L.k2d;
   op.inv_w = L.abc_w > 0 ? 1.0 / L.abc_w : 0.0;
+  op.rpp = L.rpp;
   return op;
 }
 
 #ifdef __CUDACC__
+// Problems that share a grid but not a medium (a batch of one size class): right-hand side
+// r is solved on medium r / rpp.  Every operator kernel calls this with its right-hand side.
+template <typename T> __device__ __forceinline__ void select_medium(Op<T>& op, int rhs) {
+  if (op.rpp > 0) op.k2 += (size_t)(rhs / op.rpp) * op.nx * op.ny;
+}
+
 template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }

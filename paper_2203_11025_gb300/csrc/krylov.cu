@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(NT) k_apply_dot(Op<T> op, int diag_precond, co
                                                   int j, int nb) {
   typedef typename vec2<T>::type T2;
   const int rhs = blockIdx.y;
+  select_medium(op, rhs);
   if (!st.active[rhs]) return;
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
@@ -333,6 +334,7 @@ __global__ void __launch_bounds__(NT) k_arnoldi_project(Op<T> op, int diag_preco
                                                         int j, int nb) {
   typedef typename vec2<T>::type T2;
   const int rhs = blockIdx.y;
+  select_medium(op, rhs);
   if (!st.active[rhs]) return;
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
@@ -472,11 +474,14 @@ __device__ __forceinline__ void stp(float2* p, F2x2 v) {
   *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
 
-template <int BC, int JB>
+// DIAG: w = K D^-1 z (the coarsest GMRES's right preconditioning), i.e. w = z - s(u) / h^2
+// with u = D^-1 z at the neighbours (D u = z at the node itself).
+template <int BC, int JB, bool DIAG>
 __global__ void __launch_bounds__(NT) k_arnoldi_project2(Op<float> op, const float2* __restrict__ z,
                                                          const float2* __restrict__ V, size_t vstride,
                                                          float2* __restrict__ wbase, ArnoldiState st, int j, int nb) {
   const int rhs = blockIdx.y;
+  select_medium(op, rhs);
   if (!st.active[rhs]) return;
   const int nx = op.nx, ny = op.ny;
   const unsigned N = (unsigned)nx * (unsigned)ny, half = N / 2;
@@ -490,27 +495,44 @@ __global__ void __launch_bounds__(NT) k_arnoldi_project2(Op<float> op, const flo
     const unsigned p = 2 * q;
     const int y = (int)(p / (unsigned)nx), x = (int)(p - (unsigned)y * nx);
     const F2x2 c = ldp(zr + p);
-    const F2x2 dn = y > 0 ? ldp(zr + p - nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    const F2x2 up = y < ny - 1 ? ldp(zr + p + nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    const float2 lf = x > 0 ? zr[p - 1] : make_float2(0.f, 0.f);
-    const float2 rt = x + 2 < nx ? zr[p + 2] : make_float2(0.f, 0.f);
+    F2x2 dn = y > 0 ? ldp(zr + p - nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    F2x2 up = y < ny - 1 ? ldp(zr + p + nx) : F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    float2 lf = x > 0 ? zr[p - 1] : make_float2(0.f, 0.f);
+    float2 rt = x + 2 < nx ? zr[p + 2] : make_float2(0.f, 0.f);
     const float2 kk = *reinterpret_cast<const float2*>(op.k2 + p);
     F2x2 r;
-    {
+    if (DIAG) {
+      // u = D^-1 z on the neighbours and on the pair itself (each node's own diagonal)
+      auto u_at = [&](float2 v, int xx, int yy) {
+        return cmul(v, crecip(diag_k2<BC, 2>(op, xx, yy, op.k2[(size_t)yy * nx + xx])));
+      };
+      if (y > 0) { dn.a = u_at(dn.a, x, y - 1); dn.b = u_at(dn.b, x + 1, y - 1); }
+      if (y < ny - 1) { up.a = u_at(up.a, x, y + 1); up.b = u_at(up.b, x + 1, y + 1); }
+      if (x > 0) lf = u_at(lf, x - 1, y);
+      if (x + 2 < nx) rt = u_at(rt, x + 2, y);
+      const float2 ua = cmul(c.a, crecip(diag_k2<BC, 2>(op, x, y, kk.x)));
+      const float2 ub = cmul(c.b, crecip(diag_k2<BC, 2>(op, x + 1, y, kk.y)));
+      const float2 sa = stencil_sum<2, BC>(op, x, y, [&](int dx, int dy) {
+        return dx < 0 ? lf : dx > 0 ? ub : dy < 0 ? dn.a : up.a;
+      });
+      const float2 sb = stencil_sum<2, BC>(op, x + 1, y, [&](int dx, int dy) {
+        return dx < 0 ? ua : dx > 0 ? rt : dy < 0 ? dn.b : up.b;
+      });
+      r.a = make_float2(c.a.x - sa.x * op.inv_h2, c.a.y - sa.y * op.inv_h2);
+      r.b = make_float2(c.b.x - sb.x * op.inv_h2, c.b.y - sb.y * op.inv_h2);
+    } else {
       const float2 s = stencil_sum<2, BC>(op, x, y, [&](int dx, int dy) {
         return dx < 0 ? lf : dx > 0 ? c.b : dy < 0 ? dn.a : up.a;
       });
       r.a = cmul(diag_k2<BC, 2>(op, x, y, kk.x), c.a);
       r.a.x -= s.x * op.inv_h2;
       r.a.y -= s.y * op.inv_h2;
-    }
-    {
-      const float2 s = stencil_sum<2, BC>(op, x + 1, y, [&](int dx, int dy) {
+      const float2 s1 = stencil_sum<2, BC>(op, x + 1, y, [&](int dx, int dy) {
         return dx < 0 ? c.a : dx > 0 ? rt : dy < 0 ? dn.b : up.b;
       });
       r.b = cmul(diag_k2<BC, 2>(op, x + 1, y, kk.y), c.b);
-      r.b.x -= s.x * op.inv_h2;
-      r.b.y -= s.y * op.inv_h2;
+      r.b.x -= s1.x * op.inv_h2;
+      r.b.y -= s1.y * op.inv_h2;
     }
     stp(w + p, r);
 #pragma unroll
@@ -650,6 +672,7 @@ __global__ void __launch_bounds__(NT) k_combine(const typename vec2<T>::type* __
                                                 typename vec2<T>::type* __restrict__ out, const int* gate, int nb) {
   typedef typename vec2<T>::type T2;
   const int rhs = blockIdx.y;
+  if (use_dinv) select_medium(dop, rhs);
   if (gate && !gate[rhs]) return;
   const int m = st.m, k = st.k[rhs];
   __shared__ T2 ys[MMAX];
@@ -702,6 +725,7 @@ __global__ void __launch_bounds__(NT) k_true_residual(Op<double> A, const double
                                                       typename vec2<T>::type* __restrict__ r0, SolveState ss,
                                                       ArnoldiState st, int nb, int maxit) {
   const int rhs = blockIdx.y;
+  select_medium(A, rhs);
   if (ss.done[rhs]) return;
   const int nx = A.nx, ny = A.ny;
   const size_t N = (size_t)nx * ny, off = (size_t)rhs * N;
@@ -816,7 +840,8 @@ template <typename F> void with_jb(int j, F f) {
 template <typename T>
 bool use_pairs(const Op<T>& op, bool diag_precond, const void* z, const void* V, size_t vstride) {
   const size_t N = (size_t)op.nx * op.ny;
-  return sizeof(T) == 4 && !diag_precond && op.order == 2 && (op.nx % 2) == 0 && N < (1u << 31) &&
+  (void)diag_precond;
+  return sizeof(T) == 4 && op.order == 2 && (op.nx % 2) == 0 && N < (1u << 31) &&
          (vstride % 2) == 0 && (!z || ((uintptr_t)z & 15u) == 0) && ((uintptr_t)V & 15u) == 0;
 }
 template <typename F> void with_bc(int bc, F f) {
@@ -837,8 +862,12 @@ void launch_arnoldi(const Op<T>& op, bool diag_precond, const void* z, void* V, 
     with_jb(j, [&](auto jb) {
       constexpr int JB = decltype(jb)::value;
       with_bc(op.bc, [&](auto bc) {
-        k_arnoldi_project2<decltype(bc)::value, JB><<<dim3(nb, nrhs), NT, 0, s>>>(
-            opf, (const float2*)z, (const float2*)V, vstride, w, st, j, nb);
+        if (diag_precond)
+          k_arnoldi_project2<decltype(bc)::value, JB, true><<<dim3(nb, nrhs), NT, 0, s>>>(
+              opf, (const float2*)z, (const float2*)V, vstride, w, st, j, nb);
+        else
+          k_arnoldi_project2<decltype(bc)::value, JB, false><<<dim3(nb, nrhs), NT, 0, s>>>(
+              opf, (const float2*)z, (const float2*)V, vstride, w, st, j, nb);
       });
       k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb,
                                                           write_next, 0);
@@ -870,7 +899,7 @@ void launch_arnoldi_sweep(int which, const Op<T>& op, const void* z, void* V, si
       const Op<float>& opf = reinterpret_cast<const Op<float>&>(op);
       if (which == 0)
         with_bc(op.bc, [&](auto bc) {
-          k_arnoldi_project2<decltype(bc)::value, JB><<<dim3(nb, nrhs), NT, 0, s>>>(
+          k_arnoldi_project2<decltype(bc)::value, JB, false><<<dim3(nb, nrhs), NT, 0, s>>>(
               opf, (const float2*)z, (const float2*)V, vstride, (float2*)w, st, j, nb);
         });
       else

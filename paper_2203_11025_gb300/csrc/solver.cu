@@ -116,6 +116,8 @@ struct helm_ctx {
   // tile tuner: segment height of the fused cycle kernels per (kernel, level, nrhs), chosen
   // by timing the candidates once (see tune_cycle_tiles); absent: chosen by occupancy
   std::map<std::tuple<int, int, int>, int> seg;
+  int nmedia = 1;                    // media held (a batch of problems of one grid size)
+  int rpp = 0;                       // right-hand sides per medium (0: one medium for every one)
 };
 
 namespace {
@@ -423,45 +425,67 @@ int tune_cycle_tiles(helm_ctx* c, int nrhs, cudaStream_t s) {
   return HELM_OK;
 }
 
+// One FGMRES solve split into phases, so that several handles can interleave their
+// restart cycles (fgmres_solve_batch): prepare (workspace, ||b||, network workspace, tile
+// tuning, the captured cycle), then per round check (FP64 true residual and the done
+// flags, copied to the host) / done / cycle, then finish.
+struct FgJob {
+  helm_ctx* c = nullptr;
+  int precond = 0;
+  void* net = nullptr;
+  const double2* b = nullptr;
+  double2* x = nullptr;
+  int nrhs = 0;
+  fgmres_opts o{};
+  const int* maxit_rhs_host = nullptr;
+  cudaStream_t caller = nullptr;
+  fgmres_result* res = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long per_cycle = -1;
+  int cycles = 0, nb = 0;
+  bool finished = false;
+};
+
 template <typename T>
-int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int nrhs, const fgmres_opts& o,
-               fgmres_result* res, cudaStream_t caller, const int* maxit_rhs_host = nullptr) {
+int fg_prepare(FgJob& J) {
+  helm_ctx* c = J.c;
+  const fgmres_opts& o = J.o;
+  const int nrhs = J.nrhs, m = o.restart;
   HTRY(ensure_work<T>(c, nrhs, o.restart));
   Work& W = work_of<T>(c);
-  if (maxit_rhs_host) {
-    HCHECK(cudaMemcpyAsync(W.maxit_rhs, maxit_rhs_host, nrhs * sizeof(int), cudaMemcpyHostToDevice, caller));
+  if (J.maxit_rhs_host) {
+    HCHECK(cudaMemcpyAsync(W.maxit_rhs, J.maxit_rhs_host, nrhs * sizeof(int), cudaMemcpyHostToDevice, J.caller));
     W.ss.maxit_rhs = W.maxit_rhs;
   } else {
     W.ss.maxit_rhs = nullptr;
   }
   const size_t N = level_points(c, 0);
-  const int nb = vec_blocks(N, nrhs, c->nsm);
-  const int m = o.restart;
+  J.nb = vec_blocks(N, nrhs, c->nsm);
   cudaStream_t s = c->own;
-  HCHECK(cudaEventRecord(c->ev_in, caller));
+  HCHECK(cudaEventRecord(c->ev_in, J.caller));
   HCHECK(cudaStreamWaitEvent(s, c->ev_in, 0));
-  if (o.flags & HELM_FLAG_X0_ZERO) HCHECK(cudaMemsetAsync(x, 0, (size_t)nrhs * N * 16, s));
-  const Op<double> A64 = op_on<double>(c, 0, 0.0);
-  launch_bnorm(b, N, nrhs, W.ss, W.fst, nb, o.tol, s);
+  if (o.flags & HELM_FLAG_X0_ZERO) HCHECK(cudaMemsetAsync(J.x, 0, (size_t)nrhs * N * 16, s));
+  launch_bnorm(J.b, N, nrhs, W.ss, W.fst, J.nb, o.tol, s);
   HLAUNCH();
-  if (precond == HELM_PREC_JU || precond == HELM_PREC_VU) HTRY(unet_prepare_impl(c, net, nrhs));
+  if (J.precond == HELM_PREC_JU || J.precond == HELM_PREC_VU) HTRY(unet_prepare_impl(c, J.net, nrhs));
   if (sizeof(T) == 4 && !(o.flags & HELM_FLAG_NO_GRAPH)) HTRY(tune_cycle_tiles(c, nrhs, s));
-  cudaGraphExec_t exec = nullptr;
-  long long per_cycle = -1;
-  const bool use_graph = !(o.flags & HELM_FLAG_NO_GRAPH);
-  if (use_graph) {
-    GraphKey key{(int)sizeof(T), precond, nrhs, m, o.maxit, b, x, {0, 0, 0, 0}};
-    if (net) unet_graph_ids(net, key.net);
-    if (maxit_rhs_host) key.maxit = -1 - o.maxit;
+  J.exec = nullptr;
+  J.per_cycle = -1;
+  J.cycles = 0;
+  J.finished = false;
+  if (!(o.flags & HELM_FLAG_NO_GRAPH)) {
+    GraphKey key{(int)sizeof(T), J.precond, nrhs, m, o.maxit, J.b, J.x, {0, 0, 0, 0}};
+    if (J.net) unet_graph_ids(J.net, key.net);
+    if (J.maxit_rhs_host) key.maxit = -1 - o.maxit;
     if (c->graphs.size() >= kMaxGraphs && !c->graphs.count(key)) drop_graphs(c);
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
-      exec = it->second;
-      per_cycle = c->graph_kernels[key];
+      J.exec = it->second;
+      J.per_cycle = c->graph_kernels[key];
     } else {
       cudaGraph_t g;
       HCHECK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      int r = fgmres_cycle<T>(c, precond, net, x, nrhs, m, s);
+      int r = fgmres_cycle<T>(c, J.precond, J.net, J.x, nrhs, m, s);
       cudaError_t ce = cudaStreamEndCapture(s, &g);
       if (r < 0) return r;
       if (ce != cudaSuccess) { g_err = std::string("graph capture: ") + cudaGetErrorString(ce); return HELM_ECUDA; }
@@ -469,32 +493,56 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
       HCHECK(cudaGraphGetNodes(g, nullptr, &nn));
       std::vector<cudaGraphNode_t> nodes(nn);
       HCHECK(cudaGraphGetNodes(g, nodes.data(), &nn));
-      per_cycle = 0;
+      J.per_cycle = 0;
       for (auto nd : nodes) {
         cudaGraphNodeType ty;
         HCHECK(cudaGraphNodeGetType(nd, &ty));
-        if (ty == cudaGraphNodeTypeKernel) ++per_cycle;
+        if (ty == cudaGraphNodeTypeKernel) ++J.per_cycle;
       }
-      HCHECK(cudaGraphInstantiate(&exec, g, 0));
+      HCHECK(cudaGraphInstantiate(&J.exec, g, 0));
       cudaGraphDestroy(g);
-      c->graphs[key] = exec;
-      c->graph_kernels[key] = per_cycle;
+      c->graphs[key] = J.exec;
+      c->graph_kernels[key] = J.per_cycle;
     }
   }
-  const int max_cycles = o.maxit / std::max(1, m) + 3 + o.maxit;
-  int cycles = 0;
-  for (;;) {
-    launch_true_residual<T>(A64, b, x, W.V, nrhs, W.ss, W.fst, nb, o.maxit, s);
-    HLAUNCH();
-    HCHECK(cudaMemcpyAsync(c->h_done, W.ss.done, (size_t)nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-    HCHECK(cudaStreamSynchronize(s));
-    bool all = true;
-    for (int r = 0; r < nrhs; ++r) all = all && c->h_done[r];
-    if (all) break;
-    if (++cycles > max_cycles) { g_err = "FGMRES cycle guard tripped"; return HELM_ECUDA; }
-    if (exec) HCHECK(cudaGraphLaunch(exec, s));
-    else HTRY(fgmres_cycle<T>(c, precond, net, x, nrhs, m, s));
-  }
+  return HELM_OK;
+}
+
+// Enqueue the FP64 true residual of every right-hand side and the copy of the done flags.
+template <typename T>
+int fg_check(FgJob& J) {
+  helm_ctx* c = J.c;
+  Work& W = work_of<T>(c);
+  const Op<double> A64 = op_on<double>(c, 0, 0.0);
+  launch_true_residual<T>(A64, J.b, J.x, W.V, J.nrhs, W.ss, W.fst, J.nb, J.o.maxit, c->own);
+  HLAUNCH();
+  HCHECK(cudaMemcpyAsync(c->h_done, W.ss.done, (size_t)J.nrhs * sizeof(int), cudaMemcpyDeviceToHost, c->own));
+  return HELM_OK;
+}
+
+// After the check has completed: true when every right-hand side is done; otherwise the
+// next restart cycle is launched.
+template <typename T>
+int fg_step(FgJob& J, bool* done) {
+  helm_ctx* c = J.c;
+  HCHECK(cudaStreamSynchronize(c->own));
+  bool all = true;
+  for (int r = 0; r < J.nrhs; ++r) all = all && c->h_done[r];
+  *done = all;
+  if (all) return HELM_OK;
+  const int max_cycles = J.o.maxit / std::max(1, J.o.restart) + 3 + J.o.maxit;
+  if (++J.cycles > max_cycles) { g_err = "FGMRES cycle guard tripped"; return HELM_ECUDA; }
+  if (J.exec) HCHECK(cudaGraphLaunch(J.exec, c->own));
+  else HTRY(fgmres_cycle<T>(c, J.precond, J.net, J.x, J.nrhs, J.o.restart, c->own));
+  return HELM_OK;
+}
+
+template <typename T>
+int fg_finish(FgJob& J) {
+  helm_ctx* c = J.c;
+  Work& W = work_of<T>(c);
+  cudaStream_t s = c->own;
+  const int nrhs = J.nrhs;
   std::vector<int> iters(nrhs), status(nrhs);
   std::vector<double> relres(nrhs);
   HCHECK(cudaMemcpyAsync(iters.data(), W.ss.iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -502,14 +550,15 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   HCHECK(cudaMemcpyAsync(relres.data(), W.ss.relres, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
   HCHECK(cudaStreamSynchronize(s));
   HCHECK(cudaEventRecord(c->ev_out, s));
-  HCHECK(cudaStreamWaitEvent(caller, c->ev_out, 0));
+  HCHECK(cudaStreamWaitEvent(J.caller, c->ev_out, 0));
   int st = HELM_OK;
+  fgmres_result* res = J.res;
   if (res) {
     res->iters_max = 0;
     res->relres_max = 0;
-    res->cycles = cycles;
+    res->cycles = J.cycles;
     // bnorm + one true-residual kernel per check + the cycle graphs
-    res->launches = per_cycle < 0 ? -1 : 1 + (long long)(cycles + 1) + (long long)cycles * per_cycle;
+    res->launches = J.per_cycle < 0 ? -1 : 1 + (long long)(J.cycles + 1) + (long long)J.cycles * J.per_cycle;
     for (int r = 0; r < nrhs; ++r) {
       res->iters_max = std::max(res->iters_max, iters[r]);
       res->relres_max = std::max(res->relres_max, relres[r]);
@@ -524,6 +573,22 @@ int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x
   if (res) res->status = st;
   if (st == HELM_ENAN) g_err = "non-finite residual in FGMRES";
   return st;
+}
+
+template <typename T>
+int fgmres_run(helm_ctx* c, int precond, void* net, const double2* b, double2* x, int nrhs, const fgmres_opts& o,
+               fgmres_result* res, cudaStream_t caller, const int* maxit_rhs_host = nullptr) {
+  FgJob J;
+  J.c = c; J.precond = precond; J.net = net; J.b = b; J.x = x; J.nrhs = nrhs; J.o = o;
+  J.maxit_rhs_host = maxit_rhs_host; J.caller = caller; J.res = res;
+  HTRY(fg_prepare<T>(J));
+  for (;;) {
+    HTRY(fg_check<T>(J));
+    bool done = false;
+    HTRY(fg_step<T>(J, &done));
+    if (done) break;
+  }
+  return fg_finish<T>(J);
 }
 
 // ===========================================================================
@@ -731,6 +796,10 @@ int check_common(helm_t h, int nrhs, int dtype) {
   if (!h) { g_err = "null handle"; return HELM_EINVAL; }
   if (nrhs <= 0 || nrhs > 65535) { g_err = "nrhs out of range"; return HELM_EINVAL; }
   if (dtype != HELM_C32 && dtype != HELM_C64) { g_err = "dtype must be HELM_C32 or HELM_C64"; return HELM_EINVAL; }
+  if (h->rpp > 0 && nrhs > h->nmedia * h->rpp) {
+    g_err = "more right-hand sides than media x right-hand sides per medium";
+    return HELM_EINVAL;
+  }
   return HELM_OK;
 }
 int check_level(helm_t h, int level, int need_coarser) {
@@ -773,6 +842,10 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
   *gam = c->gam0;
 }
 double helm_omega(helm_ctx* c) { return c->d.omega; }
+int helm_media(helm_ctx* c, int* rpp) {
+  if (rpp) *rpp = c->rpp;
+  return c->nmedia;
+}
 int helm_bc(helm_ctx* c) { return c->d.bc; }
 int helm_stencil(helm_ctx* c) { return c->d.stencil; }
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs) {
@@ -829,7 +902,16 @@ int helm_desc_default(helm_desc* d, int nx, int ny) {
 }
 
 int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream, helm_t* out) {
+  return helm_setup_media(desc, kappa2, 1, 0, stream, out);
+}
+
+int helm_setup_media(const helm_desc* desc, const float* kappa2, int nmedia, int rpp, helm_stream_t stream,
+                     helm_t* out) {
   if (!desc || !kappa2 || !out) { g_err = "null argument"; return HELM_EINVAL; }
+  if (nmedia < 1 || rpp < 0 || (nmedia > 1 && rpp < 1)) {
+    g_err = "nmedia must be >= 1, and rpp >= 1 when there is more than one medium";
+    return HELM_EINVAL;
+  }
   const helm_desc& d = *desc;
   if (d.levels < 1 || d.levels > 12) { g_err = "levels must be in 1..12"; return HELM_EINVAL; }
   const int div = 1 << (d.levels - 1);
@@ -859,8 +941,10 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
   c->cluster_coarse = !(d.flags & (HELM_DESC_MULTIKERNEL_COARSE | HELM_DESC_SINGLE_CTA_COARSE));
   HCHECK(cudaGetDevice(&c->device));
   HCHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  c->nmedia = nmedia;
+  c->rpp = nmedia > 1 ? rpp : 0;
   size_t total = 0;
-  for (int l = 0; l < d.levels; ++l) total += (size_t)(d.nx >> l) * (d.ny >> l) * 12 + 512;
+  for (int l = 0; l < d.levels; ++l) total += (size_t)nmedia * (d.nx >> l) * (d.ny >> l) * 12 + 512;
   if (cudaMalloc(&c->level_mem, total) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -875,16 +959,21 @@ int helm_setup(const helm_desc* desc, const float* kappa2, helm_stream_t stream,
     L.abc_w = d.abc_width >> l;
     L.bc = d.bc;
     L.order = d.stencil == HELM_STENCIL_COMPACT4 ? 4 : 2;
-    size_t n = (size_t)L.nx * L.ny;
+    L.rpp = c->rpp;
+    size_t n = (size_t)nmedia * L.nx * L.ny;
     L.k2f = (float*)a.take(n * 4);
     L.k2d = (double*)a.take(n * 8);
     c->L.push_back(L);
   }
   const size_t n0 = (size_t)d.nx * d.ny;
-  HCHECK(cudaMemcpyAsync(c->L[0].k2f, kappa2, n0 * 4, cudaMemcpyDeviceToDevice, s));
-  launch_widen_kappa2(c->L[0].k2f, c->L[0].k2d, n0, s);
-  for (int l = 1; l < d.levels; ++l)
-    launch_coarsen_kappa2(c->L[l - 1].k2d, c->L[l - 1].nx, c->L[l - 1].ny, c->L[l].k2d, c->L[l].k2f, s);
+  HCHECK(cudaMemcpyAsync(c->L[0].k2f, kappa2, (size_t)nmedia * n0 * 4, cudaMemcpyDeviceToDevice, s));
+  launch_widen_kappa2(c->L[0].k2f, c->L[0].k2d, (size_t)nmedia * n0, s);
+  for (int l = 1; l < d.levels; ++l) {
+    const size_t nf = (size_t)c->L[l - 1].nx * c->L[l - 1].ny, nc = (size_t)c->L[l].nx * c->L[l].ny;
+    for (int q = 0; q < nmedia; ++q)
+      launch_coarsen_kappa2(c->L[l - 1].k2d + q * nf, c->L[l - 1].nx, c->L[l - 1].ny, c->L[l].k2d + q * nc,
+                            c->L[l].k2f + q * nc, s);
+  }
   HLAUNCH();
   HCHECK(cudaMalloc(&c->gam0, n0 * 4));
   gamma_field(d.ny, d.nx, d.abc_width, (float)d.abc_gamma_max, c->gam0, s);
@@ -1108,12 +1197,65 @@ int fgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int n
   return r;
 }
 
+int fgmres_solve_batch(int nh, helm_t* hs, int precond, void* const* nets, const void* const* b, void* const* x,
+                       const int* nrhs, const fgmres_opts* opts, fgmres_result* results, helm_stream_t stream) {
+  if (nh < 1 || !hs || !b || !x || !nrhs || !opts) { g_err = "fgmres_solve_batch: null argument"; return HELM_EINVAL; }
+  const fgmres_opts o = *opts;
+  if (o.restart < 1 || o.restart > 32) { g_err = "restart must be in 1..32"; return HELM_EINVAL; }
+  if (!(o.tol >= 0) || o.maxit < 0) { g_err = "bad tol/maxit"; return HELM_EINVAL; }
+  if (o.flags & (HELM_FLAG_HOST_IO | HELM_FLAG_FP64 | HELM_FLAG_FALLBACK_V | HELM_FLAG_NO_GRAPH)) {
+    g_err = "fgmres_solve_batch takes device vectors and captured FP32 cycles (no HOST_IO, FP64, FALLBACK_V, NO_GRAPH)";
+    return HELM_EUNSUPPORTED;
+  }
+  const bool unet = precond == HELM_PREC_JU || precond == HELM_PREC_VU;
+  std::vector<FgJob> jobs(nh);
+  for (int i = 0; i < nh; ++i) {
+    HTRY(check_common(hs[i], nrhs[i], HELM_C32));
+    if (!b[i] || !x[i]) { g_err = "fgmres_solve_batch: null vector"; return HELM_EINVAL; }
+    for (int k = 0; k < i; ++k) {
+      if (hs[k] == hs[i]) { g_err = "fgmres_solve_batch: a handle appears twice"; return HELM_EINVAL; }
+      // a network keeps one activation workspace, sized for one grid
+      if (unet && nets && nets[k] == nets[i] &&
+          (hs[k]->d.nx != hs[i]->d.nx || hs[k]->d.ny != hs[i]->d.ny)) {
+        g_err = "fgmres_solve_batch: handles of different grids need their own network handles";
+        return HELM_EINVAL;
+      }
+    }
+    if (unet && (!nets || !nets[i])) { g_err = "U-Net preconditioner needs a network per handle"; return HELM_EINVAL; }
+    FgJob& J = jobs[i];
+    J.c = hs[i]; J.precond = precond; J.net = unet ? nets[i] : nullptr; J.b = (const double2*)b[i];
+    J.x = (double2*)x[i]; J.nrhs = nrhs[i]; J.o = o; J.caller = (cudaStream_t)stream;
+    J.res = results ? &results[i] : nullptr;
+  }
+  for (auto& J : jobs) HTRY(fg_prepare<float>(J));
+  // rounds: every unfinished handle's residual check is enqueued on its stream, then each
+  // in turn is waited for and given its next cycle, so the handles' cycles overlap
+  for (int left = nh; left > 0;) {
+    for (auto& J : jobs)
+      if (!J.finished) HTRY(fg_check<float>(J));
+    for (auto& J : jobs) {
+      if (J.finished) continue;
+      bool done = false;
+      HTRY(fg_step<float>(J, &done));
+      if (done) { J.finished = true; --left; }
+    }
+  }
+  int worst = HELM_OK;
+  for (auto& J : jobs) {
+    const int r = fg_finish<float>(J);
+    if (r < 0 && worst >= 0) worst = r;
+    else if (r == HELM_MAXIT && worst == HELM_OK) worst = r;
+  }
+  return worst;
+}
+
 int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int nrhs, const fgmres_opts* opts,
                   fgmres_result* result, helm_stream_t stream) {
   HTRY(check_common(h, nrhs, HELM_C32));
   if (!b || !x || !opts) { g_err = "null argument"; return HELM_EINVAL; }
   fgmres_opts o = *opts;
   if (nrhs > 16) { g_err = "block size (nrhs) must be at most 16"; return HELM_EINVAL; }
+  if (h->nmedia > 1) { g_err = "block FGMRES needs one operator for every column (one medium)"; return HELM_EUNSUPPORTED; }
   if (o.flags & HELM_FLAG_FALLBACK_V) { g_err = "HELM_FLAG_FALLBACK_V is for fgmres_solve"; return HELM_EUNSUPPORTED; }
   if (o.restart < 1 || o.restart > 32 || (o.restart + 1) * nrhs * nrhs > 4608) {
     g_err = "restart must be in 1..32 with (restart + 1) nrhs^2 <= 4608";
@@ -1149,6 +1291,7 @@ int bfgmres_solve(helm_t h, int precond, void* net, const void* b, void* x, int 
 int helm_gen_pairs(helm_t h, int count, unsigned long long seed, int kmax, void* r, void* e, helm_stream_t stream) {
   HTRY(check_common(h, count, HELM_C64));
   if (!r || !e || r == e || kmax < 1 || kmax > 1000) { g_err = "bad arguments"; return HELM_EINVAL; }
+  if (h->nmedia > 1) { g_err = "training pairs are generated on a handle of one medium"; return HELM_EUNSUPPORTED; }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)h->d.nx * h->d.ny;
   HTRY(ensure_work<float>(h, count, h->d.coarse_its > 10 ? h->d.coarse_its : 10));

@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(256) k_apply(Op<T> op, const typename vec2<T>:
                                                const typename vec2<T>::type* __restrict__ b,
                                                typename vec2<T>::type* __restrict__ y, const int* active) {
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= op.nx || iy >= op.ny) return;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(256) k_jacobi(Op<T> op, T w, const typename ve
                                                 typename vec2<T>::type* __restrict__ xout, const int* active) {
   typedef typename vec2<T>::type T2;
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
   if (ix >= op.nx || iy >= op.ny) return;
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict(Op<T> op, T w, const typ
   __shared__ T2 s_r[IY][IX];
   __shared__ T s_k[IY][IX];
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int nx = op.nx, ny = op.ny, nxc = nx / 2, nyc = ny / 2;
   const size_t N = (size_t)nx * ny;
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(256) k_prolong_jacobi(Op<T> op, T w, const typ
   __shared__ T2 s_f[TY][BX];
   __shared__ T s_k[TY][BX];
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int nx = op.nx, ny = op.ny;
   const size_t N = (size_t)nx * ny;
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float>
                                                                      float2* __restrict__ fc, const int* active,
                                                                      int nstrips) {
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
   if (strip >= nstrips) return;                  // uniform per warp
@@ -457,6 +462,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float>
                                                                      float2* __restrict__ out, const int* active,
                                                                      int nstrips) {
   const int rhs = blockIdx.z;
+  select_medium(op, rhs);
   if (active && !active[rhs]) return;
   const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
   if (strip >= nstrips) return;

@@ -812,6 +812,7 @@ void helm_geometry(helm_ctx* c, int* nx, int* ny, double* h, int* abc_w, double*
                    const float** gam);
 void* helm_scratch(helm_ctx* c, int real_bytes, int which, int nrhs);
 double helm_omega(helm_ctx* c);
+int helm_media(helm_ctx* c, int* rpp);
 int helm_bc(helm_ctx* c);
 int helm_stencil(helm_ctx* c);
 }  // namespace helm
@@ -828,6 +829,11 @@ static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool ad
   if (n->cfg.in_ch != 4 || n->cfg.out_ch != 2) { set_error("preconditioner net needs 4 inputs, 2 outputs"); return HELM_EINVAL; }
   const int cb = apply_chunk(n, nrhs, ny, nx);
   if (cb == 0) { set_error("grid too large for one U-Net image"); return HELM_EUNSUPPORTED; }
+  int rpp = 0;
+  if (helm_media(hc, &rpp) > 1 && n->encoder) {
+    set_error("the encoder-solver pair runs on a handle of one medium");
+    return HELM_EUNSUPPORTED;
+  }
   if (n->ws == nullptr || n->B != cb || n->ny != ny || n->nx != nx) {
     cudaStreamCaptureStatus cs;
     cudaStreamIsCapturing(s, &cs);
@@ -842,7 +848,7 @@ static int unet_apply(helm_ctx* hc, unet_ctx* n, const void* r, void* e, bool ad
     const int* gc = gate ? gate + c0 : nullptr;
     const bool s2d = s2d_input(n);
     make_input(rc, real_bytes == 8, cb, ny, nx, h, k2f, gam, s2d ? n->xs2d : n->x_in, xin_ld(n), n->scale, n->part,
-               gc, s, s2d);
+               gc, s, s2d, rpp, c0);
     n->xs2d_valid = s2d;
     UTRY(forward_impl(n, false, s));
     write_output(n->out, real_bytes == 8, cb, ny, nx, n->scale, ec, add, gc, s);
@@ -1165,6 +1171,10 @@ int unet_train_step(unet_t n, helm_t h, const float* x, const float* target, int
   double hh, gmax;
   const float *k2f, *gam;
   helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  if (helm_media(h, nullptr) > 1) {
+    set_error("this entry point needs a handle of one medium (helm_setup)");
+    return HELM_EUNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   if (n->encoder) UTRY(unet_encode(n, h, 1, stream));
   UTRY(unet_zero_grad(n, stream));
@@ -1285,6 +1295,7 @@ int unet_encode(unet_t solver, helm_t h, int train, helm_stream_t stream) {
   double hh, gmax;
   const float *k2f, *gam;
   helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  if (helm_media(h, nullptr) > 1) { set_error("the encoder runs on a handle of one medium"); return HELM_EUNSUPPORTED; }
   if (e->cfg.in_ch != 2) { set_error("encoder must take 2 inputs (kappa^2, gamma)"); return HELM_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
   UTRY(ensure_ws(e, 1, ny, nx));
@@ -1308,6 +1319,10 @@ int unet_make_batch(helm_t h, const void* r, const void* e, int npairs, int coun
   double hh, gmax;
   const float *k2f, *gam;
   helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  if (helm_media(h, nullptr) > 1) {
+    set_error("this entry point needs a handle of one medium (helm_setup)");
+    return HELM_EUNSUPPORTED;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nq = (size_t)count * nmix;
   int* d_idx = nullptr;
@@ -1338,6 +1353,10 @@ int unet_residual_loss(helm_t h, const float* out, const float* x, int B, float*
   double hh, gmax;
   const float *k2f, *gam;
   helm_geometry(h, &nx, &ny, &hh, &abc_w, &gmax, &k2f, &gam);
+  if (helm_media(h, nullptr) > 1) {
+    set_error("this entry point needs a handle of one medium (helm_setup)");
+    return HELM_EUNSUPPORTED;
+  }
   const double om = helm_omega(h);
   cudaStream_t s = (cudaStream_t)stream;
   float *rho = nullptr, *part = nullptr;

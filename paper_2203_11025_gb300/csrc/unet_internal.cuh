@@ -107,7 +107,8 @@ void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s)
 // Network input (Sec. 3.4): Re r, Im r divided by rms(r), kappa^2, gamma; s2d: into the
 // space-to-depth layout [b][y/2][x/2][2x2 block][4] (ny, nx even), else ldx-channel pixels.
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d);
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d, int rpp = 0,
+                int b0 = 0);
 // FP32 4-channel pixels [M][lds] into the space-to-depth BF16 layout, and that layout back to
 // ldd-channel pixels (channels past 4 zeroed).
 void to_bf16_s2d(const float* src, int lds, __nv_bfloat16* dst, int B, int ny, int nx, cudaStream_t s);

@@ -582,9 +582,10 @@ template <typename T2, bool S2D>
 __global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, int N, int nx, double h2,
                                                      const float* __restrict__ k2, const float* __restrict__ gam,
                                                      const float* __restrict__ part, __nv_bfloat16* __restrict__ x,
-                                                     int ldx, float* __restrict__ sc, const int* gate) {
+                                                     int ldx, float* __restrict__ sc, const int* gate, int rpp, int b0) {
   const int b = blockIdx.y;
   if (gate && !gate[b]) return;
+  if (rpp > 0) k2 += (size_t)((b0 + b) / rpp) * N;   // this right-hand side's medium (a batch of problems)
   __shared__ float s_scale;
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -911,17 +912,26 @@ void f32_to_bf16(const float* src, __nv_bfloat16* dst, size_t n, cudaStream_t s)
 }
 
 void make_input(const void* r, bool fp64, int B, int ny, int nx, double h, const float* k2, const float* gam,
-                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d) {
+                __nv_bfloat16* x, int ldx, float* sc, float* part, const int* gate, cudaStream_t s, bool s2d, int rpp,
+                int b0) {
   const int N = nx * ny;
   const dim3 grid(kInBlocks, B);
   if (fp64) {
     k_input_partial<double2><<<grid, 256, 0, s>>>((const double2*)r, N, part, gate);
-    if (s2d) k_input_write<double2, true><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
-    else k_input_write<double2, false><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
+    if (s2d)
+      k_input_write<double2, true><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc,
+                                                        gate, rpp, b0);
+    else
+      k_input_write<double2, false><<<grid, 256, 0, s>>>((const double2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc,
+                                                         gate, rpp, b0);
   } else {
     k_input_partial<float2><<<grid, 256, 0, s>>>((const float2*)r, N, part, gate);
-    if (s2d) k_input_write<float2, true><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
-    else k_input_write<float2, false><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc, gate);
+    if (s2d)
+      k_input_write<float2, true><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc,
+                                                       gate, rpp, b0);
+    else
+      k_input_write<float2, false><<<grid, 256, 0, s>>>((const float2*)r, N, nx, h * h, k2, gam, part, x, ldx, sc,
+                                                        gate, rpp, b0);
   }
 }
 

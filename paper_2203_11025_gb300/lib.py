@@ -31,7 +31,8 @@ ABI_SYMBOLS = [
     "helm_desc_default", "helm_setup", "helm_destroy", "helm_last_error", "helm_level_shape",
     "helm_level_kappa2", "helm_apply", "helm_residual", "helm_jacobi", "helm_restrict",
     "helm_prolong_add", "helm_coarse_solve", "sl_vcycle", "fgmres_solve", "bfgmres_solve", "helm_time_kernel",
-    "helm_coarse_solve_static", "helm_tile_choice", "helm_set_tile_choice",
+    "helm_coarse_solve_static", "helm_tile_choice", "helm_set_tile_choice", "helm_setup_media",
+    "fgmres_solve_batch",
     # include/unet.h
     "unet_cfg_default", "unet_create", "unet_destroy", "unet_sizes", "unet_set_params", "unet_get_params",
     "unet_set_bn_stats", "unet_get_bn_stats", "unet_get_grads", "unet_zero_grad", "unet_forward", "unet_backward",
@@ -92,6 +93,8 @@ def load():
     sig = {
         "helm_desc_default": (I, [ctypes.POINTER(helm_desc), I, I]),
         "helm_setup": (I, [ctypes.POINTER(helm_desc), P, P, ctypes.POINTER(P)]),
+        "helm_setup_media": (I, [ctypes.POINTER(helm_desc), P, I, I, P, ctypes.POINTER(P)]),
+        "fgmres_solve_batch": (I, [I, P, I, P, P, P, P, ctypes.POINTER(fgmres_opts), P, P]),
         "helm_destroy": (None, [P]),
         "helm_last_error": (ctypes.c_char_p, []),
         "helm_level_shape": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -231,19 +234,29 @@ def desc_value(field: str, value):
 
 
 class Helmholtz:
-    """A solver handle: medium kappa^2 (float32 CUDA tensor [ny, nx]) plus desc."""
+    """A solver handle: medium kappa^2 (float32 CUDA tensor [ny, nx]) plus desc.  A tensor
+    [nmedia, ny, nx] with rpp makes a batch handle of one grid size (helm_setup_media):
+    right-hand side r is solved on medium r // rpp."""
 
-    def __init__(self, kappa2, desc=None, **overrides):
+    def __init__(self, kappa2, desc=None, rpp=0, **overrides):
         import torch
         if kappa2.dtype != torch.float32 or not kappa2.is_cuda:
             raise TypeError("kappa2 must be a float32 CUDA tensor")
-        ny, nx = kappa2.shape
+        ny, nx = kappa2.shape[-2:]
+        self.nmedia = kappa2.shape[0] if kappa2.dim() == 3 else 1
+        self.rpp = rpp if self.nmedia > 1 else 0
         self.desc = desc if desc is not None else helm_desc_default(nx, ny)
         for k, v in overrides.items():
             setattr(self.desc, k, desc_value(k, v))
         self.kappa2 = kappa2.contiguous()
-        self.h = helm_setup(self.desc, self.kappa2)
         self.lib = load()
+        if self.nmedia == 1:
+            self.h = helm_setup(self.desc, self.kappa2)
+        else:
+            h = ctypes.c_void_p()
+            _check(self.lib.helm_setup_media(ctypes.byref(self.desc), _ptr(self.kappa2), self.nmedia, self.rpp, None,
+                                             ctypes.byref(h)), "helm_setup_media")
+            self.h = h
 
     def close(self):
         if self.h:
@@ -414,6 +427,36 @@ class Helmholtz:
         return x, {"status": code, "iters": list(iters), "relres": list(relres), "iters_max": res.iters_max,
                    "relres_max": res.relres_max, "cycles": res.cycles, "launches": res.launches,
                    "fallbacks": res.fallbacks}
+
+
+def fgmres_batch(handles, bs, precond=HELM_PREC_V, nets=None, restart=10, tol=1e-7, maxit=5000, xs=None,
+                 stream=None):
+    """Solve the problems of several handles (e.g. one per grid size) in one call
+    (fgmres_solve_batch): bs[i] complex128 CUDA tensors [nrhs_i, ny_i, nx_i]; nets: one
+    network per handle for the U-Net preconditioners.  Returns (xs, infos)."""
+    import torch
+    nh = len(handles)
+    if xs is None:
+        xs = [torch.zeros_like(b) for b in bs]
+    flags = HELM_FLAG_X0_ZERO
+    opts = fgmres_opts(restart, tol, maxit, flags)
+    H = (ctypes.c_void_p * nh)(*[hz.h.value if hasattr(hz.h, "value") else hz.h for hz in handles])
+    B = (ctypes.c_void_p * nh)(*[b.data_ptr() for b in bs])
+    X = (ctypes.c_void_p * nh)(*[x.data_ptr() for x in xs])
+    nr = [int(b.shape[0]) for b in bs]
+    NR = (ctypes.c_int * nh)(*nr)
+    NETS = None
+    if nets is not None:
+        NETS = (ctypes.c_void_p * nh)(*[n.handle.value if hasattr(n.handle, "value") else n.handle for n in nets])
+    its = [(ctypes.c_int * k)() for k in nr]
+    rel = [(ctypes.c_double * k)() for k in nr]
+    RES = (fgmres_result * nh)(*[fgmres_result(0, 0, 0.0, 0, its[i], rel[i], 0) for i in range(nh)])
+    code = load().fgmres_solve_batch(nh, H, precond, NETS, B, X, NR, ctypes.byref(opts), RES, _stream(stream))
+    _check(code, "fgmres_solve_batch", ok=(HELM_OK, HELM_MAXIT))
+    infos = [{"status": RES[i].status, "iters": list(its[i]), "relres": list(rel[i]), "iters_max": RES[i].iters_max,
+              "relres_max": RES[i].relres_max, "cycles": RES[i].cycles, "launches": RES[i].launches}
+             for i in range(nh)]
+    return xs, infos
 
 
 def unet_cfg_default(kind=UNET_STANDALONE):

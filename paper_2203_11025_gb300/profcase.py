@@ -14,8 +14,6 @@
   python -m paper_2203_11025_gb300.profcase resloss 256 16 # the residual loss of a batch of 16
   python -m paper_2203_11025_gb300.profcase variants 1024 8 # stencil-kernel times and the M_V solve per
                                                            # boundary mode and stencil
-  python -m paper_2203_11025_gb300.profcase homog 128 10   # homogeneous medium: train, then M_V / M_JU /
-                                                           # M_VU iterations and Eq. 4.1 factors
 
 Inputs are seeded and synthetic; nothing here checks results (the tests do).
 """
@@ -157,24 +155,6 @@ def main(argv):
             rec.update({"mv_ms": round(e0.elapsed_time(e1), 2), "mv_iters": info["iters_max"]})
             print(json.dumps(rec), flush=True)
             hz.close()
-    elif what == "homog":
-        # the homogeneous-medium experiment of Sec. 4 (kappa = 1): a network trained on that
-        # medium, then FGMRES(10) with M_V, M_JU and M_VU on b point sources; iterations and
-        # Eq. 4.1 factors per preconditioner
-        import json
-        from paper_2203_11025_gb300 import metrics
-        from paper_2203_11025_gb300 import train as T
-        k2 = torch.ones(n, n, dtype=torch.float32, device="cuda")
-        hz = lib.Helmholtz(k2)
-        net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=7)
-        T.train(hz, net, pairs=hz.gen_pairs(512, 5151, 10), epochs=40, batch=16, lr=1e-3, seed=11)
-        pos = synth.source_positions(n, n, b, synth.rhs_seed(0), n // 8)
-        rhs = torch.from_numpy(synth.point_sources(n, n, pos, 1.0 / n)).cuda()
-        for name, pc in (("M_V", lib.HELM_PREC_V), ("M_JU", lib.HELM_PREC_JU), ("M_VU", lib.HELM_PREC_VU)):
-            _, info = hz.fgmres(rhs, precond=pc, net=net if pc != lib.HELM_PREC_V else None, tol=1e-6,
-                                maxit=5000)
-            print(json.dumps({"precond": name, "iters": info["iters"], "status": info["status"],
-                              **metrics.summary(info["relres"], info["iters"])}), flush=True)
     else:
         raise SystemExit(f"unknown case {what}")
 

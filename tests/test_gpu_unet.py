@@ -643,3 +643,37 @@ def test_trained_network_gains_over_plain_sl(lib):
     x = x.cpu().numpy()
     for k in range(8):
         assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])
+
+
+@pytest.mark.slow
+def test_general_network_gains_on_an_unseen_medium(lib):
+    """The general network of Sec. 3.4.1 / 4: trained on Eq. 3.8-3.9 pairs of 16 random
+    256^2 media (64 pairs each, none of them the test medium), it lowers FGMRES(M_VU)
+    iterations against plain SL on a medium it never saw (measured: 106-132 against
+    196-230 on three unseen media); every solution is checked by the oracle's FP64 residual."""
+    from paper_2203_11025_gb300 import train as T
+    n = 256
+    media = []
+    for i in range(16):
+        hz_i = lib.Helmholtz(torch.from_numpy(synth.grf_kappa2(n, n, 10 ** 6 + i)).cuda())
+        media.append((hz_i, hz_i.gen_pairs(64, 4000 + i, 10)))
+    net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=7)
+    hist = T.train_media(media, net, epochs=96, batch=16, lr=1e-3, seed=11)
+    assert hist[-1] < 0.6 * hist[0]
+    for hz_i, _ in media:
+        hz_i.close()
+    k2 = synth.grf_kappa2(n, n, 777)               # unseen
+    hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+    d = hz.desc
+    prob = H.Problem(k2.astype(np.float64), omega=d.omega, h=d.h, abc_width=d.abc_width, levels=d.levels)
+    pos = synth.source_positions(n, n, 4, synth.rhs_seed(7), 16)
+    b = synth.point_sources(n, n, pos, 1.0 / n)
+    bt = torch.from_numpy(b).cuda()
+    _, iv = hz.fgmres(bt, precond=lib.HELM_PREC_V, tol=1e-7, maxit=20000)
+    x, iu = hz.fgmres(bt, precond=lib.HELM_PREC_VU, net=net, tol=1e-7, maxit=20000)
+    assert iv["status"] == lib.HELM_OK and iu["status"] == lib.HELM_OK
+    for k in range(4):
+        assert iu["iters"][k] <= 0.75 * iv["iters"][k], (k, iu["iters"], iv["iters"])
+    x = x.cpu().numpy()
+    for k in range(4):
+        assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])

@@ -37,6 +37,7 @@ def test_benchmark_preset_matches_the_benchmark_problem():
                                                                bench.RETRAIN_LR)
     g = presets.get("general_256")
     assert g.train_pairs == bench.TRAIN_MEDIA * bench.TRAIN_PAIRS_PER_MEDIUM and g.train_epochs == bench.TRAIN_EPOCHS
+    assert bench.TRAIN_PAIRS == g.train_pairs
 
 
 def test_mixed_right_hand_sides():
