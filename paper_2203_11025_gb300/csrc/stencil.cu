@@ -372,6 +372,26 @@ __device__ __forceinline__ float2 op_at(const Op<float>& op, int x, int y, float
   return k;
 }
 
+// Rows of a strip away from every boundary and the absorbing layer (warp-uniform test):
+// there g = 0, no neighbour is outside the grid and no boundary mode applies, so the
+// diagonal and the stencil take their plain forms.
+__device__ __forceinline__ bool strip_interior(const Op<float>& op, int xs, int y) {
+  const int A = op.abc_w > 1 ? op.abc_w : 1;
+  return y >= A && y < op.ny - A && xs >= A && xs + 63 < op.nx - A;
+}
+__device__ __forceinline__ float2 diag_plain(const Op<float>& op, float k2) {
+  const float wk = op.omega2 * k2;
+  return make_float2(4.f * op.inv_h2 - wk, wk * op.beta);
+}
+__device__ __forceinline__ float2 op_plain(const Op<float>& op, float2 d, float2 c, float2 l, float2 r, float2 dn,
+                                           float2 up) {
+  float2 k = cmul(d, c);
+  const float2 s = cadd(cadd(l, r), cadd(dn, up));   // the general form's summation order
+  k.x -= s.x * op.inv_h2;
+  k.y -= s.y * op.inv_h2;
+  return k;
+}
+
 // f_c = R (f - K v) (v == nullptr: v = w D^-1 f) for coarse rows [I0, I0 + TI) of one strip.
 template <int BC, int TI>
 __global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float> op, float w,
@@ -407,12 +427,18 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float>
     }
     return q;
   };
+  const int xs = strip * kStripW - 2;
   auto prep = [&](int yy, const Raw& q, CPair& vv, CPair& dd) {
     vv = q.v;
     dd = cp_zero();
     if (colin && yy >= 0 && yy < ny) {
-      dd.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
-      dd.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      if (strip_interior(op, xs, yy)) {
+        dd.a = diag_plain(op, q.k.x);
+        dd.b = diag_plain(op, q.k.y);
+      } else {
+        dd.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
+        dd.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      }
       if (!vr) {
         vv.a = jacobi_from_zero(q.f.a, dd.a, w);
         vv.b = jacobi_from_zero(q.f.b, dd.b, w);
@@ -432,7 +458,10 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float>
       const int y = yy - 1;
       const float2 lft = shfl_up1(v0.b), rgt = shfl_dn1(v0.a);
       CPair rc = cp_zero();
-      if (colin && y >= 0 && y < ny) {
+      if (strip_interior(op, xs, y)) {
+        rc.a = csub(f0.a, op_plain(op, d0.a, v0.a, lft, v0.b, vm.a, vp.a));
+        rc.b = csub(f0.b, op_plain(op, d0.b, v0.b, v0.a, rgt, vm.b, vp.b));
+      } else if (colin && y >= 0 && y < ny) {
         rc.a = csub(f0.a, op_at<BC>(op, c0, y, d0.a, v0.a, lft, v0.b, vm.a, vp.a));
         rc.b = csub(f0.b, op_at<BC>(op, c0 + 1, y, d0.b, v0.b, v0.a, rgt, vm.b, vp.b));
       }
@@ -511,8 +540,13 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float>
     }
     CPair xp = cp_zero(), dp = cp_zero();
     if (colin && yy >= 0 && yy < ny) {
-      dp.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
-      dp.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      if (strip_interior(op, c0 - 2 * lane, yy)) {
+        dp.a = diag_plain(op, q.k.x);
+        dp.b = diag_plain(op, q.k.y);
+      } else {
+        dp.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
+        dp.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+      }
       CPair base = q.v;
       if (!vr && implicit_v) { base.a = jacobi_from_zero(q.f.a, dp.a, w); base.b = jacobi_from_zero(q.f.b, dp.b, w); }
       // P e_c: even rows take coarse row yy / 2, odd rows the mean of two coarse rows;
@@ -526,8 +560,11 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float>
       const int y = yy - 1;
       const float2 lft = shfl_up1(x0.b), rgt = shfl_dn1(x0.a);
       if (colin && lane >= 1 && lane <= 30 && y < ny) {
-        const float2 ka = op_at<BC>(op, c0, y, d0.a, x0.a, lft, x0.b, xm.a, xp.a);
-        const float2 kb = op_at<BC>(op, c0 + 1, y, d0.b, x0.b, x0.a, rgt, xm.b, xp.b);
+        const bool in = strip_interior(op, c0 - 2 * lane, y);
+        const float2 ka = in ? op_plain(op, d0.a, x0.a, lft, x0.b, xm.a, xp.a)
+                             : op_at<BC>(op, c0, y, d0.a, x0.a, lft, x0.b, xm.a, xp.a);
+        const float2 kb = in ? op_plain(op, d0.b, x0.b, x0.a, rgt, xm.b, xp.b)
+                             : op_at<BC>(op, c0 + 1, y, d0.b, x0.b, x0.a, rgt, xm.b, xp.b);
         CPair r;
         r.a = cadd(x0.a, jacobi_from_zero(csub(f0.a, ka), d0.a, w));
         r.b = cadd(x0.b, jacobi_from_zero(csub(f0.b, kb), d0.b, w));
