@@ -139,6 +139,20 @@ __host__ __device__ constexpr uint32_t idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+// Division by a divisor fixed at launch: n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31,
+// with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1 (the round-up multiplier of
+// Granlund and Montgomery, "Division by invariant integers using multiplication", 1994).
+struct FDiv { uint32_t d, m, s; };
+inline FDiv make_fdiv(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ull << s) < d) ++s;
+  const uint64_t m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  return {d, (uint32_t)m, s};
+}
+__device__ __forceinline__ int fdiv(const FDiv& f, int n) {
+  return (int)((__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
+}
+
 struct TmaArgs {
   int B, Ho, Wo, Cout, NT;
   int k, stride, pad, transposed;
@@ -169,7 +183,20 @@ struct TmaArgs {
   float* part; size_t slice;
   int* cnt;
   int* err;
+  FDiv f_tile, f_tx, f_ty, f_ks;  // tx * ty * tb, tx, ty, ksplit
+  FDiv f_ns;                      // nst (stage ring position and phase of K-block g)
+  int lg_nacc;                    // log2(nacc)
 };
+
+// The divisors decode() uses, from the filled-in tile counts.
+void set_fdivs(TmaArgs& a) {
+  a.f_tile = make_fdiv((uint32_t)(a.tx * a.ty * a.tb));
+  a.f_tx = make_fdiv((uint32_t)a.tx);
+  a.f_ty = make_fdiv((uint32_t)a.ty);
+  a.f_ks = make_fdiv((uint32_t)a.ksplit);
+  a.f_ns = make_fdiv((uint32_t)a.nst);
+  a.lg_nacc = a.nacc == 4 ? 2 : (a.nacc == 2 ? 1 : 0);
+}
 
 // eLU for BF16 results: exp(x) - 1 with the fast exponential (absolute error ~1e-7,
 // far below the BF16 rounding of the stored value; expm1f made the epilogue issue-bound).
@@ -181,11 +208,9 @@ struct Item {
 };
 
 __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
-  const int ntile = a.tx * a.ty * a.tb;
-  int t = w % ntile;
-  const int r = w / ntile;
-  const int nph = a.transposed ? 4 : 1;
-  const int z = r % nph, ys = r / nph;
+  const int r = fdiv(a.f_tile, w);
+  int t = w - r * (int)a.f_tile.d;
+  const int z = a.transposed ? (r & 3) : 0, ys = a.transposed ? (r >> 2) : r;
   Item it;
   it.py = a.transposed ? (z >> 1) : 0;
   it.px = a.transposed ? (z & 1) : 0;
@@ -196,11 +221,13 @@ __device__ __forceinline__ Item decode(const TmaArgs& a, int w) {
   it.nchk = a.nch0 + a.nch1;
   const int nkb_all = nty * it.ntx * it.nchk;
   // balanced K ranges; the host keeps ksplit <= nkb_all, so nkb >= 1
-  it.kbeg = ys * nkb_all / a.ksplit;
-  it.nkb = (ys + 1) * nkb_all / a.ksplit - it.kbeg;
+  it.kbeg = fdiv(a.f_ks, ys * nkb_all);
+  it.nkb = fdiv(a.f_ks, (ys + 1) * nkb_all) - it.kbeg;
   it.split = ys;
-  const int tix = t % a.tx; t /= a.tx;
-  const int tiy = t % a.ty; t /= a.ty;
+  const int t1 = fdiv(a.f_tx, t), tix = t - t1 * a.tx;
+  t = t1;
+  const int t2 = fdiv(a.f_ty, t), tiy = t - t2 * a.ty;
+  t = t2;
   it.x0 = tix * a.BX; it.y0 = tiy * a.BY; it.b0 = t * a.BB;
   return it;
 }
@@ -232,16 +259,35 @@ __device__ __forceinline__ bool epi_any(bool p, int g, bool alt) {
   return r != 0;
 }
 
-// Bias, residual, BatchNorm and eLU on 16 consecutive channels [cb, cb + 16) of one
-// pixel, then the store (BF16 y, or FP32 out).  k: per-channel constants in shared memory.
+// Per-column epilogue constants: with BatchNorm (BF16 results) y = (acc + bias + res) *
+// scale + shift = acc * mul + add + res * mul with mul = scale and add = bias * scale +
+// shift; without it mul = 1 and add = bias.  One FMA per value (two with a residual).
+__device__ __forceinline__ void epi_constants(const TmaArgs& a, float* s_mul, float* s_add) {
+  const bool bn = a.ybf && a.scale;
+  for (int c = threadIdx.x; c < a.Cout && c < 256; c += blockDim.x) {
+    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
+    const float m = bn ? a.scale[ch] : 1.f;
+    s_mul[c] = m;
+    s_add[c] = (a.bias ? a.bias[ch] : 0.f) * m + (bn ? a.shift[ch] : 0.f);
+  }
+}
+
+// Bias, residual, BatchNorm and eLU on 16 consecutive columns [cb, cb + 16) of one pixel,
+// then the store (BF16 y, or FP32 out).  km / ka: the per-column constants in shared memory.
 __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix, int cb, int sc, bool add_lin,
-                                         const uint4* r4, const float* kb, const float* ks, const float* kh) {
+                                         const uint4* r4, const float* km, const float* ka) {
   // cb: first column (per-column constants), sc: first channel of the stored pixel
   if (cb + 16 <= a.Cout && a.vec) {
     if (add_lin) {
-      if (a.bias) {
+      const float4* m4 = reinterpret_cast<const float4*>(km + cb);
+      const float4* a4 = reinterpret_cast<const float4*>(ka + cb);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) f[j] += kb[cb + j];
+      for (int q = 0; q < 4; ++q) {
+        const float4 m = m4[q], c = a4[q];
+        f[4 * q] = fmaf(f[4 * q], m.x, c.x);
+        f[4 * q + 1] = fmaf(f[4 * q + 1], m.y, c.y);
+        f[4 * q + 2] = fmaf(f[4 * q + 2], m.z, c.z);
+        f[4 * q + 3] = fmaf(f[4 * q + 3], m.w, c.w);
       }
       if (a.res) {
 #pragma unroll
@@ -250,17 +296,17 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const float2 rf = __bfloat1622float2(r2[j]);
-            f[8 * h + 2 * j] += rf.x;
-            f[8 * h + 2 * j + 1] += rf.y;
+            const int i = 8 * h + 2 * j;
+            f[i] = fmaf(rf.x, km[cb + i], f[i]);
+            f[i + 1] = fmaf(rf.y, km[cb + i + 1], f[i + 1]);
           }
         }
       }
     }
     if (a.ybf) {
+      if (a.act) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (a.scale) f[j] = f[j] * ks[cb + j] + kh[cb + j];
-        if (a.act) f[j] = elu_bf(f[j]);
+        for (int j = 0; j < 16; ++j) f[j] = elu_bf(f[j]);
       }
       uint4 o4[2];
       __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(o4);
@@ -292,10 +338,11 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
     const int co = cb + j, so = sc + j;
     if (co >= a.Cout) break;
     float g = f[j];
-    if (add_lin && a.bias) g += kb[co];
-    if (add_lin && a.res) g += __bfloat162float(a.res[pix * a.ldr + so]);
+    if (add_lin) {
+      g = fmaf(g, km[co], ka[co]);
+      if (a.res) g = fmaf(__bfloat162float(a.res[pix * a.ldr + so]), km[co], g);
+    }
     if (a.ybf) {
-      if (a.scale) g = g * ks[co] + kh[co];
       if (a.act) g = elu_bf(g);
       const __nv_bfloat16 gb = __float2bfloat16_rn(g);
       a.ybf[pix * a.ldy + so] = gb;
@@ -309,12 +356,11 @@ __device__ __forceinline__ void finish16(const TmaArgs& a, float* f, size_t pix,
   }
 }
 
-// One value of column n stored as channel sc of pixel pix (bias, BatchNorm, eLU as finish16).
-__device__ __forceinline__ void finish1(const TmaArgs& a, float g, size_t pix, int n, int sc, const float* kb,
-                                        const float* ks, const float* kh) {
-  if (a.bias) g += kb[n];
+// One value of column n stored as channel sc of pixel pix (constants and eLU as finish16).
+__device__ __forceinline__ void finish1(const TmaArgs& a, float g, size_t pix, int n, int sc, const float* km,
+                                        const float* ka) {
+  g = fmaf(g, km[n], ka[n]);
   if (a.ybf) {
-    if (a.scale) g = g * ks[n] + kh[n];
     if (a.act) g = elu_bf(g);
     const __nv_bfloat16 gb = __float2bfloat16_rn(g);
     a.ybf[pix * a.ldy + sc] = gb;
@@ -334,15 +380,14 @@ __device__ __forceinline__ void epi_sync(int g, bool alt) {
 // The epilogue of columns [c0, c0 + 16) of pixel pix of an item (non-split layout rules:
 // plain, or the sub-pixel scatter of transposed layers), from accumulated values f.
 __device__ __forceinline__ void finish_chunk(const TmaArgs& a, float* f, size_t pix, int b, int oy, int ox, int c0,
-                                             const uint4* rc, const float* s_bias, const float* s_scale,
-                                             const float* s_shift) {
+                                             const uint4* rc, const float* km, const float* ka) {
   if (!a.shuf) {
-    finish16(a, f, pix, c0, c0, true, rc, s_bias, s_scale, s_shift);
+    finish16(a, f, pix, c0, c0, true, rc, km, ka);
   } else if (a.cr % 16 == 0) {
     // sub-pixel: the chunk is one phase's channels [co0, co0 + 16)
     const int ph = c0 / a.cr, co0 = c0 - ph * a.cr;
     const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
-    finish16(a, f, opix, c0, co0, true, rc, s_bias, s_scale, s_shift);
+    finish16(a, f, opix, c0, co0, true, rc, km, ka);
   } else {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -350,9 +395,29 @@ __device__ __forceinline__ void finish_chunk(const TmaArgs& a, float* f, size_t 
       if (n >= a.Cout) break;
       const int ph = n / a.cr, co = n - ph * a.cr;
       const size_t opix = ((size_t)b * (2 * a.Ho) + 2 * oy + (ph >> 1)) * (2 * a.Wo) + 2 * ox + (ph & 1);
-      finish1(a, f[j], opix, n, co, s_bias, s_scale, s_shift);
+      finish1(a, f[j], opix, n, co, km, ka);
     }
   }
+}
+
+// Start reading 16 consecutive TMEM columns of this warp's 32 lanes (32x32b shape: thread t
+// gets lane t); complete with tcgen05.wait::ld before using v.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// Wait for the outstanding TMEM reads; v is tied to the wait so that no use of it can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&v)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
 }
 
 // Epilogue warps (0 .. NEPI-1) of both convolution kernels: drain TMEM accumulator
@@ -362,8 +427,7 @@ __device__ __forceinline__ void finish_chunk(const TmaArgs& a, float* f, size_t 
 // drain at a time); otherwise group w / 4 takes the 16-column chunks w / 4, w / 4 + 2, ...
 // of every item (wide tiles).
 __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
-                                              int* s_fail, const float* s_bias, const float* s_scale,
-                                              const float* s_shift) {
+                                              int* s_fail, const float* km, const float* ka) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.NT;
   volatile int* fail = s_fail;
@@ -377,8 +441,8 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
   for (int w = blockIdx.x + (alt ? grp : 0) * gridDim.x; w < a.nitems; w += istep * gridDim.x, li += istep) {
     if (epi_any(failed(fail), grp, alt)) break;
     const Item it = decode(a, w);
-    const int acc = li % a.nacc;
-    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li / a.nacc) & 1u);
+    const int acc = li & (a.nacc - 1);
+    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> a.lg_nacc) & 1u);
     if (epi_any(!ok, grp, alt)) { atomicExch(s_fail, 1); break; }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
@@ -392,24 +456,22 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
       const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + cfirst);
       rn[0] = rp[0]; rn[1] = rp[1];
     }
+    // TMEM columns of chunk c0 for this warp's lane quadrant; the next chunk's read is
+    // issued before the current chunk is finished, so its latency overlaps that work
+    const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * a.colsz);
     for (int c0 = cfirst; c0 < N; c0 += cstep) {
+      uint32_t v[16];
+      tmem_ld16(trow + (uint32_t)c0, v);
       const uint4 rc[2] = {rn[0], rn[1]};
       if (pre && c0 + cstep + 16 <= a.Cout) {
         const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0 + cstep);
         rn[0] = rp[0]; rn[1] = rp[1];
       }
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * a.colsz + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (!rv) continue;
+      tmem_wait16(v);
       float f[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(v[j]);
+      if (!rv) continue;
       if (a.ksplit > 1) {
         // partial sums of this K range into the split's slice (plain stores)
         float* dst = a.part + (size_t)it.split * a.slice + pix * a.Cout + c0;
@@ -423,7 +485,7 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
             if (c0 + j < a.Cout) dst[j] = f[j];
         }
       } else {
-        finish_chunk(a, f, pix, b, oy, ox, c0, rc, s_bias, s_scale, s_shift);
+        finish_chunk(a, f, pix, b, oy, ox, c0, rc, km, ka);
       }
     }
     // accumulator read: hand buffer acc back to the MMA warp
@@ -468,7 +530,7 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
             const uint4* rp = reinterpret_cast<const uint4*>(a.res + pix * a.ldr + c0);
             rc[0] = rp[0]; rc[1] = rp[1];
           }
-          finish_chunk(a, f, pix, b, oy, ox, c0, rc, s_bias, s_scale, s_shift);
+          finish_chunk(a, f, pix, b, oy, ox, c0, rc, km, ka);
         }
         if ((warp & 3) == 0 && lane == 0 && (alt || grp == 0)) a.cnt[tile] = 0;   // ready for the next launch
       }
@@ -488,7 +550,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
   __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[NACC], tempty[NACC], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  __shared__ float s_bias[256], s_scale[256], s_shift[256];
+  __shared__ __align__(16) float s_mul[256], s_add[256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.NT, NS = a.nst;
 
@@ -515,12 +577,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
   // everything above overlaps the previous kernel; global memory is read from here on
   griddep_wait();
   griddep_launch();
-  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
-    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
-    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
-    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
-    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
-  }
+  epi_constants(a, s_mul, s_add);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -537,8 +594,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
         int ch = it.kbeg % it.nchk, tap = it.kbeg / it.nchk;
         int ty = tap / it.ntx, tx = tap - ty * it.ntx;
         for (int kb = 0; kb < it.nkb; ++kb, ++g) {
-          const int s = (int)(g % (uint32_t)NS);
-          const uint32_t use = g / (uint32_t)NS;
+          const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+          const int s = (int)(g - use * (uint32_t)NS);
           if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
           const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
           int ix, iy;
@@ -567,16 +624,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
       int li = 0;
       for (int w = blockIdx.x; w < a.nitems && !failed(fail); w += gridDim.x, ++li) {
         const Item it = decode(a, w);
-        const int acc = li % a.nacc;
-        const uint32_t use = (uint32_t)(li / a.nacc);
+        const int acc = li & (a.nacc - 1);
+        const uint32_t use = (uint32_t)(li >> a.lg_nacc);
         if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (use - 1) & 1u)) { atomicExch(&s_fail, 1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
         bool ok = true;
         int kch = it.kbeg % it.nchk;   // chunk of K-block kbeg + kb, stepped below
         for (int kb = 0; kb < it.nkb; ++kb, ++g, kch = (kch + 1 == it.nchk) ? 0 : kch + 1) {
-          const int s = (int)(g % (uint32_t)NS);
-          if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
+          const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+          const int s = (int)(g - use * (uint32_t)NS);
+          if (!mb_wait(su32(&full[s]), use & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sA = base + (uint32_t)s * stage;
           const uint64_t da = desc_k(sA, TK), db = desc_k(sA + a_bytes, TK);
@@ -608,7 +666,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
       mb_wait(su32(&drain), 0);
     }
   } else {
-    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_bias, s_scale, s_shift);
+    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_mul, s_add);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -639,7 +697,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
   __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[NACC], tempty[NACC], drain, wres;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
-  __shared__ float s_bias[256], s_scale[256], s_shift[256];
+  __shared__ __align__(16) float s_mul[256], s_add[256];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.NT, NS = a.nst;
   const uint32_t wbase = (su32(smem) + 1023u) & ~1023u;          // resident weights
@@ -669,12 +727,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
   // everything above overlaps the previous kernel; global memory is read from here on
   griddep_wait();
   griddep_launch();
-  for (int c = tid; c < a.Cout && c < 256; c += NTHR) {
-    const int ch = a.shuf ? c % a.cr : c;   // per column (sub-pixel: the column's channel)
-    s_bias[c] = a.bias ? a.bias[ch] : 0.f;
-    s_scale[c] = a.scale ? a.scale[ch] : 1.f;
-    s_shift[c] = a.shift ? a.shift[ch] : 0.f;
-  }
+  epi_constants(a, s_mul, s_add);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -699,8 +752,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
         for (int ch = 0; ch < nch && ok; ++ch)
           for (int cls = 0; cls < ncls && ok; ++cls)
             for (int xt = 0; xt < nxt; ++xt, ++g) {
-              const int s = (int)(g % (uint32_t)NS);
-              const uint32_t use = g / (uint32_t)NS;
+              const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+              const int s = (int)(g - use * (uint32_t)NS);
               if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
               int ix, iy;
               if (!tr) {
@@ -730,8 +783,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
       int li = 0;
       for (int w = blockIdx.x; w < a.nitems && wok && !failed(fail); w += gridDim.x, ++li) {
         const Item it = decode(a, w);
-        const int acc = li % a.nacc;
-        if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (uint32_t)(li / a.nacc - 1) & 1u)) {
+        const int acc = li & (a.nacc - 1);
+        if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> a.lg_nacc) - 1) & 1u)) {
           atomicExch(&s_fail, 1);
           break;
         }
@@ -743,8 +796,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
         for (int ch = 0; ch < nch && ok; ++ch)
           for (int cls = 0; cls < ncls && ok; ++cls)
             for (int xt = 0; xt < nxt; ++xt, ++g) {
-              const int s = (int)(g % (uint32_t)NS);
-              if (!mb_wait(su32(&full[s]), (g / (uint32_t)NS) & 1u)) { ok = false; break; }
+              const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+              const int s = (int)(g - use * (uint32_t)NS);
+              if (!mb_wait(su32(&full[s]), use & 1u)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
               const uint32_t sA = base + (uint32_t)s * stage;
               const int kx = tr ? it.kx0 + 2 * xt : xt;
@@ -782,7 +836,7 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
       mb_wait(su32(&drain), 0);
     }
   } else {
-    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_bias, s_scale, s_shift);
+    conv_epilogue(a, tmem, tfull, tempty, &s_fail, s_mul, s_add);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -1160,6 +1214,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   r.nyt = nyt;
   r.bres = (int)bres;
   const int grid = std::min(a.nitems, sm_count() * per_sm);
+  set_fdivs(a);
   launch_pdl(k_conv_tma_reuse, dim3(grid), dim3(NTHR), smem, s, mA, mB, a, r);
   return true;
 }
@@ -1261,6 +1316,7 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   const long long max_dyn = opt_in_dynamic_smem(once, k_conv_tma);
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
+  set_fdivs(a);
   launch_pdl(k_conv_tma, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
   if (a.ksplit > 1 && !a.cnt) {
     const int M = c.B * c.Ho * c.Wo;
