@@ -341,10 +341,6 @@ constexpr int kStripWarps = 4;       // warps (strips) per block
 struct CPair { float2 a, b; };       // complex values of columns c0 and c0 + 1
 
 __device__ __forceinline__ CPair cp_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
-__device__ __forceinline__ CPair ld_pair(const float2* p) {
-  const float4 q = *reinterpret_cast<const float4*>(p);
-  return {make_float2(q.x, q.y), make_float2(q.z, q.w)};
-}
 __device__ __forceinline__ void st_pair(float2* p, CPair v) {
   *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
@@ -392,73 +388,103 @@ __device__ __forceinline__ float2 op_plain(const Op<float>& op, float2 d, float2
   return k;
 }
 
-// f_c = R (f - K v) (v == nullptr: v = w D^-1 f) for coarse rows [I0, I0 + TI) of one strip.
-template <int BC, int TI>
-__global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float> op, float w,
+// Row staging: each lane copies its own two columns of the rows ahead into a per-warp ring
+// in shared memory with cp.async (zero-filled outside the grid) and reads them back when
+// the walk reaches them, so that kRing - 1 rows per warp are in flight instead of the one
+// a register prefetch allows.  A lane reads only the slots it wrote itself, so the
+// group wait orders everything and no barrier is needed; a slot is refilled one row
+// after it was read.
+constexpr int kRing = 4;
+__device__ __forceinline__ void row_cp16(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void row_cp8(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void row_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void row_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 2) : "memory"); }
+__device__ __forceinline__ CPair cp_of(float4 q) { return {make_float2(q.x, q.y), make_float2(q.z, q.w)}; }
+
+// f_c = R (f - K v) (v == nullptr: v = w D^-1 f) for coarse rows [I0, I0 + TI) of one strip;
+// HAS_V: v is given.
+template <int BC, int TI, bool HAS_V>
+__global__ void __launch_bounds__(32 * kStripWarps, 8) k_resid_restrict_m(Op<float> op, float w,
                                                                      const float2* __restrict__ f,
                                                                      const float2* __restrict__ v,
                                                                      float2* __restrict__ fc, const int* active,
                                                                      int nstrips) {
+  constexpr int R = 2 * TI + 3;                  // fine rows 2 I0 - 2 .. 2 I0 + 2 TI
+  __shared__ float4 s_f[kStripWarps][kRing][32];
+  __shared__ float2 s_k[kStripWarps][kRing][32];
+  __shared__ float4 s_v[HAS_V ? kStripWarps : 1][kRing][32];
   const int rhs = blockIdx.z;
   select_medium(op, rhs);
   if (active && !active[rhs]) return;
-  const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+  const int wi = threadIdx.x >> 5;
+  const int strip = blockIdx.x * kStripWarps + wi;
   if (strip >= nstrips) return;                  // uniform per warp
   const int lane = threadIdx.x & 31;
   const int nx = op.nx, ny = op.ny, nxc = nx >> 1, nyc = ny >> 1;
-  const int c0 = strip * kStripW - 2 + 2 * lane;   // even
+  const int xs = strip * kStripW - 2;              // first column of the strip
+  const int c0 = xs + 2 * lane;                    // even
   const bool colin = c0 >= 0 && c0 < nx;           // both columns in or both out (nx even)
   const size_t N = (size_t)nx * ny;
   const float2* fr = f + (size_t)rhs * N;
-  const float2* vr = v ? v + (size_t)rhs * N : nullptr;
+  const float2* vr = HAS_V ? v + (size_t)rhs * N : nullptr;
   const int I0 = blockIdx.y * TI;
-  // raw row data, fetched one row ahead so that a row's loads are in flight while the
-  // previous row is computed
-  struct Raw { CPair f, v; float2 k; };
-  auto fetch = [&](int yy) {
-    Raw q;
-    q.f = q.v = cp_zero();
-    q.k = make_float2(0.f, 0.f);
-    if (colin && yy >= 0 && yy < ny) {
-      const size_t p = (size_t)yy * nx + c0;
-      q.f = ld_pair(fr + p);
-      q.k = *reinterpret_cast<const float2*>(op.k2 + p);
-      if (vr) q.v = ld_pair(vr + p);
+  const int ys = 2 * I0 - 2;                       // fine row of ring index 0
+  auto issue = [&](int i) {
+    if (i < R) {
+      const int yy = ys + i, sl = i % kRing;
+      const bool ok = colin && yy >= 0 && yy < ny;
+      const size_t p = ok ? (size_t)yy * nx + c0 : 0;
+      row_cp16(&s_f[wi][sl][lane], fr + p, ok);
+      row_cp8(&s_k[wi][sl][lane], op.k2 + p, ok);
+      if (HAS_V) row_cp16(&s_v[HAS_V ? wi : 0][sl][lane], vr + p, ok);
     }
-    return q;
+    row_commit();
   };
-  const int xs = strip * kStripW - 2;
-  auto prep = [&](int yy, const Raw& q, CPair& vv, CPair& dd) {
-    vv = q.v;
+  // ring row i: f, v (or w D^-1 f), the diagonal of both columns and whether the row is
+  // interior (strip_interior)
+  auto take = [&](int i, CPair& ff, CPair& vv, CPair& dd, bool& in) {
+    row_wait();
+    const int yy = ys + i, sl = i % kRing;
+    ff = cp_of(s_f[wi][sl][lane]);
+    const float2 k = s_k[wi][sl][lane];
+    vv = HAS_V ? cp_of(s_v[HAS_V ? wi : 0][sl][lane]) : cp_zero();
     dd = cp_zero();
+    in = strip_interior(op, xs, yy);
     if (colin && yy >= 0 && yy < ny) {
-      if (strip_interior(op, xs, yy)) {
-        dd.a = diag_plain(op, q.k.x);
-        dd.b = diag_plain(op, q.k.y);
+      if (in) {
+        dd.a = diag_plain(op, k.x);
+        dd.b = diag_plain(op, k.y);
       } else {
-        dd.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
-        dd.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+        dd.a = diag_k2<BC, 2>(op, c0, yy, k.x);
+        dd.b = diag_k2<BC, 2>(op, c0 + 1, yy, k.y);
       }
-      if (!vr) {
-        vv.a = jacobi_from_zero(q.f.a, dd.a, w);
-        vv.b = jacobi_from_zero(q.f.b, dd.b, w);
+      if (!HAS_V) {
+        vv.a = jacobi_from_zero(ff.a, dd.a, w);
+        vv.b = jacobi_from_zero(ff.b, dd.b, w);
       }
     }
+    issue(i + kRing - 1);
   };
-  CPair vm = cp_zero(), v0, d0, vp, dp, ra = cp_zero(), rb = cp_zero();
-  Raw q0 = fetch(2 * I0 - 2), qn = fetch(2 * I0 - 1);
-  CPair f0 = q0.f;
-  prep(2 * I0 - 2, q0, v0, d0);
+#pragma unroll
+  for (int i = 0; i < kRing - 1; ++i) issue(i);
+  CPair vm = cp_zero(), v0, d0, f0, vp, dp, fp, ra = cp_zero(), rb = cp_zero();
+  bool in0, inp;
+  take(0, f0, v0, d0, in0);
   float2* fco = fc + (size_t)rhs * nxc * nyc;
-  for (int yy = 2 * I0 - 1; yy <= 2 * I0 + 2 * TI; ++yy) {
-    const Raw q = qn;
-    if (yy < 2 * I0 + 2 * TI) qn = fetch(yy + 1);
-    prep(yy, q, vp, dp);
-    if (yy >= 2 * I0) {
-      const int y = yy - 1;
+#pragma unroll 4
+  for (int i = 1; i < R; ++i) {
+    take(i, fp, vp, dp, inp);
+    const int y = ys + i - 1;                      // the row whose residual is formed
+    if (i >= 2) {
       const float2 lft = shfl_up1(v0.b), rgt = shfl_dn1(v0.a);
       CPair rc = cp_zero();
-      if (strip_interior(op, xs, y)) {
+      if (in0) {
         rc.a = csub(f0.a, op_plain(op, d0.a, v0.a, lft, v0.b, vm.a, vp.a));
         rc.b = csub(f0.b, op_plain(op, d0.b, v0.b, v0.a, rgt, vm.b, vp.b));
       } else if (colin && y >= 0 && y < ny) {
@@ -477,78 +503,104 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_resid_restrict_m(Op<float>
       ra = rb;
       rb = rc;
     }
-    vm = v0; v0 = vp; f0 = q.f; d0 = dp;
+    vm = v0; v0 = vp; f0 = fp; d0 = dp; in0 = inp;
   }
 }
 
 // out = x + w D^-1 (f - K x), x = v + P e_c (v == nullptr: v = w D^-1 f if implicit_v,
-// else 0), for fine rows [Y0, Y0 + TY) of one strip.
-template <int BC, int TY>
-__global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float> op, float w,
+// else 0), for fine rows [Y0, Y0 + TY) of one strip; HAS_V: v is given.
+template <int BC, int TY, bool HAS_V>
+__global__ void __launch_bounds__(32 * kStripWarps, 8) k_prolong_jacobi_m(Op<float> op, float w,
                                                                      const float2* __restrict__ f,
                                                                      const float2* __restrict__ v, int implicit_v,
                                                                      const float2* __restrict__ ec, int nxc, int nyc,
                                                                      float2* __restrict__ out, const int* active,
                                                                      int nstrips) {
+  constexpr int R = TY + 2;                      // fine rows Y0 - 1 .. Y0 + TY
+  __shared__ float4 s_f[kStripWarps][kRing][32];
+  __shared__ float2 s_k[kStripWarps][kRing][32];
+  __shared__ float4 s_v[HAS_V ? kStripWarps : 1][kRing][32];
+  __shared__ float2 s_e[kStripWarps][kRing][33];   // coarse row entered at an even fine row
   const int rhs = blockIdx.z;
   select_medium(op, rhs);
   if (active && !active[rhs]) return;
-  const int strip = blockIdx.x * kStripWarps + (threadIdx.x >> 5);
+  const int wi = threadIdx.x >> 5;
+  const int strip = blockIdx.x * kStripWarps + wi;
   if (strip >= nstrips) return;
   const int lane = threadIdx.x & 31;
   const int nx = op.nx, ny = op.ny;
-  const int c0 = strip * kStripW - 2 + 2 * lane;
+  const int xs = strip * kStripW - 2;
+  const int c0 = xs + 2 * lane;
   const bool colin = c0 >= 0 && c0 < nx;
   const int J = c0 >> 1;                           // coarse column of c0 (c0 + 1 lies between J and J + 1)
   const size_t N = (size_t)nx * ny;
   const float2* fr = f + (size_t)rhs * N;
-  const float2* vr = v ? v + (size_t)rhs * N : nullptr;
+  const float2* vr = HAS_V ? v + (size_t)rhs * N : nullptr;
   const float2* er = ec + (size_t)rhs * nxc * nyc;
-  const int Y0 = blockIdx.y * TY;
-  // coarse row I at columns J and J + 1 (zero outside the coarse grid)
-  auto ec_row = [&](int I, float2& e0, float2& e1) {
+  const int Y0 = blockIdx.y * TY, ys = Y0 - 1;
+  // coarse row I at columns J (every lane) and J + 1 of lane 31, zero outside the coarse grid
+  auto ec_cp = [&](int I, float2* dst) {
     const bool rin = I >= 0 && I < nyc;
-    e0 = (rin && J >= 0 && J < nxc) ? er[(size_t)I * nxc + J] : make_float2(0.f, 0.f);
-    e1 = shfl_dn1(e0);
-    if (lane == 31) e1 = (rin && J + 1 < nxc) ? er[(size_t)I * nxc + J + 1] : make_float2(0.f, 0.f);
+    const bool ok0 = rin && J >= 0 && J < nxc, ok1 = rin && J + 1 < nxc;
+    row_cp8(dst + lane, er + (ok0 ? (size_t)I * nxc + J : 0), ok0);
+    if (lane == 31) row_cp8(dst + 32, er + (ok1 ? (size_t)I * nxc + J + 1 : 0), ok1);
+  };
+  auto issue = [&](int i) {
+    if (i < R) {
+      const int yy = ys + i, sl = i % kRing;
+      const bool ok = colin && yy >= 0 && yy < ny;
+      const size_t p = ok ? (size_t)yy * nx + c0 : 0;
+      row_cp8(&s_k[wi][sl][lane], op.k2 + p, ok);
+      const bool fok = ok && (implicit_v || (yy >= Y0 && yy < Y0 + TY));
+      row_cp16(&s_f[wi][sl][lane], fr + (fok ? p : 0), fok);
+      if (HAS_V) row_cp16(&s_v[HAS_V ? wi : 0][sl][lane], vr + p, ok);
+      if (i > 0 && !(yy & 1)) ec_cp((yy >> 1) + 1, &s_e[wi][sl][0]);
+    }
+    row_commit();
   };
   float2 elo0, elo1, ehi0, ehi1;
-  ec_row((Y0 - 1) >> 1, elo0, elo1);
-  ec_row(((Y0 - 1) >> 1) + 1, ehi0, ehi1);
-  struct Raw { CPair f, v; float2 k; };
-  auto fetch = [&](int yy) {
-    Raw q;
-    q.f = q.v = cp_zero();
-    q.k = make_float2(0.f, 0.f);
-    if (colin && yy >= 0 && yy < ny) {
-      const size_t p = (size_t)yy * nx + c0;
-      q.k = *reinterpret_cast<const float2*>(op.k2 + p);
-      if (implicit_v || (yy >= Y0 && yy < Y0 + TY)) q.f = ld_pair(fr + p);
-      if (vr) q.v = ld_pair(vr + p);
-    }
-    return q;
-  };
+  {
+    // the two coarse rows around the first fine row, read directly
+    auto ec_row = [&](int I, float2& e0, float2& e1) {
+      const bool rin = I >= 0 && I < nyc;
+      e0 = (rin && J >= 0 && J < nxc) ? er[(size_t)I * nxc + J] : make_float2(0.f, 0.f);
+      e1 = shfl_dn1(e0);
+      if (lane == 31) e1 = (rin && J + 1 < nxc) ? er[(size_t)I * nxc + J + 1] : make_float2(0.f, 0.f);
+    };
+    ec_row(ys >> 1, elo0, elo1);
+    ec_row((ys >> 1) + 1, ehi0, ehi1);
+  }
+#pragma unroll
+  for (int i = 0; i < kRing - 1; ++i) issue(i);
   CPair xm = cp_zero(), x0 = cp_zero(), f0 = cp_zero(), d0 = cp_zero();
+  bool in0 = false;
   float2* o = out + (size_t)rhs * N;
-  Raw qn = fetch(Y0 - 1);
-  for (int yy = Y0 - 1; yy <= Y0 + TY; ++yy) {
-    const Raw q = qn;
-    if (yy < Y0 + TY) qn = fetch(yy + 1);
-    if (yy > Y0 - 1 && !(yy & 1)) {               // entering coarse row yy / 2
+#pragma unroll 4
+  for (int i = 0; i < R; ++i) {
+    row_wait();
+    const int yy = ys + i, sl = i % kRing;
+    const CPair fq = cp_of(s_f[wi][sl][lane]);
+    const float2 kq = s_k[wi][sl][lane];
+    const CPair vq = HAS_V ? cp_of(s_v[HAS_V ? wi : 0][sl][lane]) : cp_zero();
+    if (i > 0 && !(yy & 1)) {                     // entering coarse row yy / 2
       elo0 = ehi0; elo1 = ehi1;
-      ec_row((yy >> 1) + 1, ehi0, ehi1);
+      ehi0 = s_e[wi][sl][lane];
+      ehi1 = shfl_dn1(ehi0);
+      if (lane == 31) ehi1 = s_e[wi][sl][32];
     }
+    issue(i + kRing - 1);
     CPair xp = cp_zero(), dp = cp_zero();
+    const bool inp = strip_interior(op, xs, yy);
     if (colin && yy >= 0 && yy < ny) {
-      if (strip_interior(op, c0 - 2 * lane, yy)) {
-        dp.a = diag_plain(op, q.k.x);
-        dp.b = diag_plain(op, q.k.y);
+      if (inp) {
+        dp.a = diag_plain(op, kq.x);
+        dp.b = diag_plain(op, kq.y);
       } else {
-        dp.a = diag_k2<BC, 2>(op, c0, yy, q.k.x);
-        dp.b = diag_k2<BC, 2>(op, c0 + 1, yy, q.k.y);
+        dp.a = diag_k2<BC, 2>(op, c0, yy, kq.x);
+        dp.b = diag_k2<BC, 2>(op, c0 + 1, yy, kq.y);
       }
-      CPair base = q.v;
-      if (!vr && implicit_v) { base.a = jacobi_from_zero(q.f.a, dp.a, w); base.b = jacobi_from_zero(q.f.b, dp.b, w); }
+      CPair base = vq;
+      if (!HAS_V && implicit_v) { base.a = jacobi_from_zero(fq.a, dp.a, w); base.b = jacobi_from_zero(fq.b, dp.b, w); }
       // P e_c: even rows take coarse row yy / 2, odd rows the mean of two coarse rows;
       // column c0 = 2J takes coarse column J, column c0 + 1 the mean of J and J + 1
       float2 e0 = elo0, e1 = elo1;
@@ -556,11 +608,11 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float>
       xp.a = cadd(base.a, e0);
       xp.b = cadd(base.b, cscale(cadd(e0, e1), 0.5f));
     }
-    if (yy >= Y0 + 1) {
+    if (i >= 2) {
       const int y = yy - 1;
       const float2 lft = shfl_up1(x0.b), rgt = shfl_dn1(x0.a);
       if (colin && lane >= 1 && lane <= 30 && y < ny) {
-        const bool in = strip_interior(op, c0 - 2 * lane, y);
+        const bool in = in0;
         const float2 ka = in ? op_plain(op, d0.a, x0.a, lft, x0.b, xm.a, xp.a)
                              : op_at<BC>(op, c0, y, d0.a, x0.a, lft, x0.b, xm.a, xp.a);
         const float2 kb = in ? op_plain(op, d0.b, x0.b, x0.a, rgt, xm.b, xp.b)
@@ -571,7 +623,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) k_prolong_jacobi_m(Op<float>
         st_pair(o + (size_t)y * nx + c0, r);
       }
     }
-    xm = x0; x0 = xp; f0 = q.f; d0 = dp;
+    xm = x0; x0 = xp; f0 = fq; d0 = dp; in0 = inp;
   }
 }
 
@@ -684,9 +736,12 @@ void launch_resid_restrict(const Op<T>& fine, T w, const void* f, const void* v,
       with_seg(ti, [&](auto tv) {
         constexpr int TI = decltype(tv)::value;
         const dim3 grid((nstrips + kStripWarps - 1) / kStripWarps, (fine.ny / 2 + TI - 1) / TI, nrhs);
-        k_resid_restrict_m<BCk, TI><<<grid, 32 * kStripWarps, 0, s>>>(op, (float)w, (const float2*)f,
-                                                                      (const float2*)v, (float2*)fc, active,
-                                                                      nstrips);
+        if (v)
+          k_resid_restrict_m<BCk, TI, true><<<grid, 32 * kStripWarps, 0, s>>>(
+              op, (float)w, (const float2*)f, (const float2*)v, (float2*)fc, active, nstrips);
+        else
+          k_resid_restrict_m<BCk, TI, false><<<grid, 32 * kStripWarps, 0, s>>>(
+              op, (float)w, (const float2*)f, nullptr, (float2*)fc, active, nstrips);
       });
     });
     return;
@@ -711,9 +766,14 @@ void launch_prolong_jacobi(const Op<T>& fine, T w, const void* f, const void* v,
       with_seg(ty, [&](auto tv) {
         constexpr int TY = decltype(tv)::value;
         const dim3 grid((nstrips + kStripWarps - 1) / kStripWarps, (fine.ny + TY - 1) / TY, nrhs);
-        k_prolong_jacobi_m<BCk, TY><<<grid, 32 * kStripWarps, 0, s>>>(
-            op, (float)w, (const float2*)f, (const float2*)v, implicit_v ? 1 : 0, (const float2*)ec, nxc, nyc,
-            (float2*)out, active, nstrips);
+        if (v)
+          k_prolong_jacobi_m<BCk, TY, true><<<grid, 32 * kStripWarps, 0, s>>>(
+              op, (float)w, (const float2*)f, (const float2*)v, 0, (const float2*)ec, nxc, nyc, (float2*)out,
+              active, nstrips);
+        else
+          k_prolong_jacobi_m<BCk, TY, false><<<grid, 32 * kStripWarps, 0, s>>>(
+              op, (float)w, (const float2*)f, nullptr, implicit_v ? 1 : 0, (const float2*)ec, nxc, nyc,
+              (float2*)out, active, nstrips);
       });
     });
     return;
