@@ -442,7 +442,7 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
     if (epi_any(failed(fail), grp, alt)) break;
     const Item it = decode(a, w);
     const int acc = li & (a.nacc - 1);
-    const bool ok = mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> a.lg_nacc) & 1u);
+    const bool ok = mb_wait(su32(&tfull[acc]), (uint32_t)(li >> a.lg_nacc) & 1u);
     if (epi_any(!ok, grp, alt)) { atomicExch(s_fail, 1); break; }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const int b = it.b0 + bb, qy = it.y0 + by, qx = it.x0 + bx;
@@ -1348,6 +1348,7 @@ struct WgArgs {
   int k, pad, kind;           // kind 0: 5x5 stride 2, 1: stride 1, 2: transposed stride 2
   int B, tx, ty, bx, by;      // K grid: tx * ty blocks of bx x by pixels per image
   int cin, cout, mblk, NT;    // 128-channel blocks of cin; N = Cout padded to 64
+  int cin_tot;                // input channels of the whole layer (rows of one tap in gW)
   int nchunks, nitems, nst, colsz;
   uint32_t lbo, sbo;          // MN-major descriptor strides (bytes)
   int vec;                    // gW rows 16-byte aligned (float4 atomics)
@@ -1494,7 +1495,7 @@ __global__ void __launch_bounds__(WG_THR, 1) k_wgrad_tma(const __grid_constant__
       if (!mb_wait_sleep(su32(&tfull[acc]), (uint32_t)(li >> 1) & 1u)) { atomicExch(&s_fail, 1); break; }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int ci = it.mb * 128 + warp * 32 + lane;
-      float* row = a.gW + ((size_t)it.tap * a.cin + ci) * a.cout;
+      float* row = a.gW + ((size_t)it.tap * a.cin_tot + ci) * a.cout;
       const bool vec = a.vec != 0;
       for (int c0 = 0; c0 < N && c0 < a.cout; c0 += 16) {
         uint32_t v[16];
@@ -1542,7 +1543,8 @@ void conv_wgrad_tma_set_desc_order(int order) { g_wg_desc_order = order; }
 
 // dW += weight gradient of the forward convolution c (single BF16 source, no on-load
 // activation) from g = dL/dy (BF16 [pixels][Cout], ld ldg).  False: not eligible.
-bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s) {
+bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s,
+                    int cin_total, bool launch) {
   if (c.in1 || c.in_act || c.in_f32 || c.Cout > 256 || c.ld0 % 8 || ldg % 8) return false;
   if (c.k != 3 && c.k != 5) return false;
   if (!get_encoder()) return false;
@@ -1558,6 +1560,7 @@ bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* g
   a.by = 64 / a.bx;
   a.tx = Wk / a.bx; a.ty = Hk / a.by;
   a.cin = c.c0; a.cout = c.Cout;
+  a.cin_tot = cin_total > 0 ? cin_total : c.c0;
   a.mblk = (c.c0 + 127) / 128;
   a.NT = 64 * ((c.Cout + 63) / 64);
   a.colsz = a.NT <= 64 ? 64 : (a.NT <= 128 ? 128 : 256);
@@ -1602,6 +1605,7 @@ bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* g
         }))
       return false;
   }
+  if (!launch) return true;
   const int grid = std::min(a.nitems, slots);
   k_wgrad_tma<<<grid, WG_THR, smem, s>>>(mX, mG, a);
   return true;

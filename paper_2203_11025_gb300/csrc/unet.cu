@@ -86,6 +86,8 @@ struct unet_ctx {
   size_t nws = 0;
   __nv_bfloat16* WDb = nullptr;                    // space-to-depth copy of a 4-channel input layer
   __nv_bfloat16* gbf = nullptr;                    // BF16 copy of a layer's output gradient
+  float* gsum = nullptr;                           // batch sum of a layer's output gradient (one image)
+  __nv_bfloat16* gsum_bf = nullptr;                // its BF16 copy
   bool use_tma = true;
   int* d_err = nullptr;                            // failure record of the tensor-core kernel
   bool use_tc = true;
@@ -280,6 +282,17 @@ void carve(unet_ctx* n, DevArena& a, int B, int ny, int nx) {
     n->splitbuf = a.take<float>((size_t)n->splitcnt_n);
     n->splitcnt = a.take<int>(kSplitTickets);   // zeroed with the workspace; each fix-up puts its ticket back
     n->gbf = a.take<__nv_bfloat16>(std::max(smax, M(0) * (size_t)gbf_ld(c.out_ch)));
+    n->gsum = nullptr;
+    n->gsum_bf = nullptr;
+    bool ctx = false;
+    for (int l = 0; l <= L; ++l) ctx = ctx || c.context[l] != 0;
+    if (ctx) {
+      // per-image output gradients (broadcast context sources: their weight gradient is
+      // the correlation of the one feature image with the batch sum of the gradient)
+      const size_t per = std::max(smax / (size_t)B, (M(0) / (size_t)B) * (size_t)gbf_ld(c.out_ch));
+      n->gsum = a.take<float>(per);
+      n->gsum_bf = a.take<__nv_bfloat16>(per);
+    }
   }
   n->part = a.take<float>((size_t)n->nblk * 2 * 512 + 1024);
   n->bncoef = a.take<float>(5 * 512);
@@ -453,15 +466,49 @@ void run_dgrad(unet_ctx* n, const ConvL& cl, const float* g, int ldg, int Hg, in
 // Weight gradient gW += dW of the forward convolution fa from g = dL/dy (FP32, ld ldg)
 // and, when dx is set, the data gradient into dx: both from one BF16 copy of g on the
 // tensor-core path.  `act_src`: the materialised eLU copy of fa's input, if any.
+// Weight gradient of a two-source convolution (input channels [0, c0) from in0, [c0, c0 +
+// c1) from the context source in1) on the tensor cores: one GEMM per source into its rows
+// of gW.  A broadcast context source (one image for the batch) correlates with the batch
+// sum of g.  eLU'd inputs need their materialised copies (act0, act1).  Launches nothing
+// and returns false unless both parts qualify.
+bool wgrad_two_sources(unet_ctx* n, const ConvL& cl, const ConvArgs& fa, const float* g, int ldg, float* gW, int Hg,
+                       int Wg, const __nv_bfloat16* act0, const __nv_bfloat16* act1, cudaStream_t s) {
+  if (fa.in_act && (!act0 || !act1)) return false;
+  if (fa.bcast1 && (!n->gsum || !n->gsum_bf)) return false;
+  const int cin = fa.c0 + fa.c1, ldgb = gbf_ld(cl.cout);
+  ConvArgs t0 = fa;
+  t0.in1 = nullptr; t0.c1 = 0; t0.bcast1 = 0;
+  if (fa.in_act) { t0.in0 = act0; t0.ld0 = fa.c0; t0.in_act = 0; }
+  ConvArgs t1 = fa;
+  t1.in0 = fa.in1; t1.c0 = fa.c1; t1.ld0 = fa.ld1; t1.in1 = nullptr; t1.c1 = 0; t1.bcast1 = 0;
+  if (fa.in_act) { t1.in0 = act1; t1.ld0 = fa.c1; t1.in_act = 0; }
+  const __nv_bfloat16* g1 = n->gbf;
+  if (fa.bcast1) { t1.B = 1; g1 = n->gsum_bf; }
+  if (!conv_wgrad_tma(t0, n->gbf, ldgb, gW, n->d_err, s, cin, false) ||
+      !conv_wgrad_tma(t1, g1, ldgb, gW + (size_t)fa.c0 * cl.cout, n->d_err, s, cin, false))
+    return false;
+  if (fa.bcast1) {
+    const size_t P = (size_t)Hg * Wg;
+    batch_sum(g, ldg, n->B, P, cl.cout, n->gsum, cl.cout, false, s);
+    to_bf16_slice(n->gsum, cl.cout, n->gsum_bf, ldgb, cl.cout, (int)P, s);
+  }
+  conv_wgrad_tma(t0, n->gbf, ldgb, gW, n->d_err, s, cin, true);
+  conv_wgrad_tma(t1, g1, ldgb, gW + (size_t)fa.c0 * cl.cout, n->d_err, s, cin, true);
+  return true;
+}
+
 void backprop_conv(unet_ctx* n, const ConvL& cl, ConvArgs fa, const float* g, int ldg, float* gW, int Hg, int Wg,
-                   float* dx, int lddx, cudaStream_t s, const __nv_bfloat16* act_src = nullptr) {
+                   float* dx, int lddx, cudaStream_t s, const __nv_bfloat16* act_src = nullptr,
+                   const __nv_bfloat16* act_ctx = nullptr) {
   bool have = false;
   if (n->use_tc && n->use_tma) {
     to_bf16_slice(g, ldg, n->gbf, gbf_ld(cl.cout), cl.cout, n->B * Hg * Wg, s);
     have = true;
     ConvArgs t = fa;
     if (t.in_act && act_src && !t.in1) { t.in0 = act_src; t.ld0 = t.c0; t.in_act = 0; }
-    if (!conv_wgrad_tma(t, n->gbf, gbf_ld(cl.cout), gW, n->d_err, s)) conv_wgrad(fa, g, ldg, gW, s);
+    const bool done = fa.in1 ? wgrad_two_sources(n, cl, fa, g, ldg, gW, Hg, Wg, act_src, act_ctx, s)
+                             : conv_wgrad_tma(t, n->gbf, gbf_ld(cl.cout), gW, n->d_err, s);
+    if (!done) conv_wgrad(fa, g, ldg, gW, s);
   } else {
     conv_wgrad(fa, g, ldg, gW, s);
   }
@@ -672,7 +719,7 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     ConvArgs fa = conv_args(n, cl, u, feat_of(n, 1), true, H, W, nullptr, 0);
     const int cu = u.c, ldU = cu + c.context[1];
     backprop_conv(n, cl, fa, gout, c.out_ch, n->G + cl.woff, n->ny, n->nx, n->gU[1], ldU, s,
-                  n->uact_ok[1] ? n->uact[1] : nullptr);
+                  n->uact_ok[1] ? n->uact[1] : nullptr, n->uact_ok[1] ? n->fact[1] : nullptr);
     elu_backward_inplace(n->gU[1], ldU, (const __nv_bfloat16*)u.p, u.ld, cu, M(1), 0, s);
     if (c.context[1]) {
       Src f = feat_of(n, 1);
@@ -697,7 +744,7 @@ int backward_impl(unet_ctx* n, const float* gout, float* const* g_own, float* gx
     int Hg, Wg;
     hw(l - 1, Hg, Wg);
     backprop_conv(n, cl, fa, n->gzup[l], cz, n->G + cl.woff, Hg, Wg, n->gU[l], ldU, s,
-                  n->uact_ok[l] ? n->uact[l] : nullptr);
+                  n->uact_ok[l] ? n->uact[l] : nullptr, n->uact_ok[l] ? n->fact[l] : nullptr);
     elu_backward_inplace(n->gU[l], ldU, (const __nv_bfloat16*)u.p, u.ld, u.c, M(l), 0, s);
     if (c.context[l]) {
       Src f = feat_of(n, l);

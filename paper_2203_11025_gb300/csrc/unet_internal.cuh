@@ -70,7 +70,12 @@ size_t conv_tma_weight_sub_elems(int c0, int c1, int cout);
 void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1, int cout, cudaStream_t s);
 // weight gradient on the tensor cores (TMA path): gW += dW of the forward convolution a
 // (one BF16 source, no on-load activation) from g = dL/dy, BF16 [pixels][Cout] with ld ldg
-bool conv_wgrad_tma(const ConvArgs& a, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s);
+// Weight gradient of source 0 of a (a.in1 must be null) added into gW on the tensor cores;
+// cin_total: input channels of the whole layer (rows of one tap in gW; 0: a.c0), so that a
+// second source's gradient can start at gW + c0 * Cout.  launch = false only checks that the
+// layer qualifies.  Returns false (nothing launched) when it does not.
+bool conv_wgrad_tma(const ConvArgs& a, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s,
+                    int cin_total = 0, bool launch = true);
 void conv_wgrad_tma_set_desc_order(int order);
 void conv_tma_weights_adjoint(const float* P, __nv_bfloat16* WPA, int k, int cin, int cout, bool flip, cudaStream_t s);
 const char* conv_tma_last_reject();      // why the last conv_forward_tma call declined ("" if it launched)   // > 1: the TMA path splits K (FP32 atomics, no fused epilogue)
