@@ -139,6 +139,57 @@ __host__ __device__ constexpr uint32_t idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+// One tcgen05.mma (M = 128, kind::f16, D in TMEM at d) of K-step descriptors da, db;
+// accumulate: add into D (else overwrite it).
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t da, uint64_t db, uint32_t id, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(da), "l"(db), "r"(id), "r"(accumulate)
+      : "memory");
+}
+
+// The MMAs of one stage as straight-line code (a single thread issues an MMA in far fewer
+// cycles when no branch separates it from the previous one): NJ taps x NK4 K-steps of 16,
+// tap j reading A at a0 + j * astep and B at w0 + j * wstep (byte offsets may be negative
+// as unsigned wrap-around).  acc0: the first MMA accumulates (else it starts D).
+template <int NJ, int NK4>
+__device__ __forceinline__ void mma_taps(uint32_t d, uint32_t a0, uint32_t astep, uint32_t w0, uint32_t wstep, int tk,
+                                         uint32_t id, uint32_t acc0) {
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const uint64_t da = desc_k(a0 + (uint32_t)j * astep, tk), db = desc_k(w0 + (uint32_t)j * wstep, tk);
+#pragma unroll
+    for (int k4 = 0; k4 < NK4; ++k4)
+      mma_f16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), id, (j == 0 && k4 == 0) ? acc0 : 1u);
+  }
+}
+template <int NJ>
+__device__ __forceinline__ void mma_taps_k(int nk4, uint32_t d, uint32_t a0, uint32_t astep, uint32_t w0,
+                                           uint32_t wstep, int tk, uint32_t id, uint32_t acc0) {
+  switch (nk4) {
+    case 1: mma_taps<NJ, 1>(d, a0, astep, w0, wstep, tk, id, acc0); break;
+    case 2: mma_taps<NJ, 2>(d, a0, astep, w0, wstep, tk, id, acc0); break;
+    case 3: mma_taps<NJ, 3>(d, a0, astep, w0, wstep, tk, id, acc0); break;
+    default: mma_taps<NJ, 4>(d, a0, astep, w0, wstep, tk, id, acc0); break;
+  }
+}
+__device__ __forceinline__ void mma_stage(int nj, int nk4, uint32_t d, uint32_t a0, uint32_t astep, uint32_t w0,
+                                          uint32_t wstep, int tk, uint32_t id, uint32_t acc0) {
+  switch (nj) {
+    case 1: mma_taps_k<1>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
+    case 2: mma_taps_k<2>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
+    case 3: mma_taps_k<3>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
+    default:   // more than three taps per box: three at a time
+      for (int j = 0; j < nj; j += 3) {
+        const uint32_t aj = a0 + (uint32_t)j * astep, wj = w0 + (uint32_t)j * wstep, cj = j == 0 ? acc0 : 1u;
+        if (nj - j >= 3) mma_taps_k<3>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
+        else if (nj - j == 2) mma_taps_k<2>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
+        else mma_taps_k<1>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
+      }
+  }
+}
+
 // Division by a divisor fixed at launch: n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31,
 // with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1 (the round-up multiplier of
 // Granlund and Montgomery, "Division by invariant integers using multiplication", 1994).
@@ -637,20 +688,10 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
           if (!mb_wait(su32(&full[s]), use & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sA = base + (uint32_t)s * stage;
-          const uint64_t da = desc_k(sA, TK), db = desc_k(sA + a_bytes, TK);
           // K-steps of 16 that hold real channels (the rest of a chunk is zero fill)
           const int cval = kch < a.nch0 ? min(TK, a.c0 - kch * TK) : min(TK, a.c1 - (kch - a.nch0) * TK);
           const int nk4 = (cval + 15) / 16;
-#pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            if (k4 >= nk4) break;
-            const uint32_t accum = (kb > 0 || k4 > 0) ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                "l"(da + (uint64_t)(2 * k4)), "l"(db + (uint64_t)(2 * k4)), "r"(id), "r"(accum)
-                : "memory");
-          }
+          mma_taps_k<1>(nk4, d, sA, 0u, sA + a_bytes, 0u, TK, id, kb > 0 ? 1u : 0u);
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               su32(&empty[s]))
               : "memory");
@@ -803,25 +844,17 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
               const uint32_t sA = base + (uint32_t)s * stage;
               const int kx = tr ? it.kx0 + 2 * xt : xt;
               const int nk4 = (min(TK, a.c0 - ch * TK) + 15) / 16;   // K-steps with real channels
-              // y-taps served by this box: j = 0 .. nj-1, box row j * BX (transposed: reversed)
+              // y-taps served by this box: j = 0 .. nj-1 (ky = ky0 + dky j), box row j * BX
+              // (transposed: rows reversed)
               const int nj = tr ? nty : (a.stride == 1 ? a.k : (a.k - cls + 1) / 2);
-              for (int j = 0; j < nj; ++j) {
-                const int ky = tr ? it.ky0 + 2 * j : (a.stride == 1 ? j : cls + 2 * j);
-                const int row = tr ? (nty - 1 - j) : j;
-                const uint64_t da = desc_k(sA + (uint32_t)(row * a.BX * 2 * TK), TK);
-                const uint64_t db = desc_k(wbase + (uint32_t)((ky * a.k + kx) * nch + ch) * wtile, TK);
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                  if (k4 >= nk4) break;
-                  const uint32_t accum = first ? 0u : 1u;
-                  first = false;
-                  asm volatile(
-                      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                      "l"(da + (uint64_t)(2 * k4)), "l"(db + (uint64_t)(2 * k4)), "r"(id), "r"(accum)
-                      : "memory");
-                }
-              }
+              const int ky0 = tr ? it.ky0 : (a.stride == 1 ? 0 : cls), dky = a.stride == 1 && !tr ? 1 : 2;
+              const uint32_t rowb = (uint32_t)(a.BX * 2 * TK);
+              const uint32_t a0 = tr ? sA + (uint32_t)(nty - 1) * rowb : sA;
+              const uint32_t astep = tr ? 0u - rowb : rowb;
+              const uint32_t w0 = wbase + (uint32_t)((ky0 * a.k + kx) * nch + ch) * wtile;
+              const uint32_t wstep = (uint32_t)(dky * a.k * nch) * wtile;
+              mma_stage(nj, nk4, d, a0, astep, w0, wstep, TK, id, first ? 0u : 1u);
+              first = false;
               asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                su32(&empty[s]))
                            : "memory");
