@@ -61,6 +61,13 @@ TRAIN_PAIRS_PER_MEDIUM = 64
 RETRAIN_PAIRS = 300
 RETRAIN_EPOCHS = 20
 RETRAIN_LR = 5e-4
+# encoder-solver case (Sec. 3.3): 512^2, 16 point sources + 16 complex Gaussian right-hand
+# sides; the pair trained jointly on ES_PAIRS pairs of the case's medium
+ES_GRID = 512
+ES_POINTS = 16
+ES_GAUSS = 16
+ES_PAIRS = 512
+ES_EPOCHS = 40
 # M_V iterations of the GPU solve of the default problem (2048^2, 16 point sources, medium
 # seed 1000, FP32 Krylov vectors): the reference arm scales its per-iteration sample by it
 M_V_ITERS_DEFAULT = 4664
@@ -264,6 +271,62 @@ def general_case(lib, dev, rank):
     out["medium"] = "the 256x256x8 case's medium (not among the 16 training media)"
     hz.close()
     gnet.close()
+    return out
+
+
+def encoder_solver_case(lib, dev, rank):
+    """The encoder-solver pair of Sec. 3.3 (512^2 unknowns, 32 right-hand sides): the encoder
+    U-Net maps the medium to context features once per medium, the solver U-Net (with those
+    features at every level) is the M_VU network.  Both are trained jointly (Eq. 3.7, Adam) on
+    Eq. 3.8-3.9 pairs of the case's medium; FGMRES with M_VU against M_V, iterations and solve
+    times."""
+    import numpy as np
+    import torch
+    from paper_2203_11025_gb300 import synth
+    from paper_2203_11025_gb300 import train as T
+    n = ES_GRID
+    k2 = synth.grf_kappa2(n, n, synth.medium_seed(rank))
+    pos = synth.source_positions(n, n, ES_POINTS, synth.rhs_seed(rank), 16)
+    b = np.concatenate([synth.point_sources(n, n, pos, 1.0 / n),
+                        synth.gaussian_rhs(n, n, ES_GAUSS, 2003 + rank)]).astype(np.complex128)
+    hz = lib.Helmholtz(torch.from_numpy(k2).to(dev))
+    bd = torch.from_numpy(b).to(dev)
+    t0 = time.perf_counter()
+    pairs = hz.gen_pairs(ES_PAIRS, 4242 + rank, 10)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    enc = lib.UNet(kind=lib.UNET_ENCODER, seed=1 + rank)
+    sol = lib.UNet(kind=lib.UNET_SOLVER, seed=2 + rank)
+    sol.attach_encoder(enc)
+    t0 = time.perf_counter()
+    hist = T.train(hz, sol, pairs=pairs, epochs=ES_EPOCHS, batch=TRAIN_BATCH, lr=TRAIN_LR, seed=11 + rank)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del pairs
+    held = hz.gen_pairs(16, 9100 + rank, 10)       # pairs the training never saw
+    rel = T.relative_error(hz, sol, held, 16)
+    del held
+    sol.encode(hz)            # context features of this medium, once
+    out = {"grid": n, "rhs": {"point_sources": ES_POINTS, "complex_gaussian": ES_GAUSS},
+           "training": {"pairs": ES_PAIRS, "epochs": ES_EPOCHS, "lr": TRAIN_LR, "batch": TRAIN_BATCH,
+                        "gen_s": round(t_gen, 2), "train_s": round(t_train, 2), "loss_first": round(hist[0], 1),
+                        "loss_last": round(hist[-1], 1), "relative_error_heldout": round(rel, 3)}}
+    for name, pc, nt in (("M_V", lib.HELM_PREC_V, None), ("M_VU", lib.HELM_PREC_VU, sol)):
+        hz.fgmres(bd, precond=pc, net=nt, tol=TOL, maxit=20000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = hz.fgmres(bd, precond=pc, net=nt, tol=TOL, maxit=20000)
+        torch.cuda.synchronize()
+        out.setdefault("solve_s", {})[name] = time.perf_counter() - t0
+        out.setdefault("fgmres_iters_max", {})[name] = info["iters_max"]
+        its = info["iters"]
+        out.setdefault("fgmres_iters_mean", {})[name] = {
+            "point_sources": float(np.mean(its[:ES_POINTS])), "complex_gaussian": float(np.mean(its[ES_POINTS:]))}
+        assert info["status"] == 0 and info["relres_max"] <= TOL, (name, info)
+    out["precond"] = "encoder-solver M_VU (solver U-Net with the encoder's context features, then the V-cycle)"
+    hz.close()
+    sol.close()
+    enc.close()
     return out
 
 
@@ -552,6 +615,7 @@ def run_ours(args):
             c2.net.close()
         extras["general_network_unseen_256x256x8"] = general_case(lib, dev, rank)
         extras["batched_uneven_64"] = c4_case(lib, dev, rank, base_path)
+        extras["encoder_solver_512x512x32"] = encoder_solver_case(lib, dev, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

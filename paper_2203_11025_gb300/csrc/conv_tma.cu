@@ -174,20 +174,56 @@ __device__ __forceinline__ void mma_taps_k(int nk4, uint32_t d, uint32_t a0, uin
     default: mma_taps<NJ, 4>(d, a0, astep, w0, wstep, tk, id, acc0); break;
   }
 }
-__device__ __forceinline__ void mma_stage(int nj, int nk4, uint32_t d, uint32_t a0, uint32_t astep, uint32_t w0,
-                                          uint32_t wstep, int tk, uint32_t id, uint32_t acc0) {
-  switch (nj) {
-    case 1: mma_taps_k<1>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
-    case 2: mma_taps_k<2>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
-    case 3: mma_taps_k<3>(nk4, d, a0, astep, w0, wstep, tk, id, acc0); break;
-    default:   // more than three taps per box: three at a time
-      for (int j = 0; j < nj; j += 3) {
-        const uint32_t aj = a0 + (uint32_t)j * astep, wj = w0 + (uint32_t)j * wstep, cj = j == 0 ? acc0 : 1u;
-        if (nj - j >= 3) mma_taps_k<3>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
-        else if (nj - j == 2) mma_taps_k<2>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
-        else mma_taps_k<1>(nk4, d, aj, astep, wj, wstep, tk, id, cj);
-      }
+// Low and high words of desc_k: the high word depends only on tk, the low word holds the
+// shared-memory address (16-byte units), so taps and K-steps step the low word alone.
+__device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return ((saddr >> 4) & 0x3FFFu) | (1u << 16); }
+__device__ __forceinline__ uint32_t desc_hi(int tk) {
+  const uint32_t lay = tk == 64 ? 2u : (tk == 32 ? 4u : 6u);
+  return ((8u * 2u * (uint32_t)tk) >> 4) | (1u << 14) | (lay << 29);
+}
+__device__ __forceinline__ void mma_lo(uint32_t d, uint32_t alo, uint32_t blo, uint32_t hi, uint32_t id,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %5, 0;\n mov.b64 da, {%1, %3};\n"
+      " mov.b64 db, {%2, %3};\n tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(d),
+      "r"(alo), "r"(blo), "r"(hi), "r"(id), "r"(accumulate)
+      : "memory");
+}
+// NX boxes x NJ taps x NK4 K-steps from low descriptor words: box x, tap j, step k reads A at
+// alo + x * xs + j * as + 2 k and B at blo + x * wxs + j * ws + 2 k (steps in 16-byte units,
+// two's complement for negative ones).
+template <int NX, int NJ, int NK4>
+__device__ __forceinline__ void mma_lo_boxes(uint32_t d, uint32_t alo, uint32_t as, uint32_t xs, uint32_t blo,
+                                             uint32_t ws, uint32_t wxs, uint32_t hi, uint32_t id, uint32_t acc0) {
+#pragma unroll
+  for (int x = 0; x < NX; ++x)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int k = 0; k < NK4; ++k)
+        mma_lo(d, alo + (uint32_t)x * xs + (uint32_t)j * as + 2u * k,
+               blo + (uint32_t)x * wxs + (uint32_t)j * ws + 2u * k, hi, id, (x == 0 && j == 0 && k == 0) ? acc0 : 1u);
+}
+// Shape code of a stage: nx | nj << 4 | nk4 << 8.  Instantiated shapes issue as one block.
+__device__ __forceinline__ bool mma_lo_shape(uint32_t shape, uint32_t d, uint32_t alo, uint32_t as, uint32_t xs,
+                                             uint32_t blo, uint32_t ws, uint32_t wxs, uint32_t hi, uint32_t id,
+                                             uint32_t acc0) {
+#define HELM_SHAPE(NX, NJ, NK)                                            \
+  case (NX) | ((NJ) << 4) | ((NK) << 8):                                  \
+    mma_lo_boxes<NX, NJ, NK>(d, alo, as, xs, blo, ws, wxs, hi, id, acc0); \
+    return true;
+  switch (shape) {
+    HELM_SHAPE(3, 3, 1) HELM_SHAPE(3, 3, 2) HELM_SHAPE(3, 3, 4)   // 3x3 stride 1
+    HELM_SHAPE(5, 3, 1) HELM_SHAPE(5, 3, 2) HELM_SHAPE(5, 3, 4)   // 5x5 stride 2, even rows
+    HELM_SHAPE(5, 2, 1) HELM_SHAPE(5, 2, 2) HELM_SHAPE(5, 2, 4)   // 5x5 stride 2, odd rows
+    HELM_SHAPE(3, 2, 1) HELM_SHAPE(3, 2, 2) HELM_SHAPE(3, 2, 4)   // transposed phases
+    HELM_SHAPE(2, 3, 1) HELM_SHAPE(2, 3, 2) HELM_SHAPE(2, 3, 4)
+    HELM_SHAPE(2, 2, 1) HELM_SHAPE(2, 2, 2) HELM_SHAPE(2, 2, 4)
+    HELM_SHAPE(1, 3, 1) HELM_SHAPE(1, 3, 2) HELM_SHAPE(1, 3, 4)   // one box per stage
+    HELM_SHAPE(1, 2, 1) HELM_SHAPE(1, 2, 2) HELM_SHAPE(1, 2, 4)
+    default: return false;
   }
+#undef HELM_SHAPE
 }
 
 // Division by a divisor fixed at launch: n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31,
@@ -725,9 +761,15 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
 // box from row j * BX on, i.e. BX * 2 tk bytes further, a whole number of 8-row
 // swizzle atoms.  Stride-2 convolutions split their y-taps into even and odd classes
 // (element stride 2 along y); transposed stride-2 convolutions use their phase's taps.
-// A K-block stage therefore holds one input box only.
+// A stage holds the boxes of every x-tap of one (channel chunk, class) when two such stages
+// fit, else one box.  The producer writes, per stage slot, what the MMA thread needs (the
+// low descriptor words of A and B, the stage's shape, whether it starts or ends an item),
+// so the single MMA-issuing thread only waits, reads that record and issues the stage's
+// MMAs (x-taps x y-taps x K-steps, 18 for a 3x3 layer of 32 channels) as one straight-line
+// block: its own instruction latency, not the tensor pipe, bounded these layers.
 struct ReuseArgs {
   int nyt;        // y-taps one box serves at most (box height BY + nyt - 1)
+  int nxt;        // x-taps (boxes) one stage holds at most
   int bres;       // bytes of the resident weights (all taps x chunks, NT rows each)
 };
 
@@ -736,6 +778,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
                                                             ReuseArgs r) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], tfull[NACC], tempty[NACC], drain, wres;
+  // per stage slot, written by the producer before it arms the slot: low descriptor words of
+  // A and B, shape code | flags << 16 (1: first stage of an item, 2: last)
+  __shared__ uint4 sdesc[MAXST];
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ __align__(16) float s_mul[256], s_add[256];
@@ -744,7 +789,8 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
   const uint32_t wbase = (su32(smem) + 1023u) & ~1023u;          // resident weights
   const uint32_t base = wbase + (((uint32_t)r.bres + 1023u) & ~1023u);
   const int TK = a.tk;
-  const uint32_t stage = (uint32_t)((a.BY + r.nyt - 1) * a.BX * 2 * TK);
+  const uint32_t box = (uint32_t)((a.BY + r.nyt - 1) * a.BX * 2 * TK);   // one x-tap's input box
+  const uint32_t stage = box * (uint32_t)r.nxt;
   const uint32_t wtile = (uint32_t)N * 2 * TK;                    // one (tap, chunk) weight tile
   const int nch = a.nch0;
   if (tid == 0) {
@@ -790,24 +836,42 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
         const int nxt = tr ? it.ntx : a.k;
         const int nty = tr ? (a.k - it.ky0 + 1) / 2 : 0;
         bool ok = true;
+        const int kx0 = tr ? it.kx0 : 0, dkx = tr ? 2 : 1;
         for (int ch = 0; ch < nch && ok; ++ch)
           for (int cls = 0; cls < ncls && ok; ++cls)
-            for (int xt = 0; xt < nxt; ++xt, ++g) {
+            for (int xg = 0; xg < nxt; xg += r.nxt, ++g) {
+              const int nx = min(r.nxt, nxt - xg);
               const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
               const int s = (int)(g - use * (uint32_t)NS);
               if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
-              int ix, iy;
-              if (!tr) {
-                ix = it.x0 * a.stride + xt - a.pad;
-                iy = a.stride == 1 ? it.y0 - a.pad : 2 * it.y0 + cls - a.pad;
-              } else {
-                const int kx = it.kx0 + 2 * xt;
-                ix = it.x0 + (it.px + a.pad - kx) / 2;
-                iy = it.y0 + (it.py + a.pad - it.ky0) / 2 - (nty - 1);
-              }
               const uint32_t sA = base + (uint32_t)s * stage;
-              mb_expect_tx(su32(&full[s]), stage);
-              tma_load_4d(sA, &mA, ch * TK, ix, iy, it.b0, su32(&full[s]));
+              // what the MMA thread needs for this stage: box x = x-tap kx0 + dkx (xg + x), its
+              // y-taps j = 0 .. nj-1 (ky = ky0 + dky j) at box row j * BX (transposed: reversed)
+              {
+                const int nk4 = (min(TK, a.c0 - ch * TK) + 15) / 16;   // K-steps with real channels
+                const int nj = tr ? nty : (a.stride == 1 ? a.k : (a.k - cls + 1) / 2);
+                const int ky0 = tr ? it.ky0 : (a.stride == 1 ? 0 : cls);
+                const uint32_t a0 = tr ? sA + (uint32_t)(nty - 1) * (uint32_t)(a.BX * 2 * TK) : sA;
+                const uint32_t w0 = wbase + (uint32_t)((ky0 * a.k + kx0 + dkx * xg) * nch + ch) * wtile;
+                const uint32_t flags = (ch == 0 && cls == 0 && xg == 0 ? 1u : 0u) |
+                                       (ch == nch - 1 && cls == ncls - 1 && xg + r.nxt >= nxt ? 2u : 0u);
+                sdesc[s] = make_uint4(desc_lo(a0), desc_lo(w0),
+                                      (uint32_t)nx | ((uint32_t)nj << 4) | ((uint32_t)nk4 << 8) | (flags << 16), 0u);
+              }
+              mb_expect_tx(su32(&full[s]), box * (uint32_t)nx);
+              for (int x = 0; x < nx; ++x) {
+                const int xt = xg + x;
+                int ix, iy;
+                if (!tr) {
+                  ix = it.x0 * a.stride + xt - a.pad;
+                  iy = a.stride == 1 ? it.y0 - a.pad : 2 * it.y0 + cls - a.pad;
+                } else {
+                  const int kx = it.kx0 + 2 * xt;
+                  ix = it.x0 + (it.px + a.pad - kx) / 2;
+                  iy = it.y0 + (it.py + a.pad - it.ky0) / 2 - (nty - 1);
+                }
+                tma_load_4d(sA + (uint32_t)x * box, &mA, ch * TK, ix, iy, it.b0, su32(&full[s]));
+              }
             }
         if (!ok) { atomicExch(&s_fail, 1); break; }
       }
@@ -817,52 +881,55 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma_reuse(const __grid_constan
     }
   } else if (warp == WMMA) {
     if (lane == 0) {
-      const uint32_t id = idesc(N);
+      // one pass per stage, from the producer's stage records: wait for the stage, on an
+      // item's first stage also for its accumulator, issue the stage's MMAs as one block,
+      // release the stage, and on an item's last stage hand the accumulator to the epilogue
+      const uint32_t id = idesc(N), hi = desc_hi(TK);
+      const uint32_t rows = (uint32_t)(a.BX * 2 * TK) >> 4;           // one box row, 16-byte units
+      const uint32_t as = tr ? 0u - rows : rows, xs = box >> 4;
+      const int dky = a.stride == 1 && !tr ? 1 : 2, dkx = tr ? 2 : 1;
+      const uint32_t ws = ((uint32_t)(dky * a.k * nch) * wtile) >> 4, wxs = ((uint32_t)(dkx * nch) * wtile) >> 4;
+      const int items = (int)blockIdx.x < a.nitems ? (a.nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
       const bool wok = mb_wait(su32(&wres), 0);
       if (!wok) atomicExch(&s_fail, 1);
       uint32_t g = 0;
       int li = 0;
-      for (int w = blockIdx.x; w < a.nitems && wok && !failed(fail); w += gridDim.x, ++li) {
-        const Item it = decode(a, w);
+      uint32_t d = tmem;
+      while (wok && li < items && !failed(fail)) {
+        const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+        const int s = (int)(g - use * (uint32_t)NS);
+        if (!mb_wait(su32(&full[s]), use & 1u)) { atomicExch(&s_fail, 1); break; }
+        const uint4 q = sdesc[s];
+        const uint32_t flags = q.z >> 16, shape = q.z & 0xFFFFu;
         const int acc = li & (a.nacc - 1);
-        if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> a.lg_nacc) - 1) & 1u)) {
-          atomicExch(&s_fail, 1);
-          break;
+        if (flags & 1u) {
+          if (li >= a.nacc && !mb_wait(su32(&tempty[acc]), (uint32_t)((li >> a.lg_nacc) - 1) & 1u)) {
+            atomicExch(&s_fail, 1);
+            break;
+          }
+          d = tmem + (uint32_t)(acc * a.colsz);
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
-        const int nxt = tr ? it.ntx : a.k;
-        const int nty = tr ? (a.k - it.ky0 + 1) / 2 : 0;
-        bool ok = true, first = true;
-        for (int ch = 0; ch < nch && ok; ++ch)
-          for (int cls = 0; cls < ncls && ok; ++cls)
-            for (int xt = 0; xt < nxt; ++xt, ++g) {
-              const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
-              const int s = (int)(g - use * (uint32_t)NS);
-              if (!mb_wait(su32(&full[s]), use & 1u)) { ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-              const uint32_t sA = base + (uint32_t)s * stage;
-              const int kx = tr ? it.kx0 + 2 * xt : xt;
-              const int nk4 = (min(TK, a.c0 - ch * TK) + 15) / 16;   // K-steps with real channels
-              // y-taps served by this box: j = 0 .. nj-1 (ky = ky0 + dky j), box row j * BX
-              // (transposed: rows reversed)
-              const int nj = tr ? nty : (a.stride == 1 ? a.k : (a.k - cls + 1) / 2);
-              const int ky0 = tr ? it.ky0 : (a.stride == 1 ? 0 : cls), dky = a.stride == 1 && !tr ? 1 : 2;
-              const uint32_t rowb = (uint32_t)(a.BX * 2 * TK);
-              const uint32_t a0 = tr ? sA + (uint32_t)(nty - 1) * rowb : sA;
-              const uint32_t astep = tr ? 0u - rowb : rowb;
-              const uint32_t w0 = wbase + (uint32_t)((ky0 * a.k + kx) * nch + ch) * wtile;
-              const uint32_t wstep = (uint32_t)(dky * a.k * nch) * wtile;
-              mma_stage(nj, nk4, d, a0, astep, w0, wstep, TK, id, first ? 0u : 1u);
-              first = false;
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                               su32(&empty[s]))
-                           : "memory");
-            }
-        if (!ok) { atomicExch(&s_fail, 1); break; }
+        const uint32_t acc0 = (flags & 1u) ? 0u : 1u;
+        if (!mma_lo_shape(shape, d, q.x, as, xs, q.y, ws, wxs, hi, id, acc0)) {
+          const int nx = (int)(shape & 15u), nj = (int)((shape >> 4) & 15u), nk4 = (int)(shape >> 8);
+          for (int x = 0; x < nx; ++x)
+            for (int j = 0; j < nj; ++j)
+              for (int k = 0; k < nk4; ++k)
+                mma_lo(d, q.x + (uint32_t)x * xs + (uint32_t)j * as + 2u * k,
+                       q.y + (uint32_t)x * wxs + (uint32_t)j * ws + 2u * k, hi, id,
+                       (x == 0 && j == 0 && k == 0) ? acc0 : 1u);
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                         su32(&tfull[acc]))
+                         su32(&empty[s]))
                      : "memory");
+        if (flags & 2u) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                           su32(&tfull[acc]))
+                       : "memory");
+          ++li;
+        }
+        ++g;
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(&drain))
                    : "memory");
@@ -1193,10 +1260,15 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   const int es = (!tr && c.stride == 2) ? 2 : 1;
   const size_t bres = (size_t)c.k * c.k * nch * NT * 2 * tk;
   const size_t bres_al = (bres + 1023) / 1024 * 1024;
-  const size_t stage = (size_t)(BY + nyt - 1) * BX * 2 * tk;
-  // these layers are bound by MMA issue rather than loads: worth it only at two CTAs per SM
-  const int per_sm = 2;
-  if (bres_al + 3 * stage + 8 * 1024 > 112 * 1024) return false;
+  // boxes per stage: every x-tap of a (chunk, class) when two such stages fit next to the
+  // weights (their MMAs then issue as one block), else one box per stage
+  const size_t box = (size_t)(BY + nyt - 1) * BX * 2 * tk;
+  const int per_sm = 2;                            // two CTAs (two MMA-issuing threads) per SM
+  const size_t budget0 = (size_t)228 * 1024 / per_sm - 7 * 1024;
+  const int nxt_all = tr ? (c.k + 1) / 2 : c.k;
+  const int nxt = bres_al + 2 * box * nxt_all <= budget0 ? nxt_all : 1;
+  const size_t stage = box * nxt;
+  if (nxt == 1 && bres_al + 3 * stage + 8 * 1024 > 112 * 1024) return false;
   const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
   if (bres_al + 2 * stage > budget) return false;
   const int nst = (int)std::min<size_t>(MAXST, (budget - bres_al) / stage);
@@ -1245,6 +1317,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
            (!c.res || ((c.ldr % 8 == 0) && !((uintptr_t)c.res & 15)))) ? 1 : 0;
   ReuseArgs r;
   r.nyt = nyt;
+  r.nxt = nxt;
   r.bres = (int)bres;
   const int grid = std::min(a.nitems, sm_count() * per_sm);
   set_fdivs(a);
