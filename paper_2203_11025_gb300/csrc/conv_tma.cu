@@ -1254,23 +1254,35 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   const int BX = Wq < 16 ? Wq : 16, BY = 128 / BX;
   if (Hq < BY || (tr && (c.Wo % 2 || c.Ho % 2))) return false;
   const int NT = ((c.Cout + 15) / 16) * 16;
-  const int tk = conv_tk(c.c0, 0);
-  const int nch = (c.c0 + tk - 1) / tk;
   const int nyt = (!tr && c.stride == 1) ? c.k : (c.k + 1) / 2;
   const int es = (!tr && c.stride == 2) ? 2 : 1;
+  const int nxt_all = tr ? (c.k + 1) / 2 : c.k;
+  // Configuration, first that fits: (1) two CTAs per SM (two MMA-issuing threads), stages
+  // of every x-tap box of a (chunk, class) -- the stage's MMAs issue as one block; (2) the
+  // same with 32-channel chunks (half the box and stage), where the padded weight layout is
+  // the same; (3) one CTA per SM with merged stages (the whole shared memory for resident
+  // weights, e.g. 64 -> 64 channels); (4) two CTAs, one box per stage.
+  const int tk0 = conv_tk(c.c0, 0);
+  const int kpad0 = tk0 * ((c.c0 + tk0 - 1) / tk0);
+  int tk = 0, per_sm = 0, nxt = 0;
+  auto fits = [&](int t, int ps, int nx, int min_st) {
+    const int nc = (c.c0 + t - 1) / t;
+    if (t * nc != kpad0) return false;
+    const size_t br = ((size_t)c.k * c.k * nc * NT * 2 * t + 1023) / 1024 * 1024;
+    const size_t st = (size_t)(BY + nyt - 1) * BX * 2 * t * nx;
+    const size_t bud = (size_t)228 * 1024 / ps - 7 * 1024;
+    if (br + (size_t)min_st * st > bud) return false;
+    tk = t; per_sm = ps; nxt = nx;
+    return true;
+  };
+  if (!fits(tk0, 2, nxt_all, 2) && !(tk0 == 64 && fits(32, 2, nxt_all, 2)) && !fits(tk0, 1, nxt_all, 2) &&
+      !fits(tk0, 2, 1, 3))
+    return false;
+  const int nch = (c.c0 + tk - 1) / tk;
   const size_t bres = (size_t)c.k * c.k * nch * NT * 2 * tk;
   const size_t bres_al = (bres + 1023) / 1024 * 1024;
-  // boxes per stage: every x-tap of a (chunk, class) when two such stages fit next to the
-  // weights (their MMAs then issue as one block), else one box per stage
-  const size_t box = (size_t)(BY + nyt - 1) * BX * 2 * tk;
-  const int per_sm = 2;                            // two CTAs (two MMA-issuing threads) per SM
-  const size_t budget0 = (size_t)228 * 1024 / per_sm - 7 * 1024;
-  const int nxt_all = tr ? (c.k + 1) / 2 : c.k;
-  const int nxt = bres_al + 2 * box * nxt_all <= budget0 ? nxt_all : 1;
-  const size_t stage = box * nxt;
-  if (nxt == 1 && bres_al + 3 * stage + 8 * 1024 > 112 * 1024) return false;
+  const size_t stage = (size_t)(BY + nyt - 1) * BX * 2 * tk * nxt;
   const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
-  if (bres_al + 2 * stage > budget) return false;
   const int nst = (int)std::min<size_t>(MAXST, (budget - bres_al) / stage);
   const size_t smem = 1024 + bres_al + (size_t)nst * stage;
   static DeviceOnce once;   // per-device opt-in (kernel attributes hold per device)
