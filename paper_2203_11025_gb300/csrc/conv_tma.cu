@@ -174,6 +174,26 @@ __device__ __forceinline__ void mma_taps_k(int nk4, uint32_t d, uint32_t a0, uin
     default: mma_taps<NJ, 4>(d, a0, astep, w0, wstep, tk, id, acc0); break;
   }
 }
+
+// NB consecutive K-blocks of a stage (K-block b's A and B kstep bytes after K-block b - 1's),
+// NK4 K-steps each, as straight-line code.
+template <int NB, int NK4>
+__device__ __forceinline__ void mma_kblocks(uint32_t d, uint32_t a0, uint32_t b0, uint32_t kstep, int tk, uint32_t id,
+                                            uint32_t acc0) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    mma_taps<1, NK4>(d, a0 + (uint32_t)b * kstep, 0u, b0 + (uint32_t)b * kstep, 0u, tk, id, b == 0 ? acc0 : 1u);
+}
+__device__ __forceinline__ void mma_kblocks_n(int nb, int nk4, uint32_t d, uint32_t a0, uint32_t b0, uint32_t kstep,
+                                              int tk, uint32_t id, uint32_t acc0) {
+#define HELM_KB(NB, NK)                                                          \
+  if (nb == (NB) && nk4 == (NK)) { mma_kblocks<NB, NK>(d, a0, b0, kstep, tk, id, acc0); return; }
+  HELM_KB(2, 4) HELM_KB(3, 4) HELM_KB(2, 2) HELM_KB(3, 2)
+#undef HELM_KB
+  for (int b = 0; b < nb; ++b)
+    mma_taps_k<1>(nk4, d, a0 + (uint32_t)b * kstep, 0u, b0 + (uint32_t)b * kstep, 0u, tk, id, b == 0 ? acc0 : 1u);
+}
+
 // Low and high words of desc_k: the high word depends only on tk, the low word holds the
 // shared-memory address (16-byte units), so taps and K-steps step the low word alone.
 __device__ __forceinline__ uint32_t desc_lo(uint32_t saddr) { return ((saddr >> 4) & 0x3FFFu) | (1u << 16); }
@@ -257,6 +277,7 @@ struct TmaArgs {
   int kpad;                       // padded K per tap = tk (nch0 + nch1)
   int tk;                         // channels per K-chunk (stage row): 16, 32 or 64
   int nacc;                       // TMEM accumulator buffers (2 or 4; item i uses buffer i % nacc)
+  int kps;                        // general kernel: K-blocks per stage (> 1 only when every chunk is full)
   int epig;                       // epilogue: 1 = warp groups on alternate items, 0 = on alternate columns
   float* out; int ldo;
   const float* bias;
@@ -630,6 +651,9 @@ __device__ __forceinline__ void conv_epilogue(const TmaArgs& a, uint32_t tmem, u
 // item i in TMEM buffer i & 1, the epilogue warps drain buffer i & 1 while the MMAs
 // of item i + 1 run.
 // (two CTAs per SM for N <= 64 need <= 102 registers per thread at 320 threads)
+// GROUPED: a.kps K-blocks per stage (the instantiation without it keeps the one-K-block loops
+// only: the widest layers, which never group, measured 7 % slower with both in one kernel).
+template <bool GROUPED>
 __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CUtensorMap mA0,
                                                     const __grid_constant__ CUtensorMap mA1,
                                                     const __grid_constant__ CUtensorMap mB, TmaArgs a) {
@@ -643,7 +667,9 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
 
   const uint32_t base = (su32(smem) + 1023u) & ~1023u;
   const int TK = a.tk;
-  const uint32_t a_bytes = TM * 2 * TK, b_bytes = (uint32_t)N * 2 * TK, stage = a_bytes + b_bytes;
+  // a stage holds kps K-blocks, each an A box followed by its B tile
+  const uint32_t a_bytes = TM * 2 * TK, b_bytes = (uint32_t)N * 2 * TK, kbytes = a_bytes + b_bytes;
+  const uint32_t stage = GROUPED ? kbytes * (uint32_t)a.kps : kbytes;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) { mb_init(su32(&full[s]), 1); mb_init(su32(&empty[s]), 1); }
     for (int q = 0; q < a.nacc; ++q) {
@@ -680,22 +706,49 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
         // K-block kbeg + kb = (tap ty * ntx + tx, chunk ch), stepped without divisions
         int ch = it.kbeg % it.nchk, tap = it.kbeg / it.nchk;
         int ty = tap / it.ntx, tx = tap - ty * it.ntx;
-        for (int kb = 0; kb < it.nkb; ++kb, ++g) {
-          const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
-          const int s = (int)(g - use * (uint32_t)NS);
-          if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
-          const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
-          int ix, iy;
-          if (!a.transposed) { ix = it.x0 * a.stride + kx - a.pad; iy = it.y0 * a.stride + ky - a.pad; }
-          else { ix = it.x0 + (it.px + a.pad - kx) / 2; iy = it.y0 + (it.py + a.pad - ky) / 2; }
-          const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
-          mb_expect_tx(su32(&full[s]), stage);
-          if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, it.b0, su32(&full[s]));
-          else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : it.b0, su32(&full[s]));
-          tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, 0, su32(&full[s]));
-          if (++ch == it.nchk) {
-            ch = 0;
-            if (++tx == it.ntx) { tx = 0; ++ty; }
+        // one K-block per stage (the producer is on the critical path of the widest layers:
+        // its loop stays minimal there)
+        if constexpr (!GROUPED) {
+          for (int kb = 0; kb < it.nkb; ++kb, ++g) {
+            const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+            const int s = (int)(g - use * (uint32_t)NS);
+            if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
+            const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
+            int ix, iy;
+            if (!a.transposed) { ix = it.x0 * a.stride + kx - a.pad; iy = it.y0 * a.stride + ky - a.pad; }
+            else { ix = it.x0 + (it.px + a.pad - kx) / 2; iy = it.y0 + (it.py + a.pad - ky) / 2; }
+            const uint32_t sA = base + (uint32_t)s * stage, sB = sA + a_bytes;
+            mb_expect_tx(su32(&full[s]), kbytes);
+            if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, it.b0, su32(&full[s]));
+            else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : it.b0, su32(&full[s]));
+            tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, 0, su32(&full[s]));
+            if (++ch == it.nchk) {
+              ch = 0;
+              if (++tx == it.ntx) { tx = 0; ++ty; }
+            }
+          }
+        } else {
+          for (int kb = 0; kb < it.nkb; ++g) {
+            const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
+            const int s = (int)(g - use * (uint32_t)NS);
+            if (g >= (uint32_t)NS && !mb_wait(su32(&empty[s]), (use - 1) & 1u)) { ok = false; break; }
+            const int nb = min(a.kps, it.nkb - kb);
+            const uint32_t sA0 = base + (uint32_t)s * stage;
+            mb_expect_tx(su32(&full[s]), kbytes * (uint32_t)nb);
+            for (int b = 0; b < nb; ++b, ++kb) {
+              const int ky = it.ky0 + it.dk * ty, kx = it.kx0 + it.dk * tx;
+              int ix, iy;
+              if (!a.transposed) { ix = it.x0 * a.stride + kx - a.pad; iy = it.y0 * a.stride + ky - a.pad; }
+              else { ix = it.x0 + (it.px + a.pad - kx) / 2; iy = it.y0 + (it.py + a.pad - ky) / 2; }
+              const uint32_t sA = sA0 + (uint32_t)b * kbytes, sB = sA + a_bytes;
+              if (ch < a.nch0) tma_load_4d(sA, &mA0, ch * TK, ix, iy, it.b0, su32(&full[s]));
+              else tma_load_4d(sA, &mA1, (ch - a.nch0) * TK, ix, iy, a.bcast1 ? 0 : it.b0, su32(&full[s]));
+              tma_load_2d(sB, &mB, (ky * a.k + kx) * a.kpad + ch * TK, 0, su32(&full[s]));
+              if (++ch == it.nchk) {
+                ch = 0;
+                if (++tx == it.ntx) { tx = 0; ++ty; }
+              }
+            }
           }
         }
         if (!ok) { atomicExch(&s_fail, 1); break; }
@@ -718,16 +771,26 @@ __global__ void __launch_bounds__(NTHR, 2) k_conv_tma(const __grid_constant__ CU
         const uint32_t d = tmem + (uint32_t)(acc * a.colsz);
         bool ok = true;
         int kch = it.kbeg % it.nchk;   // chunk of K-block kbeg + kb, stepped below
-        for (int kb = 0; kb < it.nkb; ++kb, ++g, kch = (kch + 1 == it.nchk) ? 0 : kch + 1) {
+        for (int kb = 0; kb < it.nkb; ++g) {
           const uint32_t use = (uint32_t)fdiv(a.f_ns, (int)g);
           const int s = (int)(g - use * (uint32_t)NS);
           if (!mb_wait(su32(&full[s]), use & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t sA = base + (uint32_t)s * stage;
-          // K-steps of 16 that hold real channels (the rest of a chunk is zero fill)
-          const int cval = kch < a.nch0 ? min(TK, a.c0 - kch * TK) : min(TK, a.c1 - (kch - a.nch0) * TK);
-          const int nk4 = (cval + 15) / 16;
-          mma_taps_k<1>(nk4, d, sA, 0u, sA + a_bytes, 0u, TK, id, kb > 0 ? 1u : 0u);
+          const uint32_t acc0 = kb > 0 ? 1u : 0u;
+          if constexpr (GROUPED) {
+            // every chunk full: TK / 16 K-steps per K-block, the stage's K-blocks as one block
+            const int nb = min(a.kps, it.nkb - kb);
+            mma_kblocks_n(nb, TK / 16, d, sA, sA + a_bytes, kbytes, TK, id, acc0);
+            kb += nb;
+          } else {
+            // K-steps of 16 that hold real channels (the rest of a chunk is zero fill)
+            const int cval = kch < a.nch0 ? min(TK, a.c0 - kch * TK) : min(TK, a.c1 - (kch - a.nch0) * TK);
+            const int nk4 = (cval + 15) / 16;
+            mma_taps_k<1>(nk4, d, sA, 0u, sA + a_bytes, 0u, TK, id, acc0);
+            kch = kch + 1 == it.nchk ? 0 : kch + 1;
+            ++kb;
+          }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               su32(&empty[s]))
               : "memory");
@@ -1316,6 +1379,7 @@ bool launch_reuse(const ConvArgs& c, int* err, cudaStream_t s) {
   a.nst = nst;
   a.colsz = NT <= 32 ? 32 : 64;
   a.nacc = NACC;                                     // 4 x <= 64 columns per CTA, two CTAs per SM
+  a.kps = 1;
   a.epig = 1;
   a.kpad = kpad;
   a.tk = tk;
@@ -1424,18 +1488,28 @@ bool conv_forward_tma(const ConvArgs& c, int* err, cudaStream_t s) {
   // reserved, 4 KB of static barriers and epilogue constants, 1 KB alignment slack, 1 KB
   // margin): 4-8 stages
   const int per_sm = ctas_per_sm(a.NT);
-  const size_t stage = ((size_t)TM + a.NT) * 2 * tk;
+  const size_t kbytes = ((size_t)TM + a.NT) * 2 * tk;
   const size_t budget = (size_t)228 * 1024 / per_sm - 7 * 1024;
+  // K-blocks per stage when every chunk is full (the MMA thread then issues them as one
+  // block behind one wait and one commit): as many (up to 3) as leave three stages
+  a.kps = 1;
+  if (c.c0 % tk == 0 && (!c.in1 || c.c1 % tk == 0))
+    for (int k = 3; k >= 2; --k)
+      if (budget / (kbytes * k) >= 3) { a.kps = k; break; }
+  const size_t stage = kbytes * a.kps;
   a.nst = (int)std::min<size_t>(MAXST, budget / stage);
   if (a.nst < 2) TMA_REJECT("shared memory");
   const size_t smem = (size_t)a.nst * stage + 1024;
   // dynamic shared memory opt-in: the per-block limit less the kernel's static barriers
   static DeviceOnce once;   // per-device opt-in (kernel attributes hold per device)
-  const long long max_dyn = opt_in_dynamic_smem(once, k_conv_tma);
+  static DeviceOnce once_g;
+  const long long max_dyn = a.kps > 1 ? opt_in_dynamic_smem(once_g, k_conv_tma<true>)
+                                      : opt_in_dynamic_smem(once, k_conv_tma<false>);
   if ((long long)smem > max_dyn) TMA_REJECT("shared memory");
   const int grid = std::min(a.nitems, sm_count() * per_sm);
   set_fdivs(a);
-  launch_pdl(k_conv_tma, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
+  if (a.kps > 1) launch_pdl(k_conv_tma<true>, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
+  else launch_pdl(k_conv_tma<false>, dim3(grid), dim3(NTHR), smem, s, mA0, mA1, mB, a);
   if (a.ksplit > 1 && !a.cnt) {
     const int M = c.B * c.Ho * c.Wo;
     const size_t n4 = (size_t)M * (c.Cout / 4);
