@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(NT) k_arnoldi_project2(Op<float> op, const flo
 }
 
 template <int JB>
-__global__ void __launch_bounds__(NT) k_arnoldi_update2(const float2* __restrict__ V, size_t vstride,
+__device__ __forceinline__ void arnoldi_update2(const float2* __restrict__ V, size_t vstride,
                                                         float2* __restrict__ wbase, unsigned N, ArnoldiState st, int j,
                                                         int nb, int write_next, int only_update) {
   const int rhs = blockIdx.y;
@@ -609,6 +609,23 @@ __global__ void __launch_bounds__(NT) k_arnoldi_update2(const float2* __restrict
   const double nu2 = tot[j + 1].x - s;
   Hw[(size_t)(j + 1) * m + j] = d2(nu2 > 0.0 ? sqrt(nu2) : 0.0, 0);
   givens_step(st, rhs, j);
+}
+
+template <int JB>
+__global__ void __launch_bounds__(NT) k_arnoldi_update2(const float2* __restrict__ V, size_t vstride,
+                                                        float2* __restrict__ wbase, unsigned N, ArnoldiState st, int j,
+                                                        int nb, int write_next, int only_update) {
+  arnoldi_update2<JB>(V, vstride, wbase, N, st, j, nb, write_next, only_update);
+}
+// The same sweep held to 80 registers (three blocks per SM instead of two at 5-8 basis
+// vectors): more bytes in flight on the fine grid's long vectors (852 -> 720 us at
+// 2048^2 x 16, j = 4); the coarsest solve's short vectors measured slower that way (fewer,
+// unevenly filled waves), and at 1-4 vectors the free form already uses 60 registers.
+template <int JB>
+__global__ void __launch_bounds__(NT, 3) k_arnoldi_update2_occ(const float2* __restrict__ V, size_t vstride,
+                                                               float2* __restrict__ wbase, unsigned N, ArnoldiState st,
+                                                               int j, int nb, int write_next, int only_update) {
+  arnoldi_update2<JB>(V, vstride, wbase, N, st, j, nb, write_next, only_update);
 }
 
 template <int JB>
@@ -869,8 +886,16 @@ void launch_arnoldi(const Op<T>& op, bool diag_precond, const void* z, void* V, 
           k_arnoldi_project2<decltype(bc)::value, JB, false><<<dim3(nb, nrhs), NT, 0, s>>>(
               opf, (const float2*)z, (const float2*)V, vstride, w, st, j, nb);
       });
-      k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb,
-                                                          write_next, 0);
+      bool occ = false;
+      if constexpr (JB == 8) {
+        occ = !diag_precond;
+        if (occ)
+          k_arnoldi_update2_occ<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j,
+                                                                  nb, write_next, 0);
+      }
+      if (!occ)
+        k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb,
+                                                            write_next, 0);
       if (write_next)
         k_arnoldi_finish2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, w, (unsigned)N, st, j, nb);
     });
@@ -903,8 +928,12 @@ void launch_arnoldi_sweep(int which, const Op<T>& op, const void* z, void* V, si
               opf, (const float2*)z, (const float2*)V, vstride, (float2*)w, st, j, nb);
         });
       else
-        k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, (float2*)w, (unsigned)N, st,
-                                                            j, nb, 0, 1);
+        if constexpr (JB == 8)
+          k_arnoldi_update2_occ<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, (float2*)w, (unsigned)N,
+                                                                  st, j, nb, 0, 1);
+        else
+          k_arnoldi_update2<JB><<<dim3(nb, nrhs), NT, 0, s>>>((const float2*)V, vstride, (float2*)w, (unsigned)N, st,
+                                                              j, nb, 0, 1);
     } else if (which == 0) {
       auto ka = op.order == 4 ? k_arnoldi_project<T, 4, JB> : k_arnoldi_project<T, 2, JB>;
       ka<<<dim3(nb, nrhs), NT, 0, s>>>(op, 0, (const T2*)z, (const T2*)V, vstride, w, st, j, nb);

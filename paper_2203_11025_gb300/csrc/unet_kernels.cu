@@ -546,8 +546,10 @@ __global__ void k_f32_to_bf16(const float* __restrict__ s, __nv_bfloat16* __rest
 // Network input from complex residuals (Sec. 3.4): channels (Re, Im) of h^2 r / s with
 // s = RMS(h^2 r) per sample, then kappa^2 and gamma.  Two passes over many blocks:
 // per-block partial sums of |r|^2, then every block of the writer sums its sample's
-// partials (fixed order) and writes the 8-channel BF16 input (channels 4..7 zero).
-constexpr int kInBlocks = 64;
+// partials (one warp, fixed order) and writes the BF16 input.  kInBlocks blocks per sample:
+// enough loads in flight for these HBM-bound sweeps at a few samples per pass (64 blocks
+// per sample left them at about 1 TB/s).
+constexpr int kInBlocks = 256;
 
 template <typename T2>
 __global__ void __launch_bounds__(256) k_input_partial(const T2* __restrict__ r, int N, float* __restrict__ part,
@@ -587,12 +589,16 @@ __global__ void __launch_bounds__(256) k_input_write(const T2* __restrict__ r, i
   if (gate && !gate[b]) return;
   if (rpp > 0) k2 += (size_t)((b0 + b) / rpp) * N;   // this right-hand side's medium (a batch of problems)
   __shared__ float s_scale;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // lane l adds partials l, l + 32, ...; then a fixed shuffle tree
     double t = 0.0;
-    for (int i = 0; i < kInBlocks; ++i) t += part[b * kInBlocks + i];
-    const float rms = (float)(sqrt(t / N) * h2);
-    s_scale = rms > 0.f ? rms : 1.f;
-    if (blockIdx.x == 0) sc[b] = s_scale;
+    for (int i = threadIdx.x; i < kInBlocks; i += 32) t += part[b * kInBlocks + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) {
+      const float rms = (float)(sqrt(t / N) * h2);
+      s_scale = rms > 0.f ? rms : 1.f;
+      if (blockIdx.x == 0) sc[b] = s_scale;
+    }
   }
   __syncthreads();
   const float f = (float)h2 / s_scale;
