@@ -368,11 +368,21 @@ __device__ __forceinline__ float2 op_at(const Op<float>& op, int x, int y, float
   return k;
 }
 
-// Rows of a strip away from every boundary and the absorbing layer (warp-uniform test):
-// there g = 0, no neighbour is outside the grid and no boundary mode applies, so the
-// diagonal and the stencil take their plain forms.
+// Rows of a strip away from every boundary and the absorbing layer: there g = 0, no
+// neighbour is outside the grid and no boundary mode applies, so the diagonal and the
+// stencil take their plain forms (for the strip of 64 columns from xs; the test is uniform
+// over a warp).  strip_interior_cols: the strip's columns qualify (tested once per strip);
+// strip_interior_row: row y does (from the kernel parameters, no registers held);
+// strip_interior: both, tested per row.
+__device__ __forceinline__ int interior_margin(const Op<float>& op) { return op.abc_w > 1 ? op.abc_w : 1; }
+__device__ __forceinline__ bool strip_interior_cols(const Op<float>& op, int xs) {
+  return xs >= interior_margin(op) && xs + 63 < op.nx - interior_margin(op);
+}
+__device__ __forceinline__ bool strip_interior_row(const Op<float>& op, int y) {
+  return y >= interior_margin(op) && y < op.ny - interior_margin(op);
+}
 __device__ __forceinline__ bool strip_interior(const Op<float>& op, int xs, int y) {
-  const int A = op.abc_w > 1 ? op.abc_w : 1;
+  const int A = interior_margin(op);
   return y >= A && y < op.ny - A && xs >= A && xs + 63 < op.nx - A;
 }
 __device__ __forceinline__ float2 diag_plain(const Op<float>& op, float k2) {
@@ -435,11 +445,12 @@ __global__ void __launch_bounds__(32 * kStripWarps, 8) k_resid_restrict_m(Op<flo
   const float2* vr = HAS_V ? v + (size_t)rhs * N : nullptr;
   const int I0 = blockIdx.y * TI;
   const int ys = 2 * I0 - 2;                       // fine row of ring index 0
+  const bool incols = strip_interior_cols(op, xs);
   auto issue = [&](int i) {
     if (i < R) {
       const int yy = ys + i, sl = i % kRing;
       const bool ok = colin && yy >= 0 && yy < ny;
-      const size_t p = ok ? (size_t)yy * nx + c0 : 0;
+      const int p = ok ? yy * nx + c0 : 0;         // one right-hand side holds < 2^31 nodes
       row_cp16(&s_f[wi][sl][lane], fr + p, ok);
       row_cp8(&s_k[wi][sl][lane], op.k2 + p, ok);
       if (HAS_V) row_cp16(&s_v[HAS_V ? wi : 0][sl][lane], vr + p, ok);
@@ -447,7 +458,7 @@ __global__ void __launch_bounds__(32 * kStripWarps, 8) k_resid_restrict_m(Op<flo
     row_commit();
   };
   // ring row i: f, v (or w D^-1 f), the diagonal of both columns and whether the row is
-  // interior (strip_interior)
+  // interior (strip_interior_cols and strip_interior_row)
   auto take = [&](int i, CPair& ff, CPair& vv, CPair& dd, bool& in) {
     row_wait();
     const int yy = ys + i, sl = i % kRing;
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(32 * kStripWarps, 8) k_resid_restrict_m(Op<flo
     const float2 k = s_k[wi][sl][lane];
     vv = HAS_V ? cp_of(s_v[HAS_V ? wi : 0][sl][lane]) : cp_zero();
     dd = cp_zero();
-    in = strip_interior(op, xs, yy);
+    in = incols && strip_interior_row(op, yy);
     if (colin && yy >= 0 && yy < ny) {
       if (in) {
         dd.a = diag_plain(op, k.x);
