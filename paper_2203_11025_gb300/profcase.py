@@ -2,6 +2,7 @@
 
   python -m paper_2203_11025_gb300.profcase unet 256 8     # one U-Net forward, 8 images of 256^2
   python -m paper_2203_11025_gb300.profcase coarse 256 8   # one coarsest-grid solve (fine grid 256^2, 8 RHS)
+  python -m paper_2203_11025_gb300.profcase hbm 2048 16    # per-launch time and GB/s of the HBM-bound kernels
   python -m paper_2203_11025_gb300.profcase layers 256 8   # per-layer times of the U-Net forward
   python -m paper_2203_11025_gb300.profcase mvu 256 8      # one FGMRES(10) restart cycle with M_VU
                                                            # (profiler range = that cycle)
@@ -50,6 +51,18 @@ def main(argv):
                 kind = {3: "direct", 2: "tma-tc", 1: "cpasync-tc"}.get(tc, "cuda-core")
                 print(f"{nm:12s} {ms * 1e3:8.1f} us {fl / ms / 1e9:7.1f} TFLOP/s {kind}")
             print(f"total {tot * 1e3:.1f} us")
+    elif what == "hbm":
+        # per-launch device time and algorithmic bandwidth of the HBM-bound kernels
+        # (helm_time_kernel: 0 apply, 1 residual + restriction, 2 prolongation + Jacobi,
+        # 3 Arnoldi update sweep at j = 4, 6 projection sweep at j = 4; 4 V-cycle, 5 coarsest solve)
+        import json
+        k2 = synth.grf_kappa2(n, n, 1000)
+        hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
+        rec = {"n": n, "nrhs": b}
+        for kern in (0, 1, 2, 3, 6, 4, 5):
+            ms, by = hz.time_kernel(kern, b, reps=10)
+            rec[str(kern)] = {"us": round(ms * 1e3, 1), "GB/s": round(by / ms / 1e6, 0) if by else None}
+        print(json.dumps(rec))
     elif what == "coarse":
         k2 = synth.grf_kappa2(n, n, 1000)
         hz = lib.Helmholtz(torch.from_numpy(k2).cuda())
