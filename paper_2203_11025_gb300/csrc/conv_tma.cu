@@ -1545,6 +1545,10 @@ struct WgArgs {
   uint32_t lbo, sbo;          // MN-major descriptor strides (bytes)
   int vec;                    // gW rows 16-byte aligned (float4 atomics)
   float* gW;
+  // deterministic sums: item (tap, block, chunk) stores its tile to part + chunk * pstride
+  // ([tap][cin][cout]) and a second launch adds the chunks in order; null: vector atomics
+  float* part;
+  size_t pstride;
   int* err;
 };
 
@@ -1563,7 +1567,7 @@ __host__ __device__ constexpr uint32_t idesc_mn(int m, int n) {
          ((uint32_t)(m >> 4) << 24);
 }
 
-struct WgItem { int tap, mb, kb0, nkb; };
+struct WgItem { int tap, mb, kb0, nkb, chunk; };
 
 __device__ __forceinline__ WgItem wg_decode(const WgArgs& a, int w) {
   WgItem it;
@@ -1573,6 +1577,7 @@ __device__ __forceinline__ WgItem wg_decode(const WgArgs& a, int w) {
   const int KB = a.B * a.tx * a.ty;
   it.kb0 = (int)((long long)chunk * KB / a.nchunks);
   it.nkb = (int)((long long)(chunk + 1) * KB / a.nchunks) - it.kb0;
+  it.chunk = chunk;
   return it;
 }
 
@@ -1698,7 +1703,16 @@ __global__ void __launch_bounds__(WG_THR, 1) k_wgrad_tma(const __grid_constant__
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (ci >= a.cin || it.nkb <= 0) continue;
+        if (ci >= a.cin) continue;
+        if (a.part) {
+          // this chunk's tile, plain stores (zero when the chunk holds no K-blocks)
+          float* prow = a.part + (size_t)it.chunk * a.pstride + ((size_t)it.tap * a.cin + ci) * a.cout;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < a.cout) prow[c0 + j] = it.nkb > 0 ? __uint_as_float(v[j]) : 0.f;
+          continue;
+        }
+        if (it.nkb <= 0) continue;
         if (vec && c0 + 16 <= a.cout) {
           float4* op = reinterpret_cast<float4*>(row + c0);
 #pragma unroll
@@ -1725,6 +1739,19 @@ __global__ void __launch_bounds__(WG_THR, 1) k_wgrad_tma(const __grid_constant__
   }
 }
 
+// gW[(tap * cin_tot + ci) * cout + co] += sum over chunks c = 0, 1, ... (in this order) of
+// part[c * pstride + (tap * cin + ci) * cout + co].
+__global__ void k_wgrad_reduce(const float* __restrict__ part, size_t pstride, int nchunks, int taps, int cin,
+                               int cout, int cin_tot, float* __restrict__ gW) {
+  const size_t n = (size_t)taps * cin * cout;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float t = 0.f;
+    for (int c = 0; c < nchunks; ++c) t += part[(size_t)c * pstride + e];
+    const size_t tap = e / ((size_t)cin * cout), r = e - tap * cin * cout;
+    gW[(tap * cin_tot) * cout + r] += t;
+  }
+}
+
 // MN-major descriptor strides: (LBO, SBO) = (channel-atom stride, 8-pixel-group stride)
 // when wg_desc_order == 0, swapped otherwise.
 int g_wg_desc_order = 0;
@@ -1736,7 +1763,7 @@ void conv_wgrad_tma_set_desc_order(int order) { g_wg_desc_order = order; }
 // dW += weight gradient of the forward convolution c (single BF16 source, no on-load
 // activation) from g = dL/dy (BF16 [pixels][Cout], ld ldg).  False: not eligible.
 bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s,
-                    int cin_total, bool launch) {
+                    int cin_total, bool launch, float* scratch, size_t scratch_cap) {
   if (c.in1 || c.in_act || c.in_f32 || c.Cout > 256 || c.ld0 % 8 || ldg % 8) return false;
   if (c.k != 3 && c.k != 5) return false;
   if (!get_encoder()) return false;
@@ -1798,8 +1825,16 @@ bool conv_wgrad_tma(const ConvArgs& c, const __nv_bfloat16* g, int ldg, float* g
       return false;
   }
   if (!launch) return true;
+  // deterministic sums when the scratch holds every chunk's tiles
+  const size_t pstride = (size_t)taps * c.c0 * c.Cout;
+  a.part = scratch && (size_t)a.nchunks * pstride <= scratch_cap ? scratch : nullptr;
+  a.pstride = pstride;
   const int grid = std::min(a.nitems, slots);
   k_wgrad_tma<<<grid, WG_THR, smem, s>>>(mX, mG, a);
+  if (a.part) {
+    const int rb = (int)std::min<size_t>((pstride + 255) / 256, (size_t)sm_count() * 8);
+    k_wgrad_reduce<<<rb, 256, 0, s>>>(a.part, pstride, a.nchunks, taps, c.c0, c.Cout, a.cin_tot, gW);
+  }
   return true;
 }
 

@@ -492,8 +492,9 @@ bool wgrad_two_sources(unet_ctx* n, const ConvL& cl, const ConvArgs& fa, const f
     batch_sum(g, ldg, n->B, P, cl.cout, n->gsum, cl.cout, false, s);
     to_bf16_slice(n->gsum, cl.cout, n->gsum_bf, ldgb, cl.cout, (int)P, s);
   }
-  conv_wgrad_tma(t0, n->gbf, ldgb, gW, n->d_err, s, cin, true);
-  conv_wgrad_tma(t1, g1, ldgb, gW + (size_t)fa.c0 * cl.cout, n->d_err, s, cin, true);
+  conv_wgrad_tma(t0, n->gbf, ldgb, gW, n->d_err, s, cin, true, n->splitbuf, (size_t)n->splitcnt_n);
+  conv_wgrad_tma(t1, g1, ldgb, gW + (size_t)fa.c0 * cl.cout, n->d_err, s, cin, true, n->splitbuf,
+                 (size_t)n->splitcnt_n);
   return true;
 }
 
@@ -507,7 +508,8 @@ void backprop_conv(unet_ctx* n, const ConvL& cl, ConvArgs fa, const float* g, in
     ConvArgs t = fa;
     if (t.in_act && act_src && !t.in1) { t.in0 = act_src; t.ld0 = t.c0; t.in_act = 0; }
     const bool done = fa.in1 ? wgrad_two_sources(n, cl, fa, g, ldg, gW, Hg, Wg, act_src, act_ctx, s)
-                             : conv_wgrad_tma(t, n->gbf, gbf_ld(cl.cout), gW, n->d_err, s);
+                             : conv_wgrad_tma(t, n->gbf, gbf_ld(cl.cout), gW, n->d_err, s, 0, true, n->splitbuf,
+                                              (size_t)n->splitcnt_n);
     if (!done) conv_wgrad(fa, g, ldg, gW, s);
   } else {
     conv_wgrad(fa, g, ldg, gW, s);

@@ -73,9 +73,11 @@ void conv_tma_weights_subpixel(const float* P, __nv_bfloat16* WS, int c0, int c1
 // Weight gradient of source 0 of a (a.in1 must be null) added into gW on the tensor cores;
 // cin_total: input channels of the whole layer (rows of one tap in gW; 0: a.c0), so that a
 // second source's gradient can start at gW + c0 * Cout.  launch = false only checks that the
-// layer qualifies.  Returns false (nothing launched) when it does not.
+// layer qualifies.  Returns false (nothing launched) when it does not.  scratch (capacity
+// scratch_cap floats): when it holds every pixel chunk's tile, the chunks are summed in a
+// fixed order by a second launch (bit-reproducible gradients); else with atomics.
 bool conv_wgrad_tma(const ConvArgs& a, const __nv_bfloat16* g, int ldg, float* gW, int* err, cudaStream_t s,
-                    int cin_total = 0, bool launch = true);
+                    int cin_total = 0, bool launch = true, float* scratch = nullptr, size_t scratch_cap = 0);
 void conv_wgrad_tma_set_desc_order(int order);
 void conv_tma_weights_adjoint(const float* P, __nv_bfloat16* WPA, int k, int cin, int cout, bool flip, cudaStream_t s);
 const char* conv_tma_last_reject();      // why the last conv_forward_tma call declined ("" if it launched)   // > 1: the TMA path splits K (FP32 atomics, no fused epilogue)

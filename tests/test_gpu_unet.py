@@ -645,6 +645,27 @@ def test_trained_network_gains_over_plain_sl(lib):
         assert np.linalg.norm(H.residual(prob.A, b[k], x[k])) <= 1e-7 * np.linalg.norm(b[k])
 
 
+def test_weight_gradients_are_bit_reproducible(lib):
+    """The default network's training step at 16 x 256^2 (the benchmark's base-training batch):
+    forward in training mode, MSE, backward -- twice from the same weights and batch -- gives
+    bit-identical gradients (the weight gradients' pixel chunks are summed in a fixed order,
+    not with atomics), so a training run is reproducible."""
+    net = lib.UNet(lib.unet_cfg_default(lib.UNET_STANDALONE), seed=5)
+    rng = np.random.default_rng(6)
+    x = cuda(rng.standard_normal((16, 256, 256, 4)))
+    t = cuda(rng.standard_normal((16, 256, 256, 2)))
+    grads = []
+    for _ in range(2):
+        net.zero_grad()
+        o = net.forward(x, train=True)
+        _, g = net.mse(o, t)
+        net.backward(g)
+        grads.append(np.array(net.get_grads()))
+    assert not net.status()
+    assert np.all(np.isfinite(grads[0])) and np.abs(grads[0]).max() > 0
+    assert np.array_equal(grads[0], grads[1])
+
+
 def test_trained_encoder_solver_gains_over_plain_sl(lib):
     """The encoder-solver pair of Sec. 3.3 with the library's default widths, trained jointly
     (Eq. 3.7 MSE, Adam) on Eq. 3.8-3.9 pairs of one 256^2 medium, the encoder run once for the
