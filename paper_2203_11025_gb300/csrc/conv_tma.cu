@@ -33,6 +33,7 @@
 #include <utility>
 
 #include "devonce.cuh"
+#include "fdiv.h"
 #include "pdl.cuh"
 #include "unet_internal.cuh"
 
@@ -244,20 +245,6 @@ __device__ __forceinline__ bool mma_lo_shape(uint32_t shape, uint32_t d, uint32_
     default: return false;
   }
 #undef HELM_SHAPE
-}
-
-// Division by a divisor fixed at launch: n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31,
-// with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1 (the round-up multiplier of
-// Granlund and Montgomery, "Division by invariant integers using multiplication", 1994).
-struct FDiv { uint32_t d, m, s; };
-inline FDiv make_fdiv(uint32_t d) {
-  uint32_t s = 0;
-  while ((1ull << s) < d) ++s;
-  const uint64_t m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
-  return {d, (uint32_t)m, s};
-}
-__device__ __forceinline__ int fdiv(const FDiv& f, int n) {
-  return (int)((__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.s);
 }
 
 struct TmaArgs {
